@@ -1,0 +1,357 @@
+"""Plain FP64 CPU oracle for ConKer's hot path (arXiv 2108.00015).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module.  The library
+(C-ABI + CUDA kernels) never imports, links or calls it, and it shares no code,
+table or constant with that library.
+
+What it computes, in the paper's order and notation (Sec. 2):
+
+* mapping (Sec. 2.2): histograms D, R of tracer counts per cubic cell of side
+  g_s; R normalised to the data total, alpha = sum D / sum R; the density
+  variation N = D - alpha R (Eq. 8) and the normalised random field
+  Rt = alpha R;
+* kernels (Sec. 2.3): the spherical-shell kernel K_s as a list of integer cell
+  offsets m (K_s(m) = 1 on the list, 0 elsewhere);
+* convolution (Sec. 2.4): W_s(r) = sum_m K_s(m) N(r + m) (Eq. 9, the inner
+  product of the kernel centred on cell r with N), B_s the same for Rt
+  (Eq. 10), and W_0 = N, B_0 = Rt;
+* summation (Sec. 2.5): for every multiset s_1 <= ... <= s_{n-1}
+  num = sum_r W_0 prod_i W_{s_i}, den = sum_r B_0 prod_i B_{s_i},
+  xi_n = num / den (Eqs. 11-13); the equidistant diagonal (Eq. 14).
+
+Equation numbers count the paper's numbered displays in order:
+(1) Delta, (2) the xi_n integral, (3) r(z), (4)-(6) X, Y, Z, (7) factorised
+randoms, (8) N = D - R, (9) W_i = N***K_i, (10) B_i = R***K_i, (11) xi_n,
+(12) xi_2, (13) xi_3, (14) xi_n diagonal, (15)-(17) continuous field,
+(18) Landy-Szalay, (19) combined regions.
+
+Readings where the paper is silent or ambiguous (each is a choice):
+
+1. Cell assignment (Sec. 2.2 says "histogram"): nearest-grid-point; a point x
+   is in cell k of an axis iff e_k <= x < e_{k+1} with the edge
+   e_k = fl64(origin + fl64(k * g)) compared exactly against the float32
+   coordinate.  Periodic grids take k mod n; otherwise points with k outside
+   [0, n) are dropped and counted.
+2. Shell membership (Sec. 2.3, "cells intersected by a sphere of radius s_i",
+   and the bins of width w of Sec. 3): rule "center_bin" (default) keeps the
+   offset m iff (s - w/2) <= |m| g < (s + w/2), distances between cell
+   centres, compared as squares in FP64; rule "intersect" keeps m iff the
+   sphere of radius s meets the closed cell cube: dmin^2 <= s^2 < dmax^2.
+3. The kernel cube is centred on a cell (Fig. 3 puts the result in the
+   centre cell), so offsets run over all integer m, not a cube of even side.
+4. Boundaries: a periodic grid uses circular index arithmetic (valid while
+   2 max|m_i| < n_i); a non-periodic grid treats cells outside the box as 0.
+5. alpha = sum D / sum R over the histograms (the data total N_tot of
+   Sec. 2.2 counts the gridded points).
+6. Multisets with repetition (the diagonal of Eq. 14 is part of the tensor).
+7. A non-positive denominator gives xi = NaN for that entry.
+
+Pins: see tests/test_oracle_pins.py (brute-force pair and triplet counts on
+cell-centred points, three-square lattice counts, closed forms, symmetry,
+translation invariance, linearity, region additivity, direct vs FFT engine).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from typing import Dict, Iterable, List, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "cell_edge", "cell_index", "grid_counts", "density_fields", "shell_offsets",
+    "check_periodic_support", "kernel_grid", "convolve_direct", "convolve_fft",
+    "w_at_cells", "multisets", "product_sums", "dense_tensor", "xi_from",
+    "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok",
+]
+
+
+# ---------------------------------------------------------------------------
+# Mapping (Sec. 2.2, Eq. 8)
+
+def cell_edge(origin: float, cell: float, k) -> np.ndarray:
+    """Lower edge of cell k on one axis: fl64(origin + fl64(k * cell))."""
+    k = np.asarray(k, dtype=np.float64)
+    return np.float64(origin) + k * np.float64(cell)
+
+
+def cell_index(x: np.ndarray, origin: float, cell: float) -> np.ndarray:
+    """The unique integer k with cell_edge(k) <= x < cell_edge(k + 1)
+    (reading 1), for float32 coordinates ``x``; returns int64."""
+    xd = np.asarray(x, dtype=np.float32).astype(np.float64)
+    k = np.floor((xd - origin) / cell).astype(np.int64)
+    for _ in range(8):
+        lo = xd < cell_edge(origin, cell, k)
+        hi = xd >= cell_edge(origin, cell, k + 1)
+        if not (lo.any() or hi.any()):
+            return k
+        k = k - lo.astype(np.int64) + hi.astype(np.int64)
+    raise AssertionError("cell_index did not settle")
+
+
+def grid_counts(x, y, z, grid) -> Tuple[np.ndarray, int]:
+    """Histogram of points per cell, shape (nz, ny, nx) uint32, and the number
+    of points dropped outside a non-periodic grid (Sec. 2.2, reading 1)."""
+    nx, ny, nz = (int(v) for v in grid.n)
+    ks = []
+    for coord, o, n in ((x, grid.origin[0], nx), (y, grid.origin[1], ny), (z, grid.origin[2], nz)):
+        k = cell_index(coord, o, grid.cell)
+        ks.append(np.mod(k, n) if grid.periodic else k)
+    kx, ky, kz = ks
+    if grid.periodic:
+        keep = np.ones(kx.shape, dtype=bool)
+    else:
+        keep = (kx >= 0) & (kx < nx) & (ky >= 0) & (ky < ny) & (kz >= 0) & (kz < nz)
+    dropped = int(kx.size - int(keep.sum()))
+    flat = (kz[keep] * ny + ky[keep]) * nx + kx[keep]
+    counts = np.bincount(flat, minlength=nx * ny * nz)
+    assert counts.max(initial=0) < 2 ** 32
+    return counts.astype(np.uint32).reshape(nz, ny, nx), dropped
+
+
+def density_fields(D: np.ndarray, R: np.ndarray):
+    """alpha = sum D / sum R, N = D - alpha R (Eq. 8 with R normalised to the
+    data total, Sec. 2.2) and Rt = alpha R, all FP64."""
+    sd = float(np.sum(D, dtype=np.float64))
+    sr = float(np.sum(R, dtype=np.float64))
+    if sr <= 0.0:
+        raise ValueError("random histogram is empty")
+    alpha = sd / sr
+    Dd = D.astype(np.float64)
+    Rd = R.astype(np.float64)
+    return alpha, Dd - alpha * Rd, alpha * Rd
+
+
+# ---------------------------------------------------------------------------
+# Kernels (Sec. 2.3)
+
+def shell_offsets(radius: float, width: float, cell: float, rule: str = "center_bin") -> np.ndarray:
+    """Integer offsets m = (mx, my, mz) with K_s(m) = 1 (readings 2 and 3),
+    int64 array [M, 3] in lexicographic (mx, my, mz) order."""
+    g2 = np.float64(cell) * np.float64(cell)
+    if rule == "center_bin":
+        outer = radius + 0.5 * width
+    elif rule == "intersect":
+        outer = radius + cell
+    else:
+        raise ValueError(rule)
+    h = int(math.ceil(outer / cell)) + 1
+    r = np.arange(-h, h + 1, dtype=np.int64)
+    mx, my, mz = np.meshgrid(r, r, r, indexing="ij")
+    mx, my, mz = mx.ravel(), my.ravel(), mz.ravel()
+    if rule == "center_bin":
+        lo = max(radius - 0.5 * width, 0.0)
+        hi = radius + 0.5 * width
+        d2 = (mx * mx + my * my + mz * mz).astype(np.float64) * g2
+        sel = (d2 >= np.float64(lo) * np.float64(lo)) & (d2 < np.float64(hi) * np.float64(hi))
+    else:
+        def near(a):
+            t = np.maximum(np.abs(a).astype(np.float64) - 0.5, 0.0)
+            return t * t
+        def far(a):
+            t = np.abs(a).astype(np.float64) + 0.5
+            return t * t
+        dmin2 = (near(mx) + near(my) + near(mz)) * g2
+        dmax2 = (far(mx) + far(my) + far(mz)) * g2
+        s2 = np.float64(radius) * np.float64(radius)
+        sel = (dmin2 <= s2) & (s2 < dmax2)
+    return np.stack([mx[sel], my[sel], mz[sel]], axis=1)
+
+
+def check_periodic_support(offsets: np.ndarray, n: Sequence[int]) -> bool:
+    """Reading 4: on a periodic axis of n cells, distinct offsets stay
+    distinct after wrapping iff 2 max|m| < n."""
+    if offsets.size == 0:
+        return True
+    m = np.abs(offsets).max(axis=0)
+    return bool(all(2 * int(m[a]) < int(n[a]) for a in range(3)))
+
+
+def kernel_grid(offsets: np.ndarray, n: Sequence[int]) -> np.ndarray:
+    """K_s on the full (nz, ny, nx) grid with offsets wrapped periodically."""
+    nx, ny, nz = (int(v) for v in n)
+    K = np.zeros((nz, ny, nx), dtype=np.float64)
+    np.add.at(K, (np.mod(offsets[:, 2], nz), np.mod(offsets[:, 1], ny),
+                  np.mod(offsets[:, 0], nx)), 1.0)
+    return K
+
+
+def kernel_spectrum_octant(offsets: np.ndarray, n: Sequence[int]) -> np.ndarray:
+    """The discrete Fourier transform of K_s on the grid, divided by N_c,
+    on the octant 0 <= k_a <= n_a/2 (shape (nz/2+1, ny/2+1, nx/2+1)).  K_s is
+    even in every axis, so its transform is real and even in every axis."""
+    nx, ny, nz = (int(v) for v in n)
+    K = kernel_grid(offsets, n)
+    Kh = np.fft.rfftn(K).real / float(nx * ny * nz)
+    return Kh[: nz // 2 + 1, : ny // 2 + 1, : nx // 2 + 1]
+
+
+# ---------------------------------------------------------------------------
+# Convolution (Sec. 2.4, Eqs. 9-10)
+
+def _shift_zero(F: np.ndarray, m: Tuple[int, int, int]) -> np.ndarray:
+    """G(r) = F(r + m) with zeros outside the box (non-periodic grid)."""
+    out = np.zeros_like(F)
+    src = []
+    dst = []
+    for axis, mm in ((0, m[2]), (1, m[1]), (2, m[0])):
+        n = F.shape[axis]
+        if abs(mm) >= n:
+            return out
+        if mm >= 0:
+            src.append(slice(mm, n)); dst.append(slice(0, n - mm))
+        else:
+            src.append(slice(0, n + mm)); dst.append(slice(-mm, n))
+    out[tuple(dst)] = F[tuple(src)]
+    return out
+
+
+def convolve_direct(F: np.ndarray, offsets: np.ndarray, periodic: bool) -> np.ndarray:
+    """W(r) = sum over the kernel's offsets m of F(r + m): the inner product of
+    the kernel centred on cell r with the field (Eq. 9 / Eq. 10), evaluated
+    directly in real space.  F has shape (nz, ny, nx)."""
+    W = np.zeros(F.shape, dtype=np.float64)
+    for mx, my, mz in offsets:
+        if periodic:
+            W += np.roll(F, shift=(-int(mz), -int(my), -int(mx)), axis=(0, 1, 2))
+        else:
+            W += _shift_zero(F, (int(mx), int(my), int(mz)))
+    return W
+
+
+def convolve_fft(F: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """The same inner product by FFT (periodic grid): the correlation
+    theorem, W = IFFT( FFT(F) * conj(FFT(K)) ), with a library FFT in FP64."""
+    n = (F.shape[2], F.shape[1], F.shape[0])
+    K = kernel_grid(offsets, n)
+    return np.fft.irfftn(np.fft.rfftn(F) * np.conj(np.fft.rfftn(K)), s=F.shape, axes=(0, 1, 2))
+
+
+def w_at_cells(F: np.ndarray, offsets: np.ndarray, cells: np.ndarray, periodic: bool) -> np.ndarray:
+    """W(r) at chosen cells r = (ix, iy, iz), one by one (direct sum)."""
+    nz, ny, nx = F.shape
+    cells = np.asarray(cells, np.int64).reshape(-1, 3)
+    out = np.zeros(cells.shape[0], dtype=np.float64)
+    for i, (ix, iy, iz) in enumerate(cells):
+        jx = ix + offsets[:, 0]
+        jy = iy + offsets[:, 1]
+        jz = iz + offsets[:, 2]
+        if periodic:
+            out[i] = F[np.mod(jz, nz), np.mod(jy, ny), np.mod(jx, nx)].sum()
+        else:
+            ok = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+            out[i] = F[jz[ok], jy[ok], jx[ok]].sum()
+    return out
+
+
+def guard_band_ok(fields: Iterable[np.ndarray], max_offset: Sequence[int]) -> bool:
+    """Circular (FFT) convolution equals the zero-outside one at every cell
+    where a field is non-zero iff, per axis, the periodic images cannot reach:
+    (extent of the non-zero cells) + max|m| < n."""
+    occ = None
+    for F in fields:
+        nz_ = F != 0
+        occ = nz_ if occ is None else (occ | nz_)
+    if occ is None or not occ.any():
+        return True
+    for axis, m in ((2, max_offset[0]), (1, max_offset[1]), (0, max_offset[2])):
+        other = tuple(a for a in range(3) if a != axis)
+        used = np.nonzero(occ.any(axis=other))[0]
+        if int(used[-1] - used[0]) + int(m) >= occ.shape[axis]:
+            return False
+    return True
+
+
+# ---------------------------------------------------------------------------
+# Summation (Sec. 2.5, Eqs. 11-14)
+
+def multisets(n_shells: int, k: int) -> List[Tuple[int, ...]]:
+    """All s_1 <= ... <= s_k over range(n_shells), lexicographic order."""
+    return list(itertools.combinations_with_replacement(range(n_shells), k))
+
+
+def product_sums(W0: np.ndarray, W: Sequence[np.ndarray], order: int):
+    """For every multiset of n - 1 = order - 1 shells: sum_r W0 prod W_{s_i}
+    (Eq. 11's numerator, or its denominator when given B) and the sum of the
+    absolute values of the same terms.  Returns (values, abs_values) in the
+    order of ``multisets``."""
+    sets = multisets(len(W), order - 1)
+    vals = np.zeros(len(sets), dtype=np.float64)
+    avals = np.zeros(len(sets), dtype=np.float64)
+    for i, ms in enumerate(sets):
+        t = W0.copy()
+        for s in ms:
+            t = t * W[s]
+        vals[i] = t.sum()
+        avals[i] = np.abs(t).sum()
+    return vals, avals
+
+
+def dense_tensor(values: np.ndarray, n_shells: int, k: int) -> np.ndarray:
+    """Fill the symmetric [n_shells]^k tensor from per-multiset values."""
+    T = np.zeros((n_shells,) * k, dtype=np.float64)
+    for v, ms in zip(values, multisets(n_shells, k)):
+        for p in set(itertools.permutations(ms)):
+            T[p] = v
+    return T
+
+
+def xi_from(num: np.ndarray, den: np.ndarray) -> np.ndarray:
+    """xi = num / den, NaN where den <= 0 (reading 7)."""
+    num = np.asarray(num, np.float64)
+    den = np.asarray(den, np.float64)
+    out = np.full(num.shape, np.nan)
+    ok = den > 0
+    out[ok] = num[ok] / den[ok]
+    return out
+
+
+def xi_diagonal(W0, W1, B0, B1, order: int) -> float:
+    """Equidistant n-point function (Eq. 14): sum W0 W1^(n-1) / sum B0 B1^(n-1)."""
+    num = float(np.sum(W0 * W1 ** (order - 1)))
+    den = float(np.sum(B0 * B1 ** (order - 1)))
+    return num / den if den > 0 else float("nan")
+
+
+def correlate(grid, shells: Sequence[float], width: float, data, randoms,
+              orders: Sequence[int] = (2, 3), engine: str = "direct",
+              rule: str = "center_bin") -> Dict[str, object]:
+    """The whole path for one catalog: mapping, convolution, summation.
+
+    Returns a dict with D, R, dropped counts, alpha, N, Rt, the offset lists,
+    W and B banks, and per order n: num, den, abs_num, abs_den (per multiset)
+    and the dense xi tensor [N_s]^(n-1).
+    """
+    D, dropped_d = grid_counts(data.x, data.y, data.z, grid)
+    R, dropped_r = grid_counts(randoms.x, randoms.y, randoms.z, grid)
+    alpha, N, Rt = density_fields(D, R)
+    offs = [shell_offsets(s, width, grid.cell, rule) for s in shells]
+    if grid.periodic:
+        for o in offs:
+            if not check_periodic_support(o, grid.n):
+                raise ValueError("shell support reaches half the periodic box")
+    if engine == "direct":
+        conv = lambda F, o: convolve_direct(F, o, grid.periodic)  # noqa: E731
+    elif engine == "fft":
+        if not grid.periodic:
+            mmax = np.max([np.abs(o).max(axis=0) for o in offs if o.size], axis=0)
+            if not guard_band_ok([D, R], mmax):
+                raise ValueError("data reach the box faces: circular convolution differs")
+        conv = convolve_fft
+    else:
+        raise ValueError(engine)
+    W = [conv(N, o) for o in offs]
+    B = [conv(Rt, o) for o in offs]
+    out: Dict[str, object] = dict(D=D, R=R, dropped_d=dropped_d, dropped_r=dropped_r,
+                                  alpha=alpha, N=N, Rt=Rt, offsets=offs, W=W, B=B)
+    ns = len(shells)
+    for n in orders:
+        num, anum = product_sums(N, W, n)
+        den, aden = product_sums(Rt, B, n)
+        out[f"num{n}"] = num
+        out[f"den{n}"] = den
+        out[f"abs_num{n}"] = anum
+        out[f"abs_den{n}"] = aden
+        out[f"xi{n}"] = dense_tensor(xi_from(num, den), ns, n - 1)
+    return out

@@ -1,0 +1,538 @@
+"""Checks that pin the FP64 oracle to facts fixed outside it.
+
+Every check takes the oracle module as an argument and returns True when the
+oracle agrees with the independent fact.  ``test_oracle_pins`` asserts each
+one; ``test_oracle_mutations`` plants mistakes in the oracle and asserts that
+at least one check then fails.
+
+The independent facts used here:
+
+* counts of points placed exactly at cell centres / edges (known by
+  construction);
+* lattice-point counts of a spherical shell, by brute-force enumeration in
+  plain Python;
+* ordered pair, triplet and higher counts of points at cell centres on a
+  periodic grid, by brute force over the points with minimum-image integer
+  separations: sum_r D W_{s_1} ... W_{s_k} equals the number of ordered
+  tuples (i, j_1, .., j_k) with the separation i-j_t in shell s_t, and the
+  same with signed weights for N = D - alpha R (Secs. 2.4-2.5, Eqs. 9-13);
+* closed forms: a constant random field gives den = N_c c^n prod |O_s|;
+  a delta field gives W_s = the indicator of the shell about the delta;
+* the discrete Fourier transform written out as a cosine sum;
+* invariances: shell relabelling, integer translations, linearity, region
+  additivity (Eq. 19) and the equidistant diagonal (Eq. 14).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+
+from synth import Catalog, GridSpec, lattice_catalog
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---------------------------------------------------------------------------
+# independent helpers (no oracle code)
+
+def brute_shell_count(radius, width, cell):
+    """Number of integer vectors with (s - w/2) <= |m| g < (s + w/2)."""
+    lo = max(radius - width / 2.0, 0.0)
+    hi = radius + width / 2.0
+    h = int(math.ceil(hi / cell)) + 1
+    c = 0
+    for i in range(-h, h + 1):
+        for j in range(-h, h + 1):
+            for k in range(-h, h + 1):
+                d = math.sqrt(i * i + j * j + k * k) * cell
+                if lo <= d < hi:
+                    c += 1
+    return c
+
+
+def _in_shell(d2_cells, radius, width, cell):
+    """Shell test on squared integer separations (cell units)."""
+    lo = max(radius - width / 2.0, 0.0)
+    hi = radius + width / 2.0
+    d = np.sqrt(d2_cells.astype(np.float64)) * cell
+    return (d >= lo) & (d < hi)
+
+
+def _min_image(ci, cj, n):
+    """Minimum-image integer separation cj - ci on a periodic axis of n."""
+    d = np.mod(cj - ci, n)
+    return np.where(d >= (n + 1) // 2, d - n, d)
+
+
+def _sep2(cells_a, cells_b, n):
+    d2 = np.zeros((cells_a.shape[0], cells_b.shape[0]), dtype=np.int64)
+    for a in range(3):
+        d = _min_image(cells_a[:, a][:, None], cells_b[:, a][None, :], n[a])
+        d2 += d * d
+    return d2
+
+
+# ---------------------------------------------------------------------------
+# mapping
+
+def check_lattice_gridding(o) -> bool:
+    """Cell-centred points on a non-cubic grid land in their own cells, and
+    lower-edge points in the cell whose edge they sit on."""
+    g = GridSpec((8, 6, 5), (-3.5, 2.0, 10.0), 2.5, False)
+    rng = _rng(11)
+    cells = np.stack([rng.integers(0, g.n[a], 60) for a in range(3)], axis=1)
+    mult = rng.integers(1, 4, 60)
+    expect = np.zeros((g.n[2], g.n[1], g.n[0]), dtype=np.int64)
+    for (ix, iy, iz), m in zip(cells, mult):
+        expect[iz, iy, ix] += m
+    ok = True
+    for where in ("centre", "edge"):
+        cat = lattice_catalog(g, cells, mult, where=where)
+        D, dropped = o.grid_counts(cat.x, cat.y, cat.z, g)
+        ok &= dropped == 0 and D.shape == expect.shape and np.array_equal(D.astype(np.int64), expect)
+    # just below a lower edge belongs to the previous cell
+    e = np.float32(g.origin[0] + 3 * g.cell)
+    below = np.nextafter(e, np.float32(-np.inf))
+    cat = Catalog(np.array([e, below], np.float32), np.array([3.0, 3.0], np.float32),
+                  np.array([11.0, 11.0], np.float32))
+    D, _ = o.grid_counts(cat.x, cat.y, cat.z, g)
+    ok &= int(D[0, 0, 3]) == 1 and int(D[0, 0, 2]) == 1
+    return bool(ok)
+
+
+def check_out_of_grid(o) -> bool:
+    """Non-periodic: points outside [origin, origin + n g) are dropped and
+    counted.  Periodic: x = L is cell 0 and x = -g/2 is cell n - 1."""
+    g = GridSpec((4, 4, 4), (0.0, 0.0, 0.0), 1.0, False)
+    x = np.array([-0.5, 4.0, 3.999, 0.0, 2.5], np.float32)
+    y = np.array([1.5, 1.5, 1.5, 1.5, 9.0], np.float32)
+    z = np.array([1.5, 1.5, 1.5, 1.5, 1.5], np.float32)
+    D, dropped = o.grid_counts(x, y, z, g)
+    ok = dropped == 3 and int(D.sum()) == 2 and int(D[1, 1, 3]) == 1 and int(D[1, 1, 0]) == 1
+    gp = GridSpec((4, 4, 4), (0.0, 0.0, 0.0), 1.0, True)
+    x = np.array([4.0, -0.5, 1.5], np.float32)
+    D, dropped = o.grid_counts(x, np.full(3, 0.5, np.float32), np.full(3, 2.5, np.float32), gp)
+    ok &= dropped == 0 and int(D[2, 0, 0]) == 1 and int(D[2, 0, 3]) == 1 and int(D[2, 0, 1]) == 1
+    return bool(ok)
+
+
+def check_alpha_and_fields(o) -> bool:
+    """alpha = sum D / sum R; N = D - alpha R; Rt = alpha R (Eq. 8)."""
+    D = np.array([[[3, 0], [1, 2]]], np.uint32)
+    R = np.array([[[10, 4], [0, 6]]], np.uint32)
+    alpha, N, Rt = o.density_fields(D, R)
+    return bool(alpha == 0.3 and np.allclose(N, [[[0.0, -1.2], [1.0, 0.2]]], rtol=0, atol=1e-15)
+                and np.allclose(Rt, [[[3.0, 1.2], [0.0, 1.8]]], rtol=0, atol=1e-15))
+
+
+# ---------------------------------------------------------------------------
+# kernels
+
+SHELL_CASES = [(20.0, 10.0, 10.0), (40.0, 10.0, 10.0), (30.0, 8.0, 8.0), (34.0, 4.0, 8.0),
+               (3.0, 1.0, 1.0), (2.0, 1.0, 1.0), (1.5, 1.0, 1.0), (50.0, 5.0, 5.0)]
+
+
+def check_shell_counts(o) -> bool:
+    """|O_s| equals a brute-force lattice count, the set is closed under sign
+    flips and axis permutations, and every member obeys the shell bounds."""
+    for s, w, g in SHELL_CASES:
+        offs = o.shell_offsets(s, w, g)
+        if offs.shape[0] != brute_shell_count(s, w, g):
+            return False
+        S = {tuple(int(v) for v in m) for m in offs}
+        if len(S) != offs.shape[0]:
+            return False
+        for m in list(S)[:50]:
+            for p in itertools.permutations(m):
+                for sg in itertools.product((1, -1), repeat=3):
+                    if tuple(a * b for a, b in zip(p, sg)) not in S:
+                        return False
+    return True
+
+
+def check_intersect_rule(o) -> bool:
+    """Rule "intersect": a cell is kept iff the sphere of radius s passes
+    through the cell cube; checked against dense sampling of each cube."""
+    s, g = 2.3, 1.0
+    offs = o.shell_offsets(s, 0.0, g, rule="intersect")
+    S = {tuple(int(v) for v in m) for m in offs}
+    t = np.linspace(-0.5, 0.5, 41)
+    px, py, pz = np.meshgrid(t, t, t, indexing="ij")
+    for i in range(-4, 5):
+        for j in range(-4, 5):
+            for k in range(-4, 5):
+                d = np.sqrt((i + px) ** 2 + (j + py) ** 2 + (k + pz) ** 2) * g
+                lo, hi = d.min(), d.max()
+                if abs(lo - s) < 0.03 or abs(hi - s) < 0.03:
+                    continue  # too close to call by sampling
+                if ((lo < s < hi) != ((i, j, k) in S)):
+                    return False
+    return True
+
+
+def check_kernel_spectrum(o) -> bool:
+    """The octant of K^/N_c equals the DFT written as a cosine sum over the
+    offset list, divided by N_c; K^(0) N_c = |O_s|."""
+    n = (10, 8, 6)
+    offs = o.shell_offsets(2.0, 1.0, 1.0)
+    Kh = o.kernel_spectrum_octant(offs, n)
+    Nc = n[0] * n[1] * n[2]
+    if Kh.shape != (n[2] // 2 + 1, n[1] // 2 + 1, n[0] // 2 + 1):
+        return False
+    if abs(Kh[0, 0, 0] * Nc - offs.shape[0]) > 1e-9:
+        return False
+    for kz in range(n[2] // 2 + 1):
+        for ky in range(n[1] // 2 + 1):
+            for kx in range(n[0] // 2 + 1):
+                ph = 2 * math.pi * (kx * offs[:, 0] / n[0] + ky * offs[:, 1] / n[1] + kz * offs[:, 2] / n[2])
+                if abs(np.cos(ph).sum() / Nc - Kh[kz, ky, kx]) > 1e-12:
+                    return False
+    return True
+
+
+# ---------------------------------------------------------------------------
+# convolution + summation: exact counting identities
+
+def _centre_points(grid, count, seed):
+    rng = _rng(seed)
+    cells = np.stack([rng.integers(0, grid.n[a], count) for a in range(3)], axis=1)
+    return cells, lattice_catalog(grid, cells)
+
+
+PGRID = GridSpec((9, 8, 7), (0.0, 0.0, 0.0), 2.0, True)
+PSHELLS = [(2.5, 1.0), (3.6, 1.2), (5.0, 2.0)]
+
+
+def _cell_rule_ok(o, shells, grid):
+    return all(o.check_periodic_support(o.shell_offsets(s, w, grid.cell), grid.n) for s, w in shells)
+
+
+def check_pair_counts(o) -> bool:
+    """sum_r D W_s = #ordered pairs (i, j) with separation in shell s."""
+    g = PGRID
+    if not _cell_rule_ok(o, PSHELLS, g):
+        return False
+    cells, cat = _centre_points(g, 45, 5)
+    D, _ = o.grid_counts(cat.x, cat.y, cat.z, g)
+    Dd = D.astype(np.float64)
+    d2 = _sep2(cells, cells, g.n)
+    for s, w in PSHELLS:
+        W = o.convolve_direct(Dd, o.shell_offsets(s, w, g.cell), True)
+        got = float((Dd * W).sum())
+        want = int(_in_shell(d2, s, w, g.cell).sum())
+        if got != want:
+            return False
+    return True
+
+
+def check_triplet_counts(o) -> bool:
+    """sum_r D W_a W_b = #ordered (i, j, k), sep(i,j) in a, sep(i,k) in b,
+    j = k allowed (Eq. 13's numerator on cell-centred points)."""
+    g = PGRID
+    cells, cat = _centre_points(g, 30, 6)
+    D, _ = o.grid_counts(cat.x, cat.y, cat.z, g)
+    Dd = D.astype(np.float64)
+    d2 = _sep2(cells, cells, g.n)
+    for (sa, wa), (sb, wb) in [(PSHELLS[0], PSHELLS[1]), (PSHELLS[1], PSHELLS[1]), (PSHELLS[2], PSHELLS[0])]:
+        Wa = o.convolve_direct(Dd, o.shell_offsets(sa, wa, g.cell), True)
+        Wb = o.convolve_direct(Dd, o.shell_offsets(sb, wb, g.cell), True)
+        got = float((Dd * Wa * Wb).sum())
+        A = _in_shell(d2, sa, wa, g.cell)
+        B = _in_shell(d2, sb, wb, g.cell)
+        want = int(np.einsum("ij,ik->", A.astype(np.int64), B.astype(np.int64)))
+        if got != want:
+            return False
+    return True
+
+
+def check_product_sums_high_order(o) -> bool:
+    """product_sums for n = 2..5 on cell-centred points equals
+    sum_i prod_t cnt_{s_t}(i), cnt_s(i) = #j with sep(i, j) in s."""
+    g = PGRID
+    cells, cat = _centre_points(g, 25, 7)
+    D, _ = o.grid_counts(cat.x, cat.y, cat.z, g)
+    Dd = D.astype(np.float64)
+    d2 = _sep2(cells, cells, g.n)
+    W = [o.convolve_direct(Dd, o.shell_offsets(s, w, g.cell), True) for s, w in PSHELLS]
+    cnt = [_in_shell(d2, s, w, g.cell).sum(axis=1).astype(np.int64) for s, w in PSHELLS]
+    for order in (2, 3, 4, 5):
+        vals, avals = o.product_sums(Dd, W, order)
+        sets = list(itertools.combinations_with_replacement(range(len(PSHELLS)), order - 1))
+        if len(vals) != len(sets):
+            return False
+        for v, av, ms in zip(vals, avals, sets):
+            want = int(np.prod(np.stack([cnt[s] for s in ms]), axis=0).sum())
+            if v != want or av != want:
+                return False
+    return True
+
+
+def check_signed_pairs(o) -> bool:
+    """With N = D - alpha R built from data (+1) and randoms (-alpha) at cell
+    centres: sum_r N W_s = sum_{i,j} w_i w_j [sep(i,j) in s], and likewise
+    sum_r Rt B_s over the randoms alone with weight alpha."""
+    g = PGRID
+    cd, dat = _centre_points(g, 20, 8)
+    cr, ran = _centre_points(g, 70, 9)
+    D, _ = o.grid_counts(dat.x, dat.y, dat.z, g)
+    R, _ = o.grid_counts(ran.x, ran.y, ran.z, g)
+    alpha, N, Rt = o.density_fields(D, R)
+    if abs(alpha - 20.0 / 70.0) > 1e-15:
+        return False
+    cells = np.concatenate([cd, cr])
+    wts = np.concatenate([np.ones(20), -alpha * np.ones(70)])
+    d2 = _sep2(cells, cells, g.n)
+    d2r = _sep2(cr, cr, g.n)
+    for s, w in PSHELLS:
+        offs = o.shell_offsets(s, w, g.cell)
+        W = o.convolve_direct(N, offs, True)
+        B = o.convolve_direct(Rt, offs, True)
+        want = float(wts @ (_in_shell(d2, s, w, g.cell) @ wts))
+        wantr = alpha * alpha * float(_in_shell(d2r, s, w, g.cell).sum())
+        if abs((N * W).sum() - want) > 1e-10 * max(1.0, abs(want)):
+            return False
+        if abs((Rt * B).sum() - wantr) > 1e-10 * max(1.0, abs(wantr)):
+            return False
+    return True
+
+
+def check_delta_response(o) -> bool:
+    """A single unit cell c gives W_s(r) = 1 exactly where c - r is in O_s
+    (periodic and zero-outside boundaries)."""
+    for periodic in (True, False):
+        n = (9, 8, 7)
+        F = np.zeros((n[2], n[1], n[0]))
+        c = (4, 3, 3)
+        F[c[2], c[1], c[0]] = 1.0
+        offs = o.shell_offsets(2.5, 1.0, 1.0)
+        W = o.convolve_direct(F, offs, periodic)
+        want = np.zeros_like(F)
+        for mx, my, mz in offs:
+            rx, ry, rz = c[0] - mx, c[1] - my, c[2] - mz
+            if periodic:
+                want[rz % n[2], ry % n[1], rx % n[0]] += 1
+            elif 0 <= rx < n[0] and 0 <= ry < n[1] and 0 <= rz < n[2]:
+                want[rz, ry, rx] += 1
+        if not np.array_equal(W, want):
+            return False
+    return True
+
+
+def check_fft_engine(o) -> bool:
+    """The FFT engine equals the direct engine on a periodic grid."""
+    rng = _rng(12)
+    F = rng.normal(size=(7, 8, 9))
+    for s, w in PSHELLS:
+        offs = o.shell_offsets(s, w, 2.0)
+        a = o.convolve_direct(F, offs, True)
+        b = o.convolve_fft(F, offs)
+        if np.abs(a - b).max() > 1e-12 * max(1.0, np.abs(a).max()):
+            return False
+    return True
+
+
+def _uniform_lattice_case(o, c_per_cell=1):
+    g = GridSpec((10, 9, 8), (0.0, 0.0, 0.0), 1.0, True)
+    allc = np.stack(np.meshgrid(np.arange(10), np.arange(9), np.arange(8), indexing="ij"), -1).reshape(-1, 3)
+    rng = _rng(13)
+    dat = lattice_catalog(g, allc[rng.integers(0, allc.shape[0], 50)])
+    ran = lattice_catalog(g, allc, np.full(allc.shape[0], c_per_cell))
+    return g, dat, ran
+
+
+def check_constant_field_den(o) -> bool:
+    """Randoms filling every cell equally (R = 2) give Rt = c = 2 alpha
+    everywhere and den_n = N_c c^n prod |O_s| (closed form)."""
+    g, dat, ran = _uniform_lattice_case(o, 2)
+    shells = (1.5, 2.5, 3.2)
+    res = o.correlate(g, shells, 1.0, dat, ran, orders=(2, 3, 4, 5))
+    alpha = 50.0 / (2 * g.n_cells)
+    c = 2 * alpha  # Rt = alpha R with R = 2 in every cell
+    sizes = [brute_shell_count(s, 1.0, 1.0) for s in shells]
+    for n in (2, 3, 4, 5):
+        sets = list(itertools.combinations_with_replacement(range(3), n - 1))
+        for v, ms in zip(res[f"den{n}"], sets):
+            want = g.n_cells * c ** n * np.prod([sizes[s] for s in ms])
+            if abs(v - want) > 1e-10 * want:
+                return False
+    return True
+
+
+def _clustered_case(seed=21):
+    from synth import neyman_scott_box, uniform_box
+    g = GridSpec((12, 10, 8), (0.0, 0.0, 0.0), 10.0, True)
+    dat = neyman_scott_box(seed, 30, 8, 6.0, 80.0)
+    # clip into the non-cubic box (x < 120, y < 100, z < 80)
+    dat = Catalog(np.mod(dat.x * 1.5, 120.0), np.mod(dat.y * 1.25, 100.0), dat.z)
+    ran = uniform_box(seed + 1, 2000, 80.0)
+    ran = Catalog(np.mod(ran.x * 1.5, 120.0), np.mod(ran.y * 1.25, 100.0), ran.z)
+    return g, dat, ran
+
+
+CSHELLS = (15.0, 25.0, 32.0)
+
+
+def check_relabel_shells(o) -> bool:
+    """Passing the shells in another order permutes the xi tensors the same
+    way (no mix-up between shell labels and W banks)."""
+    g, dat, ran = _clustered_case()
+    a = o.correlate(g, CSHELLS, 10.0, dat, ran, orders=(2, 3, 4))
+    perm = (2, 0, 1)
+    b = o.correlate(g, tuple(CSHELLS[p] for p in perm), 10.0, dat, ran, orders=(2, 3, 4))
+    for n in (2, 3, 4):
+        A = a[f"xi{n}"]
+        B = b[f"xi{n}"]
+        idx = np.ix_(*([list(perm)] * (n - 1)))
+        if not np.allclose(A[idx], B, rtol=1e-12, atol=0, equal_nan=True):
+            return False
+        if not np.allclose(A, np.swapaxes(A, 0, -1), rtol=1e-12, equal_nan=True):
+            return False
+    return True
+
+
+def check_translation(o) -> bool:
+    """Moving every point by whole cells on a periodic grid leaves num, den
+    and xi unchanged."""
+    g, dat, ran = _clustered_case()
+    a = o.correlate(g, CSHELLS, 10.0, dat, ran, orders=(2, 3))
+    sh = (30.0, 70.0, 10.0)
+
+    def mv(c):
+        return Catalog(np.mod(c.x.astype(np.float64) + sh[0], 120.0),
+                       np.mod(c.y.astype(np.float64) + sh[1], 100.0),
+                       np.mod(c.z.astype(np.float64) + sh[2], 80.0))
+    b = o.correlate(g, CSHELLS, 10.0, mv(dat), mv(ran), orders=(2, 3))
+    for n in (2, 3):
+        for key in ("num", "den"):
+            x, y = a[f"{key}{n}"], b[f"{key}{n}"]
+            if np.abs(x - y).max() > 1e-9 * np.abs(x).max():
+                return False
+    return True
+
+
+def check_linearity(o) -> bool:
+    """W of N = D - alpha R equals W(D) - alpha W(R) (Eq. 9 is linear)."""
+    g, dat, ran = _clustered_case()
+    D, _ = o.grid_counts(dat.x, dat.y, dat.z, g)
+    R, _ = o.grid_counts(ran.x, ran.y, ran.z, g)
+    alpha, N, _ = o.density_fields(D, R)
+    offs = o.shell_offsets(25.0, 10.0, 10.0)
+    a = o.convolve_direct(N, offs, True)
+    b = o.convolve_direct(D.astype(np.float64), offs, True) - alpha * o.convolve_direct(R.astype(np.float64), offs, True)
+    return bool(np.abs(a - b).max() <= 1e-12 * np.abs(b).max())
+
+
+def check_region_additivity(o) -> bool:
+    """Two regions further apart than the largest shell, each with its own
+    alpha, in one zero-outside box: the product sums of the combined field
+    are the sums over the regions (Eq. 19)."""
+    g = GridSpec((24, 10, 10), (0.0, 0.0, 0.0), 1.0, False)
+    rng = _rng(31)
+
+    def region(x0, nd, nr):
+        cd = np.stack([rng.integers(x0, x0 + 6, nd), rng.integers(2, 8, nd), rng.integers(2, 8, nd)], 1)
+        cr = np.stack([rng.integers(x0, x0 + 6, nr), rng.integers(2, 8, nr), rng.integers(2, 8, nr)], 1)
+        D, _ = o.grid_counts(*_xyz(lattice_catalog(g, cd)), g)
+        R, _ = o.grid_counts(*_xyz(lattice_catalog(g, cr)), g)
+        return o.density_fields(D, R)
+
+    aA, NA, RA = region(1, 40, 200)
+    aB, NB, RB = region(16, 25, 300)
+    shells = [(1.5, 1.0), (2.5, 1.0), (3.5, 1.0)]
+    offs = [o.shell_offsets(s, w, 1.0) for s, w in shells]
+
+    def sums(N, Rt):
+        W = [o.convolve_direct(N, x, False) for x in offs]
+        B = [o.convolve_direct(Rt, x, False) for x in offs]
+        return o.product_sums(N, W, 3)[0], o.product_sums(Rt, B, 3)[0]
+    nA, dA = sums(NA, RA)
+    nB, dB = sums(NB, RB)
+    nC, dC = sums(NA + NB, RA + RB)
+    return bool(np.allclose(nC, nA + nB, rtol=1e-12, atol=1e-9) and np.allclose(dC, dA + dB, rtol=1e-12))
+
+
+def _xyz(c):
+    return c.x, c.y, c.z
+
+
+def check_diagonal(o) -> bool:
+    """xi_n(s, .., s) equals Eq. 14 evaluated on its own."""
+    g, dat, ran = _clustered_case()
+    res = o.correlate(g, CSHELLS, 10.0, dat, ran, orders=(2, 3, 4, 5))
+    for n in (2, 3, 4, 5):
+        T = res[f"xi{n}"]
+        for s in range(len(CSHELLS)):
+            want = o.xi_diagonal(res["N"], res["W"][s], res["Rt"], res["B"][s], n)
+            if not math.isclose(T[(s,) * (n - 1)], want, rel_tol=1e-12):
+                return False
+    return True
+
+
+def check_sum_of_w(o) -> bool:
+    """On a periodic grid sum_r W_s = (sum_r N) |O_s|."""
+    rng = _rng(41)
+    F = rng.normal(size=(8, 9, 10))
+    for s, w in PSHELLS:
+        offs = o.shell_offsets(s, w, 2.0)
+        W = o.convolve_direct(F, offs, True)
+        if abs(W.sum() - F.sum() * offs.shape[0]) > 1e-10 * np.abs(F).sum() * offs.shape[0]:
+            return False
+    return True
+
+
+def check_sampled_cells(o) -> bool:
+    """w_at_cells agrees with the full convolution at sampled cells."""
+    rng = _rng(42)
+    F = rng.normal(size=(7, 8, 9))
+    offs = o.shell_offsets(3.6, 1.2, 2.0)
+    cells = np.stack([rng.integers(0, 9, 20), rng.integers(0, 8, 20), rng.integers(0, 7, 20)], 1)
+    for periodic in (True, False):
+        W = o.convolve_direct(F, offs, periodic)
+        got = o.w_at_cells(F, offs, cells, periodic)
+        if np.abs(got - W[cells[:, 2], cells[:, 1], cells[:, 0]]).max() > 1e-12:
+            return False
+    return True
+
+
+def check_multisets(o) -> bool:
+    """C(N_s + k - 1, k) sorted multisets in lexicographic order."""
+    for ns in (1, 4, 16):
+        for k in (1, 2, 3, 4):
+            m = o.multisets(ns, k)
+            if len(m) != math.comb(ns + k - 1, k) or m != sorted(m):
+                return False
+            if any(list(t) != sorted(t) for t in m):
+                return False
+    return True
+
+
+def check_guard_band(o) -> bool:
+    """The guard-band test accepts exactly when periodic images cannot reach:
+    on a non-periodic grid with data inside the band, FFT and direct agree."""
+    F = np.zeros((16, 16, 16))
+    F[5:11, 6:9, 4:12] = 1.0
+    offs = o.shell_offsets(3.0, 1.0, 1.0)
+    m = np.abs(offs).max(axis=0)
+    if not o.guard_band_ok([F], m):
+        return False
+    a = o.convolve_direct(F, offs, False)
+    b = o.convolve_fft(F, offs)
+    ok = np.abs((a - b) * (F != 0)).max() < 1e-12
+    G = np.zeros((16, 16, 16))
+    G[0, 0, 0] = 1.0
+    G[0, 0, 14] = 1.0
+    return bool(ok and not o.guard_band_ok([G], m))
+
+
+ALL_CHECKS = [
+    check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
+    check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
+    check_product_sums_high_order, check_signed_pairs, check_delta_response, check_fft_engine,
+    check_constant_field_den, check_relabel_shells, check_translation, check_linearity,
+    check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
+    check_multisets, check_guard_band,
+]
