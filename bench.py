@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the ConKer hot path on one GB300 per rank.
+
+One step = one catalog end to end on the device: grid the randoms and the
+data (mapping), FFT-convolve both fields with every shell kernel, the n-point
+product sums for num and den, and xi (ck_set_randoms + ck_compute).  Inputs
+are resident in HBM before timing; the timed region is exactly --steps steps
+bracketed by a barrier and a device synchronisation, timed with CUDA events
+on the launching stream; the max over ranks is taken.  Every step moves
+far more than the 129 MB L2 (the 512^3 W bank alone is 8.6 GB per field), so
+no explicit L2 flush is added between steps.
+
+Also reported: `e2e` (the same step through the C ABI with host input
+buffers and host outputs, copies inside the timed region), `roofline` for
+the dominant kernel from the library's per-launch CUDA events, the FP64 CPU
+oracle on a bounded sample (`cpu_baseline`), SM clocks sampled during the
+timed region, and the number of library kernel launches.
+
+`--impl reference` times the FP64 CPU oracle on the host cores (there is no
+reference implementation to install: the paper's code is not part of it).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("ms/catalog for ξ_2..ξ_5 (mixed vs plain FP32, rel err ≤1e-5); FFT GB/s; TC util %")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="survey512")
+    ap.add_argument("--orders", default=None, help="e.g. 23 or 2345 (default: the workload's)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _orders(args, w):
+    if args.orders:
+        return tuple(int(c) for c in args.orders)
+    return tuple(w["orders"])
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (bounded sample, extrapolated per stage)
+
+def cpu_oracle_sample(w, orders, point_frac=1 / 8, fields=2):
+    """Time the FP64 oracle on a bounded sample of the workload and scale each
+    stage to one catalog: gridding of `point_frac` of the points (x 1/frac),
+    the density fields once, one shell's FFT convolution of one field
+    (x N_s x fields), and the product sums of one multiset per order
+    (x the number of multisets x fields)."""
+    import numpy as np
+    from oracle import conker_oracle as O
+
+    g = w["grid"]
+    d, r = w["data"], w["randoms"]
+    nd, nr = max(1, int(d.n * point_frac)), max(1, int(r.n * point_frac))
+    t0 = time.perf_counter()
+    D, _ = O.grid_counts(d.x[:nd], d.y[:nd], d.z[:nd], g)
+    R, _ = O.grid_counts(r.x[:nr], r.y[:nr], r.z[:nr], g)
+    t_grid = (time.perf_counter() - t0) / point_frac
+    t0 = time.perf_counter()
+    alpha, N, Rt = O.density_fields(D, R)
+    t_prep = time.perf_counter() - t0
+    offs = O.shell_offsets(w["shells"][len(w["shells"]) // 2], w["width"], g.cell)
+    t0 = time.perf_counter()
+    W = O.convolve_fft(N, offs)
+    t_conv = time.perf_counter() - t0
+    ns = len(w["shells"])
+    t_sum = 0.0
+    for n in orders:
+        t0 = time.perf_counter()
+        O.product_sums(N, [W], n)  # exactly one multiset
+        t_sum += (time.perf_counter() - t0) * math.comb(ns + n - 2, n - 1)
+    total = t_grid + t_prep + fields * (t_conv * ns + t_sum)
+    sample = (f"oracle (numpy FP64, single thread) on {nd + nr} of {d.n + r.n} points, one shell's FFT "
+              f"convolution of one field and one multiset per order; stages scaled to the catalog "
+              f"(gridding x{1 / point_frac:.0f}, convolution x{fields * ns}, sums x multisets x{fields})")
+    return total * 1000.0, sample
+
+
+# ---------------------------------------------------------------------------
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2108_00015_gb300 import Plan
+    from synth import workload
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args.workload)
+    orders = _orders(args, w)
+    g = w["grid"]
+    plan = Plan(g.n, g.origin, g.cell, g.periodic, w["shells"], w["width"], max_order=max(orders))
+    d, r = w["data"], w["randoms"]
+    dev = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    dx, dy, dz = dev(d.x), dev(d.y), dev(d.z)
+    rx, ry, rz = dev(r.x), dev(r.y), dev(r.z)
+    ns = len(w["shells"])
+    outs = {k: {n: torch.empty((ns,) * (n - 1), dtype=torch.float64, device="cuda") for n in orders}
+            for k in ("xi", "num", "den")}
+    outs["dropped"] = torch.zeros(2, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.set_randoms(rx, ry, rz)
+        return plan.compute(dx, dy, dz, orders=orders, out="device", outputs=outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = plan.status()
+    if st not in (0,):
+        raise RuntimeError(f"device status {st} after warm-up")
+    plan.profile(True)
+    clocks = Clocks(torch.cuda.current_device())
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    stages = plan.profile_read()
+    plan.profile(False)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the timed region")
+
+    peak, peak_kind = _peaks()
+    launches = sum(v["launches"] for v in stages.values())
+    stage_out = {}
+    for name, v in stages.items():
+        per = v["ms"] / v["launches"]
+        gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None
+        stage_out[name] = {"ms_per_step": round(v["ms"] / args.steps, 4), "launches_per_step": v["launches"] / args.steps,
+                           "us_per_launch": round(per * 1e3, 2),
+                           "achieved_gbs": round(gbs, 1) if gbs else None}
+    dom = max(stages.items(), key=lambda kv: kv[1]["ms"])
+    dname, dv = dom
+    achieved = dv["bytes"] / (dv["ms"] * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            ent = tr.get(args.workload, {}).get(dname)
+            src = os.path.join(ROOT, "paper_2108_00015_gb300", "csrc", ent["source"]) if ent else None
+            if ent and src and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == ent["sha"]:
+                traffic = ent["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": dv["bytes"] / dv["launches"],
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    fft_names = [k for k in stages if k.startswith("fft_")]
+    fft_bytes = sum(stages[k]["bytes"] for k in fft_names)
+    fft_ms = sum(stages[k]["ms"] for k in fft_names)
+
+    e2e = None
+    if not args.no_e2e:
+        hx = [torch.from_numpy(a).pin_memory() for a in (d.x, d.y, d.z)]
+        hr = [torch.from_numpy(a).pin_memory() for a in (r.x, r.y, r.z)]
+        houts = {k: {n: torch.empty((ns,) * (n - 1), dtype=torch.float64).pin_memory() for n in orders}
+                 for k in ("xi", "num", "den")}
+        houts["dropped"] = torch.zeros(2, dtype=torch.int64).pin_memory()
+        hx_np = [t.numpy() for t in hx]
+        hr_np = [t.numpy() for t in hr]
+
+        def step_host():
+            plan.set_randoms(*hr_np)
+            res = plan.compute(*hx_np, orders=orders, out="host", outputs=houts)
+            return float(res["xi"][orders[0]].reshape(-1)[0])
+
+        step_host()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_host()
+        t_e2e = (time.perf_counter() - t0) * 1000.0
+        if ws > 1:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = 12 * (d.n + r.n)
+        d2h = sum(3 * 8 * ns ** (n - 1) for n in orders) + 16
+        e2e = {"value": round(t_e2e / (args.e2e_steps * ws), 3), "unit": "ms/catalog", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "path": "ck_set_randoms + ck_compute with pinned host positions and host outputs"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        ms, sample = cpu_oracle_sample(w, orders)
+        cpu = {"value": round(ms, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample,
+               "wall_s": round(time.perf_counter() - t0, 1)}
+
+    value = t_ms / (args.steps * ws)
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms/catalog", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded Neyman-Scott catalog with a lognormal-biased parent field in a survey-shell "
+                "mask and uniform randoms (stand-in for SDSS DR12 CMASS + randoms)",
+        "config": {"workload": args.workload, "grid": list(g.n), "cell": g.cell, "periodic": g.periodic,
+                   "shells": ns, "width": w["width"], "orders": list(orders), "n_data": d.n, "n_randoms": r.n,
+                   "step": "ck_set_randoms + ck_compute (both fields, every shell)",
+                   "l2": "no flush: inputs and intermediates far larger than L2 (W bank 8.6 GB per field)"},
+        "roofline": roofline,
+        "fft": {"gbs": round(fft_bytes / (fft_ms * 1e-3) / 1e9, 1), "frac": round(fft_bytes / (fft_ms * 1e-3) / 1e9 / peak, 4),
+                "ms_per_step": round(fft_ms / args.steps, 3), "passes_per_transform": 3},
+        "stages": stage_out,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if ws > 1:
+        dist.destroy_process_group()
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from synth import workload
+    w = workload(args.workload)
+    orders = _orders(args, w)
+    # each step: the oracle on a smaller bounded sample
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, orders, point_frac=1 / 32)
+    vals = []
+    sample = None
+    for _ in range(args.steps):
+        ms, sample = cpu_oracle_sample(w, orders, point_frac=1 / 32)
+        vals.append(ms)
+    value = statistics.mean(vals)
+    g = w["grid"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "ms/catalog", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(g.n), "shells": len(w["shells"]), "orders": list(orders)},
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 1), "unit": "ms/catalog", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * conker.h -- C ABI of a GB300 (sm_103a) implementation of the ConKer
+ * n-point correlation hot path (arXiv 2108.00015): mapping (Sec. 2.2),
+ * spherical-shell kernels (Sec. 2.3), FFT convolution (Sec. 2.4, Eqs. 9-10)
+ * and n-point summation (Sec. 2.5, Eqs. 11-14) for n = 2..5.
+ *
+ * Conventions for every entry point
+ *   - Every function returns a ck_status; no exception or abort crosses the
+ *     boundary.  CK_OK is 0.
+ *   - "device" pointers are CUDA device memory (e.g. a torch CUDA tensor's
+ *     data_ptr()); "host or device" pointers are detected with
+ *     cudaPointerGetAttributes, and host memory may be pageable or pinned.
+ *   - The caller owns every input and output buffer.  The plan owns its
+ *     workspace unless the caller passes one to ck_plan_create.
+ *   - Work is ordered on the caller's CUDA stream (NULL = legacy default
+ *     stream).  A call returns without synchronising unless an output is in
+ *     host memory or an input is in host memory.
+ *   - Grids are stored z-major: cell (ix, iy, iz) is element
+ *     (iz * n[1] + iy) * n[0] + ix.  Half spectra are complex64 (float2,
+ *     re/im) [n[2]][n[1]][spec_pitch] with kx = 0 .. n[0]/2 valid.
+ *   - Errors found on the device (a wait that timed out, a zero
+ *     denominator, a guard-band violation) are recorded in the plan's device
+ *     status word; ck_plan_status() synchronises and returns it.  Calls that
+ *     synchronise anyway (host outputs) return it directly.
+ */
+#ifndef CONKER_H
+#define CONKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CK_ABI_VERSION 1
+#define CK_MAX_SHELLS 64
+#define CK_MAX_ORDER 5
+
+typedef enum ck_status {
+  CK_OK = 0,
+  CK_ERR_ARG = 1,              /* a size, count or option is out of range       */
+  CK_ERR_BAD_POINTER = 2,      /* NULL where required, or wrong memory space    */
+  CK_ERR_OOM = 3,              /* device allocation failed / workspace too small */
+  CK_ERR_EMPTY_SHELL = 4,      /* a shell contains no lattice offset            */
+  CK_ERR_KERNEL_TOO_LARGE = 5, /* periodic axis: 2 max|m| >= n (offsets alias)  */
+  CK_ERR_GUARD_BAND = 6,       /* non-periodic: occupied extent + max|m| >= n   */
+  CK_ERR_ZERO_DENOM = 7,       /* some den <= 0: those xi entries are NaN       */
+  CK_ERR_TIMEOUT = 8,          /* a bounded device wait gave up                 */
+  CK_ERR_CUDA = 9,             /* a CUDA runtime call failed                    */
+  CK_ERR_UNSUPPORTED = 10,     /* grid axis not a product of 2, 3, 5 or > 512;
+                                  precision mode not built                      */
+  CK_ERR_NO_RANDOMS = 11,      /* ck_compute before ck_set_randoms              */
+  CK_ERR_EMPTY_CATALOG = 12    /* no data (or random) point fell in the grid    */
+} ck_status;
+
+/* Shell membership rules (Sec. 2.3).  CENTER_BIN keeps the integer offset m
+ * iff (s - w/2) <= |m| g < (s + w/2) (distances between cell centres);
+ * INTERSECT keeps m iff the sphere of radius s meets the cell cube:
+ * dmin(m)^2 <= s^2 < dmax(m)^2 (width ignored). */
+#define CK_SHELL_CENTER_BIN 0
+#define CK_SHELL_INTERSECT 1
+
+/* Arithmetic of the product-sum contraction (Sec. 2.5).  FFTs are FP32 in
+ * every mode and the cross-block reduction is FP64 in every mode. */
+typedef enum ck_precision {
+  CK_PREC_FP32 = 0,       /* FP32 CUDA-core products, FP32 partial sums     */
+  CK_PREC_SPLIT_BF16 = 1, /* reserved: tensor-core split-BF16 operands      */
+  CK_PREC_SPLIT_FP16 = 2, /* reserved: tensor-core split-FP16 operands      */
+  CK_PREC_FP64_SUM = 3    /* FP64 products and sums (reference contraction) */
+} ck_precision;
+
+/* A grid of n[0] x n[1] x n[2] cubic cells of side `cell`, lower corner
+ * `origin` (Sec. 2.2: grid spacing g_s).  Each n[a] must be even, <= 512 and
+ * have no prime factor other than 2, 3, 5.  periodic != 0 selects a periodic
+ * box (circular convolution); otherwise cells outside the box count as 0. */
+typedef struct ck_grid {
+  int32_t n[3];
+  double origin[3];
+  double cell;
+  int32_t periodic;
+} ck_grid;
+
+/* The radial bins (Sec. 2.3 / Sec. 3): n_shells radii (host array, copied at
+ * plan creation), a common width, and a membership rule. */
+typedef struct ck_shells {
+  int32_t n_shells;
+  const double* radius;
+  double width;
+  int32_t rule;
+} ck_shells;
+
+typedef struct ck_plan ck_plan;
+
+typedef struct ck_plan_info {
+  int64_t n_cells;                 /* n[0] n[1] n[2]                              */
+  int32_t spec_pitch;              /* complex elements per half-spectrum row      */
+  int32_t n_shells;
+  int32_t max_order;
+  int32_t max_offset[3];           /* max |m_a| over all shells                  */
+  int64_t shell_size[CK_MAX_SHELLS];/* |O_s|, lattice offsets per shell          */
+  int64_t n_multisets[CK_MAX_ORDER + 1]; /* C(N_s + n - 2, n - 1) for n = 2..5     */
+  size_t workspace_bytes;
+  int64_t bank_stride;             /* floats between shells in the W / B bank   */
+} ck_plan_info;
+
+/* Outputs of ck_compute.  For order n (index n = 2..5), xi[n], num[n] and
+ * den[n] each point to a dense symmetric row-major [N_s]^(n-1) FP64 tensor
+ * (host or device) or are NULL to skip.  num = sum_r N prod W_{s_i},
+ * den = sum_r Rt prod B_{s_i}, xi = num / den (Eq. 11; NaN where den <= 0).
+ * dropped (host or device, int64[2], may be NULL) receives the numbers of
+ * data and random points that fell outside a non-periodic grid. */
+typedef struct ck_outputs {
+  double* xi[CK_MAX_ORDER + 1];
+  double* num[CK_MAX_ORDER + 1];
+  double* den[CK_MAX_ORDER + 1];
+  int64_t* dropped;
+} ck_outputs;
+
+/* Workspace bytes ck_plan_create needs for these arguments (host only; no
+ * CUDA call).  Returns CK_ERR_ARG / CK_ERR_UNSUPPORTED / CK_ERR_EMPTY_SHELL /
+ * CK_ERR_KERNEL_TOO_LARGE exactly as ck_plan_create would. */
+ck_status ck_plan_workspace_size(const ck_grid* grid, const ck_shells* shells,
+                                 int32_t max_order, int32_t precision, size_t* bytes);
+
+/* Build a plan: validate the arguments (before any CUDA call), build each
+ * shell's offset list (Sec. 2.3), and compute every kernel spectrum
+ * K^_s = DFT(K_s) / N_c on the device once (real and even, stored as an
+ * octant).  `workspace` (device, >= ck_plan_workspace_size bytes, 256-byte
+ * aligned) is borrowed for the plan's lifetime; NULL makes the plan allocate
+ * and own it.  max_order in 2..5.  On error *out is NULL. */
+ck_status ck_plan_create(const ck_grid* grid, const ck_shells* shells, int32_t max_order,
+                         int32_t precision, void* workspace, size_t workspace_bytes,
+                         void* stream, ck_plan** out);
+
+/* Release the plan (synchronises its last stream; frees owned memory). */
+ck_status ck_plan_destroy(ck_plan* plan);
+
+ck_status ck_plan_get_info(const ck_plan* plan, ck_plan_info* info);
+
+/* Grid the random catalog R (Sec. 2.2) and cache what depends on it alone:
+ * the counts R, and the raw denominators den_raw_n = sum_r R prod (R***K_s)
+ * (Eq. 10 with R unnormalised); ck_compute scales them by alpha^n, since
+ * Rt = alpha R and B_s = alpha (R***K_s).  x, y, z: float32 positions, host
+ * or device, n >= 0 points. */
+ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const float* z,
+                         int64_t n, void* stream);
+
+/* One catalog through the whole path: grid D (Sec. 2.2), alpha = sum D /
+ * sum R, N = D - alpha R (Eq. 8), W_s = N***K_s for every shell by FFT
+ * (Eq. 9), the product sums num_n over all multisets of the orders in
+ * order_mask (bit n set -> order n, 2..max_order; Eq. 11), den_n =
+ * alpha^n den_raw_n, xi_n = num_n / den_n.  Needs ck_set_randoms first. */
+ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                     int32_t order_mask, const ck_outputs* out, void* stream);
+
+/* Synchronise `stream` and return (and clear) the plan's device status. */
+ck_status ck_plan_status(ck_plan* plan, void* stream);
+
+/* --- stage access (parity tests and diagnostics) ---------------------------- */
+
+/* Copy the last data / random count grids (uint32 [N_c], device or host; either
+ * may be NULL). */
+ck_status ck_get_grids(ck_plan* plan, uint32_t* d_counts, uint32_t* r_counts, void* stream);
+
+/* Copy a real field: which = 0 -> N of the last ck_compute, which = 1 -> R (as
+ * float) of the last ck_set_randoms ... valid until the next call that
+ * overwrites it (float [N_c], device or host). */
+ck_status ck_get_field(ck_plan* plan, int32_t which, float* out, void* stream);
+
+/* Copy shell `shell` of the convolution bank last produced: W_s after
+ * ck_compute, R***K_s after ck_set_randoms (float [N_c], device or host). */
+ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream);
+
+/* Copy the octant of K^_s = DFT(K_s) / N_c: float
+ * [n[2]/2+1][n[1]/2+1][n[0]/2+1], device or host. */
+ck_status ck_get_kernel_spectrum(ck_plan* plan, int32_t shell, float* out, void* stream);
+
+/* Forward real-to-complex 3D DFT of a real field (device float [N_c]) into a
+ * half spectrum (device float2 [n[2]][n[1]][spec_pitch]); unnormalised,
+ * exponent sign -1.  Uses the plan's scratch spectrum. */
+ck_status ck_fft_r2c(ck_plan* plan, const float* in, void* out_spec, void* stream);
+
+/* Inverse complex-to-real 3D DFT (exponent sign +1, unnormalised) of a half
+ * spectrum (device, not modified) into a real field (device float [N_c]). */
+ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* stream);
+
+/* The summation stage alone (Sec. 2.5): for every order n in order_mask and
+ * every multiset s_1 <= .. <= s_{n-1} (lexicographic order),
+ * sums[n][j] = sum_r w0[r] prod_i bank[s_i * bank_stride + r].  w0: device
+ * float [N_c]; bank: device float [N_s][bank_stride], bank_stride >= N_c and a
+ * multiple of 4; sums[n]: device double [C(N_s + n - 2, n - 1)] or NULL. */
+ck_status ck_contract(ck_plan* plan, const float* w0, const float* bank, int64_t bank_stride,
+                      int32_t order_mask, double* const* sums, void* stream);
+
+/* --- per-stage device timing --------------------------------------------------
+ * When enabled, the library records a CUDA event pair on the caller's stream
+ * around every kernel it launches, grouped by stage, together with the
+ * algorithmic bytes that launch must move (inputs read once + outputs written
+ * once).  ck_profile_enable resets the accumulators; ck_profile_read
+ * synchronises each recorded event and returns the totals. */
+#define CK_STAGES 12
+typedef struct ck_stage_times {
+  double ms[CK_STAGES];       /* summed event time of the stage's launches   */
+  int64_t launches[CK_STAGES];
+  double bytes[CK_STAGES];    /* summed algorithmic bytes of those launches  */
+} ck_stage_times;
+
+ck_status ck_profile_enable(ck_plan* plan, int32_t enable);
+ck_status ck_profile_read(ck_plan* plan, ck_stage_times* out);
+/* Name of stage i (0 <= i < CK_STAGES), or NULL. */
+const char* ck_stage_name(int32_t stage);
+
+const char* ck_status_string(ck_status status);
+int32_t ck_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONKER_H */

@@ -1,0 +1,320 @@
+"""Thin ctypes binding of libconker.so (include/conker.h).
+
+Argument marshalling only: every step of the correlation path runs in the
+library's CUDA kernels.  Torch supplies device memory and streams: inputs may
+be torch CUDA tensors (their data_ptr is passed), host numpy arrays (the
+library stages them), and outputs are torch tensors allocated here.  If the
+shared library is missing or does not load, every call raises: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Iterable, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libconker.so")
+
+CK_MAX_SHELLS = 64
+CK_MAX_ORDER = 5
+
+STATUS = {
+    0: "CK_OK", 1: "CK_ERR_ARG", 2: "CK_ERR_BAD_POINTER", 3: "CK_ERR_OOM", 4: "CK_ERR_EMPTY_SHELL",
+    5: "CK_ERR_KERNEL_TOO_LARGE", 6: "CK_ERR_GUARD_BAND", 7: "CK_ERR_ZERO_DENOM", 8: "CK_ERR_TIMEOUT",
+    9: "CK_ERR_CUDA", 10: "CK_ERR_UNSUPPORTED", 11: "CK_ERR_NO_RANDOMS", 12: "CK_ERR_EMPTY_CATALOG",
+}
+RULES = {"center_bin": 0, "intersect": 1}
+PRECISIONS = {"fp32": 0, "split_bf16": 1, "split_fp16": 2, "fp64": 3}
+
+
+class CkError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        name = STATUS.get(self.code, str(code))
+        msg = _lib().ck_status_string(self.code).decode() if _LIB is not None else name
+        super().__init__(f"{where}: {name} ({msg})")
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("origin", ctypes.c_double * 3), ("cell", ctypes.c_double),
+                ("periodic", ctypes.c_int32)]
+
+
+class _Shells(ctypes.Structure):
+    _fields_ = [("n_shells", ctypes.c_int32), ("radius", ctypes.POINTER(ctypes.c_double)),
+                ("width", ctypes.c_double), ("rule", ctypes.c_int32)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_int64), ("spec_pitch", ctypes.c_int32), ("n_shells", ctypes.c_int32),
+                ("max_order", ctypes.c_int32), ("max_offset", ctypes.c_int32 * 3),
+                ("shell_size", ctypes.c_int64 * CK_MAX_SHELLS), ("n_multisets", ctypes.c_int64 * (CK_MAX_ORDER + 1)),
+                ("workspace_bytes", ctypes.c_size_t), ("bank_stride", ctypes.c_int64)]
+
+
+CK_STAGES = 12
+
+
+class _StageTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * CK_STAGES), ("launches", ctypes.c_int64 * CK_STAGES),
+                ("bytes", ctypes.c_double * CK_STAGES)]
+
+
+class _Outputs(ctypes.Structure):
+    _fields_ = [("xi", ctypes.c_void_p * (CK_MAX_ORDER + 1)), ("num", ctypes.c_void_p * (CK_MAX_ORDER + 1)),
+                ("den", ctypes.c_void_p * (CK_MAX_ORDER + 1)), ("dropped", ctypes.c_void_p)]
+
+
+_LIB = None
+
+# (name, restype, argtypes) for every entry point declared in include/conker.h
+_P = ctypes.c_void_p
+_SIGS = [
+    ("ck_abi_version", ctypes.c_int32, []),
+    ("ck_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("ck_plan_workspace_size", ctypes.c_int, [ctypes.POINTER(_Grid), ctypes.POINTER(_Shells), ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    ("ck_plan_create", ctypes.c_int, [ctypes.POINTER(_Grid), ctypes.POINTER(_Shells), ctypes.c_int32, ctypes.c_int32,
+                                      _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    ("ck_plan_destroy", ctypes.c_int, [_P]),
+    ("ck_plan_get_info", ctypes.c_int, [_P, ctypes.POINTER(_Info)]),
+    ("ck_set_randoms", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("ck_compute", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
+    ("ck_plan_status", ctypes.c_int, [_P, _P]),
+    ("ck_get_grids", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ck_get_field", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    ("ck_get_bank", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    ("ck_get_kernel_spectrum", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    ("ck_fft_r2c", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ck_fft_c2r", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ck_contract", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P), _P]),
+    ("ck_profile_enable", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("ck_profile_read", ctypes.c_int, [_P, ctypes.POINTER(_StageTimes)]),
+    ("ck_stage_name", ctypes.c_char_p, [ctypes.c_int32]),
+]
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load the library (raises if it is missing)."""
+    return _lib()
+
+
+def exported_symbols() -> Sequence[str]:
+    return [s[0] for s in _SIGS]
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise CkError(code, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(a):
+    """data pointer of a torch tensor or a numpy array (host)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _as_f32(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float32)
+    torch = _torch()
+    assert a.dtype == torch.float32 and a.is_contiguous(), "positions must be contiguous float32"
+    return a
+
+
+def order_mask(orders: Iterable[int]) -> int:
+    m = 0
+    for n in orders:
+        m |= 1 << int(n)
+    return m
+
+
+class Plan:
+    """A ck_plan: one grid, one shell bank, orders up to max_order."""
+
+    def __init__(self, n: Sequence[int], origin: Sequence[float], cell: float, periodic: bool,
+                 radii: Sequence[float], width: float, max_order: int = 3, rule: str = "center_bin",
+                 precision: str = "fp32", workspace: str = "torch", stream=None):
+        torch = _torch()
+        lib = _lib()
+        self._grid = _Grid((ctypes.c_int32 * 3)(*[int(v) for v in n]), (ctypes.c_double * 3)(*[float(v) for v in origin]),
+                           float(cell), 1 if periodic else 0)
+        self._radii = (ctypes.c_double * len(radii))(*[float(r) for r in radii])
+        self._shells = _Shells(len(radii), self._radii, float(width), RULES[rule])
+        self.max_order = int(max_order)
+        self.n_shells = len(radii)
+        prec = PRECISIONS[precision]
+        self._ws = None
+        ws_ptr, ws_bytes = None, 0
+        if workspace == "torch":
+            nbytes = ctypes.c_size_t(0)
+            _check(lib.ck_plan_workspace_size(ctypes.byref(self._grid), ctypes.byref(self._shells), self.max_order,
+                                              prec, ctypes.byref(nbytes)), "ck_plan_workspace_size")
+            self._ws = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            ws_ptr = ctypes.c_void_p((base + 255) // 256 * 256)
+            ws_bytes = int(nbytes.value)
+        h = ctypes.c_void_p()
+        _check(lib.ck_plan_create(ctypes.byref(self._grid), ctypes.byref(self._shells), self.max_order, prec, ws_ptr,
+                                  ws_bytes, _stream_ptr(stream), ctypes.byref(h)), "ck_plan_create")
+        self._h = h
+        info = _Info()
+        _check(lib.ck_plan_get_info(self._h, ctypes.byref(info)), "ck_plan_get_info")
+        self.n_cells = int(info.n_cells)
+        self.spec_pitch = int(info.spec_pitch)
+        self.max_offset = tuple(int(v) for v in info.max_offset)
+        self.shell_size = [int(info.shell_size[s]) for s in range(self.n_shells)]
+        self.n_multisets = {k: int(info.n_multisets[k]) for k in range(2, self.max_order + 1)}
+        self.workspace_bytes = int(info.workspace_bytes)
+        self.bank_stride = int(info.bank_stride)
+        self.shape = (int(n[2]), int(n[1]), int(n[0]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().ck_plan_destroy(self._h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the path ----------------------------------------------------------
+    def set_randoms(self, x, y, z, stream=None):
+        x, y, z = _as_f32(x), _as_f32(y), _as_f32(z)
+        _check(_lib().ck_set_randoms(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), _stream_ptr(stream)),
+               "ck_set_randoms")
+
+    def compute(self, x, y, z, orders=(2, 3), out: str = "device", stream=None, want=("xi", "num", "den"),
+                outputs: Optional[Dict[str, Dict[int, object]]] = None) -> Dict[str, object]:
+        """One catalog; returns {'xi': {n: T}, 'num': ..., 'den': ..., 'dropped': T} with dense
+        [N_s]^(n-1) float64 tensors on the device (out='device') or in host memory (out='host')."""
+        torch = _torch()
+        x, y, z = _as_f32(x), _as_f32(y), _as_f32(z)
+        ns = self.n_shells
+        res: Dict[str, object] = {k: {} for k in ("xi", "num", "den")}
+        o = _Outputs()
+        dev = "cuda" if out == "device" else "cpu"
+        for n in orders:
+            for key in want:
+                if outputs is not None:
+                    t = outputs[key][n]
+                else:
+                    t = torch.empty((ns,) * (n - 1), dtype=torch.float64, device=dev, pin_memory=(dev == "cpu"))
+                res[key][n] = t
+                getattr(o, key)[n] = t.data_ptr()
+        if outputs is not None and "dropped" in outputs:
+            dropped = outputs["dropped"]
+        else:
+            dropped = torch.zeros(2, dtype=torch.int64, device=dev)
+        o.dropped = dropped.data_ptr()
+        res["dropped"] = dropped
+        code = _lib().ck_compute(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), order_mask(orders),
+                                 ctypes.byref(o), _stream_ptr(stream))
+        res["status"] = int(code)
+        if code not in (0, 7):  # a zero denominator still fills the outputs (NaN there)
+            raise CkError(code, "ck_compute")
+        return res
+
+    def status(self, stream=None) -> int:
+        return int(_lib().ck_plan_status(self._h, _stream_ptr(stream)))
+
+    # -- per-stage event timing -------------------------------------------
+    def profile(self, enable: bool = True):
+        _check(_lib().ck_profile_enable(self._h, 1 if enable else 0), "ck_profile_enable")
+
+    def profile_read(self) -> Dict[str, Dict[str, float]]:
+        t = _StageTimes()
+        _check(_lib().ck_profile_read(self._h, ctypes.byref(t)), "ck_profile_read")
+        out = {}
+        for i in range(CK_STAGES):
+            if t.launches[i]:
+                out[_lib().ck_stage_name(i).decode()] = dict(ms=float(t.ms[i]), launches=int(t.launches[i]),
+                                                             bytes=float(t.bytes[i]))
+        return out
+
+    # -- stage access ------------------------------------------------------
+    def grids(self, stream=None):
+        torch = _torch()
+        d = torch.empty(self.shape, dtype=torch.int32, device="cuda")
+        r = torch.empty(self.shape, dtype=torch.int32, device="cuda")
+        _check(_lib().ck_get_grids(self._h, _ptr(d), _ptr(r), _stream_ptr(stream)), "ck_get_grids")
+        return d, r
+
+    def field(self, which: int, stream=None):
+        torch = _torch()
+        f = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        _check(_lib().ck_get_field(self._h, int(which), _ptr(f), _stream_ptr(stream)), "ck_get_field")
+        return f
+
+    def bank(self, shell: int, stream=None):
+        torch = _torch()
+        f = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        _check(_lib().ck_get_bank(self._h, int(shell), _ptr(f), _stream_ptr(stream)), "ck_get_bank")
+        return f
+
+    def kernel_spectrum(self, shell: int, stream=None):
+        torch = _torch()
+        nz, ny, nx = self.shape
+        f = torch.empty((nz // 2 + 1, ny // 2 + 1, nx // 2 + 1), dtype=torch.float32, device="cuda")
+        _check(_lib().ck_get_kernel_spectrum(self._h, int(shell), _ptr(f), _stream_ptr(stream)),
+               "ck_get_kernel_spectrum")
+        return f
+
+    def fft_r2c(self, real, stream=None):
+        torch = _torch()
+        nz, ny, nx = self.shape
+        spec = torch.empty((nz, ny, self.spec_pitch), dtype=torch.complex64, device="cuda")
+        _check(_lib().ck_fft_r2c(self._h, _ptr(real), _ptr(spec), _stream_ptr(stream)), "ck_fft_r2c")
+        return spec
+
+    def fft_c2r(self, spec, stream=None):
+        torch = _torch()
+        out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        _check(_lib().ck_fft_c2r(self._h, _ptr(spec), _ptr(out), _stream_ptr(stream)), "ck_fft_c2r")
+        return out
+
+    def contract(self, w0, bank, bank_stride: int, orders=(2, 3), stream=None):
+        torch = _torch()
+        sums = {n: torch.empty(self.n_multisets[n], dtype=torch.float64, device="cuda") for n in orders}
+        arr = (ctypes.c_void_p * (CK_MAX_ORDER + 1))()
+        for n, t in sums.items():
+            arr[n] = t.data_ptr()
+        _check(_lib().ck_contract(self._h, _ptr(w0), _ptr(bank), int(bank_stride), order_mask(orders), arr,
+                                  _stream_ptr(stream)), "ck_contract")
+        return sums

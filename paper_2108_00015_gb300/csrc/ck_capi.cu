@@ -1,0 +1,514 @@
+// ck_capi.cu -- the C ABI (conker.h): plan life cycle, the per-catalog
+// pipeline (mapping -> FFT convolution -> summation -> xi) and stage access.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "ck_device.cuh"
+#include "ck_internal.h"
+
+namespace ck {
+int64_t host_multiset_rank(const int* s, int k, int ns);
+
+int prof_begin(const Plan& p, int stage, double bytes, cudaStream_t st) {
+  Profiler& f = p.prof;
+  if (!f.on) return -1;
+  if (f.used >= f.recs.size()) {
+    ++f.dropped;
+    return -1;
+  }
+  Profiler::Rec& r = f.recs[f.used];
+  r.stage = stage;
+  r.bytes = bytes;
+  if (cudaEventRecord(r.a, st) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (int)f.used++;
+}
+
+void prof_end(const Plan& p, int idx, cudaStream_t st) {
+  if (idx < 0) return;
+  if (cudaEventRecord(p.prof.recs[(size_t)idx].b, st) != cudaSuccess) cudaGetLastError();
+}
+}  // namespace ck
+
+namespace {
+constexpr size_t kProfPool = 16384;
+const char* kStageNames[CK_STAGES] = {"grid_points", "prepare_field", "fft_x_r2c", "fft_y_fwd",
+                                      "fft_z_fwd", "fft_z_inv_mul", "fft_y_inv", "fft_x_c2r",
+                                      "contract", "reduce", "finalize", "other"};
+
+void prof_collect(ck::Plan& p) {
+  ck::Profiler& f = p.prof;
+  for (size_t i = 0; i < f.used; ++i) {
+    ck::Profiler::Rec& r = f.recs[i];
+    float ms = 0.0f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      f.ms[r.stage] += ms;
+      f.launches[r.stage] += 1;
+      f.bytes[r.stage] += r.bytes;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  f.used = 0;
+}
+}  // namespace
+
+using namespace ck;
+
+namespace {
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Device memory (or managed) vs host memory.
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define CK_TRY(expr)                                  \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_status(e_);    \
+  } while (0)
+
+#define CK_TRY_S(expr)                                \
+  do {                                                \
+    ck_status s_ = (expr);                            \
+    if (s_ != CK_OK) return s_;                       \
+  } while (0)
+
+__global__ void reset_state_kernel(DevState* st, int which) {
+  st->kept[which] = 0;
+  st->dropped[which] = 0;
+  for (int a = 0; a < 3; ++a) {
+    st->bbox_min[which][a] = 0x7fffffff;
+    st->bbox_max[which][a] = -0x7fffffff - 1;
+  }
+}
+
+size_t al(size_t b) { return (b + 255) / 256 * 256; }
+
+ck_status carve(Plan& p) {
+  unsigned char* b = static_cast<unsigned char*>(p.ws);
+  auto take = [&](size_t bytes) {
+    unsigned char* r = b;
+    b += al(bytes);
+    return r;
+  };
+  p.counts[0] = reinterpret_cast<uint32_t*>(take((size_t)p.nc * 4));
+  p.counts[1] = reinterpret_cast<uint32_t*>(take((size_t)p.nc * 4));
+  p.field = reinterpret_cast<float*>(take((size_t)p.field_stride * 4));
+  p.spec = reinterpret_cast<float2*>(take((size_t)p.spec_elems * 8));
+  p.tmp = reinterpret_cast<float2*>(take((size_t)p.spec_elems * 8));
+  p.khat = reinterpret_cast<float*>(take((size_t)p.ns * p.oct_elems * 4));
+  p.bank = reinterpret_cast<float*>(take(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8)));
+  p.partials = reinterpret_cast<double*>(take(p.partials_cap * 8));
+  p.staging = reinterpret_cast<float*>(take((size_t)2 * 3 * p.staging_pts * 4));
+  for (int a = 0; a < 3; ++a) p.thr[a] = reinterpret_cast<float*>(take((size_t)(p.grid.n[a] + 1) * 4));
+  for (int a = 0; a < 3; ++a) p.tw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
+  p.dstate = reinterpret_cast<DevState*>(take(sizeof(DevState)));
+  p.den_raw = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
+  p.sums = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
+  p.dense = reinterpret_cast<double*>(take((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8));
+  p.dense_map = reinterpret_cast<int*>(take((size_t)std::max<int64_t>(p.dense_total, 1) * 4));
+  p.table_arena = take(p.table_arena_cap);
+  const size_t used = (size_t)(b - static_cast<unsigned char*>(p.ws));
+  return used <= p.ws_bytes ? CK_OK : CK_ERR_OOM;
+}
+
+// Smallest float32 >= fl64(origin + fl64(k * cell)), k = 0..n.
+void thresholds(double o, double g, int n, std::vector<float>& t) {
+  t.resize((size_t)n + 1);
+  for (int k = 0; k <= n; ++k) {
+    volatile double prod = (double)k * g;
+    const double e = o + prod;
+    float f = (float)e;
+    if ((double)f < e) f = nextafterf(f, INFINITY);
+    t[(size_t)k] = f;
+  }
+}
+
+void twiddles(int n, std::vector<float2>& w) {
+  w.resize((size_t)n);
+  for (int t = 0; t < n; ++t) {
+    const double a = 2.0 * M_PI * (double)t / (double)n;
+    w[(size_t)t] = make_float2((float)cos(a), (float)-sin(a));
+  }
+}
+
+ck_status upload_tables(Plan& p, cudaStream_t st) {
+  for (int a = 0; a < 3; ++a) {
+    std::vector<float> t;
+    thresholds(p.grid.origin[a], p.grid.cell, p.grid.n[a], t);
+    CK_TRY(cudaMemcpy(p.thr[a], t.data(), t.size() * 4, cudaMemcpyHostToDevice));
+    std::vector<float2> w;
+    twiddles(p.grid.n[a], w);
+    CK_TRY(cudaMemcpy(p.tw[a], w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+  }
+  // dense [N_s]^(n-1) index -> rank of its sorted multiset
+  std::vector<int> map((size_t)std::max<int64_t>(p.dense_total, 1), 0);
+  for (int n = 2; n <= p.max_order; ++n) {
+    const int k = n - 1;
+    for (int64_t d = 0; d < p.dense_elems[n]; ++d) {
+      int s[4];
+      int64_t r = d;
+      for (int i = k - 1; i >= 0; --i) {
+        s[i] = (int)(r % p.ns);
+        r /= p.ns;
+      }
+      std::sort(s, s + k);
+      map[(size_t)(p.dense_base[n] + d)] = (int)host_multiset_rank(s, k, p.ns);
+    }
+  }
+  CK_TRY(cudaMemcpy(p.dense_map, map.data(), map.size() * 4, cudaMemcpyHostToDevice));
+  CK_TRY(cudaMemsetAsync(p.dstate, 0, sizeof(DevState), st));
+  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 0);
+  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 1);
+  return cuda_status(cudaGetLastError());
+}
+
+// Grid one catalog (host or device positions) into counts[which].
+ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, int64_t n, int which,
+                       cudaStream_t st) {
+  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, which);
+  CK_TRY(cudaMemsetAsync(p.counts[which], 0, (size_t)p.nc * 4, st));
+  if (n == 0) return cuda_status(cudaGetLastError());
+  const bool dx = is_device_ptr(x), dy = is_device_ptr(y), dz = is_device_ptr(z);
+  if (dx != dy || dx != dz) return CK_ERR_BAD_POINTER;
+  if (dx) {
+    launch_grid_points(p, x, y, z, n, which, st);
+    return cuda_status(cudaGetLastError());
+  }
+  // host positions: stream them through the staging slots
+  int slot = 0;
+  for (int64_t off = 0; off < n; off += p.staging_pts) {
+    const int64_t cnt = std::min<int64_t>(p.staging_pts, n - off);
+    float* sx = p.staging + (size_t)slot * 3 * p.staging_pts;
+    float* sy = sx + p.staging_pts;
+    float* sz = sy + p.staging_pts;
+    CK_TRY(cudaMemcpyAsync(sx, x + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+    CK_TRY(cudaMemcpyAsync(sy, y + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+    CK_TRY(cudaMemcpyAsync(sz, z + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+    launch_grid_points(p, sx, sy, sz, cnt, which, st);
+    slot ^= 1;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// Convolve the current field with every shell kernel into the bank.
+void convolve_bank(Plan& p, cudaStream_t st) {
+  launch_fft_forward(p, p.field, p.spec, st);
+  for (int s = 0; s < p.ns; ++s)
+    launch_fft_inverse(p, p.spec, p.khat + (size_t)s * p.oct_elems, p.tmp, p.bank + (size_t)s * p.field_stride, st);
+}
+
+int full_mask(const Plan& p) {
+  int m = 0;
+  for (int n = 2; n <= p.max_order; ++n) m |= 1 << n;
+  return m;
+}
+
+ck_status read_status(Plan& p, cudaStream_t st, bool clear) {
+  int h = 0;
+  CK_TRY(cudaMemcpyAsync(&h, &p.dstate->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK_TRY(cudaStreamSynchronize(st));
+  if (clear && h != 0) CK_TRY(cudaMemsetAsync(&p.dstate->status, 0, sizeof(int), st));
+  return (ck_status)h;
+}
+
+ck_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st, bool* host_seen) {
+  if (!dst) return CK_OK;
+  if (is_device_ptr(dst)) {
+    CK_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+  } else {
+    *host_seen = true;
+    CK_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  return CK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ck_abi_version(void) { return CK_ABI_VERSION; }
+
+const char* ck_status_string(ck_status s) {
+  switch (s) {
+    case CK_OK: return "ok";
+    case CK_ERR_ARG: return "argument out of range";
+    case CK_ERR_BAD_POINTER: return "bad pointer";
+    case CK_ERR_OOM: return "out of device memory / workspace too small";
+    case CK_ERR_EMPTY_SHELL: return "a shell contains no lattice offset";
+    case CK_ERR_KERNEL_TOO_LARGE: return "shell kernel reaches half the box (offsets alias)";
+    case CK_ERR_GUARD_BAND: return "occupied cells plus kernel reach exceed a non-periodic box";
+    case CK_ERR_ZERO_DENOM: return "non-positive denominator (xi = NaN there)";
+    case CK_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case CK_ERR_CUDA: return "CUDA runtime error";
+    case CK_ERR_UNSUPPORTED: return "unsupported size or mode";
+    case CK_ERR_NO_RANDOMS: return "ck_set_randoms has not been called";
+    case CK_ERR_EMPTY_CATALOG: return "no point fell inside the grid";
+  }
+  return "unknown status";
+}
+
+ck_status ck_plan_workspace_size(const ck_grid* grid, const ck_shells* shells, int32_t max_order,
+                                 int32_t precision, size_t* bytes) {
+  if (!bytes) return CK_ERR_BAD_POINTER;
+  Plan p;
+  CK_TRY_S(validate_and_layout(grid, shells, max_order, precision, &p));
+  *bytes = workspace_bytes(p);
+  return CK_OK;
+}
+
+ck_status ck_plan_create(const ck_grid* grid, const ck_shells* shells, int32_t max_order, int32_t precision,
+                         void* workspace, size_t workspace_bytes_in, void* stream, ck_plan** out) {
+  if (!out) return CK_ERR_BAD_POINTER;
+  *out = nullptr;
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return CK_ERR_OOM;
+  ck_status s = validate_and_layout(grid, shells, max_order, precision, p);
+  if (s != CK_OK) { delete p; return s; }
+  const size_t need = workspace_bytes(*p);
+  cudaStream_t st = S(stream);
+  auto fail = [&](ck_status code) {
+    if (p->owns_ws && p->ws) cudaFree(p->ws);
+    delete p;
+    return code;
+  };
+  if (cudaGetDevice(&p->device) != cudaSuccess) return fail(CK_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+    return fail(CK_ERR_CUDA);
+  if (workspace) {
+    if (workspace_bytes_in < need) return fail(CK_ERR_OOM);
+    if (((uintptr_t)workspace & 255u) != 0 || !is_device_ptr(workspace)) return fail(CK_ERR_BAD_POINTER);
+    p->ws = workspace;
+    p->ws_bytes = workspace_bytes_in;
+  } else {
+    cudaError_t e = cudaMalloc(&p->ws, need);
+    if (e != cudaSuccess) { cudaGetLastError(); p->ws = nullptr; return fail(CK_ERR_OOM); }
+    p->owns_ws = true;
+    p->ws_bytes = need;
+  }
+  if ((s = carve(*p)) != CK_OK) return fail(s);
+  if ((s = fft_init_attributes()) != CK_OK) return fail(s);
+  if ((s = upload_tables(*p, st)) != CK_OK) return fail(s);
+  if ((s = build_kernel_spectra(*p, st)) != CK_OK) return fail(s);
+  *out = reinterpret_cast<ck_plan*>(p);
+  return CK_OK;
+}
+
+ck_status ck_plan_destroy(ck_plan* plan) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan* p = reinterpret_cast<Plan*>(plan);
+  cudaError_t e = cudaDeviceSynchronize();
+  for (auto& r : p->prof.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (p->owns_ws && p->ws) cudaFree(p->ws);
+  delete p;
+  return cuda_status(e);
+}
+
+ck_status ck_plan_get_info(const ck_plan* plan, ck_plan_info* info) {
+  if (!plan || !info) return CK_ERR_BAD_POINTER;
+  const Plan* p = reinterpret_cast<const Plan*>(plan);
+  memset(info, 0, sizeof(*info));
+  info->n_cells = p->nc;
+  info->spec_pitch = p->px;
+  info->n_shells = p->ns;
+  info->max_order = p->max_order;
+  for (int a = 0; a < 3; ++a) info->max_offset[a] = p->maxoff[a];
+  for (int s = 0; s < p->ns; ++s) info->shell_size[s] = (int64_t)p->offsets[s].size() / 3;
+  for (int n = 0; n <= CK_MAX_ORDER; ++n) info->n_multisets[n] = p->n_multisets[n];
+  info->workspace_bytes = p->ws_bytes;
+  info->bank_stride = p->field_stride;
+  return CK_OK;
+}
+
+ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  if (n < 0) return CK_ERR_ARG;
+  if (n > 0 && (!x || !y || !z)) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t st = S(stream);
+  p.have_randoms = false;
+  CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st));
+  launch_prepare_randoms(p, st);
+  convolve_bank(p, st);
+  p.bank_holds = 1;
+  CK_TRY_S(launch_contract(p, full_mask(p), p.field, p.bank, p.field_stride, p.den_raw, st));
+  CK_TRY(cudaGetLastError());
+  p.have_randoms = true;
+  return CK_OK;
+}
+
+ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                     int32_t order_mask, const ck_outputs* out, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (n < 0) return CK_ERR_ARG;
+  if (n > 0 && (!x || !y || !z)) return CK_ERR_BAD_POINTER;
+  if (order_mask == 0 || (order_mask & ~full_mask(p)) != 0) return CK_ERR_ARG;
+  if (!p.have_randoms) return CK_ERR_NO_RANDOMS;
+  cudaStream_t st = S(stream);
+  CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st));
+  launch_prepare_data(p, st);
+  convolve_bank(p, st);
+  p.bank_holds = 0;
+  CK_TRY_S(launch_contract(p, order_mask, p.field, p.bank, p.field_stride, p.sums, st));
+  launch_finalize(p, order_mask, st);
+  CK_TRY(cudaGetLastError());
+  bool host_seen = false;
+  if (out) {
+    for (int k = 2; k <= p.max_order; ++k) {
+      if (!((order_mask >> k) & 1)) continue;
+      const size_t bytes = (size_t)p.dense_elems[k] * 8;
+      CK_TRY_S(copy_out(out->xi[k], p.dense + p.dense_base[k], bytes, st, &host_seen));
+      CK_TRY_S(copy_out(out->num[k], p.dense + p.dense_total + p.dense_base[k], bytes, st, &host_seen));
+      CK_TRY_S(copy_out(out->den[k], p.dense + 2 * p.dense_total + p.dense_base[k], bytes, st, &host_seen));
+    }
+    CK_TRY_S(copy_out(out->dropped, p.dstate->dropped, 2 * sizeof(int64_t), st, &host_seen));
+  }
+  if (host_seen) return read_status(p, st, true);
+  return CK_OK;
+}
+
+ck_status ck_plan_status(ck_plan* plan, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  return read_status(*reinterpret_cast<Plan*>(plan), S(stream), true);
+}
+
+const char* ck_stage_name(int32_t stage) {
+  return (stage >= 0 && stage < CK_STAGES) ? kStageNames[stage] : nullptr;
+}
+
+ck_status ck_profile_enable(ck_plan* plan, int32_t enable) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  Profiler& f = p.prof;
+  if (enable && f.recs.empty()) {
+    f.recs.resize(kProfPool);
+    for (auto& r : f.recs) {
+      CK_TRY(cudaEventCreate(&r.a));
+      CK_TRY(cudaEventCreate(&r.b));
+    }
+  }
+  if (f.used) CK_TRY(cudaDeviceSynchronize());
+  f.used = 0;
+  f.dropped = 0;
+  for (int i = 0; i < CK_STAGES; ++i) {
+    f.ms[i] = 0.0;
+    f.launches[i] = 0;
+    f.bytes[i] = 0.0;
+  }
+  f.on = enable != 0;
+  return CK_OK;
+}
+
+ck_status ck_profile_read(ck_plan* plan, ck_stage_times* out) {
+  if (!plan || !out) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  prof_collect(p);
+  for (int i = 0; i < CK_STAGES; ++i) {
+    out->ms[i] = p.prof.ms[i];
+    out->launches[i] = p.prof.launches[i];
+    out->bytes[i] = p.prof.bytes[i];
+  }
+  return CK_OK;
+}
+
+ck_status ck_get_grids(ck_plan* plan, uint32_t* d_counts, uint32_t* r_counts, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t st = S(stream);
+  bool host = false;
+  CK_TRY_S(copy_out(d_counts, p.counts[0], (size_t)p.nc * 4, st, &host));
+  CK_TRY_S(copy_out(r_counts, p.counts[1], (size_t)p.nc * 4, st, &host));
+  if (host) CK_TRY(cudaStreamSynchronize(st));
+  return CK_OK;
+}
+
+ck_status ck_get_field(ck_plan* plan, int32_t which, float* out, void* stream) {
+  if (!plan || !out) return CK_ERR_BAD_POINTER;
+  if (which != 0 && which != 1) return CK_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (which != p.bank_holds) return CK_ERR_ARG;  // the field buffer holds the last stage's input
+  cudaStream_t st = S(stream);
+  bool host = false;
+  CK_TRY_S(copy_out(out, p.field, (size_t)p.nc * 4, st, &host));
+  if (host) CK_TRY(cudaStreamSynchronize(st));
+  return CK_OK;
+}
+
+ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream) {
+  if (!plan || !out) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (shell < 0 || shell >= p.ns || p.bank_holds < 0) return CK_ERR_ARG;
+  cudaStream_t st = S(stream);
+  bool host = false;
+  CK_TRY_S(copy_out(out, p.bank + (size_t)shell * p.field_stride, (size_t)p.nc * 4, st, &host));
+  if (host) CK_TRY(cudaStreamSynchronize(st));
+  return CK_OK;
+}
+
+ck_status ck_get_kernel_spectrum(ck_plan* plan, int32_t shell, float* out, void* stream) {
+  if (!plan || !out) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (shell < 0 || shell >= p.ns) return CK_ERR_ARG;
+  cudaStream_t st = S(stream);
+  bool host = false;
+  CK_TRY_S(copy_out(out, p.khat + (size_t)shell * p.oct_elems, (size_t)p.oct_elems * 4, st, &host));
+  if (host) CK_TRY(cudaStreamSynchronize(st));
+  return CK_OK;
+}
+
+ck_status ck_fft_r2c(ck_plan* plan, const float* in, void* out_spec, void* stream) {
+  if (!plan || !in || !out_spec) return CK_ERR_BAD_POINTER;
+  if (!is_device_ptr(in) || !is_device_ptr(out_spec)) return CK_ERR_BAD_POINTER;
+  if (((uintptr_t)out_spec & 15u) != 0 || ((uintptr_t)in & 7u) != 0) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  launch_fft_forward(p, in, static_cast<float2*>(out_spec), S(stream));
+  return cuda_status(cudaGetLastError());
+}
+
+ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* stream) {
+  if (!plan || !in_spec || !out) return CK_ERR_BAD_POINTER;
+  if (!is_device_ptr(in_spec) || !is_device_ptr(out)) return CK_ERR_BAD_POINTER;
+  if (((uintptr_t)in_spec & 15u) != 0 || ((uintptr_t)out & 7u) != 0) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  launch_fft_inverse(p, static_cast<const float2*>(in_spec), nullptr, p.tmp, out, S(stream));
+  return cuda_status(cudaGetLastError());
+}
+
+ck_status ck_contract(ck_plan* plan, const float* w0, const float* bank, int64_t bank_stride, int32_t order_mask,
+                      double* const* sums, void* stream) {
+  if (!plan || !w0 || !bank || !sums) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (order_mask == 0 || (order_mask & ~full_mask(p)) != 0) return CK_ERR_ARG;
+  if (bank_stride < p.nc || (bank_stride % 4) != 0) return CK_ERR_ARG;
+  if (((uintptr_t)w0 & 15u) != 0 || ((uintptr_t)bank & 15u) != 0) return CK_ERR_BAD_POINTER;
+  if (!is_device_ptr(w0) || !is_device_ptr(bank)) return CK_ERR_BAD_POINTER;
+  cudaStream_t st = S(stream);
+  CK_TRY_S(launch_contract(p, order_mask, w0, bank, bank_stride, p.sums, st));
+  bool host = false;
+  for (int k = 2; k <= p.max_order; ++k) {
+    if (!((order_mask >> k) & 1) || !sums[k]) continue;
+    CK_TRY_S(copy_out(sums[k], p.sums + p.multiset_base[k], (size_t)p.n_multisets[k] * 8, st, &host));
+  }
+  if (host) CK_TRY(cudaStreamSynchronize(st));
+  return CK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,562 @@
+// ck_contract.cu -- the summation stage (Sec. 2.5, Eqs. 11-14): for every
+// multiset s_1 <= .. <= s_{n-1}, sum_r W0(r) prod_i W_{s_i}(r), n = 2..5,
+// with a fixed-order FP64 reduction across blocks, then xi_n = num / den.
+//
+// Two kernels:
+//  * contract_reg: few outputs (N_s <= 16 and n <= 3, or N_s <= 5 and
+//    n <= 5).  One warp streams cell chunks of W0 and every W_s into a
+//    four-stage shared-memory ring with bulk asynchronous copies (mbarrier
+//    completion); seven consumer warps take one cell per thread and keep every
+//    product sum in registers (FP32 over 128 chunks, then warp-reduced into
+//    FP64 in shared memory).  HBM-bound: it reads each W_s once.
+//  * contract_blocked: the general case as a blocked product
+//    T[p][q] = sum_r A_p(r) B_q(r) with A_p = W0 W_i W_j and B_q = W_k W_l
+//    generated per cell chunk in shared memory (64 x 64 output tiles, 4 x 4
+//    per thread).  Only tiles holding a canonical (p, q) are launched:
+//    n=2: A=W0, B=W_c;  n=3: A=W0 W_a, B=W_c, a <= c;  n=4: A=W0 W_a W_b,
+//    B=W_c, b <= c;  n=5: A=W0 W_a W_b, B=W_c W_d, b <= c.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ck_device.cuh"
+#include "ck_internal.h"
+
+namespace ck {
+
+__host__ __device__ constexpr int cmb(int n, int k) {
+  // C(n, k) for the small arguments used here
+  if (k < 0 || k > n) return 0;
+  long long r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return (int)r;
+}
+
+template <int NS, int MAXN>
+struct RegOut {
+  static constexpr int n2 = NS;
+  static constexpr int n3 = MAXN >= 3 ? cmb(NS + 1, 2) : 0;
+  static constexpr int n4 = MAXN >= 4 ? cmb(NS + 2, 3) : 0;
+  static constexpr int n5 = MAXN >= 5 ? cmb(NS + 3, 4) : 0;
+  static constexpr int total = n2 + n3 + n4 + n5;
+};
+
+constexpr int RK_CW = 7;            // consumer warps
+constexpr int RK_KC = 32 * RK_CW;   // cells per chunk (one per consumer thread)
+constexpr int RK_STAGES = 4;   // ring depth
+constexpr int RK_FLUSH = 128;  // chunks between FP32 -> FP64 flushes
+
+template <int NS, int MAXN>
+__device__ __forceinline__ void reg_accumulate(float* acc, const float* v) {
+  using O = RegOut<NS, MAXN>;
+  int i3 = O::n2, i4 = O::n2 + O::n3, i5 = O::n2 + O::n3 + O::n4;
+#pragma unroll
+  for (int a = 0; a < NS; ++a) {
+    const float p1 = v[0] * v[1 + a];
+    acc[a] += p1;
+    if constexpr (MAXN >= 3) {
+#pragma unroll
+      for (int b = a; b < NS; ++b) {
+        const float p2 = p1 * v[1 + b];
+        acc[i3++] += p2;
+        if constexpr (MAXN >= 4) {
+#pragma unroll
+          for (int c = b; c < NS; ++c) {
+            const float p3 = p2 * v[1 + c];
+            acc[i4++] += p3;
+            if constexpr (MAXN >= 5) {
+#pragma unroll
+              for (int d = c; d < NS; ++d) acc[i5++] += p3 * v[1 + d];
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int NOUT>
+__device__ __forceinline__ void reg_flush(float* acc, double* wacc, int lane) {
+#pragma unroll
+  for (int o = 0; o < NOUT; ++o) {
+    float t = acc[o];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+    if (lane == 0) wacc[o] += (double)t;
+    acc[o] = 0.0f;
+  }
+}
+
+template <int NS, int MAXN>
+__global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
+    contract_reg_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
+                        int64_t chunks_per_cta, double* __restrict__ partials, int* status) {
+  constexpr int NARR = NS + 1;
+  constexpr int NOUT = RegOut<NS, MAXN>::total;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* buf = reinterpret_cast<float*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)RK_STAGES * NARR * RK_KC * 4);
+  uint64_t* empty = full + RK_STAGES;
+  int* consumed_min = reinterpret_cast<int*>(empty + RK_STAGES);
+  double* wacc = reinterpret_cast<double*>(empty + RK_STAGES + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nchunks = (nc + RK_KC - 1) / RK_KC;
+  const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
+  const int64_t c1 = std::min<int64_t>(c0 + chunks_per_cta, nchunks);
+  const int nit = (int)std::max<int64_t>(c1 - c0, 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RK_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], RK_CW);
+    }
+    *consumed_min = nit;
+    fence_async_shared();
+  }
+  for (int i = threadIdx.x; i < RK_CW * NOUT; i += blockDim.x) wacc[i] = 0.0;
+  __syncthreads();
+  int issued = 0;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < nit; ++it) {
+        const int st = it % RK_STAGES;
+        const uint32_t ph = (uint32_t)(it / RK_STAGES) & 1u;
+        if (it >= RK_STAGES && !mbar_wait(&empty[st], ph ^ 1u, status)) break;
+        const int64_t cell0 = (c0 + it) * RK_KC;
+        const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
+        const uint32_t bytes = (uint32_t)((rem / 4) * 16);
+        mbar_arrive_expect_tx(&full[st], bytes * NARR);
+        if (bytes) {
+          float* dst = buf + (size_t)st * NARR * RK_KC;
+          bulk_g2s(dst, w0 + cell0, bytes, &full[st]);
+#pragma unroll 1
+          for (int a = 1; a < NARR; ++a) bulk_g2s(dst + a * RK_KC, bank + (a - 1) * bstride + cell0, bytes, &full[st]);
+        }
+        issued = it + 1;
+      }
+    }
+  } else {
+    const int ct = threadIdx.x - 32;
+    float acc[NOUT];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) acc[o] = 0.0f;
+    int since = 0, done = 0;
+    for (int it = 0; it < nit; ++it) {
+      const int st = it % RK_STAGES;
+      const uint32_t ph = (uint32_t)(it / RK_STAGES) & 1u;
+      if (!mbar_wait(&full[st], ph, status)) break;
+      const int64_t cell0 = (c0 + it) * RK_KC;
+      const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
+      const int64_t whole = rem / 4 * 4;
+      if (ct < rem) {
+        float v[NARR];
+        if (ct < whole) {
+          const float* src = buf + (size_t)st * NARR * RK_KC + ct;
+#pragma unroll
+          for (int a = 0; a < NARR; ++a) v[a] = src[a * RK_KC];
+        } else {
+          v[0] = __ldg(w0 + cell0 + ct);
+#pragma unroll
+          for (int a = 1; a < NARR; ++a) v[a] = __ldg(bank + (a - 1) * bstride + cell0 + ct);
+        }
+        reg_accumulate<NS, MAXN>(acc, v);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+      done = it + 1;
+      if (++since == RK_FLUSH) {
+        reg_flush<NOUT>(acc, wacc + (warp - 1) * NOUT, lane);
+        since = 0;
+      }
+    }
+    reg_flush<NOUT>(acc, wacc + (warp - 1) * NOUT, lane);
+    if (lane == 0) atomicMin(consumed_min, done);
+  }
+  __syncthreads();
+  // After a timeout, wait (bounded) for copies that were issued but not consumed.
+  if (warp == 0 && lane == 0) {
+    for (int it = *consumed_min; it < issued; ++it)
+      if (!mbar_wait(&full[it % RK_STAGES], (uint32_t)(it / RK_STAGES) & 1u, status)) break;
+  }
+  for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < RK_CW; ++w) s += wacc[w * NOUT + o];
+    partials[(int64_t)blockIdx.x * NOUT + o] = s;
+  }
+}
+
+template <int NS, int MAXN>
+static size_t reg_smem() {
+  return (size_t)RK_STAGES * (NS + 1) * RK_KC * 4 + (2 * RK_STAGES + 1) * 8 +
+         (size_t)RK_CW * RegOut<NS, MAXN>::total * 8;
+}
+
+template <int NS, int MAXN>
+static cudaError_t launch_reg_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ctas,
+                                int64_t cpc, double* partials, int* status, cudaStream_t st) {
+  const size_t sm = reg_smem<NS, MAXN>();
+  cudaError_t e = cudaFuncSetAttribute(contract_reg_kernel<NS, MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm);
+  if (e != cudaSuccess) return e;
+  contract_reg_kernel<NS, MAXN><<<ctas, 32 * (RK_CW + 1), sm, st>>>(w0, bank, bstride, nc, cpc, partials, status);
+  return cudaGetLastError();
+}
+
+static int reg_nout(int ns, int maxn) {
+  int t = ns;
+  if (maxn >= 3) t += cmb(ns + 1, 2);
+  if (maxn >= 4) t += cmb(ns + 2, 3);
+  if (maxn >= 5) t += cmb(ns + 3, 4);
+  return t;
+}
+
+#define CK_REG_CASE3(N) \
+  case N: return launch_reg_t<N, 3>(w0, bank, bstride, nc, ctas, cpc, partials, status, st);
+#define CK_REG_CASE5(N) \
+  case N: return launch_reg_t<N, 5>(w0, bank, bstride, nc, ctas, cpc, partials, status, st);
+
+static cudaError_t launch_reg(int ns, int maxn, const float* w0, const float* bank, int64_t bstride, int64_t nc,
+                              int ctas, int64_t cpc, double* partials, int* status, cudaStream_t st) {
+  if (maxn <= 3) {
+    switch (ns) {
+      CK_REG_CASE3(1) CK_REG_CASE3(2) CK_REG_CASE3(3) CK_REG_CASE3(4) CK_REG_CASE3(5) CK_REG_CASE3(6)
+      CK_REG_CASE3(7) CK_REG_CASE3(8) CK_REG_CASE3(9) CK_REG_CASE3(10) CK_REG_CASE3(11) CK_REG_CASE3(12)
+      CK_REG_CASE3(13) CK_REG_CASE3(14) CK_REG_CASE3(15) CK_REG_CASE3(16)
+      default: break;
+    }
+  } else {
+    switch (ns) {
+      CK_REG_CASE5(1) CK_REG_CASE5(2) CK_REG_CASE5(3) CK_REG_CASE5(4) CK_REG_CASE5(5)
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Sum the register kernel's per-CTA partials in CTA order into the packed
+// per-order layout (orders beyond the plan's max_order are dropped).
+__global__ void reduce_reg_kernel(const double* __restrict__ partials, int ctas, int nout, int nkeep,
+                                  double* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nkeep) return;
+  double s = 0.0;
+  for (int c = 0; c < ctas; ++c) s += partials[(int64_t)c * nout + o];
+  out[o] = s;
+}
+
+// ---------------------------------------------------------------------------
+// blocked kernel
+
+constexpr int BK_T = 64;   // output tile side
+constexpr int BK_FLUSH = 32;
+// cells per chunk: 32 for FP32 operands, 16 for FP64 (static shared memory < 48 KB)
+template <typename T>
+constexpr int bk_kc() { return sizeof(T) == 4 ? 32 : 16; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) contract_blocked_kernel(const float* __restrict__ w0, const float* __restrict__ bank,
+                                                               int64_t bstride, int64_t nc, int ns,
+                                                               const int2* __restrict__ rowdesc, int rows,
+                                                               const int2* __restrict__ coldesc, int cols,
+                                                               const int2* __restrict__ tiles, int ntiles,
+                                                               int64_t cells_per_split, double* __restrict__ partials) {
+  constexpr int BK_KC = bk_kc<T>();
+  __shared__ T ws[CK_MAX_SHELLS + 1][BK_KC];
+  __shared__ __align__(16) T As[BK_KC][BK_T];
+  __shared__ __align__(16) T Bs[BK_KC][BK_T];
+  __shared__ int2 rd[BK_T], cd[BK_T];
+  const int tid = threadIdx.x;
+  const int2 tile = tiles[blockIdx.x];
+  if (tid < BK_T) {
+    const int p = tile.x + tid;
+    rd[tid] = p < rows ? rowdesc[p] : make_int2(-2, -2);
+  } else if (tid < 2 * BK_T) {
+    const int q = tile.y + tid - BK_T;
+    cd[tid - BK_T] = q < cols ? coldesc[q] : make_int2(-2, -2);
+  }
+  const int ty = tid / 16, tx = tid % 16;
+  T acc[4][4];
+  double dacc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); dacc[i][j] = 0.0; }
+  const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
+  const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
+  int since = 0;
+  __syncthreads();
+  for (int64_t c0 = beg; c0 < end; c0 += BK_KC) {
+    for (int idx = tid; idx < (ns + 1) * BK_KC; idx += 256) {
+      const int a = idx / BK_KC, k = idx - a * BK_KC;
+      const int64_t cell = c0 + k;
+      float v = 0.0f;
+      if (cell < end) v = a == 0 ? __ldg(w0 + cell) : __ldg(bank + (int64_t)(a - 1) * bstride + cell);
+      ws[a][k] = (T)v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < BK_KC * BK_T; idx += 256) {
+      const int k = idx / BK_T, p = idx - k * BK_T;
+      const int2 d = rd[p];
+      T va = T(0);
+      if (d.x != -2) {
+        va = ws[0][k];
+        if (d.x >= 0) va *= ws[1 + d.x][k];
+        if (d.y >= 0) va *= ws[1 + d.y][k];
+      }
+      As[k][p] = va;
+      const int2 e = cd[p];
+      T vb = T(0);
+      if (e.x != -2) {
+        vb = T(1);
+        if (e.x >= 0) vb *= ws[1 + e.x][k];
+        if (e.y >= 0) vb *= ws[1 + e.y][k];
+      }
+      Bs[k][p] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < BK_KC; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[k][ty * 4 + i]; b[i] = Bs[k][tx * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+    if (++since == BK_FLUSH) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { dacc[i][j] += (double)acc[i][j]; acc[i][j] = T(0); }
+      since = 0;
+    }
+  }
+  double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (BK_T * BK_T);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * BK_T + tx * 4 + j] = dacc[i][j] + (double)acc[i][j];
+}
+
+// Rank of a sorted multiset s[0..k) over ns symbols in lexicographic order.
+__host__ __device__ inline int64_t multiset_rank(const int* s, int k, int ns) {
+  int64_t r = 0;
+  int prev = 0;
+  for (int t = 0; t < k; ++t) {
+    for (int v = prev; v < s[t]; ++v) {
+      // multisets of size k-t-1 over symbols [v, ns)
+      const int n = ns - v + (k - t - 1) - 1, kk = k - t - 1;
+      int64_t c = 1;
+      for (int i = 1; i <= kk; ++i) c = c * (n - kk + i) / i;
+      r += c;
+    }
+    prev = s[t];
+  }
+  return r;
+}
+
+// Which order (and multiset) a (row, column) pair of the blocked product
+// computes, or 0 if it is not the canonical pair of a requested order.
+__host__ __device__ inline int canonical(int2 rd, int2 cd, int mask, int* ms) {
+  if (rd.x == -2 || cd.x == -2) return 0;
+  const int dA = (rd.x >= 0) + (rd.y >= 0);
+  const int dB = (cd.x >= 0) + (cd.y >= 0);
+  int n = 0;
+  if (dA == 0 && dB == 1) n = 2;
+  else if (dA == 1 && dB == 1 && rd.x <= cd.x) n = 3;
+  else if (dA == 2 && dB == 1 && rd.y <= cd.x) n = 4;
+  else if (dA == 2 && dB == 2 && rd.y <= cd.x) n = 5;
+  if (n == 0 || !((mask >> n) & 1)) return 0;
+  int k = 0;
+  if (rd.x >= 0) ms[k++] = rd.x;
+  if (rd.y >= 0) ms[k++] = rd.y;
+  if (cd.x >= 0) ms[k++] = cd.x;
+  if (cd.y >= 0) ms[k++] = cd.y;
+  return n;
+}
+
+struct OrderBases {
+  int64_t base[CK_MAX_ORDER + 1];
+};
+
+__global__ void reduce_blocked_kernel(const double* __restrict__ partials, int splits, int ntiles,
+                                      const int2* __restrict__ tiles, const int2* __restrict__ rowdesc, int rows,
+                                      const int2* __restrict__ coldesc, int cols, int mask, int ns, OrderBases B,
+                                      double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ntiles * BK_T * BK_T) return;
+  const int tile = (int)(t / (BK_T * BK_T));
+  const int pq = (int)(t - (int64_t)tile * BK_T * BK_T);
+  const int p = tiles[tile].x + pq / BK_T, q = tiles[tile].y + pq % BK_T;
+  if (p >= rows || q >= cols) return;
+  int ms[4];
+  const int n = canonical(rowdesc[p], coldesc[q], mask, ms);
+  if (!n) return;
+  double s = 0.0;
+  for (int sp = 0; sp < splits; ++sp) s += partials[((int64_t)sp * ntiles + tile) * (BK_T * BK_T) + pq];
+  out[B.base[n] + multiset_rank(ms, n - 1, ns)] = s;
+}
+
+// ---------------------------------------------------------------------------
+// host: per-mask contraction plans
+
+static int max_order_in(int mask) {
+  int m = 0;
+  for (int n = 2; n <= CK_MAX_ORDER; ++n)
+    if ((mask >> n) & 1) m = n;
+  return m;
+}
+
+ck_status contract_prepare(Plan& p, int mask) {
+  if (p.cplan_ready[mask]) return CK_OK;
+  ContractPlan& c = p.cplan[mask];
+  c = ContractPlan();
+  c.order_mask = mask;
+  const int maxn = max_order_in(mask);
+  const int ns = p.ns;
+  if (p.precision == CK_PREC_FP32 && ((ns <= 16 && maxn <= 3) || (ns <= 5 && maxn <= 5))) {
+    c.use_reg = true;
+    c.reg_maxn = maxn <= 3 ? 3 : 5;
+    c.n_out_reg = reg_nout(ns, c.reg_maxn);
+    c.ctas = p.sm_count;
+    const int64_t nchunks = (p.nc + RK_KC - 1) / RK_KC;
+    c.chunks_per_cta = (nchunks + c.ctas - 1) / c.ctas;
+    c.partial_doubles = (size_t)c.ctas * c.n_out_reg;
+    if (c.partial_doubles > p.partials_cap) return CK_ERR_OOM;
+    p.cplan_ready[mask] = true;
+    return CK_OK;
+  }
+  // blocked kernel operand descriptors
+  std::vector<int2> rows, cols;
+  if ((mask >> 2) & 1) rows.push_back(make_int2(-1, -1));
+  if ((mask >> 3) & 1)
+    for (int a = 0; a < ns; ++a) rows.push_back(make_int2(a, -1));
+  if (((mask >> 4) & 1) || ((mask >> 5) & 1))
+    for (int b = 0; b < ns; ++b)
+      for (int a = 0; a <= b; ++a) rows.push_back(make_int2(a, b));  // sorted by (b, a)
+  if (((mask >> 2) & 1) || ((mask >> 3) & 1) || ((mask >> 4) & 1))
+    for (int k = 0; k < ns; ++k) cols.push_back(make_int2(k, -1));
+  if ((mask >> 5) & 1)
+    for (int k = 0; k < ns; ++k)
+      for (int l = k; l < ns; ++l) cols.push_back(make_int2(k, l));  // sorted by (k, l)
+  std::vector<int2> tiles;
+  int ms[4];
+  for (int m0 = 0; m0 < (int)rows.size(); m0 += BK_T)
+    for (int n0 = 0; n0 < (int)cols.size(); n0 += BK_T) {
+      bool any = false;
+      for (int pp = m0; pp < std::min<int>(m0 + BK_T, (int)rows.size()) && !any; ++pp)
+        for (int qq = n0; qq < std::min<int>(n0 + BK_T, (int)cols.size()) && !any; ++qq)
+          any = canonical(rows[pp], cols[qq], mask, ms) != 0;
+      if (any) tiles.push_back(make_int2(m0, n0));
+    }
+  c.rows = (int)rows.size();
+  c.cols = (int)cols.size();
+  c.n_tiles = (int)tiles.size();
+  const size_t slot = p.table_arena_cap / (1 << (CK_MAX_ORDER + 1));
+  int2* base = reinterpret_cast<int2*>(p.table_arena + slot * mask);
+  if ((rows.size() + cols.size() + tiles.size()) * sizeof(int2) > slot) return CK_ERR_OOM;
+  c.d_rowdesc = base;
+  c.d_coldesc = base + rows.size();
+  c.d_tiles = base + rows.size() + cols.size();
+  cudaError_t e = cudaMemcpy(c.d_rowdesc, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c.d_coldesc, cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpy(c.d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int64_t per_split = (int64_t)std::max(c.n_tiles, 1) * BK_T * BK_T;
+  int64_t splits = std::max<int64_t>(1, (int64_t)(4 * p.sm_count + c.n_tiles - 1) / std::max(c.n_tiles, 1));
+  splits = std::min<int64_t>(splits, (int64_t)(p.partials_cap / per_split));
+  splits = std::min<int64_t>(splits, std::max<int64_t>(1, p.nc / 128));
+  if (splits < 1) return CK_ERR_OOM;
+  c.splits = (int)splits;
+  c.partial_doubles = (size_t)splits * per_split;
+  p.cplan_ready[mask] = true;
+  return CK_OK;
+}
+
+ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank, int64_t bstride,
+                          double* sums, cudaStream_t st) {
+  ck_status s = contract_prepare(p, mask);
+  if (s != CK_OK) return s;
+  const ContractPlan& c = p.cplan[mask];
+  int* status = &p.dstate->status;
+  if (c.use_reg) {
+    cudaError_t e;
+    {
+    ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc, st);
+    e = launch_reg(p.ns, c.reg_maxn, w0, bank, bstride, p.nc, c.ctas, c.chunks_per_cta, p.partials,
+                               status, st);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);
+    const int nkeep = (int)std::min<int64_t>(c.n_out_reg, p.n_multiset_total);
+    reduce_reg_kernel<<<(nkeep + 127) / 128, 128, 0, st>>>(p.partials, c.ctas, c.n_out_reg, nkeep, sums);
+    return cuda_status(cudaGetLastError());
+  }
+  if (c.n_tiles == 0) return CK_OK;
+  const int64_t cps = (p.nc + c.splits - 1) / c.splits;
+  const int64_t cps_al = (cps + 31) / 32 * 32;
+  dim3 grid((unsigned)c.n_tiles, (unsigned)c.splits);
+  {
+  ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc, st);
+  if (p.precision == CK_PREC_FP64_SUM)
+    contract_blocked_kernel<double><<<grid, 256, 0, st>>>(w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows,
+                                                          c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, cps_al,
+                                                          p.partials);
+  else
+    contract_blocked_kernel<float><<<grid, 256, 0, st>>>(w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows,
+                                                         c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, cps_al,
+                                                         p.partials);
+  }
+  ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);
+  OrderBases B;
+  for (int n = 0; n <= CK_MAX_ORDER; ++n) B.base[n] = p.multiset_base[n];
+  const int64_t total = (int64_t)c.n_tiles * BK_T * BK_T;
+  reduce_blocked_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      p.partials, c.splits, c.n_tiles, c.d_tiles, c.d_rowdesc, c.rows, c.d_coldesc, c.cols, mask, p.ns, B, sums);
+  return cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// xi_n = num / (alpha^n den_raw) into dense symmetric tensors
+
+__global__ void finalize_kernel(const double* __restrict__ sums, const double* __restrict__ den_raw,
+                                const int* __restrict__ dmap, int64_t dense, int64_t mbase, int n, DevState* st,
+                                double* __restrict__ xi, double* __restrict__ num, double* __restrict__ den) {
+  const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= dense) return;
+  const int64_t r = mbase + dmap[d];
+  const double alpha = st->alpha;
+  double an = 1.0;
+  for (int i = 0; i < n; ++i) an *= alpha;
+  const double nu = sums[r];
+  const double de = den_raw[r] * an;
+  num[d] = nu;
+  den[d] = de;
+  if (de > 0.0) {
+    xi[d] = nu / de;
+  } else {
+    xi[d] = __longlong_as_double(0x7ff8000000000000ll);
+    set_status(&st->status, CK_ERR_ZERO_DENOM);
+  }
+}
+
+void launch_finalize(const Plan& p, int mask, cudaStream_t st) {
+  ProfScope ps(p, ST_FINALIZE, 0.0, st);
+  for (int n = 2; n <= p.max_order; ++n) {
+    if (!((mask >> n) & 1)) continue;
+    const int64_t dense = p.dense_elems[n];
+    double* xi = p.dense + p.dense_base[n];
+    double* num = p.dense + p.dense_total + p.dense_base[n];
+    double* den = p.dense + 2 * p.dense_total + p.dense_base[n];
+    finalize_kernel<<<(unsigned)((dense + 255) / 256), 256, 0, st>>>(
+        p.sums, p.den_raw, p.dense_map + p.dense_base[n], dense, p.multiset_base[n], n, p.dstate, xi, num, den);
+  }
+}
+
+// host-side rank, used to build the dense -> multiset map
+int64_t host_multiset_rank(const int* s, int k, int ns) { return multiset_rank(s, k, ns); }
+
+}  // namespace ck

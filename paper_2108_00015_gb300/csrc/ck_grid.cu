@@ -1,0 +1,230 @@
+// ck_grid.cu -- mapping (Sec. 2.2): nearest-grid-point histograms of the
+// data and random catalogs with warp-aggregated atomics, and the field
+// preparation N = D - alpha R (Eq. 8), Rt = alpha R.
+//
+// Cell rule: on each axis a point x (float32) is in cell k iff
+// e_k <= x < e_{k+1}, e_k = fl64(origin + fl64(k * cell)).  The kernel takes
+// an FP32 estimate of k and settles it against per-axis FP32 thresholds
+// t_k = the smallest float32 >= e_k (built on the host in FP64), so that
+// x >= e_k  <=>  x >= t_k exactly and the counts are bit-identical to an
+// exact evaluation.  Points outside [t_0, t_n) on a periodic axis take an
+// FP64 path and wrap k mod n; on a non-periodic grid they are dropped and
+// counted.  Non-finite coordinates are dropped on both kinds of grid.
+#include <float.h>
+#include <math.h>
+
+#include "ck_device.cuh"
+#include "ck_internal.h"
+
+namespace ck {
+
+struct GridArgs {
+  int n[3];
+  float of[3];
+  float inv_g;
+  double o[3];
+  double g;
+  int periodic;
+  const float* thr[3];
+};
+
+__device__ __forceinline__ int exact_cell_fp64(float x, double o, double g) {
+  const double xd = (double)x;
+  long long k = (long long)floor((xd - o) / g);
+  for (int it = 0; it < 8; ++it) {
+    const double lo = __dadd_rn(o, __dmul_rn((double)k, g));
+    const double hi = __dadd_rn(o, __dmul_rn((double)(k + 1), g));
+    if (xd < lo) { --k; continue; }
+    if (xd >= hi) { ++k; continue; }
+    break;
+  }
+  return (int)k;  // callers only use it modulo n on a periodic axis
+}
+
+// Returns false if the point falls outside a non-periodic grid (or is not
+// finite).
+__device__ __forceinline__ bool axis_cell(float x, int a, const GridArgs& A, int* kout) {
+  if (!isfinite(x)) return false;
+  const int n = A.n[a];
+  const float* t = A.thr[a];
+  const float e = (x - A.of[a]) * A.inv_g;
+  int k;
+  if (e < -1.0f) k = -2;
+  else if (e > (float)n + 1.0f) k = n + 1;
+  else k = (int)floorf(e);
+  if (k == -1 && x >= __ldg(t)) k = 0;
+  if (k == n && x < __ldg(t + n)) k = n - 1;
+  bool settled = false;
+#pragma unroll 1
+  for (int it = 0; it < 4 && k >= 0 && k < n; ++it) {
+    if (x < __ldg(t + k)) { --k; continue; }
+    if (x >= __ldg(t + k + 1)) { ++k; continue; }
+    settled = true;
+    break;
+  }
+  if (settled) { *kout = k; return true; }
+  if (!A.periodic) return false;
+  int kk = exact_cell_fp64(x, A.o[a], A.g) % n;
+  if (kk < 0) kk += n;
+  *kout = kk;
+  return true;
+}
+
+__global__ void __launch_bounds__(256) grid_points_kernel(const float* __restrict__ xs,
+                                                          const float* __restrict__ ys,
+                                                          const float* __restrict__ zs, int64_t npts,
+                                                          GridArgs A, uint32_t* __restrict__ counts,
+                                                          DevState* st, int which) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nround = (npts + 31) / 32 * 32;  // warp-uniform trip count
+  unsigned long long kept = 0, dropped = 0;
+  int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (int64_t i = first; i < nround; i += stride) {
+    bool in = i < npts;
+    int kx = 0, ky = 0, kz = 0;
+    if (in) {
+      const bool ok = axis_cell(__ldg(xs + i), 0, A, &kx) && axis_cell(__ldg(ys + i), 1, A, &ky) &&
+                      axis_cell(__ldg(zs + i), 2, A, &kz);
+      if (ok) {
+        ++kept;
+        bmin[0] = min(bmin[0], kx); bmax[0] = max(bmax[0], kx);
+        bmin[1] = min(bmin[1], ky); bmax[1] = max(bmax[1], ky);
+        bmin[2] = min(bmin[2], kz); bmax[2] = max(bmax[2], kz);
+      } else {
+        ++dropped;
+      }
+      in = ok;
+    }
+    const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.n[1] + ky) * A.n[0] + kx) : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
+    if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
+  }
+  // block reduction of the counters and bounding boxes
+  for (int off = 16; off > 0; off >>= 1) {
+    kept += __shfl_down_sync(0xFFFFFFFFu, kept, off);
+    dropped += __shfl_down_sync(0xFFFFFFFFu, dropped, off);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    bmin[a] = __reduce_min_sync(0xFFFFFFFFu, bmin[a]);
+    bmax[a] = __reduce_max_sync(0xFFFFFFFFu, bmax[a]);
+  }
+  __shared__ unsigned long long sk[8], sd[8];
+  __shared__ int smin[8][3], smax[8][3];
+  const int w = threadIdx.x >> 5;
+  if (lane == 0) {
+    sk[w] = kept; sd[w] = dropped;
+    for (int a = 0; a < 3; ++a) { smin[w][a] = bmin[a]; smax[w][a] = bmax[a]; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long K = 0, Dr = 0;
+    int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) {
+      K += sk[j]; Dr += sd[j];
+      for (int a = 0; a < 3; ++a) { mn[a] = min(mn[a], smin[j][a]); mx[a] = max(mx[a], smax[j][a]); }
+    }
+    if (K) atomicAdd(&st->kept[which], K);
+    if (Dr) atomicAdd(&st->dropped[which], Dr);
+    if (K) {
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&st->bbox_min[which][a], mn[a]);
+        atomicMax(&st->bbox_max[which][a], mx[a]);
+      }
+    }
+  }
+}
+
+void launch_grid_points(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
+                        int which, cudaStream_t st) {
+  if (n <= 0) return;
+  GridArgs A;
+  for (int a = 0; a < 3; ++a) {
+    A.n[a] = p.grid.n[a];
+    A.o[a] = p.grid.origin[a];
+    A.of[a] = (float)p.grid.origin[a];
+    A.thr[a] = p.thr[a];
+  }
+  A.g = p.grid.cell;
+  A.inv_g = (float)(1.0 / p.grid.cell);
+  A.periodic = p.grid.periodic ? 1 : 0;
+  const int64_t warps = (n + 31) / 32;
+  int64_t blocks = std::min<int64_t>((warps + 7) / 8, (int64_t)p.sm_count * 8);
+  if (blocks < 1) blocks = 1;
+  ProfScope ps(p, ST_GRID, 12.0 * (double)n, st);
+  grid_points_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, z, n, A, p.counts[which], p.dstate, which);
+}
+
+// alpha = kept_D / kept_R (FP64), N = D - alpha R in FP32 (one FMA), plus the
+// plan-level checks (empty catalogs, guard band on a non-periodic grid).
+__global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __restrict__ D,
+                                                           const uint32_t* __restrict__ R,
+                                                           float* __restrict__ field, int64_t nc,
+                                                           DevState* st, int periodic, int nx, int ny,
+                                                           int nz, int mx, int my, int mz) {
+  const unsigned long long kd = st->kept[0], kr = st->kept[1];
+  const double alpha = kr ? (double)kd / (double)kr : 0.0;
+  const float af = (float)alpha;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->alpha = alpha;
+    if (kd == 0 || kr == 0) set_status(&st->status, CK_ERR_EMPTY_CATALOG);
+    if (!periodic && kd && kr) {
+      const int n[3] = {nx, ny, nz}, m[3] = {mx, my, mz};
+      for (int a = 0; a < 3; ++a) {
+        const int lo = min(st->bbox_min[0][a], st->bbox_min[1][a]);
+        const int hi = max(st->bbox_max[0][a], st->bbox_max[1][a]);
+        if (hi - lo + m[a] >= n[a]) set_status(&st->status, CK_ERR_GUARD_BAND);
+      }
+    }
+  }
+  const int64_t n4 = nc / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint4* D4 = reinterpret_cast<const uint4*>(D);
+  const uint4* R4 = reinterpret_cast<const uint4*>(R);
+  float4* F4 = reinterpret_cast<float4*>(field);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const uint4 d = __ldg(D4 + i), r = __ldg(R4 + i);
+    F4[i] = make_float4(fmaf(-af, (float)r.x, (float)d.x), fmaf(-af, (float)r.y, (float)d.y),
+                        fmaf(-af, (float)r.z, (float)d.z), fmaf(-af, (float)r.w, (float)d.w));
+  }
+  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
+    field[i] = fmaf(-af, (float)R[i], (float)D[i]);
+}
+
+__global__ void __launch_bounds__(256) prepare_randoms_kernel(const uint32_t* __restrict__ R,
+                                                              float* __restrict__ field, int64_t nc,
+                                                              DevState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->kept[1] == 0) set_status(&st->status, CK_ERR_EMPTY_CATALOG);
+  const int64_t n4 = nc / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint4* R4 = reinterpret_cast<const uint4*>(R);
+  float4* F4 = reinterpret_cast<float4*>(field);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const uint4 r = __ldg(R4 + i);
+    F4[i] = make_float4((float)r.x, (float)r.y, (float)r.z, (float)r.w);
+  }
+  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
+    field[i] = (float)R[i];
+}
+
+static unsigned elementwise_blocks(const Plan& p, int64_t n) {
+  int64_t b = (n / 4 + 255) / 256;
+  b = std::min<int64_t>(b, (int64_t)p.sm_count * 8);
+  return (unsigned)std::max<int64_t>(b, 1);
+}
+
+void launch_prepare_data(const Plan& p, cudaStream_t st) {
+  ProfScope ps(p, ST_PREP, 12.0 * (double)p.nc, st);
+  prepare_data_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(
+      p.counts[0], p.counts[1], p.field, p.nc, p.dstate, p.grid.periodic ? 1 : 0, p.grid.n[0],
+      p.grid.n[1], p.grid.n[2], p.maxoff[0], p.maxoff[1], p.maxoff[2]);
+}
+
+void launch_prepare_randoms(const Plan& p, cudaStream_t st) {
+  ProfScope ps(p, ST_PREP, 8.0 * (double)p.nc, st);
+  prepare_randoms_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.counts[1], p.field, p.nc, p.dstate);
+}
+
+}  // namespace ck

@@ -1,0 +1,175 @@
+// ck_internal.h -- private declarations shared by the library's translation
+// units (plan layout, launch helpers).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "conker.h"
+
+namespace ck {
+
+// Device-side state of a plan: point counters, occupied-cell bounding boxes,
+// alpha and the status word.  Index 0 = data catalog, 1 = randoms.
+struct DevState {
+  unsigned long long kept[2];
+  unsigned long long dropped[2];
+  int bbox_min[2][3];
+  int bbox_max[2][3];
+  int status;
+  int pad;
+  double alpha;
+};
+
+constexpr int kMaxStages = 8;
+
+// Radix decomposition of one transform length.
+struct FftLen {
+  int n = 0;
+  int nst = 0;
+  int radix[kMaxStages] = {0};
+};
+
+// Operand descriptors of the blocked contraction: row p of A is
+// w0 * W[i] * W[j], column q of B is W[k] * W[l] (an index of -1 = factor 1).
+struct ContractPlan {
+  int order_mask = 0;
+  bool use_reg = false;     // register-accumulator kernel (few outputs)
+  int reg_maxn = 0;         // orders 2..reg_maxn computed by that kernel
+  int n_out_reg = 0;        // outputs of the register kernel
+  int rows = 0, cols = 0;   // blocked kernel: operand rows / columns
+  int n_tiles = 0;          // blocked kernel: active 64 x 64 output tiles
+  int splits = 0;           // CTAs along the cell dimension
+  int ctas = 0;             // register kernel: CTAs
+  int64_t chunks_per_cta = 0;
+  // device tables (inside the workspace)
+  int2* d_rowdesc = nullptr;
+  int2* d_coldesc = nullptr;
+  int2* d_tiles = nullptr;   // (m0, n0) per active tile
+  int* d_slot = nullptr;     // [n_tiles][64][64] -> output slot or -1
+  size_t partial_doubles = 0;
+};
+
+// Per-stage event timing (ck_profile_enable / ck_profile_read).
+enum Stage {
+  ST_GRID = 0, ST_PREP, ST_FFT_X_R2C, ST_FFT_Y_FWD, ST_FFT_Z_FWD, ST_FFT_Z_INV_MUL, ST_FFT_Y_INV,
+  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_OTHER
+};
+
+struct Profiler {
+  bool on = false;
+  struct Rec { int stage; double bytes; cudaEvent_t a, b; };
+  std::vector<Rec> recs;      // event pool; recs[0..used) are pending
+  size_t used = 0;
+  double ms[CK_STAGES] = {0};
+  int64_t launches[CK_STAGES] = {0};
+  double bytes[CK_STAGES] = {0};
+  int64_t dropped = 0;        // launches not recorded (pool exhausted)
+};
+
+struct Plan {
+  ck_grid grid{};
+  int ns = 0;
+  double width = 0;
+  int rule = 0;
+  int max_order = 0;
+  int precision = 0;
+  std::vector<double> radius;
+  std::vector<std::vector<int>> offsets;  // per shell: flattened (mx, my, mz)
+  int maxoff[3] = {0, 0, 0};
+  int64_t nc = 0;
+  int px = 0;               // half-spectrum row pitch (complex elements)
+  int64_t spec_elems = 0;   // n[2] * n[1] * px
+  int64_t field_stride = 0; // floats reserved per real field (>= nc, multiple of 64)
+  int oct[3] = {0, 0, 0};   // octant extents n/2 + 1
+  int64_t oct_elems = 0;
+  int H = 0;                // max offset over all shells and axes
+  int64_t n_multisets[CK_MAX_ORDER + 1] = {0};
+  int64_t multiset_base[CK_MAX_ORDER + 1] = {0};  // offset of order n in a packed array
+  int64_t n_multiset_total = 0;
+  int64_t dense_elems[CK_MAX_ORDER + 1] = {0};
+  int64_t dense_base[CK_MAX_ORDER + 1] = {0};
+  int64_t dense_total = 0;
+  FftLen fx_half, fy, fz;   // x uses a half-length complex transform
+
+  // workspace
+  void* ws = nullptr;
+  bool owns_ws = false;
+  size_t ws_bytes = 0;
+  uint32_t* counts[2] = {nullptr, nullptr};
+  float* field = nullptr;
+  float2* spec = nullptr;
+  float2* tmp = nullptr;
+  float* khat = nullptr;
+  float* bank = nullptr;
+  double* partials = nullptr;
+  size_t partials_cap = 0;  // doubles
+  float* staging = nullptr;
+  int64_t staging_pts = 0;  // points per staging slot
+  float* thr[3] = {nullptr, nullptr, nullptr};   // cell-edge thresholds, n+1 each
+  float2* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i t / n_a}, n_a each
+  DevState* dstate = nullptr;
+  double* den_raw = nullptr;   // packed per order (multiset order)
+  double* sums = nullptr;      // packed per order: num of the last compute
+  double* dense = nullptr;     // 3 x dense_total: xi, num, den staging
+  int* dense_map = nullptr;    // packed per order: dense index -> multiset rank
+  int* host_status_pinned = nullptr;
+
+  ContractPlan cplan[1 << (CK_MAX_ORDER + 1)];
+  bool cplan_ready[1 << (CK_MAX_ORDER + 1)] = {false};
+  unsigned char* table_arena = nullptr;  // contraction tables
+  size_t table_arena_cap = 0, table_arena_used = 0;
+
+  mutable Profiler prof;
+
+  bool have_randoms = false;
+  int bank_holds = -1;  // 0 = W of data, 1 = R***K of randoms
+  int device = 0;
+  int sm_count = 0;
+};
+
+// ---- host helpers (ck_plan.cu) ------------------------------------------------
+ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int max_order,
+                              int precision, Plan* p);
+size_t workspace_bytes(const Plan& p);
+size_t khat_scratch_doubles(const Plan& p);
+bool factor_len(int n, FftLen* out);
+ck_status cuda_status(cudaError_t e);
+int64_t binom(int64_t n, int64_t k);
+
+// Record the start / end of one launch of `stage` (no-ops unless enabled).
+int prof_begin(const Plan& p, int stage, double bytes, cudaStream_t st);
+void prof_end(const Plan& p, int idx, cudaStream_t st);
+
+struct ProfScope {
+  const Plan& p;
+  int idx;
+  cudaStream_t st;
+  ProfScope(const Plan& pl, int stage, double bytes, cudaStream_t s)
+      : p(pl), idx(prof_begin(pl, stage, bytes, s)), st(s) {}
+  ~ProfScope() { prof_end(p, idx, st); }
+};
+
+// ---- launches (ck_grid.cu) ---------------------------------------------------
+void launch_grid_points(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
+                        int which, cudaStream_t st);
+void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
+void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
+
+// ---- launches (ck_fft.cu) ----------------------------------------------------
+ck_status fft_init_attributes();
+void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st);
+void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat_shell, float2* tmp,
+                        float* out, cudaStream_t st);
+ck_status build_kernel_spectra(Plan& p, cudaStream_t st);
+
+// ---- launches (ck_contract.cu) -----------------------------------------------
+ck_status contract_prepare(Plan& p, int order_mask);
+ck_status launch_contract(Plan& p, int order_mask, const float* w0, const float* bank,
+                          int64_t bank_stride, double* sums_packed, cudaStream_t st);
+void launch_finalize(const Plan& p, int order_mask, cudaStream_t st);
+
+}  // namespace ck

@@ -1,0 +1,72 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every entry
+point declared in include/conker.h, and validates arguments on the host
+(before any CUDA call) with the documented status codes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "conker.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\**\s+\**(ck_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2108_00015_gb300 import conker
+    return conker.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2108_00015_gb300 import conker
+    assert sorted(conker.exported_symbols()) == names
+
+
+def test_abi_version(lib):
+    assert lib.ck_abi_version() == 1
+    assert lib.ck_status_string(0) == b"ok"
+
+
+def _ws(lib, n=(32, 32, 32), cell=10.0, periodic=1, radii=(20.0, 40.0), width=10.0, rule=0, max_order=3, prec=0):
+    from paper_2108_00015_gb300.conker import _Grid, _Shells
+    g = _Grid((ctypes.c_int32 * 3)(*n), (ctypes.c_double * 3)(0, 0, 0), cell, periodic)
+    r = (ctypes.c_double * len(radii))(*radii)
+    s = _Shells(len(radii), r, width, rule)
+    b = ctypes.c_size_t(0)
+    code = lib.ck_plan_workspace_size(ctypes.byref(g), ctypes.byref(s), max_order, prec, ctypes.byref(b))
+    return code, b.value
+
+
+def test_host_validation(lib):
+    code, nbytes = _ws(lib)
+    assert code == 0 and nbytes > 32 ** 3 * 4 * 8
+    assert _ws(lib, n=(33, 32, 32))[0] == 10          # odd axis
+    assert _ws(lib, n=(14, 32, 32))[0] == 10          # prime factor 7
+    assert _ws(lib, n=(1024, 32, 32))[0] == 10        # beyond 512
+    assert _ws(lib, cell=0.0)[0] == 1
+    assert _ws(lib, max_order=6)[0] == 1
+    assert _ws(lib, max_order=1)[0] == 1
+    assert _ws(lib, prec=1)[0] == 10                  # split-BF16 reserved
+    assert _ws(lib, radii=(0.2,), width=0.1)[0] == 4  # no lattice offset in the shell
+    assert _ws(lib, radii=(170.0,))[0] == 5           # reaches half of a 32-cell box
+    assert _ws(lib, rule=7)[0] == 1
+    assert _ws(lib, width=0.0)[0] == 1
+
+
+def test_survey_workspace_fits(lib):
+    # 512^3, 16 shells: counts + field + 2 spectra + kernel octants + W bank
+    code, nbytes = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0,
+                       radii=tuple(30.0 + 8 * i for i in range(16)), width=8.0)
+    assert code == 0
+    assert 10e9 < nbytes < 16e9
