@@ -113,6 +113,20 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _smi_index(torch, local):
+    """nvidia-smi's name for this rank's GPU (UUID when torch reports it)."""
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u and u != "None":
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[local]
+    return str(local)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -204,7 +218,7 @@ def run_gb300(args):
     if st not in (0,):
         raise RuntimeError(f"device status {st} after warm-up")
     plan.profile(True)
-    clocks = Clocks(torch.cuda.current_device())
+    clocks = Clocks(_smi_index(torch, local))
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()

@@ -231,6 +231,8 @@ class Plan:
         o = _Outputs()
         dev = "cuda" if out == "device" else "cpu"
         for n in orders:
+            if not 2 <= int(n) <= CK_MAX_ORDER:
+                continue  # the library rejects the order mask
             for key in want:
                 if outputs is not None:
                     t = outputs[key][n]

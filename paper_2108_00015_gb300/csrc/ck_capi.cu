@@ -109,7 +109,7 @@ ck_status carve(Plan& p) {
   p.counts[1] = reinterpret_cast<uint32_t*>(take((size_t)p.nc * 4));
   p.field = reinterpret_cast<float*>(take((size_t)p.field_stride * 4));
   p.spec = reinterpret_cast<float2*>(take((size_t)p.spec_elems * 8));
-  p.tmp = reinterpret_cast<float2*>(take((size_t)p.spec_elems * 8));
+  p.tmp = reinterpret_cast<float2*>(take((size_t)p.ns * p.spec_elems * 8));
   p.khat = reinterpret_cast<float*>(take((size_t)p.ns * p.oct_elems * 4));
   p.bank = reinterpret_cast<float*>(take(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8)));
   p.partials = reinterpret_cast<double*>(take(p.partials_cap * 8));
@@ -208,8 +208,7 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
 // Convolve the current field with every shell kernel into the bank.
 void convolve_bank(Plan& p, cudaStream_t st) {
   launch_fft_forward(p, p.field, p.spec, st);
-  for (int s = 0; s < p.ns; ++s)
-    launch_fft_inverse(p, p.spec, p.khat + (size_t)s * p.oct_elems, p.tmp, p.bank + (size_t)s * p.field_stride, st);
+  launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
 }
 
 int full_mask(const Plan& p) {
@@ -488,7 +487,7 @@ ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* strea
   if (!is_device_ptr(in_spec) || !is_device_ptr(out)) return CK_ERR_BAD_POINTER;
   if (((uintptr_t)in_spec & 15u) != 0 || ((uintptr_t)out & 7u) != 0) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
-  launch_fft_inverse(p, static_cast<const float2*>(in_spec), nullptr, p.tmp, out, S(stream));
+  launch_fft_inverse(p, static_cast<const float2*>(in_spec), nullptr, 1, p.tmp, out, 0, S(stream));
   return cuda_status(cudaGetLastError());
 }
 

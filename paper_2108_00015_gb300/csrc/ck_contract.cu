@@ -5,7 +5,7 @@
 // Two kernels:
 //  * contract_reg: few outputs (N_s <= 16 and n <= 3, or N_s <= 5 and
 //    n <= 5).  One warp streams cell chunks of W0 and every W_s into a
-//    four-stage shared-memory ring with bulk asynchronous copies (mbarrier
+//    eight-stage shared-memory ring with bulk asynchronous copies (mbarrier
 //    completion); seven consumer warps take one cell per thread and keep every
 //    product sum in registers (FP32 over 128 chunks, then warp-reduced into
 //    FP64 in shared memory).  HBM-bound: it reads each W_s once.
@@ -44,7 +44,7 @@ struct RegOut {
 
 constexpr int RK_CW = 7;            // consumer warps
 constexpr int RK_KC = 32 * RK_CW;   // cells per chunk (one per consumer thread)
-constexpr int RK_STAGES = 4;   // ring depth
+constexpr int RK_STAGES = 8;   // ring depth
 constexpr int RK_FLUSH = 128;  // chunks between FP32 -> FP64 flushes
 
 template <int NS, int MAXN>

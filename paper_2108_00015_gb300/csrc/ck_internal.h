@@ -26,7 +26,30 @@ struct DevState {
 
 constexpr int kMaxStages = 8;
 
-// Radix decomposition of one transform length.
+// Radix decomposition of one transform length: radices 5 and 3 first, then
+// the power of two as radix 8 and 4 (radix 2 only when 2 is the whole power
+// of two), or a single radix 1 for length 1.
+struct RPlan {
+  int nst;
+  int r[kMaxStages];
+};
+
+__host__ __device__ constexpr RPlan rplan(int n) {
+  RPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+  int m = n, p2 = 0;
+  while (m > 0 && m % 2 == 0) { m /= 2; ++p2; }
+  while (m > 1 && m % 5 == 0 && p.nst < kMaxStages) { p.r[p.nst++] = 5; m /= 5; }
+  while (m > 1 && m % 3 == 0 && p.nst < kMaxStages) { p.r[p.nst++] = 3; m /= 3; }
+  if (m != 1) return RPlan{-1, {0, 0, 0, 0, 0, 0, 0, 0}};
+  if (p2 >= 4 && p2 % 3 == 1) { p.r[p.nst++] = 4; p.r[p.nst++] = 4; p2 -= 4; }
+  while (p2 >= 3 && p.nst < kMaxStages) { p.r[p.nst++] = 8; p2 -= 3; }
+  if (p2 == 2) p.r[p.nst++] = 4;
+  if (p2 == 1) p.r[p.nst++] = 2;
+  if (p.nst == 0) p.r[p.nst++] = 1;
+  return p;
+}
+
+// Radix decomposition of one transform length (runtime copy of rplan).
 struct FftLen {
   int n = 0;
   int nst = 0;
@@ -162,8 +185,11 @@ void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> fi
 // ---- launches (ck_fft.cu) ----------------------------------------------------
 ck_status fft_init_attributes();
 void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st);
-void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat_shell, float2* tmp,
-                        float* out, cudaStream_t st);
+// Inverse transforms of nshells spectra (spec * K^_s for s < nshells, or spec
+// alone when khat is null) through scratch spectra tmp[s] into real fields
+// out + s * out_stride.
+void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
+                        float* out, int64_t out_stride, cudaStream_t st);
 ck_status build_kernel_spectra(Plan& p, cudaStream_t st);
 
 // ---- launches (ck_contract.cu) -----------------------------------------------

@@ -22,26 +22,13 @@ int64_t binom(int64_t n, int64_t k) {
   return r;
 }
 
-// Factor n into radices 5, 3, 8, 4 (and 2 only for n = 2 * odd).
 bool factor_len(int n, FftLen* out) {
+  const RPlan r = rplan(n);
+  if (r.nst <= 0) return false;
   FftLen f;
   f.n = n;
-  int m = n;
-  int p2 = 0;
-  while (m % 2 == 0) { m /= 2; ++p2; }
-  std::vector<int> r;
-  while (m % 5 == 0) { r.push_back(5); m /= 5; }
-  while (m % 3 == 0) { r.push_back(3); m /= 3; }
-  if (m != 1) return false;
-  // powers of two as radix 8 and 4 (radix 2 only when 2 is the whole power)
-  if (p2 >= 4 && p2 % 3 == 1) { r.push_back(4); r.push_back(4); p2 -= 4; }
-  while (p2 >= 3) { r.push_back(8); p2 -= 3; }
-  if (p2 == 2) r.push_back(4);
-  if (p2 == 1) r.push_back(2);
-  if (r.empty()) r.push_back(1);  // length 1: identity
-  if ((int)r.size() > kMaxStages) return false;
-  f.nst = (int)r.size();
-  for (int i = 0; i < f.nst; ++i) f.radix[i] = r[i];
+  f.nst = r.nst;
+  for (int i = 0; i < r.nst; ++i) f.radix[i] = r.r[i];
   *out = f;
   return true;
 }
@@ -181,7 +168,8 @@ size_t workspace_bytes(const Plan& p) {
   size_t b = 0;
   b += 2 * al((size_t)p.nc * 4);                              // counts D, R
   b += al((size_t)p.field_stride * 4);                         // field
-  b += 2 * al((size_t)p.spec_elems * 8);                       // spec, tmp
+  b += al((size_t)p.spec_elems * 8);                           // spec
+  b += al((size_t)p.ns * p.spec_elems * 8);                    // tmp: one scratch spectrum per shell
   b += al((size_t)p.ns * p.oct_elems * 4);                     // khat
   b += al(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8));  // bank
   b += al(p.partials_cap * 8);                                 // partials

@@ -264,6 +264,14 @@ WORKLOADS: Dict[str, dict] = {
         data=("ns_box", dict(seed=4, n_parents=1_000_000, n_children=20, sigma=8.0)),
         randoms=("uniform_box", dict(seed=5, n=40_000_000)),
     ),
+    # Small periodic case for profiler captures: 384^3 of 8 h^-1 Mpc (spectra
+    # 228 MB, larger than L2), 4 shells, 50k clustered points, 2M randoms.
+    "profile384": dict(
+        grid=GridSpec((384, 384, 384), (0.0, 0.0, 0.0), 8.0, True),
+        shells=(40.0, 60.0, 80.0, 100.0), width=8.0, orders=(2, 3),
+        data=("ns_box", dict(seed=6, n_parents=2_500, n_children=20, sigma=8.0)),
+        randoms=("uniform_box", dict(seed=7, n=2_000_000)),
+    ),
 }
 
 

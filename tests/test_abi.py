@@ -69,4 +69,4 @@ def test_survey_workspace_fits(lib):
     code, nbytes = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0,
                        radii=tuple(30.0 + 8 * i for i in range(16)), width=8.0)
     assert code == 0
-    assert 10e9 < nbytes < 16e9
+    assert 15e9 < nbytes < 25e9
