@@ -178,11 +178,12 @@ ck_status ck_get_kernel_spectrum(ck_plan* plan, int32_t shell, float* out, void*
 
 /* Forward real-to-complex 3D DFT of a real field (device float [N_c]) into a
  * half spectrum (device float2 [n[2]][n[1]][spec_pitch]); unnormalised,
- * exponent sign -1.  Uses the plan's scratch spectrum. */
+ * exponent sign -1.  Both pointers 16-byte aligned. */
 ck_status ck_fft_r2c(ck_plan* plan, const float* in, void* out_spec, void* stream);
 
 /* Inverse complex-to-real 3D DFT (exponent sign +1, unnormalised) of a half
- * spectrum (device, not modified) into a real field (device float [N_c]). */
+ * spectrum (device, not modified) into a real field (device float [N_c]).
+ * Both pointers 16-byte aligned; uses the plan's scratch spectra. */
 ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* stream);
 
 /* The summation stage alone (Sec. 2.5): for every order n in order_mask and

@@ -110,7 +110,7 @@ ck_status carve(Plan& p) {
   p.field = reinterpret_cast<float*>(take((size_t)p.field_stride * 4));
   p.spec = reinterpret_cast<float2*>(take((size_t)p.spec_elems * 8));
   p.tmp = reinterpret_cast<float2*>(take((size_t)p.ns * p.spec_elems * 8));
-  p.khat = reinterpret_cast<float*>(take((size_t)p.ns * p.oct_elems * 4));
+  p.khat = reinterpret_cast<float*>(take((size_t)p.ns * p.khat_stride * 4));
   p.bank = reinterpret_cast<float*>(take(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8)));
   p.partials = reinterpret_cast<double*>(take(p.partials_cap * 8));
   p.staging = reinterpret_cast<float*>(take((size_t)2 * 3 * p.staging_pts * 4));
@@ -467,16 +467,19 @@ ck_status ck_get_kernel_spectrum(ck_plan* plan, int32_t shell, float* out, void*
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (shell < 0 || shell >= p.ns) return CK_ERR_ARG;
   cudaStream_t st = S(stream);
-  bool host = false;
-  CK_TRY_S(copy_out(out, p.khat + (size_t)shell * p.oct_elems, (size_t)p.oct_elems * 4, st, &host));
-  if (host) CK_TRY(cudaStreamSynchronize(st));
+  const bool dev = is_device_ptr(out);
+  // strip the row padding: pitch px -> n[0]/2 + 1
+  CK_TRY(cudaMemcpy2DAsync(out, (size_t)p.oct[0] * 4, p.khat + (size_t)shell * p.khat_stride, (size_t)p.px * 4,
+                           (size_t)p.oct[0] * 4, (size_t)p.oct[1] * p.oct[2],
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (!dev) CK_TRY(cudaStreamSynchronize(st));
   return CK_OK;
 }
 
 ck_status ck_fft_r2c(ck_plan* plan, const float* in, void* out_spec, void* stream) {
   if (!plan || !in || !out_spec) return CK_ERR_BAD_POINTER;
   if (!is_device_ptr(in) || !is_device_ptr(out_spec)) return CK_ERR_BAD_POINTER;
-  if (((uintptr_t)out_spec & 15u) != 0 || ((uintptr_t)in & 7u) != 0) return CK_ERR_BAD_POINTER;
+  if (((uintptr_t)out_spec & 15u) != 0 || ((uintptr_t)in & 15u) != 0) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   launch_fft_forward(p, in, static_cast<float2*>(out_spec), S(stream));
   return cuda_status(cudaGetLastError());
@@ -485,7 +488,7 @@ ck_status ck_fft_r2c(ck_plan* plan, const float* in, void* out_spec, void* strea
 ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* stream) {
   if (!plan || !in_spec || !out) return CK_ERR_BAD_POINTER;
   if (!is_device_ptr(in_spec) || !is_device_ptr(out)) return CK_ERR_BAD_POINTER;
-  if (((uintptr_t)in_spec & 15u) != 0 || ((uintptr_t)out & 7u) != 0) return CK_ERR_BAD_POINTER;
+  if (((uintptr_t)in_spec & 15u) != 0 || ((uintptr_t)out & 15u) != 0) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   launch_fft_inverse(p, static_cast<const float2*>(in_spec), nullptr, 1, p.tmp, out, 0, S(stream));
   return cuda_status(cudaGetLastError());

@@ -5,10 +5,11 @@
 // Two kernels:
 //  * contract_reg: few outputs (N_s <= 16 and n <= 3, or N_s <= 5 and
 //    n <= 5).  One warp streams cell chunks of W0 and every W_s into a
-//    eight-stage shared-memory ring with bulk asynchronous copies (mbarrier
-//    completion); seven consumer warps take one cell per thread and keep every
-//    product sum in registers (FP32 over 128 chunks, then warp-reduced into
-//    FP64 in shared memory).  HBM-bound: it reads each W_s once.
+//    six-stage shared-memory ring with bulk asynchronous copies of 1792 bytes
+//    (mbarrier completion); seven consumer warps take two cells per thread
+//    and chunk and keep every product sum in registers (FP32 over 64 chunks,
+//    then warp-reduced into FP64 in shared memory).  HBM-bound: it reads each
+//    W_s once.
 //  * contract_blocked: the general case as a blocked product
 //    T[p][q] = sum_r A_p(r) B_q(r) with A_p = W0 W_i W_j and B_q = W_k W_l
 //    generated per cell chunk in shared memory (64 x 64 output tiles, 4 x 4
@@ -42,10 +43,11 @@ struct RegOut {
   static constexpr int total = n2 + n3 + n4 + n5;
 };
 
-constexpr int RK_CW = 7;            // consumer warps
-constexpr int RK_KC = 32 * RK_CW;   // cells per chunk (one per consumer thread)
-constexpr int RK_STAGES = 8;   // ring depth
-constexpr int RK_FLUSH = 128;  // chunks between FP32 -> FP64 flushes
+constexpr int RK_CW = 7;                 // consumer warps
+constexpr int RK_CPT = 2;                // cells per consumer thread and chunk
+constexpr int RK_KC = 32 * RK_CW * RK_CPT;  // cells per chunk (1792-byte copies)
+constexpr int RK_STAGES = 6;             // ring depth
+constexpr int RK_FLUSH = 64;             // chunks between FP32 -> FP64 flushes
 
 template <int NS, int MAXN>
 __device__ __forceinline__ void reg_accumulate(float* acc, const float* v) {
@@ -148,18 +150,22 @@ __global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
       const int64_t cell0 = (c0 + it) * RK_KC;
       const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
       const int64_t whole = rem / 4 * 4;
-      if (ct < rem) {
-        float v[NARR];
-        if (ct < whole) {
-          const float* src = buf + (size_t)st * NARR * RK_KC + ct;
 #pragma unroll
-          for (int a = 0; a < NARR; ++a) v[a] = src[a * RK_KC];
-        } else {
-          v[0] = __ldg(w0 + cell0 + ct);
+      for (int u = 0; u < RK_CPT; ++u) {
+        const int cc = u * 32 * RK_CW + ct;
+        if (cc < rem) {
+          float v[NARR];
+          if (cc < whole) {
+            const float* src = buf + (size_t)st * NARR * RK_KC + cc;
 #pragma unroll
-          for (int a = 1; a < NARR; ++a) v[a] = __ldg(bank + (a - 1) * bstride + cell0 + ct);
+            for (int a = 0; a < NARR; ++a) v[a] = src[a * RK_KC];
+          } else {
+            v[0] = __ldg(w0 + cell0 + cc);
+#pragma unroll
+            for (int a = 1; a < NARR; ++a) v[a] = __ldg(bank + (a - 1) * bstride + cell0 + cc);
+          }
+          reg_accumulate<NS, MAXN>(acc, v);
         }
-        reg_accumulate<NS, MAXN>(acc, v);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);

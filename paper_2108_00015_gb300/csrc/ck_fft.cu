@@ -52,7 +52,7 @@ void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, in
   {
     ProfScope ps(p, ST_FFT_Z_INV_MUL, 8.0 * H + nshells * (8.0 * H + (khat ? 4.0 * (double)p.oct_elems : 0.0)), st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
-    KhatArgs K{khat, p.oct_elems, p.px, ny, nz, p.oct[0], p.oct[1]};
+    KhatArgs K{khat, p.khat_stride, p.px, ny, nz, p.oct[1]};
     fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.tw[2], K, p.sm_count, st);
   }
   {
@@ -104,15 +104,22 @@ __global__ void khat_pass_y(const double* __restrict__ A1, const double* __restr
   }
 }
 
+// Writes the octant with rows padded to the pitch px (zeros for kx >= ox).
 __global__ void khat_pass_z(const double* __restrict__ A2, const double* __restrict__ Cz, float* __restrict__ khat,
-                            int ns, int H1, int oz, int oy, int ox, double inv_nc) {
+                            int ns, int H1, int oz, int oy, int ox, int px, double inv_nc) {
   const int64_t plane = (int64_t)oy * ox;
-  const int64_t total = (int64_t)ns * oz * plane;
+  const int64_t total = (int64_t)ns * oz * oy * px;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t yx = t % plane;
-    const int kz = (int)((t / plane) % oz);
-    const int s = (int)(t / (plane * oz));
-    const double* a = A2 + (int64_t)s * H1 * plane + yx;
+    const int kx = (int)(t % px);
+    const int64_t r = t / px;  // (s, kz, ky)
+    const int ky = (int)(r % oy);
+    const int kz = (int)((r / oy) % oz);
+    const int s = (int)(r / ((int64_t)oy * oz));
+    if (kx >= ox) {
+      khat[t] = 0.0f;
+      continue;
+    }
+    const double* a = A2 + (int64_t)s * H1 * plane + (int64_t)ky * ox + kx;
     const double* c = Cz + (int64_t)kz * H1;
     double acc = 0.0;
     for (int m = 0; m < H1; ++m) acc = fma(a[(int64_t)m * plane], c[m], acc);
@@ -162,7 +169,8 @@ ck_status build_kernel_spectra(Plan& p, cudaStream_t st) {
   const unsigned blocks = (unsigned)std::max(1, p.sm_count * 8);
   khat_pass_x<<<blocks, 256, 0, st>>>(dK, dCx, dA1, ns, H1, p.oct[0]);
   khat_pass_y<<<blocks, 256, 0, st>>>(dA1, dCy, dA2, ns, H1, p.oct[1], p.oct[0]);
-  khat_pass_z<<<blocks, 256, 0, st>>>(dA2, dCz, p.khat, ns, H1, p.oct[2], p.oct[1], p.oct[0], 1.0 / (double)p.nc);
+  khat_pass_z<<<blocks, 256, 0, st>>>(dA2, dCz, p.khat, ns, H1, p.oct[2], p.oct[1], p.oct[0], p.px,
+                                      1.0 / (double)p.nc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   // the host vectors must outlive the copies

@@ -3,7 +3,8 @@
 // instantiate the passes for each transform length.
 //
 // Every pass transforms one axis.  A tile is kT = 8 independent lines of
-// length L <= 512 held in shared memory as s[l * TP + c].  Persistent CTAs of
+// length L <= 512 held in shared memory (column layout s[l * kT + c] for the
+// strided axes, row layout s[c * LP + l] for the x axis).  Persistent CTAs of
 // 256 threads walk the tiles; the next tile is fetched with cp.async into a
 // second buffer while the current one is transformed in place: in each
 // mixed-radix (2, 3, 4, 5, 8) Stockham iteration every thread first reads its
@@ -26,7 +27,6 @@ namespace fft {
 
 constexpr int kThreads = 256;
 constexpr int kT = 8;        // lines per tile
-constexpr int kTPx = kT + 1; // padded line stride of the x-pass tiles
 
 // Resident CTAs per SM the compile-time kernels are built for: 3 for lengths
 // that are powers of two (<= 85 registers), 2 for those with radix 3 or 5.
@@ -116,7 +116,10 @@ __device__ __forceinline__ void dft(float2* v) {
 // ---------------------------------------------------------------------------
 // One Stockham iteration: radix R, Ns = product of the radices already
 // applied, in place on kT lines of length L.  Twiddles tw[t * TWS] =
-// e^{-2 pi i t / (L * TWS)}.
+// e^{-2 pi i t / (L * TWS)}.  Element (l, c) of line c sits at
+// s[l * kT + c] (column layout, strided passes; consecutive threads take
+// consecutive lines) or s[c * LP + l] (row layout, x passes; consecutive
+// threads take consecutive butterflies of one line).
 
 __host__ __device__ constexpr int span_before(const RPlan& p, int s) {
   int ns = 1;
@@ -124,7 +127,17 @@ __host__ __device__ constexpr int span_before(const RPlan& p, int s) {
   return ns;
 }
 
-template <int L, int S, bool INV, int TP, int TWS>
+template <bool ROW, int NBF>
+__device__ __forceinline__ void split_b(int b, int nbf_rt, int& c, int& j) {
+  const int nbf = NBF > 0 ? NBF : nbf_rt;
+  if (ROW) { c = b / nbf; j = b - c * nbf; }
+  else { c = b % kT; j = b / kT; }
+}
+
+template <bool ROW>
+__device__ __forceinline__ int at(int l, int c, int lp) { return ROW ? c * lp + l : l * kT + c; }
+
+template <int L, int S, bool INV, bool ROW, int LP, int TWS>
 __device__ __forceinline__ void stage_ct(float2* s, const float2* tw) {
   constexpr RPlan P = rplan(L);
   constexpr int R = P.r[S];
@@ -138,10 +151,11 @@ __device__ __forceinline__ void stage_ct(float2* s, const float2* tw) {
   for (int q = 0; q < NB; ++q) {
     const int b = threadIdx.x + q * kThreads;
     if (total % kThreads == 0 || b < total) {
-      const int c = b % kT, j = b / kT;
+      int c, j;
+      split_b<ROW, nbf>(b, nbf, c, j);
       const int k = j % Ns;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[(j + r * nbf) * TP + c];
+      for (int r = 0; r < R; ++r) v[q][r] = s[at<ROW>(j + r * nbf, c, LP)];
       if constexpr (Ns > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -158,28 +172,29 @@ __device__ __forceinline__ void stage_ct(float2* s, const float2* tw) {
   for (int q = 0; q < NB; ++q) {
     const int b = threadIdx.x + q * kThreads;
     if (total % kThreads == 0 || b < total) {
-      const int c = b % kT, j = b / kT;
+      int c, j;
+      split_b<ROW, nbf>(b, nbf, c, j);
       const int k = j % Ns;
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[(base + r * Ns) * TP + c] = v[q][r];
+      for (int r = 0; r < R; ++r) s[at<ROW>(base + r * Ns, c, LP)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-template <int L, int S, bool INV, int TP, int TWS>
+template <int L, int S, bool INV, bool ROW, int LP, int TWS>
 __device__ __forceinline__ void fft_ct(float2* s, const float2* tw) {
   constexpr RPlan P = rplan(L);
   if constexpr (S < P.nst) {
-    if constexpr (P.r[S] != 1) stage_ct<L, S, INV, TP, TWS>(s, tw);
-    fft_ct<L, S + 1, INV, TP, TWS>(s, tw);
+    if constexpr (P.r[S] != 1) stage_ct<L, S, INV, ROW, LP, TWS>(s, tw);
+    fft_ct<L, S + 1, INV, ROW, LP, TWS>(s, tw);
   }
 }
 
 // Runtime-length fallback: the same iteration with runtime R, Ns, L.
-template <int R, bool INV, int TP>
-__device__ __forceinline__ void stage_rt(float2* s, const float2* tw, int tws, int L, int Ns) {
+template <int R, bool INV, bool ROW>
+__device__ __forceinline__ void stage_rt(float2* s, const float2* tw, int tws, int L, int Ns, int lp) {
   constexpr int MAXB = (512 * kT / kThreads + R - 1) / R;
   const int nbf = L / R;
   const int total = nbf * kT;
@@ -189,10 +204,11 @@ __device__ __forceinline__ void stage_rt(float2* s, const float2* tw, int tws, i
   for (int q = 0; q < MAXB; ++q) {
     const int b = threadIdx.x + q * kThreads;
     if (b < total) {
-      const int c = b % kT, j = b / kT;
+      int c, j;
+      split_b<ROW, 0>(b, nbf, c, j);
       const int k = j % Ns;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[(j + r * nbf) * TP + c];
+      for (int r = 0; r < R; ++r) v[q][r] = s[at<ROW>(j + r * nbf, c, lp)];
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         float2 w = tw[r * k * twstep];
@@ -207,36 +223,48 @@ __device__ __forceinline__ void stage_rt(float2* s, const float2* tw, int tws, i
   for (int q = 0; q < MAXB; ++q) {
     const int b = threadIdx.x + q * kThreads;
     if (b < total) {
-      const int c = b % kT, j = b / kT;
+      int c, j;
+      split_b<ROW, 0>(b, nbf, c, j);
       const int k = j % Ns;
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[(base + r * Ns) * TP + c] = v[q][r];
+      for (int r = 0; r < R; ++r) s[at<ROW>(base + r * Ns, c, lp)] = v[q][r];
     }
   }
   __syncthreads();
 }
 
-template <bool INV, int TP>
-__device__ __forceinline__ void fft_rt(float2* s, const float2* tw, int tws, const FftLen& f) {
+template <bool INV, bool ROW>
+__device__ __forceinline__ void fft_rt(float2* s, const float2* tw, int tws, const FftLen& f, int lp) {
   int Ns = 1;
   for (int i = 0; i < f.nst; ++i) {
     switch (f.radix[i]) {
-      case 2: stage_rt<2, INV, TP>(s, tw, tws, f.n, Ns); break;
-      case 3: stage_rt<3, INV, TP>(s, tw, tws, f.n, Ns); break;
-      case 4: stage_rt<4, INV, TP>(s, tw, tws, f.n, Ns); break;
-      case 5: stage_rt<5, INV, TP>(s, tw, tws, f.n, Ns); break;
-      case 8: stage_rt<8, INV, TP>(s, tw, tws, f.n, Ns); break;
+      case 2: stage_rt<2, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
+      case 3: stage_rt<3, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
+      case 4: stage_rt<4, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
+      case 5: stage_rt<5, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
+      case 8: stage_rt<8, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
       default: break;  // radix 1: identity
     }
     Ns *= f.radix[i];
   }
 }
 
-template <int LC, bool INV, int TP, int TWS>
-__device__ __forceinline__ void fft_lines(float2* s, const float2* tw, const FftLen& f) {
-  if constexpr (LC > 0) fft_ct<LC, 0, INV, TP, TWS>(s, tw);
-  else fft_rt<INV, TP>(s, tw, TWS, f);
+// Column-layout transform of kT lines (strided passes).
+template <int LC, bool INV>
+__device__ __forceinline__ void fft_cols(float2* s, const float2* tw, const FftLen& f) {
+  if constexpr (LC > 0) fft_ct<LC, 0, INV, false, 0, 1>(s, tw);
+  else fft_rt<INV, false>(s, tw, 1, f, 0);
+}
+
+// Row pitch of the x-pass tiles: M + 2 complex (even: 16-byte aligned rows).
+__host__ __device__ constexpr int row_pitch(int M) { return M + 2; }
+
+// Row-layout transform of kT lines of length M (x passes; twiddles of 2M).
+template <int MC, bool INV>
+__device__ __forceinline__ void fft_rows(float2* s, const float2* tw, const FftLen& f) {
+  if constexpr (MC > 0) fft_ct<MC, 0, INV, true, row_pitch(MC), 2>(s, tw);
+  else fft_rt<INV, true>(s, tw, 2, f, row_pitch(f.n));
 }
 
 // ---------------------------------------------------------------------------
@@ -250,27 +278,23 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid
   const int n = valid ? 8 : 0;
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Kernel-spectrum lookup for the fused multiply: element (kz, i) of the z
-// pass, i = ky * px + kx, reads the octant at (min(kz, nz-kz), min(ky, ny-ky),
-// kx); kx beyond n[0]/2 (row padding) gets 0.
+// Kernel spectra for the fused multiply: the octant K^_s[kzf][kyf][kx] with
+// rows padded to the spectrum pitch px (zeros for kx > n[0]/2).  Element
+// (kz, i) of the z pass, i = ky * px + kx, uses (min(kz, nz-kz),
+// min(ky, ny-ky), kx).
 struct KhatArgs {
   const float* khat;  // octant of shell 0 (nullptr: multiply by 1)
   int64_t shell_stride;
-  int px, ny, nz, ox, oy;
+  int px, ny, nz, oy;
 };
-
-__device__ __forceinline__ float khat_at(const KhatArgs& K, const float* kh, int kz, int i) {
-  const int ky = i / K.px;
-  const int kx = i - ky * K.px;
-  if (kx >= K.ox) return 0.0f;
-  const int kzf = min(kz, K.nz - kz);
-  const int kyf = min(ky, K.ny - ky);
-  return __ldg(kh + ((int64_t)kzf * K.oy + kyf) * K.ox + kx);
-}
 
 // A strided-axis view: element (o, l, i) at o*so + l*sl + i, l in [0, L),
 // i in [0, inner); a tile is one o and kT consecutive i.
@@ -334,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(LC))
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    fft_lines<LC, INV, kT, 1>(cur, tws, f);
+    fft_cols<LC, INV>(cur, tws, f);
     store_strided_tile(cur, out, v, L, t);
     __syncthreads();
     t = tn;
@@ -344,34 +368,53 @@ __global__ void __launch_bounds__(kThreads, min_blocks(LC))
 // Inverse z pass of every shell at once: a half-spectrum tile is read once,
 // then for each shell s it is multiplied by K^_s (Eq. 9 in Fourier space),
 // transformed along z and stored to that shell's scratch spectrum
-// out + s * out_stride.  khat == nullptr: one transform, factor 1.
+// out + s * out_stride.  The tile's slab of K^_s (nz/2 + 1 rows of kT
+// values) is fetched with cp.async while the previous shell is transformed.
+// khat == nullptr: one transform, factor 1.
 template <int LC>
 __global__ void __launch_bounds__(kThreads, min_blocks(LC))
     zmulti_kernel(const float2* in, float2* out, int64_t out_stride, int nshells, StridedView v, FftLen f,
                   const float2* __restrict__ tw, KhatArgs K) {
   extern __shared__ float4 smem4[];
   const int L = LC > 0 ? LC : f.n;
+  const int OZ = L / 2 + 1;
   float2* pristine = reinterpret_cast<float2*>(smem4);
   float2* work = pristine + L * kT;
   float2* tws = work + L * kT;
+  float* slab0 = reinterpret_cast<float*>(tws + L);
+  float* slab1 = slab0 + OZ * kT;
   const int64_t ntiles = (v.inner + kT - 1) / kT;
   for (int i = threadIdx.x; i < L; i += kThreads) tws[i] = __ldg(tw + i);
+  // two halves of 4 columns per tile: px is a multiple of 4 and i0 of 8, so
+  // each half lies in one ky row of the spectrum
+  auto load_slab = [&](float* dst, int s, int64_t tile) {
+    const float* kh = K.khat + (int64_t)s * K.shell_stride;
+    for (int idx = threadIdx.x; idx < 2 * OZ; idx += kThreads) {
+      const int kzf = idx >> 1, h = idx & 1;
+      const int i = (int)tile * kT + 4 * h;
+      const bool ok = i < v.inner;
+      const int ky = i / K.px, kx = i - (i / K.px) * K.px;
+      const int kyf = min(ky, K.ny - ky);
+      cp_async16(dst + kzf * kT + 4 * h, ok ? kh + ((int64_t)kzf * K.oy + kyf) * K.px + kx : K.khat, ok);
+    }
+  };
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     load_strided_tile(pristine, in, v, L, t);
+    if (K.khat) load_slab(slab0, 0, t);
     cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    const int i0 = (int)t * kT;
     for (int s = 0; s < nshells; ++s) {
-      const float* kh = K.khat ? K.khat + (int64_t)s * K.shell_stride : nullptr;
+      const float* slab = (s & 1) ? slab1 : slab0;
+      if (K.khat && s + 1 < nshells) load_slab((s & 1) ? slab0 : slab1, s + 1, t);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
       for (int idx = threadIdx.x; idx < L * kT; idx += kThreads) {
         const int l = idx / kT, c = idx % kT;
-        const int i = i0 + c;
-        const float m = kh ? (i < v.inner ? khat_at(K, kh, l, i) : 0.0f) : 1.0f;
+        const float m = K.khat ? slab[min(l, L - l) * kT + c] : 1.0f;
         work[idx] = cscale(pristine[idx], m);
       }
       __syncthreads();
-      fft_lines<LC, true, kT, 1>(work, tws, f);
+      fft_cols<LC, true>(work, tws, f);
       store_strided_tile(work, out + (int64_t)s * out_stride, v, L, t);
       __syncthreads();
     }
@@ -381,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(LC))
 // Forward x pass: real rows of length nx = 2M -> half-spectrum rows (pitch
 // px).  z[m] = x[2m] + i x[2m+1], Z = DFT_M(z), then X[k] = E[k] +
 // e^{-2 pi i k/nx} O[k], E = (Z[k] + conj Z[M-k]) / 2,
-// O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M.
+// O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M.  Tiles of kT rows in row layout.
 template <int MC>
 __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     x_r2c_kernel(const float* __restrict__ in, float2* __restrict__ out, int nx, int px, int64_t rows, FftLen f,
@@ -389,19 +432,29 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   extern __shared__ float4 smem4[];
   const int M = MC > 0 ? MC : nx / 2;
   const int NX = 2 * M;
+  const int LP = row_pitch(M);
   float2* buf0 = reinterpret_cast<float2*>(smem4);
-  float2* buf1 = buf0 + (M + 1) * kTPx;
-  float2* tws = buf1 + (M + 1) * kTPx;
+  float2* buf1 = buf0 + kT * LP;
+  float2* tws = buf1 + kT * LP;
   const int64_t ntiles = (rows + kT - 1) / kT;
   int64_t t = blockIdx.x;
   if (t >= ntiles) return;
   for (int i = threadIdx.x; i < NX; i += kThreads) tws[i] = __ldg(tw + i);
   auto load = [&](float2* s, int64_t tile) {
     const int64_t r0 = tile * kT;
-    for (int idx = threadIdx.x; idx < kT * M; idx += kThreads) {
-      const int c = idx / M, m = idx - c * M;
-      const bool ok = r0 + c < rows;
-      cp_async8(s + m * kTPx + c, ok ? (const void*)(in + (r0 + c) * NX + 2 * m) : (const void*)in, ok);
+    if (M % 2 == 0) {  // rows 16-byte aligned: two z values per copy
+      const int np = M / 2;
+      for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
+        const int c = idx / np, m = 2 * (idx - c * np);
+        const bool ok = r0 + c < rows;
+        cp_async16(s + c * LP + m, ok ? (const void*)(in + (r0 + c) * NX + 2 * m) : (const void*)in, ok);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kT * M; idx += kThreads) {
+        const int c = idx / M, m = idx - c * M;
+        const bool ok = r0 + c < rows;
+        cp_async8(s + c * LP + m, ok ? (const void*)(in + (r0 + c) * NX + 2 * m) : (const void*)in, ok);
+      }
     }
   };
   load(buf0, t);
@@ -413,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    fft_lines<MC, false, kTPx, 2>(s, tws, f);
+    fft_rows<MC, false>(s, tws, f);
     const int64_t r0 = t * kT;
     for (int idx = threadIdx.x; idx < kT * px; idx += kThreads) {
       const int c = idx / px, k = idx - c * px;
@@ -421,8 +474,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
       if (row >= rows) continue;
       float2 X = make_float2(0.f, 0.f);
       if (k <= M) {
-        const float2 zk = s[(k == M ? 0 : k) * kTPx + c];
-        const float2 zc = cconj(s[(k == 0 ? 0 : M - k) * kTPx + c]);
+        const float2 zk = s[c * LP + (k == M ? 0 : k)];
+        const float2 zc = cconj(s[c * LP + (k == 0 ? 0 : M - k)]);
         const float2 E = cscale(cadd(zk, zc), 0.5f);
         const float2 O = cscale(cmul_mi<false>(csub(zk, zc)), 0.5f);
         X = cadd(E, cmul(tws[k], O));
@@ -446,19 +499,23 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   extern __shared__ float4 smem4[];
   const int M = MC > 0 ? MC : nx / 2;
   const int NX = 2 * M;
+  const int LP = row_pitch(M);
   float2* buf0 = reinterpret_cast<float2*>(smem4);
-  float2* buf1 = buf0 + (M + 1) * kTPx;
-  float2* tws = buf1 + (M + 1) * kTPx;
+  float2* buf1 = buf0 + kT * LP;
+  float2* tws = buf1 + kT * LP;
   const int64_t ntiles = (rows + kT - 1) / kT;
   int64_t t = blockIdx.x;
   if (t >= ntiles) return;
   for (int i = threadIdx.x; i < NX; i += kThreads) tws[i] = __ldg(tw + i);
+  // X[0..M] as pairs (k, k+1), k even: M/2 + 1 copies per row; for even M
+  // the last pair also reads padding column M + 1 (< px)
+  const int np = M / 2 + 1;
   auto load = [&](float2* s, int64_t tile) {
     const int64_t r0 = tile * kT;
-    for (int idx = threadIdx.x; idx < kT * (M + 1); idx += kThreads) {
-      const int c = idx / (M + 1), k = idx - c * (M + 1);
+    for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
+      const int c = idx / np, k = 2 * (idx - c * np);
       const bool ok = r0 + c < rows;
-      cp_async8(s + k * kTPx + c, ok ? (const void*)(in + (r0 + c) * px + k) : (const void*)in, ok);
+      cp_async16(s + c * LP + k, ok ? (const void*)(in + (r0 + c) * px + k) : (const void*)in, ok);
     }
   };
   load(buf0, t);
@@ -473,25 +530,38 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     __syncthreads();
     for (int idx = threadIdx.x; idx < kT * half; idx += kThreads) {
       const int c = idx / half, k = idx - c * half;
-      const float2 a = s[k * kTPx + c];
-      const float2 b = s[(M - k) * kTPx + c];
+      const float2 a = s[c * LP + k];
+      const float2 b = s[c * LP + M - k];
       const float2 ca = cconj(a), cb = cconj(b);
       const float2 zk = cadd(cadd(a, cb), cmul_mi<true>(cmul(cconj(tws[k]), csub(a, cb))));
-      s[k * kTPx + c] = zk;
+      s[c * LP + k] = zk;
       if (k != 0 && 2 * k != M) {
         const float2 zm = cadd(cadd(b, ca), cmul_mi<true>(cmul(cconj(tws[M - k]), csub(b, ca))));
-        s[(M - k) * kTPx + c] = zm;
+        s[c * LP + M - k] = zm;
       }
     }
     __syncthreads();
-    fft_lines<MC, true, kTPx, 2>(s, tws, f);
+    fft_rows<MC, true>(s, tws, f);
     const int64_t r0 = t * kT;
-    for (int idx = threadIdx.x; idx < kT * M; idx += kThreads) {
-      const int c = idx / M, m = idx - c * M;
-      const int64_t row = r0 + c;
-      if (row < rows) {
-        const int64_t sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
-        *reinterpret_cast<float2*>(out + sh * out_shell_stride + rr * NX + 2 * m) = s[m * kTPx + c];
+    if (M % 2 == 0) {  // two z values (four reals) per 16-byte store
+      const int nq = M / 2;
+      for (int idx = threadIdx.x; idx < kT * nq; idx += kThreads) {
+        const int c = idx / nq, m = 2 * (idx - c * nq);
+        const int64_t row = r0 + c;
+        if (row < rows) {
+          const int64_t sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
+          const float2 a = s[c * LP + m], b = s[c * LP + m + 1];
+          *reinterpret_cast<float4*>(out + sh * out_shell_stride + rr * NX + 2 * m) = make_float4(a.x, a.y, b.x, b.y);
+        }
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < kT * M; idx += kThreads) {
+        const int c = idx / M, m = idx - c * M;
+        const int64_t row = r0 + c;
+        if (row < rows) {
+          const int64_t sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
+          *reinterpret_cast<float2*>(out + sh * out_shell_stride + rr * NX + 2 * m) = s[c * LP + m];
+        }
       }
     }
     __syncthreads();
@@ -501,8 +571,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
 
 // shared-memory bytes of each kernel
 inline size_t strided_smem(int L) { return (size_t)L * (2 * kT + 1) * sizeof(float2); }
-inline size_t zmulti_smem(int L) { return (size_t)L * (2 * kT + 1) * sizeof(float2); }
-inline size_t xpass_smem(int nx) { return ((size_t)2 * (nx / 2 + 1) * kTPx + nx) * sizeof(float2); }
+inline size_t zmulti_smem(int L) {
+  return (size_t)L * (2 * kT + 1) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * kT * sizeof(float);
+}
+inline size_t xpass_smem(int nx) { return ((size_t)2 * kT * row_pitch(nx / 2) + nx) * sizeof(float2); }
 
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).

@@ -109,6 +109,7 @@ struct Plan {
   int64_t field_stride = 0; // floats reserved per real field (>= nc, multiple of 64)
   int oct[3] = {0, 0, 0};   // octant extents n/2 + 1
   int64_t oct_elems = 0;
+  int64_t khat_stride = 0;  // floats per shell spectrum: octant rows padded to px (zeros beyond n[0]/2)
   int H = 0;                // max offset over all shells and axes
   int64_t n_multisets[CK_MAX_ORDER + 1] = {0};
   int64_t multiset_base[CK_MAX_ORDER + 1] = {0};  // offset of order n in a packed array

@@ -123,6 +123,7 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   p->oct[1] = ny / 2 + 1;
   p->oct[2] = nz / 2 + 1;
   p->oct_elems = (int64_t)p->oct[0] * p->oct[1] * p->oct[2];
+  p->khat_stride = (int64_t)p->px * p->oct[1] * p->oct[2];
   factor_len(nx / 2, &p->fx_half);
   factor_len(ny, &p->fy);
   factor_len(nz, &p->fz);
@@ -170,7 +171,7 @@ size_t workspace_bytes(const Plan& p) {
   b += al((size_t)p.field_stride * 4);                         // field
   b += al((size_t)p.spec_elems * 8);                           // spec
   b += al((size_t)p.ns * p.spec_elems * 8);                    // tmp: one scratch spectrum per shell
-  b += al((size_t)p.ns * p.oct_elems * 4);                     // khat
+  b += al((size_t)p.ns * p.khat_stride * 4);                   // khat (padded octants)
   b += al(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8));  // bank
   b += al(p.partials_cap * 8);                                 // partials
   b += al((size_t)2 * 3 * p.staging_pts * 4);                  // staging

@@ -272,6 +272,14 @@ WORKLOADS: Dict[str, dict] = {
         data=("ns_box", dict(seed=6, n_parents=2_500, n_children=20, sigma=8.0)),
         randoms=("uniform_box", dict(seed=7, n=2_000_000)),
     ),
+    # Profiler case for the 16-shell contraction: periodic 256^3 of 10 h^-1
+    # Mpc (W bank 1.07 GB per field), 50k clustered points, 2M randoms.
+    "profile256s16": dict(
+        grid=GridSpec((256, 256, 256), (0.0, 0.0, 0.0), 10.0, True),
+        shells=_shells(20.0, 10.0, 16), width=10.0, orders=(2, 3),
+        data=("ns_box", dict(seed=8, n_parents=2_500, n_children=20, sigma=8.0)),
+        randoms=("uniform_box", dict(seed=9, n=2_000_000)),
+    ),
 }
 
 
