@@ -194,6 +194,27 @@ ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* strea
 ck_status ck_contract(ck_plan* plan, const float* w0, const float* bank, int64_t bank_stride,
                       int32_t order_mask, double* const* sums, void* stream);
 
+/* No-allocation variant of ck_contract (the paper has no counterpart): the
+ * same summation (sums[n][j] = sum_r w0[r] prod_i bank[s_i * bank_stride + r]
+ * over the multisets of order n in lexicographic order), for callers that
+ * cannot allocate device memory -- a caller running inside another
+ * framework's memory pool or a captured allocation-free region, or one that
+ * must not grow its footprint after start-up.  It needs no plan: its scratch
+ * (per-CTA partial sums and a status word, about 0.6 MB) is a fixed
+ * file-scope device array that every GPU loading this library holds until
+ * the process exits; it calls no allocator.  Limits: n_shells <= 16 with
+ * orders <= 3, or n_shells <= 5 with orders <= 5 (otherwise
+ * CK_ERR_UNSUPPORTED); at most 512 CTAs.  w0, bank: device float, 16-byte
+ * aligned, n_cells cells each, bank_stride >= n_cells and a multiple of 4;
+ * sums[n]: device double [C(n_shells + n - 2, n - 1)] or NULL.  The first
+ * call on a device looks up the scratch address (cudaGetSymbolAddress) with
+ * that device current, so make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (other
+ * streams or threads) race and must be serialised by the caller.  If a
+ * bounded device wait gives up, the outputs are NaN. */
+ck_status ck_contract_static(const float* w0, const float* bank, int64_t bank_stride, int64_t n_cells,
+                             int32_t n_shells, int32_t order_mask, double* const* sums, void* stream);
+
 /* --- per-stage device timing --------------------------------------------------
  * When enabled, the library records a CUDA event pair on the caller's stream
  * around every kernel it launches, grouped by stage, together with the

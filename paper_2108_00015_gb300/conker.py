@@ -10,6 +10,7 @@ fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from typing import Dict, Iterable, Optional, Sequence
 
@@ -91,6 +92,8 @@ _SIGS = [
     ("ck_fft_r2c", ctypes.c_int, [_P, _P, _P, _P]),
     ("ck_fft_c2r", ctypes.c_int, [_P, _P, _P, _P]),
     ("ck_contract", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P), _P]),
+    ("ck_contract_static", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(_P), _P]),
     ("ck_profile_enable", ctypes.c_int, [_P, ctypes.c_int32]),
     ("ck_profile_read", ctypes.c_int, [_P, ctypes.POINTER(_StageTimes)]),
     ("ck_stage_name", ctypes.c_char_p, [ctypes.c_int32]),
@@ -153,6 +156,19 @@ def _as_f32(a):
     torch = _torch()
     assert a.dtype == torch.float32 and a.is_contiguous(), "positions must be contiguous float32"
     return a
+
+
+def contract_static(w0, bank, bank_stride: int, n_cells: int, n_shells: int, orders=(2, 3), stream=None):
+    """ck_contract_static: the summation without a plan or any device
+    allocation by the library (outputs are torch tensors allocated here)."""
+    torch = _torch()
+    sums = {n: torch.empty(math.comb(n_shells + n - 2, n - 1), dtype=torch.float64, device="cuda") for n in orders}
+    arr = (ctypes.c_void_p * (CK_MAX_ORDER + 1))()
+    for n, t in sums.items():
+        arr[n] = t.data_ptr()
+    _check(_lib().ck_contract_static(_ptr(w0), _ptr(bank), int(bank_stride), int(n_cells), int(n_shells),
+                                     order_mask(orders), arr, _stream_ptr(stream)), "ck_contract_static")
+    return sums
 
 
 def order_mask(orders: Iterable[int]) -> int:

@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ck_device.cuh"
@@ -566,3 +567,86 @@ void launch_finalize(const Plan& p, int mask, cudaStream_t st) {
 int64_t host_multiset_rank(const int* s, int k, int ns) { return multiset_rank(s, k, ns); }
 
 }  // namespace ck
+
+// ---------------------------------------------------------------------------
+// ck_contract_static: the register contraction with its scratch (per-CTA
+// partial sums and a status word) in a fixed file-scope device array instead
+// of plan workspace, for callers that cannot allocate device memory.
+
+namespace ck {
+namespace {
+
+constexpr int kStaticMaxCtas = 512;
+constexpr int kStaticMaxOut = 152;  // register-kernel outputs: 16 shells, n <= 3
+constexpr int kStaticMaxDevices = 64;
+constexpr size_t kStaticDoubles = (size_t)kStaticMaxCtas * kStaticMaxOut + 32;
+
+// Held by every GPU that loads this library, until the process exits.
+static __device__ __align__(256) double g_contract_scratch[kStaticDoubles];
+
+void* g_scratch_addr[kStaticMaxDevices] = {nullptr};
+std::mutex g_scratch_mutex;
+
+// Partials (CTA order, fixed) into each requested order's caller pointer;
+// NaN everywhere if a device wait of the contraction gave up.
+__global__ void static_reduce_kernel(const double* __restrict__ partials, int ctas, int nout, int ns, int maxn,
+                                     const int* __restrict__ status, double* o2, double* o3, double* o4,
+                                     double* o5) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double s = 0.0;
+  for (int c = 0; c < ctas; ++c) s += partials[(int64_t)c * nout + o];
+  if (*status != 0) s = __longlong_as_double(0x7ff8000000000000ll);
+  const int n2 = ns, n3 = maxn >= 3 ? cmb(ns + 1, 2) : 0, n4 = maxn >= 4 ? cmb(ns + 2, 3) : 0;
+  if (o < n2) { if (o2) o2[o] = s; return; }
+  if (o < n2 + n3) { if (o3) o3[o - n2] = s; return; }
+  if (o < n2 + n3 + n4) { if (o4) o4[o - n2 - n3] = s; return; }
+  if (o5) o5[o - n2 - n3 - n4] = s;
+}
+
+}  // namespace
+}  // namespace ck
+
+using namespace ck;
+
+extern "C" ck_status ck_contract_static(const float* w0, const float* bank, int64_t bank_stride, int64_t n_cells,
+                                        int32_t n_shells, int32_t order_mask, double* const* sums, void* stream) {
+  if (!w0 || !bank || !sums) return CK_ERR_BAD_POINTER;
+  if (n_cells < 1 || n_shells < 1 || bank_stride < n_cells || (bank_stride % 4) != 0) return CK_ERR_ARG;
+  if (order_mask == 0 || (order_mask & ~0x3c) != 0) return CK_ERR_ARG;
+  const int maxn = max_order_in(order_mask);
+  // the fixed scratch holds the register kernel's partial sums only
+  if (!((n_shells <= 16 && maxn <= 3) || (n_shells <= 5 && maxn <= 5))) return CK_ERR_UNSUPPORTED;
+  if (((uintptr_t)w0 & 15u) != 0 || ((uintptr_t)bank & 15u) != 0) return CK_ERR_BAD_POINTER;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return CK_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CK_ERR_CUDA;
+  const int ctas = std::min(sms, kStaticMaxCtas);
+  const int reg_maxn = maxn <= 3 ? 3 : 5;
+  const int nout = reg_nout(n_shells, reg_maxn);
+  if ((size_t)ctas * nout + 1 > kStaticDoubles - 31) return CK_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+      void* a = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&a, g_contract_scratch);
+      if (e != cudaSuccess || !a) return CK_ERR_CUDA;
+      g_scratch_addr[dev] = a;
+    }
+    base = g_scratch_addr[dev];
+  }
+  double* partials = static_cast<double*>(base);
+  int* status = reinterpret_cast<int*>(partials + (size_t)ctas * nout);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return CK_ERR_CUDA;
+  const int64_t nchunks = (n_cells + RK_KC - 1) / RK_KC;
+  const int64_t cpc = (nchunks + ctas - 1) / ctas;
+  cudaError_t e = launch_reg(n_shells, reg_maxn, w0, bank, bank_stride, n_cells, ctas, cpc, partials, status, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  double* o[CK_MAX_ORDER + 1] = {nullptr};
+  for (int n = 2; n <= CK_MAX_ORDER; ++n) o[n] = ((order_mask >> n) & 1) ? sums[n] : nullptr;
+  static_reduce_kernel<<<(nout + 127) / 128, 128, 0, st>>>(partials, ctas, nout, n_shells, reg_maxn, status, o[2],
+                                                           o[3], o[4], o[5]);
+  return cuda_status(cudaGetLastError());
+}
