@@ -63,7 +63,7 @@ __all__ = [
     "cell_edge", "cell_index", "grid_counts", "density_fields", "shell_offsets",
     "check_periodic_support", "kernel_grid", "convolve_direct", "convolve_fft",
     "w_at_cells", "multisets", "product_sums", "dense_tensor", "xi_from",
-    "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok",
+    "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok", "pair_sums_fft",
 ]
 
 
@@ -242,6 +242,20 @@ def w_at_cells(F: np.ndarray, offsets: np.ndarray, cells: np.ndarray, periodic: 
         else:
             ok = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
             out[i] = F[jz[ok], jy[ok], jx[ok]].sum()
+    return out
+
+
+def pair_sums_fft(F: np.ndarray, offsets_list: Sequence[np.ndarray]) -> np.ndarray:
+    """Order-2 sums sum_r F(r) W_s(r) = sum_{m in O_s} C(m) for every shell,
+    C(m) = sum_r F(r) F(r + m) the circular autocorrelation of F, from one
+    forward and one inverse library FFT (FP64).  On a periodic grid this is
+    Eq. 12's numerator (or denominator); on a zero-outside grid it equals it
+    when the guard band holds."""
+    C = np.fft.irfftn(np.abs(np.fft.rfftn(F)) ** 2, s=F.shape, axes=(0, 1, 2))
+    nz, ny, nx = F.shape
+    out = np.zeros(len(offsets_list))
+    for i, o in enumerate(offsets_list):
+        out[i] = C[np.mod(o[:, 2], nz), np.mod(o[:, 1], ny), np.mod(o[:, 0], nx)].sum()
     return out
 
 

@@ -116,6 +116,7 @@ ck_status carve(Plan& p) {
   p.staging = reinterpret_cast<float*>(take((size_t)2 * 3 * p.staging_pts * 4));
   for (int a = 0; a < 3; ++a) p.thr[a] = reinterpret_cast<float*>(take((size_t)(p.grid.n[a] + 1) * 4));
   for (int a = 0; a < 3; ++a) p.tw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
+  for (int a = 0; a < 3; ++a) p.stw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
   p.dstate = reinterpret_cast<DevState*>(take(sizeof(DevState)));
   p.den_raw = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
   p.sums = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
@@ -138,6 +139,26 @@ void thresholds(double o, double g, int n, std::vector<float>& t) {
   }
 }
 
+// Per-iteration twiddles of a length-n transform: for iteration i (radix R,
+// Ns = product of the earlier radices), entries k * (R - 1) + r - 1 hold
+// e^{-2 pi i r k / (Ns R)}, k < Ns, 1 <= r < R.
+void stage_twiddles(int n, std::vector<float2>& w) {
+  const RPlan pl = rplan(n);
+  w.clear();
+  int ns = 1;
+  for (int i = 0; i < pl.nst; ++i) {
+    const int R = pl.r[i];
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < R; ++r) {
+        const long long num = ((long long)r * k) % ((long long)ns * R);
+        const double a = 2.0 * M_PI * (double)num / (double)(ns * R);
+        w.push_back(make_float2((float)cos(a), (float)-sin(a)));
+      }
+    ns *= R;
+  }
+  if (w.empty()) w.push_back(make_float2(1.f, 0.f));
+}
+
 void twiddles(int n, std::vector<float2>& w) {
   w.resize((size_t)n);
   for (int t = 0; t < n; ++t) {
@@ -154,6 +175,10 @@ ck_status upload_tables(Plan& p, cudaStream_t st) {
     std::vector<float2> w;
     twiddles(p.grid.n[a], w);
     CK_TRY(cudaMemcpy(p.tw[a], w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+    // y and z transform full lengths, x the half length
+    stage_twiddles(a == 0 ? p.grid.n[0] / 2 : p.grid.n[a], w);
+    if (w.size() > (size_t)p.grid.n[a]) return CK_ERR_ARG;
+    CK_TRY(cudaMemcpy(p.stw[a], w.data(), w.size() * 8, cudaMemcpyHostToDevice));
   }
   // dense [N_s]^(n-1) index -> rank of its sorted multiset
   std::vector<int> map((size_t)std::max<int64_t>(p.dense_total, 1), 0);

@@ -91,12 +91,75 @@ __device__ __forceinline__ void reg_flush(float* acc, double* wacc, int lane) {
   }
 }
 
-template <int NS, int MAXN>
-__global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
+// Orders 2 and 3 for the shells a in [A0, A1) only, in the local order
+// (a, then b >= a): acc[i] for n = 2 at (a), then n = 3 at (a, a..NS-1).
+template <int NS, int A0, int A1>
+__device__ __forceinline__ void reg_accumulate_range(float* acc, const float* v) {
+  int i = 0;
+#pragma unroll
+  for (int a = A0; a < A1; ++a) {
+    const float p1 = v[0] * v[1 + a];
+    acc[i++] += p1;
+#pragma unroll
+    for (int b = a; b < NS; ++b) acc[i++] += p1 * v[1 + b];
+  }
+}
+
+__host__ __device__ constexpr int rank3(int ns, int a, int b) {  // (a <= b) in lexicographic order
+  return a * ns - a * (a - 1) / 2 + (b - a);
+}
+
+// Flush the local accumulators of shells [A0, A1) into the warp's FP64 row
+// (global order: n = 2 at a, n = 3 at ns + rank3(a, b)).
+template <int NS, int A0, int A1>
+__device__ __forceinline__ void reg_flush_range(float* acc, double* wacc, int lane) {
+  int i = 0;
+#pragma unroll
+  for (int a = A0; a < A1; ++a) {
+#pragma unroll
+    for (int b = a - 1; b < NS; ++b) {
+      float t = acc[i];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
+      const int o = b < a ? a : NS + rank3(NS, a, b);
+      if (lane == 0) wacc[o] += (double)t;
+      acc[i++] = 0.0f;
+    }
+  }
+}
+
+// Split of the shells between two consumer groups with about half of the
+// order-2 and order-3 outputs each.
+__host__ __device__ constexpr int split_shell(int ns) {
+  const int total = ns + ns * (ns + 1) / 2;
+  int acc = 0;
+  for (int a = 0; a < ns; ++a) {
+    acc += 1 + (ns - a);
+    if (2 * acc >= total) return a + 1;
+  }
+  return ns;
+}
+
+__host__ __device__ constexpr int outs_range(int ns, int a0, int a1) {
+  int t = 0;
+  for (int a = a0; a < a1; ++a) t += 1 + (ns - a);
+  return t;
+}
+
+// G = 1: every consumer thread keeps all outputs.  G = 2 (orders <= 3 only):
+// two groups of RK_CW consumer warps see every cell, each keeping the sums of
+// half of the shells, so twice as many warps fit with half the registers.
+template <int NS, int MAXN, int G>
+__global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
     contract_reg_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
                         int64_t chunks_per_cta, double* __restrict__ partials, int* status) {
+  static_assert(G == 1 || (G == 2 && MAXN == 3), "two consumer groups only for orders <= 3");
   constexpr int NARR = NS + 1;
   constexpr int NOUT = RegOut<NS, MAXN>::total;
+  constexpr int CWT = RK_CW * G;
+  constexpr int SPLIT = split_shell(NS);
+  constexpr int GOUT0 = outs_range(NS, 0, SPLIT), GOUT1 = outs_range(NS, SPLIT, NS);
+  constexpr int NACC = G == 1 ? NOUT : (GOUT0 > GOUT1 ? GOUT0 : GOUT1);
   extern __shared__ __align__(128) unsigned char smem[];
   float* buf = reinterpret_cast<float*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)RK_STAGES * NARR * RK_KC * 4);
@@ -111,12 +174,12 @@ __global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < RK_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], RK_CW);
+      mbar_init(&empty[s], CWT);
     }
     *consumed_min = nit;
     fence_async_shared();
   }
-  for (int i = threadIdx.x; i < RK_CW * NOUT; i += blockDim.x) wacc[i] = 0.0;
+  for (int i = threadIdx.x; i < CWT * NOUT; i += blockDim.x) wacc[i] = 0.0;
   __syncthreads();
   int issued = 0;
   if (warp == 0) {
@@ -139,10 +202,12 @@ __global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
       }
     }
   } else {
-    const int ct = threadIdx.x - 32;
-    float acc[NOUT];
+    const int grp = (warp - 1) / RK_CW;
+    const int ct = threadIdx.x - 32 - grp * 32 * RK_CW;
+    double* wrow = wacc + (warp - 1) * NOUT;
+    float acc[NACC];
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) acc[o] = 0.0f;
+    for (int o = 0; o < NACC; ++o) acc[o] = 0.0f;
     int since = 0, done = 0;
     for (int it = 0; it < nit; ++it) {
       const int st = it % RK_STAGES;
@@ -165,18 +230,24 @@ __global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
 #pragma unroll
             for (int a = 1; a < NARR; ++a) v[a] = __ldg(bank + (a - 1) * bstride + cell0 + cc);
           }
-          reg_accumulate<NS, MAXN>(acc, v);
+          if constexpr (G == 1) reg_accumulate<NS, MAXN>(acc, v);
+          else if (grp == 0) reg_accumulate_range<NS, 0, SPLIT>(acc, v);
+          else reg_accumulate_range<NS, SPLIT, NS>(acc, v);
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
       done = it + 1;
       if (++since == RK_FLUSH) {
-        reg_flush<NOUT>(acc, wacc + (warp - 1) * NOUT, lane);
+        if constexpr (G == 1) reg_flush<NOUT>(acc, wrow, lane);
+        else if (grp == 0) reg_flush_range<NS, 0, SPLIT>(acc, wrow, lane);
+        else reg_flush_range<NS, SPLIT, NS>(acc, wrow, lane);
         since = 0;
       }
     }
-    reg_flush<NOUT>(acc, wacc + (warp - 1) * NOUT, lane);
+    if constexpr (G == 1) reg_flush<NOUT>(acc, wrow, lane);
+    else if (grp == 0) reg_flush_range<NS, 0, SPLIT>(acc, wrow, lane);
+    else reg_flush_range<NS, SPLIT, NS>(acc, wrow, lane);
     if (lane == 0) atomicMin(consumed_min, done);
   }
   __syncthreads();
@@ -187,25 +258,31 @@ __global__ void __launch_bounds__(32 * (RK_CW + 1), 1)
   }
   for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < RK_CW; ++w) s += wacc[w * NOUT + o];
+    for (int w = 0; w < CWT; ++w) s += wacc[w * NOUT + o];
     partials[(int64_t)blockIdx.x * NOUT + o] = s;
   }
 }
 
+// two consumer groups for the larger order-3 shell counts
+template <int NS, int MAXN>
+constexpr int reg_groups() { return 1; }  // two groups measured slower (shared-memory reads double)
+
 template <int NS, int MAXN>
 static size_t reg_smem() {
   return (size_t)RK_STAGES * (NS + 1) * RK_KC * 4 + (2 * RK_STAGES + 1) * 8 +
-         (size_t)RK_CW * RegOut<NS, MAXN>::total * 8;
+         (size_t)RK_CW * reg_groups<NS, MAXN>() * RegOut<NS, MAXN>::total * 8;
 }
 
 template <int NS, int MAXN>
 static cudaError_t launch_reg_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ctas,
                                 int64_t cpc, double* partials, int* status, cudaStream_t st) {
+  constexpr int G = reg_groups<NS, MAXN>();
   const size_t sm = reg_smem<NS, MAXN>();
-  cudaError_t e = cudaFuncSetAttribute(contract_reg_kernel<NS, MAXN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(contract_reg_kernel<NS, MAXN, G>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  contract_reg_kernel<NS, MAXN><<<ctas, 32 * (RK_CW + 1), sm, st>>>(w0, bank, bstride, nc, cpc, partials, status);
+  contract_reg_kernel<NS, MAXN, G><<<ctas, 32 * (RK_CW * G + 1), sm, st>>>(w0, bank, bstride, nc, cpc, partials,
+                                                                           status);
   return cudaGetLastError();
 }
 

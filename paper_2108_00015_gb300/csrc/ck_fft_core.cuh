@@ -3,8 +3,7 @@
 // instantiate the passes for each transform length.
 //
 // Every pass transforms one axis.  A tile is kT = 8 independent lines of
-// length L <= 512 held in shared memory (column layout s[l * kT + c] for the
-// strided axes, row layout s[c * LP + l] for the x axis).  Persistent CTAs of
+// length L <= 512 held in shared memory in the column layout s[l * kT + c].  Persistent CTAs of
 // 256 threads walk the tiles; the next tile is fetched with cp.async into a
 // second buffer while the current one is transformed in place: in each
 // mixed-radix (2, 3, 4, 5, 8) Stockham iteration every thread first reads its
@@ -114,12 +113,20 @@ __device__ __forceinline__ void dft(float2* v) {
 }
 
 // ---------------------------------------------------------------------------
-// One Stockham iteration: radix R, Ns = product of the radices already
-// applied, in place on kT lines of length L.  Twiddles tw[t * TWS] =
-// e^{-2 pi i t / (L * TWS)}.  Element (l, c) of line c sits at
-// s[l * kT + c] (column layout, strided passes; consecutive threads take
-// consecutive lines) or s[c * LP + l] (row layout, x passes; consecutive
-// threads take consecutive butterflies of one line).
+// Stockham iterations with pluggable input and output.
+//
+// Iteration S of a length-L transform (radix R, Ns = product of the radices
+// before it): butterfly j (0 <= j < L/R) of a line reads elements
+// j + r L/R, multiplies input r by w_S[k][r] = e^{-+2 pi i r k/(Ns R)}
+// (k = j mod Ns), runs the radix-R DFT and writes element
+// (j - k) R + k + r Ns.  A work item is butterfly j of a pair of adjacent
+// lines (2 cp, 2 cp + 1): its inputs and outputs are 16-byte values holding
+// both lines' elements, and its twiddles serve both.  Item b takes
+// cp = b mod 4 and j = b / 4, so a warp touches 8 consecutive j of all 8
+// lines.  Loaders and storers take (element l, line pair cp) and a float4
+// (x, y: line 2 cp; z, w: line 2 cp + 1).
+
+constexpr int kPairs = kT / 2;
 
 __host__ __device__ constexpr int span_before(const RPlan& p, int s) {
   int ns = 1;
@@ -127,144 +134,221 @@ __host__ __device__ constexpr int span_before(const RPlan& p, int s) {
   return ns;
 }
 
-template <bool ROW, int NBF>
-__device__ __forceinline__ void split_b(int b, int nbf_rt, int& c, int& j) {
-  const int nbf = NBF > 0 ? NBF : nbf_rt;
-  if (ROW) { c = b / nbf; j = b - c * nbf; }
-  else { c = b % kT; j = b / kT; }
+// offset of iteration s in the per-length twiddle table
+__host__ __device__ constexpr int tw_offset(const RPlan& p, int s) {
+  int off = 0, ns = 1;
+  for (int i = 0; i < s; ++i) {
+    off += ns * (p.r[i] - 1);
+    ns *= p.r[i];
+  }
+  return off;
 }
 
-template <bool ROW>
-__device__ __forceinline__ int at(int l, int c, int lp) { return ROW ? c * lp + l : l * kT + c; }
+__host__ __device__ constexpr int tw_table_len(const RPlan& p) { return tw_offset(p, p.nst); }
 
-template <int L, int S, bool INV, bool ROW, int LP, int TWS>
-__device__ __forceinline__ void stage_ct(float2* s, const float2* tw) {
+__device__ __forceinline__ float2 lo2(float4 t) { return make_float2(t.x, t.y); }
+__device__ __forceinline__ float2 hi2(float4 t) { return make_float2(t.z, t.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+template <int R, bool INV>
+__device__ __forceinline__ void pair_butterfly(float4* t, int k, const float2* tw_row) {
+  float2 v0[R], v1[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    v0[r] = lo2(t[r]);
+    v1[r] = hi2(t[r]);
+  }
+  if (tw_row != nullptr && k != 0) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw_row[r - 1];
+      if (INV) w.y = -w.y;
+      v0[r] = cmul(v0[r], w);
+      v1[r] = cmul(v1[r], w);
+    }
+  }
+  dft<R, INV>(v0);
+  dft<R, INV>(v1);
+#pragma unroll
+  for (int r = 0; r < R; ++r) t[r] = cat4(v0[r], v1[r]);
+}
+
+// compile-time iteration
+template <int L, int S, bool INV, class LD, class ST>
+__device__ __forceinline__ void iter_ct(const float2* __restrict__ tw, LD&& ld, ST&& st) {
   constexpr RPlan P = rplan(L);
   constexpr int R = P.r[S];
   constexpr int Ns = span_before(P, S);
   constexpr int nbf = L / R;
-  constexpr int total = nbf * kT;
+  constexpr int total = nbf * kPairs;
   constexpr int NB = (total + kThreads - 1) / kThreads;
-  constexpr int twstep = (L / (Ns * R)) * TWS;
-  float2 v[NB][R];
+  constexpr int TO = tw_offset(P, S);
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
     const int b = threadIdx.x + q * kThreads;
     if (total % kThreads == 0 || b < total) {
-      int c, j;
-      split_b<ROW, nbf>(b, nbf, c, j);
+      const int cp = b % kPairs, j = b / kPairs;
       const int k = j % Ns;
+      float4 t[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[at<ROW>(j + r * nbf, c, LP)];
-      if constexpr (Ns > 1) {
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = tw[r * k * twstep];
-          if (INV) w.y = -w.y;
-          v[q][r] = cmul(v[q][r], w);
-        }
-      }
-      dft<R, INV>(v[q]);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < NB; ++q) {
-    const int b = threadIdx.x + q * kThreads;
-    if (total % kThreads == 0 || b < total) {
-      int c, j;
-      split_b<ROW, nbf>(b, nbf, c, j);
-      const int k = j % Ns;
+      for (int r = 0; r < R; ++r) t[r] = ld(j + r * nbf, cp);
+      pair_butterfly<R, INV>(t, k, Ns > 1 ? tw + TO + k * (R - 1) : nullptr);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) s[at<ROW>(base + r * Ns, c, LP)] = v[q][r];
+      for (int r = 0; r < R; ++r) st(base + r * Ns, cp, t[r]);
     }
   }
-  __syncthreads();
 }
 
-template <int L, int S, bool INV, bool ROW, int LP, int TWS>
-__device__ __forceinline__ void fft_ct(float2* s, const float2* tw) {
-  constexpr RPlan P = rplan(L);
-  if constexpr (S < P.nst) {
-    if constexpr (P.r[S] != 1) stage_ct<L, S, INV, ROW, LP, TWS>(s, tw);
-    fft_ct<L, S + 1, INV, ROW, LP, TWS>(s, tw);
-  }
-}
-
-// Runtime-length fallback: the same iteration with runtime R, Ns, L.
-template <int R, bool INV, bool ROW>
-__device__ __forceinline__ void stage_rt(float2* s, const float2* tw, int tws, int L, int Ns, int lp) {
-  constexpr int MAXB = (512 * kT / kThreads + R - 1) / R;
+// runtime iteration
+template <int R, bool INV, class LD, class ST>
+__device__ __forceinline__ void iter_rt(const float2* __restrict__ tw, int to, int L, int Ns, LD&& ld, ST&& st) {
   const int nbf = L / R;
-  const int total = nbf * kT;
-  const int twstep = (L / (Ns * R)) * tws;
-  float2 v[MAXB][R];
+  const int total = nbf * kPairs;
+  for (int b = threadIdx.x; b < total; b += kThreads) {
+    const int cp = b % kPairs, j = b / kPairs;
+    const int k = j % Ns;
+    float4 t[R];
 #pragma unroll
-  for (int q = 0; q < MAXB; ++q) {
-    const int b = threadIdx.x + q * kThreads;
-    if (b < total) {
-      int c, j;
-      split_b<ROW, 0>(b, nbf, c, j);
-      const int k = j % Ns;
+    for (int r = 0; r < R; ++r) t[r] = ld(j + r * nbf, cp);
+    pair_butterfly<R, INV>(t, k, tw + to + k * (R - 1));
+    const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q][r] = s[at<ROW>(j + r * nbf, c, lp)];
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = tw[r * k * twstep];
-        if (INV) w.y = -w.y;
-        v[q][r] = cmul(v[q][r], w);
-      }
-      dft<R, INV>(v[q]);
-    }
+    for (int r = 0; r < R; ++r) st(base + r * Ns, cp, t[r]);
   }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < MAXB; ++q) {
-    const int b = threadIdx.x + q * kThreads;
-    if (b < total) {
-      int c, j;
-      split_b<ROW, 0>(b, nbf, c, j);
-      const int k = j % Ns;
-      const int base = (j - k) * R + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) s[at<ROW>(base + r * Ns, c, lp)] = v[q][r];
-    }
-  }
-  __syncthreads();
 }
 
-template <bool INV, bool ROW>
-__device__ __forceinline__ void fft_rt(float2* s, const float2* tw, int tws, const FftLen& f, int lp) {
-  int Ns = 1;
+struct SmemLd {
+  const float2* s;
+  __device__ __forceinline__ float4 operator()(int l, int cp) const {
+    return reinterpret_cast<const float4*>(s)[l * kPairs + cp];
+  }
+};
+struct SmemSt {
+  float2* s;
+  __device__ __forceinline__ void operator()(int l, int cp, float4 v) const {
+    reinterpret_cast<float4*>(s)[l * kPairs + cp] = v;
+  }
+};
+
+// Whole transform of kT lines, compile-time length.  ld_first feeds
+// iteration 0, st_last takes the last iteration's outputs; the others
+// ping-pong between a and b.  Ends with the block synchronised.
+template <int L, int S, bool INV, class LD, class ST>
+__device__ __forceinline__ void chain_ct(float2* a, float2* b, const float2* tw, LD& ld_first, ST& st_last) {
+  constexpr RPlan P = rplan(L);
+  constexpr int NST = P.nst;
+  if constexpr (P.r[0] == 1) {  // length 1: copy
+    for (int cp = threadIdx.x; cp < kPairs; cp += kThreads) st_last(0, cp, ld_first(0, cp));
+    __syncthreads();
+  } else if constexpr (NST == 1) {
+    iter_ct<L, 0, INV>(tw, ld_first, st_last);
+    __syncthreads();
+  } else if constexpr (S == 0) {
+    iter_ct<L, 0, INV>(tw, ld_first, SmemSt{a});
+    __syncthreads();
+    chain_ct<L, 1, INV>(b, a, tw, ld_first, st_last);
+  } else if constexpr (S == NST - 1) {
+    // here b holds the previous iteration's output
+    iter_ct<L, S, INV>(tw, SmemLd{b}, st_last);
+    __syncthreads();
+  } else {
+    iter_ct<L, S, INV>(tw, SmemLd{b}, SmemSt{a});
+    __syncthreads();
+    chain_ct<L, S + 1, INV>(b, a, tw, ld_first, st_last);
+  }
+}
+
+// Iteration 0 split into its loads and its butterflies, so a kernel can
+// issue the next tile's loads (into registers) while the current tile runs
+// its remaining iterations.  Iteration 0 has Ns = 1: no twiddles.
+template <int L>
+struct Iter0 {
+  static constexpr RPlan P = rplan(L);
+  static constexpr int R = P.r[0];
+  static constexpr int nbf = L / R;
+  static constexpr int total = nbf * kPairs;
+  static constexpr int NB = (total + kThreads - 1) / kThreads;
+};
+
+template <int L, class LD>
+__device__ __forceinline__ void gather0(float4 (&x)[Iter0<L>::NB][Iter0<L>::R], LD& ld) {
+  using I = Iter0<L>;
+#pragma unroll
+  for (int q = 0; q < I::NB; ++q) {
+    const int b = threadIdx.x + q * kThreads;
+    if (I::total % kThreads == 0 || b < I::total) {
+      const int cp = b % kPairs, j = b / kPairs;
+#pragma unroll
+      for (int r = 0; r < I::R; ++r) x[q][r] = ld(j + r * I::nbf, cp);
+    }
+  }
+}
+
+template <int L, bool INV, class ST>
+__device__ __forceinline__ void butterfly0(float4 (&x)[Iter0<L>::NB][Iter0<L>::R], ST&& st) {
+  using I = Iter0<L>;
+#pragma unroll
+  for (int q = 0; q < I::NB; ++q) {
+    const int b = threadIdx.x + q * kThreads;
+    if (I::total % kThreads == 0 || b < I::total) {
+      const int cp = b % kPairs, j = b / kPairs;
+      pair_butterfly<I::R, INV>(x[q], 0, nullptr);
+#pragma unroll
+      for (int r = 0; r < I::R; ++r) st(j * I::R + r, cp, x[q][r]);
+    }
+  }
+}
+
+template <bool INV, class LD, class ST>
+__device__ __forceinline__ void iter_rt_dispatch(int R, const float2* tw, int to, int L, int Ns, LD&& ld, ST&& st) {
+  switch (R) {
+    case 2: iter_rt<2, INV>(tw, to, L, Ns, ld, st); break;
+    case 3: iter_rt<3, INV>(tw, to, L, Ns, ld, st); break;
+    case 4: iter_rt<4, INV>(tw, to, L, Ns, ld, st); break;
+    case 5: iter_rt<5, INV>(tw, to, L, Ns, ld, st); break;
+    case 8: iter_rt<8, INV>(tw, to, L, Ns, ld, st); break;
+    default:  // radix 1
+      for (int idx = threadIdx.x; idx < L * kPairs; idx += kThreads)
+        st(idx / kPairs, idx % kPairs, ld(idx / kPairs, idx % kPairs));
+  }
+}
+
+// Whole transform, runtime length.
+template <bool INV, class LD, class ST>
+__device__ __forceinline__ void chain_rt(float2* a, float2* b, const float2* tw, const FftLen& f, LD& ld_first,
+                                         ST& st_last) {
+  int Ns = 1, to = 0;
   for (int i = 0; i < f.nst; ++i) {
-    switch (f.radix[i]) {
-      case 2: stage_rt<2, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
-      case 3: stage_rt<3, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
-      case 4: stage_rt<4, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
-      case 5: stage_rt<5, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
-      case 8: stage_rt<8, INV, ROW>(s, tw, tws, f.n, Ns, lp); break;
-      default: break;  // radix 1: identity
-    }
-    Ns *= f.radix[i];
+    const int R = f.radix[i];
+    const bool first = i == 0, last = i == f.nst - 1;
+    float2* src = (i & 1) ? a : b;  // output of iteration i - 1
+    float2* dst = (i & 1) ? b : a;
+    if (first && last) iter_rt_dispatch<INV>(R, tw, to, f.n, Ns, ld_first, st_last);
+    else if (first) iter_rt_dispatch<INV>(R, tw, to, f.n, Ns, ld_first, SmemSt{dst});
+    else if (last) iter_rt_dispatch<INV>(R, tw, to, f.n, Ns, SmemLd{src}, st_last);
+    else iter_rt_dispatch<INV>(R, tw, to, f.n, Ns, SmemLd{src}, SmemSt{dst});
+    __syncthreads();
+    to += Ns * (R > 1 ? R - 1 : 0);
+    Ns *= R;
   }
 }
 
-// Column-layout transform of kT lines (strided passes).
-template <int LC, bool INV>
-__device__ __forceinline__ void fft_cols(float2* s, const float2* tw, const FftLen& f) {
-  if constexpr (LC > 0) fft_ct<LC, 0, INV, false, 0, 1>(s, tw);
-  else fft_rt<INV, false>(s, tw, 1, f, 0);
+template <int LC, bool INV, class LD, class ST>
+__device__ __forceinline__ void transform(float2* a, float2* b, const float2* tw, const FftLen& f, LD& ld_first,
+                                          ST& st_last) {
+  if constexpr (LC > 0) chain_ct<LC, 0, INV>(a, b, tw, ld_first, st_last);
+  else chain_rt<INV>(a, b, tw, f, ld_first, st_last);
 }
 
-// Row pitch of the x-pass tiles: M + 2 complex (even: 16-byte aligned rows).
-__host__ __device__ constexpr int row_pitch(int M) { return M + 2; }
-
-// Row-layout transform of kT lines of length M (x passes; twiddles of 2M).
-template <int MC, bool INV>
-__device__ __forceinline__ void fft_rows(float2* s, const float2* tw, const FftLen& f) {
-  if constexpr (MC > 0) fft_ct<MC, 0, INV, true, row_pitch(MC), 2>(s, tw);
-  else fft_rt<INV, true>(s, tw, 2, f, row_pitch(f.n));
+// Twiddle-table entries of a runtime length.
+__device__ __forceinline__ int tw_len_rt(const FftLen& f) {
+  int off = 0, ns = 1;
+  for (int i = 0; i < f.nst; ++i) {
+    off += ns * (f.radix[i] > 1 ? f.radix[i] - 1 : 0);
+    ns *= f.radix[i];
+  }
+  return off;
 }
 
 // ---------------------------------------------------------------------------
@@ -274,17 +358,96 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
   const int n = valid ? 16 : 0;  // 0 source bytes: the destination is zero-filled
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
-  const int n = valid ? 8 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
-  const int n = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// A strided-axis view: element (o, l, i) at o*so + l*sl + i, l in [0, L),
+// i in [0, inner); a tile is one o and kT consecutive i.
+struct StridedView {
+  int64_t sl, so;
+  int inner;
+  int64_t n_outer;
+};
+
+struct StridedTile {
+  const float2* in;
+  float2* out;
+  int64_t sl;
+  int valid;  // columns of this tile inside [0, inner): 4 or 8 (inner is a multiple of 4)
+  __device__ __forceinline__ float4 operator()(int l, int cp) const {
+    return 2 * cp < valid ? __ldcg(reinterpret_cast<const float4*>(in + (int64_t)l * sl + 2 * cp))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __device__ __forceinline__ void operator()(int l, int cp, float4 v) const {
+    if (2 * cp < valid) *reinterpret_cast<float4*>(out + (int64_t)l * sl + 2 * cp) = v;
+  }
+};
+
+__device__ __forceinline__ StridedTile strided_tile(const float2* in, float2* out, const StridedView& v,
+                                                    int64_t tile) {
+  const int tpo = (v.inner + kT - 1) / kT;
+  const int64_t o = tile / tpo;
+  const int i0 = (int)(tile - o * tpo) * kT;
+  return StridedTile{in + o * v.so + i0, out + o * v.so + i0, v.sl, min(kT, v.inner - i0)};
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+
+// Strided-axis transform (in place allowed: a tile's reads all happen in the
+// first iteration, before the barrier that precedes its writes).
+// Tile of a strided view staged into shared memory (column layout) with
+// 16-byte cp.async copies; columns past the view's end are zero-filled.
+__device__ __forceinline__ void stage_strided_tile(float2* s, const float2* in, const StridedView& v, int L,
+                                                   int64_t tile) {
+  const int tpo = (v.inner + kT - 1) / kT;
+  const int64_t o = tile / tpo;
+  const int i0 = (int)(tile - o * tpo) * kT;
+  const float2* base = in + o * v.so + i0;
+  for (int idx = threadIdx.x; idx < L * kPairs; idx += kThreads) {
+    const int l = idx / kPairs, cp = idx % kPairs;
+    const bool ok = i0 + 2 * cp < v.inner;
+    cp_async16(s + l * kT + 2 * cp, ok ? base + (int64_t)l * v.sl + 2 * cp : in, ok);
+  }
+}
+
+// Strided-axis transform (in place allowed: a tile is read, through the
+// staging copy, before any of its elements is written).  Persistent CTAs
+// stage the next tile with cp.async while the current one is transformed;
+// iteration 0 reads the staged tile, the iterations ping-pong between the
+// work buffer and the staged tile's buffer, and the last one stores to
+// global memory.
+template <int LC, bool INV>
+__global__ void __launch_bounds__(kThreads, LC > 0 ? 2 : 1)
+    strided_kernel(const float2* in, float2* out, StridedView v, FftLen f, const float2* __restrict__ stw) {
+  extern __shared__ float4 smem4[];
+  const int L = LC > 0 ? LC : f.n;
+  float2* p0 = reinterpret_cast<float2*>(smem4);
+  float2* p1 = p0 + L * kT;
+  float2* w = p1 + L * kT;
+  float2* tws = w + L * kT;
+  const int ntw = LC > 0 ? tw_table_len(rplan(LC)) : tw_len_rt(f);
+  for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
+  const int64_t ntiles = v.n_outer * ((v.inner + kT - 1) / kT);
+  int64_t t = blockIdx.x;
+  if (t >= ntiles) return;
+  stage_strided_tile(p0, in, v, L, t);
+  cp_async_commit();
+  for (int it = 0; t < ntiles; ++it) {
+    const int64_t tn = t + gridDim.x;
+    float2* cur = (it & 1) ? p1 : p0;
+    if (tn < ntiles) stage_strided_tile((it & 1) ? p0 : p1, in, v, L, tn);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    StridedTile io = strided_tile(in, out, v, t);
+    SmemLd ld{cur};
+    // iteration 0 writes w, then the chain alternates w <-> cur
+    transform<LC, INV>(w, cur, tws, f, ld, io);
+    t = tn;
+  }
+}
 
 // Kernel spectra for the fused multiply: the octant K^_s[kzf][kyf][kx] with
 // rows padded to the spectrum pitch px (zeros for kx > n[0]/2).  Element
@@ -296,98 +459,31 @@ struct KhatArgs {
   int px, ny, nz, oy;
 };
 
-// A strided-axis view: element (o, l, i) at o*so + l*sl + i, l in [0, L),
-// i in [0, inner); a tile is one o and kT consecutive i.
-struct StridedView {
-  int64_t sl, so;
-  int inner;
-  int64_t n_outer;
-};
-
-__device__ __forceinline__ void load_strided_tile(float2* s, const float2* in, const StridedView& v, int L,
-                                                  int64_t tile) {
-  const int tpo = (v.inner + kT - 1) / kT;
-  const int64_t o = tile / tpo;
-  const int i0 = (int)(tile - o * tpo) * kT;
-  const float2* base = in + o * v.so + i0;
-  for (int idx = threadIdx.x; idx < L * (kT / 2); idx += kThreads) {
-    const int l = idx / (kT / 2), c = (idx % (kT / 2)) * 2;
-    const bool ok = i0 + c < v.inner;
-    cp_async16(s + l * kT + c, ok ? base + (int64_t)l * v.sl + c : in, ok);
-  }
-}
-
-__device__ __forceinline__ void store_strided_tile(const float2* s, float2* out, const StridedView& v, int L,
-                                                   int64_t tile) {
-  const int tpo = (v.inner + kT - 1) / kT;
-  const int64_t o = tile / tpo;
-  const int i0 = (int)(tile - o * tpo) * kT;
-  float2* base = out + o * v.so + i0;
-  for (int idx = threadIdx.x; idx < L * (kT / 2); idx += kThreads) {
-    const int l = idx / (kT / 2), c = (idx % (kT / 2)) * 2;
-    if (i0 + c < v.inner) {
-      const float2 a = s[l * kT + c], b = s[l * kT + c + 1];
-      *reinterpret_cast<float4*>(base + (int64_t)l * v.sl + c) = make_float4(a.x, a.y, b.x, b.y);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// kernels
-
-// Strided-axis transform (in place allowed), persistent with a prefetched
-// second tile buffer.
-template <int LC, bool INV>
-__global__ void __launch_bounds__(kThreads, min_blocks(LC))
-    strided_kernel(const float2* in, float2* out, StridedView v, FftLen f, const float2* __restrict__ tw) {
-  extern __shared__ float4 smem4[];
-  const int L = LC > 0 ? LC : f.n;
-  float2* buf0 = reinterpret_cast<float2*>(smem4);
-  float2* buf1 = buf0 + L * kT;
-  float2* tws = buf1 + L * kT;
-  const int64_t ntiles = v.n_outer * ((v.inner + kT - 1) / kT);
-  int64_t t = blockIdx.x;
-  if (t >= ntiles) return;
-  for (int i = threadIdx.x; i < L; i += kThreads) tws[i] = __ldg(tw + i);
-  load_strided_tile(buf0, in, v, L, t);
-  cp_async_commit();
-  for (int it = 0; t < ntiles; ++it) {
-    const int64_t tn = t + gridDim.x;
-    float2* cur = (it & 1) ? buf1 : buf0;
-    if (tn < ntiles) load_strided_tile((it & 1) ? buf0 : buf1, in, v, L, tn);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    fft_cols<LC, INV>(cur, tws, f);
-    store_strided_tile(cur, out, v, L, t);
-    __syncthreads();
-    t = tn;
-  }
-}
-
-// Inverse z pass of every shell at once: a half-spectrum tile is read once,
-// then for each shell s it is multiplied by K^_s (Eq. 9 in Fourier space),
-// transformed along z and stored to that shell's scratch spectrum
-// out + s * out_stride.  The tile's slab of K^_s (nz/2 + 1 rows of kT
-// values) is fetched with cp.async while the previous shell is transformed.
-// khat == nullptr: one transform, factor 1.
+// Inverse z pass of every shell at once: a half-spectrum tile is staged in
+// shared memory once, then for each shell s the first iteration reads it
+// multiplied by K^_s (Eq. 9 in Fourier space) and the last writes the
+// z-transformed product to that shell's scratch spectrum out + s * out_stride.
+// The tile's slab of K^_s (nz/2 + 1 rows of kT values) is fetched with
+// cp.async while the previous shell finishes.  khat == nullptr: one
+// transform, factor 1.
 template <int LC>
-__global__ void __launch_bounds__(kThreads, min_blocks(LC))
+__global__ void __launch_bounds__(kThreads, 2)
     zmulti_kernel(const float2* in, float2* out, int64_t out_stride, int nshells, StridedView v, FftLen f,
-                  const float2* __restrict__ tw, KhatArgs K) {
+                  const float2* __restrict__ stw, KhatArgs K) {
   extern __shared__ float4 smem4[];
   const int L = LC > 0 ? LC : f.n;
   const int OZ = L / 2 + 1;
   float2* pristine = reinterpret_cast<float2*>(smem4);
-  float2* work = pristine + L * kT;
-  float2* tws = work + L * kT;
-  float* slab0 = reinterpret_cast<float*>(tws + L);
-  float* slab1 = slab0 + OZ * kT;
+  float2* a = pristine + L * kT;
+  float2* b = a + L * kT;
+  float2* tws = b + L * kT;
+  const int ntw = LC > 0 ? tw_table_len(rplan(LC)) : tw_len_rt(f);
+  float* slab = reinterpret_cast<float*>(tws + ((ntw + 1) & ~1));
+  for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
   const int64_t ntiles = (v.inner + kT - 1) / kT;
-  for (int i = threadIdx.x; i < L; i += kThreads) tws[i] = __ldg(tw + i);
   // two halves of 4 columns per tile: px is a multiple of 4 and i0 of 8, so
   // each half lies in one ky row of the spectrum
-  auto load_slab = [&](float* dst, int s, int64_t tile) {
+  auto load_slab = [&](int s, int64_t tile) {
     const float* kh = K.khat + (int64_t)s * K.shell_stride;
     for (int idx = threadIdx.x; idx < 2 * OZ; idx += kThreads) {
       const int kzf = idx >> 1, h = idx & 1;
@@ -395,122 +491,184 @@ __global__ void __launch_bounds__(kThreads, min_blocks(LC))
       const bool ok = i < v.inner;
       const int ky = i / K.px, kx = i - (i / K.px) * K.px;
       const int kyf = min(ky, K.ny - ky);
-      cp_async16(dst + kzf * kT + 4 * h, ok ? kh + ((int64_t)kzf * K.oy + kyf) * K.px + kx : K.khat, ok);
+      cp_async16(slab + kzf * kT + 4 * h, ok ? kh + ((int64_t)kzf * K.oy + kyf) * K.px + kx : K.khat, ok);
     }
   };
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    load_strided_tile(pristine, in, v, L, t);
-    if (K.khat) load_slab(slab0, 0, t);
+    const int i0 = (int)t * kT;
+    const int valid = min(kT, v.inner - i0);
+    for (int idx = threadIdx.x; idx < L * (kT / 2); idx += kThreads) {
+      const int l = idx / (kT / 2), c = (idx % (kT / 2)) * 2;
+      const bool ok = c < valid;
+      cp_async16(pristine + l * kT + c, ok ? in + (int64_t)l * v.sl + i0 + c : in, ok);
+    }
+    if (K.khat) load_slab(0, t);
     cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
     for (int s = 0; s < nshells; ++s) {
-      const float* slab = (s & 1) ? slab1 : slab0;
-      if (K.khat && s + 1 < nshells) load_slab((s & 1) ? slab0 : slab1, s + 1, t);
-      cp_async_commit();
-      cp_async_wait<1>();
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < L * kT; idx += kThreads) {
-        const int l = idx / kT, c = idx % kT;
-        const float m = K.khat ? slab[min(l, L - l) * kT + c] : 1.0f;
-        work[idx] = cscale(pristine[idx], m);
+      const bool mul = K.khat != nullptr;
+      auto ld = [&](int l, int cp) {
+        const float4 x = reinterpret_cast<const float4*>(pristine)[l * kPairs + cp];
+        if (!mul) return x;
+        const float2 m = reinterpret_cast<const float2*>(slab)[min(l, L - l) * kPairs + cp];
+        return make_float4(x.x * m.x, x.y * m.x, x.z * m.y, x.w * m.y);
+      };
+      StridedTile st{nullptr, out + (int64_t)s * out_stride + i0, v.sl, valid};
+      if constexpr (LC > 0) {
+        constexpr RPlan P = rplan(LC);
+        static_assert(P.nst >= 2, "the multi-shell z pass needs two or more iterations");
+        iter_ct<LC, 0, true>(tws, ld, SmemSt{a});
+        __syncthreads();
+        // the slab of shell s has been consumed: fetch the next shell's
+        if (mul && s + 1 < nshells) load_slab(s + 1, t);
+        cp_async_commit();
+        chain_ct<LC, 1, true>(b, a, tws, ld, st);
+      } else {
+        chain_rt<true>(a, b, tws, f, ld, st);
+        if (mul && s + 1 < nshells) load_slab(s + 1, t);
+        cp_async_commit();
       }
-      __syncthreads();
-      fft_cols<LC, true>(work, tws, f);
-      store_strided_tile(work, out + (int64_t)s * out_stride, v, L, t);
+      cp_async_wait<0>();
       __syncthreads();
     }
   }
 }
+
+// x-pass tiles: kT rows of one axis line each.  Loads, the even/odd
+// (un)packing and stores map consecutive threads to consecutive rows first.
 
 // Forward x pass: real rows of length nx = 2M -> half-spectrum rows (pitch
 // px).  z[m] = x[2m] + i x[2m+1], Z = DFT_M(z), then X[k] = E[k] +
 // e^{-2 pi i k/nx} O[k], E = (Z[k] + conj Z[M-k]) / 2,
-// O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M.  Tiles of kT rows in row layout.
+// O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M.  The transform's first iteration
+// reads the real rows from global memory; its output stays in shared memory
+// for the split.
 template <int MC>
 __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     x_r2c_kernel(const float* __restrict__ in, float2* __restrict__ out, int nx, int px, int64_t rows, FftLen f,
+                 const float2* __restrict__ stw, const float2* __restrict__ tw) {
+  extern __shared__ float4 smem4[];
+  const int M = MC > 0 ? MC : nx / 2;
+  const int NX = 2 * M;
+  float2* a = reinterpret_cast<float2*>(smem4);
+  float2* b = a + M * kT;
+  float2* tws = b + M * kT;
+  const int ntw = MC > 0 ? tw_table_len(rplan(MC)) : tw_len_rt(f);
+  float2* twn = tws + ntw;
+  for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
+  for (int i = threadIdx.x; i <= M; i += kThreads) twn[i] = __ldg(tw + i);
+  __syncthreads();
+  const int64_t ntiles = (rows + kT - 1) / kT;
+  auto rows_ld = [&](int64_t tile) {
+    const int64_t r0 = tile * kT;
+    const int valid = (int)(rows - r0 < kT ? rows - r0 : kT);
+    const float* rin = in + r0 * NX;
+    return [=](int m, int cp) {
+      const int c = 2 * cp;
+      const float2 z0 = c < valid ? __ldg(reinterpret_cast<const float2*>(rin + (int64_t)c * NX) + m)
+                                  : make_float2(0.f, 0.f);
+      const float2 z1 = c + 1 < valid ? __ldg(reinterpret_cast<const float2*>(rin + (int64_t)(c + 1) * NX) + m)
+                                      : make_float2(0.f, 0.f);
+      return cat4(z0, z1);
+    };
+  };
+  // the transform's output buffer: not the one its last iteration reads
+  float2* res = nullptr;
+  if constexpr (MC > 0) res = (rplan(MC).nst % 2 == 1) ? a : b;
+  else res = (f.nst % 2 == 1) ? a : b;
+  auto split = [&](int64_t t) {
+    const int64_t r0 = t * kT;
+    const int valid = (int)(rows - r0 < kT ? rows - r0 : kT);
+    const float2* s = res;
+    for (int idx = threadIdx.x; idx < kT * px; idx += kThreads) {
+      const int c = idx % kT, k = idx / kT;
+      if (c >= valid) continue;
+      float2 X = make_float2(0.f, 0.f);
+      if (k <= M) {
+        const float2 zk = s[(k == M ? 0 : k) * kT + c];
+        const float2 zc = cconj(s[(k == 0 ? 0 : M - k) * kT + c]);
+        const float2 E = cscale(cadd(zk, zc), 0.5f);
+        const float2 O = cscale(cmul_mi<false>(csub(zk, zc)), 0.5f);
+        X = cadd(E, cmul(twn[k], O));
+      }
+      out[(r0 + c) * px + k] = X;
+    }
+    __syncthreads();
+  };
+  if constexpr (MC > 0 && rplan(MC).nst >= 2) {
+    float4 x[Iter0<MC>::NB][Iter0<MC>::R];
+    int64_t t = blockIdx.x;
+    if (t < ntiles) {
+      auto ld = rows_ld(t);
+      gather0<MC>(x, ld);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+      butterfly0<MC, false>(x, SmemSt{a});
+      __syncthreads();
+      const int64_t tn = t + gridDim.x;
+      if (tn < ntiles) {
+        auto ld = rows_ld(tn);
+        gather0<MC>(x, ld);
+      }
+      SmemSt st{res};
+      auto unused = rows_ld(t);
+      chain_ct<MC, 1, false>(b, a, tws, unused, st);
+      split(t);
+    }
+  } else {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      auto ld = rows_ld(t);
+      SmemSt st{res};
+      transform<MC, false>(a, b, tws, f, ld, st);
+      split(t);
+    }
+  }
+}
+
+struct RealRowsOut {
+  float* out;
+  int nx;
+  int valid;
+  __device__ __forceinline__ void operator()(int m, int cp, float4 v) const {
+    const int c = 2 * cp;
+    if (c < valid) *reinterpret_cast<float2*>(out + (int64_t)c * nx + 2 * m) = lo2(v);
+    if (c + 1 < valid) *reinterpret_cast<float2*>(out + (int64_t)(c + 1) * nx + 2 * m) = hi2(v);
+  }
+};
+
+// Inverse x pass: half-spectrum rows -> real rows.  Persistent CTAs stage
+// the next tile's rows (X[0..M], row pitch M + 2) with 16-byte cp.async
+// copies while the current tile is unpacked into Z (pairs (k, M-k)),
+// transformed (z = IDFT_M(Z), unnormalised) and written by the last
+// iteration as x[2m] = Re z[m], x[2m+1] = Im z[m].  Input rows are contiguous
+// (pitch px); output row r goes to
+// out + (r / rows_per_shell) * out_shell_stride + (r % rows_per_shell) * nx.
+__host__ __device__ constexpr int stage_pitch(int M) { return M + 2; }
+
+template <int MC>
+__global__ void __launch_bounds__(kThreads, min_blocks(MC))
+    x_c2r_kernel(const float2* __restrict__ in, float* __restrict__ out, int nx, int px, int64_t rows,
+                 int64_t rows_per_shell, int64_t out_shell_stride, FftLen f, const float2* __restrict__ stw,
                  const float2* __restrict__ tw) {
   extern __shared__ float4 smem4[];
   const int M = MC > 0 ? MC : nx / 2;
   const int NX = 2 * M;
-  const int LP = row_pitch(M);
-  float2* buf0 = reinterpret_cast<float2*>(smem4);
-  float2* buf1 = buf0 + kT * LP;
-  float2* tws = buf1 + kT * LP;
+  const int LP = stage_pitch(M);
+  float2* s0 = reinterpret_cast<float2*>(smem4);
+  float2* s1 = s0 + kT * LP;
+  float2* u = s1 + kT * LP;
+  float2* w = u + (M + 1) * kT;
+  float2* tws = w + (M + 1) * kT;
+  const int ntw = MC > 0 ? tw_table_len(rplan(MC)) : tw_len_rt(f);
+  float2* twn = tws + ntw;
+  for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
+  for (int i = threadIdx.x; i <= M; i += kThreads) twn[i] = __ldg(tw + i);
   const int64_t ntiles = (rows + kT - 1) / kT;
-  int64_t t = blockIdx.x;
-  if (t >= ntiles) return;
-  for (int i = threadIdx.x; i < NX; i += kThreads) tws[i] = __ldg(tw + i);
-  auto load = [&](float2* s, int64_t tile) {
-    const int64_t r0 = tile * kT;
-    if (M % 2 == 0) {  // rows 16-byte aligned: two z values per copy
-      const int np = M / 2;
-      for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
-        const int c = idx / np, m = 2 * (idx - c * np);
-        const bool ok = r0 + c < rows;
-        cp_async16(s + c * LP + m, ok ? (const void*)(in + (r0 + c) * NX + 2 * m) : (const void*)in, ok);
-      }
-    } else {
-      for (int idx = threadIdx.x; idx < kT * M; idx += kThreads) {
-        const int c = idx / M, m = idx - c * M;
-        const bool ok = r0 + c < rows;
-        cp_async8(s + c * LP + m, ok ? (const void*)(in + (r0 + c) * NX + 2 * m) : (const void*)in, ok);
-      }
-    }
-  };
-  load(buf0, t);
-  cp_async_commit();
-  for (int it = 0; t < ntiles; ++it) {
-    const int64_t tn = t + gridDim.x;
-    float2* s = (it & 1) ? buf1 : buf0;
-    if (tn < ntiles) load((it & 1) ? buf0 : buf1, tn);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    fft_rows<MC, false>(s, tws, f);
-    const int64_t r0 = t * kT;
-    for (int idx = threadIdx.x; idx < kT * px; idx += kThreads) {
-      const int c = idx / px, k = idx - c * px;
-      const int64_t row = r0 + c;
-      if (row >= rows) continue;
-      float2 X = make_float2(0.f, 0.f);
-      if (k <= M) {
-        const float2 zk = s[c * LP + (k == M ? 0 : k)];
-        const float2 zc = cconj(s[c * LP + (k == 0 ? 0 : M - k)]);
-        const float2 E = cscale(cadd(zk, zc), 0.5f);
-        const float2 O = cscale(cmul_mi<false>(csub(zk, zc)), 0.5f);
-        X = cadd(E, cmul(tws[k], O));
-      }
-      out[row * px + k] = X;
-    }
-    __syncthreads();
-    t = tn;
-  }
-}
-
-// Inverse x pass: half-spectrum rows -> real rows.  With w^-k =
-// e^{+2 pi i k/nx}: Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k]),
-// z = IDFT_M(Z) (unnormalised), x[2m] = Re z[m], x[2m+1] = Im z[m].  Input
-// rows are contiguous (pitch px); output row r goes to
-// out + (r / rows_per_shell) * out_shell_stride + (r % rows_per_shell) * nx.
-template <int MC>
-__global__ void __launch_bounds__(kThreads, min_blocks(MC))
-    x_c2r_kernel(const float2* __restrict__ in, float* __restrict__ out, int nx, int px, int64_t rows,
-                 int64_t rows_per_shell, int64_t out_shell_stride, FftLen f, const float2* __restrict__ tw) {
-  extern __shared__ float4 smem4[];
-  const int M = MC > 0 ? MC : nx / 2;
-  const int NX = 2 * M;
-  const int LP = row_pitch(M);
-  float2* buf0 = reinterpret_cast<float2*>(smem4);
-  float2* buf1 = buf0 + kT * LP;
-  float2* tws = buf1 + kT * LP;
-  const int64_t ntiles = (rows + kT - 1) / kT;
-  int64_t t = blockIdx.x;
-  if (t >= ntiles) return;
-  for (int i = threadIdx.x; i < NX; i += kThreads) tws[i] = __ldg(tw + i);
   // X[0..M] as pairs (k, k+1), k even: M/2 + 1 copies per row; for even M
   // the last pair also reads padding column M + 1 (< px)
   const int np = M / 2 + 1;
-  auto load = [&](float2* s, int64_t tile) {
+  auto stage = [&](float2* s, int64_t tile) {
     const int64_t r0 = tile * kT;
     for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
       const int c = idx / np, k = 2 * (idx - c * np);
@@ -518,74 +676,73 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
       cp_async16(s + c * LP + k, ok ? (const void*)(in + (r0 + c) * px + k) : (const void*)in, ok);
     }
   };
-  load(buf0, t);
+  int64_t t = blockIdx.x;
+  if (t >= ntiles) return;
+  stage(s0, t);
   cp_async_commit();
   const int half = M / 2 + 1;
   for (int it = 0; t < ntiles; ++it) {
     const int64_t tn = t + gridDim.x;
-    float2* s = (it & 1) ? buf1 : buf0;
-    if (tn < ntiles) load((it & 1) ? buf0 : buf1, tn);
+    const float2* sc = (it & 1) ? s1 : s0;
+    if (tn < ntiles) stage((it & 1) ? s0 : s1, tn);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    for (int idx = threadIdx.x; idx < kT * half; idx += kThreads) {
-      const int c = idx / half, k = idx - c * half;
-      const float2 a = s[c * LP + k];
-      const float2 b = s[c * LP + M - k];
-      const float2 ca = cconj(a), cb = cconj(b);
-      const float2 zk = cadd(cadd(a, cb), cmul_mi<true>(cmul(cconj(tws[k]), csub(a, cb))));
-      s[c * LP + k] = zk;
-      if (k != 0 && 2 * k != M) {
-        const float2 zm = cadd(cadd(b, ca), cmul_mi<true>(cmul(cconj(tws[M - k]), csub(b, ca))));
-        s[c * LP + M - k] = zm;
-      }
-    }
-    __syncthreads();
-    fft_rows<MC, true>(s, tws, f);
     const int64_t r0 = t * kT;
-    if (M % 2 == 0) {  // two z values (four reals) per 16-byte store
-      const int nq = M / 2;
-      for (int idx = threadIdx.x; idx < kT * nq; idx += kThreads) {
-        const int c = idx / nq, m = 2 * (idx - c * nq);
-        const int64_t row = r0 + c;
-        if (row < rows) {
-          const int64_t sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
-          const float2 a = s[c * LP + m], b = s[c * LP + m + 1];
-          *reinterpret_cast<float4*>(out + sh * out_shell_stride + rr * NX + 2 * m) = make_float4(a.x, a.y, b.x, b.y);
-        }
-      }
-    } else {
-      for (int idx = threadIdx.x; idx < kT * M; idx += kThreads) {
-        const int c = idx / M, m = idx - c * M;
-        const int64_t row = r0 + c;
-        if (row < rows) {
-          const int64_t sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
-          *reinterpret_cast<float2*>(out + sh * out_shell_stride + rr * NX + 2 * m) = s[c * LP + m];
-        }
-      }
+    const int valid = (int)(rows - r0 < kT ? rows - r0 : kT);
+    // unpack: Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k])
+    for (int idx = threadIdx.x; idx < kT * half; idx += kThreads) {
+      const int c = idx % kT, k = idx / kT;
+      const float2 a = sc[c * LP + k], b = sc[c * LP + M - k];
+      const float2 ca = cconj(a), cb = cconj(b);
+      u[k * kT + c] = cadd(cadd(a, cb), cmul_mi<true>(cmul(cconj(twn[k]), csub(a, cb))));
+      if (k != 0 && 2 * k != M)
+        u[(M - k) * kT + c] = cadd(cadd(b, ca), cmul_mi<true>(cmul(cconj(twn[M - k]), csub(b, ca))));
     }
     __syncthreads();
+    SmemLd ld{u};
+    // rows of this tile may belong to two shells: split the output per row
+    const int64_t sh0 = r0 / rows_per_shell;
+    const int64_t rr0 = r0 - sh0 * rows_per_shell;
+    if (rr0 + valid <= rows_per_shell) {
+      RealRowsOut st{out + sh0 * out_shell_stride + rr0 * NX, NX, valid};
+      transform<MC, true>(w, u, tws, f, ld, st);
+    } else {
+      auto st = [&](int m, int cp, float4 v) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * cp + h;
+          if (c >= valid) continue;
+          const int64_t row = r0 + c, sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
+          *reinterpret_cast<float2*>(out + sh * out_shell_stride + rr * NX + 2 * m) = h ? hi2(v) : lo2(v);
+        }
+      };
+      transform<MC, true>(w, u, tws, f, ld, st);
+    }
     t = tn;
   }
 }
 
 // shared-memory bytes of each kernel
-inline size_t strided_smem(int L) { return (size_t)L * (2 * kT + 1) * sizeof(float2); }
+inline size_t strided_smem(int L) { return ((size_t)3 * L * kT + L) * sizeof(float2); }
 inline size_t zmulti_smem(int L) {
-  return (size_t)L * (2 * kT + 1) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * kT * sizeof(float);
+  return ((size_t)3 * L * kT + L + 2) * sizeof(float2) + (size_t)(L / 2 + 1) * kT * sizeof(float);
 }
-inline size_t xpass_smem(int nx) { return ((size_t)2 * kT * row_pitch(nx / 2) + nx) * sizeof(float2); }
+inline size_t xpass_smem(int nx) {
+  return ((size_t)2 * kT * stage_pitch(nx / 2) + (size_t)2 * kT * (nx / 2 + 1) + nx + 2) * sizeof(float2);
+}
 
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* tw, int sm_count, cudaStream_t st);
+                    const float2* stw, int sm_count, cudaStream_t st);
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
-                   const FftLen& f, const float2* tw, const KhatArgs& K, int sm_count, cudaStream_t st);
+                   const FftLen& f, const float2* stw, const KhatArgs& K, int sm_count, cudaStream_t st);
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
-                  const float2* tw, int sm_count, cudaStream_t st);
+                  const float2* stw, const float2* tw, int sm_count, cudaStream_t st);
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,
-                  int64_t out_shell_stride, const FftLen& f, const float2* tw, int sm_count, cudaStream_t st);
+                  int64_t out_shell_stride, const FftLen& f, const float2* stw, const float2* tw, int sm_count,
+                  cudaStream_t st);
 
 // Persistent grid: the resident CTAs of every SM, at most one CTA per tile.
 template <typename K>

@@ -135,6 +135,7 @@ struct Plan {
   int64_t staging_pts = 0;  // points per staging slot
   float* thr[3] = {nullptr, nullptr, nullptr};   // cell-edge thresholds, n+1 each
   float2* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i t / n_a}, n_a each
+  float2* stw[3] = {nullptr, nullptr, nullptr};  // per-iteration twiddles of the y, z and half-x lengths
   DevState* dstate = nullptr;
   double* den_raw = nullptr;   // packed per order (multiset order)
   double* sums = nullptr;      // packed per order: num of the last compute

@@ -280,6 +280,14 @@ WORKLOADS: Dict[str, dict] = {
         data=("ns_box", dict(seed=8, n_parents=2_500, n_children=20, sigma=8.0)),
         randoms=("uniform_box", dict(seed=9, n=2_000_000)),
     ),
+    # Profiler case with the survey grid's transform lengths: periodic 512^3 of
+    # 8 h^-1 Mpc, 2 shells (about 5 GB on the device), small catalogs.
+    "profile512": dict(
+        grid=GridSpec((512, 512, 512), (0.0, 0.0, 0.0), 8.0, True),
+        shells=(40.0, 80.0), width=8.0, orders=(2, 3),
+        data=("ns_box", dict(seed=10, n_parents=5_000, n_children=20, sigma=8.0)),
+        randoms=("uniform_box", dict(seed=11, n=4_000_000)),
+    ),
 }
 
 

@@ -528,11 +528,23 @@ def check_guard_band(o) -> bool:
     return bool(ok and not o.guard_band_ok([G], m))
 
 
+def check_pair_sums_fft(o) -> bool:
+    """The autocorrelation route to the order-2 sums equals the brute-force
+    ordered pair counts of cell-centred points."""
+    g = PGRID
+    cells, cat = _centre_points(g, 45, 5)
+    D, _ = o.grid_counts(cat.x, cat.y, cat.z, g)
+    d2 = _sep2(cells, cells, g.n)
+    got = o.pair_sums_fft(D.astype(np.float64), [o.shell_offsets(s, w, g.cell) for s, w in PSHELLS])
+    want = [int(_in_shell(d2, s, w, g.cell).sum()) for s, w in PSHELLS]
+    return bool(np.allclose(got, want, rtol=0, atol=1e-6))
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
     check_product_sums_high_order, check_signed_pairs, check_delta_response, check_fft_engine,
     check_constant_field_den, check_relabel_shells, check_translation, check_linearity,
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
-    check_multisets, check_guard_band,
+    check_multisets, check_guard_band, check_pair_sums_fft,
 ]

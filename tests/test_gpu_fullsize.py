@@ -1,0 +1,98 @@
+"""The survey workload at its full size (512^3 cells of 8 h^-1 Mpc, 800k
+galaxies, 40M randoms, 16 shells, orders 2 and 3), in the launch
+configuration bench.py times, against what the oracle can compute at this
+size:
+
+* the count grids, bit for bit;
+* the order-2 numerators and denominators exactly, through the oracle's
+  autocorrelation route (one FP64 FFT pair per field);
+* W_s at sampled cells, one by one by direct summation;
+* the random bank's sum rule sum_r (R***K_s) = (sum_r R) |O_s|;
+* symmetry and finiteness of the order-3 tensors.
+"""
+import numpy as np
+import pytest
+
+import oracle.conker_oracle as O
+from synth import workload
+from tests.gpu_util import cuda_torch, dev_cat, normwise, plan_for
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def run():
+    torch = cuda_torch()
+    w = workload("survey512")
+    g = w["grid"]
+    plan = plan_for(w, max_order=3)
+    plan.set_randoms(*dev_cat(torch, w["randoms"]))
+    bank_r = {s: plan.bank(s).cpu().numpy() for s in (0, 7, 15)}
+    res = plan.compute(*dev_cat(torch, w["data"]), orders=(2, 3), out="host")
+    D, R = plan.grids()
+    out = dict(w=w, g=g, plan=plan, res=res, bank_r=bank_r, D=D.cpu().numpy().astype(np.uint32),
+               R=R.cpu().numpy().astype(np.uint32), N=plan.field(0).cpu().numpy(),
+               W={s: plan.bank(s).cpu().numpy() for s in (0, 7, 15)})
+    yield out
+    plan.close()
+
+
+def test_counts_exact(run):
+    w, g = run["w"], run["g"]
+    D, dd = O.grid_counts(w["data"].x, w["data"].y, w["data"].z, g)
+    R, dr = O.grid_counts(w["randoms"].x, w["randoms"].y, w["randoms"].z, g)
+    assert np.array_equal(run["D"], D)
+    assert np.array_equal(run["R"], R)
+    assert run["res"]["dropped"].tolist() == [dd, dr]
+
+
+def test_order2_exact_route(run):
+    w, g = run["w"], run["g"]
+    alpha, N, Rt = O.density_fields(run["D"], run["R"])
+    offs = [O.shell_offsets(s, w["width"], g.cell) for s in w["shells"]]
+    num = O.pair_sums_fft(N, offs)
+    den = O.pair_sums_fft(Rt, offs)
+    # scale of the terms: sum_r |N| (|N| *** K_s) bounds sum_r |N W_s|
+    anum = O.pair_sums_fft(np.abs(N), offs)
+    aden = den
+    got_num = run["res"]["num"][2].numpy()
+    got_den = run["res"]["den"][2].numpy()
+    assert normwise(got_num, num, anum) <= TOL
+    assert normwise(got_den, den, aden) <= TOL
+    xi = run["res"]["xi"][2].numpy()
+    assert np.all(np.isfinite(xi))
+    assert np.allclose(xi, num / den, rtol=0, atol=TOL * np.max(anum / den))
+
+
+def test_sampled_w(run):
+    w, g = run["w"], run["g"]
+    alpha, N, _ = O.density_fields(run["D"], run["R"])
+    assert np.abs(run["N"] - N).max() <= 1e-6 * np.abs(N).max()
+    occ = np.argwhere(run["R"] > 0)
+    rng = np.random.default_rng(9)
+    pick = occ[rng.integers(0, occ.shape[0], 24)]
+    cells = pick[:, ::-1]  # (iz, iy, ix) -> (ix, iy, iz)
+    for s, Ws in run["W"].items():
+        offs = O.shell_offsets(w["shells"][s], w["width"], g.cell)
+        want = O.w_at_cells(N, offs, cells, periodic=False)
+        scale = O.w_at_cells(np.abs(N), offs, cells, periodic=False)
+        got = Ws[pick[:, 0], pick[:, 1], pick[:, 2]]
+        assert np.all(np.abs(got - want) <= TOL * np.maximum(scale, 1.0)), f"shell {s}"
+
+
+def test_random_bank_sum_rule(run):
+    w, g = run["w"], run["g"]
+    total = float(run["R"].sum(dtype=np.float64))
+    for s, B in run["bank_r"].items():
+        size = O.shell_offsets(w["shells"][s], w["width"], g.cell).shape[0]
+        assert abs(float(B.sum(dtype=np.float64)) - total * size) <= 1e-5 * total * size
+
+
+def test_order3_structure(run):
+    for key in ("num", "den", "xi"):
+        T = run["res"][key][3].numpy()
+        assert np.all(np.isfinite(T))
+        assert np.array_equal(T, T.T)
+    assert np.all(run["res"]["den"][3].numpy() > 0)
