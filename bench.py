@@ -270,7 +270,7 @@ def run_gb300(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": dv["bytes"] / dv["launches"],
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
-    fft_names = [k for k in stages if k.startswith("fft_")]
+    fft_names = [k for k in stages if k.startswith("fft_") or k == "x_c2r_contract"]
     fft_bytes = sum(stages[k]["bytes"] for k in fft_names)
     fft_ms = sum(stages[k]["ms"] for k in fft_names)
 

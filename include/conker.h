@@ -102,6 +102,8 @@ typedef struct ck_plan_info {
   int64_t n_multisets[CK_MAX_ORDER + 1]; /* C(N_s + n - 2, n - 1) for n = 2..5     */
   size_t workspace_bytes;
   int64_t bank_stride;             /* floats between shells in the W / B bank   */
+  int32_t fused;                   /* 1: the last inverse FFT pass and the sums
+                                      run as one kernel and no bank is kept     */
 } ck_plan_info;
 
 /* Outputs of ck_compute.  For order n (index n = 2..5), xi[n], num[n] and
@@ -168,8 +170,12 @@ ck_status ck_get_grids(ck_plan* plan, uint32_t* d_counts, uint32_t* r_counts, vo
  * overwrites it (float [N_c], device or host). */
 ck_status ck_get_field(ck_plan* plan, int32_t which, float* out, void* stream);
 
-/* Copy shell `shell` of the convolution bank last produced: W_s after
- * ck_compute, R***K_s after ck_set_randoms (float [N_c], device or host). */
+/* Copy shell `shell` of the convolution of the field whose spectrum is
+ * resident: W_s = N***K_s after ck_compute, R***K_s after ck_set_randoms
+ * (float [N_c], device or host).  Plans with FP32 sums, at most 16 shells and
+ * max_order <= 3 fuse the last inverse pass with the sums and keep no bank;
+ * for them this call recomputes the shell from the resident spectrum (one
+ * inverse transform on the stream, overwriting internal scratch only). */
 ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream);
 
 /* Copy the octant of K^_s = DFT(K_s) / N_c: float
@@ -221,7 +227,10 @@ ck_status ck_contract_static(const float* w0, const float* bank, int64_t bank_st
  * algorithmic bytes that launch must move (inputs read once + outputs written
  * once).  ck_profile_enable resets the accumulators; ck_profile_read
  * synchronises each recorded event and returns the totals. */
-#define CK_STAGES 12
+/* Stages 0..12: grid_points, prepare_field, fft_x_r2c, fft_y_fwd, fft_z_fwd,
+ * fft_z_inv_mul, fft_y_inv, fft_x_c2r, contract, reduce, finalize,
+ * x_c2r_contract (the inverse x pass fused with the order-2/3 sums), other. */
+#define CK_STAGES 13
 typedef struct ck_stage_times {
   double ms[CK_STAGES];       /* summed event time of the stage's launches   */
   int64_t launches[CK_STAGES];

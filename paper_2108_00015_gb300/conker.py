@@ -53,10 +53,11 @@ class _Info(ctypes.Structure):
     _fields_ = [("n_cells", ctypes.c_int64), ("spec_pitch", ctypes.c_int32), ("n_shells", ctypes.c_int32),
                 ("max_order", ctypes.c_int32), ("max_offset", ctypes.c_int32 * 3),
                 ("shell_size", ctypes.c_int64 * CK_MAX_SHELLS), ("n_multisets", ctypes.c_int64 * (CK_MAX_ORDER + 1)),
-                ("workspace_bytes", ctypes.c_size_t), ("bank_stride", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_size_t), ("bank_stride", ctypes.c_int64),
+                ("fused", ctypes.c_int32)]
 
 
-CK_STAGES = 12
+CK_STAGES = 13
 
 
 class _StageTimes(ctypes.Structure):
@@ -216,6 +217,7 @@ class Plan:
         self.n_multisets = {k: int(info.n_multisets[k]) for k in range(2, self.max_order + 1)}
         self.workspace_bytes = int(info.workspace_bytes)
         self.bank_stride = int(info.bank_stride)
+        self.fused = bool(info.fused)
         self.shape = (int(n[2]), int(n[1]), int(n[0]))
 
     def close(self):

@@ -40,7 +40,7 @@ namespace {
 constexpr size_t kProfPool = 16384;
 const char* kStageNames[CK_STAGES] = {"grid_points", "prepare_field", "fft_x_r2c", "fft_y_fwd",
                                       "fft_z_fwd", "fft_z_inv_mul", "fft_y_inv", "fft_x_c2r",
-                                      "contract", "reduce", "finalize", "other"};
+                                      "contract", "reduce", "finalize", "x_c2r_contract", "other"};
 
 void prof_collect(ck::Plan& p) {
   ck::Profiler& f = p.prof;
@@ -111,7 +111,7 @@ ck_status carve(Plan& p) {
   p.spec = reinterpret_cast<float2*>(take((size_t)p.spec_elems * 8));
   p.tmp = reinterpret_cast<float2*>(take((size_t)p.ns * p.spec_elems * 8));
   p.khat = reinterpret_cast<float*>(take((size_t)p.ns * p.khat_stride * 4));
-  p.bank = reinterpret_cast<float*>(take(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8)));
+  p.bank = reinterpret_cast<float*>(take(std::max((size_t)p.bank_fields * p.field_stride * 4, khat_scratch_doubles(p) * 8)));
   p.partials = reinterpret_cast<double*>(take(p.partials_cap * 8));
   p.staging = reinterpret_cast<float*>(take((size_t)2 * 3 * p.staging_pts * 4));
   for (int a = 0; a < 3; ++a) p.thr[a] = reinterpret_cast<float*>(take((size_t)(p.grid.n[a] + 1) * 4));
@@ -230,10 +230,15 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
   return cuda_status(cudaGetLastError());
 }
 
-// Convolve the current field with every shell kernel into the bank.
-void convolve_bank(Plan& p, cudaStream_t st) {
+// Convolve the current field with every shell kernel (Eqs. 9-10) and form
+// the product sums of the orders in `mask` (Eq. 11) into `sums`: through the
+// bank and the contraction kernels, or in one fused pass (fused plans, which
+// always form every order up to max_order).
+ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st) {
   launch_fft_forward(p, p.field, p.spec, st);
+  if (p.fused) return launch_convolve_contract(p, p.field, sums, st);
   launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
+  return launch_contract(p, mask, p.field, p.bank, p.field_stride, sums, st);
 }
 
 int full_mask(const Plan& p) {
@@ -358,6 +363,7 @@ ck_status ck_plan_get_info(const ck_plan* plan, ck_plan_info* info) {
   for (int n = 0; n <= CK_MAX_ORDER; ++n) info->n_multisets[n] = p->n_multisets[n];
   info->workspace_bytes = p->ws_bytes;
   info->bank_stride = p->field_stride;
+  info->fused = p->fused ? 1 : 0;
   return CK_OK;
 }
 
@@ -370,9 +376,9 @@ ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const fl
   p.have_randoms = false;
   CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st));
   launch_prepare_randoms(p, st);
-  convolve_bank(p, st);
+  p.bank_holds = -1;
+  CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st));
   p.bank_holds = 1;
-  CK_TRY_S(launch_contract(p, full_mask(p), p.field, p.bank, p.field_stride, p.den_raw, st));
   CK_TRY(cudaGetLastError());
   p.have_randoms = true;
   return CK_OK;
@@ -389,9 +395,9 @@ ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float*
   cudaStream_t st = S(stream);
   CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st));
   launch_prepare_data(p, st);
-  convolve_bank(p, st);
+  p.bank_holds = -1;
+  CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st));
   p.bank_holds = 0;
-  CK_TRY_S(launch_contract(p, order_mask, p.field, p.bank, p.field_stride, p.sums, st));
   launch_finalize(p, order_mask, st);
   CK_TRY(cudaGetLastError());
   bool host_seen = false;
@@ -482,7 +488,13 @@ ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream) {
   if (shell < 0 || shell >= p.ns || p.bank_holds < 0) return CK_ERR_ARG;
   cudaStream_t st = S(stream);
   bool host = false;
-  CK_TRY_S(copy_out(out, p.bank + (size_t)shell * p.field_stride, (size_t)p.nc * 4, st, &host));
+  const float* src = p.bank + (size_t)shell * p.field_stride;
+  if (p.fused) {  // recompute W_s from the resident spectrum
+    launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, p.bank, p.field_stride, st);
+    CK_TRY(cudaGetLastError());
+    src = p.bank;
+  }
+  CK_TRY_S(copy_out(out, src, (size_t)p.nc * 4, st, &host));
   if (host) CK_TRY(cudaStreamSynchronize(st));
   return CK_OK;
 }

@@ -24,72 +24,15 @@
 
 #include "ck_device.cuh"
 #include "ck_internal.h"
+#include "ck_sums.cuh"
 
 namespace ck {
-
-__host__ __device__ constexpr int cmb(int n, int k) {
-  // C(n, k) for the small arguments used here
-  if (k < 0 || k > n) return 0;
-  long long r = 1;
-  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
-  return (int)r;
-}
-
-template <int NS, int MAXN>
-struct RegOut {
-  static constexpr int n2 = NS;
-  static constexpr int n3 = MAXN >= 3 ? cmb(NS + 1, 2) : 0;
-  static constexpr int n4 = MAXN >= 4 ? cmb(NS + 2, 3) : 0;
-  static constexpr int n5 = MAXN >= 5 ? cmb(NS + 3, 4) : 0;
-  static constexpr int total = n2 + n3 + n4 + n5;
-};
 
 constexpr int RK_CW = 7;                 // consumer warps
 constexpr int RK_CPT = 2;                // cells per consumer thread and chunk
 constexpr int RK_KC = 32 * RK_CW * RK_CPT;  // cells per chunk (1792-byte copies)
 constexpr int RK_STAGES = 6;             // ring depth
 constexpr int RK_FLUSH = 64;             // chunks between FP32 -> FP64 flushes
-
-template <int NS, int MAXN>
-__device__ __forceinline__ void reg_accumulate(float* acc, const float* v) {
-  using O = RegOut<NS, MAXN>;
-  int i3 = O::n2, i4 = O::n2 + O::n3, i5 = O::n2 + O::n3 + O::n4;
-#pragma unroll
-  for (int a = 0; a < NS; ++a) {
-    const float p1 = v[0] * v[1 + a];
-    acc[a] += p1;
-    if constexpr (MAXN >= 3) {
-#pragma unroll
-      for (int b = a; b < NS; ++b) {
-        const float p2 = p1 * v[1 + b];
-        acc[i3++] += p2;
-        if constexpr (MAXN >= 4) {
-#pragma unroll
-          for (int c = b; c < NS; ++c) {
-            const float p3 = p2 * v[1 + c];
-            acc[i4++] += p3;
-            if constexpr (MAXN >= 5) {
-#pragma unroll
-              for (int d = c; d < NS; ++d) acc[i5++] += p3 * v[1 + d];
-            }
-          }
-        }
-      }
-    }
-  }
-}
-
-template <int NOUT>
-__device__ __forceinline__ void reg_flush(float* acc, double* wacc, int lane) {
-#pragma unroll
-  for (int o = 0; o < NOUT; ++o) {
-    float t = acc[o];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, off);
-    if (lane == 0) wacc[o] += (double)t;
-    acc[o] = 0.0f;
-  }
-}
 
 // Orders 2 and 3 for the shells a in [A0, A1) only, in the local order
 // (a, then b >= a): acc[i] for n = 2 at (a), then n = 3 at (a, a..NS-1).

@@ -42,11 +42,11 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
   }
 }
 
-// Inverse transforms of nshells spectra: spec * K^_s (khat != nullptr) or
-// spec itself (khat == nullptr, nshells == 1), through the scratch spectra
-// tmp[s] (stride spec_elems), into real fields out + s * out_stride.
-void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp, float* out,
-                        int64_t out_stride, cudaStream_t st) {
+// Inverse z and y passes of nshells spectra: spec * K^_s (khat != nullptr)
+// or spec itself (khat == nullptr, nshells == 1), into the scratch spectra
+// tmp[s] (stride spec_elems).
+void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
+                       cudaStream_t st) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const double H = (double)nz * ny * (nx / 2 + 1);
   {
@@ -60,6 +60,15 @@ void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, in
     StridedView v{p.px, (int64_t)ny * p.px, p.px, (int64_t)nz * nshells};
     fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.sm_count, st);
   }
+}
+
+// The whole inverse: the z and y passes, then the x pass from tmp[s] into
+// real fields out + s * out_stride.
+void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp, float* out,
+                        int64_t out_stride, cudaStream_t st) {
+  const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
+  const double H = (double)nz * ny * (nx / 2 + 1);
+  launch_inverse_zy(p, spec, khat, nshells, tmp, st);
   {
     const int64_t rows = (int64_t)ny * nz * nshells;
     ProfScope ps(p, ST_FFT_X_C2R, nshells * (4.0 * (double)p.nc + 8.0 * H), st);

@@ -103,6 +103,44 @@ __device__ __forceinline__ void dft5(float2* v) {
   v[3] = csub(m2, j2);
 }
 
+// x * e^{-+ i theta} (forward: c - i s, INV: c + i s), (c, s) = (cos theta, sin theta)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 x, float c, float s) {
+  return INV ? make_float2(x.x * c - x.y * s, x.x * s + x.y * c) : make_float2(x.x * c + x.y * s, x.y * c - x.x * s);
+}
+
+constexpr float kC1_16 = 0.92387953251128675613f;  // cos(pi / 8)
+constexpr float kS1_16 = 0.38268343236508977173f;  // sin(pi / 8)
+
+// 16 points as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; DFT over n1, twiddle
+// w16^(n2 k1), DFT over n2.  Natural order in and out.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  float2 a[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) a[n2][n1] = v[4 * n1 + n2];
+    dft4<INV>(a[n2]);
+  }
+  a[1][1] = rot<INV>(a[1][1], kC1_16, kS1_16);        // w^1
+  a[1][2] = rot<INV>(a[1][2], kSqrtHalf, kSqrtHalf);  // w^2
+  a[1][3] = rot<INV>(a[1][3], kS1_16, kC1_16);        // w^3
+  a[2][1] = rot<INV>(a[2][1], kSqrtHalf, kSqrtHalf);  // w^2
+  a[2][2] = cmul_mi<INV>(a[2][2]);                    // w^4
+  a[2][3] = rot<INV>(a[2][3], -kSqrtHalf, kSqrtHalf); // w^6
+  a[3][1] = rot<INV>(a[3][1], kS1_16, kC1_16);        // w^3
+  a[3][2] = rot<INV>(a[3][2], -kSqrtHalf, kSqrtHalf); // w^6
+  a[3][3] = rot<INV>(a[3][3], -kC1_16, -kS1_16);      // w^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<INV>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) dft2<INV>(v[0], v[1]);
@@ -110,6 +148,7 @@ __device__ __forceinline__ void dft(float2* v) {
   else if constexpr (R == 4) dft4<INV>(v);
   else if constexpr (R == 5) dft5<INV>(v);
   else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,6 +395,11 @@ __device__ __forceinline__ int tw_len_rt(const FftLen& f) {
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
   const int n = valid ? 16 : 0;  // 0 source bytes: the destination is zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
+}
+
+// Copy the first n (0..16) bytes of src; the rest of the 16-byte destination is zero-filled.
+__device__ __forceinline__ void cp_async16n(void* dst, const void* src, int n) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -644,7 +688,8 @@ struct RealRowsOut {
 // iteration as x[2m] = Re z[m], x[2m+1] = Im z[m].  Input rows are contiguous
 // (pitch px); output row r goes to
 // out + (r / rows_per_shell) * out_shell_stride + (r % rows_per_shell) * nx.
-__host__ __device__ constexpr int stage_pitch(int M) { return M + 2; }
+// Even, so that every staged row starts on a 16-byte boundary (odd M too).
+__host__ __device__ constexpr int stage_pitch(int M) { return (M + 3) / 2 * 2; }
 
 template <int MC>
 __global__ void __launch_bounds__(kThreads, min_blocks(MC))

@@ -79,7 +79,7 @@ struct ContractPlan {
 // Per-stage event timing (ck_profile_enable / ck_profile_read).
 enum Stage {
   ST_GRID = 0, ST_PREP, ST_FFT_X_R2C, ST_FFT_Y_FWD, ST_FFT_Z_FWD, ST_FFT_Z_INV_MUL, ST_FFT_Y_INV,
-  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_OTHER
+  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_X_C2R_CONTRACT, ST_OTHER
 };
 
 struct Profiler {
@@ -151,7 +151,11 @@ struct Plan {
   mutable Profiler prof;
 
   bool have_randoms = false;
-  int bank_holds = -1;  // 0 = W of data, 1 = R***K of randoms
+  int bank_holds = -1;  // field whose spectrum is resident: 0 = data, 1 = randoms
+  // Convolution and sums in one pass (FP32, <= 16 shells, orders <= 3): the
+  // bank is not kept; `bank` holds one field, recomputed on request.
+  bool fused = false;
+  int bank_fields = 0;      // real fields reserved in `bank`
   int device = 0;
   int sm_count = 0;
 };
@@ -192,7 +196,17 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
 // out + s * out_stride.
 void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
                         float* out, int64_t out_stride, cudaStream_t st);
+// Its first two passes alone: tmp[s] = (y, z inverse of spec * K^_s), rows of pitch px.
+void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
+                       cudaStream_t st);
 ck_status build_kernel_spectra(Plan& p, cudaStream_t st);
+
+// ---- fused inverse x pass + sums (ck_xc.cu) -----------------------------------
+int xc_pad_shells(int ns);               // supported padded shell count, 0 if none
+size_t xc_smem_bytes(int M, int ns_pad);  // shared memory of the fused kernel
+// Inverse z, y passes and the fused x pass + order-2/3 sums of the resident
+// spectrum p.spec with cell values w0; packed sums (orders <= max_order).
+ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st);
 
 // ---- launches (ck_contract.cu) -----------------------------------------------
 ck_status contract_prepare(Plan& p, int order_mask);

@@ -63,6 +63,9 @@ static std::vector<int> shell_list(double s, double w, double g, int rule) {
   return out;
 }
 
+// Largest dynamic shared memory a CTA may opt in to (227 KB).
+constexpr size_t kMaxSmemOptin = 227 * 1024;
+
 static bool finite(double v) { return isfinite(v) != 0; }
 
 ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int max_order,
@@ -124,6 +127,13 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   p->oct[2] = nz / 2 + 1;
   p->oct_elems = (int64_t)p->oct[0] * p->oct[1] * p->oct[2];
   p->khat_stride = (int64_t)p->px * p->oct[1] * p->oct[2];
+  // One fused pass for the inverse x transform and the sums where its
+  // shared-memory tile fits; the bank is then not kept.
+  {
+    const int pad = xc_pad_shells(p->ns);
+    p->fused = precision == CK_PREC_FP32 && max_order <= 3 && pad > 0 && xc_smem_bytes(nx / 2, pad) <= kMaxSmemOptin;
+    p->bank_fields = p->fused ? 1 : p->ns;
+  }
   factor_len(nx / 2, &p->fx_half);
   factor_len(ny, &p->fy);
   factor_len(nz, &p->fz);
@@ -172,7 +182,7 @@ size_t workspace_bytes(const Plan& p) {
   b += al((size_t)p.spec_elems * 8);                           // spec
   b += al((size_t)p.ns * p.spec_elems * 8);                    // tmp: one scratch spectrum per shell
   b += al((size_t)p.ns * p.khat_stride * 4);                   // khat (padded octants)
-  b += al(std::max((size_t)p.ns * p.field_stride * 4, khat_scratch_doubles(p) * 8));  // bank
+  b += al(std::max((size_t)p.bank_fields * p.field_stride * 4, khat_scratch_doubles(p) * 8));  // bank
   b += al(p.partials_cap * 8);                                 // partials
   b += al((size_t)2 * 3 * p.staging_pts * 4);                  // staging
   for (int a = 0; a < 3; ++a) b += al((size_t)(p.grid.n[a] + 1) * 4);  // thresholds

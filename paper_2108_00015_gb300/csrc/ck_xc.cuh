@@ -1,0 +1,502 @@
+// ck_xc.cuh -- the last inverse FFT pass fused with the summation stage:
+// W_s = N *** K_s (Sec. 2.4) leaves the x transform straight into shared
+// memory, where the order-2 and order-3 products of Eq. 11,
+//   S2[a]    = sum_r N(r) W_a(r),
+//   S3[a][b] = sum_r N(r) W_a(r) W_b(r)   (a <= b kept),
+// are accumulated without W_s ever being written to global memory.
+//
+// Tiles and transforms.  A tile is kRows consecutive grid rows (y, z) of
+// every shell; a job fills the kT transform lines with SPJ = kT / kRows
+// shells of those rows (line c: row c / SPJ, shell q SPJ + c % SPJ).  The
+// half-spectrum rows of a job are staged with cp.async (the next job's
+// while the current one is transformed), unpacked into the half-length
+// complex sequence and transformed; the last iteration writes the real rows
+// into a store that holds the whole tile for every shell.
+//
+// Sums on the tensor cores.  Over the cells of a tile, S3 and S2 form one
+// rank-K update D[a][b] += sum_c A[a][c] B[c][b] with A[a][c] = N(c) W_a(c),
+// B[c][b] = W_b(c) for b < NS and B[c][NS..] = 1 (column 16 of the third
+// n-tile for NS = 16).  Each warp takes k-steps of 8 cells and issues
+// m16n8k8 TF32 MMAs whose fragments come straight from the store: lane
+// (g, t) = (lane / 4, lane % 4) loads W_g and W_{g+8} at cells t and t + 4,
+// which are both its A elements (times N) and its B elements.  Operands are
+// split x = hi + lo into two TF32 numbers and the product is taken as
+// hi*hi + hi*lo + lo*hi (three MMAs; the dropped lo*lo term is below
+// 2^-22 relative), accumulated in FP32 over the tile and then in FP64
+// registers.  At the end the warps' FP64 sums are added in a fixed order
+// and each CTA writes its partials (reduced across CTAs by the caller).
+//
+// NS is the shell count rounded up to 2, 4, 8 or 16; shells at or beyond
+// `nshells` are staged as zeros and their outputs ignored.
+#pragma once
+
+#include "ck_fft_core.cuh"
+
+namespace ck {
+namespace fft {
+
+constexpr int kWarps = kThreads / 32;
+
+__host__ __device__ constexpr int xc_rows(int NS) { return NS >= kT ? 1 : kT / NS; }  // grid rows per tile
+__host__ __device__ constexpr int xc_spj(int NS) { return kT / xc_rows(NS); }         // shells per job
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Shared-memory layout of the fused kernel (byte offsets).
+struct XcLayout {
+  size_t s0, s1, u, w, tws, twn, wst, nb0, nb1, total;
+  int tcp;  // cells per tile rounded up to the 8-cell k-step
+};
+
+__host__ __device__ inline XcLayout xc_layout(int M, int NS, int ntw) {
+  const int TC = xc_rows(NS) * 2 * M;
+  XcLayout L{};
+  L.tcp = (TC + 7) / 8 * 8;
+  size_t o = 0;
+  L.s0 = o;   o += align16((size_t)kT * stage_pitch(M) * sizeof(float2));
+  L.s1 = o;   o += align16((size_t)kT * stage_pitch(M) * sizeof(float2));
+  L.u = o;    o += align16((size_t)(M + 1) * kT * sizeof(float2));
+  L.w = o;    o += align16((size_t)(M + 1) * kT * sizeof(float2));
+  L.tws = o;  o += align16((size_t)ntw * sizeof(float2));
+  L.twn = o;  o += align16((size_t)(M + 1) * sizeof(float2));
+  L.wst = o;  o += align16((size_t)NS * L.tcp * sizeof(float));
+  L.nb0 = o;  o += align16((size_t)L.tcp * sizeof(float));
+  L.nb1 = o;  o += align16((size_t)L.tcp * sizeof(float));
+  // the final cross-warp sum reuses the buffers from offset 0
+  const size_t red = (size_t)kWarps * NS * (NS + 1) * sizeof(double);
+  L.total = o > red ? o : red;
+  return L;
+}
+
+// Per-iteration twiddle entries of the half-length transform.
+inline int xc_ntw(int M) {
+  const RPlan p = rplan(M);
+  return p.nst > 0 ? tw_table_len(p) : 0;
+}
+
+// Round to TF32 (nearest, ties away) and the TF32 remainder of x - hi.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+// D (16 x 8, FP32) += A (16 x 8, TF32, row-major) * B (8 x 8, TF32, column-major)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int MC, int NS>
+__global__ void __launch_bounds__(kThreads, 2)
+    xc_contract_kernel(const float2* __restrict__ spec, int64_t spec_stride, const float* __restrict__ w0, int nx,
+                       int px, int64_t rows, int nshells, FftLen f, const float2* __restrict__ stw,
+                       const float2* __restrict__ tw, double* __restrict__ partials) {
+  static_assert(NS == 2 || NS == 4 || NS == 8 || NS == 16, "padded shell counts");
+  constexpr int ROWS = xc_rows(NS);
+  constexpr int SPJ = xc_spj(NS);
+  constexpr int NQ = NS / SPJ;                 // jobs per tile
+  constexpr int NOUT = NS + NS * (NS + 1) / 2;
+  constexpr int NTW = NS > 8 ? 2 : 1;          // n-tiles of W columns; the next one holds the ones column
+  extern __shared__ float4 smem4[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
+  const int M = MC > 0 ? MC : nx / 2;
+  const int NX = 2 * M;
+  const int TC = ROWS * NX;
+  const int LP = stage_pitch(M);
+  const int ntw = MC > 0 ? tw_table_len(rplan(MC)) : tw_len_rt(f);
+  const XcLayout lay = xc_layout(M, NS, ntw);
+  const int TCP = lay.tcp;
+  float2* s0 = reinterpret_cast<float2*>(sm + lay.s0);
+  float2* s1 = reinterpret_cast<float2*>(sm + lay.s1);
+  float2* u = reinterpret_cast<float2*>(sm + lay.u);
+  float2* w = reinterpret_cast<float2*>(sm + lay.w);
+  float2* tws = reinterpret_cast<float2*>(sm + lay.tws);
+  float2* twn = reinterpret_cast<float2*>(sm + lay.twn);
+  float* wst = reinterpret_cast<float*>(sm + lay.wst);
+  auto nbuf = [&](int b) { return reinterpret_cast<float*>(sm + (b ? lay.nb1 : lay.nb0)); };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+
+  for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
+  for (int i = threadIdx.x; i <= M; i += kThreads) twn[i] = __ldg(tw + i);
+  // cells TC..TCP-1 of the store and of both N buffers stay zero
+  for (int i = threadIdx.x; i < (TCP - TC) * (NS + 2); i += kThreads) {
+    const int r = i / (TCP - TC), c = TC + i % (TCP - TC);
+    if (r < NS) wst[r * TCP + c] = 0.0f;
+    else nbuf(r - NS)[c] = 0.0f;
+  }
+
+  const int64_t ntiles = (rows + ROWS - 1) / ROWS;
+  const int np = M / 2 + 1;  // 16-byte copies per staged row (X[0..M], see x_c2r_kernel)
+  auto stage = [&](float2* s, float* nb, int64_t t, int q) {
+    const int64_t r0 = t * ROWS;
+    for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
+      const int c = idx / np, k = 2 * (idx - c * np);
+      const int i = c / SPJ, sh = q * SPJ + c % SPJ;
+      const bool ok = r0 + i < rows && sh < nshells;
+      cp_async16(s + c * LP + k, ok ? (const void*)(spec + sh * spec_stride + (r0 + i) * px + k) : (const void*)spec,
+                 ok);
+    }
+    if (q == 0) {
+      const int64_t vc = (rows - r0 < ROWS ? rows - r0 : ROWS) * (int64_t)NX;  // valid cells of the tile
+      if (TC % 4 == 0) {  // tile starts on a 16-byte boundary of w0
+        for (int idx = threadIdx.x; idx < TC / 4; idx += kThreads) {
+          const int64_t c4 = 4 * (int64_t)idx;
+          const bool ok = c4 < vc;
+          cp_async16n(nb + c4, ok ? (const void*)(w0 + r0 * NX + c4) : (const void*)w0,
+                      ok ? (int)(vc - c4 >= 4 ? 16 : 4 * (vc - c4)) : 0);
+        }
+      } else {  // plain loads: the buffer is not read before the next barrier
+        for (int c = threadIdx.x; c < TC; c += kThreads) nb[c] = c < vc ? __ldg(w0 + r0 * NX + c) : 0.0f;
+      }
+    }
+  };
+
+  float dacc32[NTW + 1][4];
+  double dacc[NTW + 1][4];
+#pragma unroll
+  for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dacc[j][e] = 0.0;
+  // the ones column: B[k][n] = 1 for n = 0 of the last n-tile
+  const uint32_t ones = g == 0 ? 0x3f800000u : 0u;
+
+  int64_t t = blockIdx.x;
+  if (t < ntiles) {
+    stage(s0, nbuf(0), t, 0);
+    cp_async_commit();
+    int q = 0, it = 0, kt = 0;  // job in tile, job counter, tile counter of this CTA
+    while (true) {
+      int64_t tn = t;
+      int qn = q + 1;
+      if (qn == NQ) {
+        qn = 0;
+        tn = t + gridDim.x;
+      }
+      const float2* sc = (it & 1) ? s1 : s0;
+      if (tn < ntiles) stage((it & 1) ? s0 : s1, nbuf((kt + 1) & 1), tn, qn);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      // unpack: Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k])
+      for (int idx = threadIdx.x; idx < kT * (M / 2 + 1); idx += kThreads) {
+        const int c = idx % kT, k = idx / kT;
+        const float2 a = sc[c * LP + k], b = sc[c * LP + M - k];
+        const float2 ca = cconj(a), cb = cconj(b);
+        u[k * kT + c] = cadd(cadd(a, cb), cmul_mi<true>(cmul(cconj(twn[k]), csub(a, cb))));
+        if (k != 0 && 2 * k != M)
+          u[(M - k) * kT + c] = cadd(cadd(b, ca), cmul_mi<true>(cmul(cconj(twn[M - k]), csub(b, ca))));
+      }
+      __syncthreads();
+      {
+        SmemLd ld{u};
+        // line pair cp: row (2 cp) / SPJ, shells q SPJ + (2 cp) % SPJ and the next one
+        auto st = [&](int m, int cp, float4 v) {
+          const int c = 2 * cp;
+          float* dst = wst + (size_t)(q * SPJ + c % SPJ) * TCP + (c / SPJ) * NX + 2 * m;
+          *reinterpret_cast<float2*>(dst) = lo2(v);
+          *reinterpret_cast<float2*>(dst + TCP) = hi2(v);
+        };
+        transform<MC, true>(w, u, tws, f, ld, st);
+      }
+      if (q == NQ - 1) {
+        // every shell of tile t is in the store: rank-8 updates per k-step
+        const float* nb = nbuf(kt & 1);
+#pragma unroll
+        for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dacc32[j][e] = 0.0f;
+#pragma unroll 1
+        for (int c0 = 8 * warp; c0 < TCP; c0 += 8 * kWarps) {
+          const float n0 = nb[c0 + tq], n1 = nb[c0 + tq + 4];
+          float wv[4];  // W_g(t), W_{g+8}(t), W_g(t+4), W_{g+8}(t+4)
+          wv[0] = g < NS ? wst[g * TCP + c0 + tq] : 0.0f;
+          wv[2] = g < NS ? wst[g * TCP + c0 + tq + 4] : 0.0f;
+          wv[1] = NS > 8 ? wst[(g + 8) * TCP + c0 + tq] : 0.0f;
+          wv[3] = NS > 8 ? wst[(g + 8) * TCP + c0 + tq + 4] : 0.0f;
+          uint32_t ah[4], al[4], bh[4], bl[4];
+          tf32_split(n0 * wv[0], ah[0], al[0]);
+          tf32_split(n0 * wv[1], ah[1], al[1]);
+          tf32_split(n1 * wv[2], ah[2], al[2]);
+          tf32_split(n1 * wv[3], ah[3], al[3]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) tf32_split(wv[e], bh[e], bl[e]);
+          // n-tile 0: b = g (W_g at t, t + 4); n-tile 1: b = 8 + g
+          mma_tf32(dacc32[0], ah, bh[0], bh[2]);
+          mma_tf32(dacc32[0], ah, bl[0], bl[2]);
+          mma_tf32(dacc32[0], al, bh[0], bh[2]);
+          if constexpr (NTW == 2) {
+            mma_tf32(dacc32[1], ah, bh[1], bh[3]);
+            mma_tf32(dacc32[1], ah, bl[1], bl[3]);
+            mma_tf32(dacc32[1], al, bh[1], bh[3]);
+          }
+          mma_tf32(dacc32[NTW], ah, ones, ones);
+          mma_tf32(dacc32[NTW], al, ones, ones);
+        }
+#pragma unroll
+        for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dacc[j][e] += (double)dacc32[j][e];
+        __syncthreads();  // the store is rewritten by the next tile
+        ++kt;
+      }
+      if (tn >= ntiles) break;
+      t = tn;
+      q = qn;
+      ++it;
+    }
+  }
+  // warp sums -> shared memory (over the staging buffers), then a fixed-order
+  // sum over warps: element (a, b) of D, b = NS for the order-2 column
+  __syncthreads();
+  constexpr int DC = NS + 1;
+  double* red = reinterpret_cast<double*>(sm);  // [kWarps][NS][DC]
+#pragma unroll
+  for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int a = g + ((e & 2) ? 8 : 0);
+      const int n = 2 * tq + (e & 1);
+      const int b = j < NTW ? (8 * j + n < NS ? 8 * j + n : -1) : (n == 0 ? NS : -1);
+      if (a < NS && b >= 0) red[(warp * NS + a) * DC + b] = dacc[j][e];
+    }
+  __syncthreads();
+  for (int o = threadIdx.x; o < NOUT; o += kThreads) {
+    int a, b;
+    if (o < NS) {
+      a = o;
+      b = NS;
+    } else {
+      int r = o - NS;
+      a = 0;
+      while (r >= NS - a) {
+        r -= NS - a;
+        ++a;
+      }
+      b = a + r;
+    }
+    double s = 0.0;
+    for (int wp = 0; wp < kWarps; ++wp) s += red[(wp * NS + a) * DC + b];
+    partials[(int64_t)blockIdx.x * NOUT + o] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Power-of-two half-lengths M = P Q (P, Q in {4, 8, 16}): the same pass with
+// the transform held in registers.  With k = Q k1 + k2 and m = m1 + P m2,
+//   z[m1 + P m2] = sum_k2 e^{2 pi i k2 m2 / Q} e^{2 pi i k2 m1 / M}
+//                  sum_k1 e^{2 pi i k1 m1 / P} Z[Q k1 + k2],
+// so step A (one thread per line and k2) unpacks its P values of Z straight
+// from the staged rows, runs a P-point DFT and applies the twiddles; the
+// results go through a padded shared transpose T; step B (one thread per
+// line and m1) runs the Q-point DFT and writes the real row
+// x[2m] = Re z[m], x[2m+1] = Im z[m] into the store W, which overlays T.
+// A tile is LT = 256 / max(P, Q) lines: ROWS = LT / NS grid rows of every
+// shell, all transformed at once (four barriers per tile).
+
+template <int P, int Q, int NS>
+struct XcrShape {
+  static constexpr int M = P * Q;
+  static constexpr int NX = 2 * M;
+  static constexpr int LT = kThreads / (P > Q ? P : Q);  // lines per tile
+  static constexpr int ROWS = LT / NS;                   // grid rows per tile
+  static constexpr int TC = ROWS * NX;                   // cells per tile
+  static constexpr int LP = stage_pitch(M);              // staged row pitch (float2)
+  static constexpr int TP = Q * (P + 1);                 // transpose floats2 per line
+  static constexpr int WP = TC + 4;                      // store pitch per shell (floats)
+  static constexpr size_t s_bytes = align16((size_t)LT * LP * sizeof(float2));
+  static constexpr size_t twu_off = 2 * s_bytes;                                   // e^{+2 pi i k / NX}, k <= M
+  static constexpr size_t twm_off = twu_off + align16((size_t)(M + 1) * sizeof(float2));  // e^{+2 pi i j / M}, j < M
+  static constexpr size_t t_off = twm_off + align16((size_t)M * sizeof(float2));
+  static constexpr size_t nb_off = t_off + align16((size_t)LT * TP * sizeof(float2));
+  static constexpr size_t nb_bytes = align16((size_t)TC * sizeof(float));
+  static constexpr size_t red_bytes = (size_t)kWarps * NS * (NS + 1) * sizeof(double);
+  static constexpr size_t total0 = nb_off + 3 * nb_bytes;
+  static constexpr size_t total = total0 > red_bytes ? total0 : red_bytes;
+  static_assert(ROWS >= 1 && LT % NS == 0, "a tile holds whole rows of every shell");
+  static_assert((size_t)NS * WP * sizeof(float) <= (size_t)LT * TP * sizeof(float2), "the store fits over T");
+  static_assert(TC % 8 == 0, "whole k-steps per tile");
+};
+
+template <int P, int Q, int NS>
+__global__ void __launch_bounds__(kThreads, 2)
+    xcr_contract_kernel(const float2* __restrict__ spec, int64_t spec_stride, const float* __restrict__ w0, int px,
+                        int64_t rows, int nshells, const float2* __restrict__ tw, double* __restrict__ partials) {
+  using S = XcrShape<P, Q, NS>;
+  constexpr int M = S::M, NX = S::NX, LT = S::LT, ROWS = S::ROWS, TC = S::TC, LP = S::LP, TP = S::TP, WP = S::WP;
+  constexpr int NOUT = NS + NS * (NS + 1) / 2;
+  constexpr int NTW = NS > 8 ? 2 : 1;
+  extern __shared__ float4 smem4[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
+  // staging buffer b at sm + b * s_bytes, N buffer b at nb_off + b * nb_bytes
+  auto sbuf = [&](int b) { return reinterpret_cast<float2*>(sm + b * S::s_bytes); };
+  auto nbuf = [&](int b) { return reinterpret_cast<float*>(sm + S::nb_off + b * S::nb_bytes); };
+  float2* twu = reinterpret_cast<float2*>(sm + S::twu_off);
+  float2* twm = reinterpret_cast<float2*>(sm + S::twm_off);
+  float2* T = reinterpret_cast<float2*>(sm + S::t_off);
+  float* W = reinterpret_cast<float*>(sm + S::t_off);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tq = lane & 3;
+
+  // tw[t] = e^{-2 pi i t / NX}, t < NX
+  for (int i = tid; i <= M; i += kThreads) twu[i] = cconj(__ldg(tw + i));
+  for (int i = tid; i < M; i += kThreads) twm[i] = cconj(__ldg(tw + 2 * i));
+
+  const int64_t ntiles = (rows + ROWS - 1) / ROWS;
+  constexpr int np = M / 2 + 1;  // 16-byte copies per staged row: X[0..M] (+ padding column M + 1)
+  auto stage = [&](float2* s, float* nb, int64_t t) {
+    const int64_t r0 = t * ROWS;
+    for (int idx = tid; idx < LT * np; idx += kThreads) {
+      const int l = idx / np, k = 2 * (idx - l * np);
+      const int sh = l / ROWS, i = l - sh * ROWS;
+      const bool ok = r0 + i < rows && sh < nshells;
+      cp_async16(s + l * LP + k, ok ? (const void*)(spec + sh * spec_stride + (r0 + i) * px + k) : (const void*)spec,
+                 ok);
+    }
+    const int64_t vc = (rows - r0 < ROWS ? rows - r0 : ROWS) * (int64_t)NX;
+    for (int idx = tid; idx < TC / 4; idx += kThreads) {
+      const int64_t c4 = 4 * (int64_t)idx;
+      const bool ok = c4 < vc;  // vc is a multiple of NX, hence of 4
+      cp_async16(nb + c4, ok ? (const void*)(w0 + r0 * NX + c4) : (const void*)w0, ok);
+    }
+  };
+
+  float dacc32[NTW + 1][4];
+  double dacc[NTW + 1][4];
+#pragma unroll
+  for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dacc[j][e] = 0.0;
+  const uint32_t ones = g == 0 ? 0x3f800000u : 0u;
+
+  int64_t t = blockIdx.x;
+  if (t < ntiles) {
+    stage(sbuf(0), nbuf(0), t);
+    cp_async_commit();
+  }
+  __syncthreads();  // tables
+  for (int kt = 0; t < ntiles; t += gridDim.x, ++kt) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) stage(sbuf((kt + 1) & 1), nbuf((kt + 1) % 3), tn);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    // step A: unpack Z[Q k1 + k2] = (X[k] + conj X[M-k]) + i e^{2 pi i k/NX} (X[k] - conj X[M-k]),
+    // P-point inverse DFT over k1, twiddle e^{2 pi i k2 m1 / M}, into T
+    if (tid < LT * Q) {
+      const int l = tid / Q, k2 = tid - l * Q;
+      const float2* xr = sbuf(kt & 1) + l * LP;
+      float2 v[P];
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) {
+        const int k = Q * k1 + k2;
+        const float2 a = xr[k], cb = cconj(xr[M - k]);
+        v[k1] = cadd(cadd(a, cb), cmul_mi<true>(cmul(twu[k], csub(a, cb))));
+      }
+      dft<P, true>(v);
+      float2* tr = T + l * TP + k2 * (P + 1);
+      tr[0] = v[0];
+#pragma unroll
+      for (int m1 = 1; m1 < P; ++m1) tr[m1] = cmul(v[m1], twm[k2 * m1]);
+    }
+    __syncthreads();
+    // step B: Q-point inverse DFT over k2 of column m1
+    float2 z[Q];
+    const int lb = tid / P, m1 = tid - lb * P;
+    if (tid < LT * P) {
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) z[k2] = T[lb * TP + k2 * (P + 1) + m1];
+    }
+    __syncthreads();  // W overlays T
+    if (tid < LT * P) {
+      dft<Q, true>(z);
+      const int sh = lb / ROWS, i = lb - sh * ROWS;
+      float* wr = W + sh * WP + i * NX + 2 * m1;
+#pragma unroll
+      for (int m2 = 0; m2 < Q; ++m2) *reinterpret_cast<float2*>(wr + 2 * P * m2) = z[m2];
+    }
+    __syncthreads();
+    // rank-8 updates on the tensor cores (see xc_contract_kernel)
+    {
+      const float* nb = nbuf(kt % 3);
+#pragma unroll
+      for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dacc32[j][e] = 0.0f;
+#pragma unroll 2
+      for (int c0 = 8 * warp; c0 < TC; c0 += 8 * kWarps) {
+        const float n0 = nb[c0 + tq], n1 = nb[c0 + tq + 4];
+        float wv[4];
+        wv[0] = g < NS ? W[g * WP + c0 + tq] : 0.0f;
+        wv[2] = g < NS ? W[g * WP + c0 + tq + 4] : 0.0f;
+        wv[1] = NS > 8 ? W[(g + 8) * WP + c0 + tq] : 0.0f;
+        wv[3] = NS > 8 ? W[(g + 8) * WP + c0 + tq + 4] : 0.0f;
+        uint32_t ah[4], al[4], bh[4], bl[4];
+        tf32_split(n0 * wv[0], ah[0], al[0]);
+        tf32_split(n0 * wv[1], ah[1], al[1]);
+        tf32_split(n1 * wv[2], ah[2], al[2]);
+        tf32_split(n1 * wv[3], ah[3], al[3]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) tf32_split(wv[e], bh[e], bl[e]);
+        mma_tf32(dacc32[0], ah, bh[0], bh[2]);
+        mma_tf32(dacc32[0], ah, bl[0], bl[2]);
+        mma_tf32(dacc32[0], al, bh[0], bh[2]);
+        if constexpr (NTW == 2) {
+          mma_tf32(dacc32[1], ah, bh[1], bh[3]);
+          mma_tf32(dacc32[1], ah, bl[1], bl[3]);
+          mma_tf32(dacc32[1], al, bh[1], bh[3]);
+        }
+        mma_tf32(dacc32[NTW], ah, ones, ones);
+        mma_tf32(dacc32[NTW], al, ones, ones);
+      }
+#pragma unroll
+      for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dacc[j][e] += (double)dacc32[j][e];
+    }
+    // the next tile's step A writes T only after its first barrier, which
+    // every warp reaches after this tile's sums; its N goes to a third buffer
+  }
+  __syncthreads();
+  constexpr int DC = NS + 1;
+  double* red = reinterpret_cast<double*>(sm);  // [kWarps][NS][DC]
+#pragma unroll
+  for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int a = g + ((e & 2) ? 8 : 0);
+      const int n = 2 * tq + (e & 1);
+      const int b = j < NTW ? (8 * j + n < NS ? 8 * j + n : -1) : (n == 0 ? NS : -1);
+      if (a < NS && b >= 0) red[(warp * NS + a) * DC + b] = dacc[j][e];
+    }
+  __syncthreads();
+  for (int o = tid; o < NOUT; o += kThreads) {
+    int a, b;
+    if (o < NS) {
+      a = o;
+      b = NS;
+    } else {
+      int r = o - NS;
+      a = 0;
+      while (r >= NS - a) {
+        r -= NS - a;
+        ++a;
+      }
+      b = a + r;
+    }
+    double s = 0.0;
+    for (int wp = 0; wp < kWarps; ++wp) s += red[(wp * NS + a) * DC + b];
+    partials[(int64_t)blockIdx.x * NOUT + o] = s;
+  }
+}
+
+}  // namespace fft
+}  // namespace ck

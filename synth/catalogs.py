@@ -117,23 +117,32 @@ def _to_periodic_f32(v: np.ndarray, length: float) -> np.ndarray:
     return f
 
 
-def uniform_box(seed: int, n: int, length: float) -> Catalog:
-    """``n`` uniform points in the periodic cube [0, L)^3."""
+def _lengths(length) -> Tuple[float, float, float]:
+    if np.ndim(length) == 0:
+        return (float(length),) * 3
+    return tuple(float(v) for v in length)
+
+
+def uniform_box(seed: int, n: int, length) -> Catalog:
+    """``n`` uniform points in the periodic box [0, L)^3 (or
+    [0, Lx) x [0, Ly) x [0, Lz) for a triple of lengths)."""
+    L = _lengths(length)
     rng = np.random.Generator(np.random.PCG64(seed))
-    return Catalog(*(_to_periodic_f32(rng.random(n) * length, length) for _ in range(3)))
+    return Catalog(*(_to_periodic_f32(rng.random(n) * L[a], L[a]) for a in range(3)))
 
 
 def neyman_scott_box(seed: int, n_parents: int, n_children: int, sigma: float,
-                     length: float) -> Catalog:
-    """Neyman-Scott process in a periodic cube: Poisson (uniform) parents,
+                     length) -> Catalog:
+    """Neyman-Scott process in a periodic box: Poisson (uniform) parents,
     each with exactly ``n_children`` children displaced by an isotropic
     Gaussian of ``sigma`` per axis, wrapped into the box.  Children of one
     parent are stored consecutively."""
+    L = _lengths(length)
     rng = np.random.Generator(np.random.PCG64(seed))
-    parents = rng.random((n_parents, 3)) * length
+    parents = rng.random((n_parents, 3)) * np.array(L)
     off = rng.normal(0.0, sigma, size=(n_parents, n_children, 3))
     pts = (parents[:, None, :] + off).reshape(-1, 3)
-    return Catalog(*(_to_periodic_f32(pts[:, a], length) for a in range(3)))
+    return Catalog(*(_to_periodic_f32(pts[:, a], L[a]) for a in range(3)))
 
 
 def uniform_survey(seed: int, n: int, mask: SurveyMask = SurveyMask(),
@@ -288,6 +297,15 @@ WORKLOADS: Dict[str, dict] = {
         data=("ns_box", dict(seed=10, n_parents=5_000, n_children=20, sigma=8.0)),
         randoms=("uniform_box", dict(seed=11, n=4_000_000)),
     ),
+    # Profiler case for the fused last pass at the survey's x length and shell
+    # count: periodic 512 x 128 x 128 of 8 h^-1 Mpc, the survey's 16 shells
+    # (16 scratch spectra of 136 MB), small catalogs.
+    "profile512x16": dict(
+        grid=GridSpec((512, 128, 128), (0.0, 0.0, 0.0), 8.0, True),
+        shells=_shells(30.0, 8.0, 16), width=8.0, orders=(2, 3),
+        data=("ns_box", dict(seed=12, n_parents=2_500, n_children=20, sigma=8.0)),
+        randoms=("uniform_box", dict(seed=13, n=2_000_000)),
+    ),
 }
 
 
@@ -295,10 +313,10 @@ def _draw(kind: str, kw: dict, grid: GridSpec, scale: float) -> Catalog:
     kw = dict(kw)
     if kind == "ns_box":
         kw["n_parents"] = max(1, int(round(kw["n_parents"] * scale)))
-        return neyman_scott_box(length=grid.length[0], **kw)
+        return neyman_scott_box(length=grid.length, **kw)
     if kind == "uniform_box":
         kw["n"] = max(1, int(round(kw["n"] * scale)))
-        return uniform_box(length=grid.length[0], **kw)
+        return uniform_box(length=grid.length, **kw)
     if kind == "ns_survey":
         kw["n_parents"] = max(1, int(round(kw["n_parents"] * scale)))
         return neyman_scott_survey(grid=grid, **kw)

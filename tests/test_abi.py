@@ -65,8 +65,13 @@ def test_host_validation(lib):
 
 
 def test_survey_workspace_fits(lib):
-    # 512^3, 16 shells: counts + field + 2 spectra + kernel octants + W bank
-    code, nbytes = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0,
-                       radii=tuple(30.0 + 8 * i for i in range(16)), width=8.0)
+    # 512^3, 16 shells, orders <= 3 (fused pass, no bank): counts + field +
+    # spectrum + 16 scratch spectra + kernel octants + one real field
+    radii = tuple(30.0 + 8 * i for i in range(16))
+    code, fused = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0, radii=radii, width=8.0, max_order=3)
     assert code == 0
-    assert 15e9 < nbytes < 25e9
+    assert 10e9 < fused < 15e9
+    # orders <= 4 keep the 16-field bank (8.6 GB more)
+    code, banked = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0, radii=radii, width=8.0, max_order=4)
+    assert code == 0
+    assert abs((banked - fused) - 15 * 512 ** 3 * 4) < 0.05e9
