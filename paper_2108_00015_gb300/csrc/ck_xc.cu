@@ -13,7 +13,7 @@ namespace fft {
 
 cudaError_t run_xc16(int M, const float2* spec, int64_t spec_stride, const float* w0, int nx, int px, int64_t rows,
                      int nshells, const FftLen& f, const float2* stw, const float2* tw, int max_ctas, int* ctas,
-                     double* partials, cudaStream_t st);
+                     double* partials, int* status, cudaStream_t st);
 
 }  // namespace fft
 
@@ -82,16 +82,16 @@ ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaS
     const FftLen& f = p.fx_half;
     if (ns_pad == 16)
       e = fft::run_xc16(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas, &ctas,
-                        p.partials, st);
+                        p.partials, &p.dstate->status, st);
     else if (ns_pad == 8)
       e = fft::run_xc_ns<8>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas,
-                            &ctas, p.partials, st);
+                            &ctas, p.partials, &p.dstate->status, st);
     else if (ns_pad == 4)
       e = fft::run_xc_ns<4>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas,
-                            &ctas, p.partials, st);
+                            &ctas, p.partials, &p.dstate->status, st);
     else
       e = fft::run_xc_ns<2>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas,
-                            &ctas, p.partials, st);
+                            &ctas, p.partials, &p.dstate->status, st);
   }
   if (e != cudaSuccess) return cuda_status(e);
   ProfScope ps2(p, ST_REDUCE, 8.0 * (double)ctas * nout_pad, st);

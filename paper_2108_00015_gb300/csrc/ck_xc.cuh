@@ -22,8 +22,8 @@
 // which are both its A elements (times N) and its B elements.  Operands are
 // split x = hi + lo into two TF32 numbers and the product is taken as
 // hi*hi + hi*lo + lo*hi (three MMAs; the dropped lo*lo term is below
-// 2^-22 relative), accumulated in FP32 over the tile and then in FP64
-// registers.  At the end the warps' FP64 sums are added in a fixed order
+// 2^-22 relative), accumulated in FP32 over a tile, in FP32 over
+// kFlushTiles tile sums, then in FP64 registers (FP64 throughput is low).  At the end the warps' FP64 sums are added in a fixed order
 // and each CTA writes its partials (reduced across CTAs by the caller).
 //
 // NS is the shell count rounded up to 2, 4, 8 or 16; shells at or beyond
@@ -36,6 +36,9 @@ namespace ck {
 namespace fft {
 
 constexpr int kWarps = kThreads / 32;
+// Tiles whose FP32 sums are added in FP32 before one FP64 flush: the FP64
+// pipe is narrow, and (24 + kFlushTiles) FP32 roundings stay below 1e-5.
+constexpr int kFlushTiles = 32;
 
 __host__ __device__ constexpr int xc_rows(int NS) { return NS >= kT ? 1 : kT / NS; }  // grid rows per tile
 __host__ __device__ constexpr int xc_spj(int NS) { return kT / xc_rows(NS); }         // shells per job
@@ -159,12 +162,17 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
   };
 
-  float dacc32[NTW + 1][4];
+  float dacc32[NTW + 1][4];  // this tile
+  float mid[NTW + 1][4];     // tiles since the last FP64 flush
   double dacc[NTW + 1][4];
 #pragma unroll
   for (int j = 0; j <= NTW; ++j)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) dacc[j][e] = 0.0;
+    for (int e = 0; e < 4; ++e) {
+      mid[j][e] = 0.0f;
+      dacc[j][e] = 0.0;
+    }
+  int since = 0;
   // the ones column: B[k][n] = 1 for n = 0 of the last n-tile
   const uint32_t ones = g == 0 ? 0x3f800000u : 0u;
 
@@ -243,7 +251,17 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int j = 0; j <= NTW; ++j)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) dacc[j][e] += (double)dacc32[j][e];
+          for (int e = 0; e < 4; ++e) mid[j][e] += dacc32[j][e];
+        if (++since == kFlushTiles) {
+#pragma unroll
+          for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              dacc[j][e] += (double)mid[j][e];
+              mid[j][e] = 0.0f;
+            }
+          since = 0;
+        }
         __syncthreads();  // the store is rewritten by the next tile
         ++kt;
       }
@@ -256,6 +274,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   // warp sums -> shared memory (over the staging buffers), then a fixed-order
   // sum over warps: element (a, b) of D, b = NS for the order-2 column
   __syncthreads();
+#pragma unroll
+  for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dacc[j][e] += (double)mid[j][e];
   constexpr int DC = NS + 1;
   double* red = reinterpret_cast<double*>(sm);  // [kWarps][NS][DC]
 #pragma unroll
@@ -299,7 +321,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 // line and m1) runs the Q-point DFT and writes the real row
 // x[2m] = Re z[m], x[2m+1] = Im z[m] into the store W, which overlays T.
 // A tile is LT = 256 / max(P, Q) lines: ROWS = LT / NS grid rows of every
-// shell, all transformed at once (four barriers per tile).
+// shell, all transformed at once.  One thread stages the next tile with
+// bulk asynchronous copies (one per row of X[0..M+1], and one for the
+// tile's N cells) completing on the buffer's mbarrier; waits are bounded.
+//
+// In the sums, k-slot t of a k-step holds cell c0 + 2t and slot t + 4 cell
+// c0 + 2t + 1, so that each lane reads its two cells with one 8-byte load.
 
 template <int P, int Q, int NS>
 struct XcrShape {
@@ -309,86 +336,103 @@ struct XcrShape {
   static constexpr int ROWS = LT / NS;                   // grid rows per tile
   static constexpr int TC = ROWS * NX;                   // cells per tile
   static constexpr int LP = stage_pitch(M);              // staged row pitch (float2)
-  static constexpr int TP = Q * (P + 1);                 // transpose floats2 per line
-  static constexpr int WP = TC + 4;                      // store pitch per shell (floats)
+  static constexpr int TP = Q * (P + 1);                 // transpose float2 per line
+  static constexpr int WP = TC + 8;                      // store pitch per shell (floats), 8 mod 32
   static constexpr size_t s_bytes = align16((size_t)LT * LP * sizeof(float2));
-  static constexpr size_t twu_off = 2 * s_bytes;                                   // e^{+2 pi i k / NX}, k <= M
-  static constexpr size_t twm_off = twu_off + align16((size_t)(M + 1) * sizeof(float2));  // e^{+2 pi i j / M}, j < M
-  static constexpr size_t t_off = twm_off + align16((size_t)M * sizeof(float2));
+  static constexpr size_t twu_off = 2 * s_bytes;  // e^{+2 pi i k / NX}, k <= M
+  static constexpr size_t twq_off = twu_off + align16((size_t)(M + 1) * sizeof(float2));  // [k2][m1], row pitch P + 1: e^{2 pi i k2 m1 / M}
+  static constexpr size_t t_off = twq_off + align16((size_t)Q * (P + 1) * sizeof(float2));
   static constexpr size_t nb_off = t_off + align16((size_t)LT * TP * sizeof(float2));
   static constexpr size_t nb_bytes = align16((size_t)TC * sizeof(float));
+  static constexpr size_t bar_off = nb_off + 3 * nb_bytes;
   static constexpr size_t red_bytes = (size_t)kWarps * NS * (NS + 1) * sizeof(double);
-  static constexpr size_t total0 = nb_off + 3 * nb_bytes;
+  static constexpr size_t total0 = bar_off + 16;
   static constexpr size_t total = total0 > red_bytes ? total0 : red_bytes;
   static_assert(ROWS >= 1 && LT % NS == 0, "a tile holds whole rows of every shell");
   static_assert((size_t)NS * WP * sizeof(float) <= (size_t)LT * TP * sizeof(float2), "the store fits over T");
-  static_assert(TC % 8 == 0, "whole k-steps per tile");
+  static_assert(TC % 32 == 0, "whole k-steps per tile and a conflict-free store pitch");
+  static_assert((LP * sizeof(float2)) % 16 == 0 && (NX * sizeof(float)) % 16 == 0, "16-byte bulk copies");
+  static_assert(red_bytes <= bar_off, "the final sum does not reach the barriers");
 };
+
+__device__ __forceinline__ uint32_t tf32_trunc(float x) { return __float_as_uint(x) & 0xffffe000u; }
 
 template <int P, int Q, int NS>
 __global__ void __launch_bounds__(kThreads, 2)
     xcr_contract_kernel(const float2* __restrict__ spec, int64_t spec_stride, const float* __restrict__ w0, int px,
-                        int64_t rows, int nshells, const float2* __restrict__ tw, double* __restrict__ partials) {
+                        int64_t rows, int nshells, const float2* __restrict__ tw, double* __restrict__ partials,
+                        int* status) {
   using S = XcrShape<P, Q, NS>;
   constexpr int M = S::M, NX = S::NX, LT = S::LT, ROWS = S::ROWS, TC = S::TC, LP = S::LP, TP = S::TP, WP = S::WP;
   constexpr int NOUT = NS + NS * (NS + 1) / 2;
   constexpr int NTW = NS > 8 ? 2 : 1;
   extern __shared__ float4 smem4[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
-  // staging buffer b at sm + b * s_bytes, N buffer b at nb_off + b * nb_bytes
+  // staging buffer b at b * s_bytes, N buffer b at nb_off + b * nb_bytes
   auto sbuf = [&](int b) { return reinterpret_cast<float2*>(sm + b * S::s_bytes); };
   auto nbuf = [&](int b) { return reinterpret_cast<float*>(sm + S::nb_off + b * S::nb_bytes); };
   float2* twu = reinterpret_cast<float2*>(sm + S::twu_off);
-  float2* twm = reinterpret_cast<float2*>(sm + S::twm_off);
+  float2* twq = reinterpret_cast<float2*>(sm + S::twq_off);
   float2* T = reinterpret_cast<float2*>(sm + S::t_off);
   float* W = reinterpret_cast<float*>(sm + S::t_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::bar_off);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tq = lane & 3;
+  const int nsv = nshells < NS ? nshells : NS;  // shells with data; the other lines stay zero
 
   // tw[t] = e^{-2 pi i t / NX}, t < NX
   for (int i = tid; i <= M; i += kThreads) twu[i] = cconj(__ldg(tw + i));
-  for (int i = tid; i < M; i += kThreads) twm[i] = cconj(__ldg(tw + 2 * i));
+  for (int i = tid; i < M; i += kThreads) twq[(i / P) * (P + 1) + i % P] = cconj(__ldg(tw + 2 * ((i / P) * (i % P))));
+  for (int i = tid; i < (int)(2 * S::s_bytes / 16); i += kThreads) reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+  }
+  fence_async_shared();  // zeroed buffers and barrier initialisation before any bulk copy
+  __syncthreads();
 
   const int64_t ntiles = (rows + ROWS - 1) / ROWS;
-  constexpr int np = M / 2 + 1;  // 16-byte copies per staged row: X[0..M] (+ padding column M + 1)
-  auto stage = [&](float2* s, float* nb, int64_t t) {
+  // thread 0: bulk copies of tile t into staging buffer b and N buffer nbi
+  auto stage = [&](int b, int nbi, int64_t t) {
     const int64_t r0 = t * ROWS;
-    for (int idx = tid; idx < LT * np; idx += kThreads) {
-      const int l = idx / np, k = 2 * (idx - l * np);
-      const int sh = l / ROWS, i = l - sh * ROWS;
-      const bool ok = r0 + i < rows && sh < nshells;
-      cp_async16(s + l * LP + k, ok ? (const void*)(spec + sh * spec_stride + (r0 + i) * px + k) : (const void*)spec,
-                 ok);
-    }
-    const int64_t vc = (rows - r0 < ROWS ? rows - r0 : ROWS) * (int64_t)NX;
-    for (int idx = tid; idx < TC / 4; idx += kThreads) {
-      const int64_t c4 = 4 * (int64_t)idx;
-      const bool ok = c4 < vc;  // vc is a multiple of NX, hence of 4
-      cp_async16(nb + c4, ok ? (const void*)(w0 + r0 * NX + c4) : (const void*)w0, ok);
-    }
+    const int vr = (int)(rows - r0 < ROWS ? rows - r0 : ROWS);
+    const uint32_t row_bytes = LP * sizeof(float2);
+    mbar_arrive_expect_tx(&full[b], (uint32_t)(nsv * vr) * row_bytes + (uint32_t)(vr * NX * sizeof(float)));
+    for (int sh = 0; sh < nsv; ++sh)
+      for (int i = 0; i < vr; ++i)
+        bulk_g2s(sbuf(b) + (sh * ROWS + i) * LP, spec + sh * spec_stride + (r0 + i) * px, row_bytes, &full[b]);
+    bulk_g2s(nbuf(nbi), w0 + r0 * NX, (uint32_t)(vr * NX * sizeof(float)), &full[b]);
   };
 
-  float dacc32[NTW + 1][4];
+  float dacc32[NTW + 1][4];  // this tile
+  float mid[NTW + 1][4];     // tiles since the last FP64 flush
   double dacc[NTW + 1][4];
 #pragma unroll
   for (int j = 0; j <= NTW; ++j)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) dacc[j][e] = 0.0;
+    for (int e = 0; e < 4; ++e) {
+      mid[j][e] = 0.0f;
+      dacc[j][e] = 0.0;
+    }
   const uint32_t ones = g == 0 ? 0x3f800000u : 0u;
+  int since = 0;
 
   int64_t t = blockIdx.x;
-  if (t < ntiles) {
-    stage(sbuf(0), nbuf(0), t);
-    cp_async_commit();
-  }
-  __syncthreads();  // tables
+  int issued = 0, used = 0;  // tiles staged / consumed by this CTA
+  if (t < ntiles && tid == 0) stage(0, 0, t);
+  if (t < ntiles) issued = 1;
   for (int kt = 0; t < ntiles; t += gridDim.x, ++kt) {
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) stage(sbuf((kt + 1) & 1), nbuf((kt + 1) % 3), tn);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
+    if (tn < ntiles) {
+      if (tid == 0) stage((kt + 1) & 1, (kt + 1) % 3, tn);
+      issued = kt + 2;
+    }
+    const bool ok = mbar_wait(&full[kt & 1], (uint32_t)(kt >> 1) & 1u, status);
+    if (__syncthreads_or(!ok)) break;
+    used = kt + 1;
+    const int64_t r0 = t * ROWS;
+    const int vc = (int)(rows - r0 < ROWS ? rows - r0 : ROWS) * NX;  // cells of the tile with data
     // step A: unpack Z[Q k1 + k2] = (X[k] + conj X[M-k]) + i e^{2 pi i k/NX} (X[k] - conj X[M-k]),
     // P-point inverse DFT over k1, twiddle e^{2 pi i k2 m1 / M}, into T
     if (tid < LT * Q) {
@@ -403,9 +447,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       dft<P, true>(v);
       float2* tr = T + l * TP + k2 * (P + 1);
+      const float2* tk = twq + k2 * (P + 1);
       tr[0] = v[0];
 #pragma unroll
-      for (int m1 = 1; m1 < P; ++m1) tr[m1] = cmul(v[m1], twm[k2 * m1]);
+      for (int m1 = 1; m1 < P; ++m1) tr[m1] = cmul(v[m1], tk[m1]);
     }
     __syncthreads();
     // step B: Q-point inverse DFT over k2 of column m1
@@ -433,26 +478,29 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int e = 0; e < 4; ++e) dacc32[j][e] = 0.0f;
 #pragma unroll 2
       for (int c0 = 8 * warp; c0 < TC; c0 += 8 * kWarps) {
-        const float n0 = nb[c0 + tq], n1 = nb[c0 + tq + 4];
-        float wv[4];
-        wv[0] = g < NS ? W[g * WP + c0 + tq] : 0.0f;
-        wv[2] = g < NS ? W[g * WP + c0 + tq + 4] : 0.0f;
-        wv[1] = NS > 8 ? W[(g + 8) * WP + c0 + tq] : 0.0f;
-        wv[3] = NS > 8 ? W[(g + 8) * WP + c0 + tq + 4] : 0.0f;
+        const int c = c0 + 2 * tq;
+        float2 nn = *reinterpret_cast<const float2*>(nb + c);
+        if (c >= vc) nn = make_float2(0.f, 0.f);  // rows past the grid (last tile)
+        const float2 wa = g < NS ? *reinterpret_cast<const float2*>(W + g * WP + c) : make_float2(0.f, 0.f);
+        const float2 wb = NS > 8 ? *reinterpret_cast<const float2*>(W + (g + 8) * WP + c) : make_float2(0.f, 0.f);
+        const float av[4] = {nn.x * wa.x, nn.x * wb.x, nn.y * wa.y, nn.y * wb.y};
+        const float bv[4] = {wa.x, wa.y, wb.x, wb.y};
         uint32_t ah[4], al[4], bh[4], bl[4];
-        tf32_split(n0 * wv[0], ah[0], al[0]);
-        tf32_split(n0 * wv[1], ah[1], al[1]);
-        tf32_split(n1 * wv[2], ah[2], al[2]);
-        tf32_split(n1 * wv[3], ah[3], al[3]);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) tf32_split(wv[e], bh[e], bl[e]);
-        mma_tf32(dacc32[0], ah, bh[0], bh[2]);
-        mma_tf32(dacc32[0], ah, bl[0], bl[2]);
-        mma_tf32(dacc32[0], al, bh[0], bh[2]);
+        for (int e = 0; e < 4; ++e) {
+          ah[e] = tf32_trunc(av[e]);
+          al[e] = __float_as_uint(av[e] - __uint_as_float(ah[e]));
+          bh[e] = tf32_trunc(bv[e]);
+          bl[e] = __float_as_uint(bv[e] - __uint_as_float(bh[e]));
+        }
+        // n-tile 0: B[k][g] = W_g; n-tile 1: B[k][g] = W_{g+8}; last: ones column
+        mma_tf32(dacc32[0], ah, bh[0], bh[1]);
+        mma_tf32(dacc32[0], ah, bl[0], bl[1]);
+        mma_tf32(dacc32[0], al, bh[0], bh[1]);
         if constexpr (NTW == 2) {
-          mma_tf32(dacc32[1], ah, bh[1], bh[3]);
-          mma_tf32(dacc32[1], ah, bl[1], bl[3]);
-          mma_tf32(dacc32[1], al, bh[1], bh[3]);
+          mma_tf32(dacc32[1], ah, bh[2], bh[3]);
+          mma_tf32(dacc32[1], ah, bl[2], bl[3]);
+          mma_tf32(dacc32[1], al, bh[2], bh[3]);
         }
         mma_tf32(dacc32[NTW], ah, ones, ones);
         mma_tf32(dacc32[NTW], al, ones, ones);
@@ -460,12 +508,30 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int j = 0; j <= NTW; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) dacc[j][e] += (double)dacc32[j][e];
+        for (int e = 0; e < 4; ++e) mid[j][e] += dacc32[j][e];
+      if (++since == kFlushTiles) {
+#pragma unroll
+        for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            dacc[j][e] += (double)mid[j][e];
+            mid[j][e] = 0.0f;
+          }
+        since = 0;
+      }
     }
     // the next tile's step A writes T only after its first barrier, which
     // every warp reaches after this tile's sums; its N goes to a third buffer
   }
+  // after a timed-out wait: let the copies already issued land (bounded)
+  if (tid == 0)
+    for (int k = used; k < issued; ++k)
+      if (!mbar_wait(&full[k & 1], (uint32_t)(k >> 1) & 1u, status)) break;
   __syncthreads();
+#pragma unroll
+  for (int j = 0; j <= NTW; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dacc[j][e] += (double)mid[j][e];
   constexpr int DC = NS + 1;
   double* red = reinterpret_cast<double*>(sm);  // [kWarps][NS][DC]
 #pragma unroll

@@ -33,14 +33,14 @@ cudaError_t run_xc(const float2* spec, int64_t spec_stride, const float* w0, int
 
 template <int P, int Q, int NS>
 cudaError_t run_xcr(const float2* spec, int64_t spec_stride, const float* w0, int px, int64_t rows, int nshells,
-                    const float2* tw, int max_ctas, int* ctas, double* partials, cudaStream_t st) {
+                    const float2* tw, int max_ctas, int* ctas, double* partials, int* status, cudaStream_t st) {
   using S = XcrShape<P, Q, NS>;
   *ctas = xc_ctas((rows + S::ROWS - 1) / S::ROWS, max_ctas);
   cudaError_t e = cudaFuncSetAttribute(xcr_contract_kernel<P, Q, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)S::total);
   if (e != cudaSuccess) return e;
   xcr_contract_kernel<P, Q, NS><<<*ctas, kThreads, S::total, st>>>(spec, spec_stride, w0, px, rows, nshells, tw,
-                                                                   partials);
+                                                                   partials, status);
   return cudaGetLastError();
 }
 
@@ -49,13 +49,13 @@ cudaError_t run_xcr(const float2* spec, int64_t spec_stride, const float* w0, in
 template <int NS>
 cudaError_t run_xc_ns(int M, const float2* spec, int64_t spec_stride, const float* w0, int nx, int px, int64_t rows,
                       int nshells, const FftLen& f, const float2* stw, const float2* tw, int max_ctas, int* ctas,
-                      double* partials, cudaStream_t st) {
+                      double* partials, int* status, cudaStream_t st) {
   switch (M) {
-    case 256: return run_xcr<16, 16, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, st);
-    case 128: return run_xcr<16, 8, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, st);
-    case 64: return run_xcr<8, 8, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, st);
-    case 32: return run_xcr<8, 4, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, st);
-    case 16: return run_xcr<4, 4, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, st);
+    case 256: return run_xcr<16, 16, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, status, st);
+    case 128: return run_xcr<16, 8, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, status, st);
+    case 64: return run_xcr<8, 8, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, status, st);
+    case 32: return run_xcr<8, 4, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, status, st);
+    case 16: return run_xcr<4, 4, NS>(spec, spec_stride, w0, px, rows, nshells, tw, max_ctas, ctas, partials, status, st);
 #define CK_CASE(N)                                                                                              \
   case N:                                                                                                       \
     return run_xc<N, NS>(spec, spec_stride, w0, nx, px, rows, nshells, f, stw, tw, max_ctas, ctas, partials, st);
