@@ -33,12 +33,12 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
   {
     ProfScope ps(p, ST_FFT_Y_FWD, 16.0 * H, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, nz};
-    fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.sm_count, st);
+    fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.tw[1], false, p.sm_count, st);
   }
   {
     ProfScope ps(p, ST_FFT_Z_FWD, 16.0 * H, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
-    fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.sm_count, st);
+    fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.tw[2], false, p.sm_count, st);
   }
 }
 
@@ -53,12 +53,12 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
     ProfScope ps(p, ST_FFT_Z_INV_MUL, 8.0 * H + nshells * (8.0 * H + (khat ? 4.0 * (double)p.oct_elems : 0.0)), st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
     KhatArgs K{khat, p.khat_stride, p.px, ny, nz, p.oct[1]};
-    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], K, p.sm_count, st);
+    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.tw[2], K, p.sm_count, st);
   }
   {
     ProfScope ps(p, ST_FFT_Y_INV, nshells * 16.0 * H, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, (int64_t)nz * nshells};
-    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.sm_count, st);
+    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1, p.sm_count, st);
   }
 }
 

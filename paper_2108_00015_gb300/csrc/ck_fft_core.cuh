@@ -779,10 +779,12 @@ inline size_t xpass_smem(int nx) {
 
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).
+// row_ordered: prefer the kernel whose stores walk consecutive rows (large in-place passes)
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, int sm_count, cudaStream_t st);
+                    const float2* stw, const float2* tw, bool row_ordered, int sm_count, cudaStream_t st);
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
-                   const FftLen& f, const float2* stw, const KhatArgs& K, int sm_count, cudaStream_t st);
+                   const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
+                   cudaStream_t st);
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
                   const float2* stw, const float2* tw, int sm_count, cudaStream_t st);
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,

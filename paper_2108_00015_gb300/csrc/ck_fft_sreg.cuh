@@ -1,0 +1,209 @@
+// ck_fft_sreg.cuh -- 512-point transforms along a strided axis (y or z)
+// with the butterflies in registers, for the passes of Sec. 2.4's FFT
+// convolution on 512-cell axes.
+//
+// A tile is C = 8 adjacent columns x 512 rows of a strided view, staged in
+// shared memory as S[row][c].  With l = 32 l1 + l2 and m = m1 + 16 m2,
+//   X[m1 + 16 m2] = sum_l2 w32^(l2 m2) w512^(l2 m1) sum_l1 w16^(l1 m1) x[32 l1 + l2]
+// (w_n = e^{-+2 pi i / n}).  Step A: thread (c, l2) runs the 16-point DFT
+// over l1 and applies w512^(l2 m1), writing the padded transpose T.  Step
+// B: threads (c, m1, h) take the even (h = 0) or odd (h = 1) l2 of column
+// m1 of T, run a 16-point DFT (E or O), the odd one multiplied by w32^k;
+// one exchange with the partner lane (lane ^ 8) gives each thread half of
+// X[m1 + 16 k] = E[k] + w32^k O[k] and X[m1 + 16 (k + 16)] = E[k] - w32^k O[k],
+// which go straight to global memory (8 columns = 64 contiguous bytes).
+//
+// sreg512_kernel: one transform per tile, double-buffered staging (in
+// place allowed).  zreg512_kernel: the first inverse pass of Eqs. 9-10: the
+// spectrum tile is staged once and, for every shell s, multiplied by the
+// tile's slab of K^_s while step A reads it; outputs go to out + s * stride.
+#pragma once
+
+#include "ck_fft_core.cuh"
+
+namespace ck {
+namespace fft {
+
+struct Sreg512 {
+  static constexpr int L = 512, P = 16, Q = 32, C = 8;
+  static constexpr int TPAD = P * C + 8;  // float2 per l2 row of T (conflict-free halves)
+  static constexpr size_t s_bytes = (size_t)L * C * sizeof(float2);
+  static constexpr size_t t_bytes = (size_t)Q * TPAD * sizeof(float2);
+  static constexpr size_t twa_bytes = (size_t)Q * (P + 1) * sizeof(float2);  // w512^(l2 m1), row pitch 17
+  static constexpr size_t w32_bytes = 16 * sizeof(float2);
+  static constexpr size_t slab_bytes = (size_t)(L / 2 + 1) * C * sizeof(float);
+  // plain: S0 S1 T twa w32; multi-shell: S slab T twa w32
+  static constexpr size_t plain_bytes = 2 * s_bytes + t_bytes + twa_bytes + w32_bytes;
+  static constexpr size_t multi_bytes = s_bytes + slab_bytes + t_bytes + twa_bytes + w32_bytes;
+};
+
+// Twiddle tables from the axis table tw[t] = e^{-2 pi i t / 512} (conjugated for INV).
+template <bool INV>
+__device__ __forceinline__ void sreg_tables(float2* twa, float2* w32, const float2* __restrict__ tw) {
+  using S = Sreg512;
+  for (int i = threadIdx.x; i < S::Q * S::P; i += kThreads) {
+    const int l2 = i / S::P, m1 = i - l2 * S::P;
+    const float2 w = __ldg(tw + l2 * m1);
+    twa[l2 * (S::P + 1) + m1] = INV ? cconj(w) : w;
+  }
+  if (threadIdx.x < 16) {
+    const float2 w = __ldg(tw + 16 * threadIdx.x);
+    w32[threadIdx.x] = INV ? cconj(w) : w;
+  }
+}
+
+// Step A for thread (c, l2); ld(row) returns x[row] of column c (times K^ in
+// the multi-shell pass).
+template <bool INV, class LD>
+__device__ __forceinline__ void sreg_step_a(float2* T, const float2* twa, int c, int l2, LD&& ld) {
+  using S = Sreg512;
+  float2 v[S::P];
+#pragma unroll
+  for (int l1 = 0; l1 < S::P; ++l1) v[l1] = ld(S::Q * l1 + l2);
+  dft16<INV>(v);
+  float2* tr = T + l2 * S::TPAD + c;
+  const float2* tk = twa + l2 * (S::P + 1);
+  tr[0] = v[0];
+#pragma unroll
+  for (int m1 = 1; m1 < S::P; ++m1) tr[m1 * S::C] = cmul(v[m1], tk[m1]);
+}
+
+// Step B for thread (c, m1, h), lane bit 3 = h; rows m1 + 16 kk and
+// m1 + 16 (kk + 16), kk = k + 8 h, k < 8, go to col[row * sl] (if valid).
+template <bool INV>
+__device__ __forceinline__ void sreg_step_b(const float2* T, const float2* w32, int c, int m1, int h, float2* col,
+                                            int64_t sl, bool valid) {
+  using S = Sreg512;
+  float2 y[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) y[j] = T[(2 * j + h) * S::TPAD + m1 * S::C + c];
+  dft16<INV>(y);
+  if (h) {
+#pragma unroll
+    for (int k = 1; k < 16; ++k) y[k] = cmul(y[k], w32[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float2 send = h ? y[k] : y[k + 8];
+    float2 recv;
+    recv.x = __shfl_xor_sync(0xFFFFFFFFu, send.x, 8);
+    recv.y = __shfl_xor_sync(0xFFFFFFFFu, send.y, 8);
+    const float2 a = h ? recv : y[k];
+    const float2 b = h ? y[k + 8] : recv;
+    const int kk = k + 8 * h;
+    if (valid) {
+      col[(int64_t)(m1 + 16 * kk) * sl] = cadd(a, b);
+      col[(int64_t)(m1 + 16 * (kk + 16)) * sl] = csub(a, b);
+    }
+  }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(kThreads, 2)
+    sreg512_kernel(const float2* in, float2* out, StridedView v, const float2* __restrict__ tw) {
+  using S = Sreg512;
+  extern __shared__ float4 smem4[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
+  float2* T = reinterpret_cast<float2*>(sm + 2 * S::s_bytes);
+  float2* twa = reinterpret_cast<float2*>(sm + 2 * S::s_bytes + S::t_bytes);
+  float2* w32 = reinterpret_cast<float2*>(sm + 2 * S::s_bytes + S::t_bytes + S::twa_bytes);
+  auto sbuf = [&](int b) { return reinterpret_cast<float2*>(sm + b * S::s_bytes); };
+  sreg_tables<INV>(twa, w32, tw);
+  const int tid = threadIdx.x;
+  const int ca = tid & 7, l2 = tid >> 3;                    // step A
+  const int cb = tid & 7, hb = (tid >> 3) & 1, m1 = tid >> 4;  // step B
+  const int64_t ntiles = v.n_outer * ((v.inner + kT - 1) / kT);
+  int64_t t = blockIdx.x;
+  if (t < ntiles) stage_strided_tile(sbuf(0), in, v, S::L, t);
+  cp_async_commit();
+  for (int it = 0; t < ntiles; ++it) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) stage_strided_tile(sbuf((it + 1) & 1), in, v, S::L, tn);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const float2* cur = sbuf(it & 1);
+    sreg_step_a<INV>(T, twa, ca, l2, [&](int row) { return cur[row * S::C + ca]; });
+    __syncthreads();
+    const StridedTile io = strided_tile(in, out, v, t);
+    sreg_step_b<INV>(T, w32, cb, m1, hb, io.out + cb, io.sl, cb < io.valid);
+    t = tn;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    zreg512_kernel(const float2* in, float2* out, int64_t out_stride, int nshells, StridedView v,
+                   const float2* __restrict__ tw, KhatArgs K) {
+  using S = Sreg512;
+  constexpr int OZ = S::L / 2 + 1;
+  extern __shared__ float4 smem4[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
+  float2* Sx = reinterpret_cast<float2*>(sm);
+  float* slab = reinterpret_cast<float*>(sm + S::s_bytes);
+  float2* T = reinterpret_cast<float2*>(sm + S::s_bytes + S::slab_bytes);
+  float2* twa = reinterpret_cast<float2*>(sm + S::s_bytes + S::slab_bytes + S::t_bytes);
+  float2* w32 = reinterpret_cast<float2*>(sm + S::s_bytes + S::slab_bytes + S::t_bytes + S::twa_bytes);
+  sreg_tables<true>(twa, w32, tw);
+  const int tid = threadIdx.x;
+  const int ca = tid & 7, l2 = tid >> 3;
+  const int cb = tid & 7, hb = (tid >> 3) & 1, m1 = tid >> 4;
+  const int64_t ntiles = (v.inner + kT - 1) / kT;
+  const bool mul = K.khat != nullptr;
+  // two halves of 4 columns per tile: px is a multiple of 4 and i0 of 8, so
+  // each half lies in one ky row of the spectrum
+  auto load_slab = [&](int s, int64_t tile) {
+    const float* kh = K.khat + (int64_t)s * K.shell_stride;
+    for (int idx = tid; idx < 2 * OZ; idx += kThreads) {
+      const int kzf = idx >> 1, h = idx & 1;
+      const int i = (int)tile * kT + 4 * h;
+      const bool ok = i < v.inner;
+      const int ky = i / K.px, kx = i - (i / K.px) * K.px;
+      const int kyf = min(ky, K.ny - ky);
+      cp_async16(slab + kzf * S::C + 4 * h, ok ? kh + ((int64_t)kzf * K.oy + kyf) * K.px + kx : K.khat, ok);
+    }
+  };
+  auto stage = [&](int64_t tile) {
+    const int i0 = (int)tile * kT;
+    for (int idx = tid; idx < S::L * (S::C / 2); idx += kThreads) {
+      const int l = idx / (S::C / 2), c = (idx % (S::C / 2)) * 2;
+      const bool ok = i0 + c < v.inner;
+      cp_async16(Sx + l * S::C + c, ok ? in + (int64_t)l * v.sl + i0 + c : in, ok);
+    }
+  };
+  int64_t t = blockIdx.x;
+  if (t < ntiles) {
+    stage(t);
+    if (mul) load_slab(0, t);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  for (; t < ntiles; t += gridDim.x) {
+    const int i0 = (int)t * kT;
+    const int valid = min(kT, v.inner - i0);
+    const int64_t tn = t + gridDim.x;
+    for (int s = 0; s < nshells; ++s) {
+      sreg_step_a<true>(T, twa, ca, l2, [&](int row) {
+        const float2 x = Sx[row * S::C + ca];
+        if (!mul) return x;
+        const float m = slab[min(row, S::L - row) * S::C + ca];
+        return make_float2(x.x * m, x.y * m);
+      });
+      __syncthreads();
+      // the slab (and, after the last shell, the tile) has been read: fetch the next
+      if (s + 1 < nshells) {
+        if (mul) load_slab(s + 1, t);
+      } else if (tn < ntiles) {
+        stage(tn);
+        if (mul) load_slab(0, tn);
+      }
+      cp_async_commit();
+      sreg_step_b<true>(T, w32, cb, m1, hb, out + (int64_t)s * out_stride + i0 + cb, v.sl, cb < valid);
+      cp_async_wait<0>();
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace fft
+}  // namespace ck

@@ -1,12 +1,45 @@
 // ck_fft_strided.cu -- instantiations of the strided-axis (y, z) FFT pass and
-// of the multi-shell inverse z pass for the transform lengths of the grids in
-// use (32 ... 512 cells per axis); other lengths use the runtime version.
+// of the multi-shell inverse z pass: 512-point axes run the register
+// two-step kernels (ck_fft_sreg.cuh) unless the caller asks for row-ordered
+// stores, the lengths of the grids in use (32 ... 512 cells per axis) the
+// compile-time Stockham kernels, and any other length the runtime version.
+//
+// Row-ordered stores: the Stockham kernel's last iteration writes 8
+// consecutive rows of the tile per warp instruction, the register kernel's
+// step B rows 128 apart.  On the 16-shell inverse y pass (8.6 GB in place,
+// rows 2 KB apart) the first sustained 5.2 TB/s on a GB300 and the second
+// 4.0 TB/s, while on single-field passes the register kernel is faster.
 #include <algorithm>
 
 #include "ck_fft_core.cuh"
+#include "ck_fft_sreg.cuh"
 
 namespace ck {
 namespace fft {
+
+static void run_sreg512(bool inv, const float2* in, float2* out, const StridedView& v, const float2* tw, int sm_count,
+                        cudaStream_t st) {
+  const size_t sm = Sreg512::plain_bytes;
+  const int64_t ntiles = v.n_outer * ((v.inner + kT - 1) / kT);
+  if (inv) {
+    allow_smem(sreg512_kernel<true>, sm);
+    sreg512_kernel<true><<<persistent_grid(sreg512_kernel<true>, sm, sm_count, ntiles), kThreads, sm, st>>>(in, out, v,
+                                                                                                          tw);
+  } else {
+    allow_smem(sreg512_kernel<false>, sm);
+    sreg512_kernel<false><<<persistent_grid(sreg512_kernel<false>, sm, sm_count, ntiles), kThreads, sm, st>>>(
+        in, out, v, tw);
+  }
+}
+
+static void run_zreg512(const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
+                        const float2* tw, const KhatArgs& K, int sm_count, cudaStream_t st) {
+  const size_t sm = Sreg512::multi_bytes;
+  const int64_t ntiles = (v.inner + kT - 1) / kT;
+  allow_smem(zreg512_kernel, sm);
+  zreg512_kernel<<<persistent_grid(zreg512_kernel, sm, sm_count, ntiles), kThreads, sm, st>>>(in, out, out_stride,
+                                                                                              nshells, v, tw, K);
+}
 
 template <int LC>
 static void run_strided(bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
@@ -39,7 +72,11 @@ static void run_zmulti(const float2* in, float2* out, int64_t out_stride, int ns
 #define CK_LENGTHS(X) X(32) X(128) X(160) X(192) X(240) X(256) X(288) X(320) X(384) X(512)
 
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, int sm_count, cudaStream_t st) {
+                    const float2* stw, const float2* tw, bool row_ordered, int sm_count, cudaStream_t st) {
+  if (L == Sreg512::L && !row_ordered) {
+    run_sreg512(inv, in, out, v, tw, sm_count, st);
+    return;
+  }
   switch (L) {
 #define CK_CASE(N) case N: run_strided<N>(inv, in, out, v, f, stw, sm_count, st); return;
     CK_LENGTHS(CK_CASE)
@@ -49,7 +86,12 @@ void launch_strided(int L, bool inv, const float2* in, float2* out, const Stride
 }
 
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
-                   const FftLen& f, const float2* stw, const KhatArgs& K, int sm_count, cudaStream_t st) {
+                   const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
+                   cudaStream_t st) {
+  if (L == Sreg512::L) {
+    run_zreg512(in, out, out_stride, nshells, v, tw, K, sm_count, st);
+    return;
+  }
   switch (L) {
 #define CK_CASE(N) case N: run_zmulti<N>(in, out, out_stride, nshells, v, f, stw, K, sm_count, st); return;
     CK_LENGTHS(CK_CASE)
