@@ -2,16 +2,17 @@
 // with the butterflies in registers, for the passes of Sec. 2.4's FFT
 // convolution on 512-cell axes.
 //
-// A tile is C = 8 adjacent columns x 512 rows of a strided view, staged in
-// shared memory as S[row][c].  With l = 32 l1 + l2 and m = m1 + 16 m2,
+// A tile is C adjacent columns (C = 8 or 16) x 512 rows of a strided view,
+// staged in shared memory as S[row][c]; a CTA has 32 C threads.  With
+// l = 32 l1 + l2 and m = m1 + 16 m2,
 //   X[m1 + 16 m2] = sum_l2 w32^(l2 m2) w512^(l2 m1) sum_l1 w16^(l1 m1) x[32 l1 + l2]
 // (w_n = e^{-+2 pi i / n}).  Step A: thread (c, l2) runs the 16-point DFT
 // over l1 and applies w512^(l2 m1), writing the padded transpose T.  Step
 // B: threads (c, m1, h) take the even (h = 0) or odd (h = 1) l2 of column
 // m1 of T, run a 16-point DFT (E or O), the odd one multiplied by w32^k;
-// one exchange with the partner lane (lane ^ 8) gives each thread half of
+// one exchange with the partner lane (lane ^ C) gives each thread half of
 // X[m1 + 16 k] = E[k] + w32^k O[k] and X[m1 + 16 (k + 16)] = E[k] - w32^k O[k],
-// which go straight to global memory (8 columns = 64 contiguous bytes).
+// which go straight to global memory (C columns = 8 C contiguous bytes).
 //
 // sreg512_kernel: one transform per tile, double-buffered staging (in
 // place allowed).  zreg512_kernel: the first inverse pass of Eqs. 9-10: the
@@ -24,9 +25,12 @@
 namespace ck {
 namespace fft {
 
-struct Sreg512 {
-  static constexpr int L = 512, P = 16, Q = 32, C = 8;
-  static constexpr int TPAD = P * C + 8;  // float2 per l2 row of T (conflict-free halves)
+template <int C>
+struct Sreg {
+  static_assert(C == 8 || C == 16, "tile widths");
+  static constexpr int L = 512, P = 16, Q = 32;
+  static constexpr int NT = 32 * C;       // threads per CTA
+  static constexpr int TPAD = P * C + 8;  // float2 per l2 row of T (conflict-free half-warps)
   static constexpr size_t s_bytes = (size_t)L * C * sizeof(float2);
   static constexpr size_t t_bytes = (size_t)Q * TPAD * sizeof(float2);
   static constexpr size_t twa_bytes = (size_t)Q * (P + 1) * sizeof(float2);  // w512^(l2 m1), row pitch 17
@@ -38,10 +42,10 @@ struct Sreg512 {
 };
 
 // Twiddle tables from the axis table tw[t] = e^{-2 pi i t / 512} (conjugated for INV).
-template <bool INV>
+template <int C, bool INV>
 __device__ __forceinline__ void sreg_tables(float2* twa, float2* w32, const float2* __restrict__ tw) {
-  using S = Sreg512;
-  for (int i = threadIdx.x; i < S::Q * S::P; i += kThreads) {
+  using S = Sreg<C>;
+  for (int i = threadIdx.x; i < S::Q * S::P; i += S::NT) {
     const int l2 = i / S::P, m1 = i - l2 * S::P;
     const float2 w = __ldg(tw + l2 * m1);
     twa[l2 * (S::P + 1) + m1] = INV ? cconj(w) : w;
@@ -52,89 +56,111 @@ __device__ __forceinline__ void sreg_tables(float2* twa, float2* w32, const floa
   }
 }
 
-// Step A for thread (c, l2); ld(row) returns x[row] of column c (times K^ in
-// the multi-shell pass).
-template <bool INV, class LD>
+// Step A for thread (c, l2); ld(l1) returns x[32 l1 + l2] of column c (times
+// K^ in the multi-shell pass).
+template <int C, bool INV, class LD>
 __device__ __forceinline__ void sreg_step_a(float2* T, const float2* twa, int c, int l2, LD&& ld) {
-  using S = Sreg512;
+  using S = Sreg<C>;
   float2 v[S::P];
 #pragma unroll
-  for (int l1 = 0; l1 < S::P; ++l1) v[l1] = ld(S::Q * l1 + l2);
+  for (int l1 = 0; l1 < S::P; ++l1) v[l1] = ld(l1);
   dft16<INV>(v);
   float2* tr = T + l2 * S::TPAD + c;
   const float2* tk = twa + l2 * (S::P + 1);
   tr[0] = v[0];
 #pragma unroll
-  for (int m1 = 1; m1 < S::P; ++m1) tr[m1 * S::C] = cmul(v[m1], tk[m1]);
+  for (int m1 = 1; m1 < S::P; ++m1) tr[m1 * C] = cmul(v[m1], tk[m1]);
 }
 
-// Step B for thread (c, m1, h), lane bit 3 = h; rows m1 + 16 kk and
+// Step B for thread (c, m1, h), lane bit log2(C) = h; rows m1 + 16 kk and
 // m1 + 16 (kk + 16), kk = k + 8 h, k < 8, go to col[row * sl] (if valid).
-template <bool INV>
+template <int C, bool INV>
 __device__ __forceinline__ void sreg_step_b(const float2* T, const float2* w32, int c, int m1, int h, float2* col,
                                             int64_t sl, bool valid) {
-  using S = Sreg512;
+  using S = Sreg<C>;
   float2 y[16];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) y[j] = T[(2 * j + h) * S::TPAD + m1 * S::C + c];
+  for (int j = 0; j < 16; ++j) y[j] = T[(2 * j + h) * S::TPAD + m1 * C + c];
   dft16<INV>(y);
   if (h) {
 #pragma unroll
     for (int k = 1; k < 16; ++k) y[k] = cmul(y[k], w32[k]);
   }
+  float2* p = col + (int64_t)(m1 + 128 * h) * sl;  // row m1 + 16 kk for k = 0
+  const int64_t s16 = 16 * sl, s256 = 256 * sl;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const float2 send = h ? y[k] : y[k + 8];
     float2 recv;
-    recv.x = __shfl_xor_sync(0xFFFFFFFFu, send.x, 8);
-    recv.y = __shfl_xor_sync(0xFFFFFFFFu, send.y, 8);
+    recv.x = __shfl_xor_sync(0xFFFFFFFFu, send.x, C);
+    recv.y = __shfl_xor_sync(0xFFFFFFFFu, send.y, C);
     const float2 a = h ? recv : y[k];
     const float2 b = h ? y[k + 8] : recv;
-    const int kk = k + 8 * h;
     if (valid) {
-      col[(int64_t)(m1 + 16 * kk) * sl] = cadd(a, b);
-      col[(int64_t)(m1 + 16 * (kk + 16)) * sl] = csub(a, b);
+      p[0] = cadd(a, b);
+      p[s256] = csub(a, b);
     }
+    p += s16;
   }
 }
 
-template <bool INV>
-__global__ void __launch_bounds__(kThreads, 2)
+// Tile `tile` of a strided view (C columns x 512 rows) into S[row][c] with
+// 16-byte cp.async copies; columns past the view's end are zero-filled.
+template <int C>
+__device__ __forceinline__ void sreg_stage(float2* s, const float2* in, const StridedView& v, int64_t tile) {
+  using S = Sreg<C>;
+  const int tpo = (v.inner + C - 1) / C;
+  const int64_t o = tile / tpo;
+  const int i0 = (int)(tile - o * tpo) * C;
+  const float2* base = in + o * v.so + i0;
+  for (int idx = threadIdx.x; idx < S::L * (C / 2); idx += S::NT) {
+    const int l = idx / (C / 2), cp = idx % (C / 2);
+    const bool ok = i0 + 2 * cp < v.inner;
+    cp_async16(s + l * C + 2 * cp, ok ? base + (int64_t)l * v.sl + 2 * cp : in, ok);
+  }
+}
+
+template <int C, bool INV>
+__global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
     sreg512_kernel(const float2* in, float2* out, StridedView v, const float2* __restrict__ tw) {
-  using S = Sreg512;
+  using S = Sreg<C>;
   extern __shared__ float4 smem4[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
   float2* T = reinterpret_cast<float2*>(sm + 2 * S::s_bytes);
   float2* twa = reinterpret_cast<float2*>(sm + 2 * S::s_bytes + S::t_bytes);
   float2* w32 = reinterpret_cast<float2*>(sm + 2 * S::s_bytes + S::t_bytes + S::twa_bytes);
   auto sbuf = [&](int b) { return reinterpret_cast<float2*>(sm + b * S::s_bytes); };
-  sreg_tables<INV>(twa, w32, tw);
+  sreg_tables<C, INV>(twa, w32, tw);
   const int tid = threadIdx.x;
-  const int ca = tid & 7, l2 = tid >> 3;                    // step A
-  const int cb = tid & 7, hb = (tid >> 3) & 1, m1 = tid >> 4;  // step B
-  const int64_t ntiles = v.n_outer * ((v.inner + kT - 1) / kT);
+  const int ca = tid % C, l2 = tid / C;                                // step A
+  const int cb = tid % C, hb = (tid / C) & 1, m1 = tid / (2 * C);      // step B
+  const int tpo = (v.inner + C - 1) / C;
+  const int64_t ntiles = v.n_outer * tpo;
   int64_t t = blockIdx.x;
-  if (t < ntiles) stage_strided_tile(sbuf(0), in, v, S::L, t);
+  if (t < ntiles) sreg_stage<C>(sbuf(0), in, v, t);
   cp_async_commit();
   for (int it = 0; t < ntiles; ++it) {
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) stage_strided_tile(sbuf((it + 1) & 1), in, v, S::L, tn);
+    if (tn < ntiles) sreg_stage<C>(sbuf((it + 1) & 1), in, v, tn);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
     const float2* cur = sbuf(it & 1);
-    sreg_step_a<INV>(T, twa, ca, l2, [&](int row) { return cur[row * S::C + ca]; });
+    const float2* cc = cur + l2 * C + ca;
+    sreg_step_a<C, INV>(T, twa, ca, l2, [&](int l1) { return cc[S::Q * l1 * C]; });
     __syncthreads();
-    const StridedTile io = strided_tile(in, out, v, t);
-    sreg_step_b<INV>(T, w32, cb, m1, hb, io.out + cb, io.sl, cb < io.valid);
+    const int64_t o = t / tpo;
+    const int i0 = (int)(t - o * tpo) * C;
+    sreg_step_b<C, INV>(T, w32, cb, m1, hb, out + o * v.so + i0 + cb, v.sl, i0 + cb < v.inner);
     t = tn;
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+template <int C>
+__global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
     zreg512_kernel(const float2* in, float2* out, int64_t out_stride, int nshells, StridedView v,
                    const float2* __restrict__ tw, KhatArgs K) {
-  using S = Sreg512;
+  using S = Sreg<C>;
   constexpr int OZ = S::L / 2 + 1;
   extern __shared__ float4 smem4[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
@@ -143,31 +169,31 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* T = reinterpret_cast<float2*>(sm + S::s_bytes + S::slab_bytes);
   float2* twa = reinterpret_cast<float2*>(sm + S::s_bytes + S::slab_bytes + S::t_bytes);
   float2* w32 = reinterpret_cast<float2*>(sm + S::s_bytes + S::slab_bytes + S::t_bytes + S::twa_bytes);
-  sreg_tables<true>(twa, w32, tw);
+  sreg_tables<C, true>(twa, w32, tw);
   const int tid = threadIdx.x;
-  const int ca = tid & 7, l2 = tid >> 3;
-  const int cb = tid & 7, hb = (tid >> 3) & 1, m1 = tid >> 4;
-  const int64_t ntiles = (v.inner + kT - 1) / kT;
+  const int ca = tid % C, l2 = tid / C;
+  const int cb = tid % C, hb = (tid / C) & 1, m1 = tid / (2 * C);
+  const int64_t ntiles = (v.inner + C - 1) / C;
   const bool mul = K.khat != nullptr;
-  // two halves of 4 columns per tile: px is a multiple of 4 and i0 of 8, so
-  // each half lies in one ky row of the spectrum
+  // C / 4 groups of 4 columns per tile: px is a multiple of 4 and i0 of C,
+  // so each group lies in one ky row of the spectrum
   auto load_slab = [&](int s, int64_t tile) {
     const float* kh = K.khat + (int64_t)s * K.shell_stride;
-    for (int idx = tid; idx < 2 * OZ; idx += kThreads) {
-      const int kzf = idx >> 1, h = idx & 1;
-      const int i = (int)tile * kT + 4 * h;
+    for (int idx = tid; idx < (C / 4) * OZ; idx += S::NT) {
+      const int kzf = idx / (C / 4), h = idx % (C / 4);
+      const int i = (int)tile * C + 4 * h;
       const bool ok = i < v.inner;
       const int ky = i / K.px, kx = i - (i / K.px) * K.px;
       const int kyf = min(ky, K.ny - ky);
-      cp_async16(slab + kzf * S::C + 4 * h, ok ? kh + ((int64_t)kzf * K.oy + kyf) * K.px + kx : K.khat, ok);
+      cp_async16(slab + kzf * C + 4 * h, ok ? kh + ((int64_t)kzf * K.oy + kyf) * K.px + kx : K.khat, ok);
     }
   };
   auto stage = [&](int64_t tile) {
-    const int i0 = (int)tile * kT;
-    for (int idx = tid; idx < S::L * (S::C / 2); idx += kThreads) {
-      const int l = idx / (S::C / 2), c = (idx % (S::C / 2)) * 2;
+    const int i0 = (int)tile * C;
+    for (int idx = tid; idx < S::L * (C / 2); idx += S::NT) {
+      const int l = idx / (C / 2), c = (idx % (C / 2)) * 2;
       const bool ok = i0 + c < v.inner;
-      cp_async16(Sx + l * S::C + c, ok ? in + (int64_t)l * v.sl + i0 + c : in, ok);
+      cp_async16(Sx + l * C + c, ok ? in + (int64_t)l * v.sl + i0 + c : in, ok);
     }
   };
   int64_t t = blockIdx.x;
@@ -179,14 +205,16 @@ __global__ void __launch_bounds__(kThreads, 2)
   cp_async_wait<0>();
   __syncthreads();
   for (; t < ntiles; t += gridDim.x) {
-    const int i0 = (int)t * kT;
-    const int valid = min(kT, v.inner - i0);
+    const int i0 = (int)t * C;
     const int64_t tn = t + gridDim.x;
     for (int s = 0; s < nshells; ++s) {
-      sreg_step_a<true>(T, twa, ca, l2, [&](int row) {
-        const float2 x = Sx[row * S::C + ca];
+      // K^ depends on min(kz, 512 - kz): kz = 32 l1 + l2 for l1 < 8, 512 - kz beyond
+      const float2* xc = Sx + l2 * C + ca;
+      const float* sa = slab + l2 * C + ca;
+      sreg_step_a<C, true>(T, twa, ca, l2, [&](int l1) {
+        const float2 x = xc[S::Q * l1 * C];
         if (!mul) return x;
-        const float m = slab[min(row, S::L - row) * S::C + ca];
+        const float m = l1 < 8 ? sa[S::Q * l1 * C] : slab[(S::L - S::Q * l1 - l2) * C + ca];
         return make_float2(x.x * m, x.y * m);
       });
       __syncthreads();
@@ -198,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (mul) load_slab(0, tn);
       }
       cp_async_commit();
-      sreg_step_b<true>(T, w32, cb, m1, hb, out + (int64_t)s * out_stride + i0 + cb, v.sl, cb < valid);
+      sreg_step_b<C, true>(T, w32, cb, m1, hb, out + (int64_t)s * out_stride + i0 + cb, v.sl, i0 + cb < v.inner);
       cp_async_wait<0>();
       __syncthreads();
     }

@@ -17,28 +17,44 @@
 namespace ck {
 namespace fft {
 
+// Tile width of the register kernels (columns per tile, 32 threads per column).
+constexpr int kSregC = 8;
+constexpr int kZregC = 8;
+
+template <int C>
 static void run_sreg512(bool inv, const float2* in, float2* out, const StridedView& v, const float2* tw, int sm_count,
                         cudaStream_t st) {
-  const size_t sm = Sreg512::plain_bytes;
-  const int64_t ntiles = v.n_outer * ((v.inner + kT - 1) / kT);
-  if (inv) {
-    allow_smem(sreg512_kernel<true>, sm);
-    sreg512_kernel<true><<<persistent_grid(sreg512_kernel<true>, sm, sm_count, ntiles), kThreads, sm, st>>>(in, out, v,
-                                                                                                          tw);
-  } else {
-    allow_smem(sreg512_kernel<false>, sm);
-    sreg512_kernel<false><<<persistent_grid(sreg512_kernel<false>, sm, sm_count, ntiles), kThreads, sm, st>>>(
-        in, out, v, tw);
-  }
+  using S = Sreg<C>;
+  const size_t sm = S::plain_bytes;
+  const int64_t ntiles = v.n_outer * ((v.inner + C - 1) / C);
+  auto go = [&](auto kernel) {
+    allow_smem(kernel, sm);
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, S::NT, sm) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * occ));
+    kernel<<<grid, S::NT, sm, st>>>(in, out, v, tw);
+  };
+  if (inv) go(sreg512_kernel<C, true>);
+  else go(sreg512_kernel<C, false>);
 }
 
+template <int C>
 static void run_zreg512(const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                         const float2* tw, const KhatArgs& K, int sm_count, cudaStream_t st) {
-  const size_t sm = Sreg512::multi_bytes;
-  const int64_t ntiles = (v.inner + kT - 1) / kT;
-  allow_smem(zreg512_kernel, sm);
-  zreg512_kernel<<<persistent_grid(zreg512_kernel, sm, sm_count, ntiles), kThreads, sm, st>>>(in, out, out_stride,
-                                                                                              nshells, v, tw, K);
+  using S = Sreg<C>;
+  const size_t sm = S::multi_bytes;
+  const int64_t ntiles = (v.inner + C - 1) / C;
+  allow_smem(zreg512_kernel<C>, sm);
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, zreg512_kernel<C>, S::NT, sm) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * occ));
+  zreg512_kernel<C><<<grid, S::NT, sm, st>>>(in, out, out_stride, nshells, v, tw, K);
 }
 
 template <int LC>
@@ -73,8 +89,8 @@ static void run_zmulti(const float2* in, float2* out, int64_t out_stride, int ns
 
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
                     const float2* stw, const float2* tw, bool row_ordered, int sm_count, cudaStream_t st) {
-  if (L == Sreg512::L && !row_ordered) {
-    run_sreg512(inv, in, out, v, tw, sm_count, st);
+  if (L == 512 && !row_ordered) {
+    run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st);
     return;
   }
   switch (L) {
@@ -88,8 +104,8 @@ void launch_strided(int L, bool inv, const float2* in, float2* out, const Stride
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
                    cudaStream_t st) {
-  if (L == Sreg512::L) {
-    run_zreg512(in, out, out_stride, nshells, v, tw, K, sm_count, st);
+  if (L == 512) {
+    run_zreg512<kZregC>(in, out, out_stride, nshells, v, tw, K, sm_count, st);
     return;
   }
   switch (L) {

@@ -319,11 +319,15 @@ __global__ void __launch_bounds__(kThreads, 2)
 // from the staged rows, runs a P-point DFT and applies the twiddles; the
 // results go through a padded shared transpose T; step B (one thread per
 // line and m1) runs the Q-point DFT and writes the real row
-// x[2m] = Re z[m], x[2m+1] = Im z[m] into the store W, which overlays T.
-// A tile is LT = 256 / max(P, Q) lines: ROWS = LT / NS grid rows of every
-// shell, all transformed at once.  One thread stages the next tile with
-// bulk asynchronous copies (one per row of X[0..M+1], and one for the
-// tile's N cells) completing on the buffer's mbarrier; waits are bounded.
+// x[2m] = Re z[m], x[2m+1] = Im z[m] into the store W, which takes the
+// place of the tile's staged rows (consumed by step A).  A tile is
+// LT = 256 / max(P, Q) lines: ROWS = LT / NS grid rows of every shell, all
+// transformed at once; three block barriers per tile.  Right after a tile's
+// first barrier, one thread stages the next tile into the other buffer
+// (whose store the previous tile's sums have read) with bulk asynchronous
+// copies, one per padded half-spectrum row (px = M + 4 complex values) and
+// one for the tile's N cells, completing on the buffer's mbarrier; waits are
+// bounded.
 //
 // In the sums, k-slot t of a k-step holds cell c0 + 2t and slot t + 4 cell
 // c0 + 2t + 1, so that each lane reads its two cells with one 8-byte load.
@@ -335,7 +339,7 @@ struct XcrShape {
   static constexpr int LT = kThreads / (P > Q ? P : Q);  // lines per tile
   static constexpr int ROWS = LT / NS;                   // grid rows per tile
   static constexpr int TC = ROWS * NX;                   // cells per tile
-  static constexpr int LP = stage_pitch(M);              // staged row pitch (float2)
+  static constexpr int LP = M + 4;                       // staged row pitch (float2): the padded row, px
   static constexpr int TP = Q * (P + 1);                 // transpose float2 per line
   static constexpr int WP = TC + 8;                      // store pitch per shell (floats), 8 mod 32
   static constexpr size_t s_bytes = align16((size_t)LT * LP * sizeof(float2));
@@ -344,12 +348,12 @@ struct XcrShape {
   static constexpr size_t t_off = twq_off + align16((size_t)Q * (P + 1) * sizeof(float2));
   static constexpr size_t nb_off = t_off + align16((size_t)LT * TP * sizeof(float2));
   static constexpr size_t nb_bytes = align16((size_t)TC * sizeof(float));
-  static constexpr size_t bar_off = nb_off + 3 * nb_bytes;
+  static constexpr size_t bar_off = nb_off + 2 * nb_bytes;
   static constexpr size_t red_bytes = (size_t)kWarps * NS * (NS + 1) * sizeof(double);
   static constexpr size_t total0 = bar_off + 16;
   static constexpr size_t total = total0 > red_bytes ? total0 : red_bytes;
   static_assert(ROWS >= 1 && LT % NS == 0, "a tile holds whole rows of every shell");
-  static_assert((size_t)NS * WP * sizeof(float) <= (size_t)LT * TP * sizeof(float2), "the store fits over T");
+  static_assert((size_t)NS * WP * sizeof(float) <= s_bytes, "the store fits in a staging buffer");
   static_assert(TC % 32 == 0, "whole k-steps per tile and a conflict-free store pitch");
   static_assert((LP * sizeof(float2)) % 16 == 0 && (NX * sizeof(float)) % 16 == 0, "16-byte bulk copies");
   static_assert(red_bytes <= bar_off, "the final sum does not reach the barriers");
@@ -374,7 +378,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* twu = reinterpret_cast<float2*>(sm + S::twu_off);
   float2* twq = reinterpret_cast<float2*>(sm + S::twq_off);
   float2* T = reinterpret_cast<float2*>(sm + S::t_off);
-  float* W = reinterpret_cast<float*>(sm + S::t_off);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::bar_off);
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -424,13 +427,15 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (t < ntiles) issued = 1;
   for (int kt = 0; t < ntiles; t += gridDim.x, ++kt) {
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) {
-      if (tid == 0) stage((kt + 1) & 1, (kt + 1) % 3, tn);
-      issued = kt + 2;
-    }
     const bool ok = mbar_wait(&full[kt & 1], (uint32_t)(kt >> 1) & 1u, status);
     if (__syncthreads_or(!ok)) break;
     used = kt + 1;
+    // every warp is past the previous tile's sums: its buffers take the next tile
+    if (tn < ntiles) {
+      if (tid == 0) stage((kt + 1) & 1, (kt + 1) & 1, tn);
+      issued = kt + 2;
+    }
+    float* W = reinterpret_cast<float*>(sbuf(kt & 1));
     const int64_t r0 = t * ROWS;
     const int vc = (int)(rows - r0 < ROWS ? rows - r0 : ROWS) * NX;  // cells of the tile with data
     // step A: unpack Z[Q k1 + k2] = (X[k] + conj X[M-k]) + i e^{2 pi i k/NX} (X[k] - conj X[M-k]),
@@ -452,16 +457,13 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int m1 = 1; m1 < P; ++m1) tr[m1] = cmul(v[m1], tk[m1]);
     }
-    __syncthreads();
+    __syncthreads();  // T complete; the staged rows are consumed
     // step B: Q-point inverse DFT over k2 of column m1
-    float2 z[Q];
     const int lb = tid / P, m1 = tid - lb * P;
     if (tid < LT * P) {
+      float2 z[Q];
 #pragma unroll
       for (int k2 = 0; k2 < Q; ++k2) z[k2] = T[lb * TP + k2 * (P + 1) + m1];
-    }
-    __syncthreads();  // W overlays T
-    if (tid < LT * P) {
       dft<Q, true>(z);
       const int sh = lb / ROWS, i = lb - sh * ROWS;
       float* wr = W + sh * WP + i * NX + 2 * m1;
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     // rank-8 updates on the tensor cores (see xc_contract_kernel)
     {
-      const float* nb = nbuf(kt % 3);
+      const float* nb = nbuf(kt & 1);
 #pragma unroll
       for (int j = 0; j <= NTW; ++j)
 #pragma unroll
@@ -520,8 +522,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         since = 0;
       }
     }
-    // the next tile's step A writes T only after its first barrier, which
-    // every warp reaches after this tile's sums; its N goes to a third buffer
+    // the next tile's step A writes T, and its staging overwrites this
+    // tile's store, only after its first barrier, which every warp reaches
+    // after these sums
   }
   // after a timed-out wait: let the copies already issued land (bounded)
   if (tid == 0)

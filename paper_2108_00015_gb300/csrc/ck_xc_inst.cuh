@@ -35,6 +35,7 @@ template <int P, int Q, int NS>
 cudaError_t run_xcr(const float2* spec, int64_t spec_stride, const float* w0, int px, int64_t rows, int nshells,
                     const float2* tw, int max_ctas, int* ctas, double* partials, int* status, cudaStream_t st) {
   using S = XcrShape<P, Q, NS>;
+  if (px != S::LP) return cudaErrorInvalidValue;  // whole padded rows are staged
   *ctas = xc_ctas((rows + S::ROWS - 1) / S::ROWS, max_ctas);
   cudaError_t e = cudaFuncSetAttribute(xcr_contract_kernel<P, Q, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)S::total);
