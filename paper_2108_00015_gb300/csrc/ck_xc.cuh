@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // x[2m] = Re z[m], x[2m+1] = Im z[m] into the store W, which takes the
 // place of the tile's staged rows (consumed by step A).  A tile is
 // LT = 256 / max(P, Q) lines: ROWS = LT / NS grid rows of every shell, all
-// transformed at once; three block barriers per tile.  Right after a tile's
+// transformed at once; two block barriers per tile (three when P != Q).  Right after a tile's
 // first barrier, one thread stages the next tile into the other buffer
 // (whose store the previous tile's sums have read) with bulk asynchronous
 // copies, one per padded half-spectrum row (px = M + 4 complex values) and
@@ -354,6 +354,8 @@ struct XcrShape {
   static constexpr size_t total = total0 > red_bytes ? total0 : red_bytes;
   static_assert(ROWS >= 1 && LT % NS == 0, "a tile holds whole rows of every shell");
   static_assert((size_t)NS * WP * sizeof(float) <= s_bytes, "the store fits in a staging buffer");
+  // steps A and B of a line in one warp, and W[line] over the line's staged row
+  static constexpr bool kWarpLocal = P == Q && ROWS == 1 && WP * sizeof(float) == LP * sizeof(float2);
   static_assert(TC % 32 == 0, "whole k-steps per tile and a conflict-free store pitch");
   static_assert((LP * sizeof(float2)) % 16 == 0 && (NX * sizeof(float)) % 16 == 0, "16-byte bulk copies");
   static_assert(red_bytes <= bar_off, "the final sum does not reach the barriers");
@@ -397,18 +399,27 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int64_t ntiles = (rows + ROWS - 1) / ROWS;
   // thread 0: bulk copies of tile t into staging buffer b and N buffer nbi
+  // warp 0: lane 0 arms the barrier, then the lanes issue one copy each
   auto stage = [&](int b, int nbi, int64_t t) {
     const int64_t r0 = t * ROWS;
     const int vr = (int)(rows - r0 < ROWS ? rows - r0 : ROWS);
     const uint32_t row_bytes = LP * sizeof(float2);
-    mbar_arrive_expect_tx(&full[b], (uint32_t)(nsv * vr) * row_bytes + (uint32_t)(vr * NX * sizeof(float)));
-    for (int sh = 0; sh < nsv; ++sh)
-      for (int i = 0; i < vr; ++i)
+    if (lane == 0)
+      mbar_arrive_expect_tx(&full[b], (uint32_t)(nsv * vr) * row_bytes + (uint32_t)(vr * NX * sizeof(float)));
+    __syncwarp();
+    const int nrows = nsv * vr;
+    for (int j = lane; j <= nrows; j += 32) {
+      if (j < nrows) {
+        const int sh = j / vr, i = j - sh * vr;
         bulk_g2s(sbuf(b) + (sh * ROWS + i) * LP, spec + sh * spec_stride + (r0 + i) * px, row_bytes, &full[b]);
-    bulk_g2s(nbuf(nbi), w0 + r0 * NX, (uint32_t)(vr * NX * sizeof(float)), &full[b]);
+      } else {
+        bulk_g2s(nbuf(nbi), w0 + r0 * NX, (uint32_t)(vr * NX * sizeof(float)), &full[b]);
+      }
+    }
   };
 
-  float dacc32[NTW + 1][4];  // this tile
+  float dacc32[NTW + 1][4];  // this tile: hi * hi
+  float dsm32[NTW + 1][4];   // this tile: hi * lo + lo * hi (a second chain of MMAs)
   float mid[NTW + 1][4];     // tiles since the last FP64 flush
   double dacc[NTW + 1][4];
 #pragma unroll
@@ -423,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   int64_t t = blockIdx.x;
   int issued = 0, used = 0;  // tiles staged / consumed by this CTA
-  if (t < ntiles && tid == 0) stage(0, 0, t);
+  if (t < ntiles && warp == 0) stage(0, 0, t);
   if (t < ntiles) issued = 1;
   for (int kt = 0; t < ntiles; t += gridDim.x, ++kt) {
     const int64_t tn = t + gridDim.x;
@@ -432,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     used = kt + 1;
     // every warp is past the previous tile's sums: its buffers take the next tile
     if (tn < ntiles) {
-      if (tid == 0) stage((kt + 1) & 1, (kt + 1) & 1, tn);
+      if (warp == 0) stage((kt + 1) & 1, (kt + 1) & 1, tn);
       issued = kt + 2;
     }
     float* W = reinterpret_cast<float*>(sbuf(kt & 1));
@@ -457,7 +468,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int m1 = 1; m1 < P; ++m1) tr[m1] = cmul(v[m1], tk[m1]);
     }
-    __syncthreads();  // T complete; the staged rows are consumed
+    // T complete, staged rows consumed.  With P == Q and one grid row per
+    // tile, the threads of a line in steps A and B are the same warp's, and
+    // the store row W[shell] covers exactly the bytes of that line's staged
+    // row: the warp alone touches them, so it need not wait for the others.
+    if constexpr (S::kWarpLocal) __syncwarp();
+    else __syncthreads();
     // step B: Q-point inverse DFT over k2 of column m1
     const int lb = tid / P, m1 = tid - lb * P;
     if (tid < LT * P) {
@@ -477,7 +493,10 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int j = 0; j <= NTW; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) dacc32[j][e] = 0.0f;
+        for (int e = 0; e < 4; ++e) {
+          dacc32[j][e] = 0.0f;
+          dsm32[j][e] = 0.0f;
+        }
 #pragma unroll 2
       for (int c0 = 8 * warp; c0 < TC; c0 += 8 * kWarps) {
         const int c = c0 + 2 * tq;
@@ -497,20 +516,20 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         // n-tile 0: B[k][g] = W_g; n-tile 1: B[k][g] = W_{g+8}; last: ones column
         mma_tf32(dacc32[0], ah, bh[0], bh[1]);
-        mma_tf32(dacc32[0], ah, bl[0], bl[1]);
-        mma_tf32(dacc32[0], al, bh[0], bh[1]);
+        mma_tf32(dsm32[0], ah, bl[0], bl[1]);
+        mma_tf32(dsm32[0], al, bh[0], bh[1]);
         if constexpr (NTW == 2) {
           mma_tf32(dacc32[1], ah, bh[2], bh[3]);
-          mma_tf32(dacc32[1], ah, bl[2], bl[3]);
-          mma_tf32(dacc32[1], al, bh[2], bh[3]);
+          mma_tf32(dsm32[1], ah, bl[2], bl[3]);
+          mma_tf32(dsm32[1], al, bh[2], bh[3]);
         }
         mma_tf32(dacc32[NTW], ah, ones, ones);
-        mma_tf32(dacc32[NTW], al, ones, ones);
+        mma_tf32(dsm32[NTW], al, ones, ones);
       }
 #pragma unroll
       for (int j = 0; j <= NTW; ++j)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) mid[j][e] += dacc32[j][e];
+        for (int e = 0; e < 4; ++e) mid[j][e] += dacc32[j][e] + dsm32[j][e];
       if (++since == kFlushTiles) {
 #pragma unroll
         for (int j = 0; j <= NTW; ++j)
