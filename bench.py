@@ -50,6 +50,9 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32"],
+                    help="headline form: mixed split-TF32 tensor-core sums (fused pass) or plain FP32")
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form beside the headline")
     return ap.parse_args()
 
 
@@ -196,7 +199,11 @@ def run_gb300(args):
     w = workload(args.workload)
     orders = _orders(args, w)
     g = w["grid"]
-    plan = Plan(g.n, g.origin, g.cell, g.periodic, w["shells"], w["width"], max_order=max(orders))
+    precision = args.precision
+    if precision == "split_tf32" and (max(orders) > 3 or len(w["shells"]) > 16):
+        precision = "fp32"  # the mixed form covers orders <= 3 with <= 16 shells
+    plan = Plan(g.n, g.origin, g.cell, g.periodic, w["shells"], w["width"], max_order=max(orders),
+                precision=precision)
     d, r = w["data"], w["randoms"]
     dev = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
     dx, dy, dz = dev(d.x), dev(d.y), dev(d.z)
@@ -314,17 +321,53 @@ def run_gb300(args):
         cpu = {"value": round(ms, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample,
                "wall_s": round(time.perf_counter() - t0, 1)}
 
+    plan.close()
+    forms = {precision: {"ms_per_catalog": round(t_ms / (args.steps * ws), 4)}}
+    if precision != "fp32" and not args.no_plain:
+        # the plain FP32 form on the same catalog, timed the same way
+        pplan = Plan(g.n, g.origin, g.cell, g.periodic, w["shells"], w["width"], max_order=max(orders),
+                     precision="fp32")
+
+        def pstep():
+            pplan.set_randoms(rx, ry, rz)
+            return pplan.compute(dx, dy, dz, orders=orders, out="device", outputs=outs)
+
+        for _ in range(max(2, args.warmup)):
+            pstep()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            pstep()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        tp = p0.elapsed_time(p1)
+        if ws > 1:
+            t = torch.tensor([tp], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tp = float(t.item())
+        if pplan.status() != 0:
+            raise RuntimeError("device status in the plain FP32 form")
+        pplan.close()
+        forms["fp32"] = {"ms_per_catalog": round(tp / (args.steps * ws), 4)}
+        forms["mixed_speedup_over_plain"] = round(tp / t_ms, 3)
+
     value = t_ms / (args.steps * ws)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms/catalog", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 FFT, split-tf32 sums" if precision == "split_tf32" else "f32",
         "data": "synthetic: seeded Neyman-Scott catalog with a lognormal-biased parent field in a survey-shell "
                 "mask and uniform randoms (stand-in for SDSS DR12 CMASS + randoms)",
         "config": {"workload": args.workload, "grid": list(g.n), "cell": g.cell, "periodic": g.periodic,
                    "shells": ns, "width": w["width"], "orders": list(orders), "n_data": d.n, "n_randoms": r.n,
+                   "precision": precision,
                    "step": "ck_set_randoms + ck_compute (both fields, every shell)",
-                   "l2": "no flush: inputs and intermediates far larger than L2 (W bank 8.6 GB per field)"},
+                   "l2": "no flush: inputs and intermediates far larger than L2 (16 scratch spectra, 8.7 GB)"},
+        "forms": forms,
         "roofline": roofline,
         "fft": {"gbs": round(fft_bytes / (fft_ms * 1e-3) / 1e9, 1), "frac": round(fft_bytes / (fft_ms * 1e-3) / 1e9 / peak, 4),
                 "ms_per_step": round(fft_ms / args.steps, 3), "passes_per_transform": 3},
@@ -336,7 +379,6 @@ def run_gb300(args):
     }
     if ws > 1:
         dist.destroy_process_group()
-    plan.close()
     if rank == 0:
         print(json.dumps(line))
 

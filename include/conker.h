@@ -62,12 +62,21 @@ typedef enum ck_status {
 #define CK_SHELL_INTERSECT 1
 
 /* Arithmetic of the product-sum contraction (Sec. 2.5).  FFTs are FP32 in
- * every mode and the cross-block reduction is FP64 in every mode. */
+ * every mode and the cross-block reduction is FP64 in every mode.
+ *
+ * CK_PREC_FP32 ("plain"): every W_s is written to the plan's bank and the
+ * products are FP32 FMAs on the CUDA cores with FP32 partial sums.
+ * CK_PREC_SPLIT_TF32 ("mixed"): the products run on the tensor cores with
+ * each operand split x = hi + lo into two TF32 numbers (hi*hi + hi*lo +
+ * lo*hi, FP32 accumulation over a tile, FP32 over 32 tiles, FP64 beyond),
+ * fused with the last inverse FFT pass so that no bank is kept.  It needs
+ * max_order <= 3 and at most 16 shells (otherwise CK_ERR_UNSUPPORTED). */
 typedef enum ck_precision {
-  CK_PREC_FP32 = 0,       /* FP32 CUDA-core products, FP32 partial sums     */
-  CK_PREC_SPLIT_BF16 = 1, /* reserved: tensor-core split-BF16 operands      */
-  CK_PREC_SPLIT_FP16 = 2, /* reserved: tensor-core split-FP16 operands      */
-  CK_PREC_FP64_SUM = 3    /* FP64 products and sums (reference contraction) */
+  CK_PREC_FP32 = 0,       /* plain: FP32 CUDA-core products and partial sums */
+  CK_PREC_SPLIT_BF16 = 1, /* reserved: tensor-core split-BF16 operands       */
+  CK_PREC_SPLIT_FP16 = 2, /* reserved: tensor-core split-FP16 operands       */
+  CK_PREC_FP64_SUM = 3,   /* FP64 products and sums (reference contraction)  */
+  CK_PREC_SPLIT_TF32 = 4  /* mixed: tensor-core split-TF32, fused pass       */
 } ck_precision;
 
 /* A grid of n[0] x n[1] x n[2] cubic cells of side `cell`, lower corner
@@ -103,7 +112,8 @@ typedef struct ck_plan_info {
   size_t workspace_bytes;
   int64_t bank_stride;             /* floats between shells in the W / B bank   */
   int32_t fused;                   /* 1: the last inverse FFT pass and the sums
-                                      run as one kernel and no bank is kept     */
+                                      run as one kernel and no bank is kept
+                                      (CK_PREC_SPLIT_TF32)                       */
 } ck_plan_info;
 
 /* Outputs of ck_compute.  For order n (index n = 2..5), xi[n], num[n] and
@@ -172,10 +182,10 @@ ck_status ck_get_field(ck_plan* plan, int32_t which, float* out, void* stream);
 
 /* Copy shell `shell` of the convolution of the field whose spectrum is
  * resident: W_s = N***K_s after ck_compute, R***K_s after ck_set_randoms
- * (float [N_c], device or host).  Plans with FP32 sums, at most 16 shells and
- * max_order <= 3 fuse the last inverse pass with the sums and keep no bank;
- * for them this call recomputes the shell from the resident spectrum (one
- * inverse transform on the stream, overwriting internal scratch only). */
+ * (float [N_c], device or host).  CK_PREC_SPLIT_TF32 plans fuse the last
+ * inverse pass with the sums and keep no bank; for them this call recomputes
+ * the shell from the resident spectrum (one inverse transform on the
+ * stream, overwriting internal scratch only). */
 ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream);
 
 /* Copy the octant of K^_s = DFT(K_s) / N_c: float

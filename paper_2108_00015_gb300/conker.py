@@ -28,7 +28,7 @@ STATUS = {
     9: "CK_ERR_CUDA", 10: "CK_ERR_UNSUPPORTED", 11: "CK_ERR_NO_RANDOMS", 12: "CK_ERR_EMPTY_CATALOG",
 }
 RULES = {"center_bin": 0, "intersect": 1}
-PRECISIONS = {"fp32": 0, "split_bf16": 1, "split_fp16": 2, "fp64": 3}
+PRECISIONS = {"fp32": 0, "split_bf16": 1, "split_fp16": 2, "fp64": 3, "split_tf32": 4}
 
 
 class CkError(RuntimeError):

@@ -443,7 +443,8 @@ ck_status contract_prepare(Plan& p, int mask) {
   c.order_mask = mask;
   const int maxn = max_order_in(mask);
   const int ns = p.ns;
-  if (p.precision == CK_PREC_FP32 && ((ns <= 16 && maxn <= 3) || (ns <= 5 && maxn <= 5))) {
+  // CUDA-core kernels for every precision but the FP64 reference (ck_contract on a mixed plan included)
+  if (p.precision != CK_PREC_FP64_SUM && ((ns <= 16 && maxn <= 3) || (ns <= 5 && maxn <= 5))) {
     c.use_reg = true;
     c.reg_maxn = maxn <= 3 ? 3 : 5;
     c.n_out_reg = reg_nout(ns, c.reg_maxn);

@@ -87,10 +87,11 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   for (int s = 0; s < shells->n_shells; ++s)
     if (!(shells->radius[s] > 0.0) || !finite(shells->radius[s])) return CK_ERR_ARG;
   if (max_order < 2 || max_order > CK_MAX_ORDER) return CK_ERR_ARG;
-  if (precision != CK_PREC_FP32 && precision != CK_PREC_FP64_SUM) {
+  if (precision != CK_PREC_FP32 && precision != CK_PREC_FP64_SUM && precision != CK_PREC_SPLIT_TF32) {
     if (precision == CK_PREC_SPLIT_BF16 || precision == CK_PREC_SPLIT_FP16) return CK_ERR_UNSUPPORTED;
     return CK_ERR_ARG;
   }
+  if (precision == CK_PREC_SPLIT_TF32 && (max_order > 3 || shells->n_shells > 16)) return CK_ERR_UNSUPPORTED;
   // The packed dense outputs must stay modest.
   int64_t dense = 1;
   for (int k = 1; k < max_order; ++k) dense *= shells->n_shells;
@@ -127,13 +128,15 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   p->oct[2] = nz / 2 + 1;
   p->oct_elems = (int64_t)p->oct[0] * p->oct[1] * p->oct[2];
   p->khat_stride = (int64_t)p->px * p->oct[1] * p->oct[2];
-  // One fused pass for the inverse x transform and the sums where its
-  // shared-memory tile fits; the bank is then not kept.
-  {
+  // Mixed precision: one fused pass for the inverse x transform and the
+  // tensor-core sums; the bank is then not kept.
+  p->fused = false;
+  if (precision == CK_PREC_SPLIT_TF32) {
     const int pad = xc_pad_shells(p->ns);
-    p->fused = precision == CK_PREC_FP32 && max_order <= 3 && pad > 0 && xc_smem_bytes(nx / 2, pad) <= kMaxSmemOptin;
-    p->bank_fields = p->fused ? 1 : p->ns;
+    if (pad == 0 || xc_smem_bytes(nx / 2, pad) > kMaxSmemOptin) return CK_ERR_UNSUPPORTED;
+    p->fused = true;
   }
+  p->bank_fields = p->fused ? 1 : p->ns;
   factor_len(nx / 2, &p->fx_half);
   factor_len(ny, &p->fy);
   factor_len(nz, &p->fz);

@@ -58,6 +58,10 @@ def test_host_validation(lib):
     assert _ws(lib, max_order=6)[0] == 1
     assert _ws(lib, max_order=1)[0] == 1
     assert _ws(lib, prec=1)[0] == 10                  # split-BF16 reserved
+    assert _ws(lib, prec=4)[0] == 0                   # split-TF32, fused
+    assert _ws(lib, prec=4, max_order=4)[0] == 10     # split-TF32: orders <= 3
+    assert _ws(lib, prec=4, radii=tuple(20.0 + 5 * i for i in range(17)), width=5.0)[0] == 10  # <= 16 shells
+    assert _ws(lib, prec=5)[0] == 1
     assert _ws(lib, radii=(0.2,), width=0.1)[0] == 4  # no lattice offset in the shell
     assert _ws(lib, radii=(170.0,))[0] == 5           # reaches half of a 32-cell box
     assert _ws(lib, rule=7)[0] == 1
@@ -65,13 +69,14 @@ def test_host_validation(lib):
 
 
 def test_survey_workspace_fits(lib):
-    # 512^3, 16 shells, orders <= 3 (fused pass, no bank): counts + field +
-    # spectrum + 16 scratch spectra + kernel octants + one real field
+    # 512^3, 16 shells, orders <= 3.  Mixed (split-TF32, fused pass, no bank):
+    # counts + field + spectrum + 16 scratch spectra + kernel octants + one field
     radii = tuple(30.0 + 8 * i for i in range(16))
-    code, fused = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0, radii=radii, width=8.0, max_order=3)
+    kw = dict(n=(512, 512, 512), cell=8.0, periodic=0, radii=radii, width=8.0, max_order=3)
+    code, fused = _ws(lib, prec=4, **kw)
     assert code == 0
     assert 10e9 < fused < 15e9
-    # orders <= 4 keep the 16-field bank (8.6 GB more)
-    code, banked = _ws(lib, n=(512, 512, 512), cell=8.0, periodic=0, radii=radii, width=8.0, max_order=4)
+    # plain FP32 keeps the 16-field bank (8.6 GB more)
+    code, banked = _ws(lib, prec=0, **kw)
     assert code == 0
     assert abs((banked - fused) - 15 * 512 ** 3 * 4) < 0.05e9

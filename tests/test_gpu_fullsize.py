@@ -1,7 +1,7 @@
 """The survey workload at its full size (512^3 cells of 8 h^-1 Mpc, 800k
-galaxies, 40M randoms, 16 shells, orders 2 and 3), in the launch
-configuration bench.py times, against what the oracle can compute at this
-size:
+galaxies, 40M randoms, 16 shells, orders 2 and 3), in both forms bench.py
+times (mixed split-TF32, the headline, and plain FP32), against what the
+oracle can compute at this size:
 
 * the count grids, bit for bit;
 * the order-2 numerators and denominators exactly, through the oracle's
@@ -22,12 +22,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-@pytest.fixture(scope="module")
-def run():
+@pytest.fixture(scope="module", params=["split_tf32", "fp32"])
+def run(request):
     torch = cuda_torch()
     w = workload("survey512")
     g = w["grid"]
-    plan = plan_for(w, max_order=3)
+    plan = plan_for(w, max_order=3, precision=request.param)
     plan.set_randoms(*dev_cat(torch, w["randoms"]))
     bank_r = {s: plan.bank(s).cpu().numpy() for s in (0, 7, 15)}
     res = plan.compute(*dev_cat(torch, w["data"]), orders=(2, 3), out="host")

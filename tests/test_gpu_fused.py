@@ -1,6 +1,7 @@
-"""The fused convolution + summation pass (inverse x transform and the
-order-2/3 product sums of Eq. 11 in one kernel, no bank in global memory)
-against the FP64 oracle, for every padded shell count (2, 4, 8, 16), an
+"""The mixed-precision form (CK_PREC_SPLIT_TF32): the fused convolution +
+summation pass (inverse x transform and the order-2/3 product sums of Eq. 11
+on the tensor cores in one kernel, no bank in global memory) against the FP64
+oracle, for every padded shell count (2, 4, 8, 16), an
 odd half-length x axis (runtime transform length) and against the plan's
 unfused path on the same catalog."""
 import numpy as np
@@ -33,7 +34,7 @@ def _box(n, cell, shells, width, seed):
     return dict(grid=g, shells=tuple(shells), width=width, data=clip(data), randoms=clip(rand))
 
 
-def _run(torch, w, max_order=3, precision="fp32"):
+def _run(torch, w, max_order=3, precision="split_tf32"):
     plan = plan_for(w, max_order=max_order, precision=precision)
     plan.set_randoms(*dev_cat(torch, w["randoms"]))
     res = plan.compute(*dev_cat(torch, w["data"]), orders=(2, 3), out="host")
@@ -51,15 +52,18 @@ def _check(res, ref, ns):
 
 
 def test_fused_selection(torch):
+    from paper_2108_00015_gb300.conker import CkError
     w = _box((32, 32, 32), 10.0, (20.0, 40.0), 10.0, 1)
-    for mo, prec, want in ((2, "fp32", True), (3, "fp32", True), (4, "fp32", False), (3, "fp64", False)):
+    for mo, prec, want in ((2, "split_tf32", True), (3, "split_tf32", True), (3, "fp32", False),
+                           (4, "fp32", False), (3, "fp64", False)):
         p = plan_for(w, max_order=mo, precision=prec)
         assert p.fused is want, (mo, prec)
         p.close()
+    with pytest.raises(CkError):
+        plan_for(w, max_order=4, precision="split_tf32")
     w17 = _box((32, 32, 32), 10.0, tuple(20.0 + 5 * i for i in range(17)), 5.0, 1)
-    p = plan_for(w17, max_order=3)
-    assert not p.fused
-    p.close()
+    with pytest.raises(CkError):
+        plan_for(w17, max_order=3, precision="split_tf32")
 
 
 @pytest.mark.parametrize("ns", [1, 3, 5, 8, 9, 16])
@@ -79,9 +83,9 @@ def test_fused_odd_half_length(torch):
     shells = (20.0, 35.0, 50.0)
     w = _box((30, 32, 20), 10.0, shells, 10.0, 31)
     ref = O.correlate(w["grid"], shells, w["width"], w["data"], w["randoms"], orders=(2, 3), engine="fft")
-    for mo in (3, 4):
-        plan, res = _run(torch, w, max_order=mo)
-        assert plan.fused is (mo == 3)
+    for prec in ("split_tf32", "fp32"):
+        plan, res = _run(torch, w, precision=prec)
+        assert plan.fused is (prec == "split_tf32")
         _check(res, ref, len(shells))
         for s in range(len(shells)):
             got = plan.bank(s).cpu().numpy()
@@ -91,14 +95,15 @@ def test_fused_odd_half_length(torch):
 
 
 def test_fused_vs_unfused(torch):
-    """Same catalog, 12 shells on a 64^3 box: the fused plan (orders <= 3) and
-    the unfused one (orders <= 4: bank + register contraction) agree on the
-    order-2/3 sums, and the fused plan's recomputed bank equals the stored one."""
+    """Same catalog, 12 shells on a 64^3 box: the mixed plan (fused pass) and
+    the plain FP32 one (bank + register contraction) agree with the oracle on
+    the order-2/3 sums, and the mixed plan's recomputed bank equals the stored
+    one."""
     shells = tuple(15.0 + 6.0 * i for i in range(12))
     w = _box((64, 64, 64), 5.0, shells, 6.0, 41)
     ref = O.correlate(w["grid"], shells, w["width"], w["data"], w["randoms"], orders=(2, 3), engine="fft")
-    pf, rf = _run(torch, w, max_order=3)
-    pu, ru = _run(torch, w, max_order=4)
+    pf, rf = _run(torch, w, precision="split_tf32")
+    pu, ru = _run(torch, w, precision="fp32")
     assert pf.fused and not pu.fused
     _check(rf, ref, 12)
     _check(ru, ref, 12)
