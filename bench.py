@@ -200,8 +200,6 @@ def run_gb300(args):
     orders = _orders(args, w)
     g = w["grid"]
     precision = args.precision
-    if precision == "split_tf32" and (max(orders) > 3 or len(w["shells"]) > 16):
-        precision = "fp32"  # the mixed form covers orders <= 3 with <= 16 shells
     plan = Plan(g.n, g.origin, g.cell, g.periodic, w["shells"], w["width"], max_order=max(orders),
                 precision=precision)
     d, r = w["data"], w["randoms"]

@@ -68,15 +68,17 @@ typedef enum ck_status {
  * products are FP32 FMAs on the CUDA cores with FP32 partial sums.
  * CK_PREC_SPLIT_TF32 ("mixed"): the products run on the tensor cores with
  * each operand split x = hi + lo into two TF32 numbers (hi*hi + hi*lo +
- * lo*hi, FP32 accumulation over a tile, FP32 over 32 tiles, FP64 beyond),
- * fused with the last inverse FFT pass so that no bank is kept.  It needs
- * max_order <= 3 and at most 16 shells (otherwise CK_ERR_UNSUPPORTED). */
+ * lo*hi, FP32 accumulation over up to 512 cells, FP32 over 16-32 such
+ * sums, FP64 beyond).  For max_order <= 3 and at most 16 shells they are
+ * fused with the last inverse FFT pass and no bank is kept; otherwise the
+ * bank is kept and the blocked product of every order runs on the tensor
+ * cores. */
 typedef enum ck_precision {
   CK_PREC_FP32 = 0,       /* plain: FP32 CUDA-core products and partial sums */
   CK_PREC_SPLIT_BF16 = 1, /* reserved: tensor-core split-BF16 operands       */
   CK_PREC_SPLIT_FP16 = 2, /* reserved: tensor-core split-FP16 operands       */
   CK_PREC_FP64_SUM = 3,   /* FP64 products and sums (reference contraction)  */
-  CK_PREC_SPLIT_TF32 = 4  /* mixed: tensor-core split-TF32, fused pass       */
+  CK_PREC_SPLIT_TF32 = 4  /* mixed: tensor-core split-TF32 sums              */
 } ck_precision;
 
 /* A grid of n[0] x n[1] x n[2] cubic cells of side `cell`, lower corner
@@ -113,7 +115,7 @@ typedef struct ck_plan_info {
   int64_t bank_stride;             /* floats between shells in the W / B bank   */
   int32_t fused;                   /* 1: the last inverse FFT pass and the sums
                                       run as one kernel and no bank is kept
-                                      (CK_PREC_SPLIT_TF32)                       */
+                                      (CK_PREC_SPLIT_TF32, n <= 3, <= 16 shells) */
 } ck_plan_info;
 
 /* Outputs of ck_compute.  For order n (index n = 2..5), xi[n], num[n] and

@@ -61,6 +61,7 @@ struct FftLen {
 struct ContractPlan {
   int order_mask = 0;
   bool use_reg = false;     // register-accumulator kernel (few outputs)
+  bool use_tc = false;      // blocked product on the tensor cores (split-TF32)
   int reg_maxn = 0;         // orders 2..reg_maxn computed by that kernel
   int n_out_reg = 0;        // outputs of the register kernel
   int rows = 0, cols = 0;   // blocked kernel: operand rows / columns

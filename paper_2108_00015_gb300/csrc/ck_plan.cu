@@ -91,7 +91,6 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
     if (precision == CK_PREC_SPLIT_BF16 || precision == CK_PREC_SPLIT_FP16) return CK_ERR_UNSUPPORTED;
     return CK_ERR_ARG;
   }
-  if (precision == CK_PREC_SPLIT_TF32 && (max_order > 3 || shells->n_shells > 16)) return CK_ERR_UNSUPPORTED;
   // The packed dense outputs must stay modest.
   int64_t dense = 1;
   for (int k = 1; k < max_order; ++k) dense *= shells->n_shells;
@@ -129,12 +128,12 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   p->oct_elems = (int64_t)p->oct[0] * p->oct[1] * p->oct[2];
   p->khat_stride = (int64_t)p->px * p->oct[1] * p->oct[2];
   // Mixed precision: one fused pass for the inverse x transform and the
-  // tensor-core sums; the bank is then not kept.
+  // tensor-core sums (orders <= 3, <= 16 shells), with no bank kept; beyond
+  // that the bank is kept and the blocked product runs on the tensor cores.
   p->fused = false;
-  if (precision == CK_PREC_SPLIT_TF32) {
+  if (precision == CK_PREC_SPLIT_TF32 && max_order <= 3) {
     const int pad = xc_pad_shells(p->ns);
-    if (pad == 0 || xc_smem_bytes(nx / 2, pad) > kMaxSmemOptin) return CK_ERR_UNSUPPORTED;
-    p->fused = true;
+    p->fused = pad > 0 && xc_smem_bytes(nx / 2, pad) <= kMaxSmemOptin;
   }
   p->bank_fields = p->fused ? 1 : p->ns;
   factor_len(nx / 2, &p->fx_half);

@@ -31,6 +31,7 @@
 #pragma once
 
 #include "ck_fft_core.cuh"
+#include "ck_mma.cuh"
 
 namespace ck {
 namespace fft {
@@ -74,26 +75,6 @@ __host__ __device__ inline XcLayout xc_layout(int M, int NS, int ntw) {
 inline int xc_ntw(int M) {
   const RPlan p = rplan(M);
   return p.nst > 0 ? tw_table_len(p) : 0;
-}
-
-// Round to TF32 (nearest, ties away) and the TF32 remainder of x - hi.
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
-  hi = tf32_rna(x);
-  lo = tf32_rna(x - __uint_as_float(hi));
-}
-
-// D (16 x 8, FP32) += A (16 x 8, TF32, row-major) * B (8 x 8, TF32, column-major)
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 template <int MC, int NS>
@@ -361,7 +342,6 @@ struct XcrShape {
   static_assert(red_bytes <= bar_off, "the final sum does not reach the barriers");
 };
 
-__device__ __forceinline__ uint32_t tf32_trunc(float x) { return __float_as_uint(x) & 0xffffe000u; }
 
 template <int P, int Q, int NS>
 __global__ void __launch_bounds__(kThreads, 2)

@@ -59,8 +59,8 @@ def test_host_validation(lib):
     assert _ws(lib, max_order=1)[0] == 1
     assert _ws(lib, prec=1)[0] == 10                  # split-BF16 reserved
     assert _ws(lib, prec=4)[0] == 0                   # split-TF32, fused
-    assert _ws(lib, prec=4, max_order=4)[0] == 10     # split-TF32: orders <= 3
-    assert _ws(lib, prec=4, radii=tuple(20.0 + 5 * i for i in range(17)), width=5.0)[0] == 10  # <= 16 shells
+    assert _ws(lib, prec=4, max_order=5)[0] == 0      # split-TF32, bank + tensor-core blocked product
+    assert _ws(lib, prec=4, radii=tuple(20.0 + 5 * i for i in range(17)), width=5.0)[0] == 0
     assert _ws(lib, prec=5)[0] == 1
     assert _ws(lib, radii=(0.2,), width=0.1)[0] == 4  # no lattice offset in the shell
     assert _ws(lib, radii=(170.0,))[0] == 5           # reaches half of a 32-cell box

@@ -188,6 +188,40 @@ def test_xi_fp64_contraction(torch, p32, ref32):
     plan.close()
 
 
+def test_xi_split_tf32_all_orders(torch, p32, ref32):
+    """Mixed form with orders up to 5: the bank is kept and every order runs
+    through the tensor-core blocked product."""
+    plan, res = _run(torch, p32, (2, 3, 4, 5), precision="split_tf32")
+    assert not plan.fused
+    _check_sums(res, ref32, len(p32["shells"]), (2, 3, 4, 5))
+    plan.close()
+
+
+@pytest.mark.parametrize("ns", [16, 20])
+def test_tc_blocked_contraction(torch, ns):
+    """The tensor-core blocked product (split-TF32) over a caller's bank,
+    orders 2..5 (n = 5 over 20 shells: 8855 multisets, several 64 x 64
+    tiles and split-K over the cells, ragged tail), against the oracle's
+    product sums of the same float32 fields."""
+    g = GridSpec((24, 20, 18), (0.0, 0.0, 0.0), 1.0, True)
+    rng = np.random.default_rng(50 + ns)
+    nc = g.n_cells
+    w0 = rng.normal(size=nc).astype(np.float32)
+    bank = rng.normal(size=(ns, nc)).astype(np.float32)
+    w = dict(grid=g, shells=tuple(1.0 + 0.05 * i for i in range(ns)), width=1.0)
+    plan = plan_for(w, max_order=5, precision="split_tf32")
+    stride = (nc + 63) // 64 * 64
+    B = np.zeros((ns, stride), np.float32)
+    B[:, :nc] = bank
+    for orders in [(2, 3), (4,), (5,), (2, 3, 4, 5)]:
+        sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=orders)
+        for n in orders:
+            want, awant = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
+            e = normwise(sums[n].cpu().numpy(), want, awant)
+            assert e <= TOL, f"order {n}: {e:.3e}"
+    plan.close()
+
+
 def test_order_subsets(torch, p32, ref32):
     for orders in [(2,), (3,), (4,), (5,), (2, 4), (3, 5)]:
         plan, res = _run(torch, p32, orders, max_order=5)
