@@ -10,9 +10,9 @@
 //    and chunk and keep every product sum in registers (FP32 over 64 chunks,
 //    then warp-reduced into FP64 in shared memory).  HBM-bound: it reads each
 //    W_s once.
-//  * contract_tc: the blocked product below on the tensor cores, split-TF32
-//    operands (CK_PREC_SPLIT_TF32 plans that keep the bank: n >= 4 or more
-//    than 16 shells).
+//  * the blocked product below on the fifth-generation tensor cores with
+//    split-TF32 operands (ck_umma.cu) for CK_PREC_SPLIT_TF32 plans that keep
+//    the bank (n >= 4 or more than 16 shells).
 //  * contract_blocked: the general case as a blocked product
 //    T[p][q] = sum_r A_p(r) B_q(r) with A_p = W0 W_i W_j and B_q = W_k W_l
 //    generated per cell chunk in shared memory (64 x 64 output tiles, 4 x 4
@@ -27,7 +27,6 @@
 
 #include "ck_device.cuh"
 #include "ck_internal.h"
-#include "ck_mma.cuh"
 #include "ck_sums.cuh"
 
 namespace ck {
@@ -371,177 +370,6 @@ __global__ void __launch_bounds__(256) contract_blocked_kernel(const float* __re
     for (int j = 0; j < 4; ++j) out[(ty * 4 + i) * BK_T + tx * 4 + j] = dacc[i][j] + (double)acc[i][j];
 }
 
-// ---------------------------------------------------------------------------
-// blocked kernel on the tensor cores (split-TF32 plans)
-//
-// The same 64 x 64 output tiles and operand descriptors as
-// contract_blocked_kernel.  Cells go in chunks of 32, software-pipelined
-// with one block barrier per chunk: after the barrier of chunk c, the CTA
-// fetches the W values of chunk c + 1 with cp.async, builds A[p][k] =
-// W0 W_a W_b and B[q][k] = W_c W_d of chunk c in shared memory (cells
-// contiguous, double-buffered), and runs the MMAs of chunk c - 1.  Its eight
-// warps (4 along p x 2 along q, 16 x 32 outputs each) take k-steps of 8
-// cells with m16n8k8 TF32 MMAs: k-slot t holds cell 2t and slot t + 4 cell
-// 2t + 1 of the step, so each fragment pair is one 8-byte load.  Operands
-// are split x = hi + lo (hi = x truncated to TF32) and the product taken as
-// hi*hi + hi*lo + lo*hi.  Sums: FP32 in the MMA accumulators over 16
-// chunks, then FP32 over 16 such groups, then FP64.
-
-constexpr int TC_KC = 32;           // cells per chunk
-constexpr int TC_PITCH = TC_KC + 8; // operand row pitch (floats), 8 mod 32: conflict-free fragment loads
-constexpr int TC_FLUSH1 = 16;       // chunks per MMA accumulation
-constexpr int TC_FLUSH2 = 16;       // MMA groups per FP32 sum
-
-inline size_t tc_smem_bytes(int ns) {
-  return (size_t)2 * (ns + 1) * TC_KC * sizeof(float) + (size_t)4 * BK_T * TC_PITCH * sizeof(float) +
-         (size_t)2 * BK_T * sizeof(int2);
-}
-
-__global__ void __launch_bounds__(256) contract_tc_kernel(const float* __restrict__ w0, const float* __restrict__ bank,
-                                                          int64_t bstride, int64_t nc, int ns,
-                                                          const int2* __restrict__ rowdesc, int rows,
-                                                          const int2* __restrict__ coldesc, int cols,
-                                                          const int2* __restrict__ tiles, int ntiles,
-                                                          int64_t cells_per_split, double* __restrict__ partials) {
-  extern __shared__ __align__(16) unsigned char tc_smem[];
-  float* opnd = reinterpret_cast<float*>(tc_smem);                 // As[2][64][PITCH], Bs[2][64][PITCH]
-  float* wsb = opnd + 4 * BK_T * TC_PITCH;                         // [2][ns + 1][KC]
-  int2* rd = reinterpret_cast<int2*>(wsb + 2 * (ns + 1) * TC_KC);  // [64]
-  int2* cd = rd + BK_T;
-  auto As = [&](int b) { return opnd + b * BK_T * TC_PITCH; };
-  auto Bs = [&](int b) { return opnd + (2 + b) * BK_T * TC_PITCH; };
-  auto Ws = [&](int b) { return wsb + b * (ns + 1) * TC_KC; };
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const int pm = 16 * (warp & 3), qn = 32 * (warp >> 2);  // this warp's outputs: rows pm.., cols qn..
-  const int2 tile = tiles[blockIdx.x];
-  if (tid < BK_T) {
-    const int p = tile.x + tid;
-    rd[tid] = p < rows ? rowdesc[p] : make_int2(-2, -2);
-  } else if (tid < 2 * BK_T) {
-    const int q = tile.y + tid - BK_T;
-    cd[tid - BK_T] = q < cols ? coldesc[q] : make_int2(-2, -2);
-  }
-  float hh[4][4], cr[4][4], mid[4][4];
-  double dacc[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      hh[j][e] = 0.0f;
-      cr[j][e] = 0.0f;
-      mid[j][e] = 0.0f;
-      dacc[j][e] = 0.0;
-    }
-  const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
-  const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
-  const int nch = end > beg ? (int)((end - beg + TC_KC - 1) / TC_KC) : 0;
-  // W values of chunk c into buffer b: 16-byte copies of 4 cells, zero past `end`
-  // (w0, the bank rows, bstride and beg are multiples of 4 floats)
-  auto stage = [&](int c, int b) {
-    const int64_t c0 = beg + (int64_t)c * TC_KC;
-    float* dst = Ws(b);
-    for (int idx = tid; idx < (ns + 1) * (TC_KC / 4); idx += 256) {
-      const int a = idx / (TC_KC / 4), j = idx - a * (TC_KC / 4);
-      const int64_t cell = c0 + 4 * j;
-      const int64_t left = end - cell;
-      const int n = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
-      const float* src = a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride;
-      cp_async16n(dst + a * TC_KC + 4 * j, n > 0 ? (const void*)(src + cell) : (const void*)w0, n);
-    }
-  };
-  if (nch > 0) stage(0, 0);
-  cp_async_commit();
-  int n1 = 0, n2 = 0;
-  for (int c = 0; c <= nch; ++c) {
-    cp_async_wait<0>();
-    __syncthreads();  // W of chunk c landed; operands of chunk c - 1 complete; MMAs of chunk c - 2 done
-    if (c + 1 < nch) stage(c + 1, (c + 1) & 1);
-    cp_async_commit();
-    if (c < nch) {
-      const float* w = Ws(c & 1);
-      float* A = As(c & 1);
-      float* B = Bs(c & 1);
-      for (int idx = tid; idx < BK_T * TC_KC; idx += 256) {
-        const int p = idx / TC_KC, k = idx - p * TC_KC;
-        const int2 d = rd[p];
-        float va = 0.0f;
-        if (d.x != -2) {
-          va = w[k];
-          if (d.x >= 0) va *= w[(1 + d.x) * TC_KC + k];
-          if (d.y >= 0) va *= w[(1 + d.y) * TC_KC + k];
-        }
-        A[p * TC_PITCH + k] = va;
-        const int2 e = cd[p];
-        float vb = 0.0f;
-        if (e.x != -2) {
-          vb = 1.0f;
-          if (e.x >= 0) vb *= w[(1 + e.x) * TC_KC + k];
-          if (e.y >= 0) vb *= w[(1 + e.y) * TC_KC + k];
-        }
-        B[p * TC_PITCH + k] = vb;
-      }
-    }
-    if (c >= 1) {
-      const float* A = As((c - 1) & 1);
-      const float* B = Bs((c - 1) & 1);
-#pragma unroll
-      for (int k8 = 0; k8 < TC_KC; k8 += 8) {
-        const float2 x0 = *reinterpret_cast<const float2*>(A + (pm + g) * TC_PITCH + k8 + 2 * t);
-        const float2 x1 = *reinterpret_cast<const float2*>(A + (pm + g + 8) * TC_PITCH + k8 + 2 * t);
-        const float av[4] = {x0.x, x1.x, x0.y, x1.y};
-        uint32_t ah[4], al[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          ah[e] = tf32_trunc(av[e]);
-          al[e] = __float_as_uint(av[e] - __uint_as_float(ah[e]));
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float2 y = *reinterpret_cast<const float2*>(B + (qn + 8 * j + g) * TC_PITCH + k8 + 2 * t);
-          const uint32_t bh0 = tf32_trunc(y.x), bh1 = tf32_trunc(y.y);
-          const uint32_t bl0 = __float_as_uint(y.x - __uint_as_float(bh0));
-          const uint32_t bl1 = __float_as_uint(y.y - __uint_as_float(bh1));
-          mma_tf32(hh[j], ah, bh0, bh1);
-          mma_tf32(cr[j], ah, bl0, bl1);
-          mma_tf32(cr[j], al, bh0, bh1);
-        }
-      }
-      if (++n1 == TC_FLUSH1) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            mid[j][e] += hh[j][e] + cr[j][e];
-            hh[j][e] = 0.0f;
-            cr[j][e] = 0.0f;
-          }
-        n1 = 0;
-        if (++n2 == TC_FLUSH2) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              dacc[j][e] += (double)mid[j][e];
-              mid[j][e] = 0.0f;
-            }
-          n2 = 0;
-        }
-      }
-    }
-  }
-  double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (BK_T * BK_T);
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int row = pm + g + ((e & 2) ? 8 : 0);
-      const int col = qn + 8 * j + 2 * t + (e & 1);
-      out[row * BK_T + col] = dacc[j][e] + (double)mid[j][e] + (double)(hh[j][e] + cr[j][e]);
-    }
-}
-
 // Rank of a sorted multiset s[0..k) over ns symbols in lexicographic order.
 __host__ __device__ inline int64_t multiset_rank(const int* s, int k, int ns) {
   int64_t r = 0;
@@ -644,17 +472,22 @@ ck_status contract_prepare(Plan& p, int mask) {
   if ((mask >> 5) & 1)
     for (int k = 0; k < ns; ++k)
       for (int l = k; l < ns; ++l) cols.push_back(make_int2(k, l));  // sorted by (k, l)
+  // output tiles holding a canonical (p, q): 64 x 64 (CUDA cores) or
+  // 128 x TN (tensor cores, split-TF32 plans)
+  c.use_tc = p.precision == CK_PREC_SPLIT_TF32;
+  const int TM = c.use_tc ? umma_tile_rows() : BK_T;
+  const int TNc = c.use_tc ? umma_tile_cols((int)cols.size()) : BK_T;
+  c.um_tn = c.use_tc ? TNc : 0;
   std::vector<int2> tiles;
   int ms[4];
-  for (int m0 = 0; m0 < (int)rows.size(); m0 += BK_T)
-    for (int n0 = 0; n0 < (int)cols.size(); n0 += BK_T) {
+  for (int m0 = 0; m0 < (int)rows.size(); m0 += TM)
+    for (int n0 = 0; n0 < (int)cols.size(); n0 += TNc) {
       bool any = false;
-      for (int pp = m0; pp < std::min<int>(m0 + BK_T, (int)rows.size()) && !any; ++pp)
-        for (int qq = n0; qq < std::min<int>(n0 + BK_T, (int)cols.size()) && !any; ++qq)
+      for (int pp = m0; pp < std::min<int>(m0 + TM, (int)rows.size()) && !any; ++pp)
+        for (int qq = n0; qq < std::min<int>(n0 + TNc, (int)cols.size()) && !any; ++qq)
           any = canonical(rows[pp], cols[qq], mask, ms) != 0;
       if (any) tiles.push_back(make_int2(m0, n0));
     }
-  c.use_tc = p.precision == CK_PREC_SPLIT_TF32;
   c.rows = (int)rows.size();
   c.cols = (int)cols.size();
   c.n_tiles = (int)tiles.size();
@@ -669,6 +502,14 @@ ck_status contract_prepare(Plan& p, int mask) {
   if (e == cudaSuccess && !tiles.empty())
     e = cudaMemcpy(c.d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_status(e);
+  if (c.use_tc) {
+    c.um_cps = umma_cells_per_split(p.nc, std::max(c.n_tiles, 1), p.sm_count);
+    c.splits = (int)((p.nc + c.um_cps - 1) / c.um_cps);
+    c.partial_doubles = (size_t)c.splits * std::max(c.n_tiles, 1) * TM * TNc;
+    if (c.partial_doubles > p.partials_cap) return CK_ERR_OOM;
+    p.cplan_ready[mask] = true;
+    return CK_OK;
+  }
   const int64_t per_split = (int64_t)std::max(c.n_tiles, 1) * BK_T * BK_T;
   int64_t splits = std::max<int64_t>(1, (int64_t)(4 * p.sm_count + c.n_tiles - 1) / std::max(c.n_tiles, 1));
   splits = std::min<int64_t>(splits, (int64_t)(p.partials_cap / per_split));
@@ -700,19 +541,24 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
     return cuda_status(cudaGetLastError());
   }
   if (c.n_tiles == 0) return CK_OK;
+  if (c.use_tc) {
+    cudaError_t e;
+    {
+      ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, st);
+      e = launch_umma(c.um_tn, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc, c.cols, c.d_tiles,
+                      c.n_tiles, c.splits, c.um_cps, p.partials, status, st);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);
+    return cuda_status(launch_umma_reduce(p.partials, c.splits, c.n_tiles, c.um_tn, c.d_tiles, c.d_rowdesc, c.rows,
+                                          c.d_coldesc, c.cols, mask, p.ns, p.multiset_base, sums, st));
+  }
   const int64_t cps = (p.nc + c.splits - 1) / c.splits;
   const int64_t cps_al = (cps + 31) / 32 * 32;
   dim3 grid((unsigned)c.n_tiles, (unsigned)c.splits);
   {
   ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc, st);
-  if (c.use_tc) {
-    const size_t sm = tc_smem_bytes(p.ns);
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return cuda_status(e);
-    contract_tc_kernel<<<grid, 256, sm, st>>>(w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc,
-                                              c.cols, c.d_tiles, c.n_tiles, cps_al, p.partials);
-  }
-  else if (p.precision == CK_PREC_FP64_SUM)
+  if (p.precision == CK_PREC_FP64_SUM)
     contract_blocked_kernel<double><<<grid, 256, 0, st>>>(w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows,
                                                           c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, cps_al,
                                                           p.partials);

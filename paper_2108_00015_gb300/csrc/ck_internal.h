@@ -61,7 +61,9 @@ struct FftLen {
 struct ContractPlan {
   int order_mask = 0;
   bool use_reg = false;     // register-accumulator kernel (few outputs)
-  bool use_tc = false;      // blocked product on the tensor cores (split-TF32)
+  bool use_tc = false;      // blocked product on the tensor cores (split-TF32, tcgen05)
+  int um_tn = 0;            // tcgen05 tiles: 128 rows x um_tn columns
+  int64_t um_cps = 0;       // tcgen05: cells per split
   int reg_maxn = 0;         // orders 2..reg_maxn computed by that kernel
   int n_out_reg = 0;        // outputs of the register kernel
   int rows = 0, cols = 0;   // blocked kernel: operand rows / columns
@@ -208,6 +210,17 @@ size_t xc_smem_bytes(int M, int ns_pad);  // shared memory of the fused kernel
 // Inverse z, y passes and the fused x pass + order-2/3 sums of the resident
 // spectrum p.spec with cell values w0; packed sums (orders <= max_order).
 ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st);
+
+// ---- tcgen05 blocked product (ck_umma.cu) -------------------------------------
+int umma_tile_rows();
+int umma_tile_cols(int cols);
+int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count);
+cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
+                        const int2* rowdesc, int rows, const int2* coldesc, int cols, const int2* tiles, int ntiles,
+                        int splits, int64_t cps, double* partials, int* status, cudaStream_t st);
+cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, int tn, const int2* tiles,
+                               const int2* rowdesc, int rows, const int2* coldesc, int cols, int mask, int ns,
+                               const int64_t* bases, double* out, cudaStream_t st);
 
 // ---- launches (ck_contract.cu) -----------------------------------------------
 ck_status contract_prepare(Plan& p, int order_mask);

@@ -159,8 +159,20 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   p->n_multiset_total = base;
   p->dense_total = dbase;
   p->staging_pts = (int64_t)1 << 21;
-  // Partial sums of the contraction kernels (doubles).
+  // Partial sums of the contraction kernels (doubles); split-TF32 plans that
+  // keep the bank need one 128 x TN tile of FP64 per tile and split of at
+  // most 16384 cells (bounded here for any device of up to 256 SMs).
   p->partials_cap = (size_t)1 << 22;
+  if (precision == CK_PREC_SPLIT_TF32 && !p->fused) {
+    const int64_t ns = p->ns;
+    const int64_t urows = 1 + (max_order >= 3 ? ns : 0) + (max_order >= 4 ? ns * (ns + 1) / 2 : 0);
+    const int64_t ucols = ns + (max_order >= 5 ? ns * (ns + 1) / 2 : 0);
+    const int tn = umma_tile_cols((int)ucols);
+    const int64_t ntiles = ((urows + umma_tile_rows() - 1) / umma_tile_rows()) * ((ucols + tn - 1) / tn);
+    const int64_t splits = std::min<int64_t>((p->nc + 31) / 32, std::max<int64_t>((p->nc + 16383) / 16384,
+                                                                                   (512 + ntiles - 1) / ntiles));
+    p->partials_cap = std::max<size_t>(p->partials_cap, (size_t)(splits * ntiles * umma_tile_rows() * tn));
+  }
   // Contraction operand tables: one slot per order mask.
   const int64_t rows = 1 + p->ns + (int64_t)p->ns * (p->ns + 1) / 2;
   const int64_t tiles = ((rows + 63) / 64) * ((rows + 63) / 64);
