@@ -18,7 +18,8 @@
 //    kind::tf32 MMAs (M = 128, N = TN, K = 8) accumulating in FP32 in
 //    tensor memory; the dropped lo*lo term is below 2^-21 relative;
 //  * every 8 chunks (256 cells) the accumulator is drained with tcgen05.ld
-//    into FP32 registers (the next chunk overwrites it), and each CTA
+//    into FP32 registers of the CTA's 16 warps (warp w: lanes 32 (w % 4)..,
+//    a quarter of the columns; the next chunk overwrites it), and each CTA
 //    writes its FP32 register sums (at most 64 groups) as FP64 partials,
 //    reduced over the splits in a fixed order.
 // Waits are bounded: on a timeout the CTA sets CK_ERR_TIMEOUT, stops
@@ -40,22 +41,26 @@ constexpr int UM_KC = 32;             // cells per chunk: 4 MMA k-steps of 8
 constexpr int UM_GROUP = 8;           // chunks per tensor-memory accumulation (256 cells)
 constexpr int UM_MAX_GROUPS = 64;     // groups per CTA (FP32 register sums)
 constexpr int UM_WPITCH = UM_KC + 4;  // W staging row pitch (floats)
-constexpr int UM_THREADS = 256;
+constexpr int UM_THREADS = 512;
+constexpr int UM_WARPS = UM_THREADS / 32;
 
 template <int TN>
 struct UmmaShape {
-  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, two column halves of 16s");
+  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, four column quarters of 8s");
   static constexpr size_t a_bytes = (size_t)UM_M * UM_KC * sizeof(float);
   static constexpr size_t b_bytes = (size_t)TN * UM_KC * sizeof(float);
   static constexpr size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // A hi, A lo, B hi, B lo
   static constexpr uint32_t ncols = TN <= 32 ? 32 : (TN <= 64 ? 64 : (TN <= 128 ? 128 : 256));
 };
 
+// W staging rows per buffer: W0, the ns shells, a row of ones and a row of zeros
+__host__ __device__ constexpr int um_wrows(int ns) { return ns + 3; }
+
 template <int TN>
 size_t umma_smem(int ns) {
   using S = UmmaShape<TN>;
-  return 2 * S::stage_bytes + (size_t)2 * (ns + 1) * UM_WPITCH * sizeof(float) + (size_t)(UM_M + TN) * sizeof(int2) +
-         64;
+  return 2 * S::stage_bytes + (size_t)2 * um_wrows(ns) * UM_WPITCH * sizeof(float) +
+         (size_t)(UM_M + TN) * sizeof(int4) + 64;
 }
 
 template <int TN>
@@ -67,11 +72,12 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   using S = UmmaShape<TN>;
   extern __shared__ __align__(1024) unsigned char um_smem[];
   unsigned char* stages = um_smem;  // [2][A hi | A lo | B hi | B lo]
-  float* wsb = reinterpret_cast<float*>(um_smem + 2 * S::stage_bytes);  // [2][ns + 1][WPITCH]
-  int2* rd = reinterpret_cast<int2*>(wsb + 2 * (ns + 1) * UM_WPITCH);     // [128]
-  int2* cd = rd + UM_M;                                                    // [TN]
+  const int WR = um_wrows(ns);
+  float* wsb = reinterpret_cast<float*>(um_smem + 2 * S::stage_bytes);  // [2][WR][WPITCH]
+  int4* fa = reinterpret_cast<int4*>(wsb + 2 * WR * UM_WPITCH);         // [128] factor rows of A_p
+  int4* fb = fa + UM_M;                                                  // [TN]  factor rows of B_q
   uint64_t* bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(cd + TN) + 15) & ~(uintptr_t)15);       // [2]
+      (reinterpret_cast<uintptr_t>(fb + TN) + 15) & ~(uintptr_t)15);     // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   auto Ahi = [&](int b) { return reinterpret_cast<float*>(stages + b * S::stage_bytes); };
   auto Alo = [&](int b) { return reinterpret_cast<float*>(stages + b * S::stage_bytes + S::a_bytes); };
@@ -79,17 +85,29 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   auto Blo = [&](int b) {
     return reinterpret_cast<float*>(stages + b * S::stage_bytes + 2 * S::a_bytes + S::b_bytes);
   };
-  auto Ws = [&](int b) { return wsb + b * (ns + 1) * UM_WPITCH; };
+  auto Ws = [&](int b) { return wsb + b * WR * UM_WPITCH; };
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int2 tile = tiles[blockIdx.x];
+  // each operand row is the product of three staged rows: A_p = W0 W_a W_b, B_q = 1 W_c W_d,
+  // with the ones row for an absent factor and the zeros row for a padding row
+  const int ONE = ns + 1, ZERO = ns + 2;
   for (int i = tid; i < UM_M; i += UM_THREADS) {
     const int p = tile.x + i;
-    rd[i] = p < rows ? rowdesc[p] : make_int2(-2, -2);
+    const int2 d = p < rows ? rowdesc[p] : make_int2(-2, -2);
+    fa[i] = d.x == -2 ? make_int4(ZERO, ONE, ONE, 0)
+                      : make_int4(0, d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0);
   }
   for (int i = tid; i < TN; i += UM_THREADS) {
     const int q = tile.y + i;
-    cd[i] = q < cols ? coldesc[q] : make_int2(-2, -2);
+    const int2 d = q < cols ? coldesc[q] : make_int2(-2, -2);
+    fb[i] = d.x == -2 ? make_int4(ZERO, ONE, ONE, 0)
+                      : make_int4(ONE, d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0);
+  }
+  for (int i = tid; i < 2 * UM_KC; i += UM_THREADS) {  // constant rows of both staging buffers
+    float* w = wsb + (i / UM_KC) * WR * UM_WPITCH;
+    w[ONE * UM_WPITCH + i % UM_KC] = 1.0f;
+    w[ZERO * UM_WPITCH + i % UM_KC] = 0.0f;
   }
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -110,7 +128,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   auto stage = [&](int c, int b) {
     const int64_t c0 = beg + (int64_t)c * UM_KC;
     float* dst = Ws(b);
-    for (int idx = tid; idx < (ns + 1) * (UM_KC / 4); idx += UM_THREADS) {
+    for (int idx = tid; idx < (ns + 1) * (UM_KC / 4); idx += UM_THREADS) {  // rows 0..ns only
       const int a = idx / (UM_KC / 4), j = idx - a * (UM_KC / 4);
       const int64_t cell = c0 + 4 * j;
       const int64_t left = end - cell;
@@ -119,44 +137,27 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       cp_async16n(dst + a * UM_WPITCH + 4 * j, n > 0 ? (const void*)(src + cell) : (const void*)w0, n);
     }
   };
-  // operands of one chunk: each warp writes whole core matrices (8 rows x 4 cells, 128 contiguous bytes)
+  // operands of one chunk: warp w builds row-cores w, w + 16, .. of A and B,
+  // all 8 cell-cores of each (8 rows x 4 cells, 128 contiguous bytes per core)
+  const int rr = lane >> 2, kk = lane & 3;
+  auto build_rows = [&](const float* w, const int4 f, float* hi, float* lo, int R, int r8) {
+    const float* x0 = w + f.x * UM_WPITCH + kk;
+    const float* x1 = w + f.y * UM_WPITCH + kk;
+    const float* x2 = w + f.z * UM_WPITCH + kk;
+    float* h = hi + r8 * 32 + lane;
+    float* l = lo + r8 * 32 + lane;
+#pragma unroll
+    for (int k4 = 0; k4 < UM_KC / 4; ++k4) {
+      const float v = x0[4 * k4] * x1[4 * k4] * x2[4 * k4];
+      const float vh = __uint_as_float(tf32_trunc(v));
+      h[k4 * (R / 8) * 32] = vh;  // core (r8, k4) of an R-row block
+      l[k4 * (R / 8) * 32] = v - vh;
+    }
+  };
   auto build = [&](int b) {
     const float* w = Ws(b);
-    const int rr = lane >> 2, kk = lane & 3;
-    float* ah = Ahi(b);
-    float* al = Alo(b);
-    for (int core = warp; core < (UM_M / 8) * (UM_KC / 4); core += UM_THREADS / 32) {
-      const int r8 = core % (UM_M / 8), k4 = core / (UM_M / 8);
-      const int r = 8 * r8 + rr, k = 4 * k4 + kk;
-      const int2 d = rd[r];
-      float v = 0.0f;
-      if (d.x != -2) {
-        v = w[k];
-        if (d.x >= 0) v *= w[(1 + d.x) * UM_WPITCH + k];
-        if (d.y >= 0) v *= w[(1 + d.y) * UM_WPITCH + k];
-      }
-      const float hi = __uint_as_float(tf32_trunc(v));
-      const int o = umma_off(UM_M, r, k);
-      ah[o] = hi;
-      al[o] = v - hi;
-    }
-    float* bh = Bhi(b);
-    float* bl = Blo(b);
-    for (int core = warp; core < (TN / 8) * (UM_KC / 4); core += UM_THREADS / 32) {
-      const int r8 = core % (TN / 8), k4 = core / (TN / 8);
-      const int r = 8 * r8 + rr, k = 4 * k4 + kk;
-      const int2 d = cd[r];
-      float v = 0.0f;
-      if (d.x != -2) {
-        v = 1.0f;
-        if (d.x >= 0) v *= w[(1 + d.x) * UM_WPITCH + k];
-        if (d.y >= 0) v *= w[(1 + d.y) * UM_WPITCH + k];
-      }
-      const float hi = __uint_as_float(tf32_trunc(v));
-      const int o = umma_off(TN, r, k);
-      bh[o] = hi;
-      bl[o] = v - hi;
-    }
+    for (int r8 = warp; r8 < UM_M / 8; r8 += UM_WARPS) build_rows(w, fa[8 * r8 + rr], Ahi(b), Alo(b), UM_M, r8);
+    for (int r8 = warp; r8 < TN / 8; r8 += UM_WARPS) build_rows(w, fb[8 * r8 + rr], Bhi(b), Blo(b), TN, r8);
   };
   // thread 0: the 12 MMAs of chunk c (operand buffer c & 1), then one commit
   auto issue = [&](int c) {
@@ -178,12 +179,12 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     umma_commit(&bar[b]);
   };
 
-  // register sums: warp w drains lanes 32 (w % 4).. of columns (w / 4) TN / 2 ..
-  constexpr int HALF = TN / 2;
-  float mid[HALF];
+  // register sums: warp w drains lanes 32 (w % 4).. of columns (w / 4) TN / 4 ..
+  constexpr int QTR = TN / 4;
+  float mid[QTR];
 #pragma unroll
-  for (int j = 0; j < HALF; ++j) mid[j] = 0.0f;
-  const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * HALF);
+  for (int j = 0; j < QTR; ++j) mid[j] = 0.0f;
+  const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * QTR);
 
   bool ok = true;
   int issued = 0;  // chunks whose MMAs have been committed
@@ -215,11 +216,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       if (ok) {
         tc_fence_after();
 #pragma unroll
-        for (int j0 = 0; j0 < HALF; j0 += 16) {
-          float v[16];
-          tmem_ld16(lane_base + j0, v);
+        for (int j0 = 0; j0 < QTR; j0 += 8) {
+          float v[8];
+          tmem_ld8(lane_base + j0, v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) mid[j0 + j] += v[j];
+          for (int j = 0; j < 8; ++j) mid[j0 + j] += v[j];
         }
         tc_fence_before();
       }
@@ -234,9 +235,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   if (warp == 0) tmem_free(tbase, S::ncols);
   double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (int64_t)(UM_M * TN);
   const int row = 32 * (warp & 3) + lane;
-  const int col0 = (warp >> 2) * HALF;
+  const int col0 = (warp >> 2) * QTR;
 #pragma unroll
-  for (int j = 0; j < HALF; ++j) out[row * TN + col0 + j] = (double)mid[j];
+  for (int j = 0; j < QTR; ++j) out[row * TN + col0 + j] = (double)mid[j];
 }
 
 // Which order (and multiset) a (row, column) pair computes: the same rule as
