@@ -168,6 +168,28 @@ ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const fl
 ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
                      int32_t order_mask, const ck_outputs* out, void* stream);
 
+/* --- batched form --------------------------------------------------------------
+ * Many catalogs over one or more plans (grid classes), each plan's randoms set
+ * once with ck_set_randoms.  Catalog i is computed on plans[cats[i].plan] and
+ * its outputs go to out[i] (as for ck_compute; out may be NULL).  On first use
+ * of a (plan, order_mask) pair the plan's compute sequence for one catalog
+ * (gridding through the normalised xi) is captured into a CUDA graph, on an
+ * internal stream, after any synchronous preparation; every catalog then costs
+ * one small descriptor kernel, one graph launch and its output copies, all in
+ * order on `stream`.  Positions must be device pointers (CK_ERR_BAD_POINTER
+ * otherwise); results are the same as ck_compute's.  Device statuses are read
+ * (and the stream synchronised) only if some output is in host memory. */
+typedef struct ck_catalog {
+  const float* x;
+  const float* y;
+  const float* z;
+  int64_t n;
+  int32_t plan;  /* index into `plans` */
+} ck_catalog;
+
+ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_catalog* cats, int32_t n_cats,
+                           int32_t order_mask, const ck_outputs* out, void* stream);
+
 /* Synchronise `stream` and return (and clear) the plan's device status. */
 ck_status ck_plan_status(ck_plan* plan, void* stream);
 

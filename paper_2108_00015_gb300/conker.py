@@ -70,6 +70,11 @@ class _Outputs(ctypes.Structure):
                 ("den", ctypes.c_void_p * (CK_MAX_ORDER + 1)), ("dropped", ctypes.c_void_p)]
 
 
+class _Catalog(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("plan", ctypes.c_int32)]
+
+
 _LIB = None
 
 # (name, restype, argtypes) for every entry point declared in include/conker.h
@@ -85,6 +90,8 @@ _SIGS = [
     ("ck_plan_get_info", ctypes.c_int, [_P, ctypes.POINTER(_Info)]),
     ("ck_set_randoms", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     ("ck_compute", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
+    ("ck_batch_compute", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_Catalog), ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_plan_status", ctypes.c_int, [_P, _P]),
     ("ck_get_grids", ctypes.c_int, [_P, _P, _P, _P]),
     ("ck_get_field", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
@@ -338,3 +345,42 @@ class Plan:
         _check(_lib().ck_contract(self._h, _ptr(w0), _ptr(bank), int(bank_stride), order_mask(orders), arr,
                                   _stream_ptr(stream)), "ck_contract")
         return sums
+
+
+def batch_compute(plans, catalogs, orders=(2, 3), out: str = "device", stream=None,
+                  want=("xi", "num", "den")):
+    """ck_batch_compute: catalogs is a sequence of (x, y, z, plan_index) with
+    device float32 positions; returns one result dict per catalog, as
+    Plan.compute does (dense [N_s]^(n-1) float64 tensors)."""
+    torch = _torch()
+    lib = _lib()
+    hs = (_P * len(plans))(*[p._h for p in plans])
+    cats = (_Catalog * max(1, len(catalogs)))()
+    outs = (_Outputs * max(1, len(catalogs)))()
+    dev = "cuda" if out == "device" else "cpu"
+    keep, results = [], []
+    for i, (x, y, z, j) in enumerate(catalogs):
+        x, y, z = _as_f32(x), _as_f32(y), _as_f32(z)
+        keep.append((x, y, z))
+        cats[i].x, cats[i].y, cats[i].z = _ptr(x), _ptr(y), _ptr(z)
+        cats[i].n = int(x.shape[0])
+        cats[i].plan = int(j)
+        ns = plans[j].n_shells if 0 <= int(j) < len(plans) else plans[0].n_shells  # the library rejects a bad index
+        res = {k: {} for k in ("xi", "num", "den")}
+        for n in orders:
+            if not 2 <= int(n) <= CK_MAX_ORDER:
+                continue
+            for key in want:
+                t = torch.empty((ns,) * (n - 1), dtype=torch.float64, device=dev, pin_memory=(dev == "cpu"))
+                res[key][n] = t
+                getattr(outs[i], key)[n] = t.data_ptr()
+        d = torch.zeros(2, dtype=torch.int64, device=dev)
+        outs[i].dropped = d.data_ptr()
+        res["dropped"] = d
+        results.append(res)
+    code = lib.ck_batch_compute(hs, len(plans), cats, len(catalogs), order_mask(orders), outs, _stream_ptr(stream))
+    if code not in (0, 7):
+        raise CkError(code, "ck_batch_compute")
+    for r in results:
+        r["status"] = int(code)
+    return results

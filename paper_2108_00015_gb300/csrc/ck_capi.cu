@@ -118,6 +118,7 @@ ck_status carve(Plan& p) {
   for (int a = 0; a < 3; ++a) p.tw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
   for (int a = 0; a < 3; ++a) p.stw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
   p.dstate = reinterpret_cast<DevState*>(take(sizeof(DevState)));
+  p.dref = reinterpret_cast<CatalogRef*>(take(sizeof(CatalogRef)));
   p.den_raw = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
   p.sums = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
   p.dense = reinterpret_cast<double*>(take((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8));
@@ -266,6 +267,52 @@ ck_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st, bo
   return CK_OK;
 }
 
+// Copy the finalised outputs of the requested orders (and the dropped
+// counts) to the caller's pointers; *host_seen is set for host destinations.
+ck_status copy_results(Plan& p, int order_mask, const ck_outputs* out, cudaStream_t st, bool* host_seen) {
+  if (!out) return CK_OK;
+  for (int k = 2; k <= p.max_order; ++k) {
+    if (!((order_mask >> k) & 1)) continue;
+    const size_t bytes = (size_t)p.dense_elems[k] * 8;
+    CK_TRY_S(copy_out(out->xi[k], p.dense + p.dense_base[k], bytes, st, host_seen));
+    CK_TRY_S(copy_out(out->num[k], p.dense + p.dense_total + p.dense_base[k], bytes, st, host_seen));
+    CK_TRY_S(copy_out(out->den[k], p.dense + 2 * p.dense_total + p.dense_base[k], bytes, st, host_seen));
+  }
+  CK_TRY_S(copy_out(out->dropped, p.dstate->dropped, 2 * sizeof(int64_t), st, host_seen));
+  return CK_OK;
+}
+
+// Capture one catalog's compute sequence (gridding from p.dref through the
+// finalised xi of order_mask) into an instantiated CUDA graph.
+ck_status capture_compute(Plan& p, int order_mask) {
+  if (p.gexec[order_mask]) return CK_OK;
+  if (!p.fused) CK_TRY_S(contract_prepare(p, order_mask));  // its table uploads are synchronous
+  if (!p.cap_stream) CK_TRY(cudaStreamCreateWithFlags(&p.cap_stream, cudaStreamNonBlocking));
+  const bool prof = p.prof.on;
+  p.prof.on = false;
+  cudaStream_t cs = p.cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  ck_status s = CK_OK;
+  if (e == cudaSuccess) {
+    reset_state_kernel<<<1, 1, 0, cs>>>(p.dstate, 0);
+    e = cudaMemsetAsync(p.counts[0], 0, (size_t)p.nc * 4, cs);
+    if (e == cudaSuccess) {
+      launch_grid_points_ref(p, 0, cs);
+      launch_prepare_data(p, cs);
+      s = convolve_and_sum(p, order_mask, p.sums, cs);
+      if (s == CK_OK) launch_finalize(p, order_mask, cs);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  p.prof.on = prof;
+  if (e == cudaSuccess && s == CK_OK) e = cudaGraphInstantiate(&p.gexec[order_mask], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (s != CK_OK) return s;
+  return cuda_status(e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -345,6 +392,9 @@ ck_status ck_plan_destroy(ck_plan* plan) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  for (auto& g : p->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->owns_ws && p->ws) cudaFree(p->ws);
   delete p;
   return cuda_status(e);
@@ -401,17 +451,49 @@ ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float*
   launch_finalize(p, order_mask, st);
   CK_TRY(cudaGetLastError());
   bool host_seen = false;
-  if (out) {
-    for (int k = 2; k <= p.max_order; ++k) {
-      if (!((order_mask >> k) & 1)) continue;
-      const size_t bytes = (size_t)p.dense_elems[k] * 8;
-      CK_TRY_S(copy_out(out->xi[k], p.dense + p.dense_base[k], bytes, st, &host_seen));
-      CK_TRY_S(copy_out(out->num[k], p.dense + p.dense_total + p.dense_base[k], bytes, st, &host_seen));
-      CK_TRY_S(copy_out(out->den[k], p.dense + 2 * p.dense_total + p.dense_base[k], bytes, st, &host_seen));
-    }
-    CK_TRY_S(copy_out(out->dropped, p.dstate->dropped, 2 * sizeof(int64_t), st, &host_seen));
-  }
+  CK_TRY_S(copy_results(p, order_mask, out, st, &host_seen));
   if (host_seen) return read_status(p, st, true);
+  return CK_OK;
+}
+
+ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_catalog* cats, int32_t n_cats,
+                           int32_t order_mask, const ck_outputs* out, void* stream) {
+  if (!plans || !cats || n_plans < 1 || n_cats < 0) return n_plans < 1 || n_cats < 0 ? CK_ERR_ARG : CK_ERR_BAD_POINTER;
+  if (n_cats == 0) return CK_OK;
+  for (int32_t j = 0; j < n_plans; ++j)
+    if (!plans[j]) return CK_ERR_BAD_POINTER;
+  for (int32_t i = 0; i < n_cats; ++i) {
+    const ck_catalog& c = cats[i];
+    if (c.plan < 0 || c.plan >= n_plans || c.n < 0) return CK_ERR_ARG;
+    Plan& p = *reinterpret_cast<Plan*>(plans[c.plan]);
+    if (order_mask == 0 || (order_mask & ~full_mask(p)) != 0) return CK_ERR_ARG;
+    if (!p.have_randoms) return CK_ERR_NO_RANDOMS;
+    if (c.n > 0 && (!c.x || !c.y || !c.z)) return CK_ERR_BAD_POINTER;
+    if (c.n > 0 && (!is_device_ptr(c.x) || !is_device_ptr(c.y) || !is_device_ptr(c.z))) return CK_ERR_BAD_POINTER;
+  }
+  cudaStream_t st = S(stream);
+  for (int32_t j = 0; j < n_plans; ++j) {
+    bool used = false;
+    for (int32_t i = 0; i < n_cats && !used; ++i) used = cats[i].plan == j;
+    if (used) CK_TRY_S(capture_compute(*reinterpret_cast<Plan*>(plans[j]), order_mask));
+  }
+  bool host_seen = false;
+  for (int32_t i = 0; i < n_cats; ++i) {
+    Plan& p = *reinterpret_cast<Plan*>(plans[cats[i].plan]);
+    launch_set_catalog_ref(p, cats[i].x, cats[i].y, cats[i].z, cats[i].n, st);
+    CK_TRY(cudaGraphLaunch(p.gexec[order_mask], st));
+    p.bank_holds = 0;
+    CK_TRY_S(copy_results(p, order_mask, out ? out + i : nullptr, st, &host_seen));
+  }
+  CK_TRY(cudaGetLastError());
+  if (host_seen) {
+    ck_status first = CK_OK;
+    for (int32_t j = 0; j < n_plans; ++j) {
+      const ck_status s = read_status(*reinterpret_cast<Plan*>(plans[j]), st, true);
+      if (first == CK_OK) first = s;
+    }
+    return first;
+  }
   return CK_OK;
 }
 

@@ -70,11 +70,9 @@ __device__ __forceinline__ bool axis_cell(float x, int a, const GridArgs& A, int
   return true;
 }
 
-__global__ void __launch_bounds__(256) grid_points_kernel(const float* __restrict__ xs,
-                                                          const float* __restrict__ ys,
-                                                          const float* __restrict__ zs, int64_t npts,
-                                                          GridArgs A, uint32_t* __restrict__ counts,
-                                                          DevState* st, int which) {
+__device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, const float* __restrict__ ys,
+                                                 const float* __restrict__ zs, int64_t npts, const GridArgs& A,
+                                                 uint32_t* __restrict__ counts, DevState* st, int which) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,9 +135,30 @@ __global__ void __launch_bounds__(256) grid_points_kernel(const float* __restric
   }
 }
 
-void launch_grid_points(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
-                        int which, cudaStream_t st) {
-  if (n <= 0) return;
+__global__ void __launch_bounds__(256) grid_points_kernel(const float* __restrict__ xs,
+                                                          const float* __restrict__ ys,
+                                                          const float* __restrict__ zs, int64_t npts,
+                                                          GridArgs A, uint32_t* __restrict__ counts,
+                                                          DevState* st, int which) {
+  grid_points_body(xs, ys, zs, npts, A, counts, st, which);
+}
+
+// The same with the catalog read from a device descriptor, so that one
+// launch (in a captured CUDA graph) serves any catalog.
+__global__ void __launch_bounds__(256) grid_points_ref_kernel(const CatalogRef* __restrict__ ref, GridArgs A,
+                                                              uint32_t* __restrict__ counts, DevState* st,
+                                                              int which) {
+  grid_points_body(ref->x, ref->y, ref->z, ref->n, A, counts, st, which);
+}
+
+__global__ void set_catalog_ref_kernel(CatalogRef* ref, const float* x, const float* y, const float* z, int64_t n) {
+  ref->x = x;
+  ref->y = y;
+  ref->z = z;
+  ref->n = n;
+}
+
+static GridArgs grid_args(const Plan& p) {
   GridArgs A;
   for (int a = 0; a < 3; ++a) {
     A.n[a] = p.grid.n[a];
@@ -150,6 +169,24 @@ void launch_grid_points(const Plan& p, const float* x, const float* y, const flo
   A.g = p.grid.cell;
   A.inv_g = (float)(1.0 / p.grid.cell);
   A.periodic = p.grid.periodic ? 1 : 0;
+  return A;
+}
+
+void launch_set_catalog_ref(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
+                            cudaStream_t st) {
+  set_catalog_ref_kernel<<<1, 1, 0, st>>>(p.dref, x, y, z, n);
+}
+
+void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st) {
+  ProfScope ps(p, ST_GRID, 0.0, st);
+  grid_points_ref_kernel<<<(unsigned)(p.sm_count * 8), 256, 0, st>>>(p.dref, grid_args(p), p.counts[which],
+                                                                     p.dstate, which);
+}
+
+void launch_grid_points(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
+                        int which, cudaStream_t st) {
+  if (n <= 0) return;
+  const GridArgs A = grid_args(p);
   const int64_t warps = (n + 31) / 32;
   int64_t blocks = std::min<int64_t>((warps + 7) / 8, (int64_t)p.sm_count * 8);
   if (blocks < 1) blocks = 1;

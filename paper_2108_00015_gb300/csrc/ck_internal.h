@@ -14,6 +14,14 @@ namespace ck {
 
 // Device-side state of a plan: point counters, occupied-cell bounding boxes,
 // alpha and the status word.  Index 0 = data catalog, 1 = randoms.
+// A catalog's device positions, read by the gridding kernel of a captured graph.
+struct CatalogRef {
+  const float* x;
+  const float* y;
+  const float* z;
+  int64_t n;
+};
+
 struct DevState {
   unsigned long long kept[2];
   unsigned long long dropped[2];
@@ -153,6 +161,11 @@ struct Plan {
 
   mutable Profiler prof;
 
+  // batched form: the catalog descriptor and one instantiated graph per order mask
+  CatalogRef* dref = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec[1 << (CK_MAX_ORDER + 1)] = {nullptr};
+
   bool have_randoms = false;
   int bank_holds = -1;  // field whose spectrum is resident: 0 = data, 1 = randoms
   // Convolution and sums in one pass (FP32, <= 16 shells, orders <= 3): the
@@ -188,6 +201,9 @@ struct ProfScope {
 // ---- launches (ck_grid.cu) ---------------------------------------------------
 void launch_grid_points(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
                         int which, cudaStream_t st);
+void launch_set_catalog_ref(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
+                            cudaStream_t st);
+void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // catalog from p.dref
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
 

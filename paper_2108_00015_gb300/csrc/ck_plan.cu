@@ -202,6 +202,7 @@ size_t workspace_bytes(const Plan& p) {
   for (int a = 0; a < 3; ++a) b += al((size_t)(p.grid.n[a] + 1) * 4);  // thresholds
   for (int a = 0; a < 3; ++a) b += 2 * al((size_t)p.grid.n[a] * 8);    // twiddles: full and per-iteration
   b += al(sizeof(DevState));
+  b += al(sizeof(CatalogRef));
   b += 2 * al((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8);   // den_raw, sums
   b += al((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8);        // dense staging
   b += al((size_t)std::max<int64_t>(p.dense_total, 1) * 4);            // dense map
