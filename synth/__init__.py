@@ -16,4 +16,5 @@ from .catalogs import (  # noqa: F401
     uniform_survey,
     workload,
     WORKLOADS,
+    batch_workload,
 )

@@ -336,3 +336,31 @@ def workload(name: str, scale: float = 1.0, with_points: bool = True) -> dict:
         w["data"] = _draw(*w["data"], w["grid"], scale)
         w["randoms"] = _draw(*w["randoms"], w["grid"], scale)
     return w
+
+# ---------------------------------------------------------------------------
+# Batched workload: 64 mocks in 8 periodic grid classes (side, cell), 8 mocks
+# per class, each with N_D log-uniform in [5e4, 2e6] points (20 children per
+# Neyman-Scott parent, sigma uniform in [4, 12], seed 100 + i) and one
+# uniform random catalog of 10M points per class (seed 200 + class); the
+# survey's 16 shells; orders 2..4.
+
+BATCH_CLASSES = ((128, 10.0), (160, 8.0), (192, 7.5), (240, 6.0), (256, 6.0), (288, 5.0), (320, 5.0), (384, 5.0))
+
+
+def batch_workload(scale: float = 1.0, mocks_per_class: int = 8, n_randoms: int = 10_000_000) -> dict:
+    """Grid classes with their randoms and the mocks as (class index, Catalog);
+    ``scale`` multiplies the point counts."""
+    classes = []
+    for c, (n, cell) in enumerate(BATCH_CLASSES):
+        g = GridSpec((n, n, n), (0.0, 0.0, 0.0), cell, True)
+        classes.append(dict(grid=g, randoms=uniform_box(200 + c, max(1, int(round(n_randoms * scale))), g.length)))
+    mocks = []
+    for i in range(len(BATCH_CLASSES) * mocks_per_class):
+        c = i // mocks_per_class
+        rng = np.random.Generator(np.random.PCG64(100 + i))
+        n_d = math.exp(rng.uniform(math.log(5e4), math.log(2e6))) * scale
+        sigma = rng.uniform(4.0, 12.0)
+        g = classes[c]["grid"]
+        mocks.append((c, neyman_scott_box(100 + i, max(1, int(round(n_d / 20))), 20, sigma, g.length)))
+    return dict(name="batch64", classes=classes, mocks=mocks, shells=_shells(30.0, 8.0, 16), width=8.0,
+                orders=(2, 3, 4))
