@@ -763,9 +763,9 @@ inline size_t xpass_smem(int nx) {
 
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).
-// row_ordered: prefer the kernel whose stores walk consecutive rows (large in-place passes)
+// wide: 16-column tiles for the 512-point register kernel (large multi-shell passes)
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, const float2* tw, bool row_ordered, int sm_count, cudaStream_t st);
+                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st);
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
                    cudaStream_t st);

@@ -1,14 +1,15 @@
 // ck_fft_strided.cu -- instantiations of the strided-axis (y, z) FFT pass and
 // of the multi-shell inverse z pass: 512-point axes run the register
-// two-step kernels (ck_fft_sreg.cuh) unless the caller asks for row-ordered
-// stores, the lengths of the grids in use (32 ... 512 cells per axis) the
-// compile-time Stockham kernels, and any other length the runtime version.
+// two-step kernels (ck_fft_sreg.cuh), the other lengths of the grids in use
+// (32 ... 384 cells per axis) the compile-time Stockham kernels, and any
+// other length the runtime version.
 //
-// Row-ordered stores: the Stockham kernel's last iteration writes 8
-// consecutive rows of the tile per warp instruction, the register kernel's
-// step B rows 128 apart.  On the 16-shell inverse y pass (8.6 GB in place,
-// rows 2 KB apart) the first sustained 5.2 TB/s on a GB300 and the second
-// 4.0 TB/s, while on single-field passes the register kernel is faster.
+// Tile width of the 512-point register kernels: 8 columns (256 threads, two
+// CTAs per SM) for single-field passes, 16 columns (512 threads, one CTA per
+// SM) when the caller asks for wide tiles.  On the 16-shell in-place inverse
+// y pass (8.6 GB) a GB300 sustained 5.6 TB/s with 16 columns, 5.2 TB/s with
+// the Stockham kernel and 4.0 TB/s with 8 columns; on single-field passes
+// 8 columns are the fastest.
 #include <algorithm>
 
 #include "ck_fft_core.cuh"
@@ -85,12 +86,13 @@ static void run_zmulti(const float2* in, float2* out, int64_t out_stride, int ns
       in, out, out_stride, nshells, v, f, stw, K);
 }
 
-#define CK_LENGTHS(X) X(32) X(128) X(160) X(192) X(240) X(256) X(288) X(320) X(384) X(512)
+#define CK_LENGTHS(X) X(32) X(128) X(160) X(192) X(240) X(256) X(288) X(320) X(384)
 
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, const float2* tw, bool row_ordered, int sm_count, cudaStream_t st) {
-  if (L == 512 && !row_ordered) {
-    run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st);
+                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st) {
+  if (L == 512) {
+    if (wide) run_sreg512<16>(inv, in, out, v, tw, sm_count, st);
+    else run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st);
     return;
   }
   switch (L) {
