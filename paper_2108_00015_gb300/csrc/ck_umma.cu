@@ -5,25 +5,33 @@
 // The outputs are the entries T[p][q] = sum_r A_p(r) B_q(r) of the blocked
 // product (A_p = W0 W_a W_b, B_q = W_c W_d, the same operand descriptors and
 // canonical pairs as contract_blocked_kernel), in output tiles of 128 rows
-// x TN columns held in tensor memory.  A CTA owns one tile and a range of
-// cells (split-K):
-//  * chunks of 32 cells are software-pipelined with one block barrier each:
-//    after the barrier of chunk c, thread 0 issues the MMAs of chunk c - 1,
-//    the CTA fetches the W values of chunk c + 1 with cp.async and builds
-//    the operands of chunk c straight into the core-matrix layout of
-//    ck_umma.cuh (double-buffered; a buffer is rebuilt once the commit of
-//    the MMAs that read it has arrived on its mbarrier);
-//  * every operand is split x = hi + lo, hi = x truncated to TF32 (exact),
-//    lo = x - hi, and each 8-cell step issues hi*hi, hi*lo and lo*hi as
-//    kind::tf32 MMAs (M = 128, N = TN, K = 8) accumulating in FP32 in
-//    tensor memory; the dropped lo*lo term is below 2^-21 relative;
-//  * every 8 chunks (256 cells) the accumulator is drained with tcgen05.ld
-//    into FP32 registers of the CTA's 16 warps (warp w: lanes 32 (w % 4)..,
-//    a quarter of the columns; the next chunk overwrites it), and each CTA
-//    writes its FP32 register sums (at most 64 groups) as FP64 partials,
-//    reduced over the splits in a fixed order.
-// Waits are bounded: on a timeout the CTA sets CK_ERR_TIMEOUT, stops
-// issuing, waits (bounded) for its own MMAs and frees its tensor memory.
+// x TN columns accumulated in tensor memory.  A CTA owns one tile and a
+// range of cells (split-K), walked in chunks of 32 cells by three kinds of
+// warps that meet only on mbarriers (no block barrier per chunk):
+//  * warp 0 stages the W values of a chunk (W0 and the bank rows, 128 bytes
+//    each) with cp.async.bulk copies into a ring of NW staging buffers;
+//  * warps 2..9 build the split operands of a chunk: warp w owns A rows
+//    32 (w % 4) .. + 31 (its tensor-memory lane quarter) for half of the
+//    chunk's cells and writes them with tcgen05.st into one of three A
+//    stages in tensor memory; together the eight warps write B into the
+//    matching shared-memory stage, in the no-swizzle K-major core layout of
+//    ck_umma.cuh;
+//  * one thread of warp 1 issues, per chunk, 12 kind::tf32 MMAs (M = 128,
+//    N = TN, K = 8; A from tensor memory, B from shared memory) and commits
+//    them to the stage's mbarrier, which frees the stage for the builders.
+// Every operand is split x = hi + lo, hi = x truncated to TF32 (exact),
+// lo = x - hi, and each 8-cell step issues hi*hi, hi*lo and lo*hi,
+// accumulating in FP32 in tensor memory; the dropped lo*lo term is below
+// 2^-21 relative.  Every 8 chunks (256 cells) close an accumulation group:
+// the builder warps drain its accumulator with tcgen05.ld into FP32
+// registers while the MMAs of the next group run into the second
+// accumulator (two accumulators where tensor memory holds them, else one,
+// drained before the next group starts).  Each CTA writes its FP32
+// register sums (at most 64 groups) as FP64 partials, reduced over the
+// splits in a fixed order.
+// Waits are bounded: on a timeout a warp sets CK_ERR_TIMEOUT and stops;
+// before tensor memory is freed the MMA thread waits (bounded) for its last
+// commit and the staging warp for its copies in flight.
 #include <algorithm>
 #include <vector>
 
@@ -41,77 +49,97 @@ constexpr int UM_KC = 32;             // cells per chunk: 4 MMA k-steps of 8
 constexpr int UM_GROUP = 8;           // chunks per tensor-memory accumulation (256 cells)
 constexpr int UM_MAX_GROUPS = 64;     // groups per CTA (FP32 register sums)
 constexpr int UM_WPITCH = UM_KC + 4;  // W staging row pitch (floats)
-constexpr int UM_THREADS = 512;
-constexpr int UM_WARPS = UM_THREADS / 32;
+constexpr int UM_NA = 3;              // operand stages
+constexpr int UM_MAX_NW = 4;          // W staging buffers (at most)
+constexpr int UM_BWARPS = 8;          // builder warps: two per tensor-memory lane quarter
+constexpr int UM_THREADS = 32 * (2 + UM_BWARPS);
+constexpr int UM_ACOLS = 2 * UM_KC;   // tensor-memory columns of one A stage: hi | lo
 
 template <int TN>
 struct UmmaShape {
-  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, four column quarters of 8s");
-  static constexpr size_t a_bytes = (size_t)UM_M * UM_KC * sizeof(float);
+  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, two column halves of 16s");
   static constexpr size_t b_bytes = (size_t)TN * UM_KC * sizeof(float);
-  static constexpr size_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // A hi, A lo, B hi, B lo
-  static constexpr uint32_t ncols = TN <= 32 ? 32 : (TN <= 64 ? 64 : (TN <= 128 ? 128 : 256));
+  static constexpr size_t stage_bytes = 2 * b_bytes;  // B hi | B lo
+  // two accumulators when they fit next to the A stages in 512 columns
+  static constexpr int nacc = 2 * TN + UM_NA * UM_ACOLS <= 512 ? 2 : 1;
+  static constexpr int a_col0 = nacc * TN;
+  static constexpr int used = a_col0 + UM_NA * UM_ACOLS;
+  static_assert(used <= 512, "tensor memory");
+  static constexpr uint32_t ncols = used <= 32 ? 32 : (used <= 64 ? 64 : (used <= 128 ? 128 : (used <= 256 ? 256 : 512)));
+  static constexpr int half = TN / 2;  // accumulator columns drained by one warp
 };
 
 // W staging rows per buffer: W0, the ns shells, a row of ones and a row of zeros
 __host__ __device__ constexpr int um_wrows(int ns) { return ns + 3; }
 
 template <int TN>
-size_t umma_smem(int ns) {
+size_t umma_smem(int ns, int nw) {
   using S = UmmaShape<TN>;
-  return 2 * S::stage_bytes + (size_t)2 * um_wrows(ns) * UM_WPITCH * sizeof(float) +
-         (size_t)(UM_M + TN) * sizeof(int4) + 64;
+  return UM_NA * S::stage_bytes + (size_t)nw * um_wrows(ns) * UM_WPITCH * sizeof(float) + (size_t)TN * sizeof(int4) +
+         (2 * UM_MAX_NW + 2 * UM_NA + 4) * sizeof(uint64_t) + 16 + 1024;
+}
+
+template <int TN>
+int umma_nw(int ns, size_t limit) {
+  for (int nw = UM_MAX_NW; nw >= 2; --nw)
+    if (umma_smem<TN>(ns, nw) <= limit) return nw;
+  return 0;
 }
 
 template <int TN>
 __global__ void __launch_bounds__(UM_THREADS, 1)
     contract_umma_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
-                         int ns, const int2* __restrict__ rowdesc, int rows, const int2* __restrict__ coldesc,
+                         int ns, int nw, const int2* __restrict__ rowdesc, int rows, const int2* __restrict__ coldesc,
                          int cols, const int2* __restrict__ tiles, int ntiles, int64_t cells_per_split,
                          double* __restrict__ partials, int* status) {
   using S = UmmaShape<TN>;
-  extern __shared__ __align__(1024) unsigned char um_smem[];
-  unsigned char* stages = um_smem;  // [2][A hi | A lo | B hi | B lo]
+  extern __shared__ unsigned char um_smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(um_smem_raw) + 1023) &
+                                                         ~(uintptr_t)1023);
+  unsigned char* stages = smem;  // [UM_NA][B hi | B lo]
   const int WR = um_wrows(ns);
-  float* wsb = reinterpret_cast<float*>(um_smem + 2 * S::stage_bytes);  // [2][WR][WPITCH]
-  int4* fa = reinterpret_cast<int4*>(wsb + 2 * WR * UM_WPITCH);         // [128] factor rows of A_p
-  int4* fb = fa + UM_M;                                                  // [TN]  factor rows of B_q
-  uint64_t* bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(fb + TN) + 15) & ~(uintptr_t)15);     // [2]
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  auto Ahi = [&](int b) { return reinterpret_cast<float*>(stages + b * S::stage_bytes); };
-  auto Alo = [&](int b) { return reinterpret_cast<float*>(stages + b * S::stage_bytes + S::a_bytes); };
-  auto Bhi = [&](int b) { return reinterpret_cast<float*>(stages + b * S::stage_bytes + 2 * S::a_bytes); };
-  auto Blo = [&](int b) {
-    return reinterpret_cast<float*>(stages + b * S::stage_bytes + 2 * S::a_bytes + S::b_bytes);
-  };
+  float* wsb = reinterpret_cast<float*>(smem + UM_NA * S::stage_bytes);  // [nw][WR][WPITCH]
+  int4* fb = reinterpret_cast<int4*>(wsb + nw * WR * UM_WPITCH);          // [TN] factor rows of B_q
+  uint64_t* bar = reinterpret_cast<uint64_t*>(fb + TN);
+  uint64_t* wfull = bar;                     // [UM_MAX_NW] W staged (bulk-copy bytes)
+  uint64_t* wempty = wfull + UM_MAX_NW;      // [UM_MAX_NW] W read by the builder warps
+  uint64_t* sfull = wempty + UM_MAX_NW;      // [UM_NA] operands of a stage written
+  uint64_t* sempty = sfull + UM_NA;          // [UM_NA] MMAs of a stage complete (commit)
+  uint64_t* afull = sempty + UM_NA;          // [2] MMAs of a group complete (commit)
+  uint64_t* aempty = afull + 2;              // [2] accumulator drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
+  auto Bhi = [&](int s) { return reinterpret_cast<float*>(stages + s * S::stage_bytes); };
+  auto Blo = [&](int s) { return reinterpret_cast<float*>(stages + s * S::stage_bytes + S::b_bytes); };
   auto Ws = [&](int b) { return wsb + b * WR * UM_WPITCH; };
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int2 tile = tiles[blockIdx.x];
-  // each operand row is the product of three staged rows: A_p = W0 W_a W_b, B_q = 1 W_c W_d,
+  // each operand row is the product of staged rows: A_p = W0 W_a W_b, B_q = W_c W_d,
   // with the ones row for an absent factor and the zeros row for a padding row
   const int ONE = ns + 1, ZERO = ns + 2;
-  for (int i = tid; i < UM_M; i += UM_THREADS) {
-    const int p = tile.x + i;
-    const int2 d = p < rows ? rowdesc[p] : make_int2(-2, -2);
-    fa[i] = d.x == -2 ? make_int4(ZERO, ONE, ONE, 0)
-                      : make_int4(0, d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0);
-  }
   for (int i = tid; i < TN; i += UM_THREADS) {
     const int q = tile.y + i;
     const int2 d = q < cols ? coldesc[q] : make_int2(-2, -2);
-    fb[i] = d.x == -2 ? make_int4(ZERO, ONE, ONE, 0)
-                      : make_int4(ONE, d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0);
+    fb[i] = d.x == -2 ? make_int4(ZERO, ONE, 0, 0) : make_int4(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0, 0);
   }
-  for (int i = tid; i < 2 * UM_KC; i += UM_THREADS) {  // constant rows of both staging buffers
-    float* w = wsb + (i / UM_KC) * WR * UM_WPITCH;
+  for (int i = tid; i < nw * UM_KC; i += UM_THREADS) {  // constant rows of every staging buffer
+    float* w = Ws(i / UM_KC);
     w[ONE * UM_WPITCH + i % UM_KC] = 1.0f;
     w[ZERO * UM_WPITCH + i % UM_KC] = 0.0f;
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int i = 0; i < UM_MAX_NW; ++i) {
+      mbar_init(&wfull[i], 1);
+      mbar_init(&wempty[i], UM_BWARPS);
+    }
+    for (int i = 0; i < UM_NA; ++i) {
+      mbar_init(&sfull[i], UM_BWARPS);
+      mbar_init(&sempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&afull[i], 1);
+      mbar_init(&aempty[i], UM_BWARPS);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tslot, S::ncols);
@@ -123,121 +151,179 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
   const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
   const int nch = end > beg ? (int)((end - beg + UM_KC - 1) / UM_KC) : 0;
-  // W values of chunk c into staging buffer b: 16-byte copies of 4 cells,
-  // zero past `end` (w0, the bank rows, bstride and beg are multiples of 4 floats)
-  auto stage = [&](int c, int b) {
-    const int64_t c0 = beg + (int64_t)c * UM_KC;
-    float* dst = Ws(b);
-    for (int idx = tid; idx < (ns + 1) * (UM_KC / 4); idx += UM_THREADS) {  // rows 0..ns only
-      const int a = idx / (UM_KC / 4), j = idx - a * (UM_KC / 4);
-      const int64_t cell = c0 + 4 * j;
-      const int64_t left = end - cell;
-      const int n = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
-      const float* src = a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride;
-      cp_async16n(dst + a * UM_WPITCH + 4 * j, n > 0 ? (const void*)(src + cell) : (const void*)w0, n);
-    }
-  };
-  // operands of one chunk: warp w builds row-cores w, w + 16, .. of A and B,
-  // all 8 cell-cores of each (8 rows x 4 cells, 128 contiguous bytes per core)
-  const int rr = lane >> 2, kk = lane & 3;
-  auto build_rows = [&](const float* w, const int4 f, float* hi, float* lo, int R, int r8) {
-    const float* x0 = w + f.x * UM_WPITCH + kk;
-    const float* x1 = w + f.y * UM_WPITCH + kk;
-    const float* x2 = w + f.z * UM_WPITCH + kk;
-    float* h = hi + r8 * 32 + lane;
-    float* l = lo + r8 * 32 + lane;
-#pragma unroll
-    for (int k4 = 0; k4 < UM_KC / 4; ++k4) {
-      const float v = x0[4 * k4] * x1[4 * k4] * x2[4 * k4];
-      const float vh = __uint_as_float(tf32_trunc(v));
-      h[k4 * (R / 8) * 32] = vh;  // core (r8, k4) of an R-row block
-      l[k4 * (R / 8) * 32] = v - vh;
-    }
-  };
-  auto build = [&](int b) {
-    const float* w = Ws(b);
-    for (int r8 = warp; r8 < UM_M / 8; r8 += UM_WARPS) build_rows(w, fa[8 * r8 + rr], Ahi(b), Alo(b), UM_M, r8);
-    for (int r8 = warp; r8 < TN / 8; r8 += UM_WARPS) build_rows(w, fb[8 * r8 + rr], Bhi(b), Blo(b), TN, r8);
-  };
-  // thread 0: the 12 MMAs of chunk c (operand buffer c & 1), then one commit
-  auto issue = [&](int c) {
-    const int b = c & 1;
-    constexpr uint32_t idesc = umma_idesc_tf32(UM_M, TN);
-    constexpr uint32_t a_lbo = UM_M / 8 * 128, b_lbo = TN / 8 * 128;
-    const uint32_t ahs = smem_u32(Ahi(b)), als = smem_u32(Alo(b));
-    const uint32_t bhs = smem_u32(Bhi(b)), bls = smem_u32(Blo(b));
-    const bool first = c % UM_GROUP == 0;
-#pragma unroll
-    for (int s = 0; s < UM_KC / 8; ++s) {
-      const uint32_t ao = 2 * s * a_lbo, bo = 2 * s * b_lbo;  // two core columns (8 cells) per step
-      const uint64_t dah = umma_desc(ahs + ao, a_lbo, 128), dal = umma_desc(als + ao, a_lbo, 128);
-      const uint64_t dbh = umma_desc(bhs + bo, b_lbo, 128), dbl = umma_desc(bls + bo, b_lbo, 128);
-      umma_tf32(tbase, dah, dbh, idesc, !(first && s == 0));
-      umma_tf32(tbase, dah, dbl, idesc, true);
-      umma_tf32(tbase, dal, dbh, idesc, true);
-    }
-    umma_commit(&bar[b]);
-  };
+  const int ngroups = (nch + UM_GROUP - 1) / UM_GROUP;
+  constexpr int NACC = S::nacc;
+  constexpr uint32_t FULL = 0xFFFFFFFFu;
 
-  // register sums: warp w drains lanes 32 (w % 4).. of columns (w / 4) TN / 4 ..
-  constexpr int QTR = TN / 4;
-  float mid[QTR];
-#pragma unroll
-  for (int j = 0; j < QTR; ++j) mid[j] = 0.0f;
-  const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * QTR);
-
-  bool ok = true;
-  int issued = 0;  // chunks whose MMAs have been committed
-  if (nch > 0) stage(0, 0);
-  cp_async_commit();
-  for (int c = 0; c <= nch; ++c) {
-    cp_async_wait<0>();
-    if (__syncthreads_or(!ok)) break;  // W of chunk c landed, operands of chunk c - 1 built
-    if (c >= 1) {
-      if (tid == 0) {
-        tc_fence_after();
-        issue(c - 1);
-      }
-      issued = c;
-    }
-    if (c + 1 < nch) stage(c + 1, (c + 1) & 1);
-    cp_async_commit();
-    if (c < nch) {
-      // buffer c & 1 was read by the MMAs of chunk c - 2
-      if (c >= 2) ok = mbar_wait(&bar[c & 1], (uint32_t)((c - 2) >> 1) & 1u, status);
-      if (ok) build(c & 1);
-      fence_async_shared();  // the operands, written by this thread, for the tensor cores
-    }
-    // chunk c - 1 closes a group: drain the accumulator once its MMAs are done
-    // (tcgen05.ld is warp-collective: the warp decides together)
-    if (c >= 1 && ((c - 1) % UM_GROUP == UM_GROUP - 1 || c - 1 == nch - 1)) {
-      if (ok) ok = mbar_wait(&bar[(c - 1) & 1], (uint32_t)((c - 1) >> 1) & 1u, status);
-      ok = __all_sync(0xFFFFFFFFu, ok);
-      if (ok) {
-        tc_fence_after();
-#pragma unroll
-        for (int j0 = 0; j0 < QTR; j0 += 8) {
-          float v[8];
-          tmem_ld8(lane_base + j0, v);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) mid[j0 + j] += v[j];
+  if (warp == 0) {
+    // ---- staging: W0 and the bank rows of chunk c into buffer c % nw
+    bool ok = true;
+    int staged = 0;
+    for (int c = 0; c < nch; ++c) {
+      const int b = c % nw;
+      if (c >= nw) ok = mbar_wait(&wempty[b], (uint32_t)(c / nw - 1) & 1u, status);
+      if (!__all_sync(FULL, ok)) break;
+      const int64_t c0 = beg + (int64_t)c * UM_KC;
+      const int valid = (int)std::min<int64_t>(UM_KC, end - c0);
+      float* dst = Ws(b);
+      if (valid == UM_KC) {  // 16-byte aligned rows of 128 bytes (c0 is a multiple of 32 cells)
+        if (lane == 0) mbar_arrive_expect_tx(&wfull[b], (uint32_t)((ns + 1) * UM_KC * sizeof(float)));
+        __syncwarp();
+        for (int a = lane; a <= ns; a += 32)
+          bulk_g2s(dst + a * UM_WPITCH, (a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride) + c0,
+                   (uint32_t)(UM_KC * sizeof(float)), &wfull[b]);
+      } else {  // the last, partial chunk: plain copies, zeros past the end
+        for (int i = lane; i < (ns + 1) * UM_KC; i += 32) {
+          const int a = i / UM_KC, k = i - a * UM_KC;
+          const float* src = a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride;
+          dst[a * UM_WPITCH + k] = k < valid ? src[c0 + k] : 0.0f;
         }
-        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&wfull[b]);
       }
+      staged = c + 1;
     }
+    // no copy may still be landing in shared memory when the CTA ends
+    for (int c = std::max(0, staged - nw); c < staged; ++c) mbar_wait(&wfull[c % nw], (uint32_t)(c / nw) & 1u, status);
+  } else if (warp == 1) {
+    // ---- MMA issue (one thread)
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_tf32(UM_M, TN);
+      constexpr uint32_t b_lbo = TN / 8 * 128;
+      bool ok = true;
+      int last = -1;
+      for (int c = 0; c < nch; ++c) {
+        const int g = c / UM_GROUP, a = g % NACC, s = c % UM_NA;
+        const bool first = c % UM_GROUP == 0;
+        if (first && g >= NACC) ok = mbar_wait(&aempty[a], (uint32_t)(g / NACC - 1) & 1u, status);
+        if (ok) ok = mbar_wait(&sfull[s], (uint32_t)(c / UM_NA) & 1u, status);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t dt = tbase + (uint32_t)(a * TN);
+        const uint32_t ah = tbase + (uint32_t)(S::a_col0 + s * UM_ACOLS), al = ah + UM_KC;
+        const uint32_t bhs = smem_u32(Bhi(s)), bls = smem_u32(Blo(s));
+#pragma unroll
+        for (int k = 0; k < UM_KC / 8; ++k) {
+          const uint32_t bo = 2 * k * b_lbo;  // two core columns (8 cells) per step
+          const uint64_t dbh = umma_desc(bhs + bo, b_lbo, 128), dbl = umma_desc(bls + bo, b_lbo, 128);
+          umma_tf32_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
+          umma_tf32_ts(dt, ah + 8 * k, dbl, idesc, true);
+          umma_tf32_ts(dt, al + 8 * k, dbh, idesc, true);
+        }
+        umma_commit(&sempty[s]);
+        if (c % UM_GROUP == UM_GROUP - 1 || c == nch - 1) umma_commit(&afull[a]);
+        last = c;
+      }
+      // every MMA issued must be complete before tensor memory is freed
+      if (last >= 0) mbar_wait(&sempty[last % UM_NA], (uint32_t)(last / UM_NA) & 1u, status);
+    }
+  } else {
+    // ---- operand build and accumulator drains
+    const int bw = warp - 2;          // 0..7
+    const int qd = warp & 3;          // tensor-memory lane quarter
+    const int hf = bw >> 2;           // half of the chunk's cells (A) / of the columns (drain)
+    const int m = 32 * qd + lane;     // A row of this thread
+    int fx, fy, fz;
+    {
+      const int p = tile.x + m;
+      const int2 d = p < rows ? rowdesc[p] : make_int2(-2, -2);
+      fx = d.x == -2 ? ZERO : 0;
+      fy = d.x >= 0 ? 1 + d.x : ONE;
+      fz = d.y >= 0 ? 1 + d.y : ONE;
+    }
+    const uint32_t tq = tbase + ((uint32_t)(32 * qd) << 16);
+    float mid[S::half];
+#pragma unroll
+    for (int j = 0; j < S::half; ++j) mid[j] = 0.0f;
+    auto drain = [&](int g) -> bool {
+      const int a = g % NACC;
+      bool ok = mbar_wait(&afull[a], (uint32_t)(g / NACC) & 1u, status);
+      if (!__all_sync(FULL, ok)) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int j0 = 0; j0 < S::half; j0 += 16) {
+        float v[16];
+        tmem_ld16(tq + (uint32_t)(a * TN + hf * S::half + j0), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mid[j0 + j] += v[j];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aempty[a]);
+      return true;
+    };
+    // group g is drained after building chunk drain_at(g): half a group
+    // later with two accumulators, else before the next group needs it
+    auto drain_at = [&](int g) {
+      return NACC == 2 ? (g + 1) * UM_GROUP + UM_GROUP / 2 - 1 : (g + 1) * UM_GROUP + UM_NA - 1;
+    };
+    const int rr = lane & 7, kq = lane >> 3;
+    bool ok = true;
+    int next = 0;  // next group to drain
+    for (int c = 0; c < nch && ok; ++c) {
+      const int b = c % nw, s = c % UM_NA;
+      ok = mbar_wait(&wfull[b], (uint32_t)(c / nw) & 1u, status);
+      if (ok && c >= UM_NA) ok = mbar_wait(&sempty[s], (uint32_t)(c / UM_NA - 1) & 1u, status);
+      if (!__all_sync(FULL, ok)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const float* w = Ws(b);
+      {  // A row m, cells 16 hf .. 16 hf + 15: hi and lo into the stage's tensor-memory columns
+        const float4* x0 = reinterpret_cast<const float4*>(w + fx * UM_WPITCH + 16 * hf);
+        const float4* x1 = reinterpret_cast<const float4*>(w + fy * UM_WPITCH + 16 * hf);
+        const float4* x2 = reinterpret_cast<const float4*>(w + fz * UM_WPITCH + 16 * hf);
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 a0 = x0[j], a1 = x1[j], a2 = x2[j];
+          const float v[4] = {a0.x * a1.x * a2.x, a0.y * a1.y * a2.y, a0.z * a1.z * a2.z, a0.w * a1.w * a2.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            hi[4 * j + e] = tf32_trunc(v[e]);
+            lo[4 * j + e] = __float_as_uint(v[e] - __uint_as_float(hi[4 * j + e]));
+          }
+        }
+        const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * UM_ACOLS + 16 * hf);
+        tmem_st16(ta, hi);
+        tmem_st16(ta + UM_KC, lo);
+        tmem_wait_st();
+      }
+      // B: items (row core r8, cell half kh); lane: row 8 r8 + rr, cell core 4 kh + kq
+      float* bh = Bhi(s);
+      float* bl = Blo(s);
+      for (int it = bw; it < TN / 4; it += UM_BWARPS) {
+        const int r8 = it >> 1, kc = 4 * (it & 1) + kq;
+        const int4 f = fb[8 * r8 + rr];
+        const float4 u = *reinterpret_cast<const float4*>(w + f.x * UM_WPITCH + 4 * kc);
+        const float4 v = *reinterpret_cast<const float4*>(w + f.y * UM_WPITCH + 4 * kc);
+        const float p0 = u.x * v.x, p1 = u.y * v.y, p2 = u.z * v.z, p3 = u.w * v.w;
+        const float4 h = make_float4(__uint_as_float(tf32_trunc(p0)), __uint_as_float(tf32_trunc(p1)),
+                                     __uint_as_float(tf32_trunc(p2)), __uint_as_float(tf32_trunc(p3)));
+        const int off = (kc * (TN / 8) + r8) * 32 + rr * 4;  // core (r8, kc), row rr
+        *reinterpret_cast<float4*>(bh + off) = h;
+        *reinterpret_cast<float4*>(bl + off) = make_float4(p0 - h.x, p1 - h.y, p2 - h.z, p3 - h.w);
+      }
+      fence_async_shared();  // the B operands, for the tensor cores
+      tc_fence_before();     // the A operands (tcgen05.st), for the MMA thread
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&wempty[b]);
+        mbar_arrive(&sfull[s]);
+      }
+      while (ok && next < ngroups && c >= drain_at(next)) ok = drain(next++);
+    }
+    while (ok && next < ngroups) ok = drain(next++);
+    // per-CTA partials: row m, this warp's half of the columns
+    double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (int64_t)(UM_M * TN);
+#pragma unroll
+    for (int j = 0; j < S::half; ++j) out[m * TN + hf * S::half + j] = (double)mid[j];
   }
-  // after a timeout: the MMAs already committed must finish before tensor memory is freed
-  if (!ok && tid == 0 && issued > 0)
-    mbar_wait(&bar[(issued - 1) & 1], (uint32_t)((issued - 1) >> 1) & 1u, status);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_free(tbase, S::ncols);
-  double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (int64_t)(UM_M * TN);
-  const int row = 32 * (warp & 3) + lane;
-  const int col0 = (warp >> 2) * QTR;
-#pragma unroll
-  for (int j = 0; j < QTR; ++j) out[row * TN + col0 + j] = (double)mid[j];
 }
 
 // Which order (and multiset) a (row, column) pair computes: the same rule as
@@ -302,11 +388,13 @@ template <int TN>
 cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, const int2* rowdesc,
                           int rows, const int2* coldesc, int cols, const int2* tiles, int ntiles, int splits,
                           int64_t cps, double* partials, int* status, cudaStream_t st) {
-  const size_t sm = umma_smem<TN>(ns);
+  const int nw = umma_nw<TN>(ns, (size_t)227 * 1024);
+  if (nw == 0) return cudaErrorInvalidValue;
+  const size_t sm = umma_smem<TN>(ns, nw);
   cudaError_t e = cudaFuncSetAttribute(contract_umma_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntiles, (unsigned)splits);
-  contract_umma_kernel<TN><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, cols,
+  contract_umma_kernel<TN><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, nw, rowdesc, rows, coldesc, cols,
                                                          tiles, ntiles, cps, partials, status);
   return cudaGetLastError();
 }

@@ -197,13 +197,15 @@ def test_xi_split_tf32_all_orders(torch, p32, ref32):
     plan.close()
 
 
-@pytest.mark.parametrize("ns", [16, 20])
-def test_tc_blocked_contraction(torch, ns):
+@pytest.mark.parametrize("ns,dims", [(16, (24, 20, 18)), (20, (24, 20, 18)), (8, (30, 18, 10)), (12, (30, 18, 10))])
+def test_tc_blocked_contraction(torch, ns, dims):
     """The tensor-core blocked product (split-TF32) over a caller's bank,
-    orders 2..5 (n = 5 over 20 shells: 8855 multisets, several 64 x 64
-    tiles and split-K over the cells, ragged tail), against the oracle's
-    product sums of the same float32 fields."""
-    g = GridSpec((24, 20, 18), (0.0, 0.0, 0.0), 1.0, True)
+    orders 2..5, against the oracle's product sums of the same float32
+    fields.  The shell counts give output tiles of 128 x TN for every TN
+    (32: orders 2-4; 64, 128, 160, 256: order 5 over 8, 12, 16 and 20
+    shells), several row tiles and split-K over the cells; the 30 x 18 x 10
+    grid (5400 cells) ends in a partial 32-cell chunk."""
+    g = GridSpec(dims, (0.0, 0.0, 0.0), 1.0, True)
     rng = np.random.default_rng(50 + ns)
     nc = g.n_cells
     w0 = rng.normal(size=nc).astype(np.float32)
