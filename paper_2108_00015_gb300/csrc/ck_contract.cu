@@ -472,27 +472,67 @@ ck_status contract_prepare(Plan& p, int mask) {
   if ((mask >> 5) & 1)
     for (int k = 0; k < ns; ++k)
       for (int l = k; l < ns; ++l) cols.push_back(make_int2(k, l));  // sorted by (k, l)
-  // output tiles holding a canonical (p, q): 64 x 64 (CUDA cores) or
-  // 128 x TN (tensor cores, split-TF32 plans)
   c.use_tc = p.precision == CK_PREC_SPLIT_TF32;
-  const int TM = c.use_tc ? umma_tile_rows() : BK_T;
-  const int TNc = c.use_tc ? umma_tile_cols((int)cols.size()) : BK_T;
-  c.um_tn = c.use_tc ? TNc : 0;
-  std::vector<int2> tiles;
+  c.rows = (int)rows.size();
+  c.cols = (int)cols.size();
+  const size_t slot = p.table_arena_cap / (1 << (CK_MAX_ORDER + 1));
+  int2* base = reinterpret_cast<int2*>(p.table_arena + slot * mask);
   int ms[4];
-  for (int m0 = 0; m0 < (int)rows.size(); m0 += TM)
-    for (int n0 = 0; n0 < (int)cols.size(); n0 += TNc) {
+  if (c.use_tc) {
+    // tensor cores: per 128-row tile, the list of columns holding a
+    // canonical (p, q) with one of its rows, cut into tiles of at most 256
+    // columns; MMA N = the list length rounded up to 32
+    std::vector<int4> tl;
+    std::vector<int> clist;
+    const int TM = umma_tile_rows();
+    int tnmax = 0;
+    for (int m0 = 0; m0 < (int)rows.size(); m0 += TM) {
+      std::vector<int> need;
+      for (int qq = 0; qq < (int)cols.size(); ++qq) {
+        bool any = false;
+        for (int pp = m0; pp < std::min<int>(m0 + TM, (int)rows.size()) && !any; ++pp)
+          any = canonical(rows[pp], cols[qq], mask, ms) != 0;
+        if (any) need.push_back(qq);
+      }
+      for (size_t i = 0; i < need.size(); i += 256) {
+        const int cnt = (int)std::min<size_t>(256, need.size() - i);
+        const int tn = (cnt + 31) / 32 * 32;
+        tl.push_back(make_int4(m0, (int)clist.size(), tn, cnt));
+        clist.insert(clist.end(), need.begin() + i, need.begin() + i + cnt);
+        tnmax = std::max(tnmax, tn);
+      }
+    }
+    c.n_tiles = (int)tl.size();
+    c.um_tn = umma_tile_cols(std::max(tnmax, 32));
+    const size_t need_b = (rows.size() + cols.size()) * sizeof(int2) + tl.size() * sizeof(int4) + clist.size() * sizeof(int) + 16;
+    if (need_b > slot) return CK_ERR_OOM;
+    c.d_rowdesc = base;
+    c.d_coldesc = base + rows.size();
+    c.d_um_tiles = reinterpret_cast<int4*>((reinterpret_cast<uintptr_t>(c.d_coldesc + cols.size()) + 15) & ~(uintptr_t)15);
+    c.d_um_cols = reinterpret_cast<int*>(c.d_um_tiles + tl.size());
+    cudaError_t e = cudaMemcpy(c.d_rowdesc, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_coldesc, cols.data(), cols.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tl.empty()) e = cudaMemcpy(c.d_um_tiles, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !clist.empty()) e = cudaMemcpy(c.d_um_cols, clist.data(), clist.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e);
+    c.um_cps = umma_cells_per_split(p.nc, std::max(c.n_tiles, 1), p.sm_count);
+    c.splits = (int)((p.nc + c.um_cps - 1) / c.um_cps);
+    c.partial_doubles = (size_t)c.splits * std::max(c.n_tiles, 1) * TM * c.um_tn;
+    if (c.partial_doubles > p.partials_cap) return CK_ERR_OOM;
+    p.cplan_ready[mask] = true;
+    return CK_OK;
+  }
+  // CUDA cores: the 64 x 64 output tiles holding a canonical (p, q)
+  std::vector<int2> tiles;
+  for (int m0 = 0; m0 < (int)rows.size(); m0 += BK_T)
+    for (int n0 = 0; n0 < (int)cols.size(); n0 += BK_T) {
       bool any = false;
-      for (int pp = m0; pp < std::min<int>(m0 + TM, (int)rows.size()) && !any; ++pp)
-        for (int qq = n0; qq < std::min<int>(n0 + TNc, (int)cols.size()) && !any; ++qq)
+      for (int pp = m0; pp < std::min<int>(m0 + BK_T, (int)rows.size()) && !any; ++pp)
+        for (int qq = n0; qq < std::min<int>(n0 + BK_T, (int)cols.size()) && !any; ++qq)
           any = canonical(rows[pp], cols[qq], mask, ms) != 0;
       if (any) tiles.push_back(make_int2(m0, n0));
     }
-  c.rows = (int)rows.size();
-  c.cols = (int)cols.size();
   c.n_tiles = (int)tiles.size();
-  const size_t slot = p.table_arena_cap / (1 << (CK_MAX_ORDER + 1));
-  int2* base = reinterpret_cast<int2*>(p.table_arena + slot * mask);
   if ((rows.size() + cols.size() + tiles.size()) * sizeof(int2) > slot) return CK_ERR_OOM;
   c.d_rowdesc = base;
   c.d_coldesc = base + rows.size();
@@ -502,14 +542,6 @@ ck_status contract_prepare(Plan& p, int mask) {
   if (e == cudaSuccess && !tiles.empty())
     e = cudaMemcpy(c.d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_status(e);
-  if (c.use_tc) {
-    c.um_cps = umma_cells_per_split(p.nc, std::max(c.n_tiles, 1), p.sm_count);
-    c.splits = (int)((p.nc + c.um_cps - 1) / c.um_cps);
-    c.partial_doubles = (size_t)c.splits * std::max(c.n_tiles, 1) * TM * TNc;
-    if (c.partial_doubles > p.partials_cap) return CK_ERR_OOM;
-    p.cplan_ready[mask] = true;
-    return CK_OK;
-  }
   const int64_t per_split = (int64_t)std::max(c.n_tiles, 1) * BK_T * BK_T;
   int64_t splits = std::max<int64_t>(1, (int64_t)(4 * p.sm_count + c.n_tiles - 1) / std::max(c.n_tiles, 1));
   splits = std::min<int64_t>(splits, (int64_t)(p.partials_cap / per_split));
@@ -545,13 +577,13 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
     cudaError_t e;
     {
       ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, st);
-      e = launch_umma(c.um_tn, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc, c.cols, c.d_tiles,
-                      c.n_tiles, c.splits, c.um_cps, p.partials, status, st);
+      e = launch_umma(c.um_tn, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
+                      c.d_um_cols, c.n_tiles, c.splits, c.um_cps, p.partials, status, st);
     }
     if (e != cudaSuccess) return cuda_status(e);
     ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);
-    return cuda_status(launch_umma_reduce(p.partials, c.splits, c.n_tiles, c.um_tn, c.d_tiles, c.d_rowdesc, c.rows,
-                                          c.d_coldesc, c.cols, mask, p.ns, p.multiset_base, sums, st));
+    return cuda_status(launch_umma_reduce(p.partials, c.splits, c.n_tiles, c.um_tn, c.d_um_tiles, c.d_um_cols,
+                                          c.d_rowdesc, c.rows, c.d_coldesc, mask, p.ns, p.multiset_base, sums, st));
   }
   const int64_t cps = (p.nc + c.splits - 1) / c.splits;
   const int64_t cps_al = (cps + 31) / 32 * 32;

@@ -70,7 +70,7 @@ struct ContractPlan {
   int order_mask = 0;
   bool use_reg = false;     // register-accumulator kernel (few outputs)
   bool use_tc = false;      // blocked product on the tensor cores (split-TF32, tcgen05)
-  int um_tn = 0;            // tcgen05 tiles: 128 rows x um_tn columns
+  int um_tn = 0;            // tcgen05 tiles: 128 rows x at most um_tn columns
   int64_t um_cps = 0;       // tcgen05: cells per split
   int reg_maxn = 0;         // orders 2..reg_maxn computed by that kernel
   int n_out_reg = 0;        // outputs of the register kernel
@@ -83,6 +83,8 @@ struct ContractPlan {
   int2* d_rowdesc = nullptr;
   int2* d_coldesc = nullptr;
   int2* d_tiles = nullptr;   // (m0, n0) per active tile
+  int4* d_um_tiles = nullptr;  // tcgen05: (m0, column-list offset, MMA N, columns) per tile
+  int* d_um_cols = nullptr;    // tcgen05: the tiles' column lists
   int* d_slot = nullptr;     // [n_tiles][64][64] -> output slot or -1
   size_t partial_doubles = 0;
 };
@@ -231,12 +233,13 @@ ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaS
 int umma_tile_rows();
 int umma_tile_cols(int cols);
 int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count);
+// A tile is (first row, offset of its column list, MMA N <= tn, list length).
 cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
-                        const int2* rowdesc, int rows, const int2* coldesc, int cols, const int2* tiles, int ntiles,
-                        int splits, int64_t cps, double* partials, int* status, cudaStream_t st);
-cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, int tn, const int2* tiles,
-                               const int2* rowdesc, int rows, const int2* coldesc, int cols, int mask, int ns,
-                               const int64_t* bases, double* out, cudaStream_t st);
+                        const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
+                        int ntiles, int splits, int64_t cps, double* partials, int* status, cudaStream_t st);
+cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, int tn, const int4* tiles,
+                               const int* collist, const int2* rowdesc, int rows, const int2* coldesc, int mask,
+                               int ns, const int64_t* bases, double* out, cudaStream_t st);
 
 // ---- launches (ck_contract.cu) -----------------------------------------------
 ck_status contract_prepare(Plan& p, int order_mask);

@@ -176,7 +176,10 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   // Contraction operand tables: one slot per order mask.
   const int64_t rows = 1 + p->ns + (int64_t)p->ns * (p->ns + 1) / 2;
   const int64_t tiles = ((rows + 63) / 64) * ((rows + 63) / 64);
-  p->table_arena_cap = (size_t)(1 << (CK_MAX_ORDER + 1)) * (size_t)(2 * rows + tiles + 8) * sizeof(int2);
+  // tcgen05 tiles: per 128-row tile, records (int4) and a column list (ints)
+  const int64_t rtiles = (rows + 127) / 128;
+  const int64_t tc = rtiles * (2 * ((rows + 255) / 256 + 1) + (rows + 1) / 2) + 16;
+  p->table_arena_cap = (size_t)(1 << (CK_MAX_ORDER + 1)) * (size_t)(2 * rows + std::max(tiles, tc) + 8) * sizeof(int2);
   return CK_OK;
 }
 
