@@ -51,79 +51,85 @@ namespace ck {
 namespace {
 
 constexpr int UM_M = 128;
-constexpr int UM_KC = 32;             // cells per chunk: 4 MMA k-steps of 8
-constexpr int UM_GROUP = 8;           // chunks per tensor-memory accumulation (256 cells)
+constexpr int UM_GCELLS = 256;        // cells per tensor-memory accumulation group
 constexpr int UM_MAX_GROUPS = 64;     // groups per CTA (FP32 register sums)
-constexpr int UM_NA = 3;              // operand stages
-constexpr int UM_MAX_NW = 3;          // W staging buffers (at most)
-constexpr int UM_BWARPS = 16;         // builder warps: four per tensor-memory lane quarter
+constexpr int UM_MAX_NA = 3;          // operand stages (at most)
+constexpr int UM_MAX_NW = 2;          // W staging buffers
+constexpr int UM_BWARPS = 8;          // builder warps: two per tensor-memory lane quarter
 constexpr int UM_THREADS = 32 * (2 + UM_BWARPS);
-constexpr int UM_ACOLS = 2 * UM_KC;   // tensor-memory columns of one A stage: hi | lo
 
+// Per tile width TN: cells per chunk KC (64, or 32 where the operand stages
+// would not fit), operand stages NA, accumulators in tensor memory (two
+// where they fit next to the A stages in 512 columns, else one).
 template <int TN>
 struct UmmaShape {
-  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, four column quarters of 8s");
-  static constexpr size_t b_bytes = (size_t)TN * UM_KC * sizeof(float);
-  static constexpr size_t stage_bytes = 2 * b_bytes;  // B hi | B lo
-  // two accumulators when they fit next to the A stages in 512 columns
-  static constexpr int nacc = 2 * TN + UM_NA * UM_ACOLS <= 512 ? 2 : 1;
+  static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, two column halves of 16s");
+  static constexpr int KC = TN <= 160 ? 64 : 32;
+  static constexpr int NK = KC / 8;                            // MMA k-steps per chunk
+  static constexpr int ACOLS = 2 * KC;                         // A stage: hi | lo
+  static constexpr int NA = (TN == 128 || TN == 160) ? 2 : 3;
+  static constexpr int G = UM_GCELLS / KC;                     // chunks per group
+  static constexpr size_t b_bytes = (size_t)TN * KC * sizeof(float);
+  static constexpr size_t stage_bytes = 2 * b_bytes;           // B hi | B lo
+  static constexpr int nacc = 2 * TN + NA * ACOLS <= 512 ? 2 : 1;
   static constexpr int a_col0 = nacc * TN;
-  static constexpr int used = a_col0 + UM_NA * UM_ACOLS;
-  static_assert(used <= 512, "tensor memory");
+  static constexpr int used = a_col0 + NA * ACOLS;
+  static_assert(NA <= UM_MAX_NA && used <= 512, "tensor memory");
   static constexpr uint32_t ncols = used <= 32 ? 32 : (used <= 64 ? 64 : (used <= 128 ? 128 : (used <= 256 ? 256 : 512)));
-  static constexpr int quarter = TN / 4;  // accumulator columns drained by one warp (at most)
+  static constexpr int half = TN / 2;     // accumulator columns drained by one warp (at most)
+  static constexpr int UN = TN / 32;      // B units per warp (at most): 2 TN / 8 units over 8 warps
 };
 
 // W staging rows per buffer: W0, the ns shells, a row of ones and a row of zeros
 __host__ __device__ constexpr int um_wrows(int ns) { return ns + 3; }
 
-// W staging row pitch (floats) for wch chunks per buffer: 16-byte rows
+// W staging row pitch (floats) for `cells` cells per buffer: 16-byte rows
 // whose 16-byte index is 1 mod 8, so eight lanes reading eight different
 // rows at the same cell hit eight different bank groups
-__host__ __device__ constexpr int um_wpitch(int wch) { return wch * UM_KC + 4; }
+__host__ __device__ constexpr int um_wpitch(int cells) { return cells + 4; }
 
 template <int TN>
-size_t umma_smem(int ns, int nw, int wch) {
+size_t umma_smem(int ns, int wcells) {
   using S = UmmaShape<TN>;
-  return UM_NA * S::stage_bytes + (size_t)nw * um_wrows(ns) * um_wpitch(wch) * sizeof(float) +
-         (size_t)TN * sizeof(int4) + (2 * UM_MAX_NW + 2 * UM_NA + 4) * sizeof(uint64_t) + 16;
+  return S::NA * S::stage_bytes + (size_t)UM_MAX_NW * um_wrows(ns) * um_wpitch(wcells) * sizeof(float) +
+         (size_t)TN * sizeof(int4) + (2 * UM_MAX_NW + 2 * UM_MAX_NA + 4) * sizeof(uint64_t) + 16;
 }
 
-// Staging buffers and chunks per buffer: the longest bulk copies that fit
-// (8 chunks = 1 KB per row), double-buffered.
+// Cells per staging buffer: the longest bulk copies that fit (256 cells =
+// 1 KB per row), a whole number of chunks, double-buffered.
 template <int TN>
-bool umma_staging(int ns, size_t limit, int* nw, int* wch) {
-  for (int c = 8; c >= 1; c /= 2)
-    if (umma_smem<TN>(ns, 2, c) <= limit) {
-      *nw = 2;
-      *wch = c;
-      return true;
-    }
-  return false;
+int umma_wcells(int ns, size_t limit) {
+  using S = UmmaShape<TN>;
+  for (int c = 256; c >= S::KC; c /= 2)
+    if (umma_smem<TN>(ns, c) <= limit) return c;
+  return 0;
 }
 
 template <int TN>
 __global__ void __launch_bounds__(UM_THREADS, 1)
     contract_umma_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
-                         int ns, int nw, int wch, const int2* __restrict__ rowdesc, int rows, const int2* __restrict__ coldesc,
-                         const int4* __restrict__ tiles, const int* __restrict__ collist, int ntiles,
-                         int64_t cells_per_split, double* __restrict__ partials, int* status) {
+                         int ns, int wcells, const int2* __restrict__ rowdesc, int rows,
+                         const int2* __restrict__ coldesc, const int4* __restrict__ tiles,
+                         const int* __restrict__ collist, int ntiles, int64_t cells_per_split,
+                         double* __restrict__ partials, int* status) {
   using S = UmmaShape<TN>;
+  constexpr int KC = S::KC, NA = S::NA, G = S::G, NACC = S::nacc;
+  constexpr int nw = UM_MAX_NW;
   // every shared-memory pointer derives from the array by pointer arithmetic
   // (no integer round trip), so the compiler emits shared-space accesses
   extern __shared__ __align__(1024) unsigned char um_smem[];
-  unsigned char* smem = um_smem;
-  unsigned char* stages = smem;  // [UM_NA][B hi | B lo]
+  unsigned char* stages = um_smem;  // [NA][B hi | B lo]
   const int WR = um_wrows(ns);
-  const int wp = um_wpitch(wch);
-  float* wsb = reinterpret_cast<float*>(smem + UM_NA * S::stage_bytes);  // [nw][WR][wp]
+  const int wp = um_wpitch(wcells);
+  const int wch = wcells / KC;  // chunks per staging buffer
+  float* wsb = reinterpret_cast<float*>(um_smem + NA * S::stage_bytes);  // [nw][WR][wp]
   int4* fb = reinterpret_cast<int4*>(wsb + nw * WR * wp);                 // [TN] factor rows of B_q
   uint64_t* bar = reinterpret_cast<uint64_t*>(fb + TN);
-  uint64_t* wfull = bar;                     // [UM_MAX_NW] W staged (bulk-copy bytes)
-  uint64_t* wempty = wfull + UM_MAX_NW;      // [UM_MAX_NW] W read by the builder warps
-  uint64_t* sfull = wempty + UM_MAX_NW;      // [UM_NA] operands of a stage written
-  uint64_t* sempty = sfull + UM_NA;          // [UM_NA] MMAs of a stage complete (commit)
-  uint64_t* afull = sempty + UM_NA;          // [2] MMAs of a group complete (commit)
+  uint64_t* wfull = bar;                     // [nw] W staged (bulk-copy bytes)
+  uint64_t* wempty = wfull + UM_MAX_NW;      // [nw] W read by the builder warps
+  uint64_t* sfull = wempty + UM_MAX_NW;      // [NA] operands of a stage written
+  uint64_t* sempty = sfull + UM_MAX_NA;      // [NA] MMAs of a stage complete (commit)
+  uint64_t* afull = sempty + UM_MAX_NA;      // [2] MMAs of a group complete (commit)
   uint64_t* aempty = afull + 2;              // [2] accumulator drained
   uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
   auto Bhi = [&](int s) { return reinterpret_cast<float*>(stages + s * S::stage_bytes); };
@@ -142,18 +148,17 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     const int2 d = i < tile.w ? coldesc[collist[tile.y + i]] : make_int2(-2, -2);
     fb[i] = d.x == -2 ? make_int4(ZERO, ONE, 0, 0) : make_int4(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0, 0);
   }
-  const int wcells = wch * UM_KC;  // cells per staging buffer
   for (int i = tid; i < nw * wcells; i += UM_THREADS) {  // constant rows of every staging buffer
     float* w = Ws(i / wcells);
     w[ONE * wp + i % wcells] = 1.0f;
     w[ZERO * wp + i % wcells] = 0.0f;
   }
   if (tid == 0) {
-    for (int i = 0; i < UM_MAX_NW; ++i) {
+    for (int i = 0; i < nw; ++i) {
       mbar_init(&wfull[i], 1);
       mbar_init(&wempty[i], UM_BWARPS);
     }
-    for (int i = 0; i < UM_NA; ++i) {
+    for (int i = 0; i < NA; ++i) {
       mbar_init(&sfull[i], UM_BWARPS);
       mbar_init(&sempty[i], 1);
     }
@@ -171,14 +176,12 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
 
   const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
   const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
-  const int nch = end > beg ? (int)((end - beg + UM_KC - 1) / UM_KC) : 0;
-  const int ngroups = (nch + UM_GROUP - 1) / UM_GROUP;
-  constexpr int NACC = S::nacc;
+  const int nch = end > beg ? (int)((end - beg + KC - 1) / KC) : 0;
+  const int ngroups = (nch + G - 1) / G;
   constexpr uint32_t FULL = 0xFFFFFFFFu;
 
   if (warp == 0) {
-    // ---- staging: W0 and the bank rows of chunks f wch .. f wch + wch - 1
-    // (fill f) into buffer f % nw
+    // ---- staging: W0 and the bank rows of fill f (chunks f wch ..) into buffer f % nw
     bool ok = true;
     int staged = 0;
     const int nfill = (nch + wch - 1) / wch;
@@ -216,17 +219,17 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       bool ok = true;
       int last = -1;
       for (int c = 0; c < nch; ++c) {
-        const int g = c / UM_GROUP, a = g % NACC, s = c % UM_NA;
-        const bool first = c % UM_GROUP == 0;
+        const int g = c / G, a = g % NACC, s = c % NA;
+        const bool first = c % G == 0;
         if (first && g >= NACC) ok = mbar_wait(&aempty[a], (uint32_t)(g / NACC - 1) & 1u, status);
-        if (ok) ok = mbar_wait(&sfull[s], (uint32_t)(c / UM_NA) & 1u, status);
+        if (ok) ok = mbar_wait(&sfull[s], (uint32_t)(c / NA) & 1u, status);
         if (!ok) break;
         tc_fence_after();
         const uint32_t dt = tbase + (uint32_t)(a * TN);
-        const uint32_t ah = tbase + (uint32_t)(S::a_col0 + s * UM_ACOLS), al = ah + UM_KC;
+        const uint32_t ah = tbase + (uint32_t)(S::a_col0 + s * S::ACOLS), al = ah + KC;
         const uint32_t bhs = smem_u32(Bhi(s)), bls = smem_u32(Blo(s));
 #pragma unroll
-        for (int k = 0; k < UM_KC / 8; ++k) {
+        for (int k = 0; k < S::NK; ++k) {
           const uint32_t bo = 2 * k * b_lbo;  // two core columns (8 cells) per step
           const uint64_t dbh = umma_desc(bhs + bo, b_lbo, 128), dbl = umma_desc(bls + bo, b_lbo, 128);
           umma_tf32_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
@@ -234,81 +237,85 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
           umma_tf32_ts(dt, al + 8 * k, dbh, idesc, true);
         }
         umma_commit(&sempty[s]);
-        if (c % UM_GROUP == UM_GROUP - 1 || c == nch - 1) umma_commit(&afull[a]);
+        if (c % G == G - 1 || c == nch - 1) umma_commit(&afull[a]);
         last = c;
       }
       // every MMA issued must be complete before tensor memory is freed
-      if (last >= 0) mbar_wait(&sempty[last % UM_NA], (uint32_t)(last / UM_NA) & 1u, status);
+      if (last >= 0) mbar_wait(&sempty[last % NA], (uint32_t)(last / NA) & 1u, status);
     }
   } else {
     // ---- operand build and accumulator drains
-    const int bw = warp - 2;          // 0..15
+    const int bw = warp - 2;          // 0..7
     const int qd = warp & 3;          // tensor-memory lane quarter
-    const int pt = bw >> 2;           // A: cells 8 pt .. 8 pt + 7; drains: column quarter pt
+    const int hf = bw >> 2;           // A: cells hf KC/2 .. + KC/2 - 1; drains: column half hf
     const int m = 32 * qd + lane;     // A row of this thread
-    int fx, fy, fz;
+    int ax, ay, az;                   // staged-row offsets of the three factors of A row m
     {
       const int p = tile.x + m;
       const int2 d = p < rows ? rowdesc[p] : make_int2(-2, -2);
-      fx = d.x == -2 ? ZERO : 0;
-      fy = d.x >= 0 ? 1 + d.x : ONE;
-      fz = d.y >= 0 ? 1 + d.y : ONE;
+      ax = (d.x == -2 ? ZERO : 0) * wp + hf * (KC / 2);
+      ay = (d.x >= 0 ? 1 + d.x : ONE) * wp + hf * (KC / 2);
+      az = (d.y >= 0 ? 1 + d.y : ONE) * wp + hf * (KC / 2);
     }
     const bool a_live = __any_sync(FULL, tile.x + m < rows);  // a lane quarter of padding rows stays zero
     const uint32_t tq = tbase + ((uint32_t)(32 * qd) << 16);
-    const int qc = tn / 4;  // accumulator columns this warp drains (a multiple of 8)
-    // B items of this warp, it = bw + 16 j: 8 columns (row core r8 = it / 2) x
-    // 4 cell cores (4 (it % 2) .. + 3); lane: column 8 r8 + rr, cell core kc
-    constexpr int IT = (TN / 4 + UM_BWARPS - 1) / UM_BWARPS;
+    const int hc = tn / 2;  // accumulator columns this warp drains (a multiple of 16)
+    // B units of this warp, u = bw + 8 j: row core r8 = u / 2, cells
+    // (u % 2) KC/2 .. + KC/2 - 1, in items of 16 cells; lane: column
+    // 8 r8 + rr, cell core 4 item + kq of the unit
     const int rr = lane & 7, kq = lane >> 3;
-    int bu[IT], bv[IT];
-    bool bl_live[IT], b_any[IT];
+    int bu[S::UN], bv[S::UN];
+    bool b_live[S::UN], b_any[S::UN];
 #pragma unroll
-    for (int j = 0; j < IT; ++j) {
-      const int it = bw + UM_BWARPS * j;
-      const int r8 = it >> 1, kc = 4 * (it & 1) + kq;
-      b_any[j] = it < tn / 4;
-      bl_live[j] = b_any[j] && 8 * r8 < tile.w;  // uniform over the warp
+    for (int j = 0; j < S::UN; ++j) {
+      const int u = bw + UM_BWARPS * j;
+      const int r8 = u >> 1;
+      b_any[j] = u < tn / 4;
+      b_live[j] = b_any[j] && 8 * r8 < tile.w;  // uniform over the warp
       const int4 f = b_any[j] ? fb[8 * r8 + rr] : make_int4(ZERO, ONE, 0, 0);
-      bu[j] = f.x * wp + 4 * kc;
-      bv[j] = f.y * wp + 4 * kc;
+      bu[j] = f.x * wp + (u & 1) * (KC / 2) + 4 * kq;
+      bv[j] = f.y * wp + (u & 1) * (KC / 2) + 4 * kq;
     }
-    auto b_off = [&](int j) {
-      const int it = bw + UM_BWARPS * j;
-      return ((4 * (it & 1) + kq) * (tn / 8) + (it >> 1)) * 32 + rr * 4;  // core (r8, kc), row rr
+    // floats: core (r8, kc), row rr of a B stage (kc = 4 item + kq)
+    auto b_off = [&](int j, int item) {
+      const int u = bw + UM_BWARPS * j;
+      const int kc = (u & 1) * (KC / 8) + 4 * item + kq;
+      return (kc * (tn / 8) + (u >> 1)) * 32 + rr * 4;
     };
     // zero, once, the operands that no chunk writes
     if (!a_live) {
-      const uint32_t z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (int s = 0; s < UM_NA; ++s) {
-        const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * UM_ACOLS + 8 * pt);
-        tmem_st8(ta, z);
-        tmem_st8(ta + UM_KC, z);
-      }
+      const uint32_t z[16] = {};
+      for (int s = 0; s < NA; ++s)
+        for (int i = 0; i < KC / 32; ++i) {
+          const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * S::ACOLS + hf * (KC / 2) + 16 * i);
+          tmem_st16(ta, z);
+          tmem_st16(ta + KC, z);
+        }
       tmem_wait_st();
     }
 #pragma unroll
-    for (int j = 0; j < IT; ++j)
-      if (b_any[j] && !bl_live[j])
-        for (int s = 0; s < UM_NA; ++s) {
-          *reinterpret_cast<float4*>(Bhi(s) + b_off(j)) = make_float4(0.f, 0.f, 0.f, 0.f);
-          *reinterpret_cast<float4*>(Blo(s) + b_off(j)) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    float mid[S::quarter];
+    for (int j = 0; j < S::UN; ++j)
+      if (b_any[j] && !b_live[j])
+        for (int s = 0; s < NA; ++s)
+          for (int i = 0; i < KC / 32; ++i) {
+            *reinterpret_cast<float4*>(Bhi(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(Blo(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+    float mid[S::half];
 #pragma unroll
-    for (int j = 0; j < S::quarter; ++j) mid[j] = 0.0f;
+    for (int j = 0; j < S::half; ++j) mid[j] = 0.0f;
     auto drain = [&](int g) -> bool {
       const int a = g % NACC;
       bool ok = mbar_wait(&afull[a], (uint32_t)(g / NACC) & 1u, status);
       if (!__all_sync(FULL, ok)) return false;
       tc_fence_after();
 #pragma unroll
-      for (int j0 = 0; j0 < S::quarter; j0 += 8) {
-        if (j0 < qc) {  // uniform over the warp
-          float v[8];
-          tmem_ld8(tq + (uint32_t)(a * TN + pt * qc + j0), v);
+      for (int j0 = 0; j0 < S::half; j0 += 16) {
+        if (j0 < hc) {  // uniform over the warp
+          float v[16];
+          tmem_ld16(tq + (uint32_t)(a * TN + hf * hc + j0), v);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) mid[j0 + j] += v[j];
+          for (int j = 0; j < 16; ++j) mid[j0 + j] += v[j];
         }
       }
       tc_fence_before();
@@ -318,58 +325,65 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     };
     // group g is drained after building chunk drain_at(g): half a group
     // later with two accumulators, else before the next group needs it
-    auto drain_at = [&](int g) {
-      return NACC == 2 ? (g + 1) * UM_GROUP + UM_GROUP / 2 - 1 : (g + 1) * UM_GROUP + UM_NA - 1;
-    };
+    auto drain_at = [&](int g) { return NACC == 2 ? (g + 1) * G + G / 2 - 1 : (g + 1) * G + NA - 1; };
     bool ok = true;
     int next = 0;  // next group to drain
     for (int c = 0; c < nch && ok; ++c) {
-      const int fl = c / wch, b = fl % nw, s = c % UM_NA;
+      const int fl = c / wch, b = fl % nw, s = c % NA;
       if (c % wch == 0) ok = mbar_wait(&wfull[b], (uint32_t)(fl / nw) & 1u, status);
-      if (ok && c >= UM_NA) ok = mbar_wait(&sempty[s], (uint32_t)(c / UM_NA - 1) & 1u, status);
+      if (ok && c >= NA) ok = mbar_wait(&sempty[s], (uint32_t)(c / NA - 1) & 1u, status);
       if (!__all_sync(FULL, ok)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const float* w = Ws(b) + (c % wch) * UM_KC;
-      if (a_live) {  // A row m, cells 8 pt .. 8 pt + 7: hi and lo into the stage's tensor-memory columns
-        const float4* x0 = reinterpret_cast<const float4*>(w + fx * wp + 8 * pt);
-        const float4* x1 = reinterpret_cast<const float4*>(w + fy * wp + 8 * pt);
-        const float4* x2 = reinterpret_cast<const float4*>(w + fz * wp + 8 * pt);
-        const float4 a0 = x0[0], a1 = x1[0], a2 = x2[0], c0 = x0[1], c1 = x1[1], c2 = x2[1];
-        const float v[8] = {a0.x * a1.x * a2.x, a0.y * a1.y * a2.y, a0.z * a1.z * a2.z, a0.w * a1.w * a2.w,
-                            c0.x * c1.x * c2.x, c0.y * c1.y * c2.y, c0.z * c1.z * c2.z, c0.w * c1.w * c2.w};
-        uint32_t hi[8], lo[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          hi[e] = tf32_trunc(v[e]);
-          lo[e] = __float_as_uint(v[e] - __uint_as_float(hi[e]));
-        }
-        const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * UM_ACOLS + 8 * pt);
-        tmem_st8(ta, hi);
-        tmem_st8(ta + UM_KC, lo);
-      }
-      // B: all loads of this warp's items first, then products, splits and stores
-      float4 u[IT], v[IT];
-#pragma unroll
-      for (int j = 0; j < IT; ++j)
-        if (bl_live[j]) {
-          u[j] = *reinterpret_cast<const float4*>(w + bu[j]);
-          v[j] = *reinterpret_cast<const float4*>(w + bv[j]);
-        }
+      const float* w = Ws(b) + (c % wch) * KC;
       float* bh = Bhi(s);
       float* bl = Blo(s);
 #pragma unroll
-      for (int j = 0; j < IT; ++j)
-        if (bl_live[j]) {
-          const float p0 = u[j].x * v[j].x, p1 = u[j].y * v[j].y, p2 = u[j].z * v[j].z, p3 = u[j].w * v[j].w;
-          const float4 h = make_float4(__uint_as_float(tf32_trunc(p0)), __uint_as_float(tf32_trunc(p1)),
-                                       __uint_as_float(tf32_trunc(p2)), __uint_as_float(tf32_trunc(p3)));
-          const int off = b_off(j);
-          *reinterpret_cast<float4*>(bh + off) = h;
-          *reinterpret_cast<float4*>(bl + off) = make_float4(p0 - h.x, p1 - h.y, p2 - h.z, p3 - h.w);
+      for (int i = 0; i < KC / 32; ++i) {  // 16 cells per item
+        if (a_live) {  // A row m, 8 cells at a time: hi and lo into the stage's tensor-memory columns
+#pragma unroll
+          for (int h8 = 0; h8 < 2; ++h8) {
+            const int o = 16 * i + 8 * h8;
+            const float4 x0 = *reinterpret_cast<const float4*>(w + ax + o);
+            const float4 x1 = *reinterpret_cast<const float4*>(w + ay + o);
+            const float4 x2 = *reinterpret_cast<const float4*>(w + az + o);
+            const float4 y0 = *reinterpret_cast<const float4*>(w + ax + o + 4);
+            const float4 y1 = *reinterpret_cast<const float4*>(w + ay + o + 4);
+            const float4 y2 = *reinterpret_cast<const float4*>(w + az + o + 4);
+            const float v[8] = {x0.x * x1.x * x2.x, x0.y * x1.y * x2.y, x0.z * x1.z * x2.z, x0.w * x1.w * x2.w,
+                                y0.x * y1.x * y2.x, y0.y * y1.y * y2.y, y0.z * y1.z * y2.z, y0.w * y1.w * y2.w};
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              hi[e] = tf32_trunc(v[e]);
+              lo[e] = __float_as_uint(v[e] - __uint_as_float(hi[e]));
+            }
+            const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * S::ACOLS + hf * (KC / 2) + o);
+            tmem_st8(ta, hi);
+            tmem_st8(ta + KC, lo);
+          }
         }
+        // this warp's B items of the same 16 cells: all loads, then products, splits and stores
+        float4 u4[S::UN], v4[S::UN];
+#pragma unroll
+        for (int j = 0; j < S::UN; ++j)
+          if (b_live[j]) {
+            u4[j] = *reinterpret_cast<const float4*>(w + bu[j] + 16 * i);
+            v4[j] = *reinterpret_cast<const float4*>(w + bv[j] + 16 * i);
+          }
+#pragma unroll
+        for (int j = 0; j < S::UN; ++j)
+          if (b_live[j]) {
+            const float p0 = u4[j].x * v4[j].x, p1 = u4[j].y * v4[j].y, p2 = u4[j].z * v4[j].z, p3 = u4[j].w * v4[j].w;
+            const float4 h = make_float4(__uint_as_float(tf32_trunc(p0)), __uint_as_float(tf32_trunc(p1)),
+                                         __uint_as_float(tf32_trunc(p2)), __uint_as_float(tf32_trunc(p3)));
+            const int off = b_off(j, i);
+            *reinterpret_cast<float4*>(bh + off) = h;
+            *reinterpret_cast<float4*>(bl + off) = make_float4(p0 - h.x, p1 - h.y, p2 - h.z, p3 - h.w);
+          }
+      }
       if (a_live) tmem_wait_st();
       fence_async_shared();  // the B operands, for the tensor cores
       tc_fence_before();     // the A operands (tcgen05.st), for the MMA thread
@@ -381,11 +395,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       while (ok && next < ngroups && c >= drain_at(next)) ok = drain(next++);
     }
     while (ok && next < ngroups) ok = drain(next++);
-    // per-CTA partials: row m, this warp's quarter of the columns
+    // per-CTA partials: row m, this warp's half of the columns
     double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (int64_t)(UM_M * TN);
 #pragma unroll
-    for (int j = 0; j < S::quarter; ++j)
-      if (j < qc) out[m * TN + pt * qc + j] = (double)mid[j];
+    for (int j = 0; j < S::half; ++j)
+      if (j < hc) out[m * TN + hf * hc + j] = (double)mid[j];
   }
   tc_fence_before();
   __syncthreads();
@@ -457,13 +471,13 @@ template <int TN>
 cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, const int2* rowdesc,
                           int rows, const int2* coldesc, const int4* tiles, const int* collist, int ntiles,
                           int splits, int64_t cps, double* partials, int* status, cudaStream_t st) {
-  int nw = 0, wch = 0;
-  if (!umma_staging<TN>(ns, (size_t)227 * 1024, &nw, &wch)) return cudaErrorInvalidValue;
-  const size_t sm = umma_smem<TN>(ns, nw, wch);
+  const int wcells = umma_wcells<TN>(ns, (size_t)227 * 1024);
+  if (wcells == 0) return cudaErrorInvalidValue;
+  const size_t sm = umma_smem<TN>(ns, wcells);
   cudaError_t e = cudaFuncSetAttribute(contract_umma_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntiles, (unsigned)splits);
-  contract_umma_kernel<TN><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, nw, wch, rowdesc, rows, coldesc,
+  contract_umma_kernel<TN><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, wcells, rowdesc, rows, coldesc,
                                                          tiles, collist, ntiles, cps, partials, status);
   return cudaGetLastError();
 }
@@ -482,12 +496,12 @@ int umma_tile_rows() { return UM_M; }
 
 // Cells per split: whole accumulation groups (256 cells), at most UM_MAX_GROUPS.
 int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count) {
-  const int64_t cap = (int64_t)UM_MAX_GROUPS * UM_GROUP * UM_KC;
+  const int64_t cap = (int64_t)UM_MAX_GROUPS * UM_GCELLS;
   int64_t splits = std::max<int64_t>(1, (2 * (int64_t)sm_count + ntiles - 1) / std::max(ntiles, 1));
   int64_t cps = (nc + splits - 1) / splits;
   cps = std::min(cps, cap);
-  cps = (cps + UM_GROUP * UM_KC - 1) / (UM_GROUP * UM_KC) * (UM_GROUP * UM_KC);  // whole staging fills
-  return std::max<int64_t>(cps, UM_GROUP * UM_KC);
+  cps = (cps + UM_GCELLS - 1) / UM_GCELLS * UM_GCELLS;  // whole groups and staging fills
+  return std::max<int64_t>(cps, UM_GCELLS);
 }
 
 cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
