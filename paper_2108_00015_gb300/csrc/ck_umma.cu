@@ -446,25 +446,31 @@ struct UmmaBases {
   int64_t base[CK_MAX_ORDER + 1];
 };
 
+// One warp per partial element (tile, row, column): lane l sums the splits
+// l, l + 32, .. in order, then a fixed shuffle tree adds the lanes, so the
+// result is the same from run to run.
 __global__ void reduce_umma_kernel(const double* __restrict__ partials, int splits, int ntiles, int tn,
                                    const int4* __restrict__ tiles, const int* __restrict__ collist,
                                    const int2* __restrict__ rowdesc, int rows, const int2* __restrict__ coldesc,
                                    int mask, int ns, UmmaBases B, double* __restrict__ out) {
   const int64_t per = (int64_t)UM_M * tn;  // partials per tile: 128 rows of pitch tn
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (t >= (int64_t)ntiles * per) return;
   const int tile = (int)(t / per);
   const int pq = (int)(t - (int64_t)tile * per);
   const int4 tl = tiles[tile];
-  const int p = tl.x + pq / tn, ci = pq % tn;
+  const int p = tl.x + pq / tn, ci = pq % tn;  // row and column of the partial
   if (p >= rows || ci >= tl.w) return;
   const int q = collist[tl.y + ci];
   int ms[4];
   const int n = umma_canonical(rowdesc[p], coldesc[q], mask, ms);
   if (!n) return;
   double s = 0.0;
-  for (int sp = 0; sp < splits; ++sp) s += partials[((int64_t)sp * ntiles + tile) * per + pq];
-  out[B.base[n] + umma_rank(ms, n - 1, ns)] = s;
+  for (int sp = lane; sp < splits; sp += 32) s += partials[((int64_t)sp * ntiles + tile) * per + pq];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) out[B.base[n] + umma_rank(ms, n - 1, ns)] = s;
 }
 
 template <int TN>
@@ -522,7 +528,7 @@ cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, i
                                int ns, const int64_t* bases, double* out, cudaStream_t st) {
   UmmaBases B;
   for (int n = 0; n <= CK_MAX_ORDER; ++n) B.base[n] = bases[n];
-  const int64_t total = (int64_t)ntiles * UM_M * tn;
+  const int64_t total = (int64_t)ntiles * UM_M * tn * 32;  // a warp per partial element
   reduce_umma_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(partials, splits, ntiles, tn, tiles, collist,
                                                                       rowdesc, rows, coldesc, mask, ns, B, out);
   return cudaGetLastError();
