@@ -66,6 +66,61 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# dense TF32 / BF16 tensor rate, NVIDIA's nominal figures (1.1 and 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+FALLBACK_BF16_SUSTAINED_TFLOPS = 1700.0
+
+
+def _tf32_peak():
+    """Sustained TF32 tensor peak: the measured sustained BF16 GEMM rate
+    times the nominal TF32/BF16 ratio (the contraction is timed inside a
+    long step)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]) * TF32_PER_BF16, "measured"
+    except Exception:
+        return FALLBACK_BF16_SUSTAINED_TFLOPS * TF32_PER_BF16, "fallback"
+
+
+def _tc_work(ns, orders):
+    """Per cell, the multiply-adds of the blocked product the tensor-core
+    contraction computes (live operand rows x the columns each 128-row tile
+    needs, the library's tile rule) and the useful ones (one per output
+    multiset)."""
+    rows, cols = [], []
+    if 2 in orders:
+        rows.append((-1, -1))
+    if 3 in orders:
+        rows += [(a, -1) for a in range(ns)]
+    if 4 in orders or 5 in orders:
+        rows += [(a, b) for b in range(ns) for a in range(b + 1)]
+    if 2 in orders or 3 in orders or 4 in orders:
+        cols += [(k, -1) for k in range(ns)]
+    if 5 in orders:
+        cols += [(k, l) for k in range(ns) for l in range(k, ns)]
+
+    def canon(r, c):
+        da, db = (r[0] >= 0) + (r[1] >= 0), (c[0] >= 0) + (c[1] >= 0)
+        n = 0
+        if da == 0 and db == 1:
+            n = 2
+        elif da == 1 and db == 1 and r[0] <= c[0]:
+            n = 3
+        elif da == 2 and db == 1 and r[1] <= c[0]:
+            n = 4
+        elif da == 2 and db == 2 and r[1] <= c[0]:
+            n = 5
+        return n in orders
+
+    dense = 0
+    for m0 in range(0, len(rows), 128):
+        tile = rows[m0:m0 + 128]
+        need = sum(1 for c in cols if any(canon(r, c) for r in tile))
+        dense += len(tile) * need
+    useful = sum(math.comb(ns + n - 2, n - 1) for n in orders)
+    return dense, useful
+
+
 class Clocks:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
@@ -275,6 +330,19 @@ def run_gb300(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": dv["bytes"] / dv["launches"],
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    if dname == "contract" and args.precision == "split_tf32" and not plan.fused:
+        # the tcgen05 blocked product: three split TF32 products per operand pair
+        dense, useful = _tc_work(len(w["shells"]), orders)
+        nc = int(np.prod(w["grid"].n))
+        flops = 3 * 2 * dense * nc
+        t_launch = dv["ms"] / dv["launches"] * 1e-3
+        tpk, tkind = _tf32_peak()
+        roofline = {"bound": "tensor", "kernel": dname, "achieved": round(flops / t_launch / 1e12, 1),
+                    "peak": round(tpk, 1), "unit": "TFLOP/s", "frac": round(flops / t_launch / 1e12 / tpk, 4),
+                    "traffic": None, "algorithmic_flops_per_launch": flops,
+                    "useful_tflops": round(2 * useful * nc / t_launch / 1e12, 1),
+                    "peak_source": (f"{tkind}: MEASURED_PEAKS.json bf16_tflops_sustained x {TF32_PER_BF16:.3f} "
+                                    "(nominal TF32/BF16 ratio)")}
     fft_names = [k for k in stages if k.startswith("fft_") or k == "x_c2r_contract"]
     fft_bytes = sum(stages[k]["bytes"] for k in fft_names)
     fft_ms = sum(stages[k]["ms"] for k in fft_names)
