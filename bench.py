@@ -53,6 +53,10 @@ def _args():
     ap.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32"],
                     help="headline form: mixed split-TF32 tensor-core sums (fused pass) or plain FP32")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form beside the headline")
+    ap.add_argument("--diagonal", action="store_true",
+                    help="time ck_set_randoms_diagonal + ck_compute_diagonal (Eq. 14, the (s, .., s) entries "
+                         "only) instead of ck_set_randoms + ck_compute; "
+                         "no e2e, plain-form or CPU legs")
     return ap.parse_args()
 
 
@@ -268,6 +272,9 @@ def run_gb300(args):
     stream = torch.cuda.current_stream()
 
     def step():
+        if args.diagonal:
+            plan.set_randoms_diagonal(rx, ry, rz)
+            return plan.compute_diagonal(dx, dy, dz, orders=orders, out="device")
         plan.set_randoms(rx, ry, rz)
         return plan.compute(dx, dy, dz, orders=orders, out="device", outputs=outs)
 
@@ -330,7 +337,7 @@ def run_gb300(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": dv["bytes"] / dv["launches"],
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
-    if dname == "contract" and args.precision == "split_tf32" and not plan.fused:
+    if dname == "contract" and args.precision == "split_tf32" and not plan.fused and not args.diagonal:
         # the tcgen05 blocked product: three split TF32 products per operand pair
         dense, useful = _tc_work(len(w["shells"]), orders)
         nc = int(np.prod(w["grid"].n))
@@ -431,7 +438,8 @@ def run_gb300(args):
         "config": {"workload": args.workload, "grid": list(g.n), "cell": g.cell, "periodic": g.periodic,
                    "shells": ns, "width": w["width"], "orders": list(orders), "n_data": d.n, "n_randoms": r.n,
                    "precision": precision,
-                   "step": "ck_set_randoms + ck_compute (both fields, every shell)",
+                   "step": ("ck_set_randoms + ck_compute_diagonal (both fields, every shell; Eq. 14 only)"
+                            if args.diagonal else "ck_set_randoms + ck_compute (both fields, every shell)"),
                    "l2": "no flush: inputs and intermediates far larger than L2 (16 scratch spectra, 8.7 GB)"},
         "forms": forms,
         "roofline": roofline,
@@ -557,6 +565,8 @@ def run_reference(args):
 
 def main():
     args = _args()
+    if args.diagonal:
+        args.no_e2e = args.no_cpu_baseline = args.no_plain = True
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":

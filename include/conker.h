@@ -168,6 +168,31 @@ ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const fl
 ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
                      int32_t order_mask, const ck_outputs* out, void* stream);
 
+/* The equidistant n-point functions alone (Sec. 2.6, Eq. 14): the same path
+ * as ck_compute up to W_s, then for every shell s and requested order n only
+ * the diagonal multiset (s, .., s):
+ *   num_n[s] = sum_r W0 W_s^(n-1),  den_n[s] = alpha^n den_raw_n(s, .., s),
+ *   xi_n[s] = num_n[s] / den_n[s],
+ * in one pass over the bank, O(N_c N_s) instead of every multiset.  Plans
+ * with the fused order-2/3 pass (no bank) take the diagonal entries of their
+ * full sums.  Outputs (ck_outputs): xi[n], num[n], den[n] each hold N_s
+ * doubles (host or device, caller-owned, NULL = skip), shell s at index s;
+ * dropped as for ck_compute.  Same arguments and errors as ck_compute;
+ * results are the diagonal entries of ck_compute's (equal to rounding of the
+ * summation order).  Needs ck_set_randoms or ck_set_randoms_diagonal
+ * first. */
+ck_status ck_compute_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                              int32_t order_mask, const ck_outputs* out, void* stream);
+
+/* ck_set_randoms for the diagonal alone: grid R and keep only the raw
+ * denominators of the (s, .., s) multisets, from one pass over the random
+ * field's bank (O(N_c N_s)); plans with the fused order-2/3 pass sum every
+ * multiset as ck_set_randoms does.  Afterwards ck_compute_diagonal works;
+ * ck_compute returns CK_ERR_NO_RANDOMS (unless every multiset was summed)
+ * until ck_set_randoms is called. */
+ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                                  void* stream);
+
 /* --- batched form --------------------------------------------------------------
  * Many catalogs over one or more plans (grid classes), each plan's randoms set
  * once with ck_set_randoms.  Catalog i is computed on plans[cats[i].plan] and

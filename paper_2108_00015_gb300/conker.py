@@ -90,6 +90,9 @@ _SIGS = [
     ("ck_plan_get_info", ctypes.c_int, [_P, ctypes.POINTER(_Info)]),
     ("ck_set_randoms", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     ("ck_compute", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
+    ("ck_set_randoms_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("ck_compute_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs),
+                                           _P]),
     ("ck_batch_compute", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_Catalog), ctypes.c_int32,
                                         ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_plan_status", ctypes.c_int, [_P, _P]),
@@ -245,6 +248,12 @@ class Plan:
         _check(_lib().ck_set_randoms(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), _stream_ptr(stream)),
                "ck_set_randoms")
 
+    def set_randoms_diagonal(self, x, y, z, stream=None):
+        """ck_set_randoms_diagonal: only the (s, .., s) denominators (for compute_diagonal)."""
+        x, y, z = _as_f32(x), _as_f32(y), _as_f32(z)
+        _check(_lib().ck_set_randoms_diagonal(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]),
+                                              _stream_ptr(stream)), "ck_set_randoms_diagonal")
+
     def compute(self, x, y, z, orders=(2, 3), out: str = "device", stream=None, want=("xi", "num", "den"),
                 outputs: Optional[Dict[str, Dict[int, object]]] = None) -> Dict[str, object]:
         """One catalog; returns {'xi': {n: T}, 'num': ..., 'den': ..., 'dropped': T} with dense
@@ -276,6 +285,33 @@ class Plan:
         res["status"] = int(code)
         if code not in (0, 7):  # a zero denominator still fills the outputs (NaN there)
             raise CkError(code, "ck_compute")
+        return res
+
+    def compute_diagonal(self, x, y, z, orders=(2, 3), out: str = "device", stream=None) -> Dict[str, object]:
+        """The equidistant functions of Eq. 14 only (ck_compute_diagonal): returns
+        {'xi': {n: T}, 'num': ..., 'den': ..., 'dropped': T} with [N_s] float64 tensors,
+        entry s = the multiset (s, .., s)."""
+        torch = _torch()
+        x, y, z = _as_f32(x), _as_f32(y), _as_f32(z)
+        ns = self.n_shells
+        res: Dict[str, object] = {k: {} for k in ("xi", "num", "den")}
+        o = _Outputs()
+        dev = "cuda" if out == "device" else "cpu"
+        for n in orders:
+            if not 2 <= int(n) <= CK_MAX_ORDER:
+                continue  # the library rejects the order mask
+            for key in ("xi", "num", "den"):
+                t = torch.empty(ns, dtype=torch.float64, device=dev, pin_memory=(dev == "cpu"))
+                res[key][n] = t
+                getattr(o, key)[n] = t.data_ptr()
+        dropped = torch.zeros(2, dtype=torch.int64, device=dev)
+        o.dropped = dropped.data_ptr()
+        res["dropped"] = dropped
+        code = _lib().ck_compute_diagonal(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), order_mask(orders),
+                                          ctypes.byref(o), _stream_ptr(stream))
+        res["status"] = int(code)
+        if code not in (0, 7):  # a zero denominator still fills the outputs (NaN there)
+            raise CkError(code, "ck_compute_diagonal")
         return res
 
     def status(self, stream=None) -> int:

@@ -423,14 +423,35 @@ ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const fl
   if (n > 0 && (!x || !y || !z)) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   cudaStream_t st = S(stream);
-  p.have_randoms = false;
+  p.have_randoms = p.have_randoms_diag = false;
   CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st));
   launch_prepare_randoms(p, st);
   p.bank_holds = -1;
   CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st));
   p.bank_holds = 1;
   CK_TRY(cudaGetLastError());
-  p.have_randoms = true;
+  p.have_randoms = p.have_randoms_diag = true;
+  return CK_OK;
+}
+
+ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                                  void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  if (n < 0) return CK_ERR_ARG;
+  if (n > 0 && (!x || !y || !z)) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t st = S(stream);
+  p.have_randoms = p.have_randoms_diag = false;
+  CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st));
+  launch_prepare_randoms(p, st);
+  p.bank_holds = -1;
+  launch_fft_forward(p, p.field, p.spec, st);
+  bool full = false;
+  CK_TRY_S(launch_diagonal_randoms(p, &full, st));
+  p.bank_holds = 1;
+  CK_TRY(cudaGetLastError());
+  p.have_randoms = full;
+  p.have_randoms_diag = true;
   return CK_OK;
 }
 
@@ -452,6 +473,37 @@ ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float*
   CK_TRY(cudaGetLastError());
   bool host_seen = false;
   CK_TRY_S(copy_results(p, order_mask, out, st, &host_seen));
+  if (host_seen) return read_status(p, st, true);
+  return CK_OK;
+}
+
+ck_status ck_compute_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                              int32_t order_mask, const ck_outputs* out, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (n < 0) return CK_ERR_ARG;
+  if (n > 0 && (!x || !y || !z)) return CK_ERR_BAD_POINTER;
+  if (order_mask == 0 || (order_mask & ~full_mask(p)) != 0) return CK_ERR_ARG;
+  if (!p.have_randoms_diag) return CK_ERR_NO_RANDOMS;
+  cudaStream_t st = S(stream);
+  CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st));
+  launch_prepare_data(p, st);
+  p.bank_holds = -1;
+  launch_fft_forward(p, p.field, p.spec, st);
+  CK_TRY_S(launch_diagonal(p, order_mask, st));
+  p.bank_holds = 0;
+  CK_TRY(cudaGetLastError());
+  bool host_seen = false;
+  if (out) {
+    for (int k = 2; k <= p.max_order; ++k) {
+      if (!((order_mask >> k) & 1)) continue;
+      const size_t bytes = (size_t)p.ns * 8;
+      CK_TRY_S(copy_out(out->xi[k], p.dense + p.dense_base[k], bytes, st, &host_seen));
+      CK_TRY_S(copy_out(out->num[k], p.dense + p.dense_total + p.dense_base[k], bytes, st, &host_seen));
+      CK_TRY_S(copy_out(out->den[k], p.dense + 2 * p.dense_total + p.dense_base[k], bytes, st, &host_seen));
+    }
+    CK_TRY_S(copy_out(out->dropped, p.dstate->dropped, 2 * sizeof(int64_t), st, &host_seen));
+  }
   if (host_seen) return read_status(p, st, true);
   return CK_OK;
 }

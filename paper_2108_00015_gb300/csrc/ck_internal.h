@@ -168,7 +168,8 @@ struct Plan {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec[1 << (CK_MAX_ORDER + 1)] = {nullptr};
 
-  bool have_randoms = false;
+  bool have_randoms = false;       // den_raw holds every multiset of the plan's orders
+  bool have_randoms_diag = false;  // den_raw holds at least the (s, .., s) multisets
   int bank_holds = -1;  // field whose spectrum is resident: 0 = data, 1 = randoms
   // Convolution and sums in one pass (FP32, <= 16 shells, orders <= 3): the
   // bank is not kept; `bank` holds one field, recomputed on request.
@@ -246,5 +247,15 @@ ck_status contract_prepare(Plan& p, int order_mask);
 ck_status launch_contract(Plan& p, int order_mask, const float* w0, const float* bank,
                           int64_t bank_stride, double* sums_packed, cudaStream_t st);
 void launch_finalize(const Plan& p, int order_mask, cudaStream_t st);
+// Eq. 14 for the orders in order_mask after the forward transform of the
+// plan's field: num/den/xi of (s, .., s) for every shell into the first N_s
+// entries of each order's dense outputs (ck_diag.cu).
+ck_status launch_diagonal(Plan& p, int order_mask, cudaStream_t st);
+// The random field's diagonal sums (s, .., s) into den_raw after its forward
+// transform; *full is set when every multiset was summed (fused plans).
+ck_status launch_diagonal_randoms(Plan& p, bool* full, cudaStream_t st);
+// Rank of the non-decreasing shell sequence s[0..k-1] among all of its
+// length over ns shells, in the packed (lexicographic) order.
+int64_t host_multiset_rank(const int* s, int k, int ns);
 
 }  // namespace ck

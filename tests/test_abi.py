@@ -68,6 +68,18 @@ def test_host_validation(lib):
     assert _ws(lib, width=0.0)[0] == 1
 
 
+def test_null_plan_entry_points(lib):
+    """Entry points taking a plan reject a null one before any CUDA call."""
+    from paper_2108_00015_gb300.conker import _Outputs
+    o = _Outputs()
+    for name in ("ck_compute", "ck_compute_diagonal"):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs),
+                                               ctypes.c_void_p]
+        assert fn(None, None, None, None, 0, 4, ctypes.byref(o), None) == 2, name  # CK_ERR_BAD_POINTER
+
+
 def test_survey_workspace_fits(lib):
     # 512^3, 16 shells, orders <= 3.  Mixed (split-TF32, fused pass, no bank):
     # counts + field + spectrum + 16 scratch spectra + kernel octants + one field
