@@ -89,8 +89,9 @@ def _tf32_peak():
 def _tc_work(ns, orders):
     """Per cell, the multiply-adds of the blocked product the tensor-core
     contraction computes (live operand rows x the columns each 128-row tile
-    needs, the library's tile rule) and the useful ones (one per output
-    multiset)."""
+    needs, the library's tile rule; thin tiles of at most 16 columns and 256
+    outputs run on the CUDA cores and are left out) and the useful ones (one
+    per output multiset)."""
     rows, cols = [], []
     if 2 in orders:
         rows.append((-1, -1))
@@ -120,6 +121,8 @@ def _tc_work(ns, orders):
     for m0 in range(0, len(rows), 128):
         tile = rows[m0:m0 + 128]
         need = sum(1 for c in cols if any(canon(r, c) for r in tile))
+        if need <= 16 and len(tile) * need <= 256:
+            continue  # a thin tile: the CUDA cores sum it
         dense += len(tile) * need
     useful = sum(math.comb(ns + n - 2, n - 1) for n in orders)
     return dense, useful

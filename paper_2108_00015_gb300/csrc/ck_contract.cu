@@ -499,9 +499,24 @@ ck_status contract_prepare(Plan& p, int mask) {
         const int tn = (cnt + 31) / 32 * 32;
         tl.push_back(make_int4(m0, (int)clist.size(), tn, cnt));
         clist.insert(clist.end(), need.begin() + i, need.begin() + i + cnt);
-        tnmax = std::max(tnmax, tn);
       }
     }
+    // thin tiles (few outputs) go last, to the CUDA cores: per MMA a thin
+    // tile costs the tensor cores as much as a full one
+    auto thin = [&](const int4& t) {
+      const int live = std::min<int>(TM, (int)rows.size() - t.x);
+      return t.w <= kThinMaxCols && live * t.w <= kThinMaxOut;
+    };
+    std::stable_partition(tl.begin(), tl.end(), [&](const int4& t) { return !thin(t); });
+    c.um_ntc = 0;
+    c.um_thin_rmax = 0;
+    for (const int4& t : tl)
+      if (!thin(t)) {
+        ++c.um_ntc;
+        tnmax = std::max(tnmax, t.z);
+      } else {
+        c.um_thin_rmax = std::max(c.um_thin_rmax, std::min<int>(TM, (int)rows.size() - t.x));
+      }
     c.n_tiles = (int)tl.size();
     c.um_tn = umma_tile_cols(std::max(tnmax, 32));
     const size_t need_b = (rows.size() + cols.size()) * sizeof(int2) + tl.size() * sizeof(int4) + clist.size() * sizeof(int) + 16;
@@ -578,7 +593,11 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
     {
       ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, st);
       e = launch_umma(c.um_tn, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
-                      c.d_um_cols, c.n_tiles, c.splits, c.um_cps, p.partials, status, st);
+                      c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, c.um_cps, p.partials, status, st);
+      if (e == cudaSuccess)
+        e = launch_umma_thin(w0, bank, bstride, p.nc, p.ns, c.um_thin_rmax, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
+                             c.d_um_cols, c.um_ntc, c.n_tiles - c.um_ntc, c.n_tiles, c.um_tn, c.splits, c.um_cps,
+                             p.partials, st);
     }
     if (e != cudaSuccess) return cuda_status(e);
     ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);

@@ -71,6 +71,8 @@ struct ContractPlan {
   bool use_reg = false;     // register-accumulator kernel (few outputs)
   bool use_tc = false;      // blocked product on the tensor cores (split-TF32, tcgen05)
   int um_tn = 0;            // tcgen05 tiles: 128 rows x at most um_tn columns
+  int um_ntc = 0;           // tiles 0 .. um_ntc - 1 on the tensor cores, the rest thin (CUDA cores)
+  int um_thin_rmax = 0;     // the most live rows of a thin tile
   int64_t um_cps = 0;       // tcgen05: cells per split
   int reg_maxn = 0;         // orders 2..reg_maxn computed by that kernel
   int n_out_reg = 0;        // outputs of the register kernel
@@ -235,9 +237,20 @@ int umma_tile_rows();
 int umma_tile_cols(int cols);
 int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count);
 // A tile is (first row, offset of its column list, MMA N <= tn, list length).
+// Tensor-core tiles 0 .. ntc - 1 of ntiles (the partials are pitched by ntiles).
 cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
-                        int ntiles, int splits, int64_t cps, double* partials, int* status, cudaStream_t st);
+                        int ntc, int ntiles, int splits, int64_t cps, double* partials, int* status,
+                        cudaStream_t st);
+// Thin tiles (at most kThinMaxOut outputs, kThinMaxCols columns) t0 .. t0 + nthin - 1 on the CUDA
+// cores in FP32, into the same partials layout (tile width tn).
+constexpr int kThinMaxOut = 256;
+constexpr int kThinMaxCols = 16;
+size_t umma_thin_smem(int ns, int rmax);  // rmax: the most live rows of a thin tile
+cudaError_t launch_umma_thin(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, int rmax,
+                             const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles,
+                             const int* collist, int t0, int nthin, int ntiles, int tn, int splits, int64_t cps,
+                             double* partials, cudaStream_t st);
 cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, int tn, const int4* tiles,
                                const int* collist, const int2* rowdesc, int rows, const int2* coldesc, int mask,
                                int ns, const int64_t* bases, double* out, cudaStream_t st);

@@ -475,14 +475,15 @@ __global__ void reduce_umma_kernel(const double* __restrict__ partials, int spli
 
 template <int TN>
 cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, const int2* rowdesc,
-                          int rows, const int2* coldesc, const int4* tiles, const int* collist, int ntiles,
+                          int rows, const int2* coldesc, const int4* tiles, const int* collist, int ntc, int ntiles,
                           int splits, int64_t cps, double* partials, int* status, cudaStream_t st) {
+  if (ntc == 0) return cudaSuccess;
   const int wcells = umma_wcells<TN>(ns, (size_t)227 * 1024);
   if (wcells == 0) return cudaErrorInvalidValue;
   const size_t sm = umma_smem<TN>(ns, wcells);
   cudaError_t e = cudaFuncSetAttribute(contract_umma_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)ntiles, (unsigned)splits);
+  dim3 grid((unsigned)ntc, (unsigned)splits);  // tiles 0 .. ntc - 1; partials pitched by all ntiles
   contract_umma_kernel<TN><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, wcells, rowdesc, rows, coldesc,
                                                          tiles, collist, ntiles, cps, partials, status);
   return cudaGetLastError();
@@ -512,15 +513,141 @@ int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count) {
 
 cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
-                        int ntiles, int splits, int64_t cps, double* partials, int* status, cudaStream_t st) {
+                        int ntc, int ntiles, int splits, int64_t cps, double* partials, int* status,
+                        cudaStream_t st) {
+#define CK_UMMA_CASE(W)                                                                                          \
+  case W:                                                                                                        \
+    return launch_umma_t<W>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntc, ntiles, splits, \
+                            cps, partials, status, st);
   switch (tn) {
-    case 32: return launch_umma_t<32>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntiles, splits, cps, partials, status, st);
-    case 64: return launch_umma_t<64>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntiles, splits, cps, partials, status, st);
-    case 128: return launch_umma_t<128>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntiles, splits, cps, partials, status, st);
-    case 160: return launch_umma_t<160>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntiles, splits, cps, partials, status, st);
-    case 256: return launch_umma_t<256>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntiles, splits, cps, partials, status, st);
+    CK_UMMA_CASE(32)
+    CK_UMMA_CASE(64)
+    CK_UMMA_CASE(128)
+    CK_UMMA_CASE(160)
+    CK_UMMA_CASE(256)
     default: return cudaErrorInvalidValue;
   }
+#undef CK_UMMA_CASE
+}
+
+// ---------------------------------------------------------------------------
+// Thin tiles (at most kThinOut outputs: few rows or few columns, e.g. the
+// 25-row, 5-column tail of order 5 over 16 shells) on the CUDA cores in FP32:
+// per MMA such a tile costs the tensor cores as much as a full one.  CTA
+// (tile, split) stages the W rows of 256 cells, forms the tile's A_p and B_q
+// over them in shared memory and sums A_p B_q for one output per thread (FP32
+// over the 256 cells, FP64 across chunks), writing the tcgen05 kernel's
+// partials layout, so the same reduction serves both.
+
+constexpr int TH_THREADS = 256;
+constexpr int TH_CELLS = 256;
+constexpr int TH_PITCH = TH_CELLS + 4;  // 16-byte rows, index 1 mod 8: conflict-free float4 reads across rows
+
+__global__ void __launch_bounds__(TH_THREADS)
+    contract_thin_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
+                         int ns, int rmax, const int2* __restrict__ rowdesc, int rows, const int2* __restrict__ coldesc,
+                         const int4* __restrict__ tiles, const int* __restrict__ collist, int t0, int ntiles, int tn,
+                         int64_t cells_per_split, double* __restrict__ partials) {
+  extern __shared__ __align__(16) float th_smem[];
+  const int tile_i = t0 + blockIdx.x;
+  const int4 tile = tiles[tile_i];
+  const int R = rows - tile.x < UM_M ? rows - tile.x : UM_M;  // live rows (<= rmax)
+  const int C = tile.w;                                          // live columns (<= kThinMaxCols)
+  float* ws = th_smem;                      // [ns + 2][TH_PITCH] W0, W_1 .. W_ns, ones
+  float* As = ws + (ns + 2) * TH_PITCH;     // [rmax][TH_PITCH]
+  float* Bs = As + rmax * TH_PITCH;         // [kThinMaxCols][TH_PITCH]
+  int2* fa = reinterpret_cast<int2*>(Bs + kThinMaxCols * TH_PITCH);  // [rmax] staged rows of W_a, W_b
+  int2* fb = fa + rmax;                                                // [kThinMaxCols] staged rows of W_c, W_d
+  const int tid = threadIdx.x;
+  const int ONE = ns + 1;
+  for (int r = tid; r < R; r += TH_THREADS) {  // A_p = W0 W_a W_b, B_q = W_c W_d (an index of -1: the ones row)
+    const int2 d = rowdesc[tile.x + r];
+    fa[r] = make_int2(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE);
+  }
+  for (int q = tid; q < C; q += TH_THREADS) {
+    const int2 d = coldesc[collist[tile.y + q]];
+    fb[q] = make_int2(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE);
+  }
+  for (int k = tid; k < TH_CELLS; k += TH_THREADS) ws[ONE * TH_PITCH + k] = 1.0f;
+  const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
+  const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
+  const int o = tid;  // this thread's output: row o / C, column o % C
+  const bool live = o < R * C;
+  const int orow = live ? o / C : 0, ocol = live ? o % C : 0;
+  double dacc = 0.0;
+  constexpr int K4 = TH_CELLS / 4;
+  for (int64_t c0 = beg; c0 < end; c0 += TH_CELLS) {
+    const int vc = (int)std::min<int64_t>(TH_CELLS, end - c0);
+    // W rows of the chunk: 16-byte loads (c0 is a multiple of 256 cells), zeros past the end
+    for (int i = tid; i < (ns + 1) * K4; i += TH_THREADS) {
+      const int a = i / K4, k4 = i - a * K4;
+      const float* src = (a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride) + c0;
+      float4 v;
+      if (4 * k4 + 3 < vc) {
+        v = *reinterpret_cast<const float4*>(src + 4 * k4);
+      } else {
+        v.x = 4 * k4 < vc ? src[4 * k4] : 0.f;
+        v.y = 4 * k4 + 1 < vc ? src[4 * k4 + 1] : 0.f;
+        v.z = 4 * k4 + 2 < vc ? src[4 * k4 + 2] : 0.f;
+        v.w = 0.f;
+      }
+      *reinterpret_cast<float4*>(ws + a * TH_PITCH + 4 * k4) = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < (R + C) * K4; i += TH_THREADS) {
+      const int r = i / K4, k4 = i - r * K4;
+      const bool isa = r < R;
+      const int2 f = isa ? fa[r] : fb[r - R];
+      const float4 x = *reinterpret_cast<const float4*>(ws + f.x * TH_PITCH + 4 * k4);
+      const float4 y = *reinterpret_cast<const float4*>(ws + f.y * TH_PITCH + 4 * k4);
+      float4 v = make_float4(x.x * y.x, x.y * y.y, x.z * y.z, x.w * y.w);
+      if (isa) {
+        const float4 n = *reinterpret_cast<const float4*>(ws + 4 * k4);
+        v = make_float4(n.x * v.x, n.y * v.y, n.z * v.z, n.w * v.w);
+      }
+      *reinterpret_cast<float4*>((isa ? As + r * TH_PITCH : Bs + (r - R) * TH_PITCH) + 4 * k4) = v;
+    }
+    __syncthreads();
+    if (live) {
+      const float4* a4 = reinterpret_cast<const float4*>(As + orow * TH_PITCH);
+      const float4* b4 = reinterpret_cast<const float4*>(Bs + ocol * TH_PITCH);
+      float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll 8
+      for (int k = 0; k < K4; k += 2) {
+        const float4 x = a4[k], y = b4[k], x1 = a4[k + 1], y1 = b4[k + 1];
+        acc0 = fmaf(x.x, y.x, acc0);
+        acc0 = fmaf(x.y, y.y, acc0);
+        acc0 = fmaf(x.z, y.z, acc0);
+        acc0 = fmaf(x.w, y.w, acc0);
+        acc1 = fmaf(x1.x, y1.x, acc1);
+        acc1 = fmaf(x1.y, y1.y, acc1);
+        acc1 = fmaf(x1.z, y1.z, acc1);
+        acc1 = fmaf(x1.w, y1.w, acc1);
+      }
+      dacc += (double)acc0 + (double)acc1;
+    }
+    __syncthreads();  // the next chunk rewrites ws, As and Bs
+  }
+  if (live) partials[((int64_t)blockIdx.y * ntiles + tile_i) * (int64_t)(UM_M * tn) + orow * tn + ocol] = dacc;
+}
+
+static_assert(kThinMaxOut <= TH_THREADS, "one output per thread");
+
+size_t umma_thin_smem(int ns, int rmax) {
+  return (size_t)(ns + 2 + rmax + kThinMaxCols) * TH_PITCH * sizeof(float) + (size_t)(rmax + kThinMaxCols) * sizeof(int2);
+}
+
+cudaError_t launch_umma_thin(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, int rmax,
+                             const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles,
+                             const int* collist, int t0, int nthin, int ntiles, int tn, int splits, int64_t cps,
+                             double* partials, cudaStream_t st) {
+  if (nthin == 0) return cudaSuccess;
+  const size_t sm = umma_thin_smem(ns, rmax);
+  cudaError_t e = cudaFuncSetAttribute(contract_thin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  contract_thin_kernel<<<dim3((unsigned)nthin, (unsigned)splits), TH_THREADS, sm, st>>>(
+      w0, bank, bstride, nc, ns, rmax, rowdesc, rows, coldesc, tiles, collist, t0, ntiles, tn, cps, partials);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, int tn, const int4* tiles,
