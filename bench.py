@@ -121,7 +121,8 @@ def _tc_work(ns, orders):
     for m0 in range(0, len(rows), 128):
         tile = rows[m0:m0 + 128]
         need = sum(1 for c in cols if any(canon(r, c) for r in tile))
-        if need <= 16 and len(tile) * need <= 256:
+        smem = (2 * (ns + 2) + len(tile) + 16) * 260 * 4 + (len(tile) + 16) * 8
+        if need <= 16 and len(tile) * need <= 256 and smem <= 227 * 1024:
             continue  # a thin tile: the CUDA cores sum it
         dense += len(tile) * need
     useful = sum(math.comb(ns + n - 2, n - 1) for n in orders)

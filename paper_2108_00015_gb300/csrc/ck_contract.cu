@@ -505,7 +505,7 @@ ck_status contract_prepare(Plan& p, int mask) {
     // tile costs the tensor cores as much as a full one
     auto thin = [&](const int4& t) {
       const int live = std::min<int>(TM, (int)rows.size() - t.x);
-      return t.w <= kThinMaxCols && live * t.w <= kThinMaxOut;
+      return t.w <= kThinMaxCols && live * t.w <= kThinMaxOut && umma_thin_smem(ns, live) <= (size_t)227 * 1024;
     };
     std::stable_partition(tl.begin(), tl.end(), [&](const int4& t) { return !thin(t); });
     c.um_ntc = 0;

@@ -553,8 +553,8 @@ __global__ void __launch_bounds__(TH_THREADS)
   const int4 tile = tiles[tile_i];
   const int R = rows - tile.x < UM_M ? rows - tile.x : UM_M;  // live rows (<= rmax)
   const int C = tile.w;                                          // live columns (<= kThinMaxCols)
-  float* ws = th_smem;                      // [ns + 2][TH_PITCH] W0, W_1 .. W_ns, ones
-  float* As = ws + (ns + 2) * TH_PITCH;     // [rmax][TH_PITCH]
+  float* wsb = th_smem;                     // [2][ns + 2][TH_PITCH] W0, W_1 .. W_ns, ones (double-buffered)
+  float* As = wsb + 2 * (ns + 2) * TH_PITCH;  // [rmax][TH_PITCH]
   float* Bs = As + rmax * TH_PITCH;         // [kThinMaxCols][TH_PITCH]
   int2* fa = reinterpret_cast<int2*>(Bs + kThinMaxCols * TH_PITCH);  // [rmax] staged rows of W_a, W_b
   int2* fb = fa + rmax;                                                // [kThinMaxCols] staged rows of W_c, W_d
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(TH_THREADS)
     const int2 d = coldesc[collist[tile.y + q]];
     fb[q] = make_int2(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE);
   }
-  for (int k = tid; k < TH_CELLS; k += TH_THREADS) ws[ONE * TH_PITCH + k] = 1.0f;
+  for (int k = tid; k < 2 * TH_CELLS; k += TH_THREADS) wsb[((k / TH_CELLS) * (ns + 2) + ONE) * TH_PITCH + k % TH_CELLS] = 1.0f;
   const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
   const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
   const int o = tid;  // this thread's output: row o / C, column o % C
@@ -576,24 +576,27 @@ __global__ void __launch_bounds__(TH_THREADS)
   const int orow = live ? o / C : 0, ocol = live ? o % C : 0;
   double dacc = 0.0;
   constexpr int K4 = TH_CELLS / 4;
-  for (int64_t c0 = beg; c0 < end; c0 += TH_CELLS) {
+  // W rows of the chunk at c0 into buffer b: 16-byte asynchronous copies
+  // (c0 is a multiple of 256 cells), zero-filled past the end
+  auto stage = [&](int64_t c0, int b) {
     const int vc = (int)std::min<int64_t>(TH_CELLS, end - c0);
-    // W rows of the chunk: 16-byte loads (c0 is a multiple of 256 cells), zeros past the end
+    float* ws = wsb + b * (ns + 2) * TH_PITCH;
     for (int i = tid; i < (ns + 1) * K4; i += TH_THREADS) {
       const int a = i / K4, k4 = i - a * K4;
-      const float* src = (a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride) + c0;
-      float4 v;
-      if (4 * k4 + 3 < vc) {
-        v = *reinterpret_cast<const float4*>(src + 4 * k4);
-      } else {
-        v.x = 4 * k4 < vc ? src[4 * k4] : 0.f;
-        v.y = 4 * k4 + 1 < vc ? src[4 * k4 + 1] : 0.f;
-        v.z = 4 * k4 + 2 < vc ? src[4 * k4 + 2] : 0.f;
-        v.w = 0.f;
-      }
-      *reinterpret_cast<float4*>(ws + a * TH_PITCH + 4 * k4) = v;
+      const float* src = (a == 0 ? w0 : bank + (int64_t)(a - 1) * bstride) + c0 + 4 * k4;
+      const int n = vc - 4 * k4 >= 4 ? 16 : (vc > 4 * k4 ? 4 * (vc - 4 * k4) : 0);
+      cp_async16n(ws + a * TH_PITCH + 4 * k4, n > 0 ? (const void*)src : (const void*)w0, n);
     }
+  };
+  if (beg < end) stage(beg, 0);
+  cp_async_commit();
+  int buf = 0;
+  for (int64_t c0 = beg; c0 < end; c0 += TH_CELLS, buf ^= 1) {
+    if (c0 + TH_CELLS < end) stage(c0 + TH_CELLS, buf ^ 1);  // read two chunks ago, before a barrier
+    cp_async_commit();
+    cp_async_wait<1>();  // this chunk's copies have landed
     __syncthreads();
+    const float* ws = wsb + buf * (ns + 2) * TH_PITCH;
     for (int i = tid; i < (R + C) * K4; i += TH_THREADS) {
       const int r = i / K4, k4 = i - r * K4;
       const bool isa = r < R;
@@ -626,15 +629,16 @@ __global__ void __launch_bounds__(TH_THREADS)
       }
       dacc += (double)acc0 + (double)acc1;
     }
-    __syncthreads();  // the next chunk rewrites ws, As and Bs
   }
+  cp_async_wait<0>();
   if (live) partials[((int64_t)blockIdx.y * ntiles + tile_i) * (int64_t)(UM_M * tn) + orow * tn + ocol] = dacc;
 }
 
 static_assert(kThinMaxOut <= TH_THREADS, "one output per thread");
 
 size_t umma_thin_smem(int ns, int rmax) {
-  return (size_t)(ns + 2 + rmax + kThinMaxCols) * TH_PITCH * sizeof(float) + (size_t)(rmax + kThinMaxCols) * sizeof(int2);
+  return (size_t)(2 * (ns + 2) + rmax + kThinMaxCols) * TH_PITCH * sizeof(float) +
+         (size_t)(rmax + kThinMaxCols) * sizeof(int2);
 }
 
 cudaError_t launch_umma_thin(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, int rmax,
