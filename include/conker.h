@@ -82,9 +82,20 @@ typedef enum ck_precision {
 } ck_precision;
 
 /* A grid of n[0] x n[1] x n[2] cubic cells of side `cell`, lower corner
- * `origin` (Sec. 2.2: grid spacing g_s).  Each n[a] must be even, <= 512 and
- * have no prime factor other than 2, 3, 5.  periodic != 0 selects a periodic
- * box (circular convolution); otherwise cells outside the box count as 0. */
+ * `origin` (Sec. 2.2: grid spacing g_s).  periodic:
+ *  CK_GRID_PERIODIC (1, or any value other than 0 and 2): a periodic box
+ *     (circular convolution);
+ *  0: a survey box, cells outside it count as 0 (linear convolution); the
+ *     transforms run on the box itself, so the occupied cells plus the
+ *     kernel's reach must fit in it (CK_ERR_GUARD_BAND otherwise);
+ *  CK_GRID_PADDED (2): a survey box as for 0, transformed on a zero-padded
+ *     grid of, per axis, the smallest supported length >= n[a] + max|m_a|
+ *     (the kernel's reach), so no guard band applies; n[a] is then any
+ *     size >= 2 whose padded length exists (<= 512).
+ * Otherwise each n[a] must be even, <= 512 and have no prime factor other
+ * than 2, 3, 5.  Points outside the box are dropped and counted (0 and 2). */
+#define CK_GRID_PERIODIC 1
+#define CK_GRID_PADDED 2
 typedef struct ck_grid {
   int32_t n[3];
   double origin[3];
@@ -104,7 +115,7 @@ typedef struct ck_shells {
 typedef struct ck_plan ck_plan;
 
 typedef struct ck_plan_info {
-  int64_t n_cells;                 /* n[0] n[1] n[2]                              */
+  int64_t n_cells;                 /* cells of the transformed grid (fft_n)       */
   int32_t spec_pitch;              /* complex elements per half-spectrum row      */
   int32_t n_shells;
   int32_t max_order;
@@ -116,6 +127,7 @@ typedef struct ck_plan_info {
   int32_t fused;                   /* 1: the last inverse FFT pass and the sums
                                       run as one kernel and no bank is kept
                                       (CK_PREC_SPLIT_TF32, n <= 3, <= 16 shells) */
+  int32_t fft_n[3];                /* the transformed grid: n, or padded         */
 } ck_plan_info;
 
 /* Outputs of ck_compute.  For order n (index n = 2..5), xi[n], num[n] and

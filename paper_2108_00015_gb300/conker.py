@@ -54,7 +54,7 @@ class _Info(ctypes.Structure):
                 ("max_order", ctypes.c_int32), ("max_offset", ctypes.c_int32 * 3),
                 ("shell_size", ctypes.c_int64 * CK_MAX_SHELLS), ("n_multisets", ctypes.c_int64 * (CK_MAX_ORDER + 1)),
                 ("workspace_bytes", ctypes.c_size_t), ("bank_stride", ctypes.c_int64),
-                ("fused", ctypes.c_int32)]
+                ("fused", ctypes.c_int32), ("fft_n", ctypes.c_int32 * 3)]
 
 
 CK_STAGES = 13
@@ -194,11 +194,13 @@ class Plan:
 
     def __init__(self, n: Sequence[int], origin: Sequence[float], cell: float, periodic: bool,
                  radii: Sequence[float], width: float, max_order: int = 3, rule: str = "center_bin",
-                 precision: str = "fp32", workspace: str = "torch", stream=None):
+                 precision: str = "fp32", workspace: str = "torch", stream=None, padded: bool = False):
+        """padded=True (a non-periodic box): transform on a zero-padded grid
+        (CK_GRID_PADDED); grids, fields and banks then have that grid's shape."""
         torch = _torch()
         lib = _lib()
         self._grid = _Grid((ctypes.c_int32 * 3)(*[int(v) for v in n]), (ctypes.c_double * 3)(*[float(v) for v in origin]),
-                           float(cell), 1 if periodic else 0)
+                           float(cell), 2 if padded else (1 if periodic else 0))
         self._radii = (ctypes.c_double * len(radii))(*[float(r) for r in radii])
         self._shells = _Shells(len(radii), self._radii, float(width), RULES[rule])
         self.max_order = int(max_order)
@@ -228,7 +230,8 @@ class Plan:
         self.workspace_bytes = int(info.workspace_bytes)
         self.bank_stride = int(info.bank_stride)
         self.fused = bool(info.fused)
-        self.shape = (int(n[2]), int(n[1]), int(n[0]))
+        self.fft_n = tuple(int(v) for v in info.fft_n)
+        self.shape = (self.fft_n[2], self.fft_n[1], self.fft_n[0])
 
     def close(self):
         if getattr(self, "_h", None):

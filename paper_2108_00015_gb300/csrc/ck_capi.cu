@@ -171,7 +171,7 @@ void twiddles(int n, std::vector<float2>& w) {
 ck_status upload_tables(Plan& p, cudaStream_t st) {
   for (int a = 0; a < 3; ++a) {
     std::vector<float> t;
-    thresholds(p.grid.origin[a], p.grid.cell, p.grid.n[a], t);
+    thresholds(p.grid.origin[a], p.grid.cell, p.box_n[a], t);  // cells of the box
     CK_TRY(cudaMemcpy(p.thr[a], t.data(), t.size() * 4, cudaMemcpyHostToDevice));
     std::vector<float2> w;
     twiddles(p.grid.n[a], w);
@@ -414,6 +414,7 @@ ck_status ck_plan_get_info(const ck_plan* plan, ck_plan_info* info) {
   info->workspace_bytes = p->ws_bytes;
   info->bank_stride = p->field_stride;
   info->fused = p->fused ? 1 : 0;
+  for (int a = 0; a < 3; ++a) info->fft_n[a] = p->grid.n[a];
   return CK_OK;
 }
 

@@ -19,7 +19,8 @@
 namespace ck {
 
 struct GridArgs {
-  int n[3];
+  int n[3];    // the box: cells 0 .. n - 1 per axis (points outside are dropped or wrapped)
+  int dim[3];  // the stored grid (the box, or its zero-padded transform grid)
   float of[3];
   float inv_g;
   double o[3];
@@ -95,7 +96,7 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
       }
       in = ok;
     }
-    const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.n[1] + ky) * A.n[0] + kx) : 0xFFFFFFFFu;
+    const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
     if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
   }
@@ -161,7 +162,8 @@ __global__ void set_catalog_ref_kernel(CatalogRef* ref, const float* x, const fl
 static GridArgs grid_args(const Plan& p) {
   GridArgs A;
   for (int a = 0; a < 3; ++a) {
-    A.n[a] = p.grid.n[a];
+    A.n[a] = p.box_n[a];
+    A.dim[a] = p.grid.n[a];
     A.o[a] = p.grid.origin[a];
     A.of[a] = (float)p.grid.origin[a];
     A.thr[a] = p.thr[a];

@@ -118,6 +118,7 @@ struct Plan {
   std::vector<double> radius;
   std::vector<std::vector<int>> offsets;  // per shell: flattened (mx, my, mz)
   int maxoff[3] = {0, 0, 0};
+  int box_n[3] = {0, 0, 0};  // the caller's box (points outside are dropped); grid.n is the transformed grid
   int64_t nc = 0;
   int px = 0;               // half-spectrum row pitch (complex elements)
   int64_t spec_elems = 0;   // n[2] * n[1] * px

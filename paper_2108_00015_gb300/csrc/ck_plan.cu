@@ -71,11 +71,16 @@ static bool finite(double v) { return isfinite(v) != 0; }
 ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int max_order,
                               int precision, Plan* p) {
   if (!grid || !shells || !p) return CK_ERR_BAD_POINTER;
+  const bool padded = grid->periodic == CK_GRID_PADDED;  // any other nonzero value: periodic
   for (int a = 0; a < 3; ++a) {
     const int n = grid->n[a];
-    if (n < 2 || n > 512 || (n % 2) != 0) return CK_ERR_UNSUPPORTED;
-    FftLen f;
-    if (!factor_len(n, &f) || !factor_len(n / 2, &f)) return CK_ERR_UNSUPPORTED;
+    if (padded) {
+      if (n < 2 || n > 512) return CK_ERR_UNSUPPORTED;
+    } else {
+      if (n < 2 || n > 512 || (n % 2) != 0) return CK_ERR_UNSUPPORTED;
+      FftLen f;
+      if (!factor_len(n, &f) || !factor_len(n / 2, &f)) return CK_ERR_UNSUPPORTED;
+    }
     if (!finite(grid->origin[a])) return CK_ERR_ARG;
   }
   if (!(grid->cell > 0.0) || !finite(grid->cell)) return CK_ERR_ARG;
@@ -112,12 +117,25 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
       for (int a = 0; a < 3; ++a) p->maxoff[a] = std::max(p->maxoff[a], abs(o[i + a]));
     p->offsets.push_back(std::move(o));
   }
+  for (int a = 0; a < 3; ++a) p->box_n[a] = grid->n[a];
+  if (padded) {
+    // the transformed grid: per axis the smallest supported length >= n + reach,
+    // so that no offset of a cell in the box wraps onto another cell of the box
+    p->grid.periodic = 0;
+    for (int a = 0; a < 3; ++a) {
+      int m = grid->n[a] + p->maxoff[a];
+      FftLen f;
+      while (m <= 512 && (m % 2 != 0 || !factor_len(m, &f) || !factor_len(m / 2, &f))) ++m;
+      if (m > 512) return CK_ERR_UNSUPPORTED;
+      p->grid.n[a] = m;
+    }
+  }
   // Offsets must stay distinct after wrapping into the FFT box.
   for (int a = 0; a < 3; ++a)
-    if (2 * p->maxoff[a] >= grid->n[a]) return CK_ERR_KERNEL_TOO_LARGE;
+    if (2 * p->maxoff[a] >= p->grid.n[a]) return CK_ERR_KERNEL_TOO_LARGE;
   p->H = std::max(p->maxoff[0], std::max(p->maxoff[1], p->maxoff[2]));
 
-  const int nx = grid->n[0], ny = grid->n[1], nz = grid->n[2];
+  const int nx = p->grid.n[0], ny = p->grid.n[1], nz = p->grid.n[2];
   p->nc = (int64_t)nx * ny * nz;
   p->field_stride = (p->nc + 63) / 64 * 64;
   p->px = ((nx / 2 + 1) + 3) / 4 * 4;

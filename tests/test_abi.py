@@ -66,6 +66,12 @@ def test_host_validation(lib):
     assert _ws(lib, radii=(170.0,))[0] == 5           # reaches half of a 32-cell box
     assert _ws(lib, rule=7)[0] == 1
     assert _ws(lib, width=0.0)[0] == 1
+    # zero-padded survey boxes (CK_GRID_PADDED): any box size whose padded length exists
+    assert _ws(lib, n=(23, 17, 15), periodic=2, cell=8.0, radii=(16.0, 24.0), width=8.0)[0] == 0
+    assert _ws(lib, n=(33, 32, 32), periodic=2)[0] == 0
+    assert _ws(lib, n=(510, 32, 32), periodic=2)[0] == 10  # 510 + reach > 512
+    padded = _ws(lib, n=(30, 30, 30), periodic=2)[1]
+    assert padded > _ws(lib, n=(30, 30, 30), periodic=0)[1]  # transformed on a larger grid
 
 
 def test_null_plan_entry_points(lib):
