@@ -46,6 +46,12 @@ Readings where the paper is silent or ambiguous (each is a choice):
    Sec. 2.2 counts the gridded points).
 6. Multisets with repetition (the diagonal of Eq. 14 is part of the tensor).
 7. A non-positive denominator gives xi = NaN for that entry.
+8. Weighted histograms (Sec. 2.2 allows "weighted counts"; Sec. 3 uses the
+   survey's systematic and FKP weights): a cell holds the sum of its points'
+   weights, each weight rounded to the nearest multiple of 2^-32 (ties to
+   even), summed exactly; a point with a non-finite weight is dropped.  The
+   rounding makes the sums independent of the order of addition; it moves a
+   weight by at most 2^-33.
 
 Pins: see tests/test_oracle_pins.py (brute-force pair and triplet counts on
 cell-centred points, three-square lattice counts, closed forms, symmetry,
@@ -60,7 +66,7 @@ from typing import Dict, Iterable, List, Sequence, Tuple
 import numpy as np
 
 __all__ = [
-    "cell_edge", "cell_index", "grid_counts", "density_fields", "shell_offsets",
+    "cell_edge", "cell_index", "grid_counts", "grid_weights", "quantize_weights", "density_fields", "shell_offsets",
     "check_periodic_support", "kernel_grid", "convolve_direct", "convolve_fft",
     "w_at_cells", "multisets", "product_sums", "dense_tensor", "xi_from",
     "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok", "pair_sums_fft",
@@ -108,6 +114,40 @@ def grid_counts(x, y, z, grid) -> Tuple[np.ndarray, int]:
     counts = np.bincount(flat, minlength=nx * ny * nz)
     assert counts.max(initial=0) < 2 ** 32
     return counts.astype(np.uint32).reshape(nz, ny, nx), dropped
+
+
+WEIGHT_FRAC_BITS = 32
+
+
+def quantize_weights(w) -> np.ndarray:
+    """Reading 8: each weight as an integer count of 2^-32 (nearest, ties to
+    even).  The product of a float32 weight and 2^32 is exact in FP64."""
+    return np.rint(np.asarray(w, np.float32).astype(np.float64) * 2.0 ** WEIGHT_FRAC_BITS).astype(np.int64)
+
+
+def grid_weights(x, y, z, w, grid) -> Tuple[np.ndarray, float, int]:
+    """Weighted histogram (Sec. 2.2, reading 8): per cell the exact sum of the
+    kept points' rounded weights, as FP64 of shape (nz, ny, nx); the total of
+    those weights; and the number of dropped points (outside a non-periodic
+    grid, or with a non-finite weight)."""
+    nx, ny, nz = (int(v) for v in grid.n)
+    w = np.asarray(w, np.float32)
+    ks = []
+    for coord, o, n in ((x, grid.origin[0], nx), (y, grid.origin[1], ny), (z, grid.origin[2], nz)):
+        k = cell_index(coord, o, grid.cell)
+        ks.append(np.mod(k, n) if grid.periodic else k)
+    kx, ky, kz = ks
+    keep = np.isfinite(w)
+    if not grid.periodic:
+        keep &= (kx >= 0) & (kx < nx) & (ky >= 0) & (ky < ny) & (kz >= 0) & (kz < nz)
+    dropped = int(w.size - int(keep.sum()))
+    flat = (kz[keep] * ny + ky[keep]) * nx + kx[keep]
+    q = quantize_weights(w[keep])
+    sums = np.zeros(nx * ny * nz, np.int64)
+    np.add.at(sums, flat, q)
+    assert np.abs(sums).max(initial=0) < 2 ** 53
+    scale = 2.0 ** -WEIGHT_FRAC_BITS
+    return (sums.astype(np.float64) * scale).reshape(nz, ny, nx), float(int(q.sum())) * scale, dropped
 
 
 def density_fields(D: np.ndarray, R: np.ndarray):
@@ -330,15 +370,21 @@ def xi_diagonal(W0, W1, B0, B1, order: int) -> float:
 
 def correlate(grid, shells: Sequence[float], width: float, data, randoms,
               orders: Sequence[int] = (2, 3), engine: str = "direct",
-              rule: str = "center_bin") -> Dict[str, object]:
+              rule: str = "center_bin", data_weights=None, random_weights=None) -> Dict[str, object]:
     """The whole path for one catalog: mapping, convolution, summation.
 
     Returns a dict with D, R, dropped counts, alpha, N, Rt, the offset lists,
     W and B banks, and per order n: num, den, abs_num, abs_den (per multiset)
     and the dense xi tensor [N_s]^(n-1).
     """
-    D, dropped_d = grid_counts(data.x, data.y, data.z, grid)
-    R, dropped_r = grid_counts(randoms.x, randoms.y, randoms.z, grid)
+    if data_weights is None:
+        D, dropped_d = grid_counts(data.x, data.y, data.z, grid)
+    else:  # weighted histograms (reading 8)
+        D, _, dropped_d = grid_weights(data.x, data.y, data.z, data_weights, grid)
+    if random_weights is None:
+        R, dropped_r = grid_counts(randoms.x, randoms.y, randoms.z, grid)
+    else:
+        R, _, dropped_r = grid_weights(randoms.x, randoms.y, randoms.z, random_weights, grid)
     alpha, N, Rt = density_fields(D, R)
     offs = [shell_offsets(s, width, grid.cell, rule) for s in shells]
     if grid.periodic:

@@ -540,11 +540,53 @@ def check_pair_sums_fft(o) -> bool:
     return bool(np.allclose(got, want, rtol=0, atol=1e-6))
 
 
+def check_grid_weights(o) -> bool:
+    """Weighted histograms (reading 8) against facts outside the function:
+    unit weights give the counts; small integer weights give the weighted
+    counts (exact); random weights differ from an FP64 sum by at most
+    2^-33 per point; exact rational arithmetic on a tiny case (signed
+    weights, ties of the rounding); non-finite weights are dropped."""
+    from fractions import Fraction
+    g = GridSpec((6, 5, 4), (1.0, -2.0, 0.5), 1.5, False)
+    rng = _rng(41)
+    cells = np.stack([rng.integers(-1, g.n[a] + 1, 400) for a in range(3)], axis=1)
+    cat = lattice_catalog(g, cells)
+    D, dropped = o.grid_counts(cat.x, cat.y, cat.z, g)
+    Dw, tot, dw = o.grid_weights(cat.x, cat.y, cat.z, np.ones(400, np.float32), g)
+    ok = dw == dropped and np.array_equal(Dw, D.astype(np.float64)) and tot == float(D.sum())
+    k = rng.integers(1, 4, 400).astype(np.float32)
+    Dk, _, _ = o.grid_weights(cat.x, cat.y, cat.z, k, g)
+    expect = np.zeros(D.shape, np.float64)
+    for (ix, iy, iz), kv in zip(cells, k):
+        if 0 <= ix < g.n[0] and 0 <= iy < g.n[1] and 0 <= iz < g.n[2]:
+            expect[iz, iy, ix] += float(kv)
+    ok &= np.array_equal(Dk, expect)
+    w = rng.uniform(0.1, 2.0, 400).astype(np.float32)
+    Dr, _, _ = o.grid_weights(cat.x, cat.y, cat.z, w, g)
+    fp = np.zeros(D.shape, np.float64)
+    for (ix, iy, iz), wv in zip(cells, w):
+        if 0 <= ix < g.n[0] and 0 <= iy < g.n[1] and 0 <= iz < g.n[2]:
+            fp[iz, iy, ix] += float(wv)
+    ok &= bool(np.all(np.abs(Dr - fp) <= D.astype(np.float64) * 2.0 ** -33 + 1e-15))
+    # tiny exact case: three points in one cell, signed weights, a rounding tie
+    tie = np.float32(3.0 * 2.0 ** -33)           # 1.5 units of 2^-32: rounds to 2 (even)
+    wt = np.array([0.75, -0.25, tie], np.float32)
+    one = lattice_catalog(g, np.array([[2, 1, 3]] * 3))
+    Dt, tt, _ = o.grid_weights(one.x, one.y, one.z, wt, g)
+    want = Fraction(3, 4) - Fraction(1, 4) + Fraction(2, 2 ** 32)
+    ok &= Fraction(float(Dt[3, 1, 2])) == want and Fraction(tt) == want and float(Dt.sum()) == float(want)
+    # non-finite weights are dropped
+    wn = np.array([1.0, np.nan, np.inf], np.float32)
+    Dn, _, dn = o.grid_weights(one.x, one.y, one.z, wn, g)
+    ok &= dn == 2 and float(Dn.sum()) == 1.0
+    return bool(ok)
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
     check_product_sums_high_order, check_signed_pairs, check_delta_response, check_fft_engine,
     check_constant_field_den, check_relabel_shells, check_translation, check_linearity,
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
-    check_multisets, check_guard_band, check_pair_sums_fft,
+    check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights,
 ]

@@ -62,6 +62,31 @@ def fft_no_conj_shift(F, offsets):
     return np.roll(_orig_fft(F, offsets), 1, axis=0)
 
 
+_orig_quant = O.quantize_weights
+
+
+def truncated_weights(w):
+    # rounds toward zero instead of to nearest (ties to even)
+    return np.trunc(np.asarray(w, np.float32).astype(np.float64) * 2.0 ** O.WEIGHT_FRAC_BITS).astype(np.int64)
+
+
+def float32_weight_sums(x, y, z, w, grid):
+    # sums the weights in float32 (order-dependent rounding)
+    nx, ny, nz = (int(v) for v in grid.n)
+    D, tot, dropped = _orig_gw(x, y, z, np.ones_like(np.asarray(w, np.float32)), grid)
+    acc = np.zeros(nx * ny * nz, np.float32)
+    k = [O.cell_index(c, o, grid.cell) for c, o in zip((x, y, z), grid.origin)]
+    keep = np.isfinite(np.asarray(w, np.float32))
+    for a, n in enumerate((nx, ny, nz)):
+        keep &= (k[a] >= 0) & (k[a] < n)
+    flat = (k[2][keep] * ny + k[1][keep]) * nx + k[0][keep]
+    np.add.at(acc, flat, np.asarray(w, np.float32)[keep])
+    return acc.astype(np.float64).reshape(nz, ny, nx), float(acc.sum()), dropped
+
+
+_orig_gw = O.grid_weights
+
+
 MUTANTS = [
     ("density_fields", wrong_sign_density),
     ("cell_index", off_by_one_index),
@@ -70,6 +95,8 @@ MUTANTS = [
     ("product_sums", dropped_w0),
     ("convolve_direct", dropped_offset),
     ("convolve_fft", fft_no_conj_shift),
+    ("quantize_weights", truncated_weights),
+    ("grid_weights", float32_weight_sums),
 ]
 
 
