@@ -180,6 +180,22 @@ ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const fl
 ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
                      int32_t order_mask, const ck_outputs* out, void* stream);
 
+/* Weighted histograms (Sec. 2.2: "weighted count of tracers"; Sec. 3: the
+ * survey's systematic and FKP weights): as ck_set_randoms / ck_compute, with
+ * a float32 weight per point (w, in the same memory space as the positions).
+ * A cell holds the sum of its points' weights: each weight is rounded to the
+ * nearest multiple of 2^-32 (ties to even) and summed exactly in 64-bit
+ * integers, so the sums do not depend on the order of addition; the cell
+ * value is that sum rounded to float32.  alpha is the ratio of the exact
+ * weight totals.  A point with a non-finite weight is dropped and counted.
+ * Weighted and unweighted fields may be mixed (weighted data over unweighted
+ * randoms and so on); ck_get_grids returns, for a weighted field, the float32
+ * bit patterns of its cells. */
+ck_status ck_set_randoms_weighted(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
+                                  int64_t n, void* stream);
+ck_status ck_compute_weighted(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
+                              int64_t n, int32_t order_mask, const ck_outputs* out, void* stream);
+
 /* The equidistant n-point functions alone (Sec. 2.6, Eq. 14): the same path
  * as ck_compute up to W_s, then for every shell s and requested order n only
  * the diagonal multiset (s, .., s):

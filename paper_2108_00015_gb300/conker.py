@@ -91,6 +91,9 @@ _SIGS = [
     ("ck_set_randoms", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     ("ck_compute", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_set_randoms_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("ck_set_randoms_weighted", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("ck_compute_weighted", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.POINTER(_Outputs), _P]),
     ("ck_compute_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs),
                                            _P]),
     ("ck_batch_compute", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_Catalog), ctypes.c_int32,
@@ -246,10 +249,16 @@ class Plan:
             pass
 
     # -- the path ----------------------------------------------------------
-    def set_randoms(self, x, y, z, stream=None):
+    def set_randoms(self, x, y, z, stream=None, w=None):
+        """Grid the randoms (ck_set_randoms; with weights w: ck_set_randoms_weighted)."""
         x, y, z = _as_f32(x), _as_f32(y), _as_f32(z)
-        _check(_lib().ck_set_randoms(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), _stream_ptr(stream)),
-               "ck_set_randoms")
+        if w is None:
+            _check(_lib().ck_set_randoms(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), _stream_ptr(stream)),
+                   "ck_set_randoms")
+        else:
+            w = _as_f32(w)
+            _check(_lib().ck_set_randoms_weighted(self._h, _ptr(x), _ptr(y), _ptr(z), _ptr(w), int(x.shape[0]),
+                                                  _stream_ptr(stream)), "ck_set_randoms_weighted")
 
     def set_randoms_diagonal(self, x, y, z, stream=None):
         """ck_set_randoms_diagonal: only the (s, .., s) denominators (for compute_diagonal)."""
@@ -258,7 +267,7 @@ class Plan:
                                               _stream_ptr(stream)), "ck_set_randoms_diagonal")
 
     def compute(self, x, y, z, orders=(2, 3), out: str = "device", stream=None, want=("xi", "num", "den"),
-                outputs: Optional[Dict[str, Dict[int, object]]] = None) -> Dict[str, object]:
+                outputs: Optional[Dict[str, Dict[int, object]]] = None, w=None) -> Dict[str, object]:
         """One catalog; returns {'xi': {n: T}, 'num': ..., 'den': ..., 'dropped': T} with dense
         [N_s]^(n-1) float64 tensors on the device (out='device') or in host memory (out='host')."""
         torch = _torch()
@@ -283,8 +292,13 @@ class Plan:
             dropped = torch.zeros(2, dtype=torch.int64, device=dev)
         o.dropped = dropped.data_ptr()
         res["dropped"] = dropped
-        code = _lib().ck_compute(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), order_mask(orders),
-                                 ctypes.byref(o), _stream_ptr(stream))
+        if w is None:
+            code = _lib().ck_compute(self._h, _ptr(x), _ptr(y), _ptr(z), int(x.shape[0]), order_mask(orders),
+                                     ctypes.byref(o), _stream_ptr(stream))
+        else:  # weighted histogram of the data (ck_compute_weighted)
+            w = _as_f32(w)
+            code = _lib().ck_compute_weighted(self._h, _ptr(x), _ptr(y), _ptr(z), _ptr(w), int(x.shape[0]),
+                                              order_mask(orders), ctypes.byref(o), _stream_ptr(stream))
         res["status"] = int(code)
         if code not in (0, 7):  # a zero denominator still fills the outputs (NaN there)
             raise CkError(code, "ck_compute")

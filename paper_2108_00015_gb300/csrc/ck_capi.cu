@@ -89,6 +89,8 @@ bool is_device_ptr(const void* p) {
 
 __global__ void reset_state_kernel(DevState* st, int which) {
   st->kept[which] = 0;
+  st->wsum[which] = 0;
+  st->weighted[which] = 0;
   st->dropped[which] = 0;
   for (int a = 0; a < 3; ++a) {
     st->bbox_min[which][a] = 0x7fffffff;
@@ -113,7 +115,8 @@ ck_status carve(Plan& p) {
   p.khat = reinterpret_cast<float*>(take((size_t)p.ns * p.khat_stride * 4));
   p.bank = reinterpret_cast<float*>(take(std::max((size_t)p.bank_fields * p.field_stride * 4, khat_scratch_doubles(p) * 8)));
   p.partials = reinterpret_cast<double*>(take(p.partials_cap * 8));
-  p.staging = reinterpret_cast<float*>(take((size_t)2 * 3 * p.staging_pts * 4));
+  p.staging = reinterpret_cast<float*>(take((size_t)2 * 4 * p.staging_pts * 4));
+  p.wacc = reinterpret_cast<long long*>(take((size_t)p.nc * 8));
   for (int a = 0; a < 3; ++a) p.thr[a] = reinterpret_cast<float*>(take((size_t)(p.grid.n[a] + 1) * 4));
   for (int a = 0; a < 3; ++a) p.tw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
   for (int a = 0; a < 3; ++a) p.stw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
@@ -204,30 +207,41 @@ ck_status upload_tables(Plan& p, cudaStream_t st) {
 }
 
 // Grid one catalog (host or device positions) into counts[which].
+// Grid field `which` (0 data, 1 randoms) from positions x, y, z and, when w
+// is not NULL, per-point weights (all four in the same memory space).
 ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, int64_t n, int which,
-                       cudaStream_t st) {
+                       cudaStream_t st, const float* w = nullptr) {
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, which);
   CK_TRY(cudaMemsetAsync(p.counts[which], 0, (size_t)p.nc * 4, st));
-  if (n == 0) return cuda_status(cudaGetLastError());
-  const bool dx = is_device_ptr(x), dy = is_device_ptr(y), dz = is_device_ptr(z);
-  if (dx != dy || dx != dz) return CK_ERR_BAD_POINTER;
-  if (dx) {
-    launch_grid_points(p, x, y, z, n, which, st);
-    return cuda_status(cudaGetLastError());
+  if (w) CK_TRY(cudaMemsetAsync(p.wacc, 0, (size_t)p.nc * 8, st));
+  if (n > 0) {
+    const bool dx = is_device_ptr(x), dy = is_device_ptr(y), dz = is_device_ptr(z);
+    if (dx != dy || dx != dz || (w && is_device_ptr(w) != dx)) return CK_ERR_BAD_POINTER;
+    auto grid = [&](const float* gx, const float* gy, const float* gz, const float* gw, int64_t cnt) {
+      if (w) launch_grid_points_weighted(p, gx, gy, gz, gw, cnt, which, st);
+      else launch_grid_points(p, gx, gy, gz, cnt, which, st);
+    };
+    if (dx) {
+      grid(x, y, z, w, n);
+    } else {
+      // host positions (and weights): stream them through the staging slots
+      int slot = 0;
+      for (int64_t off = 0; off < n; off += p.staging_pts) {
+        const int64_t cnt = std::min<int64_t>(p.staging_pts, n - off);
+        float* sx = p.staging + (size_t)slot * 4 * p.staging_pts;
+        float* sy = sx + p.staging_pts;
+        float* sz = sy + p.staging_pts;
+        float* sw = sz + p.staging_pts;
+        CK_TRY(cudaMemcpyAsync(sx, x + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+        CK_TRY(cudaMemcpyAsync(sy, y + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+        CK_TRY(cudaMemcpyAsync(sz, z + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+        if (w) CK_TRY(cudaMemcpyAsync(sw, w + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
+        grid(sx, sy, sz, sw, cnt);
+        slot ^= 1;
+      }
+    }
   }
-  // host positions: stream them through the staging slots
-  int slot = 0;
-  for (int64_t off = 0; off < n; off += p.staging_pts) {
-    const int64_t cnt = std::min<int64_t>(p.staging_pts, n - off);
-    float* sx = p.staging + (size_t)slot * 3 * p.staging_pts;
-    float* sy = sx + p.staging_pts;
-    float* sz = sy + p.staging_pts;
-    CK_TRY(cudaMemcpyAsync(sx, x + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
-    CK_TRY(cudaMemcpyAsync(sy, y + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
-    CK_TRY(cudaMemcpyAsync(sz, z + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, st));
-    launch_grid_points(p, sx, sy, sz, cnt, which, st);
-    slot ^= 1;
-  }
+  if (w) launch_weights_to_cells(p, which, st);
   return cuda_status(cudaGetLastError());
 }
 
@@ -418,14 +432,15 @@ ck_status ck_plan_get_info(const ck_plan* plan, ck_plan_info* info) {
   return CK_OK;
 }
 
-ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n, void* stream) {
+static ck_status set_randoms_impl(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
+                                  int64_t n, void* stream) {
   if (!plan) return CK_ERR_BAD_POINTER;
   if (n < 0) return CK_ERR_ARG;
   if (n > 0 && (!x || !y || !z)) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   cudaStream_t st = S(stream);
   p.have_randoms = p.have_randoms_diag = false;
-  CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st));
+  CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st, w));
   launch_prepare_randoms(p, st);
   p.bank_holds = -1;
   CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st));
@@ -433,6 +448,16 @@ ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const fl
   CK_TRY(cudaGetLastError());
   p.have_randoms = p.have_randoms_diag = true;
   return CK_OK;
+}
+
+ck_status ck_set_randoms(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n, void* stream) {
+  return set_randoms_impl(plan, x, y, z, nullptr, n, stream);
+}
+
+ck_status ck_set_randoms_weighted(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
+                                  int64_t n, void* stream) {
+  if (n > 0 && !w) return CK_ERR_BAD_POINTER;
+  return set_randoms_impl(plan, x, y, z, w, n, stream);
 }
 
 ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
@@ -456,8 +481,8 @@ ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y,
   return CK_OK;
 }
 
-ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
-                     int32_t order_mask, const ck_outputs* out, void* stream) {
+static ck_status compute_impl(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
+                              int64_t n, int32_t order_mask, const ck_outputs* out, void* stream) {
   if (!plan) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   if (n < 0) return CK_ERR_ARG;
@@ -465,7 +490,7 @@ ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float*
   if (order_mask == 0 || (order_mask & ~full_mask(p)) != 0) return CK_ERR_ARG;
   if (!p.have_randoms) return CK_ERR_NO_RANDOMS;
   cudaStream_t st = S(stream);
-  CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st));
+  CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st, w));
   launch_prepare_data(p, st);
   p.bank_holds = -1;
   CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st));
@@ -476,6 +501,17 @@ ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float*
   CK_TRY_S(copy_results(p, order_mask, out, st, &host_seen));
   if (host_seen) return read_status(p, st, true);
   return CK_OK;
+}
+
+ck_status ck_compute(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
+                     int32_t order_mask, const ck_outputs* out, void* stream) {
+  return compute_impl(plan, x, y, z, nullptr, n, order_mask, out, stream);
+}
+
+ck_status ck_compute_weighted(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
+                              int64_t n, int32_t order_mask, const ck_outputs* out, void* stream) {
+  if (n > 0 && !w) return CK_ERR_BAD_POINTER;
+  return compute_impl(plan, x, y, z, w, n, order_mask, out, stream);
 }
 
 ck_status ck_compute_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,

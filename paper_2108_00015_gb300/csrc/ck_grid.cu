@@ -71,23 +71,37 @@ __device__ __forceinline__ bool axis_cell(float x, int a, const GridArgs& A, int
   return true;
 }
 
+// Counts (W = false: warp-aggregated 32-bit atomics on counts) or weights
+// (W = true: each weight rounded to a multiple of 2^-32, a 64-bit atomic on
+// acc per point, so the integer sums do not depend on the order of the
+// atomics; a point with a non-finite weight is dropped).
+template <bool W>
 __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, const float* __restrict__ ys,
-                                                 const float* __restrict__ zs, int64_t npts, const GridArgs& A,
-                                                 uint32_t* __restrict__ counts, DevState* st, int which) {
+                                                 const float* __restrict__ zs, const float* __restrict__ ws,
+                                                 int64_t npts, const GridArgs& A, uint32_t* __restrict__ counts,
+                                                 long long* __restrict__ acc, DevState* st, int which) {
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nround = (npts + 31) / 32 * 32;  // warp-uniform trip count
   unsigned long long kept = 0, dropped = 0;
+  long long qsum = 0;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
   for (int64_t i = first; i < nround; i += stride) {
     bool in = i < npts;
     int kx = 0, ky = 0, kz = 0;
+    long long q = 0;
     if (in) {
-      const bool ok = axis_cell(__ldg(xs + i), 0, A, &kx) && axis_cell(__ldg(ys + i), 1, A, &ky) &&
-                      axis_cell(__ldg(zs + i), 2, A, &kz);
+      bool ok = axis_cell(__ldg(xs + i), 0, A, &kx) && axis_cell(__ldg(ys + i), 1, A, &ky) &&
+                axis_cell(__ldg(zs + i), 2, A, &kz);
+      if constexpr (W) {
+        const float w = __ldg(ws + i);
+        ok = ok && isfinite(w);
+        if (ok) q = llrint((double)w * 4294967296.0);  // exact product; nearest, ties to even
+      }
       if (ok) {
         ++kept;
+        qsum += q;
         bmin[0] = min(bmin[0], kx); bmax[0] = max(bmax[0], kx);
         bmin[1] = min(bmin[1], ky); bmax[1] = max(bmax[1], ky);
         bmin[2] = min(bmin[2], kz); bmax[2] = max(bmax[2], kz);
@@ -97,13 +111,18 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
       in = ok;
     }
     const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
-    if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
+    if constexpr (W) {
+      if (in) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
+    } else {
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
+      if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
+    }
   }
   // block reduction of the counters and bounding boxes
   for (int off = 16; off > 0; off >>= 1) {
     kept += __shfl_down_sync(0xFFFFFFFFu, kept, off);
     dropped += __shfl_down_sync(0xFFFFFFFFu, dropped, off);
+    if constexpr (W) qsum += __shfl_down_sync(0xFFFFFFFFu, qsum, off);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -111,21 +130,24 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
     bmax[a] = __reduce_max_sync(0xFFFFFFFFu, bmax[a]);
   }
   __shared__ unsigned long long sk[8], sd[8];
+  __shared__ long long sq[8];
   __shared__ int smin[8][3], smax[8][3];
   const int w = threadIdx.x >> 5;
   if (lane == 0) {
-    sk[w] = kept; sd[w] = dropped;
+    sk[w] = kept; sd[w] = dropped; sq[w] = qsum;
     for (int a = 0; a < 3; ++a) { smin[w][a] = bmin[a]; smax[w][a] = bmax[a]; }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long K = 0, Dr = 0;
+    long long Q = 0;
     int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
     for (int j = 0; j < (int)(blockDim.x >> 5); ++j) {
-      K += sk[j]; Dr += sd[j];
+      K += sk[j]; Dr += sd[j]; Q += sq[j];
       for (int a = 0; a < 3; ++a) { mn[a] = min(mn[a], smin[j][a]); mx[a] = max(mx[a], smax[j][a]); }
     }
     if (K) atomicAdd(&st->kept[which], K);
+    if (W && Q) atomicAdd(reinterpret_cast<unsigned long long*>(&st->wsum[which]), (unsigned long long)Q);
     if (Dr) atomicAdd(&st->dropped[which], Dr);
     if (K) {
       for (int a = 0; a < 3; ++a) {
@@ -141,7 +163,27 @@ __global__ void __launch_bounds__(256) grid_points_kernel(const float* __restric
                                                           const float* __restrict__ zs, int64_t npts,
                                                           GridArgs A, uint32_t* __restrict__ counts,
                                                           DevState* st, int which) {
-  grid_points_body(xs, ys, zs, npts, A, counts, st, which);
+  grid_points_body<false>(xs, ys, zs, nullptr, npts, A, counts, nullptr, st, which);
+}
+
+__global__ void __launch_bounds__(256) grid_points_weighted_kernel(const float* __restrict__ xs,
+                                                                   const float* __restrict__ ys,
+                                                                   const float* __restrict__ zs,
+                                                                   const float* __restrict__ ws, int64_t npts,
+                                                                   GridArgs A, long long* __restrict__ acc,
+                                                                   DevState* st, int which) {
+  grid_points_body<true>(xs, ys, zs, ws, npts, A, nullptr, acc, st, which);
+}
+
+// A weighted field's cells: the exact sums of the rounded weights as
+// float32 (nearest), in the field's 32-bit count buffer; the field is marked
+// weighted for the preparation kernels.
+__global__ void weights_to_cells_kernel(const long long* __restrict__ acc, uint32_t* __restrict__ cells, int64_t nc,
+                                        DevState* st, int which) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
+    cells[i] = __float_as_uint((float)((double)acc[i] * 2.3283064365386962890625e-10));  // 2^-32
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->weighted[which] = 1;
 }
 
 // The same with the catalog read from a device descriptor, so that one
@@ -149,7 +191,7 @@ __global__ void __launch_bounds__(256) grid_points_kernel(const float* __restric
 __global__ void __launch_bounds__(256) grid_points_ref_kernel(const CatalogRef* __restrict__ ref, GridArgs A,
                                                               uint32_t* __restrict__ counts, DevState* st,
                                                               int which) {
-  grid_points_body(ref->x, ref->y, ref->z, ref->n, A, counts, st, which);
+  grid_points_body<false>(ref->x, ref->y, ref->z, nullptr, ref->n, A, counts, nullptr, st, which);
 }
 
 __global__ void set_catalog_ref_kernel(CatalogRef* ref, const float* x, const float* y, const float* z, int64_t n) {
@@ -204,11 +246,15 @@ __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __res
                                                            DevState* st, int periodic, int nx, int ny,
                                                            int nz, int mx, int my, int mz) {
   const unsigned long long kd = st->kept[0], kr = st->kept[1];
-  const double alpha = kr ? (double)kd / (double)kr : 0.0;
+  const bool wd = st->weighted[0] != 0, wr = st->weighted[1] != 0;
+  // totals: counts, or exact weight sums (units of 2^-32)
+  const double td = wd ? (double)st->wsum[0] * 2.3283064365386962890625e-10 : (double)kd;
+  const double tr = wr ? (double)st->wsum[1] * 2.3283064365386962890625e-10 : (double)kr;
+  const double alpha = tr > 0.0 ? td / tr : 0.0;
   const float af = (float)alpha;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->alpha = alpha;
-    if (kd == 0 || kr == 0) set_status(&st->status, CK_ERR_EMPTY_CATALOG);
+    if (kd == 0 || kr == 0 || !(tr > 0.0)) set_status(&st->status, CK_ERR_EMPTY_CATALOG);
     if (!periodic && kd && kr) {
       const int n[3] = {nx, ny, nz}, m[3] = {mx, my, mz};
       for (int a = 0; a < 3; ++a) {
@@ -223,29 +269,33 @@ __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __res
   const uint4* D4 = reinterpret_cast<const uint4*>(D);
   const uint4* R4 = reinterpret_cast<const uint4*>(R);
   float4* F4 = reinterpret_cast<float4*>(field);
+  // a cell: a count, or the float32 bits of a weight sum
+  auto val = [](uint32_t u, bool weighted) { return weighted ? __uint_as_float(u) : (float)u; };
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
     const uint4 d = __ldg(D4 + i), r = __ldg(R4 + i);
-    F4[i] = make_float4(fmaf(-af, (float)r.x, (float)d.x), fmaf(-af, (float)r.y, (float)d.y),
-                        fmaf(-af, (float)r.z, (float)d.z), fmaf(-af, (float)r.w, (float)d.w));
+    F4[i] = make_float4(fmaf(-af, val(r.x, wr), val(d.x, wd)), fmaf(-af, val(r.y, wr), val(d.y, wd)),
+                        fmaf(-af, val(r.z, wr), val(d.z, wd)), fmaf(-af, val(r.w, wr), val(d.w, wd)));
   }
   for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
-    field[i] = fmaf(-af, (float)R[i], (float)D[i]);
+    field[i] = fmaf(-af, val(R[i], wr), val(D[i], wd));
 }
 
 __global__ void __launch_bounds__(256) prepare_randoms_kernel(const uint32_t* __restrict__ R,
                                                               float* __restrict__ field, int64_t nc,
                                                               DevState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && st->kept[1] == 0) set_status(&st->status, CK_ERR_EMPTY_CATALOG);
+  const bool wr = st->weighted[1] != 0;
+  auto val = [](uint32_t u, bool weighted) { return weighted ? __uint_as_float(u) : (float)u; };
   const int64_t n4 = nc / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const uint4* R4 = reinterpret_cast<const uint4*>(R);
   float4* F4 = reinterpret_cast<float4*>(field);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
     const uint4 r = __ldg(R4 + i);
-    F4[i] = make_float4((float)r.x, (float)r.y, (float)r.z, (float)r.w);
+    F4[i] = make_float4(val(r.x, wr), val(r.y, wr), val(r.z, wr), val(r.w, wr));
   }
   for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
-    field[i] = (float)R[i];
+    field[i] = val(R[i], wr);
 }
 
 static unsigned elementwise_blocks(const Plan& p, int64_t n) {
@@ -259,6 +309,23 @@ void launch_prepare_data(const Plan& p, cudaStream_t st) {
   prepare_data_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(
       p.counts[0], p.counts[1], p.field, p.nc, p.dstate, p.grid.periodic ? 1 : 0, p.grid.n[0],
       p.grid.n[1], p.grid.n[2], p.maxoff[0], p.maxoff[1], p.maxoff[2]);
+}
+
+void launch_grid_points_weighted(const Plan& p, const float* x, const float* y, const float* z, const float* w,
+                                 int64_t n, int which, cudaStream_t st) {
+  if (n <= 0) return;
+  const GridArgs A = grid_args(p);
+  const int64_t warps = (n + 31) / 32;
+  int64_t blocks = std::min<int64_t>((warps + 7) / 8, (int64_t)p.sm_count * 8);
+  if (blocks < 1) blocks = 1;
+  ProfScope ps(p, ST_GRID, 16.0 * (double)n, st);
+  grid_points_weighted_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, y, z, w, n, A, p.wacc, p.dstate, which);
+}
+
+void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st) {
+  ProfScope ps(p, ST_GRID, 12.0 * (double)p.nc, st);
+  weights_to_cells_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.wacc, p.counts[which], p.nc, p.dstate,
+                                                                        which);
 }
 
 void launch_prepare_randoms(const Plan& p, cudaStream_t st) {

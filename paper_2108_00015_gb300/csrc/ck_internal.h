@@ -24,6 +24,8 @@ struct CatalogRef {
 
 struct DevState {
   unsigned long long kept[2];
+  long long wsum[2];  // weighted fields: the kept points' weights, in units of 2^-32
+  int weighted[2];    // field k gridded with weights: its cells hold float32 weight sums
   unsigned long long dropped[2];
   int bbox_min[2][3];
   int bbox_max[2][3];
@@ -139,7 +141,8 @@ struct Plan {
   void* ws = nullptr;
   bool owns_ws = false;
   size_t ws_bytes = 0;
-  uint32_t* counts[2] = {nullptr, nullptr};
+  uint32_t* counts[2] = {nullptr, nullptr};  // counts, or the float32 bits of weight sums (DevState::weighted)
+  long long* wacc = nullptr;  // [nc] fixed-point weight sums of the field being gridded
   float* field = nullptr;
   float2* spec = nullptr;
   float2* tmp = nullptr;
@@ -212,6 +215,10 @@ void launch_set_catalog_ref(const Plan& p, const float* x, const float* y, const
 void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // catalog from p.dref
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
+// Weighted gridding into p.wacc (zeroed by the caller), then the cells of field `which`.
+void launch_grid_points_weighted(const Plan& p, const float* x, const float* y, const float* z, const float* w,
+                                 int64_t n, int which, cudaStream_t st);
+void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st);
 
 // ---- launches (ck_fft.cu) ----------------------------------------------------
 ck_status fft_init_attributes();

@@ -219,7 +219,8 @@ size_t workspace_bytes(const Plan& p) {
   b += al((size_t)p.ns * p.khat_stride * 4);                   // khat (padded octants)
   b += al(std::max((size_t)p.bank_fields * p.field_stride * 4, khat_scratch_doubles(p) * 8));  // bank
   b += al(p.partials_cap * 8);                                 // partials
-  b += al((size_t)2 * 3 * p.staging_pts * 4);                  // staging
+  b += al((size_t)2 * 4 * p.staging_pts * 4);                  // staging: x, y, z, w per slot
+  b += al((size_t)p.nc * 8);                                   // fixed-point weight sums
   for (int a = 0; a < 3; ++a) b += al((size_t)(p.grid.n[a] + 1) * 4);  // thresholds
   for (int a = 0; a < 3; ++a) b += 2 * al((size_t)p.grid.n[a] * 8);    // twiddles: full and per-iteration
   b += al(sizeof(DevState));
