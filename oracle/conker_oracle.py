@@ -52,6 +52,9 @@ Readings where the paper is silent or ambiguous (each is a choice):
    even), summed exactly; a point with a non-finite weight is dropped.  The
    rounding makes the sums independent of the order of addition; it moves a
    weight by at most 2^-33.
+9. Sky coordinates (Sec. 2.1): right ascension and declination in degrees;
+   r(z) is Eq. 3's line-of-sight integral exactly as printed (no curvature
+   transform), and X, Y, Z follow Eqs. 4-6.
 
 Pins: see tests/test_oracle_pins.py (brute-force pair and triplet counts on
 cell-centred points, three-square lattice counts, closed forms, symmetry,
@@ -70,6 +73,7 @@ __all__ = [
     "check_periodic_support", "kernel_grid", "convolve_direct", "convolve_fft",
     "w_at_cells", "multisets", "product_sums", "dense_tensor", "xi_from",
     "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok", "pair_sums_fft",
+    "comoving_distance", "sky_to_cartesian",
 ]
 
 
@@ -161,6 +165,31 @@ def density_fields(D: np.ndarray, R: np.ndarray):
     Dd = D.astype(np.float64)
     Rd = R.astype(np.float64)
     return alpha, Dd - alpha * Rd, alpha * Rd
+
+
+# ---------------------------------------------------------------------------
+# Input coordinates (Sec. 2.1, Eqs. 3-6)
+
+def comoving_distance(z, h0: float, omega_m: float, omega_k: float, omega_l: float, c: float) -> np.ndarray:
+    """Eq. 3: r(z) = (c / H0) int_0^z dz' / sqrt(O_M (1+z')^3 + O_k (1+z')^2 + O_L),
+    by adaptive quadrature (a library primitive) for every redshift, FP64."""
+    from scipy.integrate import quad
+    z = np.asarray(z, np.float64)
+    f = lambda t: 1.0 / math.sqrt(omega_m * (1 + t) ** 3 + omega_k * (1 + t) ** 2 + omega_l)  # noqa: E731
+    out = np.empty(z.shape, np.float64)
+    for i, zi in np.ndenumerate(z):
+        out[i] = (c / h0) * quad(f, 0.0, float(zi), epsabs=0.0, epsrel=1e-13, limit=200)[0]
+    return out
+
+
+def sky_to_cartesian(ra_deg, dec_deg, z, h0: float, omega_m: float, omega_k: float, omega_l: float,
+                     c: float) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Eqs. 4-6: X = r cos(dec) cos(ra), Y = r cos(dec) sin(ra), Z = r sin(dec),
+    r = r(z) of Eq. 3, angles in degrees (reading 9), FP64."""
+    r = comoving_distance(z, h0, omega_m, omega_k, omega_l, c)
+    a = np.radians(np.asarray(ra_deg, np.float64))
+    d = np.radians(np.asarray(dec_deg, np.float64))
+    return r * np.cos(d) * np.cos(a), r * np.cos(d) * np.sin(a), r * np.sin(d)
 
 
 # ---------------------------------------------------------------------------

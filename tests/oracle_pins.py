@@ -582,11 +582,40 @@ def check_grid_weights(o) -> bool:
     return bool(ok)
 
 
+def check_sky_coordinates(o) -> bool:
+    """r(z) of Eq. 3 against closed forms: Einstein-de Sitter (O_M = 1:
+    2 (c/H0) (1 - 1/sqrt(1+z))), pure Lambda (O_L = 1: c z / H0), curvature
+    only (O_k = 1: (c/H0) ln(1+z)); Eqs. 4-6 on the axes and |X| = r."""
+    z = np.array([0.0, 0.05, 0.3, 0.57, 1.0, 2.5])
+    c, h0 = 299792.458, 67.7
+    ok = np.allclose(o.comoving_distance(z, h0, 1.0, 0.0, 0.0, c),
+                     2.0 * c / h0 * (1.0 - 1.0 / np.sqrt(1.0 + z)), rtol=1e-12, atol=1e-9)
+    ok &= np.allclose(o.comoving_distance(z, h0, 0.0, 0.0, 1.0, c), c * z / h0, rtol=1e-12, atol=1e-9)
+    ok &= np.allclose(o.comoving_distance(z, h0, 0.0, 1.0, 0.0, c), c / h0 * np.log1p(z), rtol=1e-12, atol=1e-9)
+    # a flat LCDM distance grows with z and lies between the EdS and Lambda ones
+    rl = o.comoving_distance(z, 100.0, 0.307, 0.0, 0.693, 300000.0)
+    ok &= bool(np.all(np.diff(rl) > 0))
+    ok &= bool(np.all(rl[1:] < 300000.0 / 100.0 * z[1:]))
+    ok &= bool(np.all(rl[1:] > 2 * 3000.0 * (1 - 1 / np.sqrt(1 + z[1:]))))
+    ra = np.array([0.0, 90.0, 0.0, 180.0, 33.0])
+    dec = np.array([0.0, 0.0, 90.0, 0.0, -41.0])
+    zz = np.full(5, 0.5)
+    X, Y, Z = o.sky_to_cartesian(ra, dec, zz, 100.0, 0.307, 0.0, 0.693, 300000.0)
+    r = o.comoving_distance(zz, 100.0, 0.307, 0.0, 0.693, 300000.0)
+    ok &= np.allclose([X[0], Y[0], Z[0]], [r[0], 0, 0], atol=1e-9)
+    ok &= np.allclose([X[1], Y[1], Z[1]], [0, r[1], 0], atol=1e-9)
+    ok &= np.allclose([X[2], Y[2], Z[2]], [0, 0, r[2]], atol=1e-9)
+    ok &= np.allclose([X[3], Y[3], Z[3]], [-r[3], 0, 0], atol=1e-9)
+    ok &= np.allclose(np.sqrt(X ** 2 + Y ** 2 + Z ** 2), r, rtol=1e-14)
+    ok &= bool(Z[4] < 0 and X[4] > 0 and Y[4] > 0)
+    return bool(ok)
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
     check_product_sums_high_order, check_signed_pairs, check_delta_response, check_fft_engine,
     check_constant_field_den, check_relabel_shells, check_translation, check_linearity,
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
-    check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights,
+    check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights, check_sky_coordinates,
 ]

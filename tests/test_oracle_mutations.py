@@ -85,6 +85,20 @@ def float32_weight_sums(x, y, z, w, grid):
 
 
 _orig_gw = O.grid_weights
+_orig_cd = O.comoving_distance
+
+
+def curvature_dropped(z, h0, omega_m, omega_k, omega_l, c):
+    # leaves out the curvature term of Eq. 3
+    return _orig_cd(z, h0, omega_m, 0.0, omega_l, c)
+
+
+def swapped_angles(ra_deg, dec_deg, z, h0, omega_m, omega_k, omega_l, c):
+    # declination and right ascension exchanged in Eqs. 4-6
+    r = _orig_cd(z, h0, omega_m, omega_k, omega_l, c)
+    a = np.radians(np.asarray(dec_deg, np.float64))
+    d = np.radians(np.asarray(ra_deg, np.float64))
+    return r * np.cos(d) * np.cos(a), r * np.cos(d) * np.sin(a), r * np.sin(d)
 
 
 MUTANTS = [
@@ -97,6 +111,8 @@ MUTANTS = [
     ("convolve_fft", fft_no_conj_shift),
     ("quantize_weights", truncated_weights),
     ("grid_weights", float32_weight_sums),
+    ("comoving_distance", curvature_dropped),
+    ("sky_to_cartesian", swapped_angles),
 ]
 
 
