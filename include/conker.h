@@ -196,6 +196,35 @@ ck_status ck_set_randoms_weighted(ck_plan* plan, const float* x, const float* y,
 ck_status ck_compute_weighted(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
                               int64_t n, int32_t order_mask, const ck_outputs* out, void* stream);
 
+/* --- survey input (Sec. 2.1) -------------------------------------------------- */
+
+/* The fiducial cosmology of Eq. 3: H0 in km/s/Mpc (100 gives distances in
+ * h^-1 Mpc), the present-day densities O_M, O_k, O_L, the speed of light c in
+ * km/s, and the largest redshift of the catalog (the range of the distance
+ * table). */
+typedef struct ck_cosmology {
+  double h0;
+  double omega_m;
+  double omega_k;
+  double omega_l;
+  double c;
+  double z_max;
+} ck_cosmology;
+
+/* Sky coordinates to the grid's Cartesian frame: r = r(z) of Eq. 3,
+ * r(z) = (c / H0) int_0^z dz' / sqrt(O_M (1+z')^3 + O_k (1+z')^2 + O_L),
+ * evaluated on the device (a table of 4097 nodes on [0, z_max], 8-point
+ * Gauss-Legendre quadrature per interval, cubic Hermite interpolation:
+ * error below 1e-12 of r), then Eqs. 4-6: X = r cos(dec) cos(ra),
+ * Y = r cos(dec) sin(ra), Z = r sin(dec), angles in degrees.  All six arrays
+ * are device float32 of n entries (CK_ERR_BAD_POINTER otherwise); a redshift
+ * outside [0, z_max] or a non-finite input gives NaN coordinates, which
+ * gridding drops and counts.  CK_ERR_ARG for a non-finite or non-positive
+ * h0, c or z_max, or E^2 <= 0 somewhere on [0, z_max].  Stream-ordered; the
+ * distance table is a stream-ordered allocation freed after use. */
+ck_status ck_sky_to_cartesian(const ck_cosmology* cosmo, const float* ra_deg, const float* dec_deg,
+                              const float* redshift, int64_t n, float* x, float* y, float* z, void* stream);
+
 /* The equidistant n-point functions alone (Sec. 2.6, Eq. 14): the same path
  * as ck_compute up to W_s, then for every shell s and requested order n only
  * the diagonal multiset (s, .., s):

@@ -44,6 +44,11 @@ class _Grid(ctypes.Structure):
                 ("periodic", ctypes.c_int32)]
 
 
+class _Cosmology(ctypes.Structure):
+    _fields_ = [("h0", ctypes.c_double), ("omega_m", ctypes.c_double), ("omega_k", ctypes.c_double),
+                ("omega_l", ctypes.c_double), ("c", ctypes.c_double), ("z_max", ctypes.c_double)]
+
+
 class _Shells(ctypes.Structure):
     _fields_ = [("n_shells", ctypes.c_int32), ("radius", ctypes.POINTER(ctypes.c_double)),
                 ("width", ctypes.c_double), ("rule", ctypes.c_int32)]
@@ -91,6 +96,8 @@ _SIGS = [
     ("ck_set_randoms", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     ("ck_compute", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_set_randoms_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("ck_sky_to_cartesian", ctypes.c_int, [ctypes.POINTER(_Cosmology), _P, _P, _P, ctypes.c_int64, _P, _P, _P,
+                                           _P]),
     ("ck_set_randoms_weighted", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, _P]),
     ("ck_compute_weighted", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
                                            ctypes.POINTER(_Outputs), _P]),
@@ -170,6 +177,26 @@ def _as_f32(a):
     torch = _torch()
     assert a.dtype == torch.float32 and a.is_contiguous(), "positions must be contiguous float32"
     return a
+
+
+def sky_to_cartesian(ra_deg, dec_deg, redshift, h0: float = 100.0, omega_m: float = 0.307,
+                     omega_k: float = 0.0, omega_l: float = 0.693, c: float = 300000.0, z_max: Optional[float] = None,
+                     stream=None):
+    """Sky coordinates (degrees, redshift; device float32 tensors) to the
+    Cartesian frame of Eqs. 3-6 (ck_sky_to_cartesian): returns device float32
+    tensors X, Y, Z.  z_max (default: the largest redshift) sets the distance
+    table's range; points outside [0, z_max] get NaN.  The defaults are the
+    paper's fiducial cosmology (Sec. 3), distances in h^-1 Mpc."""
+    torch = _torch()
+    ra, dec, z = _as_f32(ra_deg), _as_f32(dec_deg), _as_f32(redshift)
+    n = int(z.shape[0])
+    if z_max is None:
+        z_max = float(z.max().item()) if n else 1.0
+    cosmo = _Cosmology(float(h0), float(omega_m), float(omega_k), float(omega_l), float(c), float(z_max))
+    X, Y, Z = (torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3))
+    _check(_lib().ck_sky_to_cartesian(ctypes.byref(cosmo), _ptr(ra), _ptr(dec), _ptr(z), n, _ptr(X), _ptr(Y),
+                                      _ptr(Z), _stream_ptr(stream)), "ck_sky_to_cartesian")
+    return X, Y, Z
 
 
 def contract_static(w0, bank, bank_stride: int, n_cells: int, n_shells: int, orders=(2, 3), stream=None):

@@ -57,16 +57,11 @@ void prof_collect(ck::Plan& p) {
   }
   f.used = 0;
 }
+
 }  // namespace
 
-using namespace ck;
-
-namespace {
-
-cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
-
 // Device memory (or managed) vs host memory.
-bool is_device_ptr(const void* p) {
+bool ck::is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -74,6 +69,12 @@ bool is_device_ptr(const void* p) {
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+using namespace ck;
+
+namespace {
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 #define CK_TRY(expr)                                  \
   do {                                                \

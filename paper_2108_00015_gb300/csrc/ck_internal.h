@@ -192,6 +192,7 @@ size_t workspace_bytes(const Plan& p);
 size_t khat_scratch_doubles(const Plan& p);
 bool factor_len(int n, FftLen* out);
 ck_status cuda_status(cudaError_t e);
+bool is_device_ptr(const void* p);  // device or managed memory
 int64_t binom(int64_t n, int64_t k);
 
 // Record the start / end of one launch of `stage` (no-ops unless enabled).

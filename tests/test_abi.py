@@ -86,6 +86,22 @@ def test_null_plan_entry_points(lib):
         assert fn(None, None, None, None, 0, 4, ctypes.byref(o), None) == 2, name  # CK_ERR_BAD_POINTER
 
 
+def test_sky_validation(lib):
+    """ck_sky_to_cartesian checks its cosmology before any CUDA call."""
+    from paper_2108_00015_gb300.conker import _Cosmology
+    f = lib.ck_sky_to_cartesian
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.POINTER(_Cosmology)] + [ctypes.c_void_p] * 3 + [ctypes.c_int64] + [ctypes.c_void_p] * 4
+    ok = _Cosmology(100.0, 0.307, 0.0, 0.693, 300000.0, 1.0)
+    assert f(ok, None, None, None, 0, None, None, None, None) == 0          # nothing to do
+    assert f(None, None, None, None, 0, None, None, None, None) == 2        # CK_ERR_BAD_POINTER
+    assert f(ok, None, None, None, -1, None, None, None, None) == 1         # CK_ERR_ARG
+    assert f(ok, None, None, None, 5, None, None, None, None) == 2          # missing arrays
+    for bad in (_Cosmology(0.0, 0.3, 0.0, 0.7, 3e5, 1.0), _Cosmology(100.0, 0.3, 0.0, 0.7, 3e5, -1.0),
+                _Cosmology(100.0, 0.3, 0.0, -2.0, 3e5, 1.0), _Cosmology(100.0, float("nan"), 0.0, 0.7, 3e5, 1.0)):
+        assert f(bad, None, None, None, 0, None, None, None, None) == 1
+
+
 def test_survey_workspace_fits(lib):
     # 512^3, 16 shells, orders <= 3.  Mixed (split-TF32, fused pass, no bank):
     # counts + field + spectrum + 16 scratch spectra + kernel octants + one field
