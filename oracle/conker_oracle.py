@@ -55,6 +55,13 @@ Readings where the paper is silent or ambiguous (each is a choice):
 9. Sky coordinates (Sec. 2.1): right ascension and declination in degrees;
    r(z) is Eq. 3's line-of-sight integral exactly as printed (no curvature
    transform), and X, Y, Z follow Eqs. 4-6.
+10. Factorised randoms (Eq. 7): P_ang is a probability per steradian on an
+   equiangular grid of right ascension [0, 360) x declination [-90, 90]
+   (nearest cell), P_z a probability per unit redshift in uniform bins of
+   [z_lo, z_hi) (0 outside); the expected count of a grid cell is the
+   density at its centre times its volume,
+   R = N_tot P_ang(ra, dec) P_z(z(r)) (dz/dr) g^3 / r^2, dz/dr = H0 E(z) / c,
+   and 0 where r exceeds r(z_max) or r = 0.
 
 Pins: see tests/test_oracle_pins.py (brute-force pair and triplet counts on
 cell-centred points, three-square lattice counts, closed forms, symmetry,
@@ -73,7 +80,7 @@ __all__ = [
     "check_periodic_support", "kernel_grid", "convolve_direct", "convolve_fft",
     "w_at_cells", "multisets", "product_sums", "dense_tensor", "xi_from",
     "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok", "pair_sums_fft",
-    "comoving_distance", "sky_to_cartesian",
+    "comoving_distance", "sky_to_cartesian", "factorised_randoms_at", "factorised_randoms",
 ]
 
 
@@ -190,6 +197,46 @@ def sky_to_cartesian(ra_deg, dec_deg, z, h0: float, omega_m: float, omega_k: flo
     a = np.radians(np.asarray(ra_deg, np.float64))
     d = np.radians(np.asarray(dec_deg, np.float64))
     return r * np.cos(d) * np.cos(a), r * np.cos(d) * np.sin(a), r * np.sin(d)
+
+
+def factorised_randoms_at(cells, grid, n_tot: float, p_ang: np.ndarray, p_z: np.ndarray, z_lo: float, z_hi: float,
+                          z_max: float, h0: float, omega_m: float, omega_k: float, omega_l: float,
+                          c: float) -> np.ndarray:
+    """Eq. 7 (reading 10) at chosen cells (ix, iy, iz) of the grid, FP64:
+    p_ang has shape (n_dec, n_ra), p_z shape (n_z,).  z(r) inverts Eq. 3 by
+    root finding (a library primitive)."""
+    from scipy.optimize import brentq
+    cells = np.asarray(cells, np.int64).reshape(-1, 3)
+    ctr = np.asarray(grid.origin, np.float64) + (cells + 0.5) * grid.cell
+    X, Y, Z = ctr[:, 0], ctr[:, 1], ctr[:, 2]
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    rmax = float(comoving_distance(z_max, h0, omega_m, omega_k, omega_l, c))
+    n_dec, n_ra = p_ang.shape
+    out = np.zeros(len(cells), np.float64)
+    for i in range(len(cells)):
+        if not (0.0 < r[i] <= rmax):
+            continue
+        zi = brentq(lambda t: float(comoving_distance(t, h0, omega_m, omega_k, omega_l, c)) - r[i], 0.0, z_max,
+                    xtol=1e-14, rtol=1e-14)
+        if not (z_lo <= zi < z_hi):
+            continue
+        ra = math.degrees(math.atan2(Y[i], X[i])) % 360.0
+        dec = math.degrees(math.asin(Z[i] / r[i]))
+        ia = min(int(ra / 360.0 * n_ra), n_ra - 1)
+        idd = min(int((dec + 90.0) / 180.0 * n_dec), n_dec - 1)
+        iz = min(int((zi - z_lo) / (z_hi - z_lo) * len(p_z)), len(p_z) - 1)
+        a = 1.0 + zi
+        dzdr = h0 * math.sqrt(omega_m * a ** 3 + omega_k * a ** 2 + omega_l) / c
+        out[i] = n_tot * float(p_ang[idd, ia]) * float(p_z[iz]) * dzdr * grid.cell ** 3 / (r[i] * r[i])
+    return out
+
+
+def factorised_randoms(grid, **sel) -> np.ndarray:
+    """The whole randoms field of Eq. 7, shape (nz, ny, nx), FP64."""
+    nx, ny, nz = grid.n
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1)
+    return factorised_randoms_at(cells, grid, **sel).reshape(nz, ny, nx)
 
 
 # ---------------------------------------------------------------------------
@@ -399,18 +446,23 @@ def xi_diagonal(W0, W1, B0, B1, order: int) -> float:
 
 def correlate(grid, shells: Sequence[float], width: float, data, randoms,
               orders: Sequence[int] = (2, 3), engine: str = "direct",
-              rule: str = "center_bin", data_weights=None, random_weights=None) -> Dict[str, object]:
+              rule: str = "center_bin", data_weights=None, random_weights=None,
+              random_field=None) -> Dict[str, object]:
     """The whole path for one catalog: mapping, convolution, summation.
 
     Returns a dict with D, R, dropped counts, alpha, N, Rt, the offset lists,
     W and B banks, and per order n: num, den, abs_num, abs_den (per multiset)
-    and the dense xi tensor [N_s]^(n-1).
+    and the dense xi tensor [N_s]^(n-1).  random_field, when given, is the
+    randoms histogram itself (the factorised field of Eq. 7) and `randoms`
+    is not read.
     """
     if data_weights is None:
         D, dropped_d = grid_counts(data.x, data.y, data.z, grid)
     else:  # weighted histograms (reading 8)
         D, _, dropped_d = grid_weights(data.x, data.y, data.z, data_weights, grid)
-    if random_weights is None:
+    if random_field is not None:
+        R, dropped_r = np.asarray(random_field, np.float64), 0
+    elif random_weights is None:
         R, dropped_r = grid_counts(randoms.x, randoms.y, randoms.z, grid)
     else:
         R, _, dropped_r = grid_weights(randoms.x, randoms.y, randoms.z, random_weights, grid)

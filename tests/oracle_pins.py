@@ -611,6 +611,67 @@ def check_sky_coordinates(o) -> bool:
     return bool(ok)
 
 
+
+def _sel(**kw):
+    base = dict(n_tot=1.0e5, p_ang=np.full((1, 1), 1.0 / (4.0 * np.pi)), p_z=np.array([1.0 / 0.04]),
+                z_lo=0.02, z_hi=0.06, z_max=0.065, h0=100.0, omega_m=0.0, omega_k=0.0, omega_l=1.0,
+                c=300000.0)
+    base.update(kw)
+    return base
+
+
+def check_factorised_randoms(o) -> bool:
+    """Eq. 7 (reading 10) against facts outside the function: P_ang (per
+    steradian) and P_z (per unit z) are probability densities, so the field
+    sums to N_tot over a grid that covers the shell (within the cells'
+    discretisation, 4 % on 20-unit cells), with masks in right ascension, declination and
+    redshift that leave nothing on the masked side; in an Einstein-de Sitter
+    universe, where 1 + z = (1 - r H0 / 2c)^-2 and dz/dr = (H0/c)(1+z)^1.5,
+    each cell's value follows in closed form; cells beyond r(z_max) are 0."""
+    g = GridSpec((20, 20, 20), (-200.0, -200.0, -200.0), 20.0, False)
+    nx, ny, nz = g.n
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    X = g.origin[0] + (ix + 0.5) * g.cell
+    Y = g.origin[1] + (iy + 0.5) * g.cell
+    Z = g.origin[2] + (iz + 0.5) * g.cell
+    # pure Lambda: r = c z / H0 over [60, 180] h^-1 Mpc, uniform densities
+    R = o.factorised_randoms(g, **_sel())
+    ok = abs(R.sum() / 1.0e5 - 1.0) < 0.04 and float(R[np.sqrt(X * X + Y * Y + Z * Z) > 195.0].max()) == 0.0
+    # northern sky only: P_ang = 1 / (2 pi) for dec >= 0
+    R = o.factorised_randoms(g, **_sel(p_ang=np.array([[0.0], [1.0 / (2.0 * np.pi)]])))
+    ok &= abs(R.sum() / 1.0e5 - 1.0) < 0.04 and float(R[Z < 0].max()) == 0.0
+    # one quadrant in right ascension, 90 <= ra < 180 (X < 0 < Y): P_ang = 1 / pi
+    pa = np.zeros((1, 4))
+    pa[0, 1] = 1.0 / np.pi
+    R = o.factorised_randoms(g, **_sel(p_ang=pa))
+    ok &= abs(R.sum() / 1.0e5 - 1.0) < 0.04 and float(R[~((X < 0) & (Y > 0))].max()) == 0.0
+    # the far half of the redshift range: nothing below r = 120
+    R = o.factorised_randoms(g, **_sel(p_z=np.array([0.0, 2.0 / 0.04])))
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    ok &= abs(R.sum() / 1.0e5 - 1.0) < 0.04 and float(R[r < 119.0].max()) == 0.0
+    # Einstein-de Sitter closed form at sampled cells, a non-uniform sky
+    rng = _rng(57)
+    pa = rng.uniform(0.5, 1.5, (6, 12))
+    pz = rng.uniform(0.5, 1.5, 5)
+    sel = _sel(p_ang=pa, p_z=pz, omega_m=1.0, omega_l=0.0, h0=70.0, c=299792.458, z_lo=0.02, z_hi=0.08,
+               z_max=0.09)
+    cells = np.stack([rng.integers(0, 20, 60) for _ in range(3)], axis=1)
+    got = o.factorised_randoms_at(cells, g, **sel)
+    ctr = np.asarray(g.origin) + (cells + 0.5) * g.cell
+    rr = np.sqrt((ctr * ctr).sum(axis=1))
+    zz = (1.0 - rr * 70.0 / (2.0 * 299792.458)) ** -2.0 - 1.0
+    ra = np.degrees(np.arctan2(ctr[:, 1], ctr[:, 0])) % 360.0
+    dec = np.degrees(np.arcsin(ctr[:, 2] / rr))
+    want = np.zeros(len(cells))
+    live = (zz >= 0.02) & (zz < 0.08)
+    for i in np.nonzero(live)[0]:
+        pav = pa[int((dec[i] + 90.0) // 30.0), int(ra[i] // 30.0)]
+        pzv = pz[int((zz[i] - 0.02) // 0.012)]
+        want[i] = 1.0e5 * pav * pzv * (70.0 / 299792.458) * (1.0 + zz[i]) ** 1.5 * 8000.0 / rr[i] ** 2
+    ok &= bool(live.sum() > 10) and bool(np.allclose(got, want, rtol=1e-9, atol=0.0))
+    return bool(ok)
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
@@ -618,4 +679,5 @@ ALL_CHECKS = [
     check_constant_field_den, check_relabel_shells, check_translation, check_linearity,
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
     check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights, check_sky_coordinates,
+    check_factorised_randoms,
 ]

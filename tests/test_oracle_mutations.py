@@ -101,6 +101,21 @@ def swapped_angles(ra_deg, dec_deg, z, h0, omega_m, omega_k, omega_l, c):
     return r * np.cos(d) * np.cos(a), r * np.cos(d) * np.sin(a), r * np.sin(d)
 
 
+
+_orig_fr = O.factorised_randoms_at
+
+
+def flipped_declination(cells, grid, **sel):
+    # declination bins counted from the north pole instead of the south
+    return _orig_fr(cells, grid, **dict(sel, p_ang=np.asarray(sel["p_ang"])[::-1]))
+
+
+def linear_jacobian(cells, grid, **sel):
+    # dV_sph taken as r dr dOmega instead of r^2 dr dOmega
+    ctr = np.asarray(grid.origin, np.float64) + (np.asarray(cells, np.float64).reshape(-1, 3) + 0.5) * grid.cell
+    return _orig_fr(cells, grid, **sel) * np.sqrt((ctr * ctr).sum(axis=1))
+
+
 MUTANTS = [
     ("density_fields", wrong_sign_density),
     ("cell_index", off_by_one_index),
@@ -113,6 +128,8 @@ MUTANTS = [
     ("grid_weights", float32_weight_sums),
     ("comoving_distance", curvature_dropped),
     ("sky_to_cartesian", swapped_angles),
+    ("factorised_randoms_at", flipped_declination),
+    ("factorised_randoms_at", linear_jacobian),
 ]
 
 
