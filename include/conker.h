@@ -225,6 +225,48 @@ typedef struct ck_cosmology {
 ck_status ck_sky_to_cartesian(const ck_cosmology* cosmo, const float* ra_deg, const float* dec_deg,
                               const float* redshift, int64_t n, float* x, float* y, float* z, void* stream);
 
+/* A factorised selection (Sec. 2.2, Eq. 7): the angular density P_ang per
+ * steradian on an equiangular grid of n_dec declination rows (row j covers
+ * dec in [-90 + 180 j / n_dec, -90 + 180 (j+1) / n_dec) degrees) by n_ra
+ * right-ascension columns (column i: ra in [360 i / n_ra, 360 (i+1) / n_ra)),
+ * row-major with declination slowest; the redshift density P_z per unit z in
+ * n_z equal bins of [z_lo, z_hi); N_tot the number of tracers.  Both tables
+ * in HOST memory (copied at the call), entries finite and >= 0. */
+typedef struct ck_selection {
+  double n_tot;
+  const double* p_ang;
+  int32_t n_ra;
+  int32_t n_dec;
+  const double* p_z;
+  int32_t n_z;
+  int32_t pad;
+  double z_lo;
+  double z_hi;
+} ck_selection;
+
+/* The randoms field from the factorised selection instead of a random
+ * catalog (Eq. 7): at every cell centre (X, Y, Z) of the plan's box, with
+ * r = |(X, Y, Z)|, z = z(r) the inverse of Eq. 3 (the distance table of
+ * ck_sky_to_cartesian, inverted per cell by Newton steps on its cubic
+ * Hermite interpolant), ra = atan2(Y, X) in [0, 360), dec = asin(Z / r),
+ *   R = N_tot P_ang(ra, dec) P_z(z) (dz/dr) g^3 / r^2,  dz/dr = H0 E(z) / c,
+ * the cell's expected count (g^3 over the spherical volume element
+ * r^2 dr dOmega, dr = dz c / (H0 E)), and R = 0 where z is outside
+ * [z_lo, z_hi), r = 0 or r > r(z_max).  The cells are stored as float32
+ * (ck_get_grids returns their bits, as for weighted fields), the field's
+ * total is their FP64 sum in a fixed order (the same on every run), and
+ * alpha = (data total) / (that total) as for any randoms field, so the xi
+ * do not depend on N_tot.  Then the denominators of every order, as
+ * ck_set_randoms.  Errors: CK_ERR_BAD_POINTER for NULL arguments or device
+ * tables; CK_ERR_ARG for a cosmology ck_sky_to_cartesian rejects, table
+ * sizes < 1 or n_ra * n_dec > 2^26, non-finite or negative entries or
+ * N_tot, z_lo < 0 or z_hi <= z_lo; a field with no nonzero cell makes the
+ * next ck_compute report CK_ERR_EMPTY_CATALOG.  On an argument error the
+ * plan's previous randoms are kept.  Stream-ordered; scratch is a
+ * stream-ordered allocation freed after use. */
+ck_status ck_set_randoms_factorised(ck_plan* plan, const ck_cosmology* cosmo, const ck_selection* sel,
+                                    void* stream);
+
 /* The equidistant n-point functions alone (Sec. 2.6, Eq. 14): the same path
  * as ck_compute up to W_s, then for every shell s and requested order n only
  * the diagonal multiset (s, .., s):

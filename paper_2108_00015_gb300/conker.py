@@ -49,6 +49,12 @@ class _Cosmology(ctypes.Structure):
                 ("omega_l", ctypes.c_double), ("c", ctypes.c_double), ("z_max", ctypes.c_double)]
 
 
+class _Selection(ctypes.Structure):
+    _fields_ = [("n_tot", ctypes.c_double), ("p_ang", ctypes.POINTER(ctypes.c_double)), ("n_ra", ctypes.c_int32),
+                ("n_dec", ctypes.c_int32), ("p_z", ctypes.POINTER(ctypes.c_double)), ("n_z", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("z_lo", ctypes.c_double), ("z_hi", ctypes.c_double)]
+
+
 class _Shells(ctypes.Structure):
     _fields_ = [("n_shells", ctypes.c_int32), ("radius", ctypes.POINTER(ctypes.c_double)),
                 ("width", ctypes.c_double), ("rule", ctypes.c_int32)]
@@ -99,6 +105,7 @@ _SIGS = [
     ("ck_sky_to_cartesian", ctypes.c_int, [ctypes.POINTER(_Cosmology), _P, _P, _P, ctypes.c_int64, _P, _P, _P,
                                            _P]),
     ("ck_set_randoms_weighted", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("ck_set_randoms_factorised", ctypes.c_int, [_P, ctypes.POINTER(_Cosmology), ctypes.POINTER(_Selection), _P]),
     ("ck_compute_weighted", ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32,
                                            ctypes.POINTER(_Outputs), _P]),
     ("ck_compute_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs),
@@ -286,6 +293,27 @@ class Plan:
             w = _as_f32(w)
             _check(_lib().ck_set_randoms_weighted(self._h, _ptr(x), _ptr(y), _ptr(z), _ptr(w), int(x.shape[0]),
                                                   _stream_ptr(stream)), "ck_set_randoms_weighted")
+
+    def set_randoms_factorised(self, n_tot: float, p_ang, p_z, z_lo: float, z_hi: float, h0: float = 100.0,
+                               omega_m: float = 0.307, omega_k: float = 0.0, omega_l: float = 0.693,
+                               c: float = 300000.0, z_max: Optional[float] = None, stream=None):
+        """ck_set_randoms_factorised: the randoms field of Eq. 7 from the
+        angular density p_ang (per steradian; shape (n_dec, n_ra), declination
+        rows from -90, right-ascension columns from 0) and the redshift density
+        p_z (per unit z, n_z bins of [z_lo, z_hi)); z_max (default z_hi) is the
+        distance table's range.  Defaults: the paper's fiducial cosmology."""
+        import numpy as np
+        pa = np.ascontiguousarray(np.asarray(p_ang, np.float64))
+        pz = np.ascontiguousarray(np.asarray(p_z, np.float64).ravel())
+        if pa.ndim != 2:
+            raise ValueError("p_ang must be 2-D (n_dec, n_ra)")
+        cosmo = _Cosmology(float(h0), float(omega_m), float(omega_k), float(omega_l), float(c),
+                           float(z_hi if z_max is None else z_max))
+        dptr = ctypes.POINTER(ctypes.c_double)
+        sel = _Selection(float(n_tot), pa.ctypes.data_as(dptr), int(pa.shape[1]), int(pa.shape[0]),
+                         pz.ctypes.data_as(dptr), int(pz.shape[0]), 0, float(z_lo), float(z_hi))
+        _check(_lib().ck_set_randoms_factorised(self._h, ctypes.byref(cosmo), ctypes.byref(sel),
+                                                _stream_ptr(stream)), "ck_set_randoms_factorised")
 
     def set_randoms_diagonal(self, x, y, z, stream=None):
         """ck_set_randoms_diagonal: only the (s, .., s) denominators (for compute_diagonal)."""

@@ -92,6 +92,7 @@ __global__ void reset_state_kernel(DevState* st, int which) {
   st->kept[which] = 0;
   st->wsum[which] = 0;
   st->weighted[which] = 0;
+  st->fsum[which] = 0.0;
   st->dropped[which] = 0;
   for (int a = 0; a < 3; ++a) {
     st->bbox_min[which][a] = 0x7fffffff;
@@ -459,6 +460,25 @@ ck_status ck_set_randoms_weighted(ck_plan* plan, const float* x, const float* y,
                                   int64_t n, void* stream) {
   if (n > 0 && !w) return CK_ERR_BAD_POINTER;
   return set_randoms_impl(plan, x, y, z, w, n, stream);
+}
+
+ck_status ck_set_randoms_factorised(ck_plan* plan, const ck_cosmology* cosmo, const ck_selection* sel,
+                                    void* stream) {
+  if (!plan || !cosmo || !sel) return CK_ERR_BAD_POINTER;
+  CK_TRY_S(check_factorised(cosmo, sel));
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  cudaStream_t st = S(stream);
+  p.have_randoms = p.have_randoms_diag = false;
+  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 1);
+  CK_TRY(cudaMemsetAsync(p.counts[1], 0, (size_t)p.nc * 4, st));
+  CK_TRY_S(launch_factorised_randoms(p, cosmo, sel, st));
+  launch_prepare_randoms(p, st);
+  p.bank_holds = -1;
+  CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st));
+  p.bank_holds = 1;
+  CK_TRY(cudaGetLastError());
+  p.have_randoms = p.have_randoms_diag = true;
+  return CK_OK;
 }
 
 ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,

@@ -247,9 +247,13 @@ __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __res
                                                            int nz, int mx, int my, int mz) {
   const unsigned long long kd = st->kept[0], kr = st->kept[1];
   const bool wd = st->weighted[0] != 0, wr = st->weighted[1] != 0;
-  // totals: counts, or exact weight sums (units of 2^-32)
-  const double td = wd ? (double)st->wsum[0] * 2.3283064365386962890625e-10 : (double)kd;
-  const double tr = wr ? (double)st->wsum[1] * 2.3283064365386962890625e-10 : (double)kr;
+  // totals: counts, exact weight sums (units of 2^-32), or FP64 field totals
+  auto total = [&](int k, unsigned long long kept) {
+    return st->weighted[k] == 2 ? st->fsum[k]
+           : st->weighted[k]    ? (double)st->wsum[k] * 2.3283064365386962890625e-10
+                                : (double)kept;
+  };
+  const double td = total(0, kd), tr = total(1, kr);
   const double alpha = tr > 0.0 ? td / tr : 0.0;
   const float af = (float)alpha;
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -25,13 +25,14 @@ struct CatalogRef {
 struct DevState {
   unsigned long long kept[2];
   long long wsum[2];  // weighted fields: the kept points' weights, in units of 2^-32
-  int weighted[2];    // field k gridded with weights: its cells hold float32 weight sums
+  int weighted[2];    // 1: cells hold float32 weight sums, total wsum; 2: float32 cells, total fsum
   unsigned long long dropped[2];
   int bbox_min[2][3];
   int bbox_max[2][3];
   int status;
   int pad;
   double alpha;
+  double fsum[2];     // fields computed in place (weighted == 2): the FP64 total of the cells
 };
 
 constexpr int kMaxStages = 8;
@@ -216,6 +217,11 @@ void launch_set_catalog_ref(const Plan& p, const float* x, const float* y, const
 void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // catalog from p.dref
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
+// The factorised randoms field of Eq. 7 (ck_sky.cu): check_factorised
+// validates the arguments; launch_factorised_randoms writes counts[1] (float
+// bits) and the field's totals, after the caller has reset field 1.
+ck_status check_factorised(const ck_cosmology* cosmo, const ck_selection* sel);
+ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck_selection* sel, cudaStream_t st);
 // Weighted gridding into p.wacc (zeroed by the caller), then the cells of field `which`.
 void launch_grid_points_weighted(const Plan& p, const float* x, const float* y, const float* z, const float* w,
                                  int64_t n, int which, cudaStream_t st);

@@ -102,6 +102,35 @@ def test_sky_validation(lib):
         assert f(bad, None, None, None, 0, None, None, None, None) == 1
 
 
+
+def test_factorised_validation(lib):
+    """ck_set_randoms_factorised checks its cosmology and selection on the
+    host before it touches the plan (a placeholder handle here)."""
+    import numpy as np
+    from paper_2108_00015_gb300.conker import _Cosmology, _Selection
+    f = lib.ck_set_randoms_factorised
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Cosmology), ctypes.POINTER(_Selection), ctypes.c_void_p]
+    handle = ctypes.create_string_buffer(64)
+    dptr = ctypes.POINTER(ctypes.c_double)
+    pa = np.full((3, 4), 0.1)
+    pz = np.ones(5)
+
+    def sel(n_tot=1e5, a=pa, z=pz, nra=4, ndec=3, nz=5, zlo=0.1, zhi=0.5):
+        return _Selection(n_tot, a.ctypes.data_as(dptr), nra, ndec, z.ctypes.data_as(dptr), nz, 0, zlo, zhi)
+    ok = _Cosmology(100.0, 0.307, 0.0, 0.693, 300000.0, 0.6)
+    h = ctypes.cast(handle, ctypes.c_void_p)
+    assert f(None, ok, sel(), None) == 2                                      # no plan
+    assert f(h, None, sel(), None) == 2
+    assert f(h, ok, None, None) == 2
+    assert f(h, _Cosmology(100.0, 0.3, 0.0, -2.0, 3e5, 1.0), sel(), None) == 1
+    assert f(h, ok, _Selection(1e5, None, 4, 3, pz.ctypes.data_as(dptr), 5, 0, 0.1, 0.5), None) == 2
+    for bad in (sel(nra=0), sel(nz=0), sel(n_tot=float("nan")), sel(n_tot=-1.0), sel(zlo=-0.1),
+                sel(zhi=0.1), sel(a=np.full((3, 4), -0.1)), sel(z=np.array([1.0, 1.0, np.inf, 1.0, 1.0])),
+                sel(nra=1 << 14, ndec=1 << 13)):
+        assert f(h, ok, bad, None) == 1
+
+
 def test_survey_workspace_fits(lib):
     # 512^3, 16 shells, orders <= 3.  Mixed (split-TF32, fused pass, no bank):
     # counts + field + spectrum + 16 scratch spectra + kernel octants + one field
