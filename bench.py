@@ -57,6 +57,11 @@ def _args():
                     help="time ck_set_randoms_diagonal + ck_compute_diagonal (Eq. 14, the (s, .., s) entries "
                          "only) instead of ck_set_randoms + ck_compute; "
                          "no e2e, plain-form or CPU legs")
+    ap.add_argument("--factorised", action="store_true",
+                    help="build the randoms field with ck_set_randoms_factorised (Eq. 7) from a CMASS-like "
+                         "selection (P_ang uniform on dec >= 30 deg, P_z uniform on 0.43 <= z < 0.70, the "
+                         "survey mask's footprint) instead of gridding the random catalog; "
+                         "no e2e, plain-form or CPU legs")
     return ap.parse_args()
 
 
@@ -275,7 +280,15 @@ def run_gb300(args):
     outs["dropped"] = torch.zeros(2, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # the factorised selection: one-degree sky cells, 27 redshift bins
+    sel_pa = np.zeros((180, 360))
+    sel_pa[120:, :] = 1.0 / (2.0 * math.pi * (1.0 - math.sin(math.radians(30.0))))  # per sr over dec >= 30
+    sel_pz = np.full(27, 1.0 / 0.27)
+
     def step():
+        if args.factorised:
+            plan.set_randoms_factorised(float(d.n), sel_pa, sel_pz, 0.43, 0.70, z_max=0.75)
+            return plan.compute(dx, dy, dz, orders=orders, out="device", outputs=outs)
         if args.diagonal:
             plan.set_randoms_diagonal(rx, ry, rz)
             return plan.compute_diagonal(dx, dy, dz, orders=orders, out="device")
@@ -443,7 +456,9 @@ def run_gb300(args):
                    "shells": ns, "width": w["width"], "orders": list(orders), "n_data": d.n, "n_randoms": r.n,
                    "precision": precision,
                    "step": ("ck_set_randoms + ck_compute_diagonal (both fields, every shell; Eq. 14 only)"
-                            if args.diagonal else "ck_set_randoms + ck_compute (both fields, every shell)"),
+                            if args.diagonal else
+                            "ck_set_randoms_factorised (Eq. 7, CMASS-like selection) + ck_compute"
+                            if args.factorised else "ck_set_randoms + ck_compute (both fields, every shell)"),
                    "l2": "no flush: inputs and intermediates far larger than L2 (16 scratch spectra, 8.7 GB)"},
         "forms": forms,
         "roofline": roofline,
@@ -569,7 +584,7 @@ def run_reference(args):
 
 def main():
     args = _args()
-    if args.diagonal:
+    if args.diagonal or args.factorised:
         args.no_e2e = args.no_cpu_baseline = args.no_plain = True
     if args.impl == "reference":
         run_reference(args)

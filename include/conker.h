@@ -252,9 +252,13 @@ typedef struct ck_selection {
  *   R = N_tot P_ang(ra, dec) P_z(z) (dz/dr) g^3 / r^2,  dz/dr = H0 E(z) / c,
  * the cell's expected count (g^3 over the spherical volume element
  * r^2 dr dOmega, dr = dz c / (H0 E)), and R = 0 where z is outside
- * [z_lo, z_hi), r = 0 or r > r(z_max).  The cells are stored as float32
- * (ck_get_grids returns their bits, as for weighted fields), the field's
- * total is their FP64 sum in a fixed order (the same on every run), and
+ * [z_lo, z_hi), r = 0 or r > r(z_max).  Every bin decision (and r against
+ * r(z_max)) is that of an FP64 evaluation: cells clear of every edge by a
+ * margin above the float32 error bound are evaluated in float32 (within
+ * 8e-7 relative of the FP64 value), the others in FP64.  The cells are
+ * stored as float32 (ck_get_grids returns their bits, as for weighted
+ * fields), the field's total is their FP64 sum in a fixed order (the same
+ * on every run), and
  * alpha = (data total) / (that total) as for any randoms field, so the xi
  * do not depend on N_tot.  Then the denominators of every order, as
  * ck_set_randoms.  Errors: CK_ERR_BAD_POINTER for NULL arguments or device
@@ -385,10 +389,12 @@ ck_status ck_contract_static(const float* w0, const float* bank, int64_t bank_st
  * algorithmic bytes that launch must move (inputs read once + outputs written
  * once).  ck_profile_enable resets the accumulators; ck_profile_read
  * synchronises each recorded event and returns the totals. */
-/* Stages 0..12: grid_points, prepare_field, fft_x_r2c, fft_y_fwd, fft_z_fwd,
+/* Stages 0..13: grid_points, prepare_field, fft_x_r2c, fft_y_fwd, fft_z_fwd,
  * fft_z_inv_mul, fft_y_inv, fft_x_c2r, contract, reduce, finalize,
- * x_c2r_contract (the inverse x pass fused with the order-2/3 sums), other. */
-#define CK_STAGES 13
+ * x_c2r_contract (the inverse x pass fused with the order-2/3 sums), other,
+ * selection_field (the factorised randoms of Eq. 7; bytes = the cells
+ * written). */
+#define CK_STAGES 14
 typedef struct ck_stage_times {
   double ms[CK_STAGES];       /* summed event time of the stage's launches   */
   int64_t launches[CK_STAGES];

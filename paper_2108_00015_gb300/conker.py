@@ -68,7 +68,7 @@ class _Info(ctypes.Structure):
                 ("fused", ctypes.c_int32), ("fft_n", ctypes.c_int32 * 3)]
 
 
-CK_STAGES = 13
+CK_STAGES = 14
 
 
 class _StageTimes(ctypes.Structure):

@@ -40,7 +40,8 @@ namespace {
 constexpr size_t kProfPool = 16384;
 const char* kStageNames[CK_STAGES] = {"grid_points", "prepare_field", "fft_x_r2c", "fft_y_fwd",
                                       "fft_z_fwd", "fft_z_inv_mul", "fft_y_inv", "fft_x_c2r",
-                                      "contract", "reduce", "finalize", "x_c2r_contract", "other"};
+                                      "contract", "reduce", "finalize", "x_c2r_contract", "other",
+                                      "selection_field"};
 
 void prof_collect(ck::Plan& p) {
   ck::Profiler& f = p.prof;

@@ -97,7 +97,7 @@ struct ContractPlan {
 // Per-stage event timing (ck_profile_enable / ck_profile_read).
 enum Stage {
   ST_GRID = 0, ST_PREP, ST_FFT_X_R2C, ST_FFT_Y_FWD, ST_FFT_Z_FWD, ST_FFT_Z_INV_MUL, ST_FFT_Y_INV,
-  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_X_C2R_CONTRACT, ST_OTHER
+  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_X_C2R_CONTRACT, ST_OTHER, ST_SELECTION
 };
 
 struct Profiler {

@@ -13,15 +13,25 @@
 //    coordinates, which the gridding drops and counts.
 // With SK_NT = 4096 the interpolation error is below 1e-12 of r for
 // z_max <= 10, far below float32 rounding.
-// The factorised randoms of Eq. 7 use the same table the other way round:
-//  * factorised_randoms_kernel: per cell of the plan's box, z(r) by a binary
-//    search of the nodes and Newton steps on the Hermite interpolant, then
-//    R = N_tot P_ang(ra, dec) P_z(z) (dz/dr) g^3 / r^2 in FP64, stored as
-//    float32; the cell centre, r and the angle bins are evaluated in the
-//    same operation order as a plain FP64 evaluation (no contraction), so
-//    that the bin decisions are those of such an evaluation;
-//  * factorised_total_kernel: the per-block FP64 partial sums added in
-//    block order (the same total from run to run).
+// The factorised randoms of Eq. 7 use the same table the other way round,
+// R = N_tot P_ang(ra, dec) P_z(z) (dz/dr) g^3 / r^2 per cell of the box.
+// FP64 runs at a small fraction of the float32 rate on this GPU, so:
+//  * factorised_tables_kernel: z(r) and dz/dr on FR_NR + 1 nodes in r (z by
+//    bisection of the distance table and Newton steps on its Hermite
+//    interpolant, FP64), the cell centres per axis, N_tot g^3 P_ang and P_z,
+//    all rounded to float32;
+//  * factorised_fast_kernel: per cell in float32 (z and dz/dr by linear
+//    interpolation in r, the angles by atan2f); a cell whose r, z or angle
+//    lies within a margin of a decision edge (r(z_max), z_lo, z_hi, a bin
+//    edge) larger than the float32 error bound is queued instead;
+//  * factorised_slow_kernel: the queued cells by the FP64 path
+//    (cell_value_fp64), whose decisions follow a plain FP64 evaluation's
+//    operation order, so every bin decision is the FP64 one;
+//  * factorised_reduce_kernel + factorised_total_kernel: the field's total,
+//    nonzero cells and bounding box from the stored cells, per block in a
+//    fixed order, then the blocks in order (the same total every run).
+// Values: float32 cells within 13 float32 roundings (8e-7 relative) of the
+// FP64 definition; FP64-path cells within one rounding.
 #include <math.h>
 
 #include <limits.h>
@@ -96,13 +106,47 @@ __global__ void sky_table_kernel(Cosmo C, GaussLegendre g, double* __restrict__ 
 }
 
 // r[k] = c / H0 * (seg[0] + .. + seg[k - 1]), added in order by one thread
-__global__ void sky_scan_kernel(Cosmo C, const double* __restrict__ seg, double* __restrict__ r) {
-  double acc = 0.0;
-  r[0] = 0.0;
-  for (int k = 0; k < SK_NT; ++k) {
-    acc += seg[k];
-    r[k + 1] = C.dh * acc;
+// r[k] = c / H0 * (seg[0] + .. + seg[k - 1]) by one block: each thread adds
+// its SK_NT / 1024 segments in order, then shuffle scans within and across
+// warps (a fixed order of additions: the same table from run to run).
+constexpr int SK_SCAN = 1024;
+static_assert(SK_NT % SK_SCAN == 0, "scan block");
+__global__ void __launch_bounds__(SK_SCAN) sky_scan_kernel(Cosmo C, const double* __restrict__ seg,
+                                                           double* __restrict__ r) {
+  constexpr int PER = SK_NT / SK_SCAN;
+  __shared__ double wtot[SK_SCAN / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  double v[PER];
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    s += seg[t * PER + j];
+    v[j] = s;
   }
+  double x = s;  // inclusive scan over the warp
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) wtot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    double y = wtot[lane];
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double q = __shfl_up_sync(0xFFFFFFFFu, y, off);
+      if (lane >= off) y += q;
+    }
+    wtot[lane] = y;  // inclusive over warps
+  }
+  __syncthreads();
+  double before = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+  if (lane == 0) before = 0.0;
+  if (w > 0) before += wtot[w - 1];
+  if (t == 0) r[0] = 0.0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) r[t * PER + j + 1] = C.dh * (before + v[j]);
 }
 
 struct Selection {
@@ -145,51 +189,217 @@ __device__ __forceinline__ double z_of_r(const Cosmo& C, const double* __restric
 }
 
 constexpr int FR_THREADS = 256;
+constexpr int FR_NR = 8192;  // intervals of the z(r), dz/dr tables on [0, r(z_max)]
 
-__global__ void __launch_bounds__(FR_THREADS) factorised_randoms_kernel(
-    Cosmo C, const double* __restrict__ r, const double* __restrict__ dr, Selection S, Box B,
-    uint32_t* __restrict__ cells, double* __restrict__ part, DevState* st) {
+// Eq. 7 at one cell in FP64: the exact path.  Every decision (r <= r(z_max),
+// the redshift, right-ascension and declination bins) and the value follow
+// the operation order of a plain FP64 evaluation.
+__device__ double cell_value_fp64(const Cosmo& C, const double* __restrict__ r, const double* __restrict__ dr,
+                                  const Selection& S, const Box& B, int ix, int iy, int iz) {
   const double kDeg = 180.0 / M_PI;
-  const double rmax = __ldg(r + SK_NT);
-  const int64_t nbox = (int64_t)B.n[0] * B.n[1] * B.n[2];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  double sum = 0.0;
-  unsigned long long kept = 0;
-  int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbox; i += stride) {
+  const double X = __dadd_rn(B.o[0], __dmul_rn(ix + 0.5, B.g));
+  const double Y = __dadd_rn(B.o[1], __dmul_rn(iy + 0.5, B.g));
+  const double Z = __dadd_rn(B.o[2], __dmul_rn(iz + 0.5, B.g));
+  const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y)), __dmul_rn(Z, Z)));
+  if (!(rr > 0.0 && rr <= __ldg(r + SK_NT))) return 0.0;
+  const double z = z_of_r(C, r, dr, rr);
+  if (!(z >= S.zlo && z < S.zhi)) return 0.0;
+  double ra = fmod(__dmul_rn(atan2(Y, X), kDeg), 360.0);
+  if (ra < 0.0) ra += 360.0;
+  const double dec = __dmul_rn(asin(__ddiv_rn(Z, rr)), kDeg);
+  // bins (truncation toward zero; clamped into the tables)
+  const int ia = max(0, min((int)__dmul_rn(__ddiv_rn(ra, 360.0), (double)S.nra), S.nra - 1));
+  const int id = max(0, min((int)__dmul_rn(__ddiv_rn(__dadd_rn(dec, 90.0), 180.0), (double)S.ndec), S.ndec - 1));
+  const int kz =
+      max(0, min((int)__dmul_rn(__ddiv_rn(__dsub_rn(z, S.zlo), __dsub_rn(S.zhi, S.zlo)), (double)S.nz), S.nz - 1));
+  const double a = 1.0 + z;
+  const double dzdr = S.h0 * sqrt(C.om * a * a * a + C.ok * a * a + C.ol) / S.c;
+  return S.ntot * __ldg(S.pang + (int64_t)id * S.nra + ia) * __ldg(S.pz + kz) * dzdr * B.g3 / (rr * rr);
+}
+
+// Float32 tables of the fast path (built by factorised_tables_kernel).
+struct FastTabs {
+  const float* zr;   // [FR_NR + 1] z at r_k = k r(z_max) / FR_NR
+  const float* dzr;  // [FR_NR + 1] dz/dr = H0 E(z) / c at r_k
+  const float* A;    // [n_dec * n_ra] N_tot g^3 P_ang
+  const float* pz;   // [n_z] P_z
+  const float* ctr[3];  // cell centres per axis, FP64 values rounded to float32
+  float ra_scale, dec_scale, z_scale;  // n_ra / 2 pi, n_dec / pi, n_z / (z_hi - z_lo)
+  float zlo, zhi, dz_bin;              // z_hi - z_lo over n_z
+  float mz;                            // redshift margin of the fast decisions
+};
+
+// Margins of the float32 decisions, about three times the float32 error
+// bounds (each coordinate within 2^-24 relative of its FP64 value): r within
+// 2.7e-7 relative (squares, two fused adds, the square root, r(z_max)'s
+// rounding); the angles within 1.6e-6 rad (atan2f within 3 ulp, input
+// rounding 2.4e-7 rad, the scale and its product, the wrap by n_ra); z
+// within 9e-7 z_max (the r and scale errors times r z'/z <= 1.6, table
+// and interpolation rounding, the bin scaling; linear interpolation on
+// FR_NR intervals adds < 1e-8).  A cell closer than its margin to a
+// decision edge takes the FP64 path.
+constexpr float FR_MR = 2e-6f;    // relative, r against r(z_max) (error bound 2.7e-7)
+constexpr float FR_MANG = 5e-6f;  // radians (error bound 1.6e-6)
+// (the redshift margin, 3e-6 z_max against a bound of 9e-7 z_max, is FastTabs::mz)
+
+__global__ void factorised_tables_kernel(Cosmo C, const double* __restrict__ r, const double* __restrict__ dr,
+                                         Selection S, Box B, double h0, double c, float* __restrict__ zr,
+                                         float* __restrict__ dzr, float* __restrict__ A, float* __restrict__ pzf,
+                                         float* __restrict__ cx, float* __restrict__ cy, float* __restrict__ cz) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  const double rmax = r[SK_NT];
+  for (int k = t; k <= FR_NR; k += stride) {
+    const double rk = rmax * k / FR_NR;
+    const double z = k == 0 ? 0.0 : (k == FR_NR ? C.zmax : z_of_r(C, r, dr, rk));
+    const double a = 1.0 + z;
+    zr[k] = (float)z;
+    dzr[k] = (float)(h0 * sqrt(C.om * a * a * a + C.ok * a * a + C.ol) / c);
+  }
+  const int na = S.nra * S.ndec;
+  for (int k = t; k < na; k += stride) A[k] = (float)(S.ntot * B.g3 * S.pang[k]);
+  for (int k = t; k < S.nz; k += stride) pzf[k] = (float)S.pz[k];
+  for (int k = t; k < B.n[0]; k += stride) cx[k] = (float)__dadd_rn(B.o[0], __dmul_rn(k + 0.5, B.g));
+  for (int k = t; k < B.n[1]; k += stride) cy[k] = (float)__dadd_rn(B.o[1], __dmul_rn(k + 0.5, B.g));
+  for (int k = t; k < B.n[2]; k += stride) cz[k] = (float)__dadd_rn(B.o[2], __dmul_rn(k + 0.5, B.g));
+}
+
+__device__ __forceinline__ bool near_int(float t, float tol) {
+  const float f = t - floorf(t);
+  return fminf(f, 1.0f - f) <= tol;
+}
+
+// Per cell of the box: Eq. 7 in float32 where every decision is clear of
+// its edge by the margins above; otherwise the cell goes to the FP64 queue
+// (or, when the queue is full, the FP64 path in place).
+__global__ void __launch_bounds__(FR_THREADS) factorised_fast_kernel(
+    Cosmo C, const double* __restrict__ r, const double* __restrict__ dr, Selection S, Box B, FastTabs T,
+    uint32_t* __restrict__ cells, uint32_t* __restrict__ queue, unsigned int* __restrict__ qn, unsigned int qcap) {
+  const float half_pi = 1.57079632679489661923f;
+  const double rmax_d = __ldg(r + SK_NT);
+  const float rmax = (float)rmax_d, inv_h = (float)(FR_NR / rmax_d);
+  // one warp per row of cells (iy, iz), lanes along x
+  const int lane = threadIdx.x & 31;
+  const int64_t nrows = (int64_t)B.n[1] * B.n[2];
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += wstride) {
+    const int iy = (int)(row % B.n[1]);
+    const int iz = (int)(row / B.n[1]);
+    const float Y = __ldg(T.ctr[1] + iy), Z = __ldg(T.ctr[2] + iz);
+    uint32_t* __restrict__ crow = cells + ((int64_t)iz * B.dim[1] + iy) * B.dim[0];
+    for (int ix = lane; ix < B.n[0]; ix += 32) {
+      const int64_t i = row * B.n[0] + ix;
+      const float X = __ldg(T.ctr[0] + ix);
+      const float rho2 = fmaf(X, X, Y * Y);
+      const float r2 = fmaf(Z, Z, rho2);
+      const float rf = sqrtf(r2);
+      float v = 0.0f;
+      bool slow = false;
+      if (r2 == 0.0f || fabsf(rf - rmax) <= FR_MR * rmax) {
+        slow = true;
+      } else if (rf < rmax) {
+        float u = rf * inv_h;
+        const int k = min((int)u, FR_NR - 1);
+        u -= (float)k;
+        const float z0 = __ldg(T.zr + k), z1 = __ldg(T.zr + k + 1);
+        const float zf = fmaf(u, z1 - z0, z0);
+        if (fabsf(zf - T.zlo) <= T.mz || fabsf(zf - T.zhi) <= T.mz) {
+          slow = true;
+        } else if (zf > T.zlo && zf < T.zhi) {
+          const float tz = (zf - T.zlo) * T.z_scale;
+          float ta = atan2f(Y, X) * T.ra_scale;
+          if (ta < 0.0f) ta += (float)S.nra;
+          const float td = (atan2f(Z, sqrtf(rho2)) + half_pi) * T.dec_scale;
+          if (near_int(tz, T.mz / T.dz_bin) || near_int(ta, FR_MANG * T.ra_scale) ||
+              near_int(td, FR_MANG * T.dec_scale)) {
+            slow = true;
+          } else {
+            const int kz = max(0, min((int)tz, S.nz - 1));
+            const int ia = max(0, min((int)ta, S.nra - 1));
+            const int id = max(0, min((int)td, S.ndec - 1));
+            const float d0 = __ldg(T.dzr + k), d1 = __ldg(T.dzr + k + 1);
+            const float dzdr = fmaf(u, d1 - d0, d0);
+            v = __ldg(T.A + id * S.nra + ia) * __ldg(T.pz + kz) * dzdr * __frcp_rn(r2);
+          }
+        }
+      }
+      if (slow) {
+        const unsigned int q = atomicAdd(qn, 1u);
+        if (q < qcap) {
+          queue[q] = (uint32_t)i;
+          continue;  // the FP64 kernel writes this cell
+        }
+        v = (float)cell_value_fp64(C, r, dr, S, B, ix, iy, iz);
+      }
+      crow[ix] = __float_as_uint(v);
+    }
+  }
+}
+
+// The queued cells in FP64, in full warps.
+__global__ void __launch_bounds__(FR_THREADS) factorised_slow_kernel(
+    Cosmo C, const double* __restrict__ r, const double* __restrict__ dr, Selection S, Box B,
+    uint32_t* __restrict__ cells, const uint32_t* __restrict__ queue, const unsigned int* __restrict__ qn,
+    unsigned int qcap) {
+  const unsigned int n = min(*qn, qcap);
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int64_t i = queue[j];
     const int ix = (int)(i % B.n[0]);
     const int64_t t = i / B.n[0];
     const int iy = (int)(t % B.n[1]);
     const int iz = (int)(t / B.n[1]);
-    const double X = __dadd_rn(B.o[0], __dmul_rn(ix + 0.5, B.g));
-    const double Y = __dadd_rn(B.o[1], __dmul_rn(iy + 0.5, B.g));
-    const double Z = __dadd_rn(B.o[2], __dmul_rn(iz + 0.5, B.g));
-    const double rr = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(X, X), __dmul_rn(Y, Y)), __dmul_rn(Z, Z)));
-    double v = 0.0;
-    if (rr > 0.0 && rr <= rmax) {
-      const double z = z_of_r(C, r, dr, rr);
-      if (z >= S.zlo && z < S.zhi) {
-        double ra = fmod(__dmul_rn(atan2(Y, X), kDeg), 360.0);
-        if (ra < 0.0) ra += 360.0;
-        const double dec = __dmul_rn(asin(__ddiv_rn(Z, rr)), kDeg);
-        // bins (truncation toward zero; clamped into the tables)
-        const int ia = max(0, min((int)__dmul_rn(__ddiv_rn(ra, 360.0), (double)S.nra), S.nra - 1));
-        const int id =
-            max(0, min((int)__dmul_rn(__ddiv_rn(__dadd_rn(dec, 90.0), 180.0), (double)S.ndec), S.ndec - 1));
-        const int kz = max(
-            0, min((int)__dmul_rn(__ddiv_rn(__dsub_rn(z, S.zlo), __dsub_rn(S.zhi, S.zlo)), (double)S.nz), S.nz - 1));
-        const double a = 1.0 + z;
-        const double dzdr = S.h0 * sqrt(C.om * a * a * a + C.ok * a * a + C.ol) / S.c;
-        v = S.ntot * __ldg(S.pang + (int64_t)id * S.nra + ia) * __ldg(S.pz + kz) * dzdr * B.g3 / (rr * rr);
+    const float v = (float)cell_value_fp64(C, r, dr, S, B, ix, iy, iz);
+    cells[((int64_t)iz * B.dim[1] + iy) * B.dim[0] + ix] = __float_as_uint(v);
+  }
+}
+
+// The field's totals from its stored cells: per block the FP64 sum (a fixed
+// shuffle tree, then the warps in order), the nonzero cells and their
+// bounding box.
+__global__ void __launch_bounds__(FR_THREADS) factorised_reduce_kernel(Box B, const uint32_t* __restrict__ cells,
+                                                                      double* __restrict__ part, DevState* st) {
+  double sum = 0.0;
+  unsigned long long kept = 0;
+  int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
+  const int lane = threadIdx.x & 31;
+  const int64_t nrows = (int64_t)B.n[1] * B.n[2];
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const bool vec = (B.n[0] & 3) == 0 && (B.dim[0] & 3) == 0;  // rows start on 16-byte boundaries
+  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += wstride) {
+    const int iy = (int)(row % B.n[1]);
+    const int iz = (int)(row / B.n[1]);
+    const uint32_t* __restrict__ crow = cells + ((int64_t)iz * B.dim[1] + iy) * B.dim[0];
+    auto take = [&](float v, int ix) {
+      if (v != 0.0f) {
+        ++kept;
+        sum += (double)v;
+        bmin[0] = min(bmin[0], ix); bmax[0] = max(bmax[0], ix);
+        bmin[1] = min(bmin[1], iy); bmax[1] = max(bmax[1], iy);
+        bmin[2] = min(bmin[2], iz); bmax[2] = max(bmax[2], iz);
       }
-    }
-    cells[((int64_t)iz * B.dim[1] + iy) * B.dim[0] + ix] = __float_as_uint((float)v);
-    if (v != 0.0) {
-      ++kept;
-      sum += v;
-      bmin[0] = min(bmin[0], ix); bmax[0] = max(bmax[0], ix);
-      bmin[1] = min(bmin[1], iy); bmax[1] = max(bmax[1], iy);
-      bmin[2] = min(bmin[2], iz); bmax[2] = max(bmax[2], iz);
+    };
+    if (vec) {
+      // 16-byte loads, four in flight per lane
+      const float4* __restrict__ c4 = reinterpret_cast<const float4*>(crow);
+      const int nv = B.n[0] >> 2;
+      for (int b0 = 0; b0 < nv; b0 += 128) {
+        float4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = b0 + u * 32 + lane;
+          q[u] = j < nv ? __ldg(c4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int ix = 4 * (b0 + u * 32 + lane);
+          take(q[u].x, ix);
+          take(q[u].y, ix + 1);
+          take(q[u].z, ix + 2);
+          take(q[u].w, ix + 3);
+        }
+      }
+    } else {
+      for (int ix = lane; ix < B.n[0]; ix += 32) take(__uint_as_float(__ldg(crow + ix)), ix);
     }
   }
   // block reduction: a fixed shuffle tree, then the warps in order
@@ -232,11 +442,17 @@ __global__ void __launch_bounds__(FR_THREADS) factorised_randoms_kernel(
   }
 }
 
+// One warp: lane j adds blocks j, j + 32, .. in order, then a fixed xor tree.
 __global__ void factorised_total_kernel(const double* __restrict__ part, int nblocks, DevState* st) {
+  const int lane = threadIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[b];
-  st->fsum[1] = s;
-  st->weighted[1] = 2;
+  for (int b = lane; b < nblocks; b += 32) s += part[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if (lane == 0) {
+    st->fsum[1] = s;
+    st->weighted[1] = 2;
+  }
 }
 
 __global__ void sky_points_kernel(Cosmo C, const double* __restrict__ r, const double* __restrict__ dr,
@@ -298,7 +514,7 @@ void launch_table(const Cosmo& C, double* tab, cudaStream_t st) {
   double* r = seg + SK_NT;
   double* dr = r + SK_NT + 1;
   sky_table_kernel<<<(SK_NT + 1 + 255) / 256, 256, 0, st>>>(C, gauss_legendre(), seg, dr);
-  sky_scan_kernel<<<1, 1, 0, st>>>(C, seg, r);
+  sky_scan_kernel<<<1, SK_SCAN, 0, st>>>(C, seg, r);
 }
 
 int device_sms() {
@@ -334,24 +550,44 @@ ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck
   const Cosmo C = make_cosmo(cosmo);
   const int64_t na = (int64_t)sel->n_ra * sel->n_dec;
   const int64_t nbox = (int64_t)p.box_n[0] * p.box_n[1] * p.box_n[2];
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nbox + FR_THREADS - 1) / FR_THREADS,
-                                                                 (int64_t)device_sms() * 8));
-  // scratch: table | p_ang | p_z | per-block sums
+  const int sms = device_sms();
+  const int64_t nrows = (int64_t)p.box_n[1] * p.box_n[2];  // a warp per row of cells
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + FR_THREADS / 32 - 1) / (FR_THREADS / 32),
+                                                                 (int64_t)sms * 8));
+  // FP64 queue for cells near a decision edge (indices into the box)
+  const unsigned int qcap = nbox < ((int64_t)1 << 32) ? (unsigned int)std::min<int64_t>(nbox, (int64_t)1 << 22) : 0u;
+  // scratch: doubles (table seg | r | dr, p_ang, p_z, per-block sums), then
+  // floats (z(r), dz/dr, A, P_z, centres), then the queue and its counter
   const size_t nd = (size_t)(3 * SK_NT + 2) + (size_t)na + (size_t)sel->n_z + (size_t)blocks;
-  double* tab = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tab), nd * sizeof(double), st);
+  const size_t nf = 2 * (size_t)(FR_NR + 1) + (size_t)na + (size_t)sel->n_z + (size_t)p.box_n[0] + p.box_n[1] +
+                    p.box_n[2];
+  const size_t nf_pad = (nf + 3) / 4 * 4;
+  const size_t bytes = nd * 8 + nf_pad * 4 + ((size_t)qcap + 4) * 4;
+  unsigned char* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return CK_ERR_OOM;
   }
+  double* tab = reinterpret_cast<double*>(scratch);
   double* r = tab + SK_NT;
   double* dr = r + SK_NT + 1;
   double* pang = dr + SK_NT + 1;
   double* pz = pang + na;
   double* part = pz + sel->n_z;
+  float* zr = reinterpret_cast<float*>(scratch + nd * 8);
+  float* dzr = zr + FR_NR + 1;
+  float* A = dzr + FR_NR + 1;
+  float* pzf = A + na;
+  float* cx = pzf + sel->n_z;
+  float* cy = cx + p.box_n[0];
+  float* cz = cy + p.box_n[1];
+  uint32_t* queue = reinterpret_cast<uint32_t*>(scratch + nd * 8 + nf_pad * 4);
+  unsigned int* qn = queue + qcap;
   e = cudaMemcpyAsync(pang, sel->p_ang, (size_t)na * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(pz, sel->p_z, (size_t)sel->n_z * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, sizeof(unsigned int), st);
   if (e == cudaSuccess) {
     launch_table(C, tab, st);
     Selection S;
@@ -373,11 +609,35 @@ ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck
     }
     B.g = p.grid.cell;
     B.g3 = p.grid.cell * p.grid.cell * p.grid.cell;
-    factorised_randoms_kernel<<<blocks, FR_THREADS, 0, st>>>(C, r, dr, S, B, p.counts[1], part, p.dstate);
-    factorised_total_kernel<<<1, 1, 0, st>>>(part, blocks, p.dstate);
+    factorised_tables_kernel<<<64, 256, 0, st>>>(C, r, dr, S, B, cosmo->h0, cosmo->c, zr, dzr, A, pzf, cx, cy, cz);
+    // the scales of the float decisions (r(z_max) is read from the table on the device)
+    FastTabs T;
+    T.zr = zr;
+    T.dzr = dzr;
+    T.A = A;
+    T.pz = pzf;
+    T.ctr[0] = cx;
+    T.ctr[1] = cy;
+    T.ctr[2] = cz;
+    const double two_pi = 2.0 * M_PI;
+    T.ra_scale = (float)(sel->n_ra / two_pi);
+    T.dec_scale = (float)(sel->n_dec / M_PI);
+    T.z_scale = (float)(sel->n_z / (sel->z_hi - sel->z_lo));
+    T.zlo = (float)sel->z_lo;
+    T.zhi = (float)sel->z_hi;
+    T.dz_bin = (float)((sel->z_hi - sel->z_lo) / sel->n_z);
+    T.mz = (float)(3e-6 * cosmo->z_max);
+    ProfScope ps(p, ST_SELECTION, 8.0 * (double)nbox, st);
+    factorised_fast_kernel<<<blocks, FR_THREADS, 0, st>>>(C, r, dr, S, B, T, p.counts[1], queue, qn, qcap);
+    factorised_slow_kernel<<<sms * 4, FR_THREADS, 0, st>>>(C, r, dr, S, B, p.counts[1], queue, qn, qcap);
+    factorised_reduce_kernel<<<blocks, FR_THREADS, 0, st>>>(B, p.counts[1], part, p.dstate);
     e = cudaGetLastError();
   }
-  const cudaError_t f = cudaFreeAsync(tab, st);
+  if (e == cudaSuccess) {
+    factorised_total_kernel<<<1, 32, 0, st>>>(part, blocks, p.dstate);
+    e = cudaGetLastError();
+  }
+  const cudaError_t f = cudaFreeAsync(scratch, st);
   return cuda_status(e != cudaSuccess ? e : f);
 }
 

@@ -79,11 +79,13 @@ def _field(plan, g):
 
 
 def _close(got, want):
-    """float32 cells of FP64 values: within one rounding (2^-24 relative)
-    plus the FP64 paths' difference (the device's z(r) interpolation, 1e-12
-    of r), zeros exactly where the oracle has zeros."""
+    """float32 cells: within 1e-6 relative of the oracle's FP64 values (the
+    float32 evaluation's bound, 13 roundings of 2^-24 = 7.7e-7; cells near a
+    bin edge are evaluated in FP64, within one rounding), and zeros exactly
+    where the oracle has zeros (every bin decision is the FP64 one)."""
     assert np.array_equal(got == 0.0, want == 0.0), int(np.sum((got == 0.0) != (want == 0.0)))
-    assert np.all(np.abs(got - want) <= (2.0 ** -24 + 1e-11) * np.abs(want))
+    err = np.abs(got - want) / np.where(want != 0.0, np.abs(want), 1.0)
+    assert float(err.max()) <= 1e-6, float(err.max())
 
 
 def test_field_whole_box(torch):
@@ -93,6 +95,25 @@ def test_field_whole_box(torch):
     plan = _plan(g, (20.0, 30.0), 10.0, 2, "fp32")
     _set(plan, sel)
     _close(_field(plan, g), want)
+    plan.close()
+
+
+
+def test_field_on_bin_edges(torch):
+    """Cell centres on the planes X = 0, Y = 0, Z = 0 (right ascension on
+    its 0, 90, 180, 270 degree bin edges, declination 0 and the poles), the
+    observer's own cell, and fine bins (0.5 degree, 50 redshift bins): many
+    cells near an edge take the FP64 path; every decision must still be the
+    oracle's."""
+    g = GridSpec((25, 25, 25), (-150.0, -150.0, -150.0), 12.0, False)
+    pa, pz = _selection(9, 720, 360, 50, 0.01, 0.08, cut=False)
+    sel = _sel(pa, pz, 0.01, 0.08, 0.09)
+    want = O.factorised_randoms(g, **sel)
+    plan = _plan(g, (24.0, 36.0), 12.0, 2, "fp32")
+    _set(plan, sel)
+    got = _field(plan, g)
+    assert got[12, 12, 12] == 0.0 and want[12, 12, 12] == 0.0     # r = 0
+    _close(got, want)
     plan.close()
 
 
