@@ -263,7 +263,7 @@ typedef struct ck_selection {
  * do not depend on N_tot.  Then the denominators of every order, as
  * ck_set_randoms.  Errors: CK_ERR_BAD_POINTER for NULL arguments or device
  * tables; CK_ERR_ARG for a cosmology ck_sky_to_cartesian rejects, table
- * sizes < 1 or n_ra * n_dec > 2^26, non-finite or negative entries or
+ * sizes < 1 or > 2^20, n_ra * n_dec > 2^26, non-finite or negative entries or
  * N_tot, z_lo < 0 or z_hi <= z_lo; a field with no nonzero cell makes the
  * next ck_compute report CK_ERR_EMPTY_CATALOG.  On an argument error the
  * plan's previous randoms are kept.  Stream-ordered; scratch is a

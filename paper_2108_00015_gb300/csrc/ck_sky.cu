@@ -222,11 +222,14 @@ struct FastTabs {
   const float* zr;   // [FR_NR + 1] z at r_k = k r(z_max) / FR_NR
   const float* dzr;  // [FR_NR + 1] dz/dr = H0 E(z) / c at r_k
   const float* A;    // [n_dec * n_ra] N_tot g^3 P_ang
+  const float* rmax;  // [2] r(z_max) and FR_NR / r(z_max)
   const float* pz;   // [n_z] P_z
   const float* ctr[3];  // cell centres per axis, FP64 values rounded to float32
   float ra_scale, dec_scale, z_scale;  // n_ra / 2 pi, n_dec / pi, n_z / (z_hi - z_lo)
-  float zlo, zhi, dz_bin;              // z_hi - z_lo over n_z
+  float zlo, zhi;
   float mz;                            // redshift margin of the fast decisions
+  float tol_z, tol_ra, tol_dec;        // the margins in bin units
+  float nra_f;
 };
 
 // Margins of the float32 decisions, about three times the float32 error
@@ -238,6 +241,9 @@ struct FastTabs {
 // and interpolation rounding, the bin scaling; linear interpolation on
 // FR_NR intervals adds < 1e-8).  A cell closer than its margin to a
 // decision edge takes the FP64 path.
+// Cells left for the FP64 kernel hold this NaN pattern until it runs.
+constexpr uint32_t kSlowMark = 0x7FC0DEADu;
+
 constexpr float FR_MR = 2e-6f;    // relative, r against r(z_max) (error bound 2.7e-7)
 constexpr float FR_MANG = 5e-6f;  // radians (error bound 1.6e-6)
 // (the redshift margin, 3e-6 z_max against a bound of 9e-7 z_max, is FastTabs::mz)
@@ -245,10 +251,15 @@ constexpr float FR_MANG = 5e-6f;  // radians (error bound 1.6e-6)
 __global__ void factorised_tables_kernel(Cosmo C, const double* __restrict__ r, const double* __restrict__ dr,
                                          Selection S, Box B, double h0, double c, float* __restrict__ zr,
                                          float* __restrict__ dzr, float* __restrict__ A, float* __restrict__ pzf,
-                                         float* __restrict__ cx, float* __restrict__ cy, float* __restrict__ cz) {
+                                         float* __restrict__ cx, float* __restrict__ cy, float* __restrict__ cz,
+                                         float* __restrict__ rmax_f) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int stride = gridDim.x * blockDim.x;
   const double rmax = r[SK_NT];
+  if (t == 0) {
+    rmax_f[0] = (float)rmax;
+    rmax_f[1] = (float)(FR_NR / rmax);
+  }
   for (int k = t; k <= FR_NR; k += stride) {
     const double rk = rmax * k / FR_NR;
     const double z = k == 0 ? 0.0 : (k == FR_NR ? C.zmax : z_of_r(C, r, dr, rk));
@@ -264,9 +275,39 @@ __global__ void factorised_tables_kernel(Cosmo C, const double* __restrict__ r, 
   for (int k = t; k < B.n[2]; k += stride) cz[k] = (float)__dadd_rn(B.o[2], __dmul_rn(k + 0.5, B.g));
 }
 
-__device__ __forceinline__ bool near_int(float t, float tol) {
-  const float f = t - floorf(t);
-  return fminf(f, 1.0f - f) <= tol;
+// The rows (iy, iz) of warp w: w, w + W, w + 2W, ... with (iy, iz) advanced
+// by carries instead of a division per row (integer division converts
+// through floating point).
+struct RowWalk {
+  unsigned row, nrows, step;
+  int iy, iz, n1, sy, sz;  // step = sz n1 + sy
+  __device__ RowWalk(unsigned first, unsigned stride, int ny, int nz) : row(first), step(stride), n1(ny) {
+    nrows = (unsigned)ny * (unsigned)nz;
+    iy = (int)(first % (unsigned)ny);
+    iz = (int)(first / (unsigned)ny);
+    sy = (int)(stride % (unsigned)ny);
+    sz = (int)(stride / (unsigned)ny);
+  }
+  __device__ bool ok() const { return row < nrows; }
+  __device__ void next() {
+    row += step;
+    iy += sy;
+    iz += sz;
+    if (iy >= n1) {
+      iy -= n1;
+      ++iz;
+    }
+  }
+};
+
+// floor(t) for 0 <= t < 2^22 without a conversion instruction: t + 2^23
+// rounded down holds floor(t) in its low mantissa bits.  Also returns
+// whether t lies within tol of an integer (a bin edge).
+__device__ __forceinline__ int bin_of(float t, float tol, bool* near) {
+  const float b = __fadd_rd(t, 8388608.0f);
+  const float f = t - (b - 8388608.0f);
+  *near = fminf(f, 1.0f - f) <= tol;
+  return __float_as_int(b) - 0x4B000000;
 }
 
 // Per cell of the box: Eq. 7 in float32 where every decision is clear of
@@ -276,19 +317,18 @@ __global__ void __launch_bounds__(FR_THREADS) factorised_fast_kernel(
     Cosmo C, const double* __restrict__ r, const double* __restrict__ dr, Selection S, Box B, FastTabs T,
     uint32_t* __restrict__ cells, uint32_t* __restrict__ queue, unsigned int* __restrict__ qn, unsigned int qcap) {
   const float half_pi = 1.57079632679489661923f;
-  const double rmax_d = __ldg(r + SK_NT);
-  const float rmax = (float)rmax_d, inv_h = (float)(FR_NR / rmax_d);
-  // one warp per row of cells (iy, iz), lanes along x
-  const int lane = threadIdx.x & 31;
-  const int64_t nrows = (int64_t)B.n[1] * B.n[2];
-  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += wstride) {
-    const int iy = (int)(row % B.n[1]);
-    const int iz = (int)(row / B.n[1]);
+  const float rmax = __ldg(T.rmax), inv_h = __ldg(T.rmax + 1);
+  // one warp per row of cells (iy, iz), lanes along x; 32-bit index
+  // arithmetic (box axes <= 512; a 64-bit division would use the FP64 pipe)
+  const unsigned lane = threadIdx.x & 31u;
+  for (RowWalk w(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), gridDim.x * (blockDim.x >> 5), B.n[1], B.n[2]);
+       w.ok(); w.next()) {
+    const unsigned row = w.row;
+    const int iy = w.iy, iz = w.iz;
     const float Y = __ldg(T.ctr[1] + iy), Z = __ldg(T.ctr[2] + iz);
     uint32_t* __restrict__ crow = cells + ((int64_t)iz * B.dim[1] + iy) * B.dim[0];
     for (int ix = lane; ix < B.n[0]; ix += 32) {
-      const int64_t i = row * B.n[0] + ix;
+      const unsigned i = row * (unsigned)B.n[0] + (unsigned)ix;
       const float X = __ldg(T.ctr[0] + ix);
       const float rho2 = fmaf(X, X, Y * Y);
       const float r2 = fmaf(Z, Z, rho2);
@@ -298,56 +338,71 @@ __global__ void __launch_bounds__(FR_THREADS) factorised_fast_kernel(
       if (r2 == 0.0f || fabsf(rf - rmax) <= FR_MR * rmax) {
         slow = true;
       } else if (rf < rmax) {
+        // rf < rmax (1 - FR_MR): u < FR_NR
         float u = rf * inv_h;
-        const int k = min((int)u, FR_NR - 1);
-        u -= (float)k;
+        bool unused;
+        const int k = min(bin_of(u, 0.0f, &unused), FR_NR - 1);
+        u -= __int_as_float(0x4B000000 + k) - 8388608.0f;
         const float z0 = __ldg(T.zr + k), z1 = __ldg(T.zr + k + 1);
         const float zf = fmaf(u, z1 - z0, z0);
         if (fabsf(zf - T.zlo) <= T.mz || fabsf(zf - T.zhi) <= T.mz) {
           slow = true;
         } else if (zf > T.zlo && zf < T.zhi) {
-          const float tz = (zf - T.zlo) * T.z_scale;
+          // bin coordinates, clamped at 0 (the lower edge of bin 0 decides nothing)
+          const float tz = fmaxf((zf - T.zlo) * T.z_scale, 0.0f);
           float ta = atan2f(Y, X) * T.ra_scale;
-          if (ta < 0.0f) ta += (float)S.nra;
-          const float td = (atan2f(Z, sqrtf(rho2)) + half_pi) * T.dec_scale;
-          if (near_int(tz, T.mz / T.dz_bin) || near_int(ta, FR_MANG * T.ra_scale) ||
-              near_int(td, FR_MANG * T.dec_scale)) {
+          if (ta < 0.0f) ta += T.nra_f;
+          const float td = fmaxf((atan2f(Z, sqrtf(rho2)) + half_pi) * T.dec_scale, 0.0f);
+          bool nz_, na_, nd_;
+          const int kz = min(bin_of(tz, T.tol_z, &nz_), S.nz - 1);
+          const int ia = min(bin_of(fmaxf(ta, 0.0f), T.tol_ra, &na_), S.nra - 1);
+          const int id = min(bin_of(td, T.tol_dec, &nd_), S.ndec - 1);
+          if (nz_ || na_ || nd_) {
             slow = true;
           } else {
-            const int kz = max(0, min((int)tz, S.nz - 1));
-            const int ia = max(0, min((int)ta, S.nra - 1));
-            const int id = max(0, min((int)td, S.ndec - 1));
             const float d0 = __ldg(T.dzr + k), d1 = __ldg(T.dzr + k + 1);
             const float dzdr = fmaf(u, d1 - d0, d0);
             v = __ldg(T.A + id * S.nra + ia) * __ldg(T.pz + kz) * dzdr * __frcp_rn(r2);
           }
         }
       }
+      uint32_t out = __float_as_uint(v);
       if (slow) {
+        // the FP64 kernel writes this cell: from the queue, or (queue full)
+        // by finding the mark
         const unsigned int q = atomicAdd(qn, 1u);
-        if (q < qcap) {
-          queue[q] = (uint32_t)i;
-          continue;  // the FP64 kernel writes this cell
-        }
-        v = (float)cell_value_fp64(C, r, dr, S, B, ix, iy, iz);
+        if (q < qcap) queue[q] = i;
+        out = kSlowMark;
       }
-      crow[ix] = __float_as_uint(v);
+      crow[ix] = out;
     }
   }
 }
 
-// The queued cells in FP64, in full warps.
+// The queued cells in FP64, in full warps; if the queue overflowed, also
+// every cell still holding the mark.
 __global__ void __launch_bounds__(FR_THREADS) factorised_slow_kernel(
     Cosmo C, const double* __restrict__ r, const double* __restrict__ dr, Selection S, Box B,
     uint32_t* __restrict__ cells, const uint32_t* __restrict__ queue, const unsigned int* __restrict__ qn,
     unsigned int qcap) {
-  const unsigned int n = min(*qn, qcap);
+  const unsigned int total = *qn;
+  if (total > qcap) {
+    for (RowWalk w(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), gridDim.x * (blockDim.x >> 5), B.n[1],
+                   B.n[2]);
+         w.ok(); w.next()) {
+      uint32_t* __restrict__ crow = cells + ((int64_t)w.iz * B.dim[1] + w.iy) * B.dim[0];
+      for (int ix = threadIdx.x & 31; ix < B.n[0]; ix += 32)
+        if (crow[ix] == kSlowMark) crow[ix] = __float_as_uint((float)cell_value_fp64(C, r, dr, S, B, ix, w.iy, w.iz));
+    }
+    return;  // the queued cells hold the mark too
+  }
+  const unsigned int n = total;
   for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const int64_t i = queue[j];
-    const int ix = (int)(i % B.n[0]);
-    const int64_t t = i / B.n[0];
-    const int iy = (int)(t % B.n[1]);
-    const int iz = (int)(t / B.n[1]);
+    const unsigned i = queue[j];
+    const int ix = (int)(i % (unsigned)B.n[0]);
+    const unsigned t = i / (unsigned)B.n[0];
+    const int iy = (int)(t % (unsigned)B.n[1]);
+    const int iz = (int)(t / (unsigned)B.n[1]);
     const float v = (float)cell_value_fp64(C, r, dr, S, B, ix, iy, iz);
     cells[((int64_t)iz * B.dim[1] + iy) * B.dim[0] + ix] = __float_as_uint(v);
   }
@@ -362,17 +417,21 @@ __global__ void __launch_bounds__(FR_THREADS) factorised_reduce_kernel(Box B, co
   unsigned long long kept = 0;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
   const int lane = threadIdx.x & 31;
-  const int64_t nrows = (int64_t)B.n[1] * B.n[2];
-  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
   const bool vec = (B.n[0] & 3) == 0 && (B.dim[0] & 3) == 0;  // rows start on 16-byte boundaries
-  for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < nrows; row += wstride) {
-    const int iy = (int)(row % B.n[1]);
-    const int iz = (int)(row / B.n[1]);
+  // per lane: a compensated float32 sum (TwoSum: hi + lo carries the
+  // rounding error of every addition), converted to FP64 once at the end
+  float hi = 0.0f, lo = 0.0f;
+  for (RowWalk w(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), gridDim.x * (blockDim.x >> 5), B.n[1], B.n[2]);
+       w.ok(); w.next()) {
+    const int iy = w.iy, iz = w.iz;
     const uint32_t* __restrict__ crow = cells + ((int64_t)iz * B.dim[1] + iy) * B.dim[0];
     auto take = [&](float v, int ix) {
       if (v != 0.0f) {
         ++kept;
-        sum += (double)v;
+        const float s2 = hi + v;
+        const float bp = s2 - hi;
+        lo += (hi - (s2 - bp)) + (v - bp);
+        hi = s2;
         bmin[0] = min(bmin[0], ix); bmax[0] = max(bmax[0], ix);
         bmin[1] = min(bmin[1], iy); bmax[1] = max(bmax[1], iy);
         bmin[2] = min(bmin[2], iz); bmax[2] = max(bmax[2], iz);
@@ -402,6 +461,7 @@ __global__ void __launch_bounds__(FR_THREADS) factorised_reduce_kernel(Box B, co
       for (int ix = lane; ix < B.n[0]; ix += 32) take(__uint_as_float(__ldg(crow + ix)), ix);
     }
   }
+  sum = (double)hi + (double)lo;
   // block reduction: a fixed shuffle tree, then the warps in order
   for (int off = 16; off > 0; off >>= 1) {
     sum += __shfl_down_sync(0xFFFFFFFFu, sum, off);
@@ -533,6 +593,7 @@ ck_status check_factorised(const ck_cosmology* cosmo, const ck_selection* sel) {
   // the tables are read here on the host: device memory is refused first
   if (is_device_ptr(sel->p_ang) || is_device_ptr(sel->p_z)) return CK_ERR_BAD_POINTER;
   if (sel->n_ra < 1 || sel->n_dec < 1 || sel->n_z < 1) return CK_ERR_ARG;
+  if (sel->n_ra > (1 << 20) || sel->n_dec > (1 << 20) || sel->n_z > (1 << 20)) return CK_ERR_ARG;
   if ((int64_t)sel->n_ra * sel->n_dec > ((int64_t)1 << 26)) return CK_ERR_ARG;
   if (!isfinite(sel->n_tot) || !(sel->n_tot >= 0.0)) return CK_ERR_ARG;
   if (!isfinite(sel->z_lo) || !isfinite(sel->z_hi) || !(sel->z_lo >= 0.0) || !(sel->z_hi > sel->z_lo))
@@ -555,12 +616,14 @@ ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + FR_THREADS / 32 - 1) / (FR_THREADS / 32),
                                                                  (int64_t)sms * 8));
   // FP64 queue for cells near a decision edge (indices into the box)
-  const unsigned int qcap = nbox < ((int64_t)1 << 32) ? (unsigned int)std::min<int64_t>(nbox, (int64_t)1 << 22) : 0u;
+  // (1/64 of the box: near-edge cells are a small fraction on real selections;
+  // beyond it the FP64 kernel finds the marked cells by a scan instead)
+  const unsigned int qcap = (unsigned int)std::min<int64_t>(nbox / 64 + 64, (int64_t)1 << 22);
   // scratch: doubles (table seg | r | dr, p_ang, p_z, per-block sums), then
   // floats (z(r), dz/dr, A, P_z, centres), then the queue and its counter
   const size_t nd = (size_t)(3 * SK_NT + 2) + (size_t)na + (size_t)sel->n_z + (size_t)blocks;
   const size_t nf = 2 * (size_t)(FR_NR + 1) + (size_t)na + (size_t)sel->n_z + (size_t)p.box_n[0] + p.box_n[1] +
-                    p.box_n[2];
+                    p.box_n[2] + 2;
   const size_t nf_pad = (nf + 3) / 4 * 4;
   const size_t bytes = nd * 8 + nf_pad * 4 + ((size_t)qcap + 4) * 4;
   unsigned char* scratch = nullptr;
@@ -582,6 +645,7 @@ ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck
   float* cx = pzf + sel->n_z;
   float* cy = cx + p.box_n[0];
   float* cz = cy + p.box_n[1];
+  float* rmf = cz + p.box_n[2];
   uint32_t* queue = reinterpret_cast<uint32_t*>(scratch + nd * 8 + nf_pad * 4);
   unsigned int* qn = queue + qcap;
   e = cudaMemcpyAsync(pang, sel->p_ang, (size_t)na * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -609,12 +673,13 @@ ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck
     }
     B.g = p.grid.cell;
     B.g3 = p.grid.cell * p.grid.cell * p.grid.cell;
-    factorised_tables_kernel<<<64, 256, 0, st>>>(C, r, dr, S, B, cosmo->h0, cosmo->c, zr, dzr, A, pzf, cx, cy, cz);
+    factorised_tables_kernel<<<64, 256, 0, st>>>(C, r, dr, S, B, cosmo->h0, cosmo->c, zr, dzr, A, pzf, cx, cy, cz, rmf);
     // the scales of the float decisions (r(z_max) is read from the table on the device)
     FastTabs T;
     T.zr = zr;
     T.dzr = dzr;
     T.A = A;
+    T.rmax = rmf;
     T.pz = pzf;
     T.ctr[0] = cx;
     T.ctr[1] = cy;
@@ -625,8 +690,11 @@ ck_status launch_factorised_randoms(Plan& p, const ck_cosmology* cosmo, const ck
     T.z_scale = (float)(sel->n_z / (sel->z_hi - sel->z_lo));
     T.zlo = (float)sel->z_lo;
     T.zhi = (float)sel->z_hi;
-    T.dz_bin = (float)((sel->z_hi - sel->z_lo) / sel->n_z);
     T.mz = (float)(3e-6 * cosmo->z_max);
+    T.tol_z = (float)(3e-6 * cosmo->z_max * sel->n_z / (sel->z_hi - sel->z_lo));
+    T.tol_ra = (float)(FR_MANG * sel->n_ra / two_pi);
+    T.tol_dec = (float)(FR_MANG * sel->n_dec / M_PI);
+    T.nra_f = (float)sel->n_ra;
     ProfScope ps(p, ST_SELECTION, 8.0 * (double)nbox, st);
     factorised_fast_kernel<<<blocks, FR_THREADS, 0, st>>>(C, r, dr, S, B, T, p.counts[1], queue, qn, qcap);
     factorised_slow_kernel<<<sms * 4, FR_THREADS, 0, st>>>(C, r, dr, S, B, p.counts[1], queue, qn, qcap);

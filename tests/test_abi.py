@@ -127,7 +127,7 @@ def test_factorised_validation(lib):
     assert f(h, ok, _Selection(1e5, None, 4, 3, pz.ctypes.data_as(dptr), 5, 0, 0.1, 0.5), None) == 2
     for bad in (sel(nra=0), sel(nz=0), sel(n_tot=float("nan")), sel(n_tot=-1.0), sel(zlo=-0.1),
                 sel(zhi=0.1), sel(a=np.full((3, 4), -0.1)), sel(z=np.array([1.0, 1.0, np.inf, 1.0, 1.0])),
-                sel(nra=1 << 14, ndec=1 << 13)):
+                sel(nra=1 << 14, ndec=1 << 13), sel(nz=(1 << 20) + 1)):
         assert f(h, ok, bad, None) == 1
 
 

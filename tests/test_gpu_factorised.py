@@ -104,7 +104,8 @@ def test_field_on_bin_edges(torch):
     its 0, 90, 180, 270 degree bin edges, declination 0 and the poles), the
     observer's own cell, and fine bins (0.5 degree, 50 redshift bins): many
     cells near an edge take the FP64 path; every decision must still be the
-    oracle's."""
+    oracle's.  (More near-edge cells than the FP64 queue holds for a box
+    this size, so the FP64 kernel also takes its scan for marked cells.)"""
     g = GridSpec((25, 25, 25), (-150.0, -150.0, -150.0), 12.0, False)
     pa, pz = _selection(9, 720, 360, 50, 0.01, 0.08, cut=False)
     sel = _sel(pa, pz, 0.01, 0.08, 0.09)
