@@ -62,6 +62,14 @@ Readings where the paper is silent or ambiguous (each is a choice):
    density at its centre times its volume,
    R = N_tot P_ang(ra, dec) P_z(z(r)) (dz/dr) g^3 / r^2, dz/dr = H0 E(z) / c,
    and 0 where r exceeds r(z_max) or r = 0.
+11. Continuous fields (Sec. 2.7, Eqs. 15-17): delta = (D - R) / R per cell
+   where R > 0 and 0 where R <= 0 (no survey there); W_0 = delta,
+   W_s = delta *** K_s and xi_n = sum_r W_0 prod W_{s_i}, no denominator.
+12. Cross-correlation (Sec. 2.8): W_0 = Delta_0, W_s = Delta_1 *** K_s, the
+   sums of Eq. 16 (xi_2 of Eq. 17 and, by the same product, higher orders).
+13. Per-cell maps (Sec. 5, the wishbone and sky-slice figures):
+   W_0 W_s / <B_0 B_s> per cell, the average over the box's cells,
+   <B_0 B_s> = den_2(s) / N_box.
 
 Pins: see tests/test_oracle_pins.py (brute-force pair and triplet counts on
 cell-centred points, three-square lattice counts, closed forms, symmetry,
@@ -81,6 +89,7 @@ __all__ = [
     "w_at_cells", "multisets", "product_sums", "dense_tensor", "xi_from",
     "xi_diagonal", "correlate", "kernel_spectrum_octant", "guard_band_ok", "pair_sums_fft",
     "comoving_distance", "sky_to_cartesian", "factorised_randoms_at", "factorised_randoms",
+    "delta_field", "field_sums", "product_map",
 ]
 
 
@@ -442,6 +451,45 @@ def xi_diagonal(W0, W1, B0, B1, order: int) -> float:
     num = float(np.sum(W0 * W1 ** (order - 1)))
     den = float(np.sum(B0 * B1 ** (order - 1)))
     return num / den if den > 0 else float("nan")
+
+
+def delta_field(D, R) -> np.ndarray:
+    """Eq. 15 (reading 11): (D - R) / R where R > 0, else 0; FP64."""
+    D = np.asarray(D, np.float64)
+    R = np.asarray(R, np.float64)
+    out = np.zeros(D.shape, np.float64)
+    ok = R > 0
+    out[ok] = (D[ok] - R[ok]) / R[ok]
+    return out
+
+
+def field_sums(grid, shells: Sequence[float], width: float, W0, F, orders: Sequence[int] = (2, 3),
+               engine: str = "direct", rule: str = "center_bin") -> Dict[str, object]:
+    """Eq. 16 for a continuous field (W0 = F = delta, reading 11) or a cross
+    pair (W0 = Delta_0, F = Delta_1, reading 12): W_s = F *** K_s and per
+    order n the sums over multisets of sum_r W0 prod W_{s_i} with the sums of
+    their absolute terms."""
+    W0 = np.asarray(W0, np.float64)
+    F = np.asarray(F, np.float64)
+    offs = [shell_offsets(s, width, grid.cell, rule) for s in shells]
+    if engine == "direct":
+        W = [convolve_direct(F, o, grid.periodic) for o in offs]
+    elif engine == "fft":
+        W = [convolve_fft(F, o) for o in offs]
+    else:
+        raise ValueError(engine)
+    out: Dict[str, object] = dict(W=W, offsets=offs)
+    for n in orders:
+        v, a = product_sums(W0, W, n)
+        out[f"num{n}"] = v
+        out[f"abs_num{n}"] = a
+        out[f"xi{n}"] = dense_tensor(v, len(shells), n - 1)
+    return out
+
+
+def product_map(W0, Ws, den2_s: float, n_box: int) -> np.ndarray:
+    """Reading 13: W_0 W_s / <B_0 B_s> per cell, <B_0 B_s> = den_2(s) / N_box."""
+    return np.asarray(W0, np.float64) * np.asarray(Ws, np.float64) / (den2_s / n_box)
 
 
 def correlate(grid, shells: Sequence[float], width: float, data, randoms,

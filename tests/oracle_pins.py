@@ -672,6 +672,90 @@ def check_factorised_randoms(o) -> bool:
     return bool(ok)
 
 
+
+def check_delta_field(o) -> bool:
+    """Eq. 15 (reading 11) by hand and by its special cases: D = R gives 0,
+    D = 2R gives 1, cells with R = 0 give 0 whatever D holds."""
+    ok = np.allclose(o.delta_field(np.array([3.0, 1.0, 5.0]), np.array([2.0, 0.0, 4.0])), [0.5, 0.0, 0.25],
+                     rtol=0, atol=1e-15)
+    rng = _rng(61)
+    R = rng.uniform(0.5, 2.0, (6, 5, 4))
+    R[0, 0, :] = 0.0
+    D = rng.uniform(0.0, 3.0, R.shape)
+    ok &= float(np.abs(o.delta_field(R, R)).max()) == 0.0
+    two = o.delta_field(2.0 * R, R)
+    ok &= bool(np.all(two[R > 0] == 1.0)) and bool(np.all(two[R == 0] == 0.0))
+    ok &= bool(np.all(o.delta_field(D, R)[0, 0, :] == 0.0))
+    return bool(ok)
+
+
+def check_field_sums(o) -> bool:
+    """Eq. 16 for continuous and cross fields (readings 11, 12): a constant
+    field c on a periodic grid gives N_c c^n prod |O_s| (brute-force shell
+    sizes); point fields give brute-force pair and triplet sums (W_0 = u at
+    cell a, the convolved field v_b at cells b: num_2(s) = u sum_{b in s} v_b,
+    num_3(s, t) = u (sum_{b in s} v_b)(sum_{b in t} v_b)); the cross sum of
+    order 2 is symmetric in its two fields (K_s is even)."""
+    g = GridSpec((12, 12, 12), (0.0, 0.0, 0.0), 1.0, True)
+    shells, width = (1.5, 2.5, 3.4), 1.0
+    c = 0.7
+    F = np.full((12, 12, 12), c)
+    res = o.field_sums(g, shells, width, F, F, orders=(2, 3))
+    sizes = [brute_shell_count(s, width, 1.0) for s in shells]
+    ok = True
+    for n in (2, 3):
+        for v, ms in zip(res[f"num{n}"], itertools.combinations_with_replacement(range(3), n - 1)):
+            want = g.n_cells * c ** n * np.prod([sizes[s] for s in ms])
+            ok &= abs(v - want) <= 1e-10 * want
+    # point fields: W_0 at one cell, the convolved field at ten others
+    rng = _rng(62)
+    a = np.array([[5, 6, 4]])
+    bs = np.unique(np.stack([rng.integers(2, 10, 10) for _ in range(3)], axis=1), axis=0)
+    bs = bs[np.any(bs != a[0], axis=1)]
+    W0 = np.zeros((12, 12, 12))
+    W0[a[0, 2], a[0, 1], a[0, 0]] = 1.3
+    F = np.zeros((12, 12, 12))
+    v = rng.uniform(-1.0, 2.0, len(bs))
+    for (x, y, z), vb in zip(bs, v):
+        F[z, y, x] = vb
+    res = o.field_sums(g, shells, width, W0, F, orders=(2, 3))
+    d2 = _sep2(a, bs, g.n)[0]
+    per = [float(np.sum(v[_in_shell(d2, s, width, 1.0)])) for s in shells]
+    ok &= np.allclose(res["num2"], [1.3 * per[s] for s in range(3)], rtol=1e-12, atol=1e-12)
+    want3 = [1.3 * per[s] * per[t] for s, t in itertools.combinations_with_replacement(range(3), 2)]
+    ok &= np.allclose(res["num3"], want3, rtol=1e-12, atol=1e-12)
+    ok &= bool(any(abs(x) > 0.1 for x in res["num2"]))
+    # symmetry of the order-2 cross sum on a non-periodic grid
+    gb = GridSpec((9, 8, 7), (0.0, 0.0, 0.0), 1.0, False)
+    f0 = rng.normal(size=(7, 8, 9))
+    f1 = rng.normal(size=(7, 8, 9))
+    x01 = o.field_sums(gb, shells, width, f0, f1, orders=(2,))["num2"]
+    x10 = o.field_sums(gb, shells, width, f1, f0, orders=(2,))["num2"]
+    ok &= np.allclose(x01, x10, rtol=1e-12, atol=1e-12) and not np.allclose(x01, o.field_sums(
+        gb, shells, width, f0, f0, orders=(2,))["num2"])
+    return bool(ok)
+
+
+def check_product_map(o) -> bool:
+    """Reading 13 against the sums: the map times <B_0 B_s> summed over the
+    cells is num_2(s); with Rt and N constant the map is the same in every
+    cell, c_N^2 |O_s| / (c_R^2 |O_s|) = (c_N / c_R)^2."""
+    g, dat, ran = _clustered_case()
+    res = o.correlate(g, CSHELLS, 10.0, dat, ran, orders=(2,))
+    ok = True
+    for s in range(len(CSHELLS)):
+        m = o.product_map(res["N"], res["W"][s], float(res["den2"][s]), g.n_cells)
+        ok &= abs(float(m.sum()) * float(res["den2"][s]) / g.n_cells - float(res["num2"][s])) <= 1e-9 * (
+            abs(float(res["abs_num2"][s])) + 1e-30)
+    # constant fields: N = 0.3, Rt = 1.2 everywhere, |O_s| offsets
+    gc = GridSpec((10, 10, 10), (0.0, 0.0, 0.0), 1.0, True)
+    size = brute_shell_count(2.5, 1.0, 1.0)
+    den2 = gc.n_cells * 1.2 * 1.2 * size
+    m = o.product_map(np.full((10, 10, 10), 0.3), np.full((10, 10, 10), 0.3 * size), den2, gc.n_cells)
+    ok &= np.allclose(m, (0.3 / 1.2) ** 2, rtol=1e-12)
+    return bool(ok)
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
@@ -679,5 +763,5 @@ ALL_CHECKS = [
     check_constant_field_den, check_relabel_shells, check_translation, check_linearity,
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
     check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights, check_sky_coordinates,
-    check_factorised_randoms,
+    check_factorised_randoms, check_delta_field, check_field_sums, check_product_map,
 ]

@@ -116,6 +116,30 @@ def linear_jacobian(cells, grid, **sel):
     return _orig_fr(cells, grid, **sel) * np.sqrt((ctr * ctr).sum(axis=1))
 
 
+
+_orig_fs = O.field_sums
+
+
+def delta_over_data(D, R):
+    # (D - R) / D instead of (D - R) / R
+    D = np.asarray(D, np.float64)
+    R = np.asarray(R, np.float64)
+    out = np.zeros(D.shape)
+    ok = (R > 0) & (D != 0)
+    out[ok] = (D[ok] - R[ok]) / D[ok]
+    return out
+
+
+def cross_convolves_w0(grid, shells, width, W0, F, orders=(2, 3), engine="direct", rule="center_bin"):
+    # W_s taken from W_0's field instead of the second tracer's
+    return _orig_fs(grid, shells, width, W0, W0, orders, engine, rule)
+
+
+def map_without_volume(W0, Ws, den2_s, n_box):
+    # <B_0 B_s> taken as the sum instead of the average over the cells
+    return np.asarray(W0, np.float64) * np.asarray(Ws, np.float64) / den2_s
+
+
 MUTANTS = [
     ("density_fields", wrong_sign_density),
     ("cell_index", off_by_one_index),
@@ -130,6 +154,9 @@ MUTANTS = [
     ("sky_to_cartesian", swapped_angles),
     ("factorised_randoms_at", flipped_declination),
     ("factorised_randoms_at", linear_jacobian),
+    ("delta_field", delta_over_data),
+    ("field_sums", cross_convolves_w0),
+    ("product_map", map_without_volume),
 ]
 
 
