@@ -196,7 +196,7 @@ ck_status ck_set_randoms_weighted(ck_plan* plan, const float* x, const float* y,
 ck_status ck_compute_weighted(ck_plan* plan, const float* x, const float* y, const float* z, const float* w,
                               int64_t n, int32_t order_mask, const ck_outputs* out, void* stream);
 
-/* --- survey input (Sec. 2.1) -------------------------------------------------- */
+/* --- survey input (Sec. 2.2) -------------------------------------------------- */
 
 /* The fiducial cosmology of Eq. 3: H0 in km/s/Mpc (100 gives distances in
  * h^-1 Mpc), the present-day densities O_M, O_k, O_L, the speed of light c in

@@ -52,7 +52,7 @@ Readings where the paper is silent or ambiguous (each is a choice):
    even), summed exactly; a point with a non-finite weight is dropped.  The
    rounding makes the sums independent of the order of addition; it moves a
    weight by at most 2^-33.
-9. Sky coordinates (Sec. 2.1): right ascension and declination in degrees;
+9. Sky coordinates (Sec. 2.2): right ascension and declination in degrees;
    r(z) is Eq. 3's line-of-sight integral exactly as printed (no curvature
    transform), and X, Y, Z follow Eqs. 4-6.
 10. Factorised randoms (Eq. 7): P_ang is a probability per steradian on an
@@ -67,7 +67,7 @@ Readings where the paper is silent or ambiguous (each is a choice):
    W_s = delta *** K_s and xi_n = sum_r W_0 prod W_{s_i}, no denominator.
 12. Cross-correlation (Sec. 2.8): W_0 = Delta_0, W_s = Delta_1 *** K_s, the
    sums of Eq. 16 (xi_2 of Eq. 17 and, by the same product, higher orders).
-13. Per-cell maps (Sec. 5, the wishbone and sky-slice figures):
+13. Per-cell maps (Sec. 4.2, the wishbone and sky-slice figures):
    W_0 W_s / <B_0 B_s> per cell, the average over the box's cells,
    <B_0 B_s> = den_2(s) / N_box.
 
@@ -184,7 +184,7 @@ def density_fields(D: np.ndarray, R: np.ndarray):
 
 
 # ---------------------------------------------------------------------------
-# Input coordinates (Sec. 2.1, Eqs. 3-6)
+# Input coordinates (Sec. 2.2, Eqs. 3-6)
 
 def comoving_distance(z, h0: float, omega_m: float, omega_k: float, omega_l: float, c: float) -> np.ndarray:
     """Eq. 3: r(z) = (c / H0) int_0^z dz' / sqrt(O_M (1+z')^3 + O_k (1+z')^2 + O_L),

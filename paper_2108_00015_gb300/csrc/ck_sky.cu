@@ -1,4 +1,4 @@
-// ck_sky.cu -- survey coordinates to the grid's Cartesian frame (Sec. 2.1):
+// ck_sky.cu -- survey coordinates to the grid's Cartesian frame (Sec. 2.2):
 // the comoving distance of Eq. 3,
 //   r(z) = (c / H0) int_0^z dz' / E(z'),  E^2 = O_M (1+z)^3 + O_k (1+z)^2 + O_L,
 // and Eqs. 4-6, X = r cos(dec) cos(ra), Y = r cos(dec) sin(ra), Z = r sin(dec).

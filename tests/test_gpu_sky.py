@@ -1,4 +1,4 @@
-"""Survey input (ck_sky_to_cartesian, Sec. 2.1, Eqs. 3-6): the device's
+"""Survey input (ck_sky_to_cartesian, Sec. 2.2, Eqs. 3-6): the device's
 distance table and coordinates against the oracle's FP64 quadrature and
 Eqs. 4-6 (float32 outputs within two units in the last place of r), in the
 paper's fiducial cosmology (Sec. 3) and an open one; the Einstein-de Sitter
