@@ -296,6 +296,44 @@ ck_status ck_compute_diagonal(ck_plan* plan, const float* x, const float* y, con
 ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
                                   void* stream);
 
+/* --- fields on the grid and per-cell maps (Secs. 2.7, 2.8, 4.2) ----------------
+ * Fields are float32 in the box's layout: n[2] x n[1] x n[0], x fastest (the
+ * caller's box; padded plans place it in the corner of their transform
+ * grid), each in device or host memory (host fields are copied through the
+ * plan's count buffers, whose contents are then not defined).  Values must
+ * be finite.  On a non-periodic box plan the nonzero cells plus the
+ * kernels' reach must fit the box (CK_ERR_GUARD_BAND otherwise, as for
+ * catalogs); padded plans have no such limit. */
+
+/* Continuous matter distribution (Sec. 2.7, Eqs. 15-17): the over-density
+ * delta = (d - r) / r where r > 0, 0 where r <= 0 (outside the survey); r
+ * NULL: d is delta itself.  W_0 = delta, W_s = delta *** K_s and
+ *   xi_n(s_1..s_{n-1}) = sum_r W_0 W_s1 .. W_s(n-1)   (no denominator).
+ * Outputs as ck_compute: xi[n] and num[n] receive the sums (dense symmetric
+ * tensors), den[n] receives 1.0, dropped receives 0, 0.  Needs no randoms.
+ * Errors: CK_ERR_BAD_POINTER (plan or d NULL), CK_ERR_ARG (order mask), the
+ * guard band as above. */
+ck_status ck_compute_continuous(ck_plan* plan, const float* d, const float* r, int32_t order_mask,
+                                const ck_outputs* out, void* stream);
+
+/* Cross-correlation of two maps (Sec. 2.8): W_0 = f0, W_s = f1 *** K_s and
+ * the same sums, sum_r f0 (f1***K_s1) .. (f1***K_s(n-1)); order 2 is Eq. 17
+ * for two tracers.  Outputs, errors and field rules as
+ * ck_compute_continuous; both fields required. */
+ck_status ck_compute_cross(ck_plan* plan, const float* f0, const float* f1, int32_t order_mask,
+                           const ck_outputs* out, void* stream);
+
+/* The per-cell map W_0 W_s / <B_0 B_s> of shell `shell` (Sec. 4.2), for the
+ * catalog of the last ck_compute (or ck_compute_weighted): W_0 = N,
+ * W_s = N***K_s, and <B_0 B_s> = alpha^2 den_raw_2(s) / N_box, the average of
+ * the random field's order-2 terms over the box's N_box cells.  map: float
+ * [N_box] in box layout, device or host (host: synchronous).  Fused plans
+ * recompute W_s from the resident spectrum first.  Errors:
+ * CK_ERR_BAD_POINTER, CK_ERR_ARG (shell out of range, or the last call was
+ * not a catalog's ck_compute), CK_ERR_NO_RANDOMS, CK_ERR_ZERO_DENOM (the
+ * average is not positive: the map is NaN). */
+ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream);
+
 /* --- batched form --------------------------------------------------------------
  * Many catalogs over one or more plans (grid classes), each plan's randoms set
  * once with ck_set_randoms.  Catalog i is computed on plans[cats[i].plan] and
@@ -327,9 +365,10 @@ ck_status ck_plan_status(ck_plan* plan, void* stream);
  * may be NULL). */
 ck_status ck_get_grids(ck_plan* plan, uint32_t* d_counts, uint32_t* r_counts, void* stream);
 
-/* Copy a real field: which = 0 -> N of the last ck_compute, which = 1 -> R (as
- * float) of the last ck_set_randoms ... valid until the next call that
- * overwrites it (float [N_c], device or host). */
+/* Copy a real field: which = 0 -> N of the last ck_compute (or the loaded
+ * field of the last ck_compute_continuous / ck_compute_cross: delta, or f1),
+ * which = 1 -> R (as float) of the last ck_set_randoms ... valid until the
+ * next call that overwrites it (float [N_c], device or host). */
 ck_status ck_get_field(ck_plan* plan, int32_t which, float* out, void* stream);
 
 /* Copy shell `shell` of the convolution of the field whose spectrum is

@@ -110,6 +110,9 @@ _SIGS = [
                                            ctypes.POINTER(_Outputs), _P]),
     ("ck_compute_diagonal", ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs),
                                            _P]),
+    ("ck_compute_continuous", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
+    ("ck_compute_cross", ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
+    ("ck_product_map", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     ("ck_batch_compute", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_Catalog), ctypes.c_int32,
                                         ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_plan_status", ctypes.c_int, [_P, _P]),
@@ -269,6 +272,7 @@ class Plan:
         self.fused = bool(info.fused)
         self.fft_n = tuple(int(v) for v in info.fft_n)
         self.shape = (self.fft_n[2], self.fft_n[1], self.fft_n[0])
+        self.box_shape = (int(n[2]), int(n[1]), int(n[0]))  # the caller's box, (nz, ny, nx)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -358,6 +362,59 @@ class Plan:
         if code not in (0, 7):  # a zero denominator still fills the outputs (NaN there)
             raise CkError(code, "ck_compute")
         return res
+
+    def _field_outputs(self, orders, out):
+        torch = _torch()
+        dev = "cuda" if out == "device" else "cpu"
+        res: Dict[str, object] = {k: {} for k in ("xi", "num", "den")}
+        o = _Outputs()
+        for n in orders:
+            for key in ("xi", "num", "den"):
+                t = torch.empty((self.n_shells,) * (int(n) - 1), dtype=torch.float64, device=dev,
+                                pin_memory=(dev == "cpu"))
+                res[key][n] = t
+                getattr(o, key)[n] = t.data_ptr()
+        return res, o
+
+    def _box_field(self, f):
+        f = _as_f32(f)
+        assert tuple(f.shape) == self.box_shape or int(np.prod(f.shape)) == int(np.prod(self.box_shape)), \
+            "fields have the box's shape (nz, ny, nx)"
+        return f
+
+    def compute_continuous(self, d, r=None, orders=(2, 3), out: str = "device", stream=None) -> Dict[str, object]:
+        """ck_compute_continuous (Eqs. 15-17): delta = (d - r) / r (r None: d
+        is delta), xi_n = sum W_0 W_s1 .. with no denominator.  d, r: box-shaped
+        float32 (device tensors or host arrays)."""
+        d = self._box_field(d)
+        r = None if r is None else self._box_field(r)
+        res, o = self._field_outputs(orders, out)
+        code = _lib().ck_compute_continuous(self._h, _ptr(d), _ptr(r), order_mask(orders), ctypes.byref(o),
+                                            _stream_ptr(stream))
+        res["status"] = int(code)
+        _check(code, "ck_compute_continuous")
+        return res
+
+    def compute_cross(self, f0, f1, orders=(2, 3), out: str = "device", stream=None) -> Dict[str, object]:
+        """ck_compute_cross (Sec. 2.8): W_0 = f0, W_s = f1 *** K_s."""
+        f0, f1 = self._box_field(f0), self._box_field(f1)
+        res, o = self._field_outputs(orders, out)
+        code = _lib().ck_compute_cross(self._h, _ptr(f0), _ptr(f1), order_mask(orders), ctypes.byref(o),
+                                       _stream_ptr(stream))
+        res["status"] = int(code)
+        _check(code, "ck_compute_cross")
+        return res
+
+    def product_map(self, shell: int, out: str = "device", stream=None):
+        """ck_product_map: W_0 W_s / <B_0 B_s> per cell of the box for the last
+        catalog (box-shaped float32, on the device or in host memory)."""
+        if out == "device":
+            torch = _torch()
+            m = torch.empty(self.box_shape, dtype=torch.float32, device="cuda")
+        else:
+            m = np.empty(self.box_shape, dtype=np.float32)
+        _check(_lib().ck_product_map(self._h, int(shell), _ptr(m), _stream_ptr(stream)), "ck_product_map")
+        return m
 
     def compute_diagonal(self, x, y, z, orders=(2, 3), out: str = "device", stream=None) -> Dict[str, object]:
         """The equidistant functions of Eq. 14 only (ck_compute_diagonal): returns

@@ -252,11 +252,13 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
 // the product sums of the orders in `mask` (Eq. 11) into `sums`: through the
 // bank and the contraction kernels, or in one fused pass (fused plans, which
 // always form every order up to max_order).
-ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st) {
+// W_0 is the transformed field itself, or w0 when given (cross-correlation).
+ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, const float* w0 = nullptr) {
+  if (!w0) w0 = p.field;
   launch_fft_forward(p, p.field, p.spec, st);
-  if (p.fused) return launch_convolve_contract(p, p.field, sums, st);
+  if (p.fused) return launch_convolve_contract(p, w0, sums, st);
   launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
-  return launch_contract(p, mask, p.field, p.bank, p.field_stride, sums, st);
+  return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st);
 }
 
 int full_mask(const Plan& p) {
@@ -536,6 +538,94 @@ ck_status ck_compute_weighted(ck_plan* plan, const float* x, const float* y, con
   return compute_impl(plan, x, y, z, w, n, order_mask, out, stream);
 }
 
+// Fields on the grid (Secs. 2.7, 2.8): a0 (and b0) are loaded into the
+// transformed field (continuous: Eq. 15's delta; cross: a copy of f1), f0
+// into the W_0 buffer for a cross pair; then the plain sums of Eq. 16.
+// Host fields are first copied into the count buffers (box layout; their
+// contents are not defined after these calls).
+static ck_status fields_impl(ck_plan* plan, const float* a0, const float* b0, const float* f0, bool delta,
+                             int32_t order_mask, const ck_outputs* out, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (!a0 || (!delta && !f0)) return CK_ERR_BAD_POINTER;
+  if (order_mask == 0 || (order_mask & ~full_mask(p)) != 0) return CK_ERR_ARG;
+  cudaStream_t st = S(stream);
+  const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
+  // a host field lands in count buffer k (box layout) before it is loaded
+  auto on_device = [&](const float* f, int k, const float** dev) -> ck_status {
+    if (is_device_ptr(f)) {
+      *dev = f;
+      return CK_OK;
+    }
+    CK_TRY(cudaMemcpyAsync(p.counts[k], f, bytes, cudaMemcpyHostToDevice, st));
+    *dev = reinterpret_cast<const float*>(p.counts[k]);
+    return CK_OK;
+  };
+  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 0);
+  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 1);
+  const bool padded = p.grid.n[0] != p.box_n[0] || p.grid.n[1] != p.box_n[1] || p.grid.n[2] != p.box_n[2];
+  if (padded) CK_TRY(cudaMemsetAsync(p.field, 0, (size_t)p.nc * 4, st));
+  float* w0 = nullptr;
+  if (!delta) {  // W_0 = f0 in count buffer 0, stored layout (staged through buffer 1)
+    const float* d0 = nullptr;
+    CK_TRY_S(on_device(f0, 1, &d0));
+    w0 = reinterpret_cast<float*>(p.counts[0]);
+    if (padded) CK_TRY(cudaMemsetAsync(w0, 0, (size_t)p.nc * 4, st));
+    launch_field_load(p, d0, nullptr, false, w0, 0, st);
+  }
+  const float* da = nullptr;
+  const float* db = nullptr;
+  CK_TRY_S(on_device(a0, delta ? 0 : 1, &da));
+  if (b0) CK_TRY_S(on_device(b0, 1, &db));
+  launch_field_load(p, da, db, delta, p.field, 1, st);
+  launch_field_check(p, st);
+  p.bank_holds = -1;
+  CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st, w0));
+  p.bank_holds = 2;  // a field's convolutions (not a catalog's)
+  launch_finalize(p, order_mask, st, true);
+  CK_TRY(cudaGetLastError());
+  bool host_seen = false;
+  CK_TRY_S(copy_results(p, order_mask, out, st, &host_seen));
+  if (host_seen) return read_status(p, st, true);
+  return CK_OK;
+}
+
+ck_status ck_compute_continuous(ck_plan* plan, const float* d, const float* r, int32_t order_mask,
+                                const ck_outputs* out, void* stream) {
+  return fields_impl(plan, d, r, nullptr, true, order_mask, out, stream);
+}
+
+ck_status ck_compute_cross(ck_plan* plan, const float* f0, const float* f1, int32_t order_mask,
+                           const ck_outputs* out, void* stream) {
+  if (!plan || !f0 || !f1) return CK_ERR_BAD_POINTER;
+  return fields_impl(plan, f1, nullptr, f0, false, order_mask, out, stream);
+}
+
+ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream) {
+  if (!plan || !map) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (shell < 0 || shell >= p.ns) return CK_ERR_ARG;
+  if (!p.have_randoms_diag) return CK_ERR_NO_RANDOMS;
+  if (p.bank_holds != 0) return CK_ERR_ARG;  // needs a catalog's ck_compute just before
+  cudaStream_t st = S(stream);
+  const float* ws = p.bank + (size_t)shell * p.field_stride;
+  if (p.fused) {  // recompute W_s from the resident spectrum
+    launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, p.bank, p.field_stride, st);
+    ws = p.bank;
+  }
+  const bool dev = is_device_ptr(map);
+  const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
+  float* dst = dev ? map : reinterpret_cast<float*>(p.counts[0]);  // host: through count buffer 0
+  launch_product_map(p, p.field, ws, shell, dst, st);
+  CK_TRY(cudaGetLastError());
+  if (!dev) {
+    CK_TRY(cudaMemcpyAsync(map, dst, bytes, cudaMemcpyDeviceToHost, st));
+    CK_TRY(cudaStreamSynchronize(st));
+    return read_status(p, st, true);
+  }
+  return CK_OK;
+}
+
 ck_status ck_compute_diagonal(ck_plan* plan, const float* x, const float* y, const float* z, int64_t n,
                               int32_t order_mask, const ck_outputs* out, void* stream) {
   if (!plan) return CK_ERR_BAD_POINTER;
@@ -667,7 +757,8 @@ ck_status ck_get_field(ck_plan* plan, int32_t which, float* out, void* stream) {
   if (!plan || !out) return CK_ERR_BAD_POINTER;
   if (which != 0 && which != 1) return CK_ERR_ARG;
   Plan& p = *reinterpret_cast<Plan*>(plan);
-  if (which != p.bank_holds) return CK_ERR_ARG;  // the field buffer holds the last stage's input
+  // the field buffer holds the last stage's input (a loaded field counts as data)
+  if (which != (p.bank_holds == 2 ? 0 : p.bank_holds)) return CK_ERR_ARG;
   cudaStream_t st = S(stream);
   bool host = false;
   CK_TRY_S(copy_out(out, p.field, (size_t)p.nc * 4, st, &host));

@@ -630,12 +630,20 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
 // ---------------------------------------------------------------------------
 // xi_n = num / (alpha^n den_raw) into dense symmetric tensors
 
+// plain != 0: field sums with no denominator (Eq. 16): xi = num, den = 1.
 __global__ void finalize_kernel(const double* __restrict__ sums, const double* __restrict__ den_raw,
                                 const int* __restrict__ dmap, int64_t dense, int64_t mbase, int n, DevState* st,
-                                double* __restrict__ xi, double* __restrict__ num, double* __restrict__ den) {
+                                double* __restrict__ xi, double* __restrict__ num, double* __restrict__ den,
+                                int plain) {
   const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= dense) return;
   const int64_t r = mbase + dmap[d];
+  if (plain) {
+    num[d] = sums[r];
+    xi[d] = sums[r];
+    den[d] = 1.0;
+    return;
+  }
   const double alpha = st->alpha;
   double an = 1.0;
   for (int i = 0; i < n; ++i) an *= alpha;
@@ -651,7 +659,7 @@ __global__ void finalize_kernel(const double* __restrict__ sums, const double* _
   }
 }
 
-void launch_finalize(const Plan& p, int mask, cudaStream_t st) {
+void launch_finalize(const Plan& p, int mask, cudaStream_t st, bool plain) {
   ProfScope ps(p, ST_FINALIZE, 0.0, st);
   for (int n = 2; n <= p.max_order; ++n) {
     if (!((mask >> n) & 1)) continue;
@@ -660,7 +668,8 @@ void launch_finalize(const Plan& p, int mask, cudaStream_t st) {
     double* num = p.dense + p.dense_total + p.dense_base[n];
     double* den = p.dense + 2 * p.dense_total + p.dense_base[n];
     finalize_kernel<<<(unsigned)((dense + 255) / 256), 256, 0, st>>>(
-        p.sums, p.den_raw, p.dense_map + p.dense_base[n], dense, p.multiset_base[n], n, p.dstate, xi, num, den);
+        p.sums, p.den_raw, p.dense_map + p.dense_base[n], dense, p.multiset_base[n], n, p.dstate, xi, num, den,
+        plain ? 1 : 0);
   }
 }
 

@@ -274,7 +274,18 @@ cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, i
 ck_status contract_prepare(Plan& p, int order_mask);
 ck_status launch_contract(Plan& p, int order_mask, const float* w0, const float* bank,
                           int64_t bank_stride, double* sums_packed, cudaStream_t st);
-void launch_finalize(const Plan& p, int order_mask, cudaStream_t st);
+// plain: field sums with no denominator (xi = num, den = 1)
+void launch_finalize(const Plan& p, int order_mask, cudaStream_t st, bool plain = false);
+
+// ---- fields on the grid and product maps (ck_fields.cu) -----------------------
+// a (and b) in box layout -> out in the stored layout: a copy, or (delta)
+// Eq. 15's (a - b) / b where b > 0, 0 elsewhere (b NULL: a itself); the
+// nonzero cells' count and box go to field `which` of the plan state.
+void launch_field_load(const Plan& p, const float* a, const float* b, bool delta, float* out, int which,
+                       cudaStream_t st);
+void launch_field_check(const Plan& p, cudaStream_t st);  // guard band over fields 0 and 1
+// out (box layout) = w0 ws / <B_0 B_s>, <B_0 B_s> = alpha^2 den_raw_2(shell) / N_box
+void launch_product_map(const Plan& p, const float* w0, const float* ws, int shell, float* out, cudaStream_t st);
 // Eq. 14 for the orders in order_mask after the forward transform of the
 // plan's field: num/den/xi of (s, .., s) for every shell into the first N_s
 // entries of each order's dense outputs (ck_diag.cu).

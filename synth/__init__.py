@@ -1,6 +1,7 @@
 """Seeded synthetic catalogs shared by the oracle, the tests and the bench.
 
-This package only draws point positions. It holds none of the correlation
+This package only draws point positions (and, for the continuous-field
+path, random maps on a grid). It holds none of the correlation
 method's arithmetic (no gridding, no kernels, no sums), so that the oracle
 and the CUDA path can both consume its output without sharing any of the
 computation they are compared on.
@@ -17,4 +18,5 @@ from .catalogs import (  # noqa: F401
     workload,
     WORKLOADS,
     batch_workload,
+    continuous_maps,
 )

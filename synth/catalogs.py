@@ -178,6 +178,30 @@ def _gaussian_field(rng: np.random.Generator, m: int, box: float, k_cut: float) 
     return g / s if s > 0 else g
 
 
+def continuous_maps(seed: int, shape, cell: float, sigma_g: float = 0.4, k_cut: float = 0.15,
+                    footprint: float = 0.8):
+    """A line-intensity-like pair of maps on a grid of ``shape`` (nz, ny, nx):
+    a random-field map R, 1.0 to 2.0 inside an ellipsoidal footprint
+    (semi-axes ``footprint`` times the half-box) and 0 outside, and a data map
+    D = R exp(sigma_g G - sigma_g^2 / 2) with G a unit-variance Gaussian field
+    (P(k) ~ k^-2 below ``k_cut`` h Mpc^-1).  Both float32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nz, ny, nx = (int(v) for v in shape)
+    white = rng.normal(size=(nz, ny, nx))
+    kz, ky, kx = np.meshgrid(*[2.0 * math.pi * np.fft.fftfreq(m, d=cell) for m in (nz, ny, nx)], indexing="ij")
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    amp = np.zeros_like(k)
+    sel = (k > 0) & (k <= k_cut)
+    amp[sel] = 1.0 / k[sel]
+    g = np.real(np.fft.ifftn(np.fft.fftn(white) * amp))
+    g = (g - g.mean()) / max(g.std(), 1e-300)
+    zz, yy, xx = np.meshgrid(*[(np.arange(m) + 0.5) / m * 2.0 - 1.0 for m in (nz, ny, nx)], indexing="ij")
+    rho2 = (xx * xx + yy * yy + zz * zz) / (footprint * footprint)
+    R = np.where(rho2 < 1.0, 1.0 + rng.uniform(0.0, 1.0, (nz, ny, nx)), 0.0)
+    D = R * np.exp(sigma_g * g - 0.5 * sigma_g * sigma_g)
+    return D.astype(np.float32), R.astype(np.float32)
+
+
 def neyman_scott_survey(seed: int, n_parents: int, n_children: int, sigma: float,
                         grid: GridSpec, mask: SurveyMask = SurveyMask(),
                         coarse: int = 64, sigma_g: float = 1.0) -> Catalog:
