@@ -62,6 +62,10 @@ def _args():
                          "selection (P_ang uniform on dec >= 30 deg, P_z uniform on 0.43 <= z < 0.70, the "
                          "survey mask's footprint) instead of gridding the random catalog; "
                          "no e2e, plain-form or CPU legs")
+    ap.add_argument("--continuous", action="store_true",
+                    help="time ck_compute_continuous (Eqs. 15-17) on line-intensity-like maps D, R of the "
+                         "workload's grid (built at 1/4 resolution and repeated; device-resident) instead of "
+                         "catalogs; no e2e, plain-form or CPU legs")
     return ap.parse_args()
 
 
@@ -285,7 +289,16 @@ def run_gb300(args):
     sel_pa[120:, :] = 1.0 / (2.0 * math.pi * (1.0 - math.sin(math.radians(30.0))))  # per sr over dec >= 30
     sel_pz = np.full(27, 1.0 / 0.27)
 
+    if args.continuous:
+        from synth import continuous_maps
+        cs = tuple(max(1, v // 4) for v in (g.n[2], g.n[1], g.n[0]))
+        D4, R4 = continuous_maps(12, cs, g.cell * 4)
+        rep = lambda a: np.ascontiguousarray(a.repeat(4, 0).repeat(4, 1).repeat(4, 2)[:g.n[2], :g.n[1], :g.n[0]])  # noqa
+        map_d, map_r = dev(rep(D4)), dev(rep(R4))
+
     def step():
+        if args.continuous:
+            return plan.compute_continuous(map_d, map_r, orders=orders, out="device")
         if args.factorised:
             plan.set_randoms_factorised(float(d.n), sel_pa, sel_pz, 0.43, 0.70, z_max=0.75)
             return plan.compute(dx, dy, dz, orders=orders, out="device", outputs=outs)
@@ -458,7 +471,9 @@ def run_gb300(args):
                    "step": ("ck_set_randoms + ck_compute_diagonal (both fields, every shell; Eq. 14 only)"
                             if args.diagonal else
                             "ck_set_randoms_factorised (Eq. 7, CMASS-like selection) + ck_compute"
-                            if args.factorised else "ck_set_randoms + ck_compute (both fields, every shell)"),
+                            if args.factorised else
+                            "ck_compute_continuous (Eqs. 15-17: one delta field, every shell, no denominator)"
+                            if args.continuous else "ck_set_randoms + ck_compute (both fields, every shell)"),
                    "l2": "no flush: inputs and intermediates far larger than L2 (16 scratch spectra, 8.7 GB)"},
         "forms": forms,
         "roofline": roofline,
@@ -584,7 +599,7 @@ def run_reference(args):
 
 def main():
     args = _args()
-    if args.diagonal or args.factorised:
+    if args.diagonal or args.factorised or args.continuous:
         args.no_e2e = args.no_cpu_baseline = args.no_plain = True
     if args.impl == "reference":
         run_reference(args)

@@ -14,6 +14,7 @@
 //    of Sec. 4.2), <B_0 B_s> = alpha^2 den_raw_2(s) / N_box, the average of
 //    the random field's order-2 terms over the box.
 #include <limits.h>
+#include <stdint.h>
 
 #include <algorithm>
 
@@ -40,25 +41,58 @@ __global__ void __launch_bounds__(FL_THREADS) field_load_kernel(Layout L, const 
   const unsigned wstride = gridDim.x * (blockDim.x >> 5);
   unsigned long long kept = 0;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
+  // whole rows of 16-byte groups: row starts (box and stored) and pointers aligned
+  const bool vec = (L.n[0] & 3) == 0 && (L.dim[0] & 3) == 0 && ((uintptr_t)a & 15) == 0 &&
+                   (!b || ((uintptr_t)b & 15) == 0) && ((uintptr_t)out & 15) == 0;
   // rows by a running (iy, iz): no integer division in the loop
   unsigned row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int iy = (int)(row % (unsigned)L.n[1]), iz = (int)(row / (unsigned)L.n[1]);
   const int sy = (int)(wstride % (unsigned)L.n[1]), sz = (int)(wstride / (unsigned)L.n[1]);
+  const bool use_b = delta && b;
+  auto value = [&](float v, float r) { return use_b ? (r > 0.0f ? (v - r) / r : 0.0f) : v; };
+  auto take = [&](float v, int ix) {
+    if (v != 0.0f) {
+      ++kept;
+      bmin[0] = min(bmin[0], ix); bmax[0] = max(bmax[0], ix);
+      bmin[1] = min(bmin[1], iy); bmax[1] = max(bmax[1], iy);
+      bmin[2] = min(bmin[2], iz); bmax[2] = max(bmax[2], iz);
+    }
+  };
   for (; row < nrows; row += wstride) {
     const size_t src = (size_t)row * L.n[0];
     float* __restrict__ orow = out + ((size_t)iz * L.dim[1] + iy) * L.dim[0];
-    for (int ix = lane; ix < L.n[0]; ix += 32) {
-      float v = __ldg(a + src + ix);
-      if (delta && b) {
-        const float r = __ldg(b + src + ix);
-        v = r > 0.0f ? (v - r) / r : 0.0f;
+    if (vec) {
+      // 16-byte accesses, four per lane in flight
+      const float4* a4 = reinterpret_cast<const float4*>(a + src);
+      const float4* b4 = reinterpret_cast<const float4*>(b + src);
+      float4* o4 = reinterpret_cast<float4*>(orow);
+      const int nv = L.n[0] >> 2;
+      for (int j0 = 0; j0 < nv; j0 += 128) {
+        float4 qa[4], qb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * 32 + lane;
+          qa[u] = j < nv ? __ldg(a4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+          qb[u] = (use_b && j < nv) ? __ldg(b4 + j) : make_float4(1.f, 1.f, 1.f, 1.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u * 32 + lane;
+          if (j >= nv) continue;
+          const float4 v = make_float4(value(qa[u].x, qb[u].x), value(qa[u].y, qb[u].y), value(qa[u].z, qb[u].z),
+                                       value(qa[u].w, qb[u].w));
+          o4[j] = v;
+          take(v.x, 4 * j);
+          take(v.y, 4 * j + 1);
+          take(v.z, 4 * j + 2);
+          take(v.w, 4 * j + 3);
+        }
       }
-      orow[ix] = v;
-      if (v != 0.0f) {
-        ++kept;
-        bmin[0] = min(bmin[0], ix); bmax[0] = max(bmax[0], ix);
-        bmin[1] = min(bmin[1], iy); bmax[1] = max(bmax[1], iy);
-        bmin[2] = min(bmin[2], iz); bmax[2] = max(bmax[2], iz);
+    } else {
+      for (int ix = lane; ix < L.n[0]; ix += 32) {
+        const float v = value(__ldg(a + src + ix), use_b ? __ldg(b + src + ix) : 1.0f);
+        orow[ix] = v;
+        take(v, ix);
       }
     }
     iy += sy;
@@ -123,6 +157,8 @@ __global__ void __launch_bounds__(FL_THREADS) product_map_kernel(Layout L, const
     if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&st->status, CK_ERR_ZERO_DENOM);
   }
   const float inv = avg > 0.0 ? (float)(1.0 / avg) : __int_as_float(0x7fc00000);
+  const bool vec = (L.n[0] & 3) == 0 && (L.dim[0] & 3) == 0 && ((uintptr_t)w0 & 15) == 0 &&
+                   ((uintptr_t)ws & 15) == 0 && ((uintptr_t)out & 15) == 0;
   const int lane = threadIdx.x & 31;
   const unsigned nrows = (unsigned)L.n[1] * (unsigned)L.n[2];
   const unsigned wstride = gridDim.x * (blockDim.x >> 5);
@@ -132,7 +168,18 @@ __global__ void __launch_bounds__(FL_THREADS) product_map_kernel(Layout L, const
   for (; row < nrows; row += wstride) {
     const size_t cell = ((size_t)iz * L.dim[1] + iy) * L.dim[0];
     float* __restrict__ orow = out + (size_t)row * L.n[0];
-    for (int ix = lane; ix < L.n[0]; ix += 32) orow[ix] = __ldg(w0 + cell + ix) * __ldg(ws + cell + ix) * inv;
+    if (vec) {
+      const float4* a4 = reinterpret_cast<const float4*>(w0 + cell);
+      const float4* b4 = reinterpret_cast<const float4*>(ws + cell);
+      float4* o4 = reinterpret_cast<float4*>(orow);
+      const int nv = L.n[0] >> 2;
+      for (int j = lane; j < nv; j += 32) {
+        const float4 x = __ldg(a4 + j), y = __ldg(b4 + j);
+        o4[j] = make_float4(x.x * y.x * inv, x.y * y.y * inv, x.z * y.z * inv, x.w * y.w * inv);
+      }
+    } else {
+      for (int ix = lane; ix < L.n[0]; ix += 32) orow[ix] = __ldg(w0 + cell + ix) * __ldg(ws + cell + ix) * inv;
+    }
     iy += sy;
     iz += sz;
     if (iy >= L.n[1]) {
