@@ -84,6 +84,19 @@ def test_null_plan_entry_points(lib):
         fn.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_Outputs),
                                                ctypes.c_void_p]
         assert fn(None, None, None, None, 0, 4, ctypes.byref(o), None) == 2, name  # CK_ERR_BAD_POINTER
+    for name in ("ck_compute_continuous", "ck_compute_cross"):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int32, ctypes.POINTER(_Outputs), ctypes.c_void_p]
+        assert fn(None, None, None, 4, ctypes.byref(o), None) == 2, name
+    fn = lib.ck_product_map
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    assert fn(None, 0, None, None) == 2
+    fn = lib.ck_set_randoms_factorised
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p] * 4
+    assert fn(None, None, None, None) == 2
 
 
 def test_sky_validation(lib):
