@@ -299,9 +299,10 @@ ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y,
 /* --- fields on the grid and per-cell maps (Secs. 2.7, 2.8, 4.2) ----------------
  * Fields are float32 in the box's layout: n[2] x n[1] x n[0], x fastest (the
  * caller's box; padded plans place it in the corner of their transform
- * grid), each in device or host memory (host fields are copied through the
- * plan's count buffers, whose contents are then not defined).  Values must
- * be finite.  On a non-periodic box plan the nonzero cells plus the
+ * grid), each in device or host memory (host fields are staged through
+ * plan scratch).  Values must be finite.  The randoms set on the plan stay
+ * valid: a catalog's ck_compute may follow.  The data count grid
+ * (ck_get_grids) is not defined afterwards.  On a non-periodic box plan the nonzero cells plus the
  * kernels' reach must fit the box (CK_ERR_GUARD_BAND otherwise, as for
  * catalogs); padded plans have no such limit. */
 
@@ -310,7 +311,8 @@ ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y,
  * NULL: d is delta itself.  W_0 = delta, W_s = delta *** K_s and
  *   xi_n(s_1..s_{n-1}) = sum_r W_0 W_s1 .. W_s(n-1)   (no denominator).
  * Outputs as ck_compute: xi[n] and num[n] receive the sums (dense symmetric
- * tensors), den[n] receives 1.0, dropped receives 0, 0.  Needs no randoms.
+ * tensors), den[n] receives 1.0, dropped[0] receives 0 (dropped[1] keeps the
+ * last randoms' count).  Needs no randoms.
  * Errors: CK_ERR_BAD_POINTER (plan or d NULL), CK_ERR_ARG (order mask), the
  * guard band as above. */
 ck_status ck_compute_continuous(ck_plan* plan, const float* d, const float* r, int32_t order_mask,
@@ -327,7 +329,8 @@ ck_status ck_compute_cross(ck_plan* plan, const float* f0, const float* f1, int3
  * catalog of the last ck_compute (or ck_compute_weighted): W_0 = N,
  * W_s = N***K_s, and <B_0 B_s> = alpha^2 den_raw_2(s) / N_box, the average of
  * the random field's order-2 terms over the box's N_box cells.  map: float
- * [N_box] in box layout, device or host (host: synchronous).  Fused plans
+ * [N_box] in box layout, device or host (host: synchronous, through the
+ * data count buffer, which is then not defined).  Fused plans
  * recompute W_s from the resident spectrum first.  Errors:
  * CK_ERR_BAD_POINTER, CK_ERR_ARG (shell out of range, or the last call was
  * not a catalog's ck_compute), CK_ERR_NO_RANDOMS, CK_ERR_ZERO_DENOM (the

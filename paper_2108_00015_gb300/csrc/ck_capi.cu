@@ -540,9 +540,11 @@ ck_status ck_compute_weighted(ck_plan* plan, const float* x, const float* y, con
 
 // Fields on the grid (Secs. 2.7, 2.8): a0 (and b0) are loaded into the
 // transformed field (continuous: Eq. 15's delta; cross: a copy of f1), f0
-// into the W_0 buffer for a cross pair; then the plain sums of Eq. 16.
-// Host fields are first copied into the count buffers (box layout; their
-// contents are not defined after these calls).
+// into the W_0 buffer (the data count buffer) for a cross pair; then the
+// plain sums of Eq. 16.  Host fields are first copied into the bank's first
+// field (and b0 into the data count buffer), in box layout.  The randoms'
+// grid, state and cached denominators are left as they are; the loaded
+// fields' extent is kept as field 0's.
 static ck_status fields_impl(ck_plan* plan, const float* a0, const float* b0, const float* f0, bool delta,
                              int32_t order_mask, const ck_outputs* out, void* stream) {
   if (!plan) return CK_ERR_BAD_POINTER;
@@ -552,32 +554,33 @@ static ck_status fields_impl(ck_plan* plan, const float* a0, const float* b0, co
   cudaStream_t st = S(stream);
   const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
   // a host field lands in count buffer k (box layout) before it is loaded
-  auto on_device = [&](const float* f, int k, const float** dev) -> ck_status {
+  auto on_device = [&](const float* f, float* stage, const float** dev) -> ck_status {
     if (is_device_ptr(f)) {
       *dev = f;
       return CK_OK;
     }
-    CK_TRY(cudaMemcpyAsync(p.counts[k], f, bytes, cudaMemcpyHostToDevice, st));
-    *dev = reinterpret_cast<const float*>(p.counts[k]);
+    CK_TRY(cudaMemcpyAsync(stage, f, bytes, cudaMemcpyHostToDevice, st));
+    *dev = stage;
     return CK_OK;
   };
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 0);
-  reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 1);
+  float* stage0 = p.bank;                                     // host a0 / f0 / f1
+  float* stage1 = reinterpret_cast<float*>(p.counts[0]);      // host b0
   const bool padded = p.grid.n[0] != p.box_n[0] || p.grid.n[1] != p.box_n[1] || p.grid.n[2] != p.box_n[2];
   if (padded) CK_TRY(cudaMemsetAsync(p.field, 0, (size_t)p.nc * 4, st));
   float* w0 = nullptr;
-  if (!delta) {  // W_0 = f0 in count buffer 0, stored layout (staged through buffer 1)
+  if (!delta) {  // W_0 = f0 in the data count buffer, stored layout
     const float* d0 = nullptr;
-    CK_TRY_S(on_device(f0, 1, &d0));
+    CK_TRY_S(on_device(f0, stage0, &d0));
     w0 = reinterpret_cast<float*>(p.counts[0]);
     if (padded) CK_TRY(cudaMemsetAsync(w0, 0, (size_t)p.nc * 4, st));
     launch_field_load(p, d0, nullptr, false, w0, 0, st);
   }
   const float* da = nullptr;
   const float* db = nullptr;
-  CK_TRY_S(on_device(a0, delta ? 0 : 1, &da));
-  if (b0) CK_TRY_S(on_device(b0, 1, &db));
-  launch_field_load(p, da, db, delta, p.field, 1, st);
+  CK_TRY_S(on_device(a0, stage0, &da));
+  if (b0) CK_TRY_S(on_device(b0, stage1, &db));
+  launch_field_load(p, da, db, delta, p.field, 0, st);
   launch_field_check(p, st);
   p.bank_holds = -1;
   CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st, w0));
@@ -615,7 +618,7 @@ ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream)
   }
   const bool dev = is_device_ptr(map);
   const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
-  float* dst = dev ? map : reinterpret_cast<float*>(p.counts[0]);  // host: through count buffer 0
+  float* dst = dev ? map : reinterpret_cast<float*>(p.counts[0]);  // host: through the data count buffer
   launch_product_map(p, p.field, ws, shell, dst, st);
   CK_TRY(cudaGetLastError());
   if (!dev) {

@@ -7,9 +7,9 @@
 //    R > 0 and 0 where R <= 0 (no survey there).  One warp per row of cells;
 //    the nonzero cells' count and bounding box go to the plan state (block
 //    reduced, then atomics), for the guard band of a box plan.
-//  * field_check_kernel: the guard band over both loaded fields (the extent
-//    of their nonzero cells plus the kernels' reach must stay inside the
-//    transformed grid on each axis).
+//  * field_check_kernel: the guard band over the loaded fields (both load
+//    into field 0's extent: their nonzero cells plus the kernels' reach must
+//    stay inside the transformed grid on each axis).
 //  * product_map_kernel: W_0 W_s / <B_0 B_s> per cell of the box (the maps
 //    of Sec. 4.2), <B_0 B_s> = alpha^2 den_raw_2(s) / N_box, the average of
 //    the random field's order-2 terms over the box.
@@ -135,16 +135,10 @@ __global__ void __launch_bounds__(FL_THREADS) field_load_kernel(Layout L, const 
 
 __global__ void field_check_kernel(DevState* st, int periodic, int nx, int ny, int nz, int mx, int my, int mz) {
   if (periodic) return;
+  if (!st->kept[0]) return;
   const int n[3] = {nx, ny, nz}, m[3] = {mx, my, mz};
-  for (int a = 0; a < 3; ++a) {
-    int lo = INT_MAX, hi = INT_MIN;
-    for (int f = 0; f < 2; ++f) {
-      if (!st->kept[f]) continue;
-      lo = min(lo, st->bbox_min[f][a]);
-      hi = max(hi, st->bbox_max[f][a]);
-    }
-    if (lo <= hi && hi - lo + m[a] >= n[a]) set_status(&st->status, CK_ERR_GUARD_BAND);
-  }
+  for (int a = 0; a < 3; ++a)
+    if (st->bbox_max[0][a] - st->bbox_min[0][a] + m[a] >= n[a]) set_status(&st->status, CK_ERR_GUARD_BAND);
 }
 
 __global__ void __launch_bounds__(FL_THREADS) product_map_kernel(Layout L, const float* __restrict__ w0,

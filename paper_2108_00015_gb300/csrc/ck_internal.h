@@ -283,7 +283,7 @@ void launch_finalize(const Plan& p, int order_mask, cudaStream_t st, bool plain 
 // nonzero cells' count and box go to field `which` of the plan state.
 void launch_field_load(const Plan& p, const float* a, const float* b, bool delta, float* out, int which,
                        cudaStream_t st);
-void launch_field_check(const Plan& p, cudaStream_t st);  // guard band over fields 0 and 1
+void launch_field_check(const Plan& p, cudaStream_t st);  // guard band over field 0's extent
 // out (box layout) = w0 ws / <B_0 B_s>, <B_0 B_s> = alpha^2 den_raw_2(shell) / N_box
 void launch_product_map(const Plan& p, const float* w0, const float* ws, int shell, float* out, cudaStream_t st);
 // Eq. 14 for the orders in order_mask after the forward transform of the

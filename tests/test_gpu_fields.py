@@ -149,3 +149,25 @@ def test_product_map(torch, precision, padded):
         plan.product_map(0)
     assert e.value.code == 1
     plan.close()
+
+
+def test_fields_leave_randoms_intact(torch):
+    """A field compute between two catalog computes (host fields, staged
+    through plan scratch) leaves the randoms' grid, state and denominators
+    as they were: the second catalog compute is bit-identical to the first."""
+    g = GridSpec((32, 32, 32), (0.0, 0.0, 0.0), 10.0, True)
+    shells = (20.0, 35.0)
+    data = neyman_scott_box(51, 300, 12, 10.0, 320.0)
+    rand = uniform_box(52, 40000, 320.0)
+    for precision in ("fp32", "split_tf32"):
+        plan = _plan(g, shells, 10.0, 3, precision)
+        plan.set_randoms(*dev_cat(torch, rand))
+        first = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
+        D, R = continuous_maps(53, (32, 32, 32), g.cell)
+        plan.compute_continuous(D, R, orders=(2, 3), out="host")                 # host maps
+        plan.compute_cross(D, R, orders=(2,), out="host")
+        again = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
+        for n in (2, 3):
+            for key in ("xi", "num", "den"):
+                assert np.array_equal(first[key][n].numpy(), again[key][n].numpy()), (precision, n, key)
+        plan.close()
