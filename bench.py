@@ -61,11 +61,11 @@ def _args():
                     help="build the randoms field with ck_set_randoms_factorised (Eq. 7) from a CMASS-like "
                          "selection (P_ang uniform on dec >= 30 deg, P_z uniform on 0.43 <= z < 0.70, the "
                          "survey mask's footprint) instead of gridding the random catalog; "
-                         "no e2e, plain-form or CPU legs")
+                         "no e2e or plain-form legs")
     ap.add_argument("--continuous", action="store_true",
                     help="time ck_compute_continuous (Eqs. 15-17) on line-intensity-like maps D, R of the "
                          "workload's grid (built at 1/4 resolution and repeated; device-resident) instead of "
-                         "catalogs; no e2e, plain-form or CPU legs")
+                         "catalogs; no e2e or plain-form legs")
     return ap.parse_args()
 
 
@@ -254,6 +254,55 @@ def cpu_oracle_sample(w, orders, point_frac=1 / 8, fields=2):
     return total * 1000.0, sample
 
 
+def cpu_oracle_mode_sample(w, orders, mode, maps=None, selection=None, cells=2000):
+    """The oracle for the --factorised and --continuous steps, on bounded
+    samples scaled to one step:
+    * factorised: Eq. 7 at `cells` sampled cells (x N_c / cells), the data
+      catalog's gridding (1/8 of its points, x 8), and both fields'
+      convolution and sums as in cpu_oracle_sample;
+    * continuous: Eq. 15 on the whole maps, and one field's convolution and
+      sums."""
+    import numpy as np
+    from oracle import conker_oracle as O
+
+    g = w["grid"]
+    nc = int(np.prod(g.n))
+    ns = len(w["shells"])
+    t0 = time.perf_counter()
+    if mode == "factorised":
+        rng = np.random.default_rng(5)
+        pick = np.stack([rng.integers(0, n, cells) for n in g.n], axis=1)
+        O.factorised_randoms_at(pick, g, **selection)
+        t_field = (time.perf_counter() - t0) * nc / cells
+        d = w["data"]
+        nd = max(1, d.n // 8)
+        t0 = time.perf_counter()
+        D, _ = O.grid_counts(d.x[:nd], d.y[:nd], d.z[:nd], g)
+        t_field += (time.perf_counter() - t0) * 8
+        F = D.astype(np.float64)
+        fields = 2
+        what = (f"oracle (numpy FP64, single thread): Eq. 7 at {cells} sampled cells (x{nc // cells}), "
+                f"gridding of 1/8 of the data (x8)")
+    else:
+        F = O.delta_field(maps[0], maps[1])
+        t_field = time.perf_counter() - t0
+        fields = 1
+        what = "oracle (numpy FP64, single thread): Eq. 15 on the whole maps"
+    offs = O.shell_offsets(w["shells"][ns // 2], w["width"], g.cell)
+    t0 = time.perf_counter()
+    W = O.convolve_fft(F, offs)
+    t_conv = time.perf_counter() - t0
+    t_sum = 0.0
+    for n in orders:
+        t0 = time.perf_counter()
+        O.product_sums(F, [W], n)
+        t_sum += (time.perf_counter() - t0) * math.comb(ns + n - 2, n - 1)
+    total = t_field + fields * (t_conv * ns + t_sum)
+    sample = what + (f", one shell's FFT convolution of one field and one multiset per order, scaled "
+                     f"(convolution x{fields * ns}, sums x multisets x{fields})")
+    return total * 1000.0, sample
+
+
 # ---------------------------------------------------------------------------
 
 def run_gb300(args):
@@ -420,7 +469,15 @@ def run_gb300(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
-        ms, sample = cpu_oracle_sample(w, orders)
+        if args.factorised:
+            sel = dict(n_tot=float(d.n), p_ang=sel_pa, p_z=sel_pz, z_lo=0.43, z_hi=0.70, z_max=0.75, h0=100.0,
+                       omega_m=0.307, omega_k=0.0, omega_l=0.693, c=300000.0)
+            ms, sample = cpu_oracle_mode_sample(w, orders, "factorised", selection=sel)
+        elif args.continuous:
+            ms, sample = cpu_oracle_mode_sample(w, orders, "continuous",
+                                                maps=(map_d.cpu().numpy(), map_r.cpu().numpy()))
+        else:
+            ms, sample = cpu_oracle_sample(w, orders)
         cpu = {"value": round(ms, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample,
                "wall_s": round(time.perf_counter() - t0, 1)}
 
@@ -599,8 +656,10 @@ def run_reference(args):
 
 def main():
     args = _args()
-    if args.diagonal or args.factorised or args.continuous:
+    if args.diagonal:
         args.no_e2e = args.no_cpu_baseline = args.no_plain = True
+    if args.factorised or args.continuous:
+        args.no_e2e = args.no_plain = True
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":
