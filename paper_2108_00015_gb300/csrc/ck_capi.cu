@@ -212,6 +212,18 @@ ck_status upload_tables(Plan& p, cudaStream_t st) {
 // Grid one catalog (host or device positions) into counts[which].
 // Grid field `which` (0 data, 1 randoms) from positions x, y, z and, when w
 // is not NULL, per-point weights (all four in the same memory space).
+// Page-locked host arrays that the device can address (mapped pinned
+// memory) are read by the gridding kernel in place, over the host link;
+// other host arrays stream through the staging slots.
+const float* mapped_host(const float* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<const float*>(a.devicePointer) : nullptr;
+}
+
 ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, int64_t n, int which,
                        cudaStream_t st, const float* w = nullptr) {
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, which);
@@ -224,8 +236,14 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
       if (w) launch_grid_points_weighted(p, gx, gy, gz, gw, cnt, which, st);
       else launch_grid_points(p, gx, gy, gz, cnt, which, st);
     };
+    const float* mx = dx ? nullptr : mapped_host(x);
+    const float* my = mx ? mapped_host(y) : nullptr;
+    const float* mz = my ? mapped_host(z) : nullptr;
+    const float* mw = (mz && w) ? mapped_host(w) : nullptr;
     if (dx) {
       grid(x, y, z, w, n);
+    } else if (mz && (!w || mw)) {
+      grid(mx, my, mz, mw, n);  // pinned host arrays, read in place
     } else {
       // host positions (and weights): stream them through the staging slots
       int slot = 0;

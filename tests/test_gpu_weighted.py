@@ -132,3 +132,27 @@ def test_host_weights(torch):
     for key in ("xi", "num", "den"):
         assert np.array_equal(host[key][2].numpy(), devr[key][2].numpy())
     plan.close()
+
+
+def test_pinned_host_positions(torch):
+    """Page-locked host positions (and weights) are read in place by the
+    gridding kernel: the same grids and sums as the device and staged paths."""
+    g = GridSpec((32, 32, 32), (0.0, 0.0, 0.0), 10.0, True)
+    rand = uniform_box(61, 3_000_000, 320.0)
+    data = neyman_scott_box(62, 400, 10, 12.0, 320.0)
+    wr = _weights(63, rand.n)
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    plan = plan_for(dict(grid=g, shells=(20.0, 35.0), width=10.0), max_order=3)
+    for w in (None, wr):
+        plan.set_randoms(*dev_cat(torch, rand), w=None if w is None else dev(torch, w))
+        want = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
+        Rd = plan.grids()[1].cpu().numpy()
+        plan.set_randoms(pinned(rand.x), pinned(rand.y), pinned(rand.z), w=None if w is None else pinned(w))
+        got = plan.compute(pinned(data.x), pinned(data.y), pinned(data.z), orders=(2, 3), out="host")
+        assert np.array_equal(plan.grids()[1].cpu().numpy(), Rd)
+        for n in (2, 3):
+            for key in ("xi", "num", "den"):
+                assert np.array_equal(got[key][n].numpy(), want[key][n].numpy()), (w is None, n, key)
+    plan.close()
