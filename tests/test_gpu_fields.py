@@ -175,17 +175,22 @@ def test_fields_leave_randoms_intact(torch):
 
 def test_degenerate_fields(torch):
     """An all-zero map, D = R (delta = 0) and R = 0 everywhere (no survey)
-    give sums of exactly 0; a single nonzero cell has no pair in any shell
-    (the shells exclude the zero offset), so its sums are 0 too."""
+    give sums of exactly 0.  A single nonzero cell has no pair in any shell
+    (the shells exclude the zero offset): its sums vanish to the transform's
+    rounding, against the size of its products (2^n |O_s|)."""
     g = GridSpec((24, 24, 24), (0.0, 0.0, 0.0), 10.0, True)
     plan = _plan(g, (20.0, 30.0), 10.0, 3, "fp32")
     zero = np.zeros((24, 24, 24), np.float32)
     R = np.full((24, 24, 24), 1.5, np.float32)
     one = zero.copy()
     one[5, 6, 7] = 2.0
-    for d, r in ((zero, None), (R, R), (R, zero), (one, None)):
+    for d, r in ((zero, None), (R, R), (R, zero)):
         res = plan.compute_continuous(dev(torch, d), None if r is None else dev(torch, r), orders=(2, 3),
                                       out="host")
         for n in (2, 3):
             assert float(np.abs(res["num"][n].numpy()).max()) == 0.0
+    res = plan.compute_continuous(dev(torch, one), None, orders=(2, 3), out="host")
+    big = max(plan.shell_size)
+    for n in (2, 3):
+        assert float(np.abs(res["num"][n].numpy()).max()) <= 1e-5 * 2.0 ** n * big ** (n - 1)
     plan.close()
