@@ -4,8 +4,9 @@
 // and Eqs. 4-6, X = r cos(dec) cos(ra), Y = r cos(dec) sin(ra), Z = r sin(dec).
 //  * sky_table_kernel: r(z) on SK_NT + 1 equally spaced nodes of [0, z_max]:
 //    each thread integrates one interval by 8-point Gauss-Legendre
-//    quadrature (FP64; the nodes and weights come from the host), one thread
-//    then adds the intervals in order (the same table from run to run);
+//    quadrature (FP64; the nodes and weights come from the host);
+//  * sky_scan_kernel: one block forms the cumulative sums in a fixed order
+//    (runs per thread, then shuffle scans), the same table from run to run;
 //  * sky_points_kernel: per point, r(z) by cubic Hermite interpolation
 //    between the two nodes around z (values and exact derivatives
 //    c / (H0 E)), then the angles (degrees, sincospi in FP64); float32
@@ -23,18 +24,18 @@
 //  * factorised_fast_kernel: per cell in float32 (z and dz/dr by linear
 //    interpolation in r, the angles by atan2f); a cell whose r, z or angle
 //    lies within a margin of a decision edge (r(z_max), z_lo, z_hi, a bin
-//    edge) larger than the float32 error bound is queued instead;
-//  * factorised_slow_kernel: the queued cells by the FP64 path
-//    (cell_value_fp64), whose decisions follow a plain FP64 evaluation's
-//    operation order, so every bin decision is the FP64 one;
+//    edge) larger than the float32 error bound is marked and queued instead;
+//  * factorised_slow_kernel: the queued cells (or, if the queue overflowed,
+//    every marked cell) by the FP64 path (cell_value_fp64), whose decisions
+//    follow a plain FP64 evaluation's operation order, so every bin decision
+//    is the FP64 one;
 //  * factorised_reduce_kernel + factorised_total_kernel: the field's total,
 //    nonzero cells and bounding box from the stored cells, per block in a
 //    fixed order, then the blocks in order (the same total every run).
 // Values: float32 cells within 13 float32 roundings (8e-7 relative) of the
 // FP64 definition; FP64-path cells within one rounding.
-#include <math.h>
-
 #include <limits.h>
+#include <math.h>
 
 #include <algorithm>
 
