@@ -31,3 +31,18 @@ def test_workload_scaled():
     w = workload("periodic32")
     assert w["data"].n == 5000 and w["randoms"].n == 50000
     assert w["grid"].n == (32, 32, 32)
+
+
+def test_continuous_maps():
+    """Seeded maps: the same arrays for the same seed; R is 1..2 inside the
+    footprint and 0 outside; D is non-negative and 0 where R is 0."""
+    from synth import continuous_maps
+    a = continuous_maps(4, (12, 10, 8), 10.0)
+    b = continuous_maps(4, (12, 10, 8), 10.0)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    D, R = a
+    assert D.shape == R.shape == (12, 10, 8) and D.dtype == R.dtype == np.float32
+    inside = R > 0
+    assert 0.1 < inside.mean() < 0.9
+    assert float(R[inside].min()) >= 1.0 and float(R[inside].max()) <= 2.0
+    assert float(D.min()) >= 0.0 and float(np.abs(D[~inside]).max()) == 0.0
