@@ -2,7 +2,11 @@
  * conker.h -- C ABI of a GB300 (sm_103a) implementation of the ConKer
  * n-point correlation hot path (arXiv 2108.00015): mapping (Sec. 2.2),
  * spherical-shell kernels (Sec. 2.3), FFT convolution (Sec. 2.4, Eqs. 9-10)
- * and n-point summation (Sec. 2.5, Eqs. 11-14) for n = 2..5.
+ * and n-point summation (Sec. 2.5, Eqs. 11-14) for n = 2..5.  Around it:
+ * weighted catalogs, zero-padded survey boxes, the equidistant functions
+ * (Sec. 2.6), sky coordinates and factorised randoms (Sec. 2.2, Eqs. 3-7),
+ * continuous fields and cross-correlation (Secs. 2.7-2.8), per-cell maps
+ * (Sec. 4.2) and a batched form.
  *
  * Conventions for every entry point
  *   - Every function returns a ck_status; no exception or abort crosses the
@@ -10,6 +14,9 @@
  *   - "device" pointers are CUDA device memory (e.g. a torch CUDA tensor's
  *     data_ptr()); "host or device" pointers are detected with
  *     cudaPointerGetAttributes, and host memory may be pageable or pinned.
+ *     Pinned host positions that the device can address are read in place
+ *     by the gridding kernel, after the call returns: keep them unchanged
+ *     until the stream's work is done, as for any asynchronous copy.
  *   - The caller owns every input and output buffer.  The plan owns its
  *     workspace unless the caller passes one to ck_plan_create.
  *   - Work is ordered on the caller's CUDA stream (NULL = legacy default
