@@ -149,8 +149,12 @@ def test_pinned_host_positions(torch):
         plan.set_randoms(*dev_cat(torch, rand), w=None if w is None else dev(torch, w))
         want = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
         Rd = plan.grids()[1].cpu().numpy()
-        plan.set_randoms(pinned(rand.x), pinned(rand.y), pinned(rand.z), w=None if w is None else pinned(w))
-        got = plan.compute(pinned(data.x), pinned(data.y), pinned(data.z), orders=(2, 3), out="host")
+        # the pinned arrays are read after the calls return: keep them alive
+        hr = [pinned(rand.x), pinned(rand.y), pinned(rand.z)]
+        hw = None if w is None else pinned(w)
+        hd = [pinned(data.x), pinned(data.y), pinned(data.z)]
+        plan.set_randoms(*hr, w=hw)
+        got = plan.compute(*hd, orders=(2, 3), out="host")
         assert np.array_equal(plan.grids()[1].cpu().numpy(), Rd)
         for n in (2, 3):
             for key in ("xi", "num", "den"):
