@@ -432,6 +432,17 @@ ck_status ck_contract(ck_plan* plan, const float* w0, const float* bank, int64_t
 ck_status ck_contract_static(const float* w0, const float* bank, int64_t bank_stride, int64_t n_cells,
                              int32_t n_shells, int32_t order_mask, double* const* sums, void* stream);
 
+/* Test hook for the failure path of the bounded device waits (the paper has
+ * no counterpart): sets, on the current device, the wall-time limit in
+ * nanoseconds of the waits in which the summation's register kernel (used by
+ * ck_contract for plain plans and by ck_contract_static) waits for its
+ * staged cell chunks; ns <= 0 restores the default of 2 s.  With a limit
+ * shorter than a chunk's copy time a launch gives up: it records
+ * CK_ERR_TIMEOUT (the plan's status word, or NaN outputs for
+ * ck_contract_static), waits with the default limit for the copies it has
+ * issued, and returns.  Synchronous (cudaMemcpyToSymbol). */
+ck_status ck_debug_set_wait_limit(int64_t ns);
+
 /* --- per-stage device timing --------------------------------------------------
  * When enabled, the library records a CUDA event pair on the caller's stream
  * around every kernel it launches, grouped by stage, together with the

@@ -125,6 +125,7 @@ _SIGS = [
     ("ck_contract", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P), _P]),
     ("ck_contract_static", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(_P), _P]),
+    ("ck_debug_set_wait_limit", ctypes.c_int, [ctypes.c_int64]),
     ("ck_profile_enable", ctypes.c_int, [_P, ctypes.c_int32]),
     ("ck_profile_read", ctypes.c_int, [_P, ctypes.POINTER(_StageTimes)]),
     ("ck_stage_name", ctypes.c_char_p, [ctypes.c_int32]),
@@ -220,6 +221,12 @@ def contract_static(w0, bank, bank_stride: int, n_cells: int, n_shells: int, ord
     _check(_lib().ck_contract_static(_ptr(w0), _ptr(bank), int(bank_stride), int(n_cells), int(n_shells),
                                      order_mask(orders), arr, _stream_ptr(stream)), "ck_contract_static")
     return sums
+
+
+def set_wait_limit(ns: int = 0):
+    """ck_debug_set_wait_limit: shorten (ns > 0) or restore (ns <= 0) the
+    register contraction's consumer wait limit on the current device."""
+    _check(_lib().ck_debug_set_wait_limit(int(ns)), "ck_debug_set_wait_limit")
 
 
 def order_mask(orders: Iterable[int]) -> int:

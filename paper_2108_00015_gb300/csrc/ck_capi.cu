@@ -215,13 +215,19 @@ ck_status upload_tables(Plan& p, cudaStream_t st) {
 // Page-locked host arrays that the device can address (mapped pinned
 // memory) are read by the gridding kernel in place, over the host link;
 // other host arrays stream through the staging slots.
+// Only memory registered with the current device's context is read in place;
+// page-locked memory of another device's context goes through staging.
 const float* mapped_host(const float* h) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
-  return a.type == cudaMemoryTypeHost ? static_cast<const float*>(a.devicePointer) : nullptr;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return nullptr;
+  return a.type == cudaMemoryTypeHost && a.device == cur && a.devicePointer
+             ? static_cast<const float*>(a.devicePointer)
+             : nullptr;
 }
 
 ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, int64_t n, int which,
@@ -399,11 +405,12 @@ ck_status ck_plan_create(const ck_grid* grid, const ck_shells* shells, int32_t m
     delete p;
     return code;
   };
+  // a caller workspace smaller than the plan needs is refused before any CUDA call
+  if (workspace && workspace_bytes_in < need) return fail(CK_ERR_OOM);
   if (cudaGetDevice(&p->device) != cudaSuccess) return fail(CK_ERR_CUDA);
   if (cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
     return fail(CK_ERR_CUDA);
   if (workspace) {
-    if (workspace_bytes_in < need) return fail(CK_ERR_OOM);
     if (((uintptr_t)workspace & 255u) != 0 || !is_device_ptr(workspace)) return fail(CK_ERR_BAD_POINTER);
     p->ws = workspace;
     p->ws_bytes = workspace_bytes_in;

@@ -92,6 +92,11 @@ __host__ __device__ constexpr int outs_range(int ns, int a0, int a1) {
   return t;
 }
 
+// Wall-time limit of the consumer waits of contract_reg_kernel (the default
+// kWaitLimitNs unless ck_debug_set_wait_limit shortened it for a test of the
+// timeout path).  The producer's drain of copies in flight keeps the default.
+__device__ uint64_t g_consumer_wait_ns = kWaitLimitNs;
+
 // G = 1: every consumer thread keeps all outputs.  G = 2 (orders <= 3 only):
 // two groups of RK_CW consumer warps see every cell, each keeping the sums of
 // half of the shells, so twice as many warps fit with half the registers.
@@ -155,10 +160,11 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
 #pragma unroll
     for (int o = 0; o < NACC; ++o) acc[o] = 0.0f;
     int since = 0, done = 0;
+    const uint64_t limit = g_consumer_wait_ns;
     for (int it = 0; it < nit; ++it) {
       const int st = it % RK_STAGES;
       const uint32_t ph = (uint32_t)(it / RK_STAGES) & 1u;
-      if (!mbar_wait(&full[st], ph, status)) break;
+      if (!mbar_wait_for(&full[st], ph, status, limit)) break;
       const int64_t cell0 = (c0 + it) * RK_KC;
       const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
       const int64_t whole = rem / 4 * 4;
@@ -735,10 +741,17 @@ extern "C" ck_status ck_contract_static(const float* w0, const float* bank, int6
   const int reg_maxn = maxn <= 3 ? 3 : 5;
   const int nout = reg_nout(n_shells, reg_maxn);
   if ((size_t)ctas * nout + 1 > kStaticDoubles - 31) return CK_ERR_UNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // The array's device address, looked up with this device current.  Outside
+  // stream capture it is looked up on every call, so that a context created
+  // again (after cudaDeviceReset, say) never sees an address of the old one;
+  // under capture the address of the last uncaptured call is used.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return CK_ERR_CUDA;
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
       void* a = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&a, g_contract_scratch);
       if (e != cudaSuccess || !a) return CK_ERR_CUDA;
@@ -748,7 +761,6 @@ extern "C" ck_status ck_contract_static(const float* w0, const float* bank, int6
   }
   double* partials = static_cast<double*>(base);
   int* status = reinterpret_cast<int*>(partials + (size_t)ctas * nout);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return CK_ERR_CUDA;
   const int64_t nchunks = (n_cells + RK_KC - 1) / RK_KC;
   const int64_t cpc = (nchunks + ctas - 1) / ctas;
@@ -759,4 +771,9 @@ extern "C" ck_status ck_contract_static(const float* w0, const float* bank, int6
   static_reduce_kernel<<<(nout + 127) / 128, 128, 0, st>>>(partials, ctas, nout, n_shells, reg_maxn, status, o[2],
                                                            o[3], o[4], o[5]);
   return cuda_status(cudaGetLastError());
+}
+
+extern "C" ck_status ck_debug_set_wait_limit(int64_t ns) {
+  const uint64_t v = ns > 0 ? (uint64_t)ns : kWaitLimitNs;
+  return cuda_status(cudaMemcpyToSymbol(g_consumer_wait_ns, &v, sizeof(v)));
 }

@@ -69,17 +69,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete; give up after
-// kWaitLimitNs, record CK_ERR_TIMEOUT and return false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+// limit_ns of wall time, record CK_ERR_TIMEOUT and return false.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, int* status, uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+    if (globaltimer_ns() - t0 > limit_ns) {
       set_status(status, CK_ERR_TIMEOUT);
       return false;
     }
   }
+}
+
+// The same with the default limit, kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  return mbar_wait_for(bar, parity, status, kWaitLimitNs);
 }
 
 // Bulk (non-tensor) asynchronous copy global -> shared, completing on `bar`.

@@ -8,33 +8,36 @@
 // rows and a list of the columns that hold a canonical pair with one of
 // them (rows sorted by their last factor, so the late row tiles of order 5
 // need few columns), MMA N = the list length rounded up to 32; it is
-// accumulated in tensor memory.  A CTA owns one tile and a
-// range of cells (split-K), walked in chunks of 32 cells by three kinds of
-// warps that meet only on mbarriers (no block barrier per chunk):
-//  * warp 0 stages the W values of up to 8 chunks at once (W0 and the bank
+// accumulated in tensor memory.  A CTA owns one tile and a range of cells
+// (split-K), walked in chunks of KC cells (KC = 64 for TN <= 160, else 32)
+// by three kinds of warps that meet only on mbarriers (no block barrier per
+// chunk), 320 threads:
+//  * warp 0 stages the W values of 256 cells at a time (W0 and the bank
 //    rows, 1 KB each) with cp.async.bulk copies into two staging buffers
 //    (a copy of 128 bytes per row and chunk kept the copy engine busy
 //    longer than the tensor cores);
-//  * warps 2..17 build the split operands of a chunk: warp w owns A rows
-//    32 (w % 4) .. + 31 (its tensor-memory lane quarter) for a quarter of
-//    the chunk's cells and writes them with tcgen05.st into one of three A
-//    stages in tensor memory; together the sixteen warps write B into the
+//  * warps 2..9 (eight builders, two per tensor-memory lane quarter) build
+//    the split operands of a chunk: warp w owns A rows 32 (w % 4) .. + 31
+//    (its lane quarter) for half of the chunk's cells and writes them with
+//    tcgen05.st into one of NA A stages in tensor memory (NA = 2 for TN =
+//    128 and 160, else 3); together the eight warps write B into the
 //    matching shared-memory stage, in the no-swizzle K-major core layout of
 //    ck_umma.cuh (each warp's B addresses are fixed for the CTA and kept in
 //    registers; operands of padding rows and columns are zeroed once);
-//  * one thread of warp 1 issues, per chunk, 12 kind::tf32 MMAs (M = 128,
-//    N = TN, K = 8; A from tensor memory, B from shared memory) and commits
-//    them to the stage's mbarrier, which frees the stage for the builders.
+//  * one thread of warp 1 issues, per chunk, 3 KC / 8 kind::tf32 MMAs (24
+//    for KC = 64; M = 128, N = TN, K = 8; A from tensor memory, B from
+//    shared memory) and commits them to the stage's mbarrier, which frees
+//    the stage for the builders.
 // Every operand is split x = hi + lo, hi = x truncated to TF32 (exact),
 // lo = x - hi, and each 8-cell step issues hi*hi, hi*lo and lo*hi,
 // accumulating in FP32 in tensor memory; the dropped lo*lo term is below
-// 2^-21 relative.  Every 8 chunks (256 cells) close an accumulation group:
-// the builder warps drain its accumulator with tcgen05.ld into FP32
+// 2^-21 relative.  Every 256 cells (256 / KC chunks) close an accumulation
+// group: the builder warps drain its accumulator with tcgen05.ld into FP32
 // registers while the MMAs of the next group run into the second
-// accumulator (two accumulators where tensor memory holds them, else one,
-// drained before the next group starts).  Each CTA writes its FP32
-// register sums (at most 64 groups) as FP64 partials, reduced over the
-// splits in a fixed order.
+// accumulator (two accumulators where tensor memory holds them next to the
+// A stages, else one, drained before the next group starts).  Each CTA
+// writes its FP32 register sums (at most 64 groups) as FP64 partials,
+// reduced over the splits in a fixed order.
 // Waits are bounded: on a timeout a warp sets CK_ERR_TIMEOUT and stops;
 // before tensor memory is freed the MMA thread waits (bounded) for its last
 // commit and the staging warp for its copies in flight.

@@ -756,6 +756,71 @@ def check_product_map(o) -> bool:
     return bool(ok)
 
 
+# ---------------------------------------------------------------------------
+# boundary support and the xi rule (readings 4 and 7)
+
+def _wraps_distinct(offsets, n):
+    """Brute force: do the offsets stay pairwise distinct once every axis is
+    taken mod n?"""
+    seen = set()
+    for m in offsets:
+        key = tuple(int(m[a]) % int(n[a]) for a in range(3))
+        if key in seen:
+            return False
+        seen.add(key)
+    return True
+
+
+def check_periodic_support(o) -> bool:
+    """On each axis separately, offsets filling -m..m stay distinct after
+    wrapping exactly when 2m < n; the oracle's support test must give the
+    brute-force answer at n = 2m - 1, 2m, 2m + 1, with the other two axes
+    long enough not to matter (and of different lengths, so that an axis
+    mix-up shows)."""
+    for m in (2, 3, 5):
+        line = np.arange(-m, m + 1, dtype=np.int64)
+        for a in range(3):
+            off = np.zeros((line.size, 3), dtype=np.int64)
+            off[:, a] = line
+            # a second, shorter line on the next axis keeps the set 3D
+            short = np.zeros((3, 3), dtype=np.int64)
+            short[:, (a + 1) % 3] = (-1, 0, 1)
+            off = np.concatenate([off, short[[0, 2]]])
+            for n_a in (2 * m - 1, 2 * m, 2 * m + 1):
+                n = [4 * m + 3 + 2 * b for b in range(3)]
+                n[a] = n_a
+                want = _wraps_distinct(off, n)
+                if want != (2 * m < n_a):
+                    return False
+                if bool(o.check_periodic_support(off, n)) != want:
+                    return False
+    return True
+
+
+def check_xi_nonpositive_den(o) -> bool:
+    """Reading 7: xi = num / den where den > 0 and NaN where den <= 0, both
+    on given arrays and end to end: randoms in a single cell give B_s = 0 at
+    that cell for a shell that excludes the zero offset, so every den is
+    exactly 0 and every xi NaN, while the data's num stay finite."""
+    num = np.array([1.0, 2.0, -3.0, 4.0, 5.0])
+    den = np.array([2.0, 0.0, -1.0, 8.0, -0.0])
+    xi = o.xi_from(num, den)
+    if not (xi[0] == 0.5 and xi[3] == 0.5 and np.isnan(xi[1]) and np.isnan(xi[2]) and np.isnan(xi[4])):
+        return False
+    g = GridSpec((8, 8, 8), (0.0, 0.0, 0.0), 1.0, True)
+    one = lattice_catalog(g, np.array([[3, 4, 5]] * 4))
+    cells, data = _centre_points(g, 30, 17)
+    r = o.correlate(g, (2.0, 3.0), 1.0, data, one, orders=(2, 3), engine="direct")
+    for n in (2, 3):
+        if not np.all(r[f"den{n}"] == 0.0):
+            return False
+        if not np.all(np.isnan(r[f"xi{n}"])):
+            return False
+        if not np.all(np.isfinite(r[f"num{n}"])):
+            return False
+    return True
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
@@ -764,4 +829,5 @@ ALL_CHECKS = [
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
     check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights, check_sky_coordinates,
     check_factorised_randoms, check_delta_field, check_field_sums, check_product_map,
+    check_periodic_support, check_xi_nonpositive_den,
 ]

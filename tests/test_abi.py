@@ -156,3 +156,21 @@ def test_survey_workspace_fits(lib):
     code, banked = _ws(lib, prec=0, **kw)
     assert code == 0
     assert abs((banked - fused) - 15 * 512 ** 3 * 4) < 0.05e9
+
+
+def test_undersized_workspace(lib):
+    """A caller workspace smaller than ck_plan_workspace_size reports is
+    refused with CK_ERR_OOM before any CUDA call (the pointer is never
+    touched, so a placeholder address serves)."""
+    from paper_2108_00015_gb300.conker import _Grid, _Shells
+    g = _Grid((ctypes.c_int32 * 3)(32, 32, 32), (ctypes.c_double * 3)(0, 0, 0), 10.0, 1)
+    r = (ctypes.c_double * 2)(20.0, 40.0)
+    s = _Shells(2, r, 10.0, 0)
+    code, need = _ws(lib)
+    assert code == 0
+    out = ctypes.c_void_p(1)
+    f = lib.ck_plan_create
+    fake = ctypes.c_void_p(1 << 20)
+    assert f(ctypes.byref(g), ctypes.byref(s), 3, 0, fake, need - 1, None, ctypes.byref(out)) == 3
+    assert out.value is None
+    assert f(ctypes.byref(g), ctypes.byref(s), 3, 0, fake, 0, None, ctypes.byref(out)) == 3

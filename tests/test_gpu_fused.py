@@ -114,3 +114,27 @@ def test_fused_vs_unfused(torch):
         assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max()
     pf.close()
     pu.close()
+
+
+def test_fused_x512_every_order3_entry(torch):
+    """The survey step's fused kernel as it runs there: a 512-cell x axis
+    (half-length M = 256, the 16 x 16 register transform) with 16 shells
+    (no padded lines).  A periodic 512 x 24 x 20 box of unit cells keeps the
+    oracle fast; every order-2 and order-3 entry of num and den is compared,
+    normwise, with the oracle's FFT engine (itself pinned to the direct
+    convolution)."""
+    n = (512, 24, 20)
+    L = tuple(float(v) for v in n)
+    shells = tuple(1.0 + 0.45 * i for i in range(16))
+    g = GridSpec(n, (0.0, 0.0, 0.0), 1.0, True)
+    w = dict(grid=g, shells=shells, width=0.5, data=neyman_scott_box(71, 700, 10, 1.5, L),
+             randoms=uniform_box(72, 250_000, L))
+    ref = O.correlate(g, shells, w["width"], w["data"], w["randoms"], orders=(2, 3), engine="fft")
+    plan, res = _run(torch, w)
+    assert plan.fused
+    _check(res, ref, len(shells))
+    # and the same sums from the plain FP32 path on the same catalog
+    pu, ru = _run(torch, w, precision="fp32")
+    _check(ru, ref, len(shells))
+    pu.close()
+    plan.close()

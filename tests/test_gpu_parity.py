@@ -271,9 +271,11 @@ def test_reg_contraction_ragged(torch):
     plan.close()
 
 
-def test_survey_subbox_s16(torch):
-    """The 512^3 survey catalog cut to a 64^3 periodic sub-box (16 shells,
-    orders 2 and 3) against the oracle."""
+@pytest.mark.parametrize("precision", ["fp32", "split_tf32"])
+def test_survey_subbox_s16(torch, precision):
+    """The 512^3 survey catalog cut to a 64^3 periodic sub-box (12 of its
+    shells, orders 2 and 3) against the oracle, in the plain and the mixed
+    (fused) form."""
     w = workload("survey512", scale=0.25)
     lo = np.array([-256.0, -256.0, 1300.0])
     def cut(c):
@@ -284,7 +286,8 @@ def test_survey_subbox_s16(torch):
     sub = dict(grid=g, shells=w["shells"][:12], width=w["width"], data=cut(w["data"]), randoms=cut(w["randoms"]))
     assert sub["data"].n > 1000 and sub["randoms"].n > 100000
     ref = O.correlate(g, sub["shells"], sub["width"], sub["data"], sub["randoms"], orders=(2, 3), engine="fft")
-    plan, res = _run(torch, sub, (2, 3))
+    plan, res = _run(torch, sub, (2, 3), precision=precision)
+    assert plan.fused is (precision == "split_tf32")
     _check_sums(res, ref, len(sub["shells"]), (2, 3))
     plan.close()
 

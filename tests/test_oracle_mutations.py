@@ -140,6 +140,39 @@ def map_without_volume(W0, Ws, den2_s, n_box):
     return np.asarray(W0, np.float64) * np.asarray(Ws, np.float64) / den2_s
 
 
+_orig_support = O.check_periodic_support
+_orig_xi = O.xi_from
+
+
+def support_closed(offsets, n):
+    # 2 max|m| <= n instead of < n
+    if offsets.size == 0:
+        return True
+    m = np.abs(offsets).max(axis=0)
+    return bool(all(2 * int(m[a]) <= int(n[a]) for a in range(3)))
+
+
+def support_wrong_axis(offsets, n):
+    # every axis tested against the x length
+    return _orig_support(offsets, [n[0], n[0], n[0]])
+
+
+def xi_keeps_negative(num, den):
+    # NaN only where den == 0: a negative denominator gives a signed xi
+    num = np.asarray(num, np.float64)
+    den = np.asarray(den, np.float64)
+    out = np.full(num.shape, np.nan)
+    ok = den != 0
+    out[ok] = num[ok] / den[ok]
+    return out
+
+
+def xi_divides_anyway(num, den):
+    # no rule: num / den everywhere (inf or a signed value instead of NaN)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.asarray(num, np.float64) / np.asarray(den, np.float64)
+
+
 MUTANTS = [
     ("density_fields", wrong_sign_density),
     ("cell_index", off_by_one_index),
@@ -157,6 +190,10 @@ MUTANTS = [
     ("delta_field", delta_over_data),
     ("field_sums", cross_convolves_w0),
     ("product_map", map_without_volume),
+    ("check_periodic_support", support_closed),
+    ("check_periodic_support", support_wrong_axis),
+    ("xi_from", xi_keeps_negative),
+    ("xi_from", xi_divides_anyway),
 ]
 
 

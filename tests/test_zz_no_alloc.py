@@ -5,6 +5,8 @@ region) can still run the summation.  Checked through the C ABI against
 ck_contract (which uses plan workspace) on two calls in a row.  Kept in a
 file collected last, so that a run stopping at the first failure has
 already run every other test."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -33,14 +35,33 @@ def test_static_contraction_matches_plan_contraction(ns, orders):
     plan = plan_for(w, max_order=max(orders))
     tw0, tB = dev(torch, w0), dev(torch, B)
     want = plan.contract(tw0, tB, stride, orders=orders)
+    # outputs allocated up front, so that the calls below allocate nothing at all
+    got = {n: torch.full_like(want[n], float("nan")) for n in orders}
+    arr = (ctypes.c_void_p * (conker.CK_MAX_ORDER + 1))()
+    for n, t in got.items():
+        arr[n] = t.data_ptr()
+    lib = conker.load()
+    torch.cuda.synchronize()
     for call in range(2):  # the shared scratch keeps the previous call's contents
-        got = conker.contract_static(tw0, tB, stride, nc, ns, orders=orders)
+        if call == 1:
+            torch.cuda.synchronize()
+            free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        code = lib.ck_contract_static(tw0.data_ptr(), tB.data_ptr(), stride, nc, ns, conker.order_mask(orders),
+                                      arr, None)
+        assert code == 0
         torch.cuda.synchronize()
+        if call == 1:
+            # the second call leaves device memory exactly as it found it
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
         for n in orders:
             ref, aref = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
             a = got[n].cpu().numpy()
-            assert normwise(a, want[n].cpu().numpy(), aref) <= TOL, f"call {call} order {n}"
+            # the same register kernel, CTA count and fixed-order reduction as
+            # the plan's contraction: the sums are identical bit for bit
+            assert torch.equal(got[n], want[n]), f"call {call} order {n}"
             assert normwise(a, ref, aref) <= TOL, f"call {call} order {n} vs oracle"
+            got[n].fill_(float("nan"))
     plan.close()
 
 
