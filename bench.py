@@ -50,8 +50,9 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="split_tf32", choices=["split_tf32", "fp32"],
-                    help="headline form: mixed split-TF32 tensor-core sums (fused pass) or plain FP32")
+    ap.add_argument("--precision", default="split_tf32", choices=["split_tf32", "split_bf16", "split_fp16", "fp32"],
+                    help="headline form: mixed split-TF32 tensor-core sums (fused pass), split-BF16 or "
+                         "split-FP16 tensor-core sums (kind::f16, bank kept), or plain FP32")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form beside the headline")
     ap.add_argument("--diagonal", action="store_true",
                     help="time ck_set_randoms_diagonal + ck_compute_diagonal (Eq. 14, the (s, .., s) entries "
@@ -84,15 +85,17 @@ TF32_PER_BF16 = 1.1 / 2.25
 FALLBACK_BF16_SUSTAINED_TFLOPS = 1700.0
 
 
-def _tf32_peak():
-    """Sustained TF32 tensor peak: the measured sustained BF16 GEMM rate
-    times the nominal TF32/BF16 ratio (the contraction is timed inside a
-    long step)."""
+def _tensor_peak(precision):
+    """Sustained dense tensor peak of the contraction's operand kind: the
+    measured sustained BF16 GEMM rate (BF16 and FP16 operands run at the same
+    dense rate), times the nominal TF32/BF16 ratio for TF32 operands (the
+    contraction is timed inside a long step)."""
+    ratio = TF32_PER_BF16 if precision == "split_tf32" else 1.0
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops_sustained"]) * TF32_PER_BF16, "measured"
+            return float(json.load(f)["bf16_tflops_sustained"]) * ratio, "measured"
     except Exception:
-        return FALLBACK_BF16_SUSTAINED_TFLOPS * TF32_PER_BF16, "fallback"
+        return FALLBACK_BF16_SUSTAINED_TFLOPS * ratio, "fallback"
 
 
 def _tc_work(ns, orders):
@@ -416,19 +419,20 @@ def run_gb300(args):
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": dv["bytes"] / dv["launches"],
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
-    if dname == "contract" and args.precision == "split_tf32" and not plan.fused and not args.diagonal:
-        # the tcgen05 blocked product: three split TF32 products per operand pair
+    if dname == "contract" and args.precision.startswith("split_") and not plan.fused and not args.diagonal:
+        # the tcgen05 blocked product: three split products per operand pair
         dense, useful = _tc_work(len(w["shells"]), orders)
         nc = int(np.prod(w["grid"].n))
         flops = 3 * 2 * dense * nc
         t_launch = dv["ms"] / dv["launches"] * 1e-3
-        tpk, tkind = _tf32_peak()
+        tpk, tkind = _tensor_peak(args.precision)
         roofline = {"bound": "tensor", "kernel": dname, "achieved": round(flops / t_launch / 1e12, 1),
                     "peak": round(tpk, 1), "unit": "TFLOP/s", "frac": round(flops / t_launch / 1e12 / tpk, 4),
                     "traffic": None, "algorithmic_flops_per_launch": flops,
                     "useful_tflops": round(2 * useful * nc / t_launch / 1e12, 1),
                     "peak_source": (f"{tkind}: MEASURED_PEAKS.json bf16_tflops_sustained x {TF32_PER_BF16:.3f} "
-                                    "(nominal TF32/BF16 ratio)")}
+                                    "(nominal TF32/BF16 ratio)" if args.precision == "split_tf32" else
+                                    f"{tkind}: MEASURED_PEAKS.json bf16_tflops_sustained (dense BF16/FP16 rate)")}
     fft_names = [k for k in stages if k.startswith("fft_") or k == "x_c2r_contract"]
     fft_bytes = sum(stages[k]["bytes"] for k in fft_names)
     fft_ms = sum(stages[k]["ms"] for k in fft_names)
@@ -519,7 +523,7 @@ def run_gb300(args):
         "metric": METRIC, "value": round(value, 4), "unit": "ms/catalog", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 FFT, split-tf32 sums" if precision == "split_tf32" else "f32",
+        "dtype": f"f32 FFT, {precision.replace('_', '-')} sums" if precision != "fp32" else "f32",
         "data": "synthetic: seeded Neyman-Scott catalog with a lognormal-biased parent field in a survey-shell "
                 "mask and uniform randoms (stand-in for SDSS DR12 CMASS + randoms)",
         "config": {"workload": args.workload, "grid": list(g.n), "cell": g.cell, "periodic": g.periodic,
@@ -608,7 +612,7 @@ def run_batch(args):
         "metric": METRIC, "value": round(value, 4), "unit": "ms/catalog", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_b / args.steps, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 FFT, split-tf32 sums" if args.precision == "split_tf32" else "f32",
+        "dtype": f"f32 FFT, {args.precision.replace('_', '-')} sums" if args.precision != "fp32" else "f32",
         "data": "synthetic: 64 seeded Neyman-Scott mocks in 8 periodic grid classes, one uniform random "
                 "catalog of 10M per class",
         "config": {"workload": "batch64", "classes": [list(c["grid"].n[:1]) + [c["grid"].cell] for c in w["classes"]],

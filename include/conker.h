@@ -366,6 +366,25 @@ typedef struct ck_catalog {
 ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_catalog* cats, int32_t n_cats,
                            int32_t order_mask, const ck_outputs* out, void* stream);
 
+/* Region of a catalog decomposed into slabs along z (Sec. 4: regions are
+ * combined by adding the numerators and the denominators of Eq. 11 before
+ * dividing, Eq. 19).  After this call the plan's sums run over the cells of
+ * the box planes z_begin <= z < z_end only (the owned planes): the whole
+ * box is still gridded and convolved, so planes outside the region act as
+ * the halo that the kernels reach into, and only W_0 = N (and B_0 = Rt) is
+ * restricted to the region.  alpha > 0 replaces sum D / sum R in
+ * N = D - alpha R and Rt = alpha R, since every region of one catalog needs
+ * the alpha of the whole catalog; 0 keeps the plan's own ratio.  With a box
+ * of owned planes plus halos at least max_offset[2] planes deep (clipped at
+ * the catalog's faces) on a CK_GRID_PADDED plan (zero outside the box), the
+ * regions' num and den add up to the undivided catalog's.  Applies to
+ * ck_set_randoms, ck_compute and their weighted forms; call ck_set_randoms
+ * again afterwards (the cached denominators are dropped, and so are the
+ * captured graphs of ck_batch_compute).  z_begin = 0, z_end = n[2],
+ * alpha = 0 restores the whole box.  CK_ERR_ARG for an empty or
+ * out-of-box range or a negative or non-finite alpha.  Host only. */
+ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, double alpha);
+
 /* Synchronise `stream` and return (and clear) the plan's device status. */
 ck_status ck_plan_status(ck_plan* plan, void* stream);
 
@@ -433,15 +452,16 @@ ck_status ck_contract_static(const float* w0, const float* bank, int64_t bank_st
                              int32_t n_shells, int32_t order_mask, double* const* sums, void* stream);
 
 /* Test hook for the failure path of the bounded device waits (the paper has
- * no counterpart): sets, on the current device, the wall-time limit in
- * nanoseconds of the waits in which the summation's register kernel (used by
- * ck_contract for plain plans and by ck_contract_static) waits for its
- * staged cell chunks; ns <= 0 restores the default of 2 s.  With a limit
- * shorter than a chunk's copy time a launch gives up: it records
- * CK_ERR_TIMEOUT (the plan's status word, or NaN outputs for
- * ck_contract_static), waits with the default limit for the copies it has
- * issued, and returns.  Synchronous (cudaMemcpyToSymbol). */
-ck_status ck_debug_set_wait_limit(int64_t ns);
+ * no counterpart).  ns > 0: on the current device, every consumer warp of
+ * the summation's register kernel (used by ck_contract for plain plans and
+ * by ck_contract_static) first waits, with a limit of ns nanoseconds, on an
+ * mbarrier that nothing arrives at.  The wait runs out, so each launch
+ * records CK_ERR_TIMEOUT (in the plan's status word; ck_contract_static
+ * returns NaN sums instead), consumes no staged chunk, waits with the
+ * default limit (2 s) for the copies it has issued, and returns: no fault,
+ * no hang, and the context stays usable.  ns <= 0 restores normal
+ * operation.  Synchronous (cudaMemcpyToSymbol). */
+ck_status ck_debug_force_timeout(int64_t ns);
 
 /* --- per-stage device timing --------------------------------------------------
  * When enabled, the library records a CUDA event pair on the caller's stream

@@ -116,6 +116,7 @@ _SIGS = [
     ("ck_batch_compute", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_Catalog), ctypes.c_int32,
                                         ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_plan_status", ctypes.c_int, [_P, _P]),
+    ("ck_plan_set_region", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
     ("ck_get_grids", ctypes.c_int, [_P, _P, _P, _P]),
     ("ck_get_field", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     ("ck_get_bank", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
@@ -125,7 +126,7 @@ _SIGS = [
     ("ck_contract", ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(_P), _P]),
     ("ck_contract_static", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(_P), _P]),
-    ("ck_debug_set_wait_limit", ctypes.c_int, [ctypes.c_int64]),
+    ("ck_debug_force_timeout", ctypes.c_int, [ctypes.c_int64]),
     ("ck_profile_enable", ctypes.c_int, [_P, ctypes.c_int32]),
     ("ck_profile_read", ctypes.c_int, [_P, ctypes.POINTER(_StageTimes)]),
     ("ck_stage_name", ctypes.c_char_p, [ctypes.c_int32]),
@@ -223,10 +224,11 @@ def contract_static(w0, bank, bank_stride: int, n_cells: int, n_shells: int, ord
     return sums
 
 
-def set_wait_limit(ns: int = 0):
-    """ck_debug_set_wait_limit: shorten (ns > 0) or restore (ns <= 0) the
-    register contraction's consumer wait limit on the current device."""
-    _check(_lib().ck_debug_set_wait_limit(int(ns)), "ck_debug_set_wait_limit")
+def force_timeout(ns: int = 0):
+    """ck_debug_force_timeout: make the register contraction's consumer waits
+    run out after ns nanoseconds on an mbarrier nothing arrives at (ns > 0),
+    or restore normal operation (ns <= 0), on the current device."""
+    _check(_lib().ck_debug_force_timeout(int(ns)), "ck_debug_force_timeout")
 
 
 def order_mask(orders: Iterable[int]) -> int:
@@ -449,6 +451,11 @@ class Plan:
         if code not in (0, 7):  # a zero denominator still fills the outputs (NaN there)
             raise CkError(code, "ck_compute_diagonal")
         return res
+
+    def set_region(self, z_begin: int, z_end: int, alpha: float = 0.0):
+        """ck_plan_set_region: sums over box planes z_begin <= z < z_end,
+        with the whole catalog's alpha (> 0) for a region of a decomposition."""
+        _check(_lib().ck_plan_set_region(self._h, int(z_begin), int(z_end), float(alpha)), "ck_plan_set_region")
 
     def status(self, stream=None) -> int:
         return int(_lib().ck_plan_status(self._h, _stream_ptr(stream)))

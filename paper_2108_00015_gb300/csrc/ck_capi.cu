@@ -130,6 +130,8 @@ ck_status carve(Plan& p) {
   p.dense = reinterpret_cast<double*>(take((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8));
   p.dense_map = reinterpret_cast<int*>(take((size_t)std::max<int64_t>(p.dense_total, 1) * 4));
   p.table_arena = take(p.table_arena_cap);
+  p.support = reinterpret_cast<int*>(take(6 * 4));
+  p.absmax = reinterpret_cast<unsigned*>(take((size_t)(CK_MAX_SHELLS + 1) * 4));
   const size_t used = (size_t)(b - static_cast<unsigned char*>(p.ws));
   return used <= p.ws_bytes ? CK_OK : CK_ERR_OOM;
 }
@@ -277,9 +279,19 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
 // bank and the contraction kernels, or in one fused pass (fused plans, which
 // always form every order up to max_order).
 // W_0 is the transformed field itself, or w0 when given (cross-correlation).
+// With a region set (ck_plan_set_region), W_0 = the field restricted to the
+// region's planes: the whole field is transformed (the halo enters the
+// convolution), then the planes outside the region are zeroed.
 ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, const float* w0 = nullptr) {
   if (!w0) w0 = p.field;
   launch_fft_forward(p, p.field, p.spec, st);
+  if (p.region && w0 == p.field) {
+    const size_t plane = (size_t)p.grid.n[0] * p.grid.n[1];
+    if (p.region_z0 > 0) CK_TRY(cudaMemsetAsync(p.field, 0, plane * p.region_z0 * sizeof(float), st));
+    if (p.region_z1 < p.grid.n[2])
+      CK_TRY(cudaMemsetAsync(p.field + plane * p.region_z1, 0, plane * (p.grid.n[2] - p.region_z1) * sizeof(float),
+                             st));
+  }
   if (p.fused) return launch_convolve_contract(p, w0, sums, st);
   launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
   return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st);
@@ -723,6 +735,27 @@ ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_cata
     }
     return first;
   }
+  return CK_OK;
+}
+
+ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, double alpha) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (z_begin < 0 || z_end <= z_begin || z_end > p.box_n[2]) return CK_ERR_ARG;
+  if (!(alpha >= 0.0) || !isfinite(alpha)) return CK_ERR_ARG;
+  p.region = !(z_begin == 0 && z_end == p.box_n[2] && alpha == 0.0);
+  p.region_z0 = z_begin;
+  p.region_z1 = z_end;
+  p.region_alpha = alpha;
+  // the captured compute graphs hold the previous setting
+  for (auto& g : p.gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  // den_raw of the randoms set so far summed over other planes
+  p.have_randoms = false;
+  p.have_randoms_diag = false;
   return CK_OK;
 }
 

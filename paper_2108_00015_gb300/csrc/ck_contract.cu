@@ -92,10 +92,12 @@ __host__ __device__ constexpr int outs_range(int ns, int a0, int a1) {
   return t;
 }
 
-// Wall-time limit of the consumer waits of contract_reg_kernel (the default
-// kWaitLimitNs unless ck_debug_set_wait_limit shortened it for a test of the
-// timeout path).  The producer's drain of copies in flight keeps the default.
-__device__ uint64_t g_consumer_wait_ns = kWaitLimitNs;
+// Test of the timeout path (ck_debug_force_timeout): when nonzero, every
+// consumer warp of contract_reg_kernel first waits, with this limit in ns,
+// on an mbarrier that nothing arrives at, so it gives up, records
+// CK_ERR_TIMEOUT and consumes nothing; the producer's waits and its drain of
+// the copies in flight keep the default limit.
+__device__ uint64_t g_force_timeout_ns = 0;
 
 // G = 1: every consumer thread keeps all outputs.  G = 2 (orders <= 3 only):
 // two groups of RK_CW consumer warps see every cell, each keeping the sums of
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)RK_STAGES * NARR * RK_KC * 4);
   uint64_t* empty = full + RK_STAGES;
   int* consumed_min = reinterpret_cast<int*>(empty + RK_STAGES);
-  double* wacc = reinterpret_cast<double*>(empty + RK_STAGES + 1);
+  uint64_t* never = empty + RK_STAGES + 1;  // armed by nobody (ck_debug_force_timeout)
+  double* wacc = reinterpret_cast<double*>(empty + RK_STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nchunks = (nc + RK_KC - 1) / RK_KC;
   const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], CWT);
     }
+    mbar_init(never, 1);
     *consumed_min = nit;
     fence_async_shared();
   }
@@ -160,11 +164,12 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
 #pragma unroll
     for (int o = 0; o < NACC; ++o) acc[o] = 0.0f;
     int since = 0, done = 0;
-    const uint64_t limit = g_consumer_wait_ns;
-    for (int it = 0; it < nit; ++it) {
+    const uint64_t forced = g_force_timeout_ns;
+    const int nrun = forced != 0 && !mbar_wait_for(never, 0u, status, forced) ? 0 : nit;
+    for (int it = 0; it < nrun; ++it) {
       const int st = it % RK_STAGES;
       const uint32_t ph = (uint32_t)(it / RK_STAGES) & 1u;
-      if (!mbar_wait_for(&full[st], ph, status, limit)) break;
+      if (!mbar_wait(&full[st], ph, status)) break;
       const int64_t cell0 = (c0 + it) * RK_KC;
       const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
       const int64_t whole = rem / 4 * 4;
@@ -221,7 +226,7 @@ constexpr int reg_groups() { return 1; }  // two groups measured slower (shared-
 
 template <int NS, int MAXN>
 static size_t reg_smem() {
-  return (size_t)RK_STAGES * (NS + 1) * RK_KC * 4 + (2 * RK_STAGES + 1) * 8 +
+  return (size_t)RK_STAGES * (NS + 1) * RK_KC * 4 + (2 * RK_STAGES + 2) * 8 +
          (size_t)RK_CW * reg_groups<NS, MAXN>() * RegOut<NS, MAXN>::total * 8;
 }
 
@@ -478,7 +483,9 @@ ck_status contract_prepare(Plan& p, int mask) {
   if ((mask >> 5) & 1)
     for (int k = 0; k < ns; ++k)
       for (int l = k; l < ns; ++l) cols.push_back(make_int2(k, l));  // sorted by (k, l)
-  c.use_tc = p.precision == CK_PREC_SPLIT_TF32;
+  c.use_tc = p.precision == CK_PREC_SPLIT_TF32 || p.precision == CK_PREC_SPLIT_BF16 ||
+             p.precision == CK_PREC_SPLIT_FP16;
+  c.um_kind = p.precision == CK_PREC_SPLIT_BF16 ? 1 : (p.precision == CK_PREC_SPLIT_FP16 ? 2 : 0);
   c.rows = (int)rows.size();
   c.cols = (int)cols.size();
   const size_t slot = p.table_arena_cap / (1 << (CK_MAX_ORDER + 1));
@@ -598,8 +605,9 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
     cudaError_t e;
     {
       ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, st);
-      e = launch_umma(c.um_tn, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
-                      c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, c.um_cps, p.partials, status, st);
+      e = launch_umma(c.um_tn, c.um_kind, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc,
+                      c.d_um_tiles, c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, c.um_cps, p.absmax, p.partials, status,
+                      st);
       if (e == cudaSuccess)
         e = launch_umma_thin(w0, bank, bstride, p.nc, p.ns, c.um_thin_rmax, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
                              c.d_um_cols, c.um_ntc, c.n_tiles - c.um_ntc, c.n_tiles, c.um_tn, c.splits, c.um_cps,
@@ -773,7 +781,7 @@ extern "C" ck_status ck_contract_static(const float* w0, const float* bank, int6
   return cuda_status(cudaGetLastError());
 }
 
-extern "C" ck_status ck_debug_set_wait_limit(int64_t ns) {
-  const uint64_t v = ns > 0 ? (uint64_t)ns : kWaitLimitNs;
-  return cuda_status(cudaMemcpyToSymbol(g_consumer_wait_ns, &v, sizeof(v)));
+extern "C" ck_status ck_debug_force_timeout(int64_t ns) {
+  const uint64_t v = ns > 0 ? (uint64_t)ns : 0;
+  return cuda_status(cudaMemcpyToSymbol(g_force_timeout_ns, &v, sizeof(v)));
 }

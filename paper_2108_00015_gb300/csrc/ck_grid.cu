@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __res
                                                            const uint32_t* __restrict__ R,
                                                            float* __restrict__ field, int64_t nc,
                                                            DevState* st, int periodic, int nx, int ny,
-                                                           int nz, int mx, int my, int mz) {
+                                                           int nz, int mx, int my, int mz, double alpha_fixed) {
   const unsigned long long kd = st->kept[0], kr = st->kept[1];
   const bool wd = st->weighted[0] != 0, wr = st->weighted[1] != 0;
   // totals: counts, exact weight sums (units of 2^-32), or FP64 field totals
@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __res
                                 : (double)kept;
   };
   const double td = total(0, kd), tr = total(1, kr);
-  const double alpha = tr > 0.0 ? td / tr : 0.0;
+  // a region of a decomposed catalog takes the alpha of the whole catalog
+  const double alpha = alpha_fixed > 0.0 ? alpha_fixed : (tr > 0.0 ? td / tr : 0.0);
   const float af = (float)alpha;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->alpha = alpha;
@@ -312,7 +313,7 @@ void launch_prepare_data(const Plan& p, cudaStream_t st) {
   ProfScope ps(p, ST_PREP, 12.0 * (double)p.nc, st);
   prepare_data_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(
       p.counts[0], p.counts[1], p.field, p.nc, p.dstate, p.grid.periodic ? 1 : 0, p.grid.n[0],
-      p.grid.n[1], p.grid.n[2], p.maxoff[0], p.maxoff[1], p.maxoff[2]);
+      p.grid.n[1], p.grid.n[2], p.maxoff[0], p.maxoff[1], p.maxoff[2], p.region_alpha);
 }
 
 void launch_grid_points_weighted(const Plan& p, const float* x, const float* y, const float* z, const float* w,

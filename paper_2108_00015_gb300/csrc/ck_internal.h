@@ -72,7 +72,8 @@ struct FftLen {
 struct ContractPlan {
   int order_mask = 0;
   bool use_reg = false;     // register-accumulator kernel (few outputs)
-  bool use_tc = false;      // blocked product on the tensor cores (split-TF32, tcgen05)
+  bool use_tc = false;      // blocked product on the tensor cores (split-TF32 / BF16 / FP16, tcgen05)
+  int um_kind = 0;          // tcgen05 operand kind: 0 TF32, 1 BF16, 2 FP16
   int um_tn = 0;            // tcgen05 tiles: 128 rows x at most um_tn columns
   int um_ntc = 0;           // tiles 0 .. um_ntc - 1 on the tensor cores, the rest thin (CUDA cores)
   int um_thin_rmax = 0;     // the most live rows of a thin tile
@@ -162,6 +163,8 @@ struct Plan {
   double* dense = nullptr;     // 3 x dense_total: xi, num, den staging
   int* dense_map = nullptr;    // packed per order: dense index -> multiset rank
   int* host_status_pinned = nullptr;
+  int* support = nullptr;      // [6] box of the cells where W_0 may be nonzero (pruned inverse passes)
+  unsigned* absmax = nullptr;  // [CK_MAX_SHELLS + 1] largest |W| per factor row (split-FP16 scales)
 
   ContractPlan cplan[1 << (CK_MAX_ORDER + 1)];
   bool cplan_ready[1 << (CK_MAX_ORDER + 1)] = {false};
@@ -184,6 +187,12 @@ struct Plan {
   int bank_fields = 0;      // real fields reserved in `bank`
   int device = 0;
   int sm_count = 0;
+  // Region of a decomposed catalog (ck_plan_set_region): the sums run over
+  // the box planes region_z0 <= z < region_z1 only; region_alpha > 0 is used
+  // in place of sum D / sum R.
+  int region_z0 = 0, region_z1 = 0;
+  bool region = false;
+  double region_alpha = 0.0;
 };
 
 // ---- host helpers (ck_plan.cu) ------------------------------------------------
@@ -253,9 +262,11 @@ int umma_tile_cols(int cols);
 int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count);
 // A tile is (first row, offset of its column list, MMA N <= tn, list length).
 // Tensor-core tiles 0 .. ntc - 1 of ntiles (the partials are pitched by ntiles).
-cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
+// kind: 0 split-TF32, 1 split-BF16, 2 split-FP16 (absmax: ns + 1 device
+// words for the FP16 scales, filled here).
+cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
-                        int ntc, int ntiles, int splits, int64_t cps, double* partials, int* status,
+                        int ntc, int ntiles, int splits, int64_t cps, unsigned* absmax, double* partials, int* status,
                         cudaStream_t st);
 // Thin tiles (at most kThinMaxOut outputs, kThinMaxCols columns) t0 .. t0 + nthin - 1 on the CUDA
 // cores in FP32, into the same partials layout (tile width tn).

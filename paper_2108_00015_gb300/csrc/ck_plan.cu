@@ -92,10 +92,9 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   for (int s = 0; s < shells->n_shells; ++s)
     if (!(shells->radius[s] > 0.0) || !finite(shells->radius[s])) return CK_ERR_ARG;
   if (max_order < 2 || max_order > CK_MAX_ORDER) return CK_ERR_ARG;
-  if (precision != CK_PREC_FP32 && precision != CK_PREC_FP64_SUM && precision != CK_PREC_SPLIT_TF32) {
-    if (precision == CK_PREC_SPLIT_BF16 || precision == CK_PREC_SPLIT_FP16) return CK_ERR_UNSUPPORTED;
+  if (precision != CK_PREC_FP32 && precision != CK_PREC_FP64_SUM && precision != CK_PREC_SPLIT_TF32 &&
+      precision != CK_PREC_SPLIT_BF16 && precision != CK_PREC_SPLIT_FP16)
     return CK_ERR_ARG;
-  }
   // The packed dense outputs must stay modest.
   int64_t dense = 1;
   for (int k = 1; k < max_order; ++k) dense *= shells->n_shells;
@@ -181,7 +180,9 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   // keep the bank need one 128 x TN tile of FP64 per tile and split of at
   // most 16384 cells (bounded here for any device of up to 256 SMs).
   p->partials_cap = (size_t)1 << 22;
-  if (precision == CK_PREC_SPLIT_TF32 && !p->fused) {
+  const bool tensor = precision == CK_PREC_SPLIT_TF32 || precision == CK_PREC_SPLIT_BF16 ||
+                      precision == CK_PREC_SPLIT_FP16;
+  if (tensor && !p->fused) {
     const int64_t ns = p->ns;
     const int64_t urows = 1 + (max_order >= 3 ? ns : 0) + (max_order >= 4 ? ns * (ns + 1) / 2 : 0);
     const int64_t ucols = ns + (max_order >= 5 ? ns * (ns + 1) / 2 : 0);
@@ -229,6 +230,8 @@ size_t workspace_bytes(const Plan& p) {
   b += al((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8);        // dense staging
   b += al((size_t)std::max<int64_t>(p.dense_total, 1) * 4);            // dense map
   b += al(p.table_arena_cap);
+  b += al(6 * 4);                                                       // support box of W_0
+  b += al((size_t)(CK_MAX_SHELLS + 1) * 4);                             // split-FP16 row maxima
   return b;
 }
 

@@ -44,6 +44,9 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "ck_device.cuh"
 #include "ck_internal.h"
 #include "ck_mma.cuh"
@@ -61,18 +64,31 @@ constexpr int UM_MAX_NW = 2;          // W staging buffers
 constexpr int UM_BWARPS = 8;          // builder warps: two per tensor-memory lane quarter
 constexpr int UM_THREADS = 32 * (2 + UM_BWARPS);
 
-// Per tile width TN: cells per chunk KC (64, or 32 where the operand stages
-// would not fit), operand stages NA, accumulators in tensor memory (two
-// where they fit next to the A stages in 512 columns, else one).
-template <int TN>
+// Operand kinds of the split product: TF32 (kind::tf32, K = 8 per MMA),
+// BF16 and FP16 (kind::f16, K = 16 per MMA, two values per 32-bit
+// tensor-memory column and per 4 bytes of a shared-memory core row).
+constexpr int UM_TF32 = 0, UM_BF16 = 1, UM_FP16 = 2;
+
+// FP16 operands are scaled by powers of two: each factor W by 2^-e with
+// max |W| <= 2^e, and every product by 2^14, so |A_p|, |B_q| <= 2^14 stay
+// inside the FP16 range; the partials are divided by the same exact scales.
+constexpr float UM_FP16_HEAD = 16384.0f;
+
+// Per tile width TN and kind: cells per chunk KC (64, or 32 where the TF32
+// operand stages would not fit), operand stages NA, accumulators in tensor
+// memory (two where they fit next to the A stages in 512 columns, else one).
+template <int TN, int KIND = UM_TF32>
 struct UmmaShape {
   static_assert(TN % 32 == 0 && TN >= 32 && TN <= 256, "N of the MMA, two column halves of 16s");
-  static constexpr int KC = TN <= 160 ? 64 : 32;
-  static constexpr int NK = KC / 8;                            // MMA k-steps per chunk
-  static constexpr int ACOLS = 2 * KC;                         // A stage: hi | lo
-  static constexpr int NA = (TN == 128 || TN == 160) ? 2 : 3;
+  static constexpr bool F16 = KIND != UM_TF32;
+  static constexpr int EB = F16 ? 2 : 4;                       // operand element bytes
+  static constexpr int KC = F16 ? 64 : (TN <= 160 ? 64 : 32);
+  static constexpr int KS = F16 ? 16 : 8;                      // cells per MMA k-step
+  static constexpr int NK = KC / KS;                           // MMA k-steps per chunk
+  static constexpr int ACOLS = F16 ? KC : 2 * KC;              // A stage columns: hi | lo
+  static constexpr int NA = F16 ? (TN == 256 ? 2 : 3) : ((TN == 128 || TN == 160) ? 2 : 3);
   static constexpr int G = UM_GCELLS / KC;                     // chunks per group
-  static constexpr size_t b_bytes = (size_t)TN * KC * sizeof(float);
+  static constexpr size_t b_bytes = (size_t)TN * KC * EB;
   static constexpr size_t stage_bytes = 2 * b_bytes;           // B hi | B lo
   static constexpr int nacc = 2 * TN + NA * ACOLS <= 512 ? 2 : 1;
   static constexpr int a_col0 = nacc * TN;
@@ -91,31 +107,75 @@ __host__ __device__ constexpr int um_wrows(int ns) { return ns + 3; }
 // rows at the same cell hit eight different bank groups
 __host__ __device__ constexpr int um_wpitch(int cells) { return cells + 4; }
 
-template <int TN>
+template <int TN, int KIND>
 size_t umma_smem(int ns, int wcells) {
-  using S = UmmaShape<TN>;
+  using S = UmmaShape<TN, KIND>;
   return S::NA * S::stage_bytes + (size_t)UM_MAX_NW * um_wrows(ns) * um_wpitch(wcells) * sizeof(float) +
-         (size_t)TN * sizeof(int4) + (2 * UM_MAX_NW + 2 * UM_MAX_NA + 4) * sizeof(uint64_t) + 16;
+         (size_t)TN * sizeof(int4) + (size_t)TN * sizeof(float) +
+         (2 * UM_MAX_NW + 2 * UM_MAX_NA + 4) * sizeof(uint64_t) + 16;
 }
 
 // Cells per staging buffer: the longest bulk copies that fit (256 cells =
 // 1 KB per row), a whole number of chunks, double-buffered.
-template <int TN>
+template <int TN, int KIND>
 int umma_wcells(int ns, size_t limit) {
-  using S = UmmaShape<TN>;
+  using S = UmmaShape<TN, KIND>;
   for (int c = 256; c >= S::KC; c /= 2)
-    if (umma_smem<TN>(ns, c) <= limit) return c;
+    if (umma_smem<TN, KIND>(ns, c) <= limit) return c;
   return 0;
 }
 
-template <int TN>
+// Power-of-two scale of one staged factor row for FP16 operands: 2^-e with
+// max |row| <= 2^e (maxima as float bits in absmax; row 0 = W0, 1 + s =
+// shell s); 1 for the ones row, for an all-zero row and for other kinds.
+template <int KIND>
+__device__ __forceinline__ float um_factor_scale(const unsigned* absmax, int row, int ones_row) {
+  if (KIND != UM_FP16 || row >= ones_row) return 1.0f;
+  const float mx = __uint_as_float(absmax[row]);
+  if (!(mx > 0.0f) || !(mx < 3.0e38f)) return 1.0f;
+  int e;
+  frexpf(mx, &e);
+  return ldexpf(1.0f, -e);
+}
+
+// Two 16-bit values (a in the low half) of the operand kind, from FP32.
+template <int KIND>
+__device__ __forceinline__ uint32_t um_pack2(float a, float b) {
+  if constexpr (KIND == UM_BF16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
+// x = hi + lo + r with hi, lo of the operand kind (round to nearest): the
+// packed pairs of hi and lo for (a, b).
+template <int KIND>
+__device__ __forceinline__ void um_split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = um_pack2<KIND>(a, b);
+  float ha, hb;
+  if constexpr (KIND == UM_BF16) {
+    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&hi);
+    ha = __low2float(h);
+    hb = __high2float(h);
+  } else {
+    const __half2 h = *reinterpret_cast<const __half2*>(&hi);
+    ha = __low2float(h);
+    hb = __high2float(h);
+  }
+  lo = um_pack2<KIND>(a - ha, b - hb);
+}
+
+template <int TN, int KIND>
 __global__ void __launch_bounds__(UM_THREADS, 1)
     contract_umma_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
                          int ns, int wcells, const int2* __restrict__ rowdesc, int rows,
                          const int2* __restrict__ coldesc, const int4* __restrict__ tiles,
                          const int* __restrict__ collist, int ntiles, int64_t cells_per_split,
-                         double* __restrict__ partials, int* status) {
-  using S = UmmaShape<TN>;
+                         const unsigned* __restrict__ absmax, double* __restrict__ partials, int* status) {
+  using S = UmmaShape<TN, KIND>;
   constexpr int KC = S::KC, NA = S::NA, G = S::G, NACC = S::nacc;
   constexpr int nw = UM_MAX_NW;
   // every shared-memory pointer derives from the array by pointer arithmetic
@@ -127,7 +187,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   const int wch = wcells / KC;  // chunks per staging buffer
   float* wsb = reinterpret_cast<float*>(um_smem + NA * S::stage_bytes);  // [nw][WR][wp]
   int4* fb = reinterpret_cast<int4*>(wsb + nw * WR * wp);                 // [TN] factor rows of B_q
-  uint64_t* bar = reinterpret_cast<uint64_t*>(fb + TN);
+  float* fsc = reinterpret_cast<float*>(fb + TN);                         // [TN] scale of B_q (FP16)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(fsc + TN);
   uint64_t* wfull = bar;                     // [nw] W staged (bulk-copy bytes)
   uint64_t* wempty = wfull + UM_MAX_NW;      // [nw] W read by the builder warps
   uint64_t* sfull = wempty + UM_MAX_NW;      // [NA] operands of a stage written
@@ -137,6 +198,8 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
   auto Bhi = [&](int s) { return reinterpret_cast<float*>(stages + s * S::stage_bytes); };
   auto Blo = [&](int s) { return reinterpret_cast<float*>(stages + s * S::stage_bytes + S::b_bytes); };
+  auto BhiB = [&](int s) { return stages + s * S::stage_bytes; };
+  auto BloB = [&](int s) { return stages + s * S::stage_bytes + S::b_bytes; };
   auto Ws = [&](int b) { return wsb + b * WR * wp; };
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -150,6 +213,10 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   for (int i = tid; i < TN; i += UM_THREADS) {
     const int2 d = i < tile.w ? coldesc[collist[tile.y + i]] : make_int2(-2, -2);
     fb[i] = d.x == -2 ? make_int4(ZERO, ONE, 0, 0) : make_int4(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0, 0);
+    fsc[i] = d.x == -2 ? 1.0f
+                       : um_factor_scale<KIND>(absmax, d.x >= 0 ? 1 + d.x : ONE, ONE) *
+                             um_factor_scale<KIND>(absmax, d.y >= 0 ? 1 + d.y : ONE, ONE) *
+                             (KIND == UM_FP16 ? UM_FP16_HEAD : 1.0f);
   }
   for (int i = tid; i < nw * wcells; i += UM_THREADS) {  // constant rows of every staging buffer
     float* w = Ws(i / wcells);
@@ -217,7 +284,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   } else if (warp == 1) {
     // ---- MMA issue (one thread)
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc_tf32(UM_M, tn);
+      const uint32_t idesc = KIND == UM_TF32 ? umma_idesc_tf32(UM_M, tn) : umma_idesc_f16(UM_M, tn, KIND == UM_BF16);
       const uint32_t b_lbo = (uint32_t)(tn / 8 * 128);
       bool ok = true;
       int last = -1;
@@ -229,15 +296,23 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
         if (!ok) break;
         tc_fence_after();
         const uint32_t dt = tbase + (uint32_t)(a * TN);
-        const uint32_t ah = tbase + (uint32_t)(S::a_col0 + s * S::ACOLS), al = ah + KC;
+        const uint32_t ah = tbase + (uint32_t)(S::a_col0 + s * S::ACOLS), al = ah + S::ACOLS / 2;
         const uint32_t bhs = smem_u32(Bhi(s)), bls = smem_u32(Blo(s));
 #pragma unroll
         for (int k = 0; k < S::NK; ++k) {
-          const uint32_t bo = 2 * k * b_lbo;  // two core columns (8 cells) per step
+          // two core columns per step (8 cells of TF32, 16 of BF16 / FP16);
+          // A advances by 8 tensor-memory columns either way
+          const uint32_t bo = 2 * k * b_lbo;
           const uint64_t dbh = umma_desc(bhs + bo, b_lbo, 128), dbl = umma_desc(bls + bo, b_lbo, 128);
-          umma_tf32_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
-          umma_tf32_ts(dt, ah + 8 * k, dbl, idesc, true);
-          umma_tf32_ts(dt, al + 8 * k, dbh, idesc, true);
+          if constexpr (KIND == UM_TF32) {
+            umma_tf32_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
+            umma_tf32_ts(dt, ah + 8 * k, dbl, idesc, true);
+            umma_tf32_ts(dt, al + 8 * k, dbh, idesc, true);
+          } else {
+            umma_f16_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
+            umma_f16_ts(dt, ah + 8 * k, dbl, idesc, true);
+            umma_f16_ts(dt, al + 8 * k, dbh, idesc, true);
+          }
         }
         umma_commit(&sempty[s]);
         if (c % G == G - 1 || c == nch - 1) umma_commit(&afull[a]);
@@ -253,12 +328,16 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     const int hf = bw >> 2;           // A: cells hf KC/2 .. + KC/2 - 1; drains: column half hf
     const int m = 32 * qd + lane;     // A row of this thread
     int ax, ay, az;                   // staged-row offsets of the three factors of A row m
+    float asc = 1.0f;                 // FP16: scale of A row m
     {
       const int p = tile.x + m;
       const int2 d = p < rows ? rowdesc[p] : make_int2(-2, -2);
       ax = (d.x == -2 ? ZERO : 0) * wp + hf * (KC / 2);
       ay = (d.x >= 0 ? 1 + d.x : ONE) * wp + hf * (KC / 2);
       az = (d.y >= 0 ? 1 + d.y : ONE) * wp + hf * (KC / 2);
+      if (KIND == UM_FP16 && d.x != -2)
+        asc = um_factor_scale<KIND>(absmax, 0, ONE) * um_factor_scale<KIND>(absmax, d.x >= 0 ? 1 + d.x : ONE, ONE) *
+              um_factor_scale<KIND>(absmax, d.y >= 0 ? 1 + d.y : ONE, ONE) * UM_FP16_HEAD;
     }
     const bool a_live = __any_sync(FULL, tile.x + m < rows);  // a lane quarter of padding rows stays zero
     const uint32_t tq = tbase + ((uint32_t)(32 * qd) << 16);
@@ -268,6 +347,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     // 8 r8 + rr, cell core 4 item + kq of the unit
     const int rr = lane & 7, kq = lane >> 3;
     int bu[S::UN], bv[S::UN];
+    float bsc[S::UN];  // FP16: scale of this lane's column of each unit
     bool b_live[S::UN], b_any[S::UN];
 #pragma unroll
     for (int j = 0; j < S::UN; ++j) {
@@ -278,6 +358,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       const int4 f = b_any[j] ? fb[8 * r8 + rr] : make_int4(ZERO, ONE, 0, 0);
       bu[j] = f.x * wp + (u & 1) * (KC / 2) + 4 * kq;
       bv[j] = f.y * wp + (u & 1) * (KC / 2) + 4 * kq;
+      bsc[j] = b_any[j] ? fsc[8 * r8 + rr] : 1.0f;
     }
     // floats: core (r8, kc), row rr of a B stage (kc = 4 item + kq)
     auto b_off = [&](int j, int item) {
@@ -285,14 +366,21 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       const int kc = (u & 1) * (KC / 8) + 4 * item + kq;
       return (kc * (tn / 8) + (u >> 1)) * 32 + rr * 4;
     };
+    // bytes, 16-bit kinds: 8 cells per core row, this lane's 4 cells in half of it
+    auto b_off16 = [&](int j, int item) {
+      const int u = bw + UM_BWARPS * j;
+      const int kc = (u & 1) * (KC / 16) + 2 * item + (kq >> 1);
+      return (kc * (tn / 8) + (u >> 1)) * 128 + rr * 16 + (kq & 1) * 8;
+    };
     // zero, once, the operands that no chunk writes
     if (!a_live) {
-      const uint32_t z[16] = {};
+      const uint32_t z[8] = {};
+      constexpr int hcols = S::ACOLS / 4;  // hi columns of this warp's half of the cells
       for (int s = 0; s < NA; ++s)
-        for (int i = 0; i < KC / 32; ++i) {
-          const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * S::ACOLS + hf * (KC / 2) + 16 * i);
-          tmem_st16(ta, z);
-          tmem_st16(ta + KC, z);
+        for (int i = 0; i < hcols / 8; ++i) {
+          const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * S::ACOLS + hf * hcols + 8 * i);
+          tmem_st8(ta, z);
+          tmem_st8(ta + S::ACOLS / 2, z);
         }
       tmem_wait_st();
     }
@@ -301,8 +389,13 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       if (b_any[j] && !b_live[j])
         for (int s = 0; s < NA; ++s)
           for (int i = 0; i < KC / 32; ++i) {
-            *reinterpret_cast<float4*>(Bhi(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4*>(Blo(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (KIND == UM_TF32) {
+              *reinterpret_cast<float4*>(Bhi(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+              *reinterpret_cast<float4*>(Blo(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+              *reinterpret_cast<uint2*>(BhiB(s) + b_off16(j, i)) = make_uint2(0u, 0u);
+              *reinterpret_cast<uint2*>(BloB(s) + b_off16(j, i)) = make_uint2(0u, 0u);
+            }
           }
     float mid[S::half];
 #pragma unroll
@@ -345,7 +438,38 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       float* bl = Blo(s);
 #pragma unroll
       for (int i = 0; i < KC / 32; ++i) {  // 16 cells per item
-        if (a_live) {  // A row m, 8 cells at a time: hi and lo into the stage's tensor-memory columns
+        if (a_live && KIND != UM_TF32) {  // A row m, 16 cells: packed hi and lo pairs
+          float v[16];
+#pragma unroll
+          for (int h8 = 0; h8 < 2; ++h8) {
+            const int o = 16 * i + 8 * h8;
+            const float4 x0 = *reinterpret_cast<const float4*>(w + ax + o);
+            const float4 x1 = *reinterpret_cast<const float4*>(w + ay + o);
+            const float4 x2 = *reinterpret_cast<const float4*>(w + az + o);
+            const float4 y0 = *reinterpret_cast<const float4*>(w + ax + o + 4);
+            const float4 y1 = *reinterpret_cast<const float4*>(w + ay + o + 4);
+            const float4 y2 = *reinterpret_cast<const float4*>(w + az + o + 4);
+            v[8 * h8 + 0] = x0.x * x1.x * x2.x;
+            v[8 * h8 + 1] = x0.y * x1.y * x2.y;
+            v[8 * h8 + 2] = x0.z * x1.z * x2.z;
+            v[8 * h8 + 3] = x0.w * x1.w * x2.w;
+            v[8 * h8 + 4] = y0.x * y1.x * y2.x;
+            v[8 * h8 + 5] = y0.y * y1.y * y2.y;
+            v[8 * h8 + 6] = y0.z * y1.z * y2.z;
+            v[8 * h8 + 7] = y0.w * y1.w * y2.w;
+          }
+          if constexpr (KIND == UM_FP16) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] *= asc;
+          }
+          uint32_t hi[8], lo[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) um_split2<KIND>(v[2 * e], v[2 * e + 1], hi[e], lo[e]);
+          const uint32_t ta = tq + (uint32_t)(S::a_col0 + s * S::ACOLS + (hf * (KC / 2) + 16 * i) / 2);
+          tmem_st8(ta, hi);
+          tmem_st8(ta + S::ACOLS / 2, lo);
+        }
+        if (a_live && KIND == UM_TF32) {  // A row m, 8 cells at a time: hi and lo into the stage's tensor-memory columns
 #pragma unroll
           for (int h8 = 0; h8 < 2; ++h8) {
             const int o = 16 * i + 8 * h8;
@@ -379,12 +503,27 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
 #pragma unroll
         for (int j = 0; j < S::UN; ++j)
           if (b_live[j]) {
-            const float p0 = u4[j].x * v4[j].x, p1 = u4[j].y * v4[j].y, p2 = u4[j].z * v4[j].z, p3 = u4[j].w * v4[j].w;
-            const float4 h = make_float4(__uint_as_float(tf32_trunc(p0)), __uint_as_float(tf32_trunc(p1)),
-                                         __uint_as_float(tf32_trunc(p2)), __uint_as_float(tf32_trunc(p3)));
-            const int off = b_off(j, i);
-            *reinterpret_cast<float4*>(bh + off) = h;
-            *reinterpret_cast<float4*>(bl + off) = make_float4(p0 - h.x, p1 - h.y, p2 - h.z, p3 - h.w);
+            float p0 = u4[j].x * v4[j].x, p1 = u4[j].y * v4[j].y, p2 = u4[j].z * v4[j].z, p3 = u4[j].w * v4[j].w;
+            if constexpr (KIND == UM_TF32) {
+              const float4 h = make_float4(__uint_as_float(tf32_trunc(p0)), __uint_as_float(tf32_trunc(p1)),
+                                           __uint_as_float(tf32_trunc(p2)), __uint_as_float(tf32_trunc(p3)));
+              const int off = b_off(j, i);
+              *reinterpret_cast<float4*>(bh + off) = h;
+              *reinterpret_cast<float4*>(bl + off) = make_float4(p0 - h.x, p1 - h.y, p2 - h.z, p3 - h.w);
+            } else {
+              if constexpr (KIND == UM_FP16) {
+                p0 *= bsc[j];
+                p1 *= bsc[j];
+                p2 *= bsc[j];
+                p3 *= bsc[j];
+              }
+              uint2 h, l;
+              um_split2<KIND>(p0, p1, h.x, l.x);
+              um_split2<KIND>(p2, p3, h.y, l.y);
+              const int off = b_off16(j, i);
+              *reinterpret_cast<uint2*>(BhiB(s) + off) = h;
+              *reinterpret_cast<uint2*>(BloB(s) + off) = l;
+            }
           }
       }
       if (a_live) tmem_wait_st();
@@ -402,7 +541,11 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     double* out = partials + ((int64_t)blockIdx.y * ntiles + blockIdx.x) * (int64_t)(UM_M * TN);
 #pragma unroll
     for (int j = 0; j < S::half; ++j)
-      if (j < hc) out[m * TN + hf * hc + j] = (double)mid[j];
+      if (j < hc) {
+        double v = (double)mid[j];
+        if constexpr (KIND == UM_FP16) v /= (double)asc * (double)fsc[hf * hc + j];  // exact powers of two
+        out[m * TN + hf * hc + j] = v;
+      }
   }
   tc_fence_before();
   __syncthreads();
@@ -476,20 +619,37 @@ __global__ void reduce_umma_kernel(const double* __restrict__ partials, int spli
   if (lane == 0) out[B.base[n] + umma_rank(ms, n - 1, ns)] = s;
 }
 
-template <int TN>
+template <int TN, int KIND>
 cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, const int2* rowdesc,
                           int rows, const int2* coldesc, const int4* tiles, const int* collist, int ntc, int ntiles,
-                          int splits, int64_t cps, double* partials, int* status, cudaStream_t st) {
+                          int splits, int64_t cps, const unsigned* absmax, double* partials, int* status,
+                          cudaStream_t st) {
   if (ntc == 0) return cudaSuccess;
-  const int wcells = umma_wcells<TN>(ns, (size_t)227 * 1024);
+  const int wcells = umma_wcells<TN, KIND>(ns, (size_t)227 * 1024);
   if (wcells == 0) return cudaErrorInvalidValue;
-  const size_t sm = umma_smem<TN>(ns, wcells);
-  cudaError_t e = cudaFuncSetAttribute(contract_umma_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = umma_smem<TN, KIND>(ns, wcells);
+  cudaError_t e =
+      cudaFuncSetAttribute(contract_umma_kernel<TN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntc, (unsigned)splits);  // tiles 0 .. ntc - 1; partials pitched by all ntiles
-  contract_umma_kernel<TN><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, wcells, rowdesc, rows, coldesc,
-                                                         tiles, collist, ntiles, cps, partials, status);
+  contract_umma_kernel<TN, KIND><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, wcells, rowdesc, rows,
+                                                               coldesc, tiles, collist, ntiles, cps, absmax, partials,
+                                                               status);
   return cudaGetLastError();
+}
+
+// Largest |value| of W0 (row 0) and of each bank row (1 + s), as float bits
+// (non-negative floats order as unsigned integers), for the FP16 scales.
+__global__ void absmax_rows_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride,
+                                   int64_t nc, int ns, unsigned* __restrict__ out) {
+  const int row = blockIdx.y;
+  const float* src = row == 0 ? w0 : bank + (int64_t)(row - 1) * bstride;
+  float m = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(__ldg(src + i)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out + row, __float_as_uint(m));
 }
 
 }  // namespace
@@ -514,22 +674,35 @@ int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count) {
   return std::max<int64_t>(cps, UM_GCELLS);
 }
 
-cudaError_t launch_umma(int tn, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
+cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
-                        int ntc, int ntiles, int splits, int64_t cps, double* partials, int* status,
+                        int ntc, int ntiles, int splits, int64_t cps, unsigned* absmax, double* partials, int* status,
                         cudaStream_t st) {
-#define CK_UMMA_CASE(W)                                                                                          \
-  case W:                                                                                                        \
-    return launch_umma_t<W>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntc, ntiles, splits, \
-                            cps, partials, status, st);
-  switch (tn) {
-    CK_UMMA_CASE(32)
-    CK_UMMA_CASE(64)
-    CK_UMMA_CASE(128)
-    CK_UMMA_CASE(160)
-    CK_UMMA_CASE(256)
-    default: return cudaErrorInvalidValue;
+  if (ntc == 0) return cudaSuccess;
+  if (kind == UM_FP16) {
+    cudaError_t e = cudaMemsetAsync(absmax, 0, (size_t)(ns + 1) * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const int64_t per = std::min<int64_t>(1024, std::max<int64_t>(1, (nc + 4095) / 4096));
+    absmax_rows_kernel<<<dim3((unsigned)per, (unsigned)(ns + 1)), 256, 0, st>>>(w0, bank, bstride, nc, ns, absmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+#define CK_UMMA_CASE(W, K)                                                                                           \
+  case W:                                                                                                            \
+    return launch_umma_t<W, K>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntc, ntiles, splits, \
+                               cps, absmax, partials, status, st);
+#define CK_UMMA_KIND(K)        \
+  switch (tn) {                \
+    CK_UMMA_CASE(32, K)        \
+    CK_UMMA_CASE(64, K)        \
+    CK_UMMA_CASE(128, K)       \
+    CK_UMMA_CASE(160, K)       \
+    CK_UMMA_CASE(256, K)       \
+    default: return cudaErrorInvalidValue; \
+  }
+  if (kind == UM_BF16) { CK_UMMA_KIND(UM_BF16) }
+  if (kind == UM_FP16) { CK_UMMA_KIND(UM_FP16) }
+  CK_UMMA_KIND(UM_TF32)
+#undef CK_UMMA_KIND
 #undef CK_UMMA_CASE
 }
 

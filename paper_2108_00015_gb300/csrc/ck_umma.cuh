@@ -1,6 +1,7 @@
 // ck_umma.cuh -- fifth-generation tensor-core (tcgen05) helpers: tensor
-// memory allocation, shared-memory matrix descriptors, the kind::tf32 MMA
-// with its commit to an mbarrier, and tensor-memory loads.
+// memory allocation, shared-memory matrix descriptors, the kind::tf32 and
+// kind::f16 MMAs with their commit to an mbarrier, and tensor-memory loads
+// and stores.
 //
 // Operands live in shared memory in the K-major layout without swizzling:
 // an R x K block is cut into core matrices of 8 rows x 4 values (16 bytes
@@ -34,6 +35,13 @@ __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16: D FP32, A and B both BF16 (bf16 =
+// true) or both FP16, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
 // One warp: allocate `ncols` (power of two, 32..512) tensor-memory columns;
 // the base address is written to *slot (shared memory).
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
@@ -64,6 +72,19 @@ __device__ __forceinline__ void umma_tf32_ts(uint32_t dtmem, uint32_t atmem, uin
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u)
+      : "memory");
+}
+
+// kind::f16 with A in tensor memory: row m of A in lane m, its K = 16
+// values packed two per 32-bit column (element 2j in the low half of column
+// atmem + j); B in shared memory as for kind::tf32 with 8 values per
+// 16-byte core row.
+__device__ __forceinline__ void umma_f16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
+                                            bool accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
       "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accumulate ? 1u : 0u)
       : "memory");
 }

@@ -57,7 +57,9 @@ def test_host_validation(lib):
     assert _ws(lib, cell=0.0)[0] == 1
     assert _ws(lib, max_order=6)[0] == 1
     assert _ws(lib, max_order=1)[0] == 1
-    assert _ws(lib, prec=1)[0] == 10                  # split-BF16 reserved
+    assert _ws(lib, prec=1)[0] == 0                   # split-BF16: bank + tensor-core blocked product
+    assert _ws(lib, prec=2, max_order=5)[0] == 0      # split-FP16
+    assert _ws(lib, prec=1)[1] > _ws(lib, prec=4)[1]  # the 16-bit forms keep the bank (no fused pass)
     assert _ws(lib, prec=4)[0] == 0                   # split-TF32, fused
     assert _ws(lib, prec=4, max_order=5)[0] == 0      # split-TF32, bank + tensor-core blocked product
     assert _ws(lib, prec=4, radii=tuple(20.0 + 5 * i for i in range(17)), width=5.0)[0] == 0

@@ -1,8 +1,9 @@
 """The failure path of the bounded device waits, made to run out on purpose
-without faulting or hanging anything: ck_debug_set_wait_limit shortens the
-register contraction's consumer waits to a few nanoseconds, so a launch gives
-up on its first staged chunk, records CK_ERR_TIMEOUT, waits (with the
-default limit) for the bulk copies it has issued and returns.  The plan's
+without faulting or hanging anything: ck_debug_force_timeout makes each
+consumer warp of the register contraction wait, with a 50 us limit, on an
+mbarrier that nothing arrives at, so every launch gives up, records
+CK_ERR_TIMEOUT, waits (with the default limit) for the bulk copies it has
+issued and returns.  The plan's
 status word then reports the timeout and the allocation-free entry point
 returns NaN; with the default limit restored, the same calls give finite
 sums equal to the oracle's."""
@@ -38,7 +39,7 @@ def test_consumer_timeout_reported_and_recovered():
     tw0, tB = dev(torch, w0), dev(torch, B)
     assert plan.status() == 0
     try:
-        conker.set_wait_limit(2)  # 2 ns: no staged chunk lands that fast
+        conker.force_timeout(50_000)
         got = plan.contract(tw0, tB, stride, orders=(2, 3))
         torch.cuda.synchronize()
         assert plan.status() == 8  # CK_ERR_TIMEOUT, read (and cleared) from the status word
@@ -48,7 +49,7 @@ def test_consumer_timeout_reported_and_recovered():
             assert torch.isnan(st[n]).all(), f"order {n}: a timed-out static call returns NaN"
         del got
     finally:
-        conker.set_wait_limit(0)
+        conker.force_timeout(0)
     # the context stays usable and the default limit is back
     want = plan.contract(tw0, tB, stride, orders=(2, 3))
     st = conker.contract_static(tw0, tB, stride, nc, ns, orders=(2, 3))

@@ -188,30 +188,39 @@ def test_xi_fp64_contraction(torch, p32, ref32):
     plan.close()
 
 
-def test_xi_split_tf32_all_orders(torch, p32, ref32):
-    """Mixed form with orders up to 5: the bank is kept and every order runs
-    through the tensor-core blocked product."""
-    plan, res = _run(torch, p32, (2, 3, 4, 5), precision="split_tf32")
+# Gates of the split tensor-core forms: hi + lo operands carry 21-22
+# significant bits in TF32 and FP16 (scaled per factor) and 16 in BF16, whose
+# dropped lo*lo term and the rounding of lo leave about 2^-16 per product.
+SPLIT_TOL = {"split_tf32": TOL, "split_fp16": TOL, "split_bf16": 5e-5}
+
+
+@pytest.mark.parametrize("precision", ["split_tf32", "split_bf16", "split_fp16"])
+def test_xi_split_all_orders(torch, p32, ref32, precision):
+    """Mixed forms with orders up to 5: the bank is kept and every order runs
+    through the tensor-core blocked product (kind::tf32, or kind::f16 with
+    BF16 or FP16 hi/lo operands)."""
+    plan, res = _run(torch, p32, (2, 3, 4, 5), precision=precision)
     assert not plan.fused
-    _check_sums(res, ref32, len(p32["shells"]), (2, 3, 4, 5))
+    _check_sums(res, ref32, len(p32["shells"]), (2, 3, 4, 5), tol=SPLIT_TOL[precision])
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["split_tf32", "split_bf16", "split_fp16"])
 @pytest.mark.parametrize("ns,dims", [(16, (24, 20, 18)), (20, (24, 20, 18)), (8, (30, 18, 10)), (12, (30, 18, 10))])
-def test_tc_blocked_contraction(torch, ns, dims):
-    """The tensor-core blocked product (split-TF32) over a caller's bank,
-    orders 2..5, against the oracle's product sums of the same float32
-    fields.  The shell counts give output tiles of 128 x TN for every TN
+def test_tc_blocked_contraction(torch, ns, dims, precision):
+    """The tensor-core blocked product over a caller's bank, orders 2..5,
+    against the oracle's product sums of the same float32 fields, in each
+    split form.  The shell counts give output tiles of 128 x TN for every TN
     (32: orders 2-4; 64, 128, 160, 256: order 5 over 8, 12, 16 and 20
     shells), several row tiles and split-K over the cells; the 30 x 18 x 10
-    grid (5400 cells) ends in a partial 32-cell chunk."""
+    grid (5400 cells) ends in a partial chunk."""
     g = GridSpec(dims, (0.0, 0.0, 0.0), 1.0, True)
     rng = np.random.default_rng(50 + ns)
     nc = g.n_cells
     w0 = rng.normal(size=nc).astype(np.float32)
     bank = rng.normal(size=(ns, nc)).astype(np.float32)
     w = dict(grid=g, shells=tuple(1.0 + 0.05 * i for i in range(ns)), width=1.0)
-    plan = plan_for(w, max_order=5, precision="split_tf32")
+    plan = plan_for(w, max_order=5, precision=precision)
     stride = (nc + 63) // 64 * 64
     B = np.zeros((ns, stride), np.float32)
     B[:, :nc] = bank
@@ -220,7 +229,38 @@ def test_tc_blocked_contraction(torch, ns, dims):
         for n in orders:
             want, awant = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
             e = normwise(sums[n].cpu().numpy(), want, awant)
-            assert e <= TOL, f"order {n}: {e:.3e}"
+            assert e <= SPLIT_TOL[precision], f"order {n}: {e:.3e}"
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "split_fp16"])
+def test_split16_dynamic_range(torch, precision):
+    """Fields far outside the FP16 range (|W0| ~ 1e3, |W_s| ~ 1e4 on one
+    shell and 1e-3 on another, products up to 1e15): the per-factor
+    power-of-two scales keep the FP16 operands finite and the split forms
+    inside their gates; all-zero shells give exact zeros."""
+    g = GridSpec((24, 20, 18), (0.0, 0.0, 0.0), 1.0, True)
+    rng = np.random.default_rng(77)
+    nc = g.n_cells
+    ns = 6
+    w0 = (1e3 * rng.normal(size=nc)).astype(np.float32)
+    bank = rng.normal(size=(ns, nc))
+    bank[0] *= 1e4
+    bank[1] *= 1e-3
+    bank[2] = 0.0
+    bank = bank.astype(np.float32)
+    w = dict(grid=g, shells=tuple(1.0 + 0.05 * i for i in range(ns)), width=1.0)
+    plan = plan_for(w, max_order=5, precision=precision)
+    stride = (nc + 63) // 64 * 64
+    B = np.zeros((ns, stride), np.float32)
+    B[:, :nc] = bank
+    sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=(2, 3, 4, 5))
+    for n in (2, 3, 4, 5):
+        want, awant = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
+        got = sums[n].cpu().numpy()
+        assert np.all(np.isfinite(got)), f"order {n}"
+        assert normwise(got, want, awant) <= SPLIT_TOL[precision], f"order {n}"
+        assert np.all(got[awant == 0.0] == 0.0), f"order {n}: zero shells"
     plan.close()
 
 
