@@ -70,6 +70,11 @@ Readings where the paper is silent or ambiguous (each is a choice):
 13. Per-cell maps (Sec. 4.2, the wishbone and sky-slice figures):
    W_0 W_s / <B_0 B_s> per cell, the average over the box's cells,
    <B_0 B_s> = den_2(s) / N_box.
+14. Regions of one catalog (Sec. 4's combination of the two galactic caps,
+   Eq. 19, adds numerators and denominators before dividing): a catalog cut
+   into slabs along z sums each slab's owned planes with every field of the
+   slab box, halo planes included, in the convolution, and with the whole
+   catalog's alpha, so that the slabs' num and den add to the whole's.
 
 Pins: see tests/test_oracle_pins.py (brute-force pair and triplet counts on
 cell-centred points, three-square lattice counts, closed forms, symmetry,
@@ -170,14 +175,17 @@ def grid_weights(x, y, z, w, grid) -> Tuple[np.ndarray, float, int]:
     return (sums.astype(np.float64) * scale).reshape(nz, ny, nx), float(int(q.sum())) * scale, dropped
 
 
-def density_fields(D: np.ndarray, R: np.ndarray):
+def density_fields(D: np.ndarray, R: np.ndarray, alpha: float = None):
     """alpha = sum D / sum R, N = D - alpha R (Eq. 8 with R normalised to the
-    data total, Sec. 2.2) and Rt = alpha R, all FP64."""
+    data total, Sec. 2.2) and Rt = alpha R, all FP64.  A given alpha (the
+    whole catalog's, for one region of it: reading 14) replaces the ratio."""
     sd = float(np.sum(D, dtype=np.float64))
     sr = float(np.sum(R, dtype=np.float64))
-    if sr <= 0.0:
-        raise ValueError("random histogram is empty")
-    alpha = sd / sr
+    if alpha is None:
+        if sr <= 0.0:
+            raise ValueError("random histogram is empty")
+        alpha = sd / sr
+    alpha = float(alpha)
     Dd = D.astype(np.float64)
     Rd = R.astype(np.float64)
     return alpha, Dd - alpha * Rd, alpha * Rd
@@ -495,7 +503,7 @@ def product_map(W0, Ws, den2_s: float, n_box: int) -> np.ndarray:
 def correlate(grid, shells: Sequence[float], width: float, data, randoms,
               orders: Sequence[int] = (2, 3), engine: str = "direct",
               rule: str = "center_bin", data_weights=None, random_weights=None,
-              random_field=None) -> Dict[str, object]:
+              random_field=None, alpha: float = None, owned_z=None) -> Dict[str, object]:
     """The whole path for one catalog: mapping, convolution, summation.
 
     Returns a dict with D, R, dropped counts, alpha, N, Rt, the offset lists,
@@ -503,6 +511,13 @@ def correlate(grid, shells: Sequence[float], width: float, data, randoms,
     and the dense xi tensor [N_s]^(n-1).  random_field, when given, is the
     randoms histogram itself (the factorised field of Eq. 7) and `randoms`
     is not read.
+
+    One region of a catalog cut into slabs along z (reading 14): alpha, when
+    given, replaces sum D / sum R (the whole catalog's ratio), and
+    owned_z = (z0, z1) keeps the sums to the planes z0 <= z < z1 (W_0 = N
+    and B_0 = Rt are zero elsewhere) while every plane of the grid, the halo
+    included, enters the convolution.  The regions' num and den then add up
+    to the whole catalog's (Eq. 19).
     """
     if data_weights is None:
         D, dropped_d = grid_counts(data.x, data.y, data.z, grid)
@@ -514,7 +529,7 @@ def correlate(grid, shells: Sequence[float], width: float, data, randoms,
         R, dropped_r = grid_counts(randoms.x, randoms.y, randoms.z, grid)
     else:
         R, _, dropped_r = grid_weights(randoms.x, randoms.y, randoms.z, random_weights, grid)
-    alpha, N, Rt = density_fields(D, R)
+    alpha, N, Rt = density_fields(D, R, alpha)
     offs = [shell_offsets(s, width, grid.cell, rule) for s in shells]
     if grid.periodic:
         for o in offs:
@@ -535,9 +550,16 @@ def correlate(grid, shells: Sequence[float], width: float, data, randoms,
     out: Dict[str, object] = dict(D=D, R=R, dropped_d=dropped_d, dropped_r=dropped_r,
                                   alpha=alpha, N=N, Rt=Rt, offsets=offs, W=W, B=B)
     ns = len(shells)
+    N0, Rt0 = N, Rt
+    if owned_z is not None:
+        z0, z1 = (int(v) for v in owned_z)
+        keep = np.zeros(N.shape[0], dtype=bool)
+        keep[z0:z1] = True
+        N0 = np.where(keep[:, None, None], N, 0.0)
+        Rt0 = np.where(keep[:, None, None], Rt, 0.0)
     for n in orders:
-        num, anum = product_sums(N, W, n)
-        den, aden = product_sums(Rt, B, n)
+        num, anum = product_sums(N0, W, n)
+        den, aden = product_sums(Rt0, B, n)
         out[f"num{n}"] = num
         out[f"den{n}"] = den
         out[f"abs_num{n}"] = anum

@@ -23,11 +23,28 @@ int prof_begin(const Plan& p, int stage, double bytes, cudaStream_t st) {
   Profiler::Rec& r = f.recs[f.used];
   r.stage = stage;
   r.bytes = bytes;
+  r.boxed = false;
   if (cudaEventRecord(r.a, st) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
   return (int)f.used++;
+}
+
+int prof_begin_box(const Plan& p, int stage, double bytes, double per_row, double per_plane, const int* box,
+                   cudaStream_t st) {
+  const int idx = prof_begin(p, stage, bytes, st);
+  if (idx < 0 || !p.prof.pin) return idx;
+  Profiler::Rec& r = p.prof.recs[(size_t)idx];
+  if (cudaMemcpyAsync(p.prof.pin + 6 * (size_t)idx, box, 6 * sizeof(int), cudaMemcpyDeviceToHost, st) ==
+      cudaSuccess) {
+    r.boxed = true;
+    r.per_row = per_row;
+    r.per_plane = per_plane;
+  } else {
+    cudaGetLastError();
+  }
+  return idx;
 }
 
 void prof_end(const Plan& p, int idx, cudaStream_t st) {
@@ -51,7 +68,13 @@ void prof_collect(ck::Plan& p) {
     if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       f.ms[r.stage] += ms;
       f.launches[r.stage] += 1;
-      f.bytes[r.stage] += r.bytes;
+      double b = r.bytes;
+      if (r.boxed) {  // the support box this launch visited (copied before it ran)
+        const int* bx = f.pin + 6 * i;
+        const double ny = std::max(0, bx[3] - bx[2] + 1), nz = std::max(0, bx[5] - bx[4] + 1);
+        b += r.per_row * ny * nz + r.per_plane * nz;
+      }
+      f.bytes[r.stage] += b;
     } else {
       cudaGetLastError();
     }
@@ -282,7 +305,11 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
 // With a region set (ck_plan_set_region), W_0 = the field restricted to the
 // region's planes: the whole field is transformed (the halo enters the
 // convolution), then the planes outside the region are zeroed.
-ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, const float* w0 = nullptr) {
+// support: 0 (a catalog: N = D - alpha R) or 1 (the randoms: Rt) lets the
+// fused pass visit only the box of occupied cells, outside which W_0 = 0;
+// -1 (fields given on the grid) visits every cell.
+ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, const float* w0 = nullptr,
+                           int support = -1) {
   if (!w0) w0 = p.field;
   launch_fft_forward(p, p.field, p.spec, st);
   if (p.region && w0 == p.field) {
@@ -292,7 +319,10 @@ ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, con
       CK_TRY(cudaMemsetAsync(p.field + plane * p.region_z1, 0, plane * (p.grid.n[2] - p.region_z1) * sizeof(float),
                              st));
   }
-  if (p.fused) return launch_convolve_contract(p, w0, sums, st);
+  if (p.fused) {
+    if (support >= 0) launch_support_box(p, support, st);
+    return launch_convolve_contract(p, w0, sums, st, support >= 0 ? p.support : nullptr);
+  }
   launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
   return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st);
 }
@@ -355,7 +385,7 @@ ck_status capture_compute(Plan& p, int order_mask) {
     if (e == cudaSuccess) {
       launch_grid_points_ref(p, 0, cs);
       launch_prepare_data(p, cs);
-      s = convolve_and_sum(p, order_mask, p.sums, cs);
+      s = convolve_and_sum(p, order_mask, p.sums, cs, nullptr, 0);
       if (s == CK_OK) launch_finalize(p, order_mask, cs);
     }
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -448,6 +478,7 @@ ck_status ck_plan_destroy(ck_plan* plan) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  if (p->prof.pin) cudaFreeHost(p->prof.pin);
   for (auto& g : p->gexec)
     if (g) cudaGraphExecDestroy(g);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
@@ -485,7 +516,7 @@ static ck_status set_randoms_impl(ck_plan* plan, const float* x, const float* y,
   CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st, w));
   launch_prepare_randoms(p, st);
   p.bank_holds = -1;
-  CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st));
+  CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st, nullptr, 1));
   p.bank_holds = 1;
   CK_TRY(cudaGetLastError());
   p.have_randoms = p.have_randoms_diag = true;
@@ -514,7 +545,7 @@ ck_status ck_set_randoms_factorised(ck_plan* plan, const ck_cosmology* cosmo, co
   CK_TRY_S(launch_factorised_randoms(p, cosmo, sel, st));
   launch_prepare_randoms(p, st);
   p.bank_holds = -1;
-  CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st));
+  CK_TRY_S(convolve_and_sum(p, full_mask(p), p.den_raw, st, nullptr, 1));
   p.bank_holds = 1;
   CK_TRY(cudaGetLastError());
   p.have_randoms = p.have_randoms_diag = true;
@@ -554,7 +585,7 @@ static ck_status compute_impl(ck_plan* plan, const float* x, const float* y, con
   CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st, w));
   launch_prepare_data(p, st);
   p.bank_holds = -1;
-  CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st));
+  CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st, nullptr, 0));
   p.bank_holds = 0;
   launch_finalize(p, order_mask, st);
   CK_TRY(cudaGetLastError());
@@ -778,6 +809,7 @@ ck_status ck_profile_enable(ck_plan* plan, int32_t enable) {
       CK_TRY(cudaEventCreate(&r.a));
       CK_TRY(cudaEventCreate(&r.b));
     }
+    CK_TRY(cudaHostAlloc(reinterpret_cast<void**>(&f.pin), kProfPool * 6 * sizeof(int), cudaHostAllocDefault));
   }
   if (f.used) CK_TRY(cudaDeviceSynchronize());
   f.used = 0;

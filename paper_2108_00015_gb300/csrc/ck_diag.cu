@@ -173,8 +173,10 @@ ck_status launch_diagonal(Plan& p, int mask, cudaStream_t st) {
   const double* packed = nullptr;
   double* dsums = p.sums;  // [max_order - 1][ns] when the bank is kept (each order has >= ns multisets)
   if (p.fused) {
-    // no bank: the fused pass computes every order-2/3 multiset, the diagonal among them
-    const ck_status s = launch_convolve_contract(p, p.field, p.sums, st);
+    // no bank: the fused pass computes every order-2/3 multiset, the diagonal
+    // among them, over the box of occupied cells (W_0 = N vanishes elsewhere)
+    launch_support_box(p, 0, st);
+    const ck_status s = launch_convolve_contract(p, p.field, p.sums, st, p.support);
     if (s != CK_OK) return s;
     packed = p.sums;
   } else {
@@ -190,7 +192,8 @@ ck_status launch_diagonal(Plan& p, int mask, cudaStream_t st) {
 ck_status launch_diagonal_randoms(Plan& p, bool* full, cudaStream_t st) {
   if (p.fused) {  // the fused pass gives every multiset of the plan's orders
     *full = true;
-    return launch_convolve_contract(p, p.field, p.den_raw, st);
+    launch_support_box(p, 1, st);
+    return launch_convolve_contract(p, p.field, p.den_raw, st, p.support);
   }
   *full = false;
   const ck_status s = launch_diag_bank_sums(p, p.sums, st);

@@ -46,19 +46,27 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
 // or spec itself (khat == nullptr, nshells == 1), into the scratch spectra
 // tmp[s] (stride spec_elems).
 void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int* box) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const double H = (double)nz * ny * (nx / 2 + 1);
+  const double row = 8.0 * (nx / 2 + 1);  // bytes of one half-spectrum row
+  // support pruning on the 512-point register passes; the other lengths
+  // transform and write every plane (the fused x pass visits the box alone)
+  const int* zbox = nz == 512 ? box : nullptr;
+  const int* ybox = ny == 512 ? box : nullptr;
   {
-    ProfScope ps(p, ST_FFT_Z_INV_MUL, 8.0 * H + nshells * (8.0 * H + (khat ? 4.0 * (double)p.oct_elems : 0.0)), st);
+    const double base = 8.0 * H + nshells * (khat ? 4.0 * (double)p.oct_elems : 0.0);
+    // written: every plane, or the box's planes
+    ProfScope ps(p, ST_FFT_Z_INV_MUL, base + (zbox ? 0.0 : nshells * 8.0 * H), 0.0, nshells * row * ny, zbox, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
     KhatArgs K{khat, p.khat_stride, p.px, ny, nz, p.oct[1]};
-    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.tw[2], K, p.sm_count, st);
+    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.tw[2], K, p.sm_count, st, zbox);
   }
   {
-    ProfScope ps(p, ST_FFT_Y_INV, nshells * 16.0 * H, st);
+    // read: the box's planes, written: their box rows
+    ProfScope ps(p, ST_FFT_Y_INV, ybox ? 0.0 : nshells * 16.0 * H, nshells * row, nshells * row * ny, ybox, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, (int64_t)nz * nshells};
-    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1, p.sm_count, st);
+    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1, p.sm_count, st, ybox, nz);
   }
 }
 

@@ -764,11 +764,16 @@ inline size_t xpass_smem(int nx) {
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).
 // wide: 16-column tiles for the 512-point register kernel (large multi-shell passes)
+// box (device, may be null; 512-point axes only): the support box of W_0.
+// For the strided pass, only its planes z (outer index s nz + z, nz planes
+// per shell) are transformed and only its rows y written; for the z pass
+// with the multiply, only its planes are written.
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st);
+                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st,
+                    const int* box = nullptr, int nz = 0);
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
-                   cudaStream_t st);
+                   cudaStream_t st, const int* box = nullptr);
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
                   const float2* stw, const float2* tw, int sm_count, cudaStream_t st);
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,

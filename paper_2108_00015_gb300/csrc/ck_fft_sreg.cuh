@@ -15,7 +15,7 @@
 // which go straight to global memory (C columns = 8 C contiguous bytes).
 //
 // sreg512_kernel: one transform per tile, double-buffered staging (in
-// place allowed).  zreg512_kernel: the first inverse pass of Eqs. 9-10: the
+// place allowed); optionally only the planes and rows of a box.  zreg512_kernel: the first inverse pass of Eqs. 9-10: the
 // spectrum tile is staged once and, for every shell s, multiplied by the
 // tile's slab of K^_s while step A reads it; outputs go to out + s * stride.
 #pragma once
@@ -73,10 +73,11 @@ __device__ __forceinline__ void sreg_step_a(float2* T, const float2* twa, int c,
 }
 
 // Step B for thread (c, m1, h), lane bit log2(C) = h; rows m1 + 16 kk and
-// m1 + 16 (kk + 16), kk = k + 8 h, k < 8, go to col[row * sl] (if valid).
+// m1 + 16 (kk + 16), kk = k + 8 h, k < 8, go to col[row * sl] (if valid
+// and rlo <= row <= rhi: rows outside are not needed downstream).
 template <int C, bool INV>
 __device__ __forceinline__ void sreg_step_b(const float2* T, const float2* w32, int c, int m1, int h, float2* col,
-                                            int64_t sl, bool valid) {
+                                            int64_t sl, bool valid, int rlo = 0, int rhi = 511) {
   using S = Sreg<C>;
   float2 y[16];
 #pragma unroll
@@ -87,6 +88,7 @@ __device__ __forceinline__ void sreg_step_b(const float2* T, const float2* w32, 
     for (int k = 1; k < 16; ++k) y[k] = cmul(y[k], w32[k]);
   }
   float2* p = col + (int64_t)(m1 + 128 * h) * sl;  // row m1 + 16 kk for k = 0
+  int row = m1 + 128 * h;
   const int64_t s16 = 16 * sl, s256 = 256 * sl;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -97,21 +99,20 @@ __device__ __forceinline__ void sreg_step_b(const float2* T, const float2* w32, 
     const float2 a = h ? recv : y[k];
     const float2 b = h ? y[k + 8] : recv;
     if (valid) {
-      p[0] = cadd(a, b);
-      p[s256] = csub(a, b);
+      if (row >= rlo && row <= rhi) p[0] = cadd(a, b);
+      if (row + 256 >= rlo && row + 256 <= rhi) p[s256] = csub(a, b);
     }
     p += s16;
+    row += 16;
   }
 }
 
-// Tile `tile` of a strided view (C columns x 512 rows) into S[row][c] with
-// 16-byte cp.async copies; columns past the view's end are zero-filled.
+// The tile of outer index o and first column i0 of a strided view (C
+// columns x 512 rows) into S[row][c] with 16-byte cp.async copies; columns
+// past the view's end are zero-filled.
 template <int C>
-__device__ __forceinline__ void sreg_stage(float2* s, const float2* in, const StridedView& v, int64_t tile) {
+__device__ __forceinline__ void sreg_stage(float2* s, const float2* in, const StridedView& v, int64_t o, int i0) {
   using S = Sreg<C>;
-  const int tpo = (v.inner + C - 1) / C;
-  const int64_t o = tile / tpo;
-  const int i0 = (int)(tile - o * tpo) * C;
   const float2* base = in + o * v.so + i0;
   for (int idx = threadIdx.x; idx < S::L * (C / 2); idx += S::NT) {
     const int l = idx / (C / 2), cp = idx % (C / 2);
@@ -120,9 +121,13 @@ __device__ __forceinline__ void sreg_stage(float2* s, const float2* in, const St
   }
 }
 
+// box (null: none): the view's outer index is o = s nz + z (nz planes per
+// shell); only the planes box[4] <= z <= box[5] are transformed, and of
+// their rows only box[2] .. box[3] are written (the support of W_0).
 template <int C, bool INV>
 __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
-    sreg512_kernel(const float2* in, float2* out, StridedView v, const float2* __restrict__ tw) {
+    sreg512_kernel(const float2* in, float2* out, StridedView v, const float2* __restrict__ tw,
+                   const int* __restrict__ box, int nz) {
   using S = Sreg<C>;
   extern __shared__ float4 smem4[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
@@ -135,13 +140,27 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
   const int ca = tid % C, l2 = tid / C;                                // step A
   const int cb = tid % C, hb = (tid / C) & 1, m1 = tid / (2 * C);      // step B
   const int tpo = (v.inner + C - 1) / C;
-  const int64_t ntiles = v.n_outer * tpo;
+  int zlo = 0, nzb = nz, rlo = 0, rhi = S::L - 1;
+  if (box) {
+    zlo = box[4];
+    nzb = max(0, box[5] - box[4] + 1);
+    rlo = box[2];
+    rhi = box[3];
+  }
+  const int64_t outers = box ? (v.n_outer / nz) * nzb : v.n_outer;
+  const int64_t ntiles = outers * tpo;
+  // tile -> outer index of the view (plane zlo + .. of a shell) and first column
+  auto outer_of = [&](int64_t tile) {
+    const int64_t ot = tile / tpo;
+    return box ? (ot / nzb) * nz + zlo + ot % nzb : ot;
+  };
+  auto col_of = [&](int64_t tile) { return (int)(tile % tpo) * C; };
   int64_t t = blockIdx.x;
-  if (t < ntiles) sreg_stage<C>(sbuf(0), in, v, t);
+  if (t < ntiles) sreg_stage<C>(sbuf(0), in, v, outer_of(t), col_of(t));
   cp_async_commit();
   for (int it = 0; t < ntiles; ++it) {
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) sreg_stage<C>(sbuf((it + 1) & 1), in, v, tn);
+    if (tn < ntiles) sreg_stage<C>(sbuf((it + 1) & 1), in, v, outer_of(tn), col_of(tn));
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -149,9 +168,9 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
     const float2* cc = cur + l2 * C + ca;
     sreg_step_a<C, INV>(T, twa, ca, l2, [&](int l1) { return cc[S::Q * l1 * C]; });
     __syncthreads();
-    const int64_t o = t / tpo;
-    const int i0 = (int)(t - o * tpo) * C;
-    sreg_step_b<C, INV>(T, w32, cb, m1, hb, out + o * v.so + i0 + cb, v.sl, i0 + cb < v.inner);
+    const int64_t o = outer_of(t);
+    const int i0 = col_of(t);
+    sreg_step_b<C, INV>(T, w32, cb, m1, hb, out + o * v.so + i0 + cb, v.sl, i0 + cb < v.inner, rlo, rhi);
     t = tn;
   }
 }
@@ -159,7 +178,7 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
 template <int C>
 __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
     zreg512_kernel(const float2* in, float2* out, int64_t out_stride, int nshells, StridedView v,
-                   const float2* __restrict__ tw, KhatArgs K) {
+                   const float2* __restrict__ tw, KhatArgs K, const int* __restrict__ box) {
   using S = Sreg<C>;
   constexpr int OZ = S::L / 2 + 1;
   extern __shared__ float4 smem4[];
@@ -175,6 +194,8 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
   const int cb = tid % C, hb = (tid / C) & 1, m1 = tid / (2 * C);
   const int64_t ntiles = (v.inner + C - 1) / C;
   const bool mul = K.khat != nullptr;
+  // box (null: none): only the output rows (kz -> z) box[4] .. box[5] are written
+  const int rlo = box ? box[4] : 0, rhi = box ? box[5] : S::L - 1;
   // C / 4 groups of 4 columns per tile: px is a multiple of 4 and i0 of C,
   // so each group lies in one ky row of the spectrum
   auto load_slab = [&](int s, int64_t tile) {
@@ -226,7 +247,8 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
         if (mul) load_slab(0, tn);
       }
       cp_async_commit();
-      sreg_step_b<C, true>(T, w32, cb, m1, hb, out + (int64_t)s * out_stride + i0 + cb, v.sl, i0 + cb < v.inner);
+      sreg_step_b<C, true>(T, w32, cb, m1, hb, out + (int64_t)s * out_stride + i0 + cb, v.sl, i0 + cb < v.inner, rlo,
+                           rhi);
       cp_async_wait<0>();
       __syncthreads();
     }

@@ -24,7 +24,7 @@ constexpr int kZregC = 8;
 
 template <int C>
 static void run_sreg512(bool inv, const float2* in, float2* out, const StridedView& v, const float2* tw, int sm_count,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* box, int nz) {
   using S = Sreg<C>;
   const size_t sm = S::plain_bytes;
   const int64_t ntiles = v.n_outer * ((v.inner + C - 1) / C);
@@ -36,7 +36,7 @@ static void run_sreg512(bool inv, const float2* in, float2* out, const StridedVi
       occ = 1;
     }
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * occ));
-    kernel<<<grid, S::NT, sm, st>>>(in, out, v, tw);
+    kernel<<<grid, S::NT, sm, st>>>(in, out, v, tw, box, nz);
   };
   if (inv) go(sreg512_kernel<C, true>);
   else go(sreg512_kernel<C, false>);
@@ -44,7 +44,7 @@ static void run_sreg512(bool inv, const float2* in, float2* out, const StridedVi
 
 template <int C>
 static void run_zreg512(const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
-                        const float2* tw, const KhatArgs& K, int sm_count, cudaStream_t st) {
+                        const float2* tw, const KhatArgs& K, int sm_count, cudaStream_t st, const int* box) {
   using S = Sreg<C>;
   const size_t sm = S::multi_bytes;
   const int64_t ntiles = (v.inner + C - 1) / C;
@@ -55,7 +55,7 @@ static void run_zreg512(const float2* in, float2* out, int64_t out_stride, int n
     occ = 1;
   }
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * occ));
-  zreg512_kernel<C><<<grid, S::NT, sm, st>>>(in, out, out_stride, nshells, v, tw, K);
+  zreg512_kernel<C><<<grid, S::NT, sm, st>>>(in, out, out_stride, nshells, v, tw, K, box);
 }
 
 template <int LC>
@@ -89,10 +89,11 @@ static void run_zmulti(const float2* in, float2* out, int64_t out_stride, int ns
 #define CK_LENGTHS(X) X(32) X(128) X(160) X(192) X(240) X(256) X(288) X(320) X(384)
 
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st) {
+                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st, const int* box,
+                    int nz) {
   if (L == 512) {
-    if (wide) run_sreg512<16>(inv, in, out, v, tw, sm_count, st);
-    else run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st);
+    if (wide) run_sreg512<16>(inv, in, out, v, tw, sm_count, st, box, nz);
+    else run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st, box, nz);
     return;
   }
   switch (L) {
@@ -105,9 +106,9 @@ void launch_strided(int L, bool inv, const float2* in, float2* out, const Stride
 
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
-                   cudaStream_t st) {
+                   cudaStream_t st, const int* box) {
   if (L == 512) {
-    run_zreg512<kZregC>(in, out, out_stride, nshells, v, tw, K, sm_count, st);
+    run_zreg512<kZregC>(in, out, out_stride, nshells, v, tw, K, sm_count, st, box);
     return;
   }
   switch (L) {

@@ -333,6 +333,38 @@ void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st) {
                                                                         which);
 }
 
+// The box of cells where W_0 may be nonzero, for the pruned inverse passes
+// of the fused path: the occupied cells of the data and the randoms (mode
+// 0, W_0 = N = D - alpha R) or of the randoms (mode 1, W_0 = Rt), clipped to
+// the region's planes; {x0, x1, y0, y1, z0, z1} inclusive, empty when a
+// lower bound exceeds its upper one.
+__global__ void support_box_kernel(const DevState* __restrict__ st, int mode, int nx, int ny, int nz, int z_lo,
+                                   int z_hi, int* __restrict__ box) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    int lo = st->bbox_min[1][a], hi = st->bbox_max[1][a];
+    if (mode == 0) {
+      lo = min(lo, st->bbox_min[0][a]);
+      hi = max(hi, st->bbox_max[0][a]);
+    }
+    lo = max(lo, 0);
+    hi = min(hi, n[a] - 1);
+    if (a == 2) {
+      lo = max(lo, z_lo);
+      hi = min(hi, z_hi);
+    }
+    box[2 * a] = lo;
+    box[2 * a + 1] = hi;
+  }
+}
+
+void launch_support_box(const Plan& p, int mode, cudaStream_t st) {
+  const int z_lo = p.region ? p.region_z0 : 0;
+  const int z_hi = p.region ? p.region_z1 - 1 : p.grid.n[2] - 1;
+  support_box_kernel<<<1, 32, 0, st>>>(p.dstate, mode, p.grid.n[0], p.grid.n[1], p.grid.n[2], z_lo, z_hi, p.support);
+}
+
 void launch_prepare_randoms(const Plan& p, cudaStream_t st) {
   ProfScope ps(p, ST_PREP, 8.0 * (double)p.nc, st);
   prepare_randoms_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.counts[1], p.field, p.nc, p.dstate);

@@ -103,13 +103,16 @@ enum Stage {
 
 struct Profiler {
   bool on = false;
-  struct Rec { int stage; double bytes; cudaEvent_t a, b; };
+  // bytes of a launch: `bytes`, plus per_row x (rows) + per_plane x (planes)
+  // of the support box copied to the pinned slot of the record (boxed)
+  struct Rec { int stage; double bytes; cudaEvent_t a, b; bool boxed; double per_row, per_plane; };
   std::vector<Rec> recs;      // event pool; recs[0..used) are pending
   size_t used = 0;
   double ms[CK_STAGES] = {0};
   int64_t launches[CK_STAGES] = {0};
   double bytes[CK_STAGES] = {0};
   int64_t dropped = 0;        // launches not recorded (pool exhausted)
+  int* pin = nullptr;         // page-locked: 6 ints per record (support boxes)
 };
 
 struct Plan {
@@ -207,6 +210,10 @@ int64_t binom(int64_t n, int64_t k);
 
 // Record the start / end of one launch of `stage` (no-ops unless enabled).
 int prof_begin(const Plan& p, int stage, double bytes, cudaStream_t st);
+// The same for a launch that visits the support box `box` (device): its
+// bytes are counted when the times are read.
+int prof_begin_box(const Plan& p, int stage, double bytes, double per_row, double per_plane, const int* box,
+                   cudaStream_t st);
 void prof_end(const Plan& p, int idx, cudaStream_t st);
 
 struct ProfScope {
@@ -215,6 +222,10 @@ struct ProfScope {
   cudaStream_t st;
   ProfScope(const Plan& pl, int stage, double bytes, cudaStream_t s)
       : p(pl), idx(prof_begin(pl, stage, bytes, s)), st(s) {}
+  ProfScope(const Plan& pl, int stage, double bytes, double per_row, double per_plane, const int* box,
+            cudaStream_t s)
+      : p(pl), idx(box ? prof_begin_box(pl, stage, bytes, per_row, per_plane, box, s) : prof_begin(pl, stage, bytes, s)),
+        st(s) {}
   ~ProfScope() { prof_end(p, idx, st); }
 };
 
@@ -226,6 +237,9 @@ void launch_set_catalog_ref(const Plan& p, const float* x, const float* y, const
 void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // catalog from p.dref
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
+// p.support = the box where W_0 may be nonzero: mode 0 data (D and R
+// occupied), 1 randoms; clipped to the region's planes.
+void launch_support_box(const Plan& p, int mode, cudaStream_t st);
 // The factorised randoms field of Eq. 7 (ck_sky.cu): check_factorised
 // validates the arguments; launch_factorised_randoms writes counts[1] (float
 // bits) and the field's totals, after the caller has reset field 1.
@@ -245,8 +259,10 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
 void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
                         float* out, int64_t out_stride, cudaStream_t st);
 // Its first two passes alone: tmp[s] = (y, z inverse of spec * K^_s), rows of pitch px.
+// box (device, may be null): only the planes z0..z1 of the output are
+// needed, and of them only the rows y0..y1 (512-point y and z axes).
 void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
-                       cudaStream_t st);
+                       cudaStream_t st, const int* box = nullptr);
 ck_status build_kernel_spectra(Plan& p, cudaStream_t st);
 
 // ---- fused inverse x pass + sums (ck_xc.cu) -----------------------------------
@@ -254,7 +270,9 @@ int xc_pad_shells(int ns);               // supported padded shell count, 0 if n
 size_t xc_smem_bytes(int M, int ns_pad);  // shared memory of the fused kernel
 // Inverse z, y passes and the fused x pass + order-2/3 sums of the resident
 // spectrum p.spec with cell values w0; packed sums (orders <= max_order).
-ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st);
+// box (device, may be null): W_0 vanishes outside it, so the passes visit
+// only its rows and planes.
+ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st, const int* box);
 
 // ---- tcgen05 blocked product (ck_umma.cu) -------------------------------------
 int umma_tile_rows();

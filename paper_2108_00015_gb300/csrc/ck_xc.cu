@@ -12,8 +12,8 @@ namespace ck {
 namespace fft {
 
 cudaError_t run_xc16(int M, const float2* spec, int64_t spec_stride, const float* w0, int nx, int px, int64_t rows,
-                     int nshells, const FftLen& f, const float2* stw, const float2* tw, int max_ctas, int* ctas,
-                     double* partials, int* status, cudaStream_t st);
+                     int ny, const int* box, int nshells, const FftLen& f, const float2* stw, const float2* tw,
+                     int max_ctas, int* ctas, double* partials, int* status, cudaStream_t st);
 
 }  // namespace fft
 
@@ -63,7 +63,7 @@ __global__ void reduce_xc_kernel(const double* __restrict__ partials, int ctas, 
   out[dst] = s;
 }
 
-ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st) {
+ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st, const int* box) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const int M = nx / 2;
   const int ns_pad = xc_pad_shells(p.ns);
@@ -74,23 +74,25 @@ ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaS
   const int max_ctas = (int)std::min<size_t>((size_t)2 * p.sm_count, p.partials_cap / nout_pad);
   int ctas = 0;
 
-  launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st);
+  launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st, box);
   cudaError_t e;
   {
     const double H = (double)nz * ny * (nx / 2 + 1);
-    ProfScope ps(p, ST_X_C2R_CONTRACT, p.ns * 8.0 * H + 4.0 * (double)p.nc, st);
+    // bytes: every row, or the box's rows (a half-spectrum row per shell and its N cells)
+    ProfScope ps(p, ST_X_C2R_CONTRACT, box ? 0.0 : p.ns * 8.0 * H + 4.0 * (double)p.nc,
+                 p.ns * 8.0 * (nx / 2 + 1) + 4.0 * nx, 0.0, box, st);
     const FftLen& f = p.fx_half;
     if (ns_pad == 16)
-      e = fft::run_xc16(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas, &ctas,
+      e = fft::run_xc16(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, ny, box, p.ns, f, p.stw[0], p.tw[0], max_ctas, &ctas,
                         p.partials, &p.dstate->status, st);
     else if (ns_pad == 8)
-      e = fft::run_xc_ns<8>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas,
+      e = fft::run_xc_ns<8>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, ny, box, p.ns, f, p.stw[0], p.tw[0], max_ctas,
                             &ctas, p.partials, &p.dstate->status, st);
     else if (ns_pad == 4)
-      e = fft::run_xc_ns<4>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas,
+      e = fft::run_xc_ns<4>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, ny, box, p.ns, f, p.stw[0], p.tw[0], max_ctas,
                             &ctas, p.partials, &p.dstate->status, st);
     else
-      e = fft::run_xc_ns<2>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, p.ns, f, p.stw[0], p.tw[0], max_ctas,
+      e = fft::run_xc_ns<2>(M, p.tmp, p.spec_elems, w0, nx, p.px, rows, ny, box, p.ns, f, p.stw[0], p.tw[0], max_ctas,
                             &ctas, p.partials, &p.dstate->status, st);
   }
   if (e != cudaSuccess) return cuda_status(e);

@@ -45,6 +45,23 @@ __host__ __device__ constexpr int xc_rows(int NS) { return NS >= kT ? 1 : kT / N
 __host__ __device__ constexpr int xc_spj(int NS) { return kT / xc_rows(NS); }         // shells per job
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 
+// The grid rows (y, z) a pass visits: with a support box (the cells where
+// W_0 may be nonzero, {x0, x1, y0, y1, z0, z1} inclusive, in device memory)
+// the rows with y0 <= y <= y1 and z0 <= z <= z1 in order, since the sums of
+// Eq. 11 vanish elsewhere; without one (box null) every row.
+struct RowMap {
+  int64_t ny, y0, nyb, z0;
+  int64_t count;  // rows visited
+  __device__ __forceinline__ int64_t row(int64_t c) const { return (z0 + c / nyb) * ny + y0 + c % nyb; }
+};
+
+__device__ __forceinline__ RowMap row_map(const int* box, int64_t rows, int ny) {
+  if (!box) return RowMap{ny, 0, ny, 0, rows};
+  const int y0 = box[2], y1 = box[3], z0 = box[4], z1 = box[5];
+  const int64_t nyb = y1 - y0 + 1, nzb = z1 - z0 + 1;
+  return RowMap{ny, y0, nyb > 0 ? nyb : 1, z0, nyb > 0 && nzb > 0 ? nyb * nzb : 0};
+}
+
 // Shared-memory layout of the fused kernel (byte offsets).
 struct XcLayout {
   size_t s0, s1, u, w, tws, twn, wst, nb0, nb1, total;
@@ -80,8 +97,9 @@ inline int xc_ntw(int M) {
 template <int MC, int NS>
 __global__ void __launch_bounds__(kThreads, 2)
     xc_contract_kernel(const float2* __restrict__ spec, int64_t spec_stride, const float* __restrict__ w0, int nx,
-                       int px, int64_t rows, int nshells, FftLen f, const float2* __restrict__ stw,
-                       const float2* __restrict__ tw, double* __restrict__ partials) {
+                       int px, int64_t rows, int ny, const int* __restrict__ box, int nshells, FftLen f,
+                       const float2* __restrict__ stw, const float2* __restrict__ tw,
+                       double* __restrict__ partials) {
   static_assert(NS == 2 || NS == 4 || NS == 8 || NS == 16, "padded shell counts");
   constexpr int ROWS = xc_rows(NS);
   constexpr int SPJ = xc_spj(NS);
@@ -117,28 +135,34 @@ __global__ void __launch_bounds__(kThreads, 2)
     else nbuf(r - NS)[c] = 0.0f;
   }
 
-  const int64_t ntiles = (rows + ROWS - 1) / ROWS;
+  const RowMap rm = row_map(box, rows, ny);
+  const int64_t ntiles = (rm.count + ROWS - 1) / ROWS;
   const int np = M / 2 + 1;  // 16-byte copies per staged row (X[0..M], see x_c2r_kernel)
   auto stage = [&](float2* s, float* nb, int64_t t, int q) {
-    const int64_t r0 = t * ROWS;
+    const int64_t r0 = t * ROWS;  // first visited row of the tile
     for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
       const int c = idx / np, k = 2 * (idx - c * np);
       const int i = c / SPJ, sh = q * SPJ + c % SPJ;
-      const bool ok = r0 + i < rows && sh < nshells;
-      cp_async16(s + c * LP + k, ok ? (const void*)(spec + sh * spec_stride + (r0 + i) * px + k) : (const void*)spec,
-                 ok);
+      const bool ok = r0 + i < rm.count && sh < nshells;
+      cp_async16(s + c * LP + k,
+                 ok ? (const void*)(spec + sh * spec_stride + rm.row(r0 + i) * px + k) : (const void*)spec, ok);
     }
     if (q == 0) {
-      const int64_t vc = (rows - r0 < ROWS ? rows - r0 : ROWS) * (int64_t)NX;  // valid cells of the tile
-      if (TC % 4 == 0) {  // tile starts on a 16-byte boundary of w0
+      const int vr = (int)(rm.count - r0 < ROWS ? rm.count - r0 : ROWS);  // visited rows of the tile
+      const int64_t vc = (int64_t)vr * NX;                                 // valid cells of the tile
+      if (NX % 4 == 0) {  // every row starts on a 16-byte boundary of w0
         for (int idx = threadIdx.x; idx < TC / 4; idx += kThreads) {
           const int64_t c4 = 4 * (int64_t)idx;
           const bool ok = c4 < vc;
-          cp_async16n(nb + c4, ok ? (const void*)(w0 + r0 * NX + c4) : (const void*)w0,
-                      ok ? (int)(vc - c4 >= 4 ? 16 : 4 * (vc - c4)) : 0);
+          const int i = (int)(c4 / NX);
+          cp_async16n(nb + c4, ok ? (const void*)(w0 + rm.row(r0 + i) * NX + (c4 - (int64_t)i * NX)) : (const void*)w0,
+                      ok ? 16 : 0);
         }
       } else {  // plain loads: the buffer is not read before the next barrier
-        for (int c = threadIdx.x; c < TC; c += kThreads) nb[c] = c < vc ? __ldg(w0 + r0 * NX + c) : 0.0f;
+        for (int c = threadIdx.x; c < TC; c += kThreads) {
+          const int i = c / NX;
+          nb[c] = c < vc ? __ldg(w0 + rm.row(r0 + i) * NX + (c - i * NX)) : 0.0f;
+        }
       }
     }
   };
@@ -346,8 +370,8 @@ struct XcrShape {
 template <int P, int Q, int NS>
 __global__ void __launch_bounds__(kThreads, 2)
     xcr_contract_kernel(const float2* __restrict__ spec, int64_t spec_stride, const float* __restrict__ w0, int px,
-                        int64_t rows, int nshells, const float2* __restrict__ tw, double* __restrict__ partials,
-                        int* status) {
+                        int64_t rows, int ny, const int* __restrict__ box, int nshells, const float2* __restrict__ tw,
+                        double* __restrict__ partials, int* status) {
   using S = XcrShape<P, Q, NS>;
   constexpr int M = S::M, NX = S::NX, LT = S::LT, ROWS = S::ROWS, TC = S::TC, LP = S::LP, TP = S::TP, WP = S::WP;
   constexpr int NOUT = NS + NS * (NS + 1) / 2;
@@ -377,23 +401,26 @@ __global__ void __launch_bounds__(kThreads, 2)
   fence_async_shared();  // zeroed buffers and barrier initialisation before any bulk copy
   __syncthreads();
 
-  const int64_t ntiles = (rows + ROWS - 1) / ROWS;
+  const RowMap rm = row_map(box, rows, ny);
+  const int64_t ntiles = (rm.count + ROWS - 1) / ROWS;
   // thread 0: bulk copies of tile t into staging buffer b and N buffer nbi
   // warp 0: lane 0 arms the barrier, then the lanes issue one copy each
+  // (a spectrum row per shell and visited row, and the row's N cells)
   auto stage = [&](int b, int nbi, int64_t t) {
-    const int64_t r0 = t * ROWS;
-    const int vr = (int)(rows - r0 < ROWS ? rows - r0 : ROWS);
+    const int64_t r0 = t * ROWS;  // first visited row of the tile
+    const int vr = (int)(rm.count - r0 < ROWS ? rm.count - r0 : ROWS);
     const uint32_t row_bytes = LP * sizeof(float2);
     if (lane == 0)
       mbar_arrive_expect_tx(&full[b], (uint32_t)(nsv * vr) * row_bytes + (uint32_t)(vr * NX * sizeof(float)));
     __syncwarp();
     const int nrows = nsv * vr;
-    for (int j = lane; j <= nrows; j += 32) {
+    for (int j = lane; j < nrows + vr; j += 32) {
       if (j < nrows) {
         const int sh = j / vr, i = j - sh * vr;
-        bulk_g2s(sbuf(b) + (sh * ROWS + i) * LP, spec + sh * spec_stride + (r0 + i) * px, row_bytes, &full[b]);
+        bulk_g2s(sbuf(b) + (sh * ROWS + i) * LP, spec + sh * spec_stride + rm.row(r0 + i) * px, row_bytes, &full[b]);
       } else {
-        bulk_g2s(nbuf(nbi), w0 + r0 * NX, (uint32_t)(vr * NX * sizeof(float)), &full[b]);
+        const int i = j - nrows;
+        bulk_g2s(nbuf(nbi) + i * NX, w0 + rm.row(r0 + i) * NX, (uint32_t)(NX * sizeof(float)), &full[b]);
       }
     }
   };
@@ -428,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     float* W = reinterpret_cast<float*>(sbuf(kt & 1));
     const int64_t r0 = t * ROWS;
-    const int vc = (int)(rows - r0 < ROWS ? rows - r0 : ROWS) * NX;  // cells of the tile with data
+    const int vc = (int)(rm.count - r0 < ROWS ? rm.count - r0 : ROWS) * NX;  // cells of the tile with data
     // step A: unpack Z[Q k1 + k2] = (X[k] + conj X[M-k]) + i e^{2 pi i k/NX} (X[k] - conj X[M-k]),
     // P-point inverse DFT over k1, twiddle e^{2 pi i k2 m1 / M}, into T
     if (tid < LT * Q) {

@@ -821,6 +821,40 @@ def check_xi_nonpositive_den(o) -> bool:
     return True
 
 
+def check_slab_decomposition(o) -> bool:
+    """Reading 14: a zero-outside box cut into 2 and 3 slabs along z, each
+    slab a box of its own (origin shifted) holding its owned planes plus a
+    halo of max|m_z| planes on either side (clipped at the faces), summed
+    over its owned planes with the whole catalog's alpha: the slabs' num and
+    den add up to the undivided box's (Eq. 19), which the brute-force pins
+    fix."""
+    g = GridSpec((10, 9, 18), (0.0, 0.0, 0.0), 1.0, False)
+    rng = _rng(41)
+    cd = np.stack([rng.integers(2, 8, 70), rng.integers(2, 7, 70), rng.integers(2, 16, 70)], 1)
+    cr = np.stack([rng.integers(2, 8, 500), rng.integers(2, 7, 500), rng.integers(2, 16, 500)], 1)
+    data, rand = lattice_catalog(g, cd), lattice_catalog(g, cr)
+    shells = (1.5, 2.5)
+    whole = o.correlate(g, shells, 1.0, data, rand, orders=(2, 3), engine="direct")
+    halo = int(max(np.abs(o.shell_offsets(s, 1.0, 1.0))[:, 2].max() for s in shells))
+    for parts in (2, 3):
+        edges = np.linspace(0, 18, parts + 1).astype(int)
+        num = {n: 0.0 for n in (2, 3)}
+        den = {n: 0.0 for n in (2, 3)}
+        for z0, z1 in zip(edges[:-1], edges[1:]):
+            lo, hi = max(0, z0 - halo), min(18, z1 + halo)
+            gs = GridSpec((10, 9, hi - lo), (0.0, 0.0, float(lo)), 1.0, False)
+            r = o.correlate(gs, shells, 1.0, data, rand, orders=(2, 3), engine="direct",
+                            alpha=whole["alpha"], owned_z=(z0 - lo, z1 - lo))
+            for n in (2, 3):
+                num[n] = num[n] + r[f"num{n}"]
+                den[n] = den[n] + r[f"den{n}"]
+        for n in (2, 3):
+            if not (np.allclose(num[n], whole[f"num{n}"], rtol=1e-12, atol=1e-9)
+                    and np.allclose(den[n], whole[f"den{n}"], rtol=1e-12, atol=1e-9)):
+                return False
+    return True
+
+
 ALL_CHECKS = [
     check_lattice_gridding, check_out_of_grid, check_alpha_and_fields, check_shell_counts,
     check_intersect_rule, check_kernel_spectrum, check_pair_counts, check_triplet_counts,
@@ -829,5 +863,5 @@ ALL_CHECKS = [
     check_region_additivity, check_diagonal, check_sum_of_w, check_sampled_cells,
     check_multisets, check_guard_band, check_pair_sums_fft, check_grid_weights, check_sky_coordinates,
     check_factorised_randoms, check_delta_field, check_field_sums, check_product_map,
-    check_periodic_support, check_xi_nonpositive_den,
+    check_periodic_support, check_xi_nonpositive_den, check_slab_decomposition,
 ]

@@ -8,7 +8,9 @@ oracle can compute at this size:
   autocorrelation route (one FP64 FFT pair per field);
 * W_s at sampled cells, one by one by direct summation;
 * the random bank's sum rule sum_r (R***K_s) = (sum_r R) |O_s|;
-* symmetry and finiteness of the order-3 tensors.
+* symmetry and finiteness of the order-3 tensors, and the mixed form's
+  order-3 sums (fused pass over the box of occupied cells, split-TF32
+  tensor cores) against the plain form's (every cell, FP32 CUDA cores).
 """
 import numpy as np
 import pytest
@@ -22,6 +24,9 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
+_ORDER3 = {}
+
+
 @pytest.fixture(scope="module", params=["split_tf32", "fp32"])
 def run(request):
     torch = cuda_torch()
@@ -31,6 +36,7 @@ def run(request):
     plan.set_randoms(*dev_cat(torch, w["randoms"]))
     bank_r = {s: plan.bank(s).cpu().numpy() for s in (0, 7, 15)}
     res = plan.compute(*dev_cat(torch, w["data"]), orders=(2, 3), out="host")
+    _ORDER3[request.param] = {k: res[k][3].numpy().copy() for k in ("num", "den")}
     D, R = plan.grids()
     out = dict(w=w, g=g, plan=plan, res=res, bank_r=bank_r, D=D.cpu().numpy().astype(np.uint32),
                R=R.cpu().numpy().astype(np.uint32), N=plan.field(0).cpu().numpy(),
@@ -96,3 +102,15 @@ def test_order3_structure(run):
         assert np.all(np.isfinite(T))
         assert np.array_equal(T, T.T)
     assert np.all(run["res"]["den"][3].numpy() > 0)
+
+
+def test_order3_forms_agree(run):
+    """Once both forms have run: the two independent order-3 paths agree.
+    Each is within 1e-5 of the exact sums relative to the sum of |terms|;
+    the bound below is a thousandth of the largest entry, far above that
+    and far below what a missed row or plane of the box would cost."""
+    if len(_ORDER3) < 2:
+        pytest.skip("needs both forms (runs with the second parameter)")
+    for key in ("num", "den"):
+        a, b = _ORDER3["split_tf32"][key], _ORDER3["fp32"][key]
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(b).max(), key

@@ -173,6 +173,21 @@ def xi_divides_anyway(num, den):
         return np.asarray(num, np.float64) / np.asarray(den, np.float64)
 
 
+_orig_corr = O.correlate
+
+
+def slab_own_alpha(*a, **kw):
+    # each region normalised by its own randoms instead of the whole catalog's
+    kw.pop("alpha", None)
+    return _orig_corr(*a, **kw)
+
+
+def slab_halo_summed(*a, **kw):
+    # the halo planes counted in the sums as well as the owned planes
+    kw.pop("owned_z", None)
+    return _orig_corr(*a, **kw)
+
+
 MUTANTS = [
     ("density_fields", wrong_sign_density),
     ("cell_index", off_by_one_index),
@@ -194,6 +209,8 @@ MUTANTS = [
     ("check_periodic_support", support_wrong_axis),
     ("xi_from", xi_keeps_negative),
     ("xi_from", xi_divides_anyway),
+    ("correlate", slab_own_alpha),
+    ("correlate", slab_halo_summed),
 ]
 
 

@@ -102,3 +102,67 @@ def test_two_rank_region_combination():
             assert np.allclose(num[n], want[n][0], rtol=1e-12, atol=0)
             assert np.allclose(den[n], want[n][1], rtol=1e-12, atol=0)
             assert np.allclose(xi[n], want[n][2], rtol=1e-12, atol=0)
+
+
+SLAB_SHELLS = (1.5, 2.5)
+
+
+def _slab_case():
+    g = GridSpec((10, 9, 20), (0.0, 0.0, 0.0), 1.0, False)
+    rng = np.random.default_rng(91)
+    cd = np.stack([rng.integers(2, 8, 90), rng.integers(2, 7, 90), rng.integers(2, 18, 90)], 1)
+    cr = np.stack([rng.integers(2, 8, 700), rng.integers(2, 7, 700), rng.integers(2, 18, 700)], 1)
+    return g, lattice_catalog(g, cd), lattice_catalog(g, cr)
+
+
+def _slab_worker(rank, world, port, q):
+    """One slab per rank: select the slab's points on the host, agree on the
+    whole catalog's alpha (all-reduce of the owned counts), sum the owned
+    planes of the slab box (the oracle stands in for the library on a
+    rank without a GPU) and combine through combine_regions."""
+    from paper_2108_00015_gb300.parallel import global_alpha, in_planes, slab_box, slab_planes
+    from synth import Catalog
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g, data, rand = _slab_case()
+        nz = g.n[2]
+        halo = int(max(np.abs(O.shell_offsets(s, 1.0, g.cell))[:, 2].max() for s in SLAB_SHELLS))
+        z0, z1 = slab_planes(nz, world, rank)
+        lo, hi = slab_box(nz, z0, z1, halo)
+        pick = lambda c, a, b: Catalog(*(v[in_planes(c.z, g.origin[2], g.cell, a, b)] for v in (c.x, c.y, c.z)))  # noqa: E731
+        alpha = global_alpha(pick(data, z0, z1).n, pick(rand, z0, z1).n)
+        gs = GridSpec((g.n[0], g.n[1], hi - lo), (g.origin[0], g.origin[1], g.origin[2] + lo * g.cell), g.cell, False)
+        r = O.correlate(gs, SLAB_SHELLS, 1.0, pick(data, lo, hi), pick(rand, lo, hi), orders=(2, 3),
+                        engine="direct", alpha=alpha, owned_z=(z0 - lo, z1 - lo))
+        num = {n: torch.from_numpy(r[f"num{n}"]) for n in (2, 3)}
+        den = {n: torch.from_numpy(r[f"den{n}"]) for n in (2, 3)}
+        cn, cd, cx = combine_regions(num, den)
+        q.put((rank, alpha, {n: cn[n].numpy() for n in cn}, {n: cd[n].numpy() for n in cd},
+               {n: cx[n].numpy() for n in cx}))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_slab_decomposition():
+    """A catalog cut into two z slabs over two gloo ranks gives the undivided
+    catalog's num, den and xi (Eq. 19 with the whole catalog's alpha)."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    g, data, rand = _slab_case()
+    whole = O.correlate(g, SLAB_SHELLS, 1.0, data, rand, orders=(2, 3), engine="direct")
+    for rank, alpha, num, den, xi in res:
+        assert alpha == pytest.approx(whole["alpha"], rel=1e-15)
+        for n in (2, 3):
+            assert np.allclose(num[n], whole[f"num{n}"], rtol=1e-12, atol=1e-9)
+            assert np.allclose(den[n], whole[f"den{n}"], rtol=1e-12, atol=1e-9)
+            assert np.allclose(xi[n], O.xi_from(whole[f"num{n}"], whole[f"den{n}"]), rtol=1e-11, atol=0)
