@@ -54,6 +54,9 @@ def _args():
                     help="headline form: mixed split-TF32 tensor-core sums (fused pass), split-BF16 or "
                          "split-FP16 tensor-core sums (kind::f16, bank kept), or plain FP32")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form beside the headline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the higher-order workloads timed beside the headline at N = 1 (stress256: xi_2..xi_5, "
+                         "survey512_s32: xi_2..xi_4, in every contraction form)")
     ap.add_argument("--diagonal", action="store_true",
                     help="time ck_set_randoms_diagonal + ck_compute_diagonal (Eq. 14, the (s, .., s) entries "
                          "only) instead of ck_set_randoms + ck_compute; "
@@ -219,7 +222,39 @@ def _orders(args, w):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle leg (bounded sample, extrapolated per stage)
+# CPU oracle legs
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_engine_catalog(w, orders):
+    """One whole catalog through the oracle's FP64 C++/OpenMP engine on all
+    host cores (gridding, forward FFT, every shell's convolution, the sums
+    of every requested order): wall-clock ms, and the description."""
+    from oracle import cpu_engine
+    t0 = time.perf_counter()
+    cpu_engine.correlate(w["grid"], w["shells"], w["width"], w["data"], w["randoms"], orders=orders, engine="fft")
+    ms = (time.perf_counter() - t0) * 1000.0
+    n = cpu_engine.threads()
+    return ms, n, (f"the whole catalog ({w['data'].n} + {w['randoms'].n} points, {len(w['shells'])} shells, orders "
+                   f"{list(orders)}) through the oracle's FP64 C++/OpenMP engine (FFT convolution) on {n} threads, "
+                   f"{os.cpu_count()} host cores ({cpu_model()}); no scaling")
+
 
 def cpu_oracle_sample(w, orders, point_frac=1 / 8, fields=2):
     """Time the FP64 oracle on a bounded sample of the workload and scale each
@@ -307,6 +342,99 @@ def cpu_oracle_mode_sample(w, orders, mode, maps=None, selection=None, cells=200
 
 
 # ---------------------------------------------------------------------------
+
+def _time_extra(torch, w, orders, precision, steps, warmup):
+    """One higher-order workload in one form: ck_set_randoms + ck_compute
+    per step on device-resident catalogs, CUDA events around `steps` steps
+    after `warmup`, the library's per-launch times for the roofline of the
+    tensor-core contraction (or of the dominant stage), clocks sampled
+    meanwhile."""
+    import numpy as np
+    from paper_2108_00015_gb300 import Plan
+    g = w["grid"]
+    ns = len(w["shells"])
+    plan = Plan(g.n, g.origin, g.cell, g.periodic, w["shells"], w["width"], max_order=max(orders),
+                precision=precision)
+    d, r = w["data"], w["randoms"]
+    dev = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    dx, dy, dz, rx, ry, rz = (dev(a) for a in (d.x, d.y, d.z, r.x, r.y, r.z))
+    outs = {k: {n: torch.empty((ns,) * (n - 1), dtype=torch.float64, device="cuda") for n in orders}
+            for k in ("xi", "num", "den")}
+    outs["dropped"] = torch.zeros(2, dtype=torch.int64, device="cuda")
+
+    def step():
+        plan.set_randoms(rx, ry, rz)
+        return plan.compute(dx, dy, dz, orders=orders, out="device", outputs=outs)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if plan.status() != 0:
+        raise RuntimeError(f"device status after warm-up ({precision})")
+    stream = torch.cuda.current_stream()
+    plan.profile(True)
+    clocks = Clocks(_smi_index(torch, torch.cuda.current_device()))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    stages = plan.profile_read()
+    plan.profile(False)
+    if plan.status() != 0:
+        raise RuntimeError(f"device status in the timed region ({precision})")
+    plan.close()
+    out = {"ms_per_catalog": round(t_ms / steps, 3), "steps": steps, "clocks": clk}
+    dname, dv = max(stages.items(), key=lambda kv: kv[1]["ms"])
+    t_launch = dv["ms"] / dv["launches"] * 1e-3
+    out["dominant"] = {"stage": dname, "ms_per_step": round(dv["ms"] / steps, 3)}
+    if "contract" in stages and precision.startswith("split_"):
+        cv = stages["contract"]
+        tc = cv["ms"] / cv["launches"] * 1e-3
+        dense, useful = _tc_work(ns, orders)
+        nc = int(np.prod(g.n))
+        flops = 3 * 2 * dense * nc
+        tpk, tkind = _tensor_peak(precision)
+        out["roofline"] = {"bound": "tensor", "kernel": "contract", "achieved": round(flops / tc / 1e12, 1),
+                           "peak": round(tpk, 1), "unit": "TFLOP/s", "frac": round(flops / tc / 1e12 / tpk, 4),
+                           "algorithmic_flops_per_launch": flops, "ms_per_launch": round(tc * 1e3, 3),
+                           "useful_tflops": round(2 * useful * nc / tc / 1e12, 1),
+                           "peak_source": f"{tkind} MEASURED_PEAKS.json bf16_tflops_sustained"
+                                          + (f" x {TF32_PER_BF16:.3f} (nominal TF32/BF16)" if precision == "split_tf32"
+                                             else " (dense BF16/FP16 rate)")}
+    else:
+        peak, _ = _peaks()
+        gbs = dv["bytes"] / (dv["ms"] * 1e-3) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": dname, "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                           "frac": round(gbs / peak, 4)}
+    return out
+
+
+def run_extras(torch, steps, warmup):
+    """The metric's higher orders beside the headline: xi_2..xi_5 on the
+    256^3 stress catalog (20M + 40M points, 16 shells) and xi_2..xi_4 on the
+    512^3 survey catalog with 32 shells, each in the mixed forms (split-TF32,
+    split-BF16, split-FP16 tensor-core sums) and the plain FP32 form."""
+    from synth import workload
+    res = {}
+    for name, orders, forms, plain_steps in (("stress256", (2, 3, 4, 5), ("split_tf32", "split_bf16", "split_fp16"), 3),
+                                             ("survey512_s32", (2, 3, 4), ("split_tf32", "split_bf16", "split_fp16"), 1)):
+        w = workload(name)
+        ent = {"grid": list(w["grid"].n), "shells": len(w["shells"]), "orders": list(orders),
+               "n_data": w["data"].n, "n_randoms": w["randoms"].n, "forms": {}}
+        for prec in forms:
+            ent["forms"][prec] = _time_extra(torch, w, orders, prec, steps, warmup)
+        ent["forms"]["fp32"] = _time_extra(torch, w, orders, "fp32", plain_steps, 1)
+        best = min(ent["forms"][p]["ms_per_catalog"] for p in forms)
+        ent["mixed_speedup_over_plain"] = round(ent["forms"]["fp32"]["ms_per_catalog"] / best, 2)
+        res[name] = ent
+        del w
+    return res
+
 
 def run_gb300(args):
     import numpy as np
@@ -481,9 +609,14 @@ def run_gb300(args):
             ms, sample = cpu_oracle_mode_sample(w, orders, "continuous",
                                                 maps=(map_d.cpu().numpy(), map_r.cpu().numpy()))
         else:
-            ms, sample = cpu_oracle_sample(w, orders)
-        cpu = {"value": round(ms, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample,
-               "wall_s": round(time.perf_counter() - t0, 1)}
+            ms, nth, sample = cpu_engine_catalog(w, orders)
+        if args.factorised or args.continuous:
+            cpu = {"value": round(ms, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample,
+                   "wall_s": round(time.perf_counter() - t0, 1)}
+        else:
+            cpu = {"value": round(ms, 1), "unit": "ms/catalog", "cores": nth, "kind": "oracle", "sample": sample,
+                   "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+                   "wall_s": round(time.perf_counter() - t0, 1)}
 
     plan.close()
     forms = {precision: {"ms_per_catalog": round(t_ms / (args.steps * ws), 4)}}
@@ -518,6 +651,12 @@ def run_gb300(args):
         forms["fp32"] = {"ms_per_catalog": round(tp / (args.steps * ws), 4)}
         forms["mixed_speedup_over_plain"] = round(tp / t_ms, 3)
 
+    extras = None
+    if ws == 1 and not args.no_extras and args.workload == "survey512" and not (
+            args.diagonal or args.factorised or args.continuous):
+        torch.cuda.empty_cache()
+        extras = run_extras(torch, max(2, min(args.steps, 5)), 2)
+
     value = t_ms / (args.steps * ws)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms/catalog", "n_gpus": ws, "steps": args.steps,
@@ -545,6 +684,7 @@ def run_gb300(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "higher_orders": extras,
     }
     if ws > 1:
         dist.destroy_process_group()
@@ -637,14 +777,19 @@ def run_reference(args):
     from synth import workload
     w = workload(args.workload)
     orders = _orders(args, w)
-    # each step: the oracle on a smaller bounded sample
+    # each step: one whole catalog through the oracle's FP64 C++/OpenMP engine
+    from oracle import cpu_engine
+    cpu_engine.build()
     for _ in range(args.warmup):
-        cpu_oracle_sample(w, orders, point_frac=1 / 32)
+        cpu_engine_catalog(w, orders)
     vals = []
     sample = None
+    nth = cpu_engine.threads()
+    t_run = time.perf_counter()
     for _ in range(args.steps):
-        ms, sample = cpu_oracle_sample(w, orders, point_frac=1 / 32)
+        ms, nth, sample = cpu_engine_catalog(w, orders)
         vals.append(ms)
+    wall = time.perf_counter() - t_run
     value = statistics.mean(vals)
     g = w["grid"]
     line = {
@@ -652,8 +797,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(value, 1), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(g.n), "shells": len(w["shells"]), "orders": list(orders)},
-        "cpu_baseline": {"value": round(value, 1), "unit": "ms/catalog", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(value, 1), "unit": "ms/catalog", "cores": nth, "kind": "oracle",
+                         "sample": sample, "cpu_model": cpu_model(), "host_cores": os.cpu_count()},
         "e2e": {"value": round(value, 1), "unit": "ms/catalog", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "timed_wall_s": round(wall, 1),
     }
     print(json.dumps(line))
 
