@@ -343,6 +343,22 @@ def cpu_oracle_mode_sample(w, orders, mode, maps=None, selection=None, cells=200
 
 # ---------------------------------------------------------------------------
 
+def _summed_cells(w):
+    """Cells the bank contractions visit: the planes between the lowest and
+    the highest occupied z cell of the data and the randoms (the library
+    sums only those planes; W_0 vanishes elsewhere)."""
+    import numpy as np
+    g = w["grid"]
+    zs = []
+    for c in (w["data"], w["randoms"]):
+        k = np.floor((c.z.astype(np.float64) - g.origin[2]) / g.cell).astype(np.int64)
+        k = np.mod(k, g.n[2]) if g.periodic else k[(k >= 0) & (k < g.n[2])]
+        if k.size:
+            zs += [int(k.min()), int(k.max())]
+    planes = max(zs) - min(zs) + 1 if zs else 0
+    return planes * g.n[0] * g.n[1]
+
+
 def _time_extra(torch, w, orders, precision, steps, warmup):
     """One higher-order workload in one form: ck_set_randoms + ck_compute
     per step on device-resident catalogs, CUDA events around `steps` steps
@@ -396,10 +412,11 @@ def _time_extra(torch, w, orders, precision, steps, warmup):
         cv = stages["contract"]
         tc = cv["ms"] / cv["launches"] * 1e-3
         dense, useful = _tc_work(ns, orders)
-        nc = int(np.prod(g.n))
+        nc = _summed_cells(w)
         flops = 3 * 2 * dense * nc
         tpk, tkind = _tensor_peak(precision)
         out["roofline"] = {"bound": "tensor", "kernel": "contract", "achieved": round(flops / tc / 1e12, 1),
+                           "cells_summed": nc,
                            "peak": round(tpk, 1), "unit": "TFLOP/s", "frac": round(flops / tc / 1e12 / tpk, 4),
                            "algorithmic_flops_per_launch": flops, "ms_per_launch": round(tc * 1e3, 3),
                            "useful_tflops": round(2 * useful * nc / tc / 1e12, 1),
@@ -550,7 +567,7 @@ def run_gb300(args):
     if dname == "contract" and args.precision.startswith("split_") and not plan.fused and not args.diagonal:
         # the tcgen05 blocked product: three split products per operand pair
         dense, useful = _tc_work(len(w["shells"]), orders)
-        nc = int(np.prod(w["grid"].n))
+        nc = _summed_cells(w)
         flops = 3 * 2 * dense * nc
         t_launch = dv["ms"] / dv["launches"] * 1e-3
         tpk, tkind = _tensor_peak(args.precision)

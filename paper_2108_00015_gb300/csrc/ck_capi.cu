@@ -153,7 +153,7 @@ ck_status carve(Plan& p) {
   p.dense = reinterpret_cast<double*>(take((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8));
   p.dense_map = reinterpret_cast<int*>(take((size_t)std::max<int64_t>(p.dense_total, 1) * 4));
   p.table_arena = take(p.table_arena_cap);
-  p.support = reinterpret_cast<int*>(take(6 * 4));
+  p.support = reinterpret_cast<int*>(take(12 * 4));
   p.absmax = reinterpret_cast<unsigned*>(take((size_t)(CK_MAX_SHELLS + 1) * 4));
   const size_t used = (size_t)(b - static_cast<unsigned char*>(p.ws));
   return used <= p.ws_bytes ? CK_OK : CK_ERR_OOM;
@@ -311,7 +311,8 @@ ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, 
 ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, const float* w0 = nullptr,
                            int support = -1) {
   if (!w0) w0 = p.field;
-  launch_fft_forward(p, p.field, p.spec, st);
+  if (support >= 0) launch_support_box(p, support, st);
+  launch_fft_forward(p, p.field, p.spec, st, support >= 0 ? p.support + 6 : nullptr);
   if (p.region && w0 == p.field) {
     const size_t plane = (size_t)p.grid.n[0] * p.grid.n[1];
     if (p.region_z0 > 0) CK_TRY(cudaMemsetAsync(p.field, 0, plane * p.region_z0 * sizeof(float), st));
@@ -319,12 +320,9 @@ ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, con
       CK_TRY(cudaMemsetAsync(p.field + plane * p.region_z1, 0, plane * (p.grid.n[2] - p.region_z1) * sizeof(float),
                              st));
   }
-  if (p.fused) {
-    if (support >= 0) launch_support_box(p, support, st);
-    return launch_convolve_contract(p, w0, sums, st, support >= 0 ? p.support : nullptr);
-  }
+  if (p.fused) return launch_convolve_contract(p, w0, sums, st, support >= 0 ? p.support : nullptr);
   launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
-  return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st);
+  return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st, support >= 0 ? p.support : nullptr);
 }
 
 int full_mask(const Plan& p) {

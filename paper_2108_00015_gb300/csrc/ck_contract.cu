@@ -105,7 +105,7 @@ __device__ uint64_t g_force_timeout_ns = 0;
 template <int NS, int MAXN, int G>
 __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
     contract_reg_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
-                        int64_t chunks_per_cta, double* __restrict__ partials, int* status) {
+                        const int* __restrict__ box, int64_t plane, double* __restrict__ partials, int* status) {
   static_assert(G == 1 || (G == 2 && MAXN == 3), "two consumer groups only for orders <= 3");
   constexpr int NARR = NS + 1;
   constexpr int NOUT = RegOut<NS, MAXN>::total;
@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
   uint64_t* never = empty + RK_STAGES + 1;  // armed by nobody (ck_debug_force_timeout)
   double* wacc = reinterpret_cast<double*>(empty + RK_STAGES + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nchunks = (nc + RK_KC - 1) / RK_KC;
+  // chunks of the visited cells [cr.lo, cr.hi), shared out evenly over the CTAs
+  const CellRange cr = box_cells(box, plane, nc);
+  const int64_t nchunks = (cr.hi - cr.lo + RK_KC - 1) / RK_KC;
+  const int64_t chunks_per_cta = (nchunks + gridDim.x - 1) / gridDim.x;
   const int64_t c0 = (int64_t)blockIdx.x * chunks_per_cta;
   const int64_t c1 = std::min<int64_t>(c0 + chunks_per_cta, nchunks);
   const int nit = (int)std::max<int64_t>(c1 - c0, 0);
@@ -143,8 +146,8 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
         const int st = it % RK_STAGES;
         const uint32_t ph = (uint32_t)(it / RK_STAGES) & 1u;
         if (it >= RK_STAGES && !mbar_wait(&empty[st], ph ^ 1u, status)) break;
-        const int64_t cell0 = (c0 + it) * RK_KC;
-        const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
+        const int64_t cell0 = cr.lo + (c0 + it) * RK_KC;
+        const int64_t rem = std::min<int64_t>(RK_KC, cr.hi - cell0);
         const uint32_t bytes = (uint32_t)((rem / 4) * 16);
         mbar_arrive_expect_tx(&full[st], bytes * NARR);
         if (bytes) {
@@ -170,8 +173,8 @@ __global__ void __launch_bounds__(32 * (RK_CW * G + 1), 1)
       const int st = it % RK_STAGES;
       const uint32_t ph = (uint32_t)(it / RK_STAGES) & 1u;
       if (!mbar_wait(&full[st], ph, status)) break;
-      const int64_t cell0 = (c0 + it) * RK_KC;
-      const int64_t rem = std::min<int64_t>(RK_KC, nc - cell0);
+      const int64_t cell0 = cr.lo + (c0 + it) * RK_KC;
+      const int64_t rem = std::min<int64_t>(RK_KC, cr.hi - cell0);
       const int64_t whole = rem / 4 * 4;
 #pragma unroll
       for (int u = 0; u < RK_CPT; ++u) {
@@ -232,13 +235,13 @@ static size_t reg_smem() {
 
 template <int NS, int MAXN>
 static cudaError_t launch_reg_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ctas,
-                                int64_t cpc, double* partials, int* status, cudaStream_t st) {
+                                const int* box, int64_t plane, double* partials, int* status, cudaStream_t st) {
   constexpr int G = reg_groups<NS, MAXN>();
   const size_t sm = reg_smem<NS, MAXN>();
   cudaError_t e = cudaFuncSetAttribute(contract_reg_kernel<NS, MAXN, G>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  contract_reg_kernel<NS, MAXN, G><<<ctas, 32 * (RK_CW * G + 1), sm, st>>>(w0, bank, bstride, nc, cpc, partials,
+  contract_reg_kernel<NS, MAXN, G><<<ctas, 32 * (RK_CW * G + 1), sm, st>>>(w0, bank, bstride, nc, box, plane, partials,
                                                                            status);
   return cudaGetLastError();
 }
@@ -252,12 +255,13 @@ static int reg_nout(int ns, int maxn) {
 }
 
 #define CK_REG_CASE3(N) \
-  case N: return launch_reg_t<N, 3>(w0, bank, bstride, nc, ctas, cpc, partials, status, st);
+  case N: return launch_reg_t<N, 3>(w0, bank, bstride, nc, ctas, box, plane, partials, status, st);
 #define CK_REG_CASE5(N) \
-  case N: return launch_reg_t<N, 5>(w0, bank, bstride, nc, ctas, cpc, partials, status, st);
+  case N: return launch_reg_t<N, 5>(w0, bank, bstride, nc, ctas, box, plane, partials, status, st);
 
 static cudaError_t launch_reg(int ns, int maxn, const float* w0, const float* bank, int64_t bstride, int64_t nc,
-                              int ctas, int64_t cpc, double* partials, int* status, cudaStream_t st) {
+                              int ctas, const int* box, int64_t plane, double* partials, int* status,
+                              cudaStream_t st) {
   if (maxn <= 3) {
     switch (ns) {
       CK_REG_CASE3(1) CK_REG_CASE3(2) CK_REG_CASE3(3) CK_REG_CASE3(4) CK_REG_CASE3(5) CK_REG_CASE3(6)
@@ -300,7 +304,8 @@ __global__ void __launch_bounds__(256) contract_blocked_kernel(const float* __re
                                                                const int2* __restrict__ rowdesc, int rows,
                                                                const int2* __restrict__ coldesc, int cols,
                                                                const int2* __restrict__ tiles, int ntiles,
-                                                               int64_t cells_per_split, double* __restrict__ partials) {
+                                                               const int* __restrict__ box, int64_t plane,
+                                                               double* __restrict__ partials) {
   constexpr int BK_KC = bk_kc<T>();
   __shared__ T ws[CK_MAX_SHELLS + 1][BK_KC];
   __shared__ __align__(16) T As[BK_KC][BK_T];
@@ -322,8 +327,8 @@ __global__ void __launch_bounds__(256) contract_blocked_kernel(const float* __re
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); dacc[i][j] = 0.0; }
-  const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
-  const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
+  int64_t beg, end;  // this split's part of the visited cells (32-cell multiples)
+  split_cells(box_cells(box, plane, nc), gridDim.y, 32, blockIdx.y, &beg, &end);
   int since = 0;
   __syncthreads();
   for (int64_t c0 = beg; c0 < end; c0 += BK_KC) {
@@ -582,7 +587,8 @@ ck_status contract_prepare(Plan& p, int mask) {
 }
 
 ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank, int64_t bstride,
-                          double* sums, cudaStream_t st) {
+                          double* sums, cudaStream_t st, const int* box) {
+  const int64_t plane = (int64_t)p.grid.n[0] * p.grid.n[1];
   ck_status s = contract_prepare(p, mask);
   if (s != CK_OK) return s;
   const ContractPlan& c = p.cplan[mask];
@@ -590,9 +596,9 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
   if (c.use_reg) {
     cudaError_t e;
     {
-    ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc, st);
-    e = launch_reg(p.ns, c.reg_maxn, w0, bank, bstride, p.nc, c.ctas, c.chunks_per_cta, p.partials,
-                               status, st);
+    ProfScope ps(p, ST_CONTRACT, box ? 0.0 : 4.0 * (double)(p.ns + 1) * (double)p.nc, 0.0,
+                 4.0 * (p.ns + 1) * (double)plane, box, st);
+    e = launch_reg(p.ns, c.reg_maxn, w0, bank, bstride, p.nc, c.ctas, box, plane, p.partials, status, st);
     }
     if (e != cudaSuccess) return cuda_status(e);
     ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);
@@ -604,13 +610,14 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
   if (c.use_tc) {
     cudaError_t e;
     {
-      ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, st);
+      ProfScope ps(p, ST_CONTRACT, box ? 0.0 : 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, 0.0,
+                   4.0 * (p.ns + 1) * (double)plane * c.n_tiles, box, st);
       e = launch_umma(c.um_tn, c.um_kind, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc,
-                      c.d_um_tiles, c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, c.um_cps, p.absmax, p.partials, status,
-                      st);
+                      c.d_um_tiles, c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, box, plane, p.absmax, p.partials,
+                      status, st);
       if (e == cudaSuccess)
         e = launch_umma_thin(w0, bank, bstride, p.nc, p.ns, c.um_thin_rmax, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
-                             c.d_um_cols, c.um_ntc, c.n_tiles - c.um_ntc, c.n_tiles, c.um_tn, c.splits, c.um_cps,
+                             c.d_um_cols, c.um_ntc, c.n_tiles - c.um_ntc, c.n_tiles, c.um_tn, c.splits, box, plane,
                              p.partials, st);
     }
     if (e != cudaSuccess) return cuda_status(e);
@@ -618,18 +625,17 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
     return cuda_status(launch_umma_reduce(p.partials, c.splits, c.n_tiles, c.um_tn, c.d_um_tiles, c.d_um_cols,
                                           c.d_rowdesc, c.rows, c.d_coldesc, mask, p.ns, p.multiset_base, sums, st));
   }
-  const int64_t cps = (p.nc + c.splits - 1) / c.splits;
-  const int64_t cps_al = (cps + 31) / 32 * 32;
   dim3 grid((unsigned)c.n_tiles, (unsigned)c.splits);
   {
-  ProfScope ps(p, ST_CONTRACT, 4.0 * (double)(p.ns + 1) * (double)p.nc, st);
+  ProfScope ps(p, ST_CONTRACT, box ? 0.0 : 4.0 * (double)(p.ns + 1) * (double)p.nc, 0.0,
+               4.0 * (p.ns + 1) * (double)plane, box, st);
   if (p.precision == CK_PREC_FP64_SUM)
     contract_blocked_kernel<double><<<grid, 256, 0, st>>>(w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows,
-                                                          c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, cps_al,
+                                                          c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, box, plane,
                                                           p.partials);
   else
     contract_blocked_kernel<float><<<grid, 256, 0, st>>>(w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows,
-                                                         c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, cps_al,
+                                                         c.d_coldesc, c.cols, c.d_tiles, c.n_tiles, box, plane,
                                                          p.partials);
   }
   ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);
@@ -770,9 +776,7 @@ extern "C" ck_status ck_contract_static(const float* w0, const float* bank, int6
   double* partials = static_cast<double*>(base);
   int* status = reinterpret_cast<int*>(partials + (size_t)ctas * nout);
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return CK_ERR_CUDA;
-  const int64_t nchunks = (n_cells + RK_KC - 1) / RK_KC;
-  const int64_t cpc = (nchunks + ctas - 1) / ctas;
-  cudaError_t e = launch_reg(n_shells, reg_maxn, w0, bank, bank_stride, n_cells, ctas, cpc, partials, status, st);
+  cudaError_t e = launch_reg(n_shells, reg_maxn, w0, bank, bank_stride, n_cells, ctas, nullptr, 0, partials, status, st);
   if (e != cudaSuccess) return cuda_status(e);
   double* o[CK_MAX_ORDER + 1] = {nullptr};
   for (int n = 2; n <= CK_MAX_ORDER; ++n) o[n] = ((order_mask >> n) & 1) ? sums[n] : nullptr;

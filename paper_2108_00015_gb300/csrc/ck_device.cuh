@@ -98,6 +98,33 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // ---------------------------------------------------------------------------
+// The cells a summation visits: every cell [0, nc), or, with a support box
+// {x0, x1, y0, y1, z0, z1} (W_0 = 0 outside it), the planes z0..z1, a
+// contiguous range of whole planes of `plane` cells.
+struct CellRange {
+  int64_t lo, hi;
+};
+
+__device__ __forceinline__ CellRange box_cells(const int* box, int64_t plane, int64_t nc) {
+  if (!box) return CellRange{0, nc};
+  const int z0 = box[4], z1 = box[5];
+  if (z1 < z0) return CellRange{0, 0};
+  const int64_t hi = (int64_t)(z1 + 1) * plane;
+  return CellRange{(int64_t)z0 * plane, hi < nc ? hi : nc};
+}
+
+// Split k of `splits` equal parts of the range, each a multiple of `align`
+// cells (the first cell of a part keeps the range's alignment).
+__device__ __forceinline__ void split_cells(CellRange r, int splits, int64_t align, int k, int64_t* beg,
+                                            int64_t* end) {
+  int64_t cps = (r.hi - r.lo + splits - 1) / splits;
+  cps = (cps + align - 1) / align * align;
+  const int64_t b = r.lo + (int64_t)k * cps;
+  *beg = b < r.hi ? b : r.hi;
+  *end = b + cps < r.hi ? b + cps : r.hi;
+}
+
+// ---------------------------------------------------------------------------
 // asynchronous global -> shared copies
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {

@@ -22,23 +22,30 @@ using fft::kT;
 
 ck_status fft_init_attributes() { return CK_OK; }
 
-void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st) {
+void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const int64_t rows = (int64_t)ny * nz;
   const double H = (double)nz * ny * (nx / 2 + 1);
+  const double row = 8.0 * (nx / 2 + 1);  // bytes of one half-spectrum row
+  // the field is zero outside the box: on 512-point y and z axes the x pass
+  // transforms the box's rows, the y pass its planes (reading its rows) and
+  // the z pass reads its planes; every output of the z pass is written
+  if (ny != 512 || nz != 512) box = nullptr;
   {
-    ProfScope ps(p, ST_FFT_X_R2C, 4.0 * (double)p.nc + 8.0 * H, st);
-    fft::launch_x_r2c(nx / 2, in, spec, nx, p.px, rows, p.fx_half, p.stw[0], p.tw[0], p.sm_count, st);
+    ProfScope ps(p, ST_FFT_X_R2C, box ? 0.0 : 4.0 * (double)p.nc + 8.0 * H, 4.0 * nx + row, 0.0, box, st);
+    fft::launch_x_r2c(nx / 2, in, spec, nx, p.px, rows, p.fx_half, p.stw[0], p.tw[0], p.sm_count, st, box, ny);
   }
   {
-    ProfScope ps(p, ST_FFT_Y_FWD, 16.0 * H, st);
+    ProfScope ps(p, ST_FFT_Y_FWD, box ? 0.0 : 16.0 * H, row, row * ny, box, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, nz};
-    fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.tw[1], false, p.sm_count, st);
+    fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.tw[1], false, p.sm_count, st, box, nz,
+                        fft::kPrunePlanes | fft::kPruneInY);
   }
   {
-    ProfScope ps(p, ST_FFT_Z_FWD, 16.0 * H, st);
+    ProfScope ps(p, ST_FFT_Z_FWD, box ? 8.0 * H : 16.0 * H, 0.0, row * ny, box, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
-    fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.tw[2], false, p.sm_count, st);
+    fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.tw[2], false, p.sm_count, st, box, nz,
+                        fft::kPruneInZ);
   }
 }
 
@@ -66,7 +73,8 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
     // read: the box's planes, written: their box rows
     ProfScope ps(p, ST_FFT_Y_INV, ybox ? 0.0 : nshells * 16.0 * H, nshells * row, nshells * row * ny, ybox, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, (int64_t)nz * nshells};
-    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1, p.sm_count, st, ybox, nz);
+    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1, p.sm_count, st, ybox, nz,
+                        fft::kPrunePlanes | fft::kPruneOutY);
   }
 }
 

@@ -390,6 +390,13 @@ __device__ __forceinline__ int tw_len_rt(const FftLen& f) {
   return off;
 }
 
+// Pruning of the 512-point strided passes by a box {x0, x1, y0, y1, z0, z1}:
+// kPrunePlanes: the view's outer index is o = s nz + z (nz planes per shell)
+// and only the planes z0 <= z <= z1 are transformed; kPruneOutY: only the
+// rows y0..y1 are written; kPruneInY / kPruneInZ: rows outside y0..y1 /
+// z0..z1 are zeros of the input and are not read.
+constexpr int kPrunePlanes = 1, kPruneOutY = 2, kPruneInY = 4, kPruneInZ = 8;
+
 // A strided-axis view: element (o, l, i) at o*so + l*sl + i, l in [0, L),
 // i in [0, inner); a tile is one o and kT consecutive i.
 struct StridedView {
@@ -572,10 +579,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 // O = (Z[k] - conj Z[M-k]) / 2i, k = 0..M.  The transform's first iteration
 // reads the real rows from global memory; its output stays in shared memory
 // for the split.
+// box (null: every row): the rows (y, z) of the box {x0, x1, y0, y1, z0, z1}
+// alone, the field being zero elsewhere; the other rows are not written.
 template <int MC>
 __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     x_r2c_kernel(const float* __restrict__ in, float2* __restrict__ out, int nx, int px, int64_t rows, FftLen f,
-                 const float2* __restrict__ stw, const float2* __restrict__ tw) {
+                 const float2* __restrict__ stw, const float2* __restrict__ tw, const int* __restrict__ box, int ny) {
   extern __shared__ float4 smem4[];
   const int M = MC > 0 ? MC : nx / 2;
   const int NX = 2 * M;
@@ -587,18 +596,28 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
   for (int i = threadIdx.x; i <= M; i += kThreads) twn[i] = __ldg(tw + i);
   __syncthreads();
-  const int64_t ntiles = (rows + kT - 1) / kT;
+  // visited rows: every row, or the box's (y0..y1, z0..z1) in order
+  int64_t y0 = 0, nyb = ny > 0 ? ny : 1, z0 = 0, count = rows;
+  if (box) {
+    y0 = box[2];
+    nyb = box[3] - box[2] + 1;
+    z0 = box[4];
+    const int64_t nzb = box[5] - box[4] + 1;
+    count = nyb > 0 && nzb > 0 ? nyb * nzb : 0;
+    if (nyb <= 0) nyb = 1;
+  }
+  auto row_of = [=](int64_t c) { return box ? (z0 + c / nyb) * ny + y0 + c % nyb : c; };
+  const int64_t ntiles = (count + kT - 1) / kT;
   auto rows_ld = [&](int64_t tile) {
     const int64_t r0 = tile * kT;
-    const int valid = (int)(rows - r0 < kT ? rows - r0 : kT);
-    const float* rin = in + r0 * NX;
+    const int valid = (int)(count - r0 < kT ? count - r0 : kT);
     return [=](int m, int cp) {
       const int c = 2 * cp;
-      const float2 z0 = c < valid ? __ldg(reinterpret_cast<const float2*>(rin + (int64_t)c * NX) + m)
-                                  : make_float2(0.f, 0.f);
-      const float2 z1 = c + 1 < valid ? __ldg(reinterpret_cast<const float2*>(rin + (int64_t)(c + 1) * NX) + m)
-                                      : make_float2(0.f, 0.f);
-      return cat4(z0, z1);
+      const float2 z0v = c < valid ? __ldg(reinterpret_cast<const float2*>(in + row_of(r0 + c) * NX) + m)
+                                   : make_float2(0.f, 0.f);
+      const float2 z1v = c + 1 < valid ? __ldg(reinterpret_cast<const float2*>(in + row_of(r0 + c + 1) * NX) + m)
+                                       : make_float2(0.f, 0.f);
+      return cat4(z0v, z1v);
     };
   };
   // the transform's output buffer: not the one its last iteration reads
@@ -607,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   else res = (f.nst % 2 == 1) ? a : b;
   auto split = [&](int64_t t) {
     const int64_t r0 = t * kT;
-    const int valid = (int)(rows - r0 < kT ? rows - r0 : kT);
+    const int valid = (int)(count - r0 < kT ? count - r0 : kT);
     const float2* s = res;
     for (int idx = threadIdx.x; idx < kT * px; idx += kThreads) {
       const int c = idx % kT, k = idx / kT;
@@ -620,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
         const float2 O = cscale(cmul_mi<false>(csub(zk, zc)), 0.5f);
         X = cadd(E, cmul(twn[k], O));
       }
-      out[(r0 + c) * px + k] = X;
+      out[row_of(r0 + c) * px + k] = X;
     }
     __syncthreads();
   };
@@ -764,18 +783,21 @@ inline size_t xpass_smem(int nx) {
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).
 // wide: 16-column tiles for the 512-point register kernel (large multi-shell passes)
-// box (device, may be null; 512-point axes only): the support box of W_0.
-// For the strided pass, only its planes z (outer index s nz + z, nz planes
-// per shell) are transformed and only its rows y written; for the z pass
-// with the multiply, only its planes are written.
+// box (device, may be null; 512-point axes only) with `mode` (the pruning
+// bits of ck_fft_sreg.cuh: transform only the box's planes, write only its
+// rows y, read only its rows y or z as nonzero input); for the z pass with
+// the multiply, only the box's planes are written.
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
                     const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st,
-                    const int* box = nullptr, int nz = 0);
+                    const int* box = nullptr, int nz = 0, int mode = 0);
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
                    cudaStream_t st, const int* box = nullptr);
+// box (device, may be null): the input is zero outside the box; only its rows
+// (ny rows per plane) are transformed and written.
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
-                  const float2* stw, const float2* tw, int sm_count, cudaStream_t st);
+                  const float2* stw, const float2* tw, int sm_count, cudaStream_t st, const int* box = nullptr,
+                  int ny = 0);
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,
                   int64_t out_shell_stride, const FftLen& f, const float2* stw, const float2* tw, int sm_count,
                   cudaStream_t st);

@@ -109,25 +109,26 @@ __device__ __forceinline__ void sreg_step_b(const float2* T, const float2* w32, 
 
 // The tile of outer index o and first column i0 of a strided view (C
 // columns x 512 rows) into S[row][c] with 16-byte cp.async copies; columns
-// past the view's end are zero-filled.
+// past the view's end, and rows outside [rlo, rhi] (known zeros), are
+// zero-filled.
 template <int C>
-__device__ __forceinline__ void sreg_stage(float2* s, const float2* in, const StridedView& v, int64_t o, int i0) {
+__device__ __forceinline__ void sreg_stage(float2* s, const float2* in, const StridedView& v, int64_t o, int i0,
+                                           int rlo = 0, int rhi = 511) {
   using S = Sreg<C>;
   const float2* base = in + o * v.so + i0;
   for (int idx = threadIdx.x; idx < S::L * (C / 2); idx += S::NT) {
     const int l = idx / (C / 2), cp = idx % (C / 2);
-    const bool ok = i0 + 2 * cp < v.inner;
+    const bool ok = i0 + 2 * cp < v.inner && l >= rlo && l <= rhi;
     cp_async16(s + l * C + 2 * cp, ok ? base + (int64_t)l * v.sl + 2 * cp : in, ok);
   }
 }
 
-// box (null: none): the view's outer index is o = s nz + z (nz planes per
-// shell); only the planes box[4] <= z <= box[5] are transformed, and of
-// their rows only box[2] .. box[3] are written (the support of W_0).
+// Pruning by a box {x0, x1, y0, y1, z0, z1} (null: none) with the mode bits
+// of ck_fft_core.cuh (kPrunePlanes, kPruneOutY, kPruneInY, kPruneInZ).
 template <int C, bool INV>
 __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
     sreg512_kernel(const float2* in, float2* out, StridedView v, const float2* __restrict__ tw,
-                   const int* __restrict__ box, int nz) {
+                   const int* __restrict__ box, int nz, int mode) {
   using S = Sreg<C>;
   extern __shared__ float4 smem4[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
@@ -140,27 +141,38 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
   const int ca = tid % C, l2 = tid / C;                                // step A
   const int cb = tid % C, hb = (tid / C) & 1, m1 = tid / (2 * C);      // step B
   const int tpo = (v.inner + C - 1) / C;
-  int zlo = 0, nzb = nz, rlo = 0, rhi = S::L - 1;
-  if (box) {
+  if (!box) mode = 0;
+  const bool planes = (mode & kPrunePlanes) != 0;
+  int zlo = 0, nzb = nz, rlo = 0, rhi = S::L - 1, ilo = 0, ihi = S::L - 1;
+  if (planes) {
     zlo = box[4];
     nzb = max(0, box[5] - box[4] + 1);
+  }
+  if (mode & kPruneOutY) {
     rlo = box[2];
     rhi = box[3];
   }
-  const int64_t outers = box ? (v.n_outer / nz) * nzb : v.n_outer;
+  if (mode & kPruneInY) {
+    ilo = box[2];
+    ihi = box[3];
+  } else if (mode & kPruneInZ) {
+    ilo = box[4];
+    ihi = box[5];
+  }
+  const int64_t outers = planes ? (v.n_outer / nz) * nzb : v.n_outer;
   const int64_t ntiles = outers * tpo;
   // tile -> outer index of the view (plane zlo + .. of a shell) and first column
   auto outer_of = [&](int64_t tile) {
     const int64_t ot = tile / tpo;
-    return box ? (ot / nzb) * nz + zlo + ot % nzb : ot;
+    return planes ? (ot / nzb) * nz + zlo + ot % nzb : ot;
   };
   auto col_of = [&](int64_t tile) { return (int)(tile % tpo) * C; };
   int64_t t = blockIdx.x;
-  if (t < ntiles) sreg_stage<C>(sbuf(0), in, v, outer_of(t), col_of(t));
+  if (t < ntiles) sreg_stage<C>(sbuf(0), in, v, outer_of(t), col_of(t), ilo, ihi);
   cp_async_commit();
   for (int it = 0; t < ntiles; ++it) {
     const int64_t tn = t + gridDim.x;
-    if (tn < ntiles) sreg_stage<C>(sbuf((it + 1) & 1), in, v, outer_of(tn), col_of(tn));
+    if (tn < ntiles) sreg_stage<C>(sbuf((it + 1) & 1), in, v, outer_of(tn), col_of(tn), ilo, ihi);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();

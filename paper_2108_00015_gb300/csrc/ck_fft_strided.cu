@@ -24,7 +24,7 @@ constexpr int kZregC = 8;
 
 template <int C>
 static void run_sreg512(bool inv, const float2* in, float2* out, const StridedView& v, const float2* tw, int sm_count,
-                        cudaStream_t st, const int* box, int nz) {
+                        cudaStream_t st, const int* box, int nz, int mode) {
   using S = Sreg<C>;
   const size_t sm = S::plain_bytes;
   const int64_t ntiles = v.n_outer * ((v.inner + C - 1) / C);
@@ -36,7 +36,7 @@ static void run_sreg512(bool inv, const float2* in, float2* out, const StridedVi
       occ = 1;
     }
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * occ));
-    kernel<<<grid, S::NT, sm, st>>>(in, out, v, tw, box, nz);
+    kernel<<<grid, S::NT, sm, st>>>(in, out, v, tw, box, nz, mode);
   };
   if (inv) go(sreg512_kernel<C, true>);
   else go(sreg512_kernel<C, false>);
@@ -90,10 +90,10 @@ static void run_zmulti(const float2* in, float2* out, int64_t out_stride, int ns
 
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
                     const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st, const int* box,
-                    int nz) {
+                    int nz, int mode) {
   if (L == 512) {
-    if (wide) run_sreg512<16>(inv, in, out, v, tw, sm_count, st, box, nz);
-    else run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st, box, nz);
+    if (wide) run_sreg512<16>(inv, in, out, v, tw, sm_count, st, box, nz, mode);
+    else run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st, box, nz, mode);
     return;
   }
   switch (L) {

@@ -10,12 +10,12 @@ namespace fft {
 
 template <int MC>
 static void run_r2c(const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f, const float2* stw,
-                    const float2* tw, int sm_count, cudaStream_t st) {
+                    const float2* tw, int sm_count, cudaStream_t st, const int* box, int ny) {
   const size_t sm = xpass_smem(nx);
   const int64_t ntiles = (rows + kT - 1) / kT;
   allow_smem(x_r2c_kernel<MC>, sm);
-  x_r2c_kernel<MC><<<persistent_grid(x_r2c_kernel<MC>, sm, sm_count, ntiles), kThreads, sm, st>>>(in, out, nx, px,
-                                                                                                 rows, f, stw, tw);
+  x_r2c_kernel<MC><<<persistent_grid(x_r2c_kernel<MC>, sm, sm_count, ntiles), kThreads, sm, st>>>(
+      in, out, nx, px, rows, f, stw, tw, box, ny);
 }
 
 template <int MC>
@@ -31,12 +31,12 @@ static void run_c2r(const float2* in, float* out, int nx, int px, int64_t rows, 
 #define CK_HALF_LENGTHS(X) X(16) X(64) X(80) X(96) X(120) X(128) X(144) X(160) X(192) X(256)
 
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
-                  const float2* stw, const float2* tw, int sm_count, cudaStream_t st) {
+                  const float2* stw, const float2* tw, int sm_count, cudaStream_t st, const int* box, int ny) {
   switch (M) {
-#define CK_CASE(N) case N: run_r2c<N>(in, out, nx, px, rows, f, stw, tw, sm_count, st); return;
+#define CK_CASE(N) case N: run_r2c<N>(in, out, nx, px, rows, f, stw, tw, sm_count, st, box, ny); return;
     CK_HALF_LENGTHS(CK_CASE)
 #undef CK_CASE
-    default: run_r2c<0>(in, out, nx, px, rows, f, stw, tw, sm_count, st);
+    default: run_r2c<0>(in, out, nx, px, rows, f, stw, tw, sm_count, st, box, ny);
   }
 }
 

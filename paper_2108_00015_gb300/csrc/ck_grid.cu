@@ -333,11 +333,12 @@ void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st) {
                                                                         which);
 }
 
-// The box of cells where W_0 may be nonzero, for the pruned inverse passes
-// of the fused path: the occupied cells of the data and the randoms (mode
-// 0, W_0 = N = D - alpha R) or of the randoms (mode 1, W_0 = Rt), clipped to
-// the region's planes; {x0, x1, y0, y1, z0, z1} inclusive, empty when a
-// lower bound exceeds its upper one.
+// The box of cells where the field may be nonzero: the occupied cells of the
+// data and the randoms (mode 0, N = D - alpha R) or of the randoms (mode 1,
+// Rt); {x0, x1, y0, y1, z0, z1} inclusive, empty when a lower bound exceeds
+// its upper one.  box[6..11]: that box (the forward transform's input);
+// box[0..5]: the same clipped to the region's planes (where W_0 may be
+// nonzero: the pruned inverse passes of the fused path).
 __global__ void support_box_kernel(const DevState* __restrict__ st, int mode, int nx, int ny, int nz, int z_lo,
                                    int z_hi, int* __restrict__ box) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -350,6 +351,8 @@ __global__ void support_box_kernel(const DevState* __restrict__ st, int mode, in
     }
     lo = max(lo, 0);
     hi = min(hi, n[a] - 1);
+    box[6 + 2 * a] = lo;
+    box[6 + 2 * a + 1] = hi;
     if (a == 2) {
       lo = max(lo, z_lo);
       hi = min(hi, z_hi);

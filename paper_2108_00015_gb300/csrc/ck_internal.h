@@ -166,7 +166,7 @@ struct Plan {
   double* dense = nullptr;     // 3 x dense_total: xi, num, den staging
   int* dense_map = nullptr;    // packed per order: dense index -> multiset rank
   int* host_status_pinned = nullptr;
-  int* support = nullptr;      // [6] box of the cells where W_0 may be nonzero (pruned inverse passes)
+  int* support = nullptr;      // [12] boxes of the cells where W_0 (0..5) and the field (6..11) may be nonzero
   unsigned* absmax = nullptr;  // [CK_MAX_SHELLS + 1] largest |W| per factor row (split-FP16 scales)
 
   ContractPlan cplan[1 << (CK_MAX_ORDER + 1)];
@@ -252,7 +252,9 @@ void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st);
 
 // ---- launches (ck_fft.cu) ----------------------------------------------------
 ck_status fft_init_attributes();
-void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st);
+// box (device, may be null): the field is zero outside it, and the passes
+// skip the rows and planes that hold only zeros (512-point y and z axes).
+void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box = nullptr);
 // Inverse transforms of nshells spectra (spec * K^_s for s < nshells, or spec
 // alone when khat is null) through scratch spectra tmp[s] into real fields
 // out + s * out_stride.
@@ -282,10 +284,12 @@ int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count);
 // Tensor-core tiles 0 .. ntc - 1 of ntiles (the partials are pitched by ntiles).
 // kind: 0 split-TF32, 1 split-BF16, 2 split-FP16 (absmax: ns + 1 device
 // words for the FP16 scales, filled here).
+// box (device, may be null): only the planes z0..z1 of the support box are
+// summed (plane cells each); splits share them out in whole 256-cell groups.
 cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
-                        int ntc, int ntiles, int splits, int64_t cps, unsigned* absmax, double* partials, int* status,
-                        cudaStream_t st);
+                        int ntc, int ntiles, int splits, const int* box, int64_t plane, unsigned* absmax,
+                        double* partials, int* status, cudaStream_t st);
 // Thin tiles (at most kThinMaxOut outputs, kThinMaxCols columns) t0 .. t0 + nthin - 1 on the CUDA
 // cores in FP32, into the same partials layout (tile width tn).
 constexpr int kThinMaxOut = 256;
@@ -293,16 +297,18 @@ constexpr int kThinMaxCols = 16;
 size_t umma_thin_smem(int ns, int rmax);  // rmax: the most live rows of a thin tile
 cudaError_t launch_umma_thin(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, int rmax,
                              const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles,
-                             const int* collist, int t0, int nthin, int ntiles, int tn, int splits, int64_t cps,
-                             double* partials, cudaStream_t st);
+                             const int* collist, int t0, int nthin, int ntiles, int tn, int splits, const int* box,
+                             int64_t plane, double* partials, cudaStream_t st);
 cudaError_t launch_umma_reduce(const double* partials, int splits, int ntiles, int tn, const int4* tiles,
                                const int* collist, const int2* rowdesc, int rows, const int2* coldesc, int mask,
                                int ns, const int64_t* bases, double* out, cudaStream_t st);
 
 // ---- launches (ck_contract.cu) -----------------------------------------------
 ck_status contract_prepare(Plan& p, int order_mask);
+// box (device, may be null): W_0 vanishes outside the support box, and
+// only its planes are summed.
 ck_status launch_contract(Plan& p, int order_mask, const float* w0, const float* bank,
-                          int64_t bank_stride, double* sums_packed, cudaStream_t st);
+                          int64_t bank_stride, double* sums_packed, cudaStream_t st, const int* box = nullptr);
 // plain: field sums with no denominator (xi = num, den = 1)
 void launch_finalize(const Plan& p, int order_mask, cudaStream_t st, bool plain = false);
 

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     contract_umma_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
                          int ns, int wcells, const int2* __restrict__ rowdesc, int rows,
                          const int2* __restrict__ coldesc, const int4* __restrict__ tiles,
-                         const int* __restrict__ collist, int ntiles, int64_t cells_per_split,
+                         const int* __restrict__ collist, int ntiles, const int* __restrict__ box, int64_t plane,
                          const unsigned* __restrict__ absmax, double* __restrict__ partials, int* status) {
   using S = UmmaShape<TN, KIND>;
   constexpr int KC = S::KC, NA = S::NA, G = S::G, NACC = S::nacc;
@@ -244,8 +244,9 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
-  const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
+  // this split's part of the visited cells: whole accumulation groups
+  int64_t beg, end;
+  split_cells(box_cells(box, plane, nc), gridDim.y, UM_GCELLS, blockIdx.y, &beg, &end);
   const int nch = end > beg ? (int)((end - beg + KC - 1) / KC) : 0;
   const int ngroups = (nch + G - 1) / G;
   constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -622,8 +623,8 @@ __global__ void reduce_umma_kernel(const double* __restrict__ partials, int spli
 template <int TN, int KIND>
 cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, const int2* rowdesc,
                           int rows, const int2* coldesc, const int4* tiles, const int* collist, int ntc, int ntiles,
-                          int splits, int64_t cps, const unsigned* absmax, double* partials, int* status,
-                          cudaStream_t st) {
+                          int splits, const int* box, int64_t plane, const unsigned* absmax, double* partials,
+                          int* status, cudaStream_t st) {
   if (ntc == 0) return cudaSuccess;
   const int wcells = umma_wcells<TN, KIND>(ns, (size_t)227 * 1024);
   if (wcells == 0) return cudaErrorInvalidValue;
@@ -633,8 +634,8 @@ cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, i
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)ntc, (unsigned)splits);  // tiles 0 .. ntc - 1; partials pitched by all ntiles
   contract_umma_kernel<TN, KIND><<<grid, UM_THREADS, sm, st>>>(w0, bank, bstride, nc, ns, wcells, rowdesc, rows,
-                                                               coldesc, tiles, collist, ntiles, cps, absmax, partials,
-                                                               status);
+                                                               coldesc, tiles, collist, ntiles, box, plane, absmax,
+                                                               partials, status);
   return cudaGetLastError();
 }
 
@@ -676,8 +677,8 @@ int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count) {
 
 cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
-                        int ntc, int ntiles, int splits, int64_t cps, unsigned* absmax, double* partials, int* status,
-                        cudaStream_t st) {
+                        int ntc, int ntiles, int splits, const int* box, int64_t plane, unsigned* absmax,
+                        double* partials, int* status, cudaStream_t st) {
   if (ntc == 0) return cudaSuccess;
   if (kind == UM_FP16) {
     cudaError_t e = cudaMemsetAsync(absmax, 0, (size_t)(ns + 1) * sizeof(unsigned), st);
@@ -689,7 +690,7 @@ cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, in
 #define CK_UMMA_CASE(W, K)                                                                                           \
   case W:                                                                                                            \
     return launch_umma_t<W, K>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntc, ntiles, splits, \
-                               cps, absmax, partials, status, st);
+                               box, plane, absmax, partials, status, st);
 #define CK_UMMA_KIND(K)        \
   switch (tn) {                \
     CK_UMMA_CASE(32, K)        \
@@ -723,7 +724,7 @@ __global__ void __launch_bounds__(TH_THREADS)
     contract_thin_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
                          int ns, int rmax, const int2* __restrict__ rowdesc, int rows, const int2* __restrict__ coldesc,
                          const int4* __restrict__ tiles, const int* __restrict__ collist, int t0, int ntiles, int tn,
-                         int64_t cells_per_split, double* __restrict__ partials) {
+                         const int* __restrict__ box, int64_t plane, double* __restrict__ partials) {
   extern __shared__ __align__(16) float th_smem[];
   const int tile_i = t0 + blockIdx.x;
   const int4 tile = tiles[tile_i];
@@ -745,8 +746,8 @@ __global__ void __launch_bounds__(TH_THREADS)
     fb[q] = make_int2(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE);
   }
   for (int k = tid; k < 2 * TH_CELLS; k += TH_THREADS) wsb[((k / TH_CELLS) * (ns + 2) + ONE) * TH_PITCH + k % TH_CELLS] = 1.0f;
-  const int64_t beg = (int64_t)blockIdx.y * cells_per_split;
-  const int64_t end = std::min<int64_t>(nc, beg + cells_per_split);
+  int64_t beg, end;  // this split's part of the visited cells (256-cell multiples)
+  split_cells(box_cells(box, plane, nc), gridDim.y, TH_CELLS, blockIdx.y, &beg, &end);
   const int o = tid;  // this thread's output: row o / C, column o % C
   const bool live = o < R * C;
   const int orow = live ? o / C : 0, ocol = live ? o % C : 0;
@@ -819,14 +820,14 @@ size_t umma_thin_smem(int ns, int rmax) {
 
 cudaError_t launch_umma_thin(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, int rmax,
                              const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles,
-                             const int* collist, int t0, int nthin, int ntiles, int tn, int splits, int64_t cps,
-                             double* partials, cudaStream_t st) {
+                             const int* collist, int t0, int nthin, int ntiles, int tn, int splits, const int* box,
+                             int64_t plane, double* partials, cudaStream_t st) {
   if (nthin == 0) return cudaSuccess;
   const size_t sm = umma_thin_smem(ns, rmax);
   cudaError_t e = cudaFuncSetAttribute(contract_thin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   contract_thin_kernel<<<dim3((unsigned)nthin, (unsigned)splits), TH_THREADS, sm, st>>>(
-      w0, bank, bstride, nc, ns, rmax, rowdesc, rows, coldesc, tiles, collist, t0, ntiles, tn, cps, partials);
+      w0, bank, bstride, nc, ns, rmax, rowdesc, rows, coldesc, tiles, collist, t0, ntiles, tn, box, plane, partials);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@ ck_contract (which uses plan workspace) on two calls in a row.  Kept in a
 file collected last, so that a run stopping at the first failure has
 already run every other test."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -44,6 +45,7 @@ def test_static_contraction_matches_plan_contraction(ns, orders):
     torch.cuda.synchronize()
     for call in range(2):  # the shared scratch keeps the previous call's contents
         if call == 1:
+            gc.collect()  # tensors of earlier tests may still be waiting to be freed
             torch.cuda.synchronize()
             free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         code = lib.ck_contract_static(tw0.data_ptr(), tB.data_ptr(), stride, nc, ns, conker.order_mask(orders),
@@ -51,9 +53,10 @@ def test_static_contraction_matches_plan_contraction(ns, orders):
         assert code == 0
         torch.cuda.synchronize()
         if call == 1:
-            # the second call leaves device memory exactly as it found it
-            assert torch.cuda.mem_get_info()[0] == free0
-            assert torch.cuda.memory_allocated() == alloc0
+            # the second call takes no device memory: neither the device's free
+            # bytes nor the caching allocator's holdings go down
+            assert torch.cuda.mem_get_info()[0] >= free0
+            assert torch.cuda.memory_allocated() <= alloc0
         for n in orders:
             ref, aref = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
             a = got[n].cpu().numpy()
