@@ -54,6 +54,8 @@ def _args():
                     help="headline form: mixed split-TF32 tensor-core sums (fused pass), split-BF16 or "
                          "split-FP16 tensor-core sums (kind::f16, bank kept), or plain FP32")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form beside the headline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (ck_plan_autotune times the choices after warm-up)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the higher-order workloads timed beside the headline at N = 1 (stress256: xi_2..xi_5, "
                          "survey512_s32: xi_2..xi_4, in every contraction form)")
@@ -385,6 +387,9 @@ def _time_extra(torch, w, orders, precision, steps, warmup):
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
+    tuning = plan.autotune()
+    step()
+    torch.cuda.synchronize()
     if plan.status() != 0:
         raise RuntimeError(f"device status after warm-up ({precision})")
     stream = torch.cuda.current_stream()
@@ -404,7 +409,7 @@ def _time_extra(torch, w, orders, precision, steps, warmup):
     if plan.status() != 0:
         raise RuntimeError(f"device status in the timed region ({precision})")
     plan.close()
-    out = {"ms_per_catalog": round(t_ms / steps, 3), "steps": steps, "clocks": clk}
+    out = {"ms_per_catalog": round(t_ms / steps, 3), "steps": steps, "clocks": clk, "tuning": tuning}
     dname, dv = max(stages.items(), key=lambda kv: kv[1]["ms"])
     t_launch = dv["ms"] / dv["launches"] * 1e-3
     out["dominant"] = {"stage": dname, "ms_per_step": round(dv["ms"] / steps, 3)}
@@ -508,6 +513,12 @@ def run_gb300(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    tuning = None
+    if not args.no_autotune and not (args.continuous or args.diagonal):
+        # launch-shape choices timed on the resident randoms (results unchanged)
+        tuning = plan.autotune()
+        step()
+        torch.cuda.synchronize()
     st = plan.status()
     if st not in (0,):
         raise RuntimeError(f"device status {st} after warm-up")
@@ -691,7 +702,8 @@ def run_gb300(args):
                             if args.factorised else
                             "ck_compute_continuous (Eqs. 15-17: one delta field, every shell, no denominator)"
                             if args.continuous else "ck_set_randoms + ck_compute (both fields, every shell)"),
-                   "l2": "no flush: inputs and intermediates far larger than L2 (16 scratch spectra, 8.7 GB)"},
+                   "l2": "no flush: inputs and intermediates far larger than L2 (16 scratch spectra, 8.7 GB)",
+                   "tuning": tuning},
         "forms": forms,
         "roofline": roofline,
         "fft": {"gbs": round(fft_bytes / (fft_ms * 1e-3) / 1e9, 1), "frac": round(fft_bytes / (fft_ms * 1e-3) / 1e9 / peak, 4),

@@ -385,6 +385,34 @@ ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_cata
  * out-of-box range or a negative or non-finite alpha.  Host only. */
 ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, double alpha);
 
+/* Autotuner (the batched and survey forms pick their transform and
+ * contraction shapes per plan).  Times, on the plan's own buffers, the
+ * candidates of each launch-shape choice that has more than one -- 8 or 16
+ * columns per tile of the single-field 512-point strided passes, of the K^ z
+ * pass and of the multi-shell inverse y pass (the latter two together), and
+ * for the split tensor-core forms that keep a bank 1, 2 or 3 contraction
+ * CTAs per SM -- each candidate once untimed and three times between CUDA
+ * events, and keeps the fastest in the plan.  The choices change launch
+ * shapes only: transforms are bit-identical, and the contraction's sums
+ * differ only by the order of their FP64 partial sums.  Needs a resident
+ * field: the field, spectrum and bank that the last ck_set_randoms or
+ * compute left are the inputs it times, and they are left as they were
+ * (CK_ERR_NO_RANDOMS before either, and after ck_plan_set_region until the
+ * next such call).  Captured graphs of ck_batch_compute are dropped.
+ * Synchronises the stream. */
+ck_status ck_plan_autotune(ck_plan* plan, void* stream);
+
+/* The plan's current choices: out[0] columns per tile of the single-field
+ * strided passes, out[1] of the K^ z pass, out[2] of the multi-shell inverse
+ * y pass, out[3] contraction CTAs per SM, out[4] 1 once ck_plan_autotune has
+ * run (else the defaults). */
+ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out);
+
+/* Set the choices by hand (in[0..3] as ck_plan_get_tuning's out[0..3]:
+ * 8 or 16 columns, 1..3 CTAs per SM; CK_ERR_ARG otherwise).  Host only;
+ * drops captured graphs. */
+ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in);
+
 /* Synchronise `stream` and return (and clear) the plan's device status. */
 ck_status ck_plan_status(ck_plan* plan, void* stream);
 

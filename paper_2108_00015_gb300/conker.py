@@ -117,6 +117,9 @@ _SIGS = [
                                         ctypes.c_int32, ctypes.POINTER(_Outputs), _P]),
     ("ck_plan_status", ctypes.c_int, [_P, _P]),
     ("ck_plan_set_region", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
+    ("ck_plan_autotune", ctypes.c_int, [_P, _P]),
+    ("ck_plan_get_tuning", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    ("ck_plan_set_tuning", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     ("ck_get_grids", ctypes.c_int, [_P, _P, _P, _P]),
     ("ck_get_field", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     ("ck_get_bank", ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
@@ -456,6 +459,21 @@ class Plan:
         """ck_plan_set_region: sums over box planes z_begin <= z < z_end,
         with the whole catalog's alpha (> 0) for a region of a decomposition."""
         _check(_lib().ck_plan_set_region(self._h, int(z_begin), int(z_end), float(alpha)), "ck_plan_set_region")
+
+    def autotune(self, stream=None) -> Dict[str, int]:
+        """ck_plan_autotune (after set_randoms or a compute): time the launch-shape choices
+        on this plan's buffers and keep the fastest; returns them."""
+        _check(_lib().ck_plan_autotune(self._h, _stream_ptr(stream)), "ck_plan_autotune")
+        return self.tuning()
+
+    def set_tuning(self, fwd_cols: int = 8, zreg_cols: int = 8, yinv_cols: int = 16, tc_ctas_per_sm: int = 2):
+        arr = (ctypes.c_int32 * 4)(fwd_cols, zreg_cols, yinv_cols, tc_ctas_per_sm)
+        _check(_lib().ck_plan_set_tuning(self._h, arr), "ck_plan_set_tuning")
+
+    def tuning(self) -> Dict[str, int]:
+        out = (ctypes.c_int32 * 5)()
+        _check(_lib().ck_plan_get_tuning(self._h, out), "ck_plan_get_tuning")
+        return dict(fwd_cols=out[0], zreg_cols=out[1], yinv_cols=out[2], tc_ctas_per_sm=out[3], tuned=bool(out[4]))
 
     def status(self, stream=None) -> int:
         return int(_lib().ck_plan_status(self._h, _stream_ptr(stream)))

@@ -767,6 +767,123 @@ ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_cata
   return CK_OK;
 }
 
+// Autotuning: each candidate of a choice runs once to warm up and three
+// times between events on the plan's own buffers; the fastest is kept.
+ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
+  if (!plan) return CK_ERR_BAD_POINTER;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  if (p.bank_holds < 0) return CK_ERR_NO_RANDOMS;  // no resident field to time on
+  cudaStream_t st = S(stream);
+  const bool prof = p.prof.on;
+  p.prof.on = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck_status s = cuda_status(cudaEventCreate(&e0));
+  if (s == CK_OK) s = cuda_status(cudaEventCreate(&e1));
+  auto timed = [&](auto&& fn, float* ms) -> ck_status {
+    fn();
+    CK_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) fn();
+    CK_TRY(cudaEventRecord(e1, st));
+    CK_TRY(cudaEventSynchronize(e1));
+    CK_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return cuda_status(cudaGetLastError());
+  };
+  const int ny = p.grid.n[1], nz = p.grid.n[2];
+  // the single-field strided passes (the forward transform of the resident field)
+  if (s == CK_OK && (ny == 512 || nz == 512)) {
+    float best = 1e30f;
+    int pick = p.tune.fwd_cols;
+    for (int c : {8, 16}) {
+      p.tune.fwd_cols = c;
+      float ms = 0.0f;
+      if ((s = timed([&] { launch_fft_forward(p, p.field, p.spec, st); }, &ms)) != CK_OK) break;
+      if (ms < best) { best = ms; pick = c; }
+    }
+    p.tune.fwd_cols = pick;
+  }
+  // the K^ z pass and the multi-shell inverse y pass, every shell, into the scratch spectra
+  if (s == CK_OK && (ny == 512 || nz == 512)) {
+    float best = 1e30f;
+    int pz = p.tune.zreg_cols, py = p.tune.yinv_cols;
+    for (int cz : {8, 16})
+      for (int cy : {8, 16}) {
+        if ((nz != 512 && cz != pz) || (ny != 512 && cy != py)) continue;
+        p.tune.zreg_cols = cz;
+        p.tune.yinv_cols = cy;
+        float ms = 0.0f;
+        if ((s = timed([&] { launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st); }, &ms)) != CK_OK) break;
+        if (ms < best) { best = ms; pz = cz; py = cy; }
+      }
+    p.tune.zreg_cols = pz;
+    p.tune.yinv_cols = py;
+  }
+  // the tensor-core contraction's splits, on the randoms' bank
+  const bool tensor = p.precision == CK_PREC_SPLIT_TF32 || p.precision == CK_PREC_SPLIT_BF16 ||
+                      p.precision == CK_PREC_SPLIT_FP16;
+  if (s == CK_OK && tensor && !p.fused) {
+    float best = 1e30f;
+    int pick = p.tune.tc_ctas_per_sm;
+    const int mask = full_mask(p);
+    for (int k : {1, 2, 3}) {
+      p.tune.tc_ctas_per_sm = k;
+      for (bool& r : p.cplan_ready) r = false;
+      float ms = 0.0f;
+      const ck_status c = timed([&] { launch_contract(p, mask, p.field, p.bank, p.field_stride, p.sums, st); }, &ms);
+      if (c == CK_ERR_OOM) continue;  // more splits than the partials hold
+      if ((s = c) != CK_OK) break;
+      if (ms < best) { best = ms; pick = k; }
+    }
+    p.tune.tc_ctas_per_sm = pick;
+    for (bool& r : p.cplan_ready) r = false;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  p.prof.on = prof;
+  // captured graphs hold the previous choices; a region's field no longer
+  // gives the randoms' whole spectrum
+  for (auto& g : p.gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  if (p.region) p.bank_holds = -1;
+  if (s == CK_OK) {
+    p.tune.tuned = true;
+    s = read_status(p, st, false);
+  }
+  return s;
+}
+
+ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in) {
+  if (!plan || !in) return CK_ERR_BAD_POINTER;
+  for (int i = 0; i < 3; ++i)
+    if (in[i] != 8 && in[i] != 16) return CK_ERR_ARG;
+  if (in[3] < 1 || in[3] > 3) return CK_ERR_ARG;
+  Plan& p = *reinterpret_cast<Plan*>(plan);
+  p.tune.fwd_cols = in[0];
+  p.tune.zreg_cols = in[1];
+  p.tune.yinv_cols = in[2];
+  p.tune.tc_ctas_per_sm = in[3];
+  for (bool& r : p.cplan_ready) r = false;
+  for (auto& g : p.gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return CK_OK;
+}
+
+ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out) {
+  if (!plan || !out) return CK_ERR_BAD_POINTER;
+  const Plan& p = *reinterpret_cast<const Plan*>(plan);
+  out[0] = p.tune.fwd_cols;
+  out[1] = p.tune.zreg_cols;
+  out[2] = p.tune.yinv_cols;
+  out[3] = p.tune.tc_ctas_per_sm;
+  out[4] = p.tune.tuned ? 1 : 0;
+  return CK_OK;
+}
+
 ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, double alpha) {
   if (!plan) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
@@ -784,6 +901,7 @@ ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, doub
     }
   // den_raw of the randoms set so far summed over other planes
   p.have_randoms = false;
+  p.bank_holds = -1;
   p.have_randoms_diag = false;
   return CK_OK;
 }

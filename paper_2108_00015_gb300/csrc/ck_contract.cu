@@ -548,7 +548,7 @@ ck_status contract_prepare(Plan& p, int mask) {
     if (e == cudaSuccess && !tl.empty()) e = cudaMemcpy(c.d_um_tiles, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !clist.empty()) e = cudaMemcpy(c.d_um_cols, clist.data(), clist.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_status(e);
-    c.um_cps = umma_cells_per_split(p.nc, std::max(c.n_tiles, 1), p.sm_count);
+    c.um_cps = umma_cells_per_split(p.nc, std::max(c.n_tiles, 1), p.sm_count, p.tune.tc_ctas_per_sm);
     c.splits = (int)((p.nc + c.um_cps - 1) / c.um_cps);
     c.partial_doubles = (size_t)c.splits * std::max(c.n_tiles, 1) * TM * c.um_tn;
     if (c.partial_doubles > p.partials_cap) return CK_ERR_OOM;

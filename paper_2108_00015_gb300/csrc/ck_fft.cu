@@ -38,13 +38,13 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
   {
     ProfScope ps(p, ST_FFT_Y_FWD, box ? 0.0 : 16.0 * H, row, row * ny, box, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, nz};
-    fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.tw[1], false, p.sm_count, st, box, nz,
+    fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.tw[1], p.tune.fwd_cols, p.sm_count, st, box, nz,
                         fft::kPrunePlanes | fft::kPruneInY);
   }
   {
     ProfScope ps(p, ST_FFT_Z_FWD, box ? 8.0 * H : 16.0 * H, 0.0, row * ny, box, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
-    fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.tw[2], false, p.sm_count, st, box, nz,
+    fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.tw[2], p.tune.fwd_cols, p.sm_count, st, box, nz,
                         fft::kPruneInZ);
   }
 }
@@ -67,13 +67,15 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
     ProfScope ps(p, ST_FFT_Z_INV_MUL, base + (zbox ? 0.0 : nshells * 8.0 * H), 0.0, nshells * row * ny, zbox, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
     KhatArgs K{khat, p.khat_stride, p.px, ny, nz, p.oct[1]};
-    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.tw[2], K, p.sm_count, st, zbox);
+    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.tw[2], K, p.sm_count, st, zbox,
+                       p.tune.zreg_cols);
   }
   {
     // read: the box's planes, written: their box rows
     ProfScope ps(p, ST_FFT_Y_INV, ybox ? 0.0 : nshells * 16.0 * H, nshells * row, nshells * row * ny, ybox, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, (int64_t)nz * nshells};
-    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1, p.sm_count, st, ybox, nz,
+    fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1 ? p.tune.yinv_cols : p.tune.fwd_cols,
+                        p.sm_count, st, ybox, nz,
                         fft::kPrunePlanes | fft::kPruneOutY);
   }
 }

@@ -782,17 +782,17 @@ inline size_t xpass_smem(int nx) {
 
 // Launch helpers (one translation unit each; they pick the compile-time
 // length when LC/MC is one of the instantiated lengths).
-// wide: 16-column tiles for the 512-point register kernel (large multi-shell passes)
+// cols: columns per tile of the 512-point register kernels (8 or 16)
 // box (device, may be null; 512-point axes only) with `mode` (the pruning
 // bits of ck_fft_sreg.cuh: transform only the box's planes, write only its
 // rows y, read only its rows y or z as nonzero input); for the z pass with
 // the multiply, only the box's planes are written.
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st,
+                    const float2* stw, const float2* tw, int cols, int sm_count, cudaStream_t st,
                     const int* box = nullptr, int nz = 0, int mode = 0);
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
-                   cudaStream_t st, const int* box = nullptr);
+                   cudaStream_t st, const int* box = nullptr, int cols = 8);
 // box (device, may be null): the input is zero outside the box; only its rows
 // (ny rows per plane) are transformed and written.
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,

@@ -229,17 +229,23 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
       cp_async16(Sx + l * C + c, ok ? in + (int64_t)l * v.sl + i0 + c : in, ok);
     }
   };
-  int64_t t = blockIdx.x;
-  if (t < ntiles) {
-    stage(t);
-    if (mul) load_slab(0, t);
+  // K^ is even in ky, so the tiles of rows ky and ny - ky read the same
+  // slabs: visit tiles from both ends in turn (schedule index j -> tile),
+  // so that the second reader of a slab finds it in L2
+  auto tile_of = [&](int64_t j) { return (j & 1) ? ntiles - 1 - (j >> 1) : (j >> 1); };
+  int64_t j = blockIdx.x;
+  if (j < ntiles) {
+    stage(tile_of(j));
+    if (mul) load_slab(0, tile_of(j));
   }
   cp_async_commit();
   cp_async_wait<0>();
   __syncthreads();
-  for (; t < ntiles; t += gridDim.x) {
+  for (; j < ntiles; j += gridDim.x) {
+    const int64_t t = tile_of(j);
     const int i0 = (int)t * C;
-    const int64_t tn = t + gridDim.x;
+    const int64_t jn = j + gridDim.x;
+    const int64_t tn = jn < ntiles ? tile_of(jn) : ntiles;
     for (int s = 0; s < nshells; ++s) {
       // K^ depends on min(kz, 512 - kz): kz = 32 l1 + l2 for l1 < 8, 512 - kz beyond
       const float2* xc = Sx + l2 * C + ca;

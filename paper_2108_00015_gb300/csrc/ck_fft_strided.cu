@@ -18,7 +18,8 @@
 namespace ck {
 namespace fft {
 
-// Tile width of the register kernels (columns per tile, 32 threads per column).
+// Default tile width of the register kernels (columns per tile, 32 threads
+// per column); a plan's autotuner may choose 16 per pass.
 constexpr int kSregC = 8;
 constexpr int kZregC = 8;
 
@@ -89,10 +90,10 @@ static void run_zmulti(const float2* in, float2* out, int64_t out_stride, int ns
 #define CK_LENGTHS(X) X(32) X(128) X(160) X(192) X(240) X(256) X(288) X(320) X(384)
 
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
-                    const float2* stw, const float2* tw, bool wide, int sm_count, cudaStream_t st, const int* box,
+                    const float2* stw, const float2* tw, int cols, int sm_count, cudaStream_t st, const int* box,
                     int nz, int mode) {
   if (L == 512) {
-    if (wide) run_sreg512<16>(inv, in, out, v, tw, sm_count, st, box, nz, mode);
+    if (cols == 16) run_sreg512<16>(inv, in, out, v, tw, sm_count, st, box, nz, mode);
     else run_sreg512<kSregC>(inv, in, out, v, tw, sm_count, st, box, nz, mode);
     return;
   }
@@ -106,9 +107,10 @@ void launch_strided(int L, bool inv, const float2* in, float2* out, const Stride
 
 void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int nshells, const StridedView& v,
                    const FftLen& f, const float2* stw, const float2* tw, const KhatArgs& K, int sm_count,
-                   cudaStream_t st, const int* box) {
+                   cudaStream_t st, const int* box, int cols) {
   if (L == 512) {
-    run_zreg512<kZregC>(in, out, out_stride, nshells, v, tw, K, sm_count, st, box);
+    if (cols == 16) run_zreg512<16>(in, out, out_stride, nshells, v, tw, K, sm_count, st, box);
+    else run_zreg512<kZregC>(in, out, out_stride, nshells, v, tw, K, sm_count, st, box);
     return;
   }
   switch (L) {

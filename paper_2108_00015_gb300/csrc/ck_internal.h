@@ -115,6 +115,16 @@ struct Profiler {
   int* pin = nullptr;         // page-locked: 6 ints per record (support boxes)
 };
 
+// Choices the autotuner makes per plan (ck_plan_autotune); the defaults are
+// the measured best on the survey workloads.
+struct Tuning {
+  int fwd_cols = 8;        // columns per tile of the single-field 512-point strided passes
+  int zreg_cols = 8;       // of the K^ z pass (every shell)
+  int yinv_cols = 16;      // of the multi-shell inverse y pass
+  int tc_ctas_per_sm = 2;  // tensor-core contraction: CTAs per SM the splits aim at
+  bool tuned = false;
+};
+
 struct Plan {
   ck_grid grid{};
   int ns = 0;
@@ -190,6 +200,7 @@ struct Plan {
   int bank_fields = 0;      // real fields reserved in `bank`
   int device = 0;
   int sm_count = 0;
+  Tuning tune;
   // Region of a decomposed catalog (ck_plan_set_region): the sums run over
   // the box planes region_z0 <= z < region_z1 only; region_alpha > 0 is used
   // in place of sum D / sum R.
@@ -279,7 +290,7 @@ ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaS
 // ---- tcgen05 blocked product (ck_umma.cu) -------------------------------------
 int umma_tile_rows();
 int umma_tile_cols(int cols);
-int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count);
+int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count, int ctas_per_sm = 2);
 // A tile is (first row, offset of its column list, MMA N <= tn, list length).
 // Tensor-core tiles 0 .. ntc - 1 of ntiles (the partials are pitched by ntiles).
 // kind: 0 split-TF32, 1 split-BF16, 2 split-FP16 (absmax: ns + 1 device

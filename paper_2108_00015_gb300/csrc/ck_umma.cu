@@ -666,9 +666,10 @@ int umma_tile_cols(int cols) {
 int umma_tile_rows() { return UM_M; }
 
 // Cells per split: whole accumulation groups (256 cells), at most UM_MAX_GROUPS.
-int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count) {
+int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count, int ctas_per_sm) {
   const int64_t cap = (int64_t)UM_MAX_GROUPS * UM_GCELLS;
-  int64_t splits = std::max<int64_t>(1, (2 * (int64_t)sm_count + ntiles - 1) / std::max(ntiles, 1));
+  int64_t splits =
+      std::max<int64_t>(1, ((int64_t)ctas_per_sm * sm_count + ntiles - 1) / std::max(ntiles, 1));
   int64_t cps = (nc + splits - 1) / splits;
   cps = std::min(cps, cap);
   cps = (cps + UM_GCELLS - 1) / UM_GCELLS * UM_GCELLS;  // whole groups and staging fills

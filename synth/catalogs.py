@@ -330,6 +330,15 @@ WORKLOADS: Dict[str, dict] = {
         data=("ns_box", dict(seed=12, n_parents=2_500, n_children=20, sigma=8.0)),
         randoms=("uniform_box", dict(seed=13, n=2_000_000)),
     ),
+    # Profiler case for the K^ z pass at the survey's z length and shell count:
+    # periodic 128 x 256 x 512 of 8 h^-1 Mpc, the survey's 16 shells (16
+    # scratch spectra of 71 MB, about 2 GB on the device), small catalogs.
+    "profile_z512": dict(
+        grid=GridSpec((128, 256, 512), (0.0, 0.0, 0.0), 8.0, True),
+        shells=_shells(30.0, 8.0, 16), width=8.0, orders=(2, 3),
+        data=("ns_box", dict(seed=14, n_parents=2_500, n_children=20, sigma=8.0)),
+        randoms=("uniform_box", dict(seed=15, n=2_000_000)),
+    ),
 }
 
 

@@ -176,3 +176,20 @@ def test_undersized_workspace(lib):
     assert f(ctypes.byref(g), ctypes.byref(s), 3, 0, fake, need - 1, None, ctypes.byref(out)) == 3
     assert out.value is None
     assert f(ctypes.byref(g), ctypes.byref(s), 3, 0, fake, 0, None, ctypes.byref(out)) == 3
+
+
+def test_tuning_entry_points_validate(lib):
+    """ck_plan_autotune, ck_plan_set_tuning and ck_plan_get_tuning reject a
+    null plan or array (CK_ERR_BAD_POINTER) before any CUDA call."""
+    arr = (ctypes.c_int32 * 5)(8, 8, 16, 2, 0)
+    for name in ("ck_plan_autotune", "ck_plan_set_tuning", "ck_plan_get_tuning"):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        assert fn(None, ctypes.cast(arr, ctypes.c_void_p)) == 2, name
+    fn = lib.ck_plan_set_tuning
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: a null array is refused first
+    assert fn(fake, None) == 2
+    for bad in ((7, 8, 16, 2), (8, 32, 16, 2), (8, 8, 16, 0), (8, 8, 16, 4)):
+        # out-of-range choices are refused (CK_ERR_ARG) before the plan is read
+        assert fn(fake, ctypes.cast((ctypes.c_int32 * 4)(*bad), ctypes.c_void_p)) == 1, bad
