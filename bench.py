@@ -56,6 +56,9 @@ def _args():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP32 form beside the headline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (ck_plan_autotune times the choices after warm-up)")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed launch shapes instead of the autotuner: fwd_cols,zreg_cols,yinv_cols,ctas_per_sm "
+                         "(8 or 16 columns per tile of the strided passes, 1..3 contraction CTAs per SM)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the higher-order workloads timed beside the headline at N = 1 (stress256: xi_2..xi_5, "
                          "survey512_s32: xi_2..xi_4, in every contraction form)")
@@ -514,7 +517,12 @@ def run_gb300(args):
         step()
     torch.cuda.synchronize()
     tuning = None
-    if not args.no_autotune and not (args.continuous or args.diagonal):
+    if args.tuning:
+        plan.set_tuning(*[int(v) for v in args.tuning.split(",")])
+        tuning = plan.tuning()
+        step()
+        torch.cuda.synchronize()
+    elif not args.no_autotune and not (args.continuous or args.diagonal):
         # launch-shape choices timed on the resident randoms (results unchanged)
         tuning = plan.autotune()
         step()

@@ -466,7 +466,7 @@ class Plan:
         _check(_lib().ck_plan_autotune(self._h, _stream_ptr(stream)), "ck_plan_autotune")
         return self.tuning()
 
-    def set_tuning(self, fwd_cols: int = 8, zreg_cols: int = 8, yinv_cols: int = 16, tc_ctas_per_sm: int = 2):
+    def set_tuning(self, fwd_cols: int = 8, zreg_cols: int = 8, yinv_cols: int = 8, tc_ctas_per_sm: int = 2):
         arr = (ctypes.c_int32 * 4)(fwd_cols, zreg_cols, yinv_cols, tc_ctas_per_sm)
         _check(_lib().ck_plan_set_tuning(self._h, arr), "ck_plan_set_tuning")
 

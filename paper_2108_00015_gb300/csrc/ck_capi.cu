@@ -146,6 +146,7 @@ ck_status carve(Plan& p) {
   for (int a = 0; a < 3; ++a) p.thr[a] = reinterpret_cast<float*>(take((size_t)(p.grid.n[a] + 1) * 4));
   for (int a = 0; a < 3; ++a) p.tw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
   for (int a = 0; a < 3; ++a) p.stw[a] = reinterpret_cast<float2*>(take((size_t)p.grid.n[a] * 8));
+  p.twm = reinterpret_cast<float2*>(take((size_t)512 * 8));
   p.dstate = reinterpret_cast<DevState*>(take(sizeof(DevState)));
   p.dref = reinterpret_cast<CatalogRef*>(take(sizeof(CatalogRef)));
   p.den_raw = reinterpret_cast<double*>(take((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8));
@@ -211,6 +212,17 @@ ck_status upload_tables(Plan& p, cudaStream_t st) {
     stage_twiddles(a == 0 ? p.grid.n[0] / 2 : p.grid.n[a], w);
     if (w.size() > (size_t)p.grid.n[a]) return CK_ERR_ARG;
     CK_TRY(cudaMemcpy(p.stw[a], w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+  }
+  {
+    // w512^(l2 m1) with the 32 values of l2 adjacent: a warp of the K^ z
+    // pass reads consecutive entries
+    std::vector<float2> w(512);
+    for (int m1 = 0; m1 < 16; ++m1)
+      for (int l2 = 0; l2 < 32; ++l2) {
+        const double a = 2.0 * M_PI * (double)(l2 * m1) / 512.0;
+        w[(size_t)m1 * 32 + l2] = make_float2((float)cos(a), (float)-sin(a));
+      }
+    CK_TRY(cudaMemcpy(p.twm, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
   }
   // dense [N_s]^(n-1) index -> rank of its sorted multiset
   std::vector<int> map((size_t)std::max<int64_t>(p.dense_total, 1), 0);

@@ -67,7 +67,7 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
     ProfScope ps(p, ST_FFT_Z_INV_MUL, base + (zbox ? 0.0 : nshells * 8.0 * H), 0.0, nshells * row * ny, zbox, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
     KhatArgs K{khat, p.khat_stride, p.px, ny, nz, p.oct[1]};
-    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.tw[2], K, p.sm_count, st, zbox,
+    fft::launch_zmulti(nz, spec, tmp, p.spec_elems, nshells, v, p.fz, p.stw[2], p.twm, K, p.sm_count, st, zbox,
                        p.tune.zreg_cols);
   }
   {

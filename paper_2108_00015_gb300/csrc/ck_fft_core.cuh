@@ -786,7 +786,9 @@ inline size_t xpass_smem(int nx) {
 // box (device, may be null; 512-point axes only) with `mode` (the pruning
 // bits of ck_fft_sreg.cuh: transform only the box's planes, write only its
 // rows y, read only its rows y or z as nonzero input); for the z pass with
-// the multiply, only the box's planes are written.
+// the multiply, only the box's planes are written.  launch_zmulti's tw: for
+// L = 512 the twiddle matrix w512^(l2 m1) at [m1 * 32 + l2] (Plan::twm),
+// unused otherwise.
 void launch_strided(int L, bool inv, const float2* in, float2* out, const StridedView& v, const FftLen& f,
                     const float2* stw, const float2* tw, int cols, int sm_count, cudaStream_t st,
                     const int* box = nullptr, int nz = 0, int mode = 0);

@@ -5,8 +5,8 @@
 // other length the runtime version.
 //
 // Tile width of the 512-point register kernels: 8 columns (256 threads, two
-// CTAs per SM) for single-field passes, 16 columns (512 threads, one CTA per
-// SM) when the caller asks for wide tiles.  On the 16-shell in-place inverse
+// CTAs per SM; three for the K^ z pass) for single-field passes, 16 columns
+// (512 threads, one CTA per SM) when the caller asks for wide tiles.  On the 16-shell in-place inverse
 // y pass (8.6 GB) a GB300 sustained 5.6 TB/s with 16 columns, 5.2 TB/s with
 // the Stockham kernel and 4.0 TB/s with 8 columns; on single-field passes
 // 8 columns are the fastest.
@@ -50,6 +50,9 @@ static void run_zreg512(const float2* in, float2* out, int64_t out_stride, int n
   const size_t sm = S::multi_bytes;
   const int64_t ntiles = (v.inner + C - 1) / C;
   allow_smem(zreg512_kernel<C>, sm);
+  // three 8-column CTAs (3 x 74.2 KB) need the largest shared-memory carveout
+  cudaFuncSetAttribute(zreg512_kernel<C>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       (int)cudaSharedmemCarveoutMaxShared);
   int occ = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, zreg512_kernel<C>, S::NT, sm) != cudaSuccess || occ < 1) {
     cudaGetLastError();

@@ -120,7 +120,7 @@ struct Profiler {
 struct Tuning {
   int fwd_cols = 8;        // columns per tile of the single-field 512-point strided passes
   int zreg_cols = 8;       // of the K^ z pass (every shell)
-  int yinv_cols = 16;      // of the multi-shell inverse y pass
+  int yinv_cols = 8;       // of the multi-shell inverse y pass
   int tc_ctas_per_sm = 2;  // tensor-core contraction: CTAs per SM the splits aim at
   bool tuned = false;
 };
@@ -169,6 +169,7 @@ struct Plan {
   int64_t staging_pts = 0;  // points per staging slot
   float* thr[3] = {nullptr, nullptr, nullptr};   // cell-edge thresholds, n+1 each
   float2* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i t / n_a}, n_a each
+  float2* twm = nullptr;  // e^{-2 pi i l2 m1 / 512} at [m1 * 32 + l2], m1 < 16, l2 < 32 (K^ z pass)
   float2* stw[3] = {nullptr, nullptr, nullptr};  // per-iteration twiddles of the y, z and half-x lengths
   DevState* dstate = nullptr;
   double* den_raw = nullptr;   // packed per order (multiset order)

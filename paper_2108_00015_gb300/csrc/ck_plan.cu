@@ -224,6 +224,7 @@ size_t workspace_bytes(const Plan& p) {
   b += al((size_t)p.nc * 8);                                   // fixed-point weight sums
   for (int a = 0; a < 3; ++a) b += al((size_t)(p.grid.n[a] + 1) * 4);  // thresholds
   for (int a = 0; a < 3; ++a) b += 2 * al((size_t)p.grid.n[a] * 8);    // twiddles: full and per-iteration
+  b += al((size_t)512 * 8);                                            // twiddle matrix of the K^ z pass
   b += al(sizeof(DevState));
   b += al(sizeof(CatalogRef));
   b += 2 * al((size_t)std::max<int64_t>(p.n_multiset_total, 1) * 8);   // den_raw, sums

@@ -76,7 +76,7 @@ def test_contraction_ctas_per_sm(precision):
     plan = plan_for(w, max_order=5, precision=precision)
     tol = 1e-5 if precision == "split_tf32" else 5e-5
     for k in (1, 2, 3):
-        plan.set_tuning(8, 8, 16, k)
+        plan.set_tuning(8, 8, 8, k)
         sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=(2, 3, 4, 5))
         for n in (2, 3, 4, 5):
             want, awant = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
