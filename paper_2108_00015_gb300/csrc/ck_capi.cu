@@ -833,19 +833,24 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
   const bool tensor = p.precision == CK_PREC_SPLIT_TF32 || p.precision == CK_PREC_SPLIT_BF16 ||
                       p.precision == CK_PREC_SPLIT_FP16;
   if (s == CK_OK && tensor && !p.fused) {
-    float best = 1e30f;
-    int pick = p.tune.tc_ctas_per_sm;
     const int mask = full_mask(p);
-    for (int k : {1, 2, 3}) {
-      p.tune.tc_ctas_per_sm = k;
-      for (bool& r : p.cplan_ready) r = false;
-      float ms = 0.0f;
-      const ck_status c = timed([&] { launch_contract(p, mask, p.field, p.bank, p.field_stride, p.sums, st); }, &ms);
-      if (c == CK_ERR_OOM) continue;  // more splits than the partials hold
-      if ((s = c) != CK_OK) break;
-      if (ms < best) { best = ms; pick = k; }
-    }
-    p.tune.tc_ctas_per_sm = pick;
+    // the widest stacked tile, then the CTAs per SM
+    auto pick_best = [&](int* knob, std::initializer_list<int> cands) {
+      float best = 1e30f;
+      int pick = *knob;
+      for (int k : cands) {
+        *knob = k;
+        for (bool& r : p.cplan_ready) r = false;
+        float ms = 0.0f;
+        const ck_status c = timed([&] { launch_contract(p, mask, p.field, p.bank, p.field_stride, p.sums, st); }, &ms);
+        if (c == CK_ERR_OOM) continue;  // more splits than the partials hold
+        if ((s = c) != CK_OK) break;
+        if (ms < best) { best = ms; pick = k; }
+      }
+      *knob = pick;
+    };
+    pick_best(&p.tune.tc_stack_cols, {0, 32, 64});
+    if (s == CK_OK) pick_best(&p.tune.tc_ctas_per_sm, {1, 2, 3});
     for (bool& r : p.cplan_ready) r = false;
   }
   if (e0) cudaEventDestroy(e0);
@@ -870,12 +875,13 @@ ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in) {
   if (!plan || !in) return CK_ERR_BAD_POINTER;
   for (int i = 0; i < 3; ++i)
     if (in[i] != 8 && in[i] != 16) return CK_ERR_ARG;
-  if (in[3] < 1 || in[3] > 3) return CK_ERR_ARG;
+  if (in[3] < 1 || in[3] > 3 || in[4] < 0 || in[4] > 128) return CK_ERR_ARG;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   p.tune.fwd_cols = in[0];
   p.tune.zreg_cols = in[1];
   p.tune.yinv_cols = in[2];
   p.tune.tc_ctas_per_sm = in[3];
+  p.tune.tc_stack_cols = in[4];
   for (bool& r : p.cplan_ready) r = false;
   for (auto& g : p.gexec)
     if (g) {
@@ -892,7 +898,8 @@ ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out) {
   out[1] = p.tune.zreg_cols;
   out[2] = p.tune.yinv_cols;
   out[3] = p.tune.tc_ctas_per_sm;
-  out[4] = p.tune.tuned ? 1 : 0;
+  out[4] = p.tune.tc_stack_cols;
+  out[5] = p.tune.tuned ? 1 : 0;
   return CK_OK;
 }
 

@@ -528,9 +528,15 @@ ck_status contract_prepare(Plan& p, int mask) {
     std::stable_partition(tl.begin(), tl.end(), [&](const int4& t) { return !thin(t); });
     c.um_ntc = 0;
     c.um_thin_rmax = 0;
-    for (const int4& t : tl)
+    for (int4& t : tl)
       if (!thin(t)) {
         ++c.um_ntc;
+        // narrow tiles: hi and lo of B side by side, two MMAs per k-step
+        const int half = (t.w + 15) / 16 * 16;
+        if (t.w <= p.tune.tc_stack_cols && 2 * half <= 256) {
+          t.z = 2 * half;
+          t.w |= kUmmaStacked;
+        }
         tnmax = std::max(tnmax, t.z);
       } else {
         c.um_thin_rmax = std::max(c.um_thin_rmax, std::min<int>(TM, (int)rows.size() - t.x));
@@ -548,7 +554,8 @@ ck_status contract_prepare(Plan& p, int mask) {
     if (e == cudaSuccess && !tl.empty()) e = cudaMemcpy(c.d_um_tiles, tl.data(), tl.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !clist.empty()) e = cudaMemcpy(c.d_um_cols, clist.data(), clist.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_status(e);
-    c.um_cps = umma_cells_per_split(p.nc, std::max(c.n_tiles, 1), p.sm_count, p.tune.tc_ctas_per_sm);
+    // the splits fill the SMs with tensor-core tiles (thin tiles take the same splits)
+    c.um_cps = umma_cells_per_split(p.nc, std::max(c.um_ntc, 1), p.sm_count, p.tune.tc_ctas_per_sm);
     c.splits = (int)((p.nc + c.um_cps - 1) / c.um_cps);
     c.partial_doubles = (size_t)c.splits * std::max(c.n_tiles, 1) * TM * c.um_tn;
     if (c.partial_doubles > p.partials_cap) return CK_ERR_OOM;

@@ -122,6 +122,7 @@ struct Tuning {
   int zreg_cols = 8;       // of the K^ z pass (every shell)
   int yinv_cols = 8;       // of the multi-shell inverse y pass
   int tc_ctas_per_sm = 2;  // tensor-core contraction: CTAs per SM the splits aim at
+  int tc_stack_cols = 32;  // tensor-core tiles of at most this many columns are stacked (0: none)
   bool tuned = false;
 };
 
@@ -289,10 +290,15 @@ size_t xc_smem_bytes(int M, int ns_pad);  // shared memory of the fused kernel
 ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st, const int* box);
 
 // ---- tcgen05 blocked product (ck_umma.cu) -------------------------------------
+constexpr int kUmmaStacked = 1 << 16;
 int umma_tile_rows();
 int umma_tile_cols(int cols);
 int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count, int ctas_per_sm = 2);
-// A tile is (first row, offset of its column list, MMA N <= tn, list length).
+// A tile is (first row, offset of its column list, MMA N <= tn, list length
+// L, plus kUmmaStacked for a stacked tile).  A stacked tile puts the hi and
+// lo parts of each B column side by side (columns q and N/2 + q, N = 2 x L
+// rounded up to 16) and issues A_hi x B and A_lo x B per k-step, two MMAs
+// instead of three; its partials hold both halves, which the reduction adds.
 // Tensor-core tiles 0 .. ntc - 1 of ntiles (the partials are pitched by ntiles).
 // kind: 0 split-TF32, 1 split-BF16, 2 split-FP16 (absmax: ns + 1 device
 // words for the FP16 scales, filled here).

@@ -178,7 +178,8 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   p->staging_pts = (int64_t)1 << 21;
   // Partial sums of the contraction kernels (doubles); split-TF32 plans that
   // keep the bank need one 128 x TN tile of FP64 per tile and split of at
-  // most 16384 cells (bounded here for any device of up to 256 SMs).
+  // most 16384 cells, the splits filling up to 3 CTAs per SM on any device
+  // of up to 256 SMs with as few as one tensor-core tile.
   p->partials_cap = (size_t)1 << 22;
   const bool tensor = precision == CK_PREC_SPLIT_TF32 || precision == CK_PREC_SPLIT_BF16 ||
                       precision == CK_PREC_SPLIT_FP16;
@@ -186,10 +187,11 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
     const int64_t ns = p->ns;
     const int64_t urows = 1 + (max_order >= 3 ? ns : 0) + (max_order >= 4 ? ns * (ns + 1) / 2 : 0);
     const int64_t ucols = ns + (max_order >= 5 ? ns * (ns + 1) / 2 : 0);
-    const int tn = umma_tile_cols((int)ucols);
+    // a stacked tile (at most 128 columns) is twice its list length wide
+    const int64_t scols = 2 * ((std::min<int64_t>(ucols, 128) + 15) / 16 * 16);
+    const int tn = umma_tile_cols((int)std::min<int64_t>(256, std::max(ucols, scols)));
     const int64_t ntiles = ((urows + umma_tile_rows() - 1) / umma_tile_rows()) * ((ucols + tn - 1) / tn);
-    const int64_t splits = std::min<int64_t>((p->nc + 31) / 32, std::max<int64_t>((p->nc + 16383) / 16384,
-                                                                                   (512 + ntiles - 1) / ntiles));
+    const int64_t splits = std::min<int64_t>((p->nc + 31) / 32, std::max<int64_t>((p->nc + 16383) / 16384, 768));
     p->partials_cap = std::max<size_t>(p->partials_cap, (size_t)(splits * ntiles * umma_tile_rows() * tn));
   }
   // Contraction operand tables: one slot per order mask.

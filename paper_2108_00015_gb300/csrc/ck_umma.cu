@@ -168,8 +168,10 @@ __device__ __forceinline__ void um_split2(float a, float b, uint32_t& hi, uint32
   lo = um_pack2<KIND>(a - ha, b - hb);
 }
 
+// Tiles of at most 64 columns fit two CTAs per SM (96 registers, under
+// 100 KB of shared memory each).
 template <int TN, int KIND>
-__global__ void __launch_bounds__(UM_THREADS, 1)
+__global__ void __launch_bounds__(UM_THREADS, TN <= 64 ? 2 : 1)
     contract_umma_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride, int64_t nc,
                          int ns, int wcells, const int2* __restrict__ rowdesc, int rows,
                          const int2* __restrict__ coldesc, const int4* __restrict__ tiles,
@@ -203,15 +205,19 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
   auto Ws = [&](int b) { return wsb + b * WR * wp; };
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  // tile: rows tile.x .. + 127, columns collist[tile.y + i] for i < tile.w,
-  // MMA N = tn = tile.z (a multiple of 32, at most TN)
+  // tile: rows tile.x .. + 127, columns collist[tile.y + i] for i < cnt,
+  // MMA N = tn = tile.z (a multiple of 32, at most TN); a stacked tile holds
+  // B's hi part in MMA columns 0 .. tnb - 1 and its lo part in tnb ..
   const int4 tile = tiles[blockIdx.x];
   const int tn = tile.z;
+  const bool stk = (tile.w & kUmmaStacked) != 0;
+  const int cnt = tile.w & (kUmmaStacked - 1);
+  const int tnb = stk ? tn / 2 : tn;  // columns whose products the builders form
   // each operand row is the product of staged rows: A_p = W0 W_a W_b, B_q = W_c W_d,
   // with the ones row for an absent factor and the zeros row for a padding row
   const int ONE = ns + 1, ZERO = ns + 2;
   for (int i = tid; i < TN; i += UM_THREADS) {
-    const int2 d = i < tile.w ? coldesc[collist[tile.y + i]] : make_int2(-2, -2);
+    const int2 d = i < cnt ? coldesc[collist[tile.y + i]] : make_int2(-2, -2);
     fb[i] = d.x == -2 ? make_int4(ZERO, ONE, 0, 0) : make_int4(d.x >= 0 ? 1 + d.x : ONE, d.y >= 0 ? 1 + d.y : ONE, 0, 0);
     fsc[i] = d.x == -2 ? 1.0f
                        : um_factor_scale<KIND>(absmax, d.x >= 0 ? 1 + d.x : ONE, ONE) *
@@ -305,7 +311,15 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
           // A advances by 8 tensor-memory columns either way
           const uint32_t bo = 2 * k * b_lbo;
           const uint64_t dbh = umma_desc(bhs + bo, b_lbo, 128), dbl = umma_desc(bls + bo, b_lbo, 128);
-          if constexpr (KIND == UM_TF32) {
+          if (stk) {  // B = [hi | lo]: hi*hi, hi*lo, lo*hi and lo*lo in two MMAs
+            if constexpr (KIND == UM_TF32) {
+              umma_tf32_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
+              umma_tf32_ts(dt, al + 8 * k, dbh, idesc, true);
+            } else {
+              umma_f16_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
+              umma_f16_ts(dt, al + 8 * k, dbh, idesc, true);
+            }
+          } else if constexpr (KIND == UM_TF32) {
             umma_tf32_ts(dt, ah + 8 * k, dbh, idesc, !(first && k == 0));
             umma_tf32_ts(dt, ah + 8 * k, dbl, idesc, true);
             umma_tf32_ts(dt, al + 8 * k, dbh, idesc, true);
@@ -354,13 +368,17 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     for (int j = 0; j < S::UN; ++j) {
       const int u = bw + UM_BWARPS * j;
       const int r8 = u >> 1;
-      b_any[j] = u < tn / 4;
-      b_live[j] = b_any[j] && 8 * r8 < tile.w;  // uniform over the warp
+      b_any[j] = u < tnb / 4;
+      b_live[j] = b_any[j] && 8 * r8 < cnt;  // uniform over the warp
       const int4 f = b_any[j] ? fb[8 * r8 + rr] : make_int4(ZERO, ONE, 0, 0);
       bu[j] = f.x * wp + (u & 1) * (KC / 2) + 4 * kq;
       bv[j] = f.y * wp + (u & 1) * (KC / 2) + 4 * kq;
       bsc[j] = b_any[j] ? fsc[8 * r8 + rr] : 1.0f;
     }
+    // where the lo part of a B item goes: the lo buffer, or (stacked tile)
+    // tnb columns = tnb / 8 cores further in the hi buffer
+    auto BloF = [&](int s) { return stk ? Bhi(s) + (tnb / 8) * 32 : Blo(s); };
+    auto BloB2 = [&](int s) { return stk ? BhiB(s) + (tnb / 8) * 128 : BloB(s); };
     // floats: core (r8, kc), row rr of a B stage (kc = 4 item + kq)
     auto b_off = [&](int j, int item) {
       const int u = bw + UM_BWARPS * j;
@@ -392,10 +410,10 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
           for (int i = 0; i < KC / 32; ++i) {
             if constexpr (KIND == UM_TF32) {
               *reinterpret_cast<float4*>(Bhi(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
-              *reinterpret_cast<float4*>(Blo(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
+              *reinterpret_cast<float4*>(BloF(s) + b_off(j, i)) = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
               *reinterpret_cast<uint2*>(BhiB(s) + b_off16(j, i)) = make_uint2(0u, 0u);
-              *reinterpret_cast<uint2*>(BloB(s) + b_off16(j, i)) = make_uint2(0u, 0u);
+              *reinterpret_cast<uint2*>(BloB2(s) + b_off16(j, i)) = make_uint2(0u, 0u);
             }
           }
     float mid[S::half];
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
       tc_fence_after();
       const float* w = Ws(b) + (c % wch) * KC;
       float* bh = Bhi(s);
-      float* bl = Blo(s);
+      float* bl = BloF(s);
 #pragma unroll
       for (int i = 0; i < KC / 32; ++i) {  // 16 cells per item
         if (a_live && KIND != UM_TF32) {  // A row m, 16 cells: packed hi and lo pairs
@@ -523,7 +541,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
               um_split2<KIND>(p2, p3, h.y, l.y);
               const int off = b_off16(j, i);
               *reinterpret_cast<uint2*>(BhiB(s) + off) = h;
-              *reinterpret_cast<uint2*>(BloB(s) + off) = l;
+              *reinterpret_cast<uint2*>(BloB2(s) + off) = l;
             }
           }
       }
@@ -544,7 +562,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1)
     for (int j = 0; j < S::half; ++j)
       if (j < hc) {
         double v = (double)mid[j];
-        if constexpr (KIND == UM_FP16) v /= (double)asc * (double)fsc[hf * hc + j];  // exact powers of two
+        if constexpr (KIND == UM_FP16) v /= (double)asc * (double)fsc[stk ? j : hf * hc + j];  // exact powers of two
         out[m * TN + hf * hc + j] = v;
       }
   }
@@ -608,13 +626,19 @@ __global__ void reduce_umma_kernel(const double* __restrict__ partials, int spli
   const int pq = (int)(t - (int64_t)tile * per);
   const int4 tl = tiles[tile];
   const int p = tl.x + pq / tn, ci = pq % tn;  // row and column of the partial
-  if (p >= rows || ci >= tl.w) return;
+  const int cnt = tl.w & (kUmmaStacked - 1);
+  if (p >= rows || ci >= cnt) return;
   const int q = collist[tl.y + ci];
   int ms[4];
   const int n = umma_canonical(rowdesc[p], coldesc[q], mask, ms);
   if (!n) return;
+  // a stacked tile's lo half sits tl.z / 2 columns to the right
+  const int lo = (tl.w & kUmmaStacked) ? tl.z / 2 : 0;
   double s = 0.0;
-  for (int sp = lane; sp < splits; sp += 32) s += partials[((int64_t)sp * ntiles + tile) * per + pq];
+  for (int sp = lane; sp < splits; sp += 32) {
+    const double* pt = partials + ((int64_t)sp * ntiles + tile) * per + pq;
+    s += lo ? pt[0] + pt[lo] : pt[0];
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
   if (lane == 0) out[B.base[n] + umma_rank(ms, n - 1, ns)] = s;

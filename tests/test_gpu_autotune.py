@@ -61,24 +61,31 @@ def test_tile_widths_bit_identical(precision):
     plan.close()
 
 
-@pytest.mark.parametrize("precision", ["split_tf32", "split_bf16"])
-def test_contraction_ctas_per_sm(precision):
+@pytest.mark.parametrize("precision", ["split_tf32", "split_bf16", "split_fp16"])
+@pytest.mark.parametrize("ns,orders", [(8, (2, 3, 4, 5)), (8, (2, 3, 4)), (32, (2, 3, 4))])
+def test_contraction_tile_choices(precision, ns, orders):
+    """Every contraction CTA count and stacked-tile width gives sums within
+    the form's gate of the oracle's: stacked tiles (B's hi and lo side by
+    side, two MMAs per k-step) cover the order-4 column lists of 8 and 32
+    shells (8 and 32 live columns) and, at width 64, the 44-column tile of
+    orders up to 5."""
     torch = cuda_torch()
     g = GridSpec((24, 20, 18), (0.0, 0.0, 0.0), 1.0, True)
-    rng = np.random.default_rng(63)
-    nc, ns = g.n_cells, 8
+    rng = np.random.default_rng(63 + ns)
+    nc = g.n_cells
     w0 = rng.normal(size=nc).astype(np.float32)
     bank = rng.normal(size=(ns, nc)).astype(np.float32)
     stride = (nc + 63) // 64 * 64
     B = np.zeros((ns, stride), np.float32)
     B[:, :nc] = bank
     w = dict(grid=g, shells=tuple(1.0 + 0.05 * i for i in range(ns)), width=1.0)
-    plan = plan_for(w, max_order=5, precision=precision)
-    tol = 1e-5 if precision == "split_tf32" else 5e-5
-    for k in (1, 2, 3):
-        plan.set_tuning(8, 8, 8, k)
-        sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=(2, 3, 4, 5))
-        for n in (2, 3, 4, 5):
-            want, awant = O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n)
-            assert normwise(sums[n].cpu().numpy(), want, awant) <= tol, (k, n)
+    plan = plan_for(w, max_order=max(orders), precision=precision)
+    tol = 5e-5 if precision == "split_bf16" else 1e-5
+    want = {n: O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n) for n in orders}
+    for stack in (0, 32, 64):
+        for k in (1, 2, 3):
+            plan.set_tuning(8, 8, 8, k, stack)
+            sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=orders)
+            for n in orders:
+                assert normwise(sums[n].cpu().numpy(), *want[n]) <= tol, (stack, k, n)
     plan.close()
