@@ -576,7 +576,10 @@ def run_gb300(args):
             tr = json.load(open(tr_path))
             ent = tr.get(args.workload, {}).get(dname)
             src = os.path.join(ROOT, "paper_2108_00015_gb300", "csrc", ent["source"]) if ent else None
-            if ent and src and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == ent["sha"]:
+            # counters of the same source and, where recorded, the same tile width
+            cols = {"fft_z_inv_mul": "zreg_cols", "fft_y_inv": "yinv_cols"}.get(dname)
+            same_shape = ent is not None and ("cols" not in ent or (tuning or plan.tuning()).get(cols) == ent["cols"])
+            if ent and src and same_shape and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == ent["sha"]:
                 traffic = ent["bytes_per_launch"]
         except Exception:
             traffic = None

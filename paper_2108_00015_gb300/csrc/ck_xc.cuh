@@ -327,12 +327,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 // x[2m] = Re z[m], x[2m+1] = Im z[m] into the store W, which takes the
 // place of the tile's staged rows (consumed by step A).  A tile is
 // LT = 256 / max(P, Q) lines: ROWS = LT / NS grid rows of every shell, all
-// transformed at once; two block barriers per tile (three when P != Q).  Right after a tile's
-// first barrier, one thread stages the next tile into the other buffer
-// (whose store the previous tile's sums have read) with bulk asynchronous
-// copies, one per padded half-spectrum row (px = M + 4 complex values) and
-// one for the tile's N cells, completing on the buffer's mbarrier; waits are
-// bounded.
+// transformed at once; one block barrier per tile (two when P != Q or
+// ROWS > 1), before the sums.  Warp 0 stages the next tile into the other
+// buffer once every warp has arrived on that buffer's "empty" mbarrier
+// after the previous tile's sums (the other warps do not wait), with bulk
+// asynchronous copies, one per padded half-spectrum row (px = M + 4 complex
+// values) and one for the tile's N cells, completing on the buffer's "full"
+// mbarrier.  Waits are bounded; a failed wait in any warp ends every warp
+// at the next block barrier.
 //
 // In the sums, k-slot t of a k-step holds cell c0 + 2t and slot t + 4 cell
 // c0 + 2t + 1, so that each lane reads its two cells with one 8-byte load.
@@ -355,7 +357,7 @@ struct XcrShape {
   static constexpr size_t nb_bytes = align16((size_t)TC * sizeof(float));
   static constexpr size_t bar_off = nb_off + 2 * nb_bytes;
   static constexpr size_t red_bytes = (size_t)kWarps * NS * (NS + 1) * sizeof(double);
-  static constexpr size_t total0 = bar_off + 16;
+  static constexpr size_t total0 = bar_off + 32;  // full[2], empty[2]
   static constexpr size_t total = total0 > red_bytes ? total0 : red_bytes;
   static_assert(ROWS >= 1 && LT % NS == 0, "a tile holds whole rows of every shell");
   static_assert((size_t)NS * WP * sizeof(float) <= s_bytes, "the store fits in a staging buffer");
@@ -384,7 +386,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   float2* twu = reinterpret_cast<float2*>(sm + S::twu_off);
   float2* twq = reinterpret_cast<float2*>(sm + S::twq_off);
   float2* T = reinterpret_cast<float2*>(sm + S::t_off);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::bar_off);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + S::bar_off);  // [2] a tile staged (bulk-copy bytes)
+  uint64_t* empty = full + 2;                                       // [2] every warp's sums of the buffer done
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tq = lane & 3;
@@ -397,6 +400,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (tid == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
+    mbar_init(&empty[0], kWarps);
+    mbar_init(&empty[1], kWarps);
   }
   fence_async_shared();  // zeroed buffers and barrier initialisation before any bulk copy
   __syncthreads();
@@ -445,20 +450,24 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (t < ntiles) issued = 1;
   for (int kt = 0; t < ntiles; t += gridDim.x, ++kt) {
     const int64_t tn = t + gridDim.x;
-    const bool ok = mbar_wait(&full[kt & 1], (uint32_t)(kt >> 1) & 1u, status);
-    if (__syncthreads_or(!ok)) break;
-    used = kt + 1;
-    // every warp is past the previous tile's sums: its buffers take the next tile
-    if (tn < ntiles) {
-      if (warp == 0) stage((kt + 1) & 1, (kt + 1) & 1, tn);
-      issued = kt + 2;
+    bool ok = mbar_wait(&full[kt & 1], (uint32_t)(kt >> 1) & 1u, status);
+    if (ok) used = kt + 1;
+    // the next tile goes to the buffers of tile kt - 1 once every warp has
+    // finished that tile's sums (empty barrier); the other warps go on
+    if (warp == 0 && ok && tn < ntiles) {
+      if (kt >= 1) ok = mbar_wait(&empty[(kt + 1) & 1], (uint32_t)((kt - 1) >> 1) & 1u, status);
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (ok) {
+        stage((kt + 1) & 1, (kt + 1) & 1, tn);
+        issued = kt + 2;
+      }
     }
     float* W = reinterpret_cast<float*>(sbuf(kt & 1));
     const int64_t r0 = t * ROWS;
     const int vc = (int)(rm.count - r0 < ROWS ? rm.count - r0 : ROWS) * NX;  // cells of the tile with data
     // step A: unpack Z[Q k1 + k2] = (X[k] + conj X[M-k]) + i e^{2 pi i k/NX} (X[k] - conj X[M-k]),
     // P-point inverse DFT over k1, twiddle e^{2 pi i k2 m1 / M}, into T
-    if (tid < LT * Q) {
+    if (ok && tid < LT * Q) {
       const int l = tid / Q, k2 = tid - l * Q;
       const float2* xr = sbuf(kt & 1) + l * LP;
       float2 v[P];
@@ -480,10 +489,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     // the store row W[shell] covers exactly the bytes of that line's staged
     // row: the warp alone touches them, so it need not wait for the others.
     if constexpr (S::kWarpLocal) __syncwarp();
-    else __syncthreads();
+    else if (__syncthreads_or(!ok)) break;
     // step B: Q-point inverse DFT over k2 of column m1
     const int lb = tid / P, m1 = tid - lb * P;
-    if (tid < LT * P) {
+    if (ok && tid < LT * P) {
       float2 z[Q];
 #pragma unroll
       for (int k2 = 0; k2 < Q; ++k2) z[k2] = T[lb * TP + k2 * (P + 1) + m1];
@@ -493,7 +502,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int m2 = 0; m2 < Q; ++m2) *reinterpret_cast<float2*>(wr + 2 * P * m2) = z[m2];
     }
-    __syncthreads();
+    // the store complete everywhere; a failed wait anywhere ends every warp here
+    if (__syncthreads_or(!ok)) break;
     // rank-8 updates on the tensor cores (see xc_contract_kernel)
     {
       const float* nb = nbuf(kt & 1);
@@ -548,9 +558,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         since = 0;
       }
     }
-    // the next tile's step A writes T, and its staging overwrites this
-    // tile's store, only after its first barrier, which every warp reaches
-    // after these sums
+    // this warp is done with the tile's buffers; the next tile's step A
+    // writes T only after this tile's second barrier
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[kt & 1]);
   }
   // after a timed-out wait: let the copies already issued land (bounded)
   if (tid == 0)
