@@ -87,35 +87,52 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
   unsigned long long kept = 0, dropped = 0;
   long long qsum = 0;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
-  for (int64_t i = first; i < nround; i += stride) {
-    bool in = i < npts;
-    int kx = 0, ky = 0, kz = 0;
-    long long q = 0;
-    if (in) {
-      bool ok = axis_cell(__ldg(xs + i), 0, A, &kx) && axis_cell(__ldg(ys + i), 1, A, &ky) &&
-                axis_cell(__ldg(zs + i), 2, A, &kz);
-      if constexpr (W) {
-        const float w = __ldg(ws + i);
-        ok = ok && isfinite(w);
-        if (ok) q = llrint((double)w * 4294967296.0);  // exact product; nearest, ties to even
-      }
-      if (ok) {
-        ++kept;
-        qsum += q;
-        bmin[0] = min(bmin[0], kx); bmax[0] = max(bmax[0], kx);
-        bmin[1] = min(bmin[1], ky); bmax[1] = max(bmax[1], ky);
-        bmin[2] = min(bmin[2], kz); bmax[2] = max(bmax[2], kz);
-      } else {
-        ++dropped;
-      }
-      in = ok;
+  // U points per thread per round: their coordinates are loaded before any
+  // is gridded, so that U independent loads per thread are in flight
+  constexpr int U = 4;
+  for (int64_t base = first; base < nround; base += U * stride) {
+    float px[U], py[U], pz[U], pw[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * stride;
+      const bool in = i < npts;
+      px[u] = in ? __ldg(xs + i) : 0.0f;
+      py[u] = in ? __ldg(ys + i) : 0.0f;
+      pz[u] = in ? __ldg(zs + i) : 0.0f;
+      if constexpr (W) pw[u] = in ? __ldg(ws + i) : 0.0f;
     }
-    const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
-    if constexpr (W) {
-      if (in) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
-    } else {
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
-      if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * stride;
+      if (i >= nround) break;  // warp-uniform: a warp's indices share one 32-aligned block
+      bool in = i < npts;
+      int kx = 0, ky = 0, kz = 0;
+      long long q = 0;
+      if (in) {
+        bool ok = axis_cell(px[u], 0, A, &kx) && axis_cell(py[u], 1, A, &ky) && axis_cell(pz[u], 2, A, &kz);
+        if constexpr (W) {
+          const float w = pw[u];
+          ok = ok && isfinite(w);
+          if (ok) q = llrint((double)w * 4294967296.0);  // exact product; nearest, ties to even
+        }
+        if (ok) {
+          ++kept;
+          qsum += q;
+          bmin[0] = min(bmin[0], kx); bmax[0] = max(bmax[0], kx);
+          bmin[1] = min(bmin[1], ky); bmax[1] = max(bmax[1], ky);
+          bmin[2] = min(bmin[2], kz); bmax[2] = max(bmax[2], kz);
+        } else {
+          ++dropped;
+        }
+        in = ok;
+      }
+      const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
+      if constexpr (W) {
+        if (in) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
+      } else {
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
+      }
     }
   }
   // block reduction of the counters and bounding boxes
