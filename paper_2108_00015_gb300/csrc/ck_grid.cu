@@ -83,56 +83,86 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nround = (npts + 31) / 32 * 32;  // warp-uniform trip count
   unsigned long long kept = 0, dropped = 0;
   long long qsum = 0;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
-  // U points per thread per round: their coordinates are loaded before any
-  // is gridded, so that U independent loads per thread are in flight
+  // one point per lane; called by every lane of the warp (in: a real point)
+  auto grid_one = [&](float x, float y, float z, float wt, bool in) {
+    int kx = 0, ky = 0, kz = 0;
+    long long q = 0;
+    if (in) {
+      bool ok = axis_cell(x, 0, A, &kx) && axis_cell(y, 1, A, &ky) && axis_cell(z, 2, A, &kz);
+      if constexpr (W) {
+        ok = ok && isfinite(wt);
+        if (ok) q = llrint((double)wt * 4294967296.0);  // exact product; nearest, ties to even
+      }
+      if (ok) {
+        ++kept;
+        qsum += q;
+        bmin[0] = min(bmin[0], kx); bmax[0] = max(bmax[0], kx);
+        bmin[1] = min(bmin[1], ky); bmax[1] = max(bmax[1], ky);
+        bmin[2] = min(bmin[2], kz); bmax[2] = max(bmax[2], kz);
+      } else {
+        ++dropped;
+      }
+      in = ok;
+    }
+    const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
+    if constexpr (W) {
+      if (in) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
+    } else {
+      const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
+      if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
+    }
+  };
+  // 16-byte aligned arrays: four consecutive points per thread and round,
+  // read with one 16-byte load per coordinate.  Trip counts are
+  // warp-uniform: a warp's indices share one 32-aligned block.
+  int64_t done = 0;
+  const uintptr_t align = reinterpret_cast<uintptr_t>(xs) | reinterpret_cast<uintptr_t>(ys) |
+                          reinterpret_cast<uintptr_t>(zs) | (W ? reinterpret_cast<uintptr_t>(ws) : 0);
+  if ((align & 15) == 0) {
+    const int64_t nq = npts / 4, nqround = (nq + 31) / 32 * 32;
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int64_t qi = first; qi < nqround; qi += stride) {
+      const bool in = qi < nq;
+      const float4 X = in ? __ldg(reinterpret_cast<const float4*>(xs) + qi) : zero4;
+      const float4 Y = in ? __ldg(reinterpret_cast<const float4*>(ys) + qi) : zero4;
+      const float4 Z = in ? __ldg(reinterpret_cast<const float4*>(zs) + qi) : zero4;
+      float4 Wt = zero4;
+      if constexpr (W) Wt = in ? __ldg(reinterpret_cast<const float4*>(ws) + qi) : zero4;
+      grid_one(X.x, Y.x, Z.x, Wt.x, in);
+      grid_one(X.y, Y.y, Z.y, Wt.y, in);
+      grid_one(X.z, Y.z, Z.z, Wt.z, in);
+      grid_one(X.w, Y.w, Z.w, Wt.w, in);
+    }
+    done = 4 * nq;
+  }
+  // the rest (every point when the arrays are not 16-byte aligned): U
+  // points per thread per round, whose coordinates are loaded before any is
+  // gridded, so that U independent loads per thread are in flight
   constexpr int U = 4;
-  for (int64_t base = first; base < nround; base += U * stride) {
+  const int64_t rest = npts - done, rround = (rest + 31) / 32 * 32;
+  const float* xr = xs + done;
+  const float* yr = ys + done;
+  const float* zr = zs + done;
+  const float* wr = W ? ws + done : nullptr;
+  for (int64_t base = first; base < rround; base += U * stride) {
     float px[U], py[U], pz[U], pw[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * stride;
-      const bool in = i < npts;
-      px[u] = in ? __ldg(xs + i) : 0.0f;
-      py[u] = in ? __ldg(ys + i) : 0.0f;
-      pz[u] = in ? __ldg(zs + i) : 0.0f;
-      if constexpr (W) pw[u] = in ? __ldg(ws + i) : 0.0f;
+      const bool in = i < rest;
+      px[u] = in ? __ldg(xr + i) : 0.0f;
+      py[u] = in ? __ldg(yr + i) : 0.0f;
+      pz[u] = in ? __ldg(zr + i) : 0.0f;
+      pw[u] = W && in ? __ldg(wr + i) : 0.0f;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = base + u * stride;
-      if (i >= nround) break;  // warp-uniform: a warp's indices share one 32-aligned block
-      bool in = i < npts;
-      int kx = 0, ky = 0, kz = 0;
-      long long q = 0;
-      if (in) {
-        bool ok = axis_cell(px[u], 0, A, &kx) && axis_cell(py[u], 1, A, &ky) && axis_cell(pz[u], 2, A, &kz);
-        if constexpr (W) {
-          const float w = pw[u];
-          ok = ok && isfinite(w);
-          if (ok) q = llrint((double)w * 4294967296.0);  // exact product; nearest, ties to even
-        }
-        if (ok) {
-          ++kept;
-          qsum += q;
-          bmin[0] = min(bmin[0], kx); bmax[0] = max(bmax[0], kx);
-          bmin[1] = min(bmin[1], ky); bmax[1] = max(bmax[1], ky);
-          bmin[2] = min(bmin[2], kz); bmax[2] = max(bmax[2], kz);
-        } else {
-          ++dropped;
-        }
-        in = ok;
-      }
-      const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
-      if constexpr (W) {
-        if (in) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
-      } else {
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
-        if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
-      }
+      if (i >= rround) break;
+      grid_one(px[u], py[u], pz[u], pw[u], i < rest);
     }
   }
   // block reduction of the counters and bounding boxes

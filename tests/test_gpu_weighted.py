@@ -160,3 +160,35 @@ def test_pinned_host_positions(torch):
             for key in ("xi", "num", "den"):
                 assert np.array_equal(got[key][n].numpy(), want[key][n].numpy()), (w is None, n, key)
     plan.close()
+
+
+@pytest.mark.parametrize("offset", [0, 1, 2, 3])
+def test_gridding_alignment_and_tails(torch, offset):
+    """Coordinate and weight arrays that start 0..3 elements into a device
+    buffer (16-byte aligned or not) and point counts that are not multiples
+    of four: the 16-byte load path, the element path and the tail give
+    counts and weight sums bit-identical to the oracle's."""
+    g = GridSpec((30, 24, 20), (5.0, -3.0, 1.0), 8.0, True)
+    L = np.array(g.n, np.float64) * g.cell
+    n = 20003 + 5 * offset  # never a multiple of four: every path has a tail
+    c = uniform_box(11 + offset, n, tuple(L))
+    cat = Catalog((c.x + 5.0).astype(np.float32), (c.y - 3.0).astype(np.float32), (c.z + 1.0).astype(np.float32))
+    wts = _weights(12 + offset, n, signed=True, bad=True)
+
+    def shifted(a):
+        buf = torch.zeros(n + 3, dtype=torch.float32, device="cuda")
+        buf[offset:offset + n] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        return buf[offset:offset + n]
+
+    x, y, z, w = (shifted(a) for a in (cat.x, cat.y, cat.z, wts))
+    assert (x.data_ptr() % 16 == 0) == (offset == 0)
+    plan = plan_for(dict(grid=g, shells=(16.0,), width=8.0), max_order=2)
+    plan.set_randoms(x, y, z)
+    res = plan.compute(x, y, z, orders=(2,), out="host", w=w)
+    D, R = plan.grids()
+    want, wdrop = O.grid_counts(cat.x, cat.y, cat.z, g)
+    assert np.array_equal(R.cpu().numpy().astype(np.uint32), want)
+    Dw, _, dd = O.grid_weights(cat.x, cat.y, cat.z, wts, g)
+    assert np.array_equal(D.cpu().numpy().view(np.float32), Dw.astype(np.float32))
+    assert res["dropped"].numpy().tolist() == [dd, wdrop]
+    plan.close()
