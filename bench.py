@@ -779,6 +779,13 @@ def run_batch(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
+    tunings = None
+    if not args.no_autotune:
+        # each grid class's launch shapes, timed on its own randoms
+        tunings = []
+        for p, r in zip(plans, rnd):
+            p.set_randoms(*r)
+            tunings.append(p.autotune())
     clocks = Clocks(_smi_index(torch, local))
     clocks.start()
     t_b = timed(step_batched)
@@ -788,6 +795,17 @@ def run_batch(args):
             raise RuntimeError("device status in the batched form")
     t_l = timed(step_loop)
     ncat = len(cats)
+    # the same batch in the plain FP32 form (CUDA-core sums), batched the same way
+    t_p = None
+    if args.precision != "fp32" and not args.no_plain:
+        for p in plans:
+            p.close()
+        plans = [Plan(c["grid"].n, c["grid"].origin, c["grid"].cell, c["grid"].periodic, w["shells"], w["width"],
+                      max_order=max(orders), precision="fp32") for c in w["classes"]]
+        t_p = timed(step_batched)
+        for p in plans:
+            if p.status() != 0:
+                raise RuntimeError("device status in the plain batched form")
     value = t_b / (args.steps * ncat)
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms/catalog", "n_gpus": ws, "steps": args.steps,
@@ -799,8 +817,11 @@ def run_batch(args):
         "config": {"workload": "batch64", "classes": [list(c["grid"].n[:1]) + [c["grid"].cell] for c in w["classes"]],
                    "mocks": ncat, "points": int(sum(m.n for _, m in w["mocks"])), "shells": len(w["shells"]),
                    "orders": list(orders), "precision": args.precision,
-                   "step": "per class ck_set_randoms, then all mocks through ck_batch_compute"},
+                   "step": "per class ck_set_randoms, then all mocks through ck_batch_compute",
+                   "tuning": tunings},
         "forms": {"batched_graphs": {"ms_per_catalog": round(value, 4)},
+                  **({"batched_graphs_plain_fp32": {"ms_per_catalog": round(t_p / (args.steps * ncat), 4)},
+                      "mixed_speedup_over_plain": round(t_p / t_b, 3)} if t_p else {}),
                   "loop_ck_compute": {"ms_per_catalog": round(t_l / (args.steps * ncat), 4)},
                   "batched_speedup_over_loop": round(t_l / t_b, 3)},
         "clocks": clk,

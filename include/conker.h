@@ -351,8 +351,12 @@ ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream)
  * of a (plan, order_mask) pair the plan's compute sequence for one catalog
  * (gridding through the normalised xi) is captured into a CUDA graph, on an
  * internal stream, after any synchronous preparation; every catalog then costs
- * one small descriptor kernel, one graph launch and its output copies, all in
- * order on `stream`.  Positions must be device pointers (CK_ERR_BAD_POINTER
+ * one small descriptor kernel, one graph launch and its output copies.  A
+ * plan's catalogs run in order; with catalogs on several plans, each plan's
+ * run on a stream of the plan's own, forked from `stream` and joined back to
+ * it, so that grid classes overlap (plans share no buffers).  The work is
+ * ordered after earlier work on `stream`, and later work on `stream` after
+ * it.  Positions must be device pointers (CK_ERR_BAD_POINTER
  * otherwise); results are the same as ck_compute's.  Device statuses are read
  * (and the stream synchronised) only if some output is in host memory. */
 typedef struct ck_catalog {

@@ -492,6 +492,9 @@ ck_status ck_plan_destroy(ck_plan* plan) {
   for (auto& g : p->gexec)
     if (g) cudaGraphExecDestroy(g);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->batch_stream) cudaStreamDestroy(p->batch_stream);
+  if (p->batch_fork) cudaEventDestroy(p->batch_fork);
+  if (p->batch_join) cudaEventDestroy(p->batch_join);
   if (p->owns_ws && p->ws) cudaFree(p->ws);
   delete p;
   return cuda_status(e);
@@ -754,19 +757,45 @@ ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_cata
     if (c.n > 0 && (!is_device_ptr(c.x) || !is_device_ptr(c.y) || !is_device_ptr(c.z))) return CK_ERR_BAD_POINTER;
   }
   cudaStream_t st = S(stream);
-  for (int32_t j = 0; j < n_plans; ++j) {
-    bool used = false;
-    for (int32_t i = 0; i < n_cats && !used; ++i) used = cats[i].plan == j;
-    if (used) CK_TRY_S(capture_compute(*reinterpret_cast<Plan*>(plans[j]), order_mask));
-  }
+  std::vector<char> used((size_t)n_plans, 0);
+  int n_used = 0;
+  for (int32_t i = 0; i < n_cats; ++i)
+    if (!used[(size_t)cats[i].plan]) {
+      used[(size_t)cats[i].plan] = 1;
+      ++n_used;
+    }
+  for (int32_t j = 0; j < n_plans; ++j)
+    if (used[(size_t)j]) CK_TRY_S(capture_compute(*reinterpret_cast<Plan*>(plans[j]), order_mask));
+  // Several plans (grid classes): each plan's catalogs in order on the
+  // plan's own stream, so that the classes run concurrently (they share no
+  // buffers), joined back to the caller's stream at the end.
+  const bool fork = n_used > 1;
+  if (fork)
+    for (int32_t j = 0; j < n_plans; ++j) {
+      if (!used[(size_t)j]) continue;
+      Plan& p = *reinterpret_cast<Plan*>(plans[j]);
+      if (!p.batch_stream) CK_TRY(cudaStreamCreateWithFlags(&p.batch_stream, cudaStreamNonBlocking));
+      if (!p.batch_fork) CK_TRY(cudaEventCreateWithFlags(&p.batch_fork, cudaEventDisableTiming));
+      if (!p.batch_join) CK_TRY(cudaEventCreateWithFlags(&p.batch_join, cudaEventDisableTiming));
+      CK_TRY(cudaEventRecord(p.batch_fork, st));
+      CK_TRY(cudaStreamWaitEvent(p.batch_stream, p.batch_fork, 0));
+    }
   bool host_seen = false;
   for (int32_t i = 0; i < n_cats; ++i) {
     Plan& p = *reinterpret_cast<Plan*>(plans[cats[i].plan]);
-    launch_set_catalog_ref(p, cats[i].x, cats[i].y, cats[i].z, cats[i].n, st);
-    CK_TRY(cudaGraphLaunch(p.gexec[order_mask], st));
+    cudaStream_t ps = fork ? p.batch_stream : st;
+    launch_set_catalog_ref(p, cats[i].x, cats[i].y, cats[i].z, cats[i].n, ps);
+    CK_TRY(cudaGraphLaunch(p.gexec[order_mask], ps));
     p.bank_holds = 0;
-    CK_TRY_S(copy_results(p, order_mask, out ? out + i : nullptr, st, &host_seen));
+    CK_TRY_S(copy_results(p, order_mask, out ? out + i : nullptr, ps, &host_seen));
   }
+  if (fork)
+    for (int32_t j = 0; j < n_plans; ++j) {
+      if (!used[(size_t)j]) continue;
+      Plan& p = *reinterpret_cast<Plan*>(plans[j]);
+      CK_TRY(cudaEventRecord(p.batch_join, p.batch_stream));
+      CK_TRY(cudaStreamWaitEvent(st, p.batch_join, 0));
+    }
   CK_TRY(cudaGetLastError());
   if (host_seen) {
     ck_status first = CK_OK;

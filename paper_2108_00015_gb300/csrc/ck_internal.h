@@ -191,6 +191,10 @@ struct Plan {
   // batched form: the catalog descriptor and one instantiated graph per order mask
   CatalogRef* dref = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // ck_batch_compute over several plans: this plan's catalogs run on its own
+  // stream, forked from and joined to the caller's (fork, join events)
+  cudaStream_t batch_stream = nullptr;
+  cudaEvent_t batch_fork = nullptr, batch_join = nullptr;
   cudaGraphExec_t gexec[1 << (CK_MAX_ORDER + 1)] = {nullptr};
 
   bool have_randoms = false;       // den_raw holds every multiset of the plan's orders
