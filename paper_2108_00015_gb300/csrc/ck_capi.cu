@@ -154,7 +154,7 @@ ck_status carve(Plan& p) {
   p.dense = reinterpret_cast<double*>(take((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8));
   p.dense_map = reinterpret_cast<int*>(take((size_t)std::max<int64_t>(p.dense_total, 1) * 4));
   p.table_arena = take(p.table_arena_cap);
-  p.support = reinterpret_cast<int*>(take(12 * 4));
+  p.support = reinterpret_cast<int*>(take(14 * 4));
   p.absmax = reinterpret_cast<unsigned*>(take((size_t)(CK_MAX_SHELLS + 1) * 4));
   const size_t used = (size_t)(b - static_cast<unsigned char*>(p.ws));
   return used <= p.ws_bytes ? CK_OK : CK_ERR_OOM;
@@ -662,6 +662,8 @@ static ck_status fields_impl(ck_plan* plan, const float* a0, const float* b0, co
   CK_TRY_S(on_device(a0, stage0, &da));
   if (b0) CK_TRY_S(on_device(b0, stage1, &db));
   launch_field_load(p, da, db, delta, p.field, 0, st);
+  // the loaded field may be nonzero anywhere: the next preparation rewrites every plane
+  CK_TRY(cudaMemsetAsync(&p.dstate->field_known, 0, sizeof(int), st));
   launch_field_check(p, st);
   p.bank_holds = -1;
   CK_TRY_S(convolve_and_sum(p, order_mask, p.sums, st, w0));

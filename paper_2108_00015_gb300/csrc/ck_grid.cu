@@ -287,10 +287,26 @@ void launch_grid_points(const Plan& p, const float* x, const float* y, const flo
 
 // alpha = kept_D / kept_R (FP64), N = D - alpha R in FP32 (one FMA), plus the
 // plan-level checks (empty catalogs, guard band on a non-periodic grid).
+// The cells [c0, c1) of the planes range[0] .. range[1] (plane cells each;
+// empty when range[0] > range[1]): a 16-byte aligned body of 4-cell groups
+// [4 q0, 4 q1) and the cells before and after it.
+struct CellSpan {
+  int64_t c0, c1, q0, q1;
+};
+__device__ __forceinline__ CellSpan plane_span(const int* range, int64_t plane) {
+  CellSpan s;
+  s.c0 = (int64_t)range[0] * plane;
+  s.c1 = range[0] <= range[1] ? ((int64_t)range[1] + 1) * plane : s.c0;
+  const int64_t a0 = min(s.c1, (s.c0 + 3) / 4 * 4);
+  s.q0 = a0 / 4;
+  s.q1 = max(s.q0, s.c1 / 4);
+  return s;
+}
+
 __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __restrict__ D,
                                                            const uint32_t* __restrict__ R,
-                                                           float* __restrict__ field, int64_t nc,
-                                                           DevState* st, int periodic, int nx, int ny,
+                                                           float* __restrict__ field, const int* __restrict__ range,
+                                                           int64_t plane, DevState* st, int periodic, int nx, int ny,
                                                            int nz, int mx, int my, int mz, double alpha_fixed) {
   const unsigned long long kd = st->kept[0], kr = st->kept[1];
   const bool wd = st->weighted[0] != 0, wr = st->weighted[1] != 0;
@@ -316,38 +332,41 @@ __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __res
       }
     }
   }
-  const int64_t n4 = nc / 4;
+  const CellSpan sp = plane_span(range, plane);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint4* D4 = reinterpret_cast<const uint4*>(D);
   const uint4* R4 = reinterpret_cast<const uint4*>(R);
   float4* F4 = reinterpret_cast<float4*>(field);
   // a cell: a count, or the float32 bits of a weight sum
   auto val = [](uint32_t u, bool weighted) { return weighted ? __uint_as_float(u) : (float)u; };
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+  for (int64_t i = sp.q0 + t0; i < sp.q1; i += stride) {
     const uint4 d = __ldg(D4 + i), r = __ldg(R4 + i);
     F4[i] = make_float4(fmaf(-af, val(r.x, wr), val(d.x, wd)), fmaf(-af, val(r.y, wr), val(d.y, wd)),
                         fmaf(-af, val(r.z, wr), val(d.z, wd)), fmaf(-af, val(r.w, wr), val(d.w, wd)));
   }
-  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
-    field[i] = fmaf(-af, val(R[i], wr), val(D[i], wd));
+  for (int64_t i = sp.c0 + t0; i < 4 * sp.q0; i += stride) field[i] = fmaf(-af, val(R[i], wr), val(D[i], wd));
+  for (int64_t i = 4 * sp.q1 + t0; i < sp.c1; i += stride) field[i] = fmaf(-af, val(R[i], wr), val(D[i], wd));
 }
 
 __global__ void __launch_bounds__(256) prepare_randoms_kernel(const uint32_t* __restrict__ R,
-                                                              float* __restrict__ field, int64_t nc,
+                                                              float* __restrict__ field,
+                                                              const int* __restrict__ range, int64_t plane,
                                                               DevState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0 && st->kept[1] == 0) set_status(&st->status, CK_ERR_EMPTY_CATALOG);
   const bool wr = st->weighted[1] != 0;
   auto val = [](uint32_t u, bool weighted) { return weighted ? __uint_as_float(u) : (float)u; };
-  const int64_t n4 = nc / 4;
+  const CellSpan sp = plane_span(range, plane);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint4* R4 = reinterpret_cast<const uint4*>(R);
   float4* F4 = reinterpret_cast<float4*>(field);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+  for (int64_t i = sp.q0 + t0; i < sp.q1; i += stride) {
     const uint4 r = __ldg(R4 + i);
     F4[i] = make_float4(val(r.x, wr), val(r.y, wr), val(r.z, wr), val(r.w, wr));
   }
-  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride)
-    field[i] = val(R[i], wr);
+  for (int64_t i = sp.c0 + t0; i < 4 * sp.q0; i += stride) field[i] = val(R[i], wr);
+  for (int64_t i = 4 * sp.q1 + t0; i < sp.c1; i += stride) field[i] = val(R[i], wr);
 }
 
 static unsigned elementwise_blocks(const Plan& p, int64_t n) {
@@ -356,10 +375,15 @@ static unsigned elementwise_blocks(const Plan& p, int64_t n) {
   return (unsigned)std::max<int64_t>(b, 1);
 }
 
+// The preparations rewrite the planes support[12] .. support[13] only (the
+// occupied box's, and those where the field may still be nonzero); the
+// field stays exact everywhere.  Bytes: those of the box's planes.
 void launch_prepare_data(const Plan& p, cudaStream_t st) {
-  ProfScope ps(p, ST_PREP, 12.0 * (double)p.nc, st);
+  launch_support_box(p, 0, st);
+  const int64_t plane = (int64_t)p.grid.n[0] * p.grid.n[1];
+  ProfScope ps(p, ST_PREP, 0.0, 0.0, 12.0 * (double)plane, p.support + 6, st);
   prepare_data_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(
-      p.counts[0], p.counts[1], p.field, p.nc, p.dstate, p.grid.periodic ? 1 : 0, p.grid.n[0],
+      p.counts[0], p.counts[1], p.field, p.support + 12, plane, p.dstate, p.grid.periodic ? 1 : 0, p.grid.n[0],
       p.grid.n[1], p.grid.n[2], p.maxoff[0], p.maxoff[1], p.maxoff[2], p.region_alpha);
 }
 
@@ -386,7 +410,7 @@ void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st) {
 // its upper one.  box[6..11]: that box (the forward transform's input);
 // box[0..5]: the same clipped to the region's planes (where W_0 may be
 // nonzero: the pruned inverse passes of the fused path).
-__global__ void support_box_kernel(const DevState* __restrict__ st, int mode, int nx, int ny, int nz, int z_lo,
+__global__ void support_box_kernel(DevState* __restrict__ st, int mode, int nx, int ny, int nz, int z_lo,
                                    int z_hi, int* __restrict__ box) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int n[3] = {nx, ny, nz};
@@ -407,6 +431,25 @@ __global__ void support_box_kernel(const DevState* __restrict__ st, int mode, in
     box[2 * a] = lo;
     box[2 * a + 1] = hi;
   }
+  // the planes the field's preparation rewrites: the box's (the field of
+  // this catalog is zero outside them) and those where the field buffer may
+  // still be nonzero (every plane while that is unknown); afterwards the
+  // field is zero outside the box's planes.  Computed again after the
+  // preparation, with the same box, it leaves the record as it is.
+  const int bz0 = box[10], bz1 = box[11];
+  int r0 = bz0, r1 = bz1;
+  if (!st->field_known) {
+    r0 = 0;
+    r1 = nz - 1;
+  } else if (st->field_z0 <= st->field_z1) {
+    r0 = r0 <= r1 ? min(r0, st->field_z0) : st->field_z0;
+    r1 = bz0 <= bz1 ? max(r1, st->field_z1) : st->field_z1;
+  }
+  box[12] = r0;
+  box[13] = r1;
+  st->field_known = 1;
+  st->field_z0 = bz0;
+  st->field_z1 = bz1;
 }
 
 void launch_support_box(const Plan& p, int mode, cudaStream_t st) {
@@ -416,8 +459,11 @@ void launch_support_box(const Plan& p, int mode, cudaStream_t st) {
 }
 
 void launch_prepare_randoms(const Plan& p, cudaStream_t st) {
-  ProfScope ps(p, ST_PREP, 8.0 * (double)p.nc, st);
-  prepare_randoms_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.counts[1], p.field, p.nc, p.dstate);
+  launch_support_box(p, 1, st);
+  const int64_t plane = (int64_t)p.grid.n[0] * p.grid.n[1];
+  ProfScope ps(p, ST_PREP, 0.0, 0.0, 8.0 * (double)plane, p.support + 6, st);
+  prepare_randoms_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.counts[1], p.field, p.support + 12, plane,
+                                                                      p.dstate);
 }
 
 }  // namespace ck

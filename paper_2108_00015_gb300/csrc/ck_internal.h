@@ -33,6 +33,11 @@ struct DevState {
   int pad;
   double alpha;
   double fsum[2];     // fields computed in place (weighted == 2): the FP64 total of the cells
+  // planes z0..z1 outside which the field buffer is zero (field_known: the
+  // record holds; 0, as at plan creation or after a field was loaded: unknown)
+  int field_known;
+  int field_z0, field_z1;
+  int pad2;
 };
 
 constexpr int kMaxStages = 8;
@@ -255,7 +260,10 @@ void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // cata
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
 // p.support = the box where W_0 may be nonzero: mode 0 data (D and R
-// occupied), 1 randoms; clipped to the region's planes.
+// occupied), 1 randoms; clipped to the region's planes (support[0..5]),
+// unclipped (support[6..11]); support[12..13]: the planes the field's
+// preparation rewrites (the box's and those where the field may be nonzero
+// from before), after which the field is zero outside the box's planes.
 void launch_support_box(const Plan& p, int mode, cudaStream_t st);
 // The factorised randoms field of Eq. 7 (ck_sky.cu): check_factorised
 // validates the arguments; launch_factorised_randoms writes counts[1] (float

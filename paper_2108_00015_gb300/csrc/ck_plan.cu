@@ -233,7 +233,7 @@ size_t workspace_bytes(const Plan& p) {
   b += al((size_t)3 * std::max<int64_t>(p.dense_total, 1) * 8);        // dense staging
   b += al((size_t)std::max<int64_t>(p.dense_total, 1) * 4);            // dense map
   b += al(p.table_arena_cap);
-  b += al(12 * 4);                                                      // support boxes
+  b += al(14 * 4);                                                      // support boxes, preparation planes
   b += al((size_t)(CK_MAX_SHELLS + 1) * 4);                             // split-FP16 row maxima
   return b;
 }

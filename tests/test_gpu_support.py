@@ -61,3 +61,47 @@ def test_fused_support_box(n, lo, hi, shells):
         assert res["status"] == 0
         _check(res, ref, ns)
         plan.close()
+
+
+@pytest.mark.parametrize("precision", ["split_tf32", "fp32"])
+def test_field_exact_across_catalogs(precision):
+    """The preparations rewrite only the planes of the occupied box and of
+    the previous occupied box: on one plan, catalogs confined to different
+    sub-boxes (and a continuous field loaded in between, which may be
+    nonzero anywhere) leave a field buffer that is N (or Rt) on every cell,
+    exactly zero where both histograms are, and sums that match the
+    oracle's."""
+    torch = cuda_torch()
+    n = (30, 40, 36)
+    g = GridSpec(n, (0.0, 0.0, 0.0), 1.0, False)
+    shells = (1.5, 2.5, 3.5)
+    boxes = [((8, 9, 4), (22, 30, 14)), ((6, 8, 20), (24, 31, 31)), ((9, 10, 12), (21, 29, 24))]
+    cats = [_confined(n, lo, hi, 300, 60_000, 7 + i) for i, (lo, hi) in enumerate(boxes)]
+    w = dict(grid=g, shells=shells, width=1.0, data=cats[0][0], randoms=cats[0][1])
+    plan = plan_for(w, max_order=3, precision=precision)
+
+    def check_field(which, D, R):
+        # which = 0: N = D - alpha R; which = 1: R as float (before alpha)
+        f = plan.field(which).cpu().numpy().astype(np.float64)
+        _, N, _ = O.density_fields(D, R)
+        want = N if which == 0 else R.astype(np.float64)
+        empty = (D == 0) & (R == 0) if which == 0 else (R == 0)
+        assert np.all(f[empty] == 0.0)
+        assert np.max(np.abs(f - want)) <= 1e-6 * max(1.0, np.max(np.abs(want)))
+
+    rng = np.random.default_rng(5)
+    for i, (data, rand) in enumerate(cats):
+        if i == 2:  # first a continuous field over more planes than this catalog's box
+            d = np.zeros((n[2], n[1], n[0]), np.float32)
+            d[5:-5, 5:-5, 5:-5] = rng.uniform(0.5, 1.5, (n[2] - 10, n[1] - 10, n[0] - 10))
+            plan.compute_continuous(torch.from_numpy(d).cuda(), None, orders=(2,), out="host")
+        D, _ = O.grid_counts(data.x, data.y, data.z, g)
+        R, _ = O.grid_counts(rand.x, rand.y, rand.z, g)
+        plan.set_randoms(*dev_cat(torch, rand))
+        check_field(1, D, R)
+        res = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
+        assert res["status"] == 0
+        check_field(0, D, R)
+        ref = O.correlate(g, shells, 1.0, data, rand, orders=(2, 3), engine="fft")
+        _check(res, ref, len(shells))
+    plan.close()
