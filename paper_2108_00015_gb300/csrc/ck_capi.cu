@@ -269,8 +269,8 @@ const float* mapped_host(const float* h) {
 
 ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, int64_t n, int which,
                        cudaStream_t st, const float* w = nullptr) {
+  launch_clear_counts(p, which, st);  // before the box it reads is reset
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, which);
-  CK_TRY(cudaMemsetAsync(p.counts[which], 0, (size_t)p.nc * 4, st));
   if (w) CK_TRY(cudaMemsetAsync(p.wacc, 0, (size_t)p.nc * 8, st));
   if (n > 0) {
     const bool dx = is_device_ptr(x), dy = is_device_ptr(y), dz = is_device_ptr(z);
@@ -390,8 +390,9 @@ ck_status capture_compute(Plan& p, int order_mask) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   ck_status s = CK_OK;
   if (e == cudaSuccess) {
+    launch_clear_counts(p, 0, cs);
     reset_state_kernel<<<1, 1, 0, cs>>>(p.dstate, 0);
-    e = cudaMemsetAsync(p.counts[0], 0, (size_t)p.nc * 4, cs);
+    e = cudaGetLastError();
     if (e == cudaSuccess) {
       launch_grid_points_ref(p, 0, cs);
       launch_prepare_data(p, cs);
@@ -553,8 +554,8 @@ ck_status ck_set_randoms_factorised(ck_plan* plan, const ck_cosmology* cosmo, co
   Plan& p = *reinterpret_cast<Plan*>(plan);
   cudaStream_t st = S(stream);
   p.have_randoms = p.have_randoms_diag = false;
+  launch_clear_counts(p, 1, st);
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 1);
-  CK_TRY(cudaMemsetAsync(p.counts[1], 0, (size_t)p.nc * 4, st));
   CK_TRY_S(launch_factorised_randoms(p, cosmo, sel, st));
   launch_prepare_randoms(p, st);
   p.bank_holds = -1;
@@ -645,6 +646,8 @@ static ck_status fields_impl(ck_plan* plan, const float* a0, const float* b0, co
     return CK_OK;
   };
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 0);
+  // the data count buffer serves as staging and as W_0 below
+  CK_TRY(cudaMemsetAsync(&p.dstate->counts_known[0], 0, sizeof(int), st));
   float* stage0 = p.bank;                                     // host a0 / f0 / f1
   float* stage1 = reinterpret_cast<float*>(p.counts[0]);      // host b0
   const bool padded = p.grid.n[0] != p.box_n[0] || p.grid.n[1] != p.box_n[1] || p.grid.n[2] != p.box_n[2];
@@ -702,6 +705,7 @@ ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream)
   const bool dev = is_device_ptr(map);
   const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
   float* dst = dev ? map : reinterpret_cast<float*>(p.counts[0]);  // host: through the data count buffer
+  if (!dev) CK_TRY(cudaMemsetAsync(&p.dstate->counts_known[0], 0, sizeof(int), st));
   launch_product_map(p, p.field, ws, shell, dst, st);
   CK_TRY(cudaGetLastError());
   if (!dev) {

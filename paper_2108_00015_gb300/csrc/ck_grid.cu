@@ -303,6 +303,22 @@ __device__ __forceinline__ CellSpan plane_span(const int* range, int64_t plane) 
   return s;
 }
 
+__global__ void __launch_bounds__(256) clear_counts_kernel(const DevState* __restrict__ st, int which,
+                                                           uint32_t* __restrict__ counts, int64_t plane, int nz) {
+  int range[2] = {0, nz - 1};
+  if (st->counts_known[which]) {
+    range[0] = max(st->bbox_min[which][2], 0);
+    range[1] = min(st->bbox_max[which][2], nz - 1);
+  }
+  const CellSpan sp = plane_span(range, plane);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint4* C4 = reinterpret_cast<uint4*>(counts);
+  for (int64_t i = sp.q0 + t0; i < sp.q1; i += stride) C4[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int64_t i = sp.c0 + t0; i < 4 * sp.q0; i += stride) counts[i] = 0u;
+  for (int64_t i = 4 * sp.q1 + t0; i < sp.c1; i += stride) counts[i] = 0u;
+}
+
 __global__ void __launch_bounds__(256) prepare_data_kernel(const uint32_t* __restrict__ D,
                                                            const uint32_t* __restrict__ R,
                                                            float* __restrict__ field, const int* __restrict__ range,
@@ -456,6 +472,13 @@ void launch_support_box(const Plan& p, int mode, cudaStream_t st) {
   const int z_lo = p.region ? p.region_z0 : 0;
   const int z_hi = p.region ? p.region_z1 - 1 : p.grid.n[2] - 1;
   support_box_kernel<<<1, 32, 0, st>>>(p.dstate, mode, p.grid.n[0], p.grid.n[1], p.grid.n[2], z_lo, z_hi, p.support);
+}
+
+void launch_clear_counts(const Plan& p, int which, cudaStream_t st) {
+  const int64_t plane = (int64_t)p.grid.n[0] * p.grid.n[1];
+  clear_counts_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.dstate, which, p.counts[which], plane,
+                                                                   p.grid.n[2]);
+  cudaMemsetAsync(&p.dstate->counts_known[which], 1, sizeof(int), st);  // nonzero: known
 }
 
 void launch_prepare_randoms(const Plan& p, cudaStream_t st) {

@@ -37,6 +37,10 @@ struct DevState {
   // record holds; 0, as at plan creation or after a field was loaded: unknown)
   int field_known;
   int field_z0, field_z1;
+  // count buffer k is zero outside the planes of bbox[k] (nonzero: the
+  // record holds; 0, as at plan creation or after the buffer served as
+  // staging: unknown)
+  int counts_known[2];
   int pad2;
 };
 
@@ -257,6 +261,10 @@ void launch_grid_points(const Plan& p, const float* x, const float* y, const flo
 void launch_set_catalog_ref(const Plan& p, const float* x, const float* y, const float* z, int64_t n,
                             cudaStream_t st);
 void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // catalog from p.dref
+// Zero count buffer `which` where it may be nonzero (the planes of the last
+// histogram's box, or everywhere if unknown) and record it as known; then
+// reset the field's state (kept, box) for a new histogram.
+void launch_clear_counts(const Plan& p, int which, cudaStream_t st);
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
 // p.support = the box where W_0 may be nonzero: mode 0 data (D and R
