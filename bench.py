@@ -58,7 +58,7 @@ def _args():
                     help="keep the default launch shapes (ck_plan_autotune times the choices after warm-up)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes instead of the autotuner: fwd_cols,zreg_cols,yinv_cols,ctas_per_sm"
-                         "[,stack_cols] (8 or 16 columns per tile of the strided passes, 1..3 contraction CTAs "
+                         "[,stack_cols[,thin_overlap]] (8 or 16 columns per tile of the strided passes, 1..3 contraction CTAs "
                          "per SM, the widest stacked contraction tile)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the higher-order workloads timed beside the headline at N = 1 (stress256: xi_2..xi_5, "

@@ -396,8 +396,9 @@ ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, doub
  * pass and of the multi-shell inverse y pass (the latter two together), and
  * for the split tensor-core forms that keep a bank the widest tile stacked
  * (0, 32 or 64 columns: B's hi and lo side by side in one MMA, two MMAs per
- * k-step instead of three, which also adds the lo*lo term) and 1, 2 or 3
- * contraction CTAs per SM -- each candidate once untimed and three times
+ * k-step instead of three, which also adds the lo*lo term), 1, 2 or 3
+ * contraction CTAs per SM, and whether the thin tiles run on a second
+ * stream beside the tensor-core kernel -- each candidate once untimed and three times
  * between CUDA events, and keeps the fastest in the plan.  The choices
  * change launch shapes only: transforms are bit-identical, and the
  * contraction's sums differ by the order of their partial sums (and, for a
@@ -412,13 +413,15 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream);
 /* The plan's current choices: out[0] columns per tile of the single-field
  * strided passes, out[1] of the K^ z pass, out[2] of the multi-shell inverse
  * y pass, out[3] contraction CTAs per SM, out[4] the widest stacked
- * contraction tile (columns; 0: none), out[5] 1 once ck_plan_autotune has
- * run (else the defaults: 8, 8, 8, 2, 32). */
+ * contraction tile (columns; 0: none), out[5] 1 when thin tiles overlap
+ * the tensor-core kernel, out[6] 1 once ck_plan_autotune has run (else the
+ * defaults: 8, 8, 8, 2, 32, 1). */
 ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out);
 
-/* Set the choices by hand (in[0..4] as ck_plan_get_tuning's out[0..4]:
- * 8 or 16 columns, 1..3 CTAs per SM, 0..128 stacked columns; CK_ERR_ARG
- * otherwise).  Host only; drops captured graphs and contraction plans. */
+/* Set the choices by hand (in[0..5] as ck_plan_get_tuning's out[0..5]:
+ * 8 or 16 columns, 1..3 CTAs per SM, 0..128 stacked columns, 0 or 1;
+ * CK_ERR_ARG otherwise).  Host only; drops captured graphs and contraction
+ * plans. */
 ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in);
 
 /* Synchronise `stream` and return (and clear) the plan's device status. */

@@ -496,6 +496,9 @@ ck_status ck_plan_destroy(ck_plan* plan) {
   if (p->batch_stream) cudaStreamDestroy(p->batch_stream);
   if (p->batch_fork) cudaEventDestroy(p->batch_fork);
   if (p->batch_join) cudaEventDestroy(p->batch_join);
+  if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+  if (p->aux_fork) cudaEventDestroy(p->aux_fork);
+  if (p->aux_join) cudaEventDestroy(p->aux_join);
   if (p->owns_ws && p->ws) cudaFree(p->ws);
   delete p;
   return cuda_status(e);
@@ -886,6 +889,7 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
     };
     pick_best(&p.tune.tc_stack_cols, {0, 32, 64});
     if (s == CK_OK) pick_best(&p.tune.tc_ctas_per_sm, {1, 2, 3});
+    if (s == CK_OK) pick_best(&p.tune.tc_thin_overlap, {0, 1});
     for (bool& r : p.cplan_ready) r = false;
   }
   if (e0) cudaEventDestroy(e0);
@@ -910,13 +914,14 @@ ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in) {
   if (!plan || !in) return CK_ERR_BAD_POINTER;
   for (int i = 0; i < 3; ++i)
     if (in[i] != 8 && in[i] != 16) return CK_ERR_ARG;
-  if (in[3] < 1 || in[3] > 3 || in[4] < 0 || in[4] > 128) return CK_ERR_ARG;
+  if (in[3] < 1 || in[3] > 3 || in[4] < 0 || in[4] > 128 || (in[5] != 0 && in[5] != 1)) return CK_ERR_ARG;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   p.tune.fwd_cols = in[0];
   p.tune.zreg_cols = in[1];
   p.tune.yinv_cols = in[2];
   p.tune.tc_ctas_per_sm = in[3];
   p.tune.tc_stack_cols = in[4];
+  p.tune.tc_thin_overlap = in[5];
   for (bool& r : p.cplan_ready) r = false;
   for (auto& g : p.gexec)
     if (g) {
@@ -934,7 +939,8 @@ ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out) {
   out[2] = p.tune.yinv_cols;
   out[3] = p.tune.tc_ctas_per_sm;
   out[4] = p.tune.tc_stack_cols;
-  out[5] = p.tune.tuned ? 1 : 0;
+  out[5] = p.tune.tc_thin_overlap;
+  out[6] = p.tune.tuned ? 1 : 0;
   return CK_OK;
 }
 

@@ -615,17 +615,42 @@ ck_status launch_contract(Plan& p, int mask, const float* w0, const float* bank,
   }
   if (c.n_tiles == 0) return CK_OK;
   if (c.use_tc) {
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    const int nthin = c.n_tiles - c.um_ntc;
+    // thin tiles beside the tensor-core kernel: on a second stream (forked
+    // from and joined to st), with the tensor-core CTAs made large enough
+    // that one per SM leaves room for a thin CTA
+    const bool overlap = p.tune.tc_thin_overlap && nthin > 0 && c.um_ntc > 0;
+    if (overlap) {
+      if (!p.aux_stream) e = cudaStreamCreateWithFlags(&p.aux_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess && !p.aux_fork) e = cudaEventCreateWithFlags(&p.aux_fork, cudaEventDisableTiming);
+      if (e == cudaSuccess && !p.aux_join) e = cudaEventCreateWithFlags(&p.aux_join, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
     {
       ProfScope ps(p, ST_CONTRACT, box ? 0.0 : 4.0 * (double)(p.ns + 1) * (double)p.nc * c.n_tiles, 0.0,
                    4.0 * (p.ns + 1) * (double)plane * c.n_tiles, box, st);
-      e = launch_umma(c.um_tn, c.um_kind, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc,
-                      c.d_um_tiles, c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, box, plane, p.absmax, p.partials,
-                      status, st);
+      cudaStream_t ts = st;
+      size_t min_smem = 0;
+      if (overlap) {
+        e = cudaEventRecord(p.aux_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p.aux_stream, p.aux_fork, 0);
+        ts = p.aux_stream;
+        min_smem = (size_t)227 * 1024 - umma_thin_smem(p.ns, c.um_thin_rmax) - 2 * 1024;
+      }
       if (e == cudaSuccess)
-        e = launch_umma_thin(w0, bank, bstride, p.nc, p.ns, c.um_thin_rmax, c.d_rowdesc, c.rows, c.d_coldesc, c.d_um_tiles,
-                             c.d_um_cols, c.um_ntc, c.n_tiles - c.um_ntc, c.n_tiles, c.um_tn, c.splits, box, plane,
-                             p.partials, st);
+        e = launch_umma_thin(w0, bank, bstride, p.nc, p.ns, c.um_thin_rmax, c.d_rowdesc, c.rows, c.d_coldesc,
+                             c.d_um_tiles, c.d_um_cols, c.um_ntc, nthin, c.n_tiles, c.um_tn, c.splits, box, plane,
+                             p.partials, ts);
+      if (e == cudaSuccess)
+        e = launch_umma(c.um_tn, c.um_kind, w0, bank, bstride, p.nc, p.ns, c.d_rowdesc, c.rows, c.d_coldesc,
+                        c.d_um_tiles, c.d_um_cols, c.um_ntc, c.n_tiles, c.splits, box, plane, p.absmax, p.partials,
+                        status, st, min_smem);
+      if (overlap) {
+        const cudaError_t e2 = cudaEventRecord(p.aux_join, p.aux_stream);
+        const cudaError_t e3 = e2 == cudaSuccess ? cudaStreamWaitEvent(st, p.aux_join, 0) : e2;
+        if (e == cudaSuccess) e = e3;
+      }
     }
     if (e != cudaSuccess) return cuda_status(e);
     ProfScope ps2(p, ST_REDUCE, 8.0 * (double)c.partial_doubles, st);

@@ -132,6 +132,7 @@ struct Tuning {
   int yinv_cols = 8;       // of the multi-shell inverse y pass
   int tc_ctas_per_sm = 2;  // tensor-core contraction: CTAs per SM the splits aim at
   int tc_stack_cols = 32;  // tensor-core tiles of at most this many columns are stacked (0: none)
+  int tc_thin_overlap = 1; // 1: thin tiles on a second stream beside the tensor-core kernel
   bool tuned = false;
 };
 
@@ -204,6 +205,9 @@ struct Plan {
   // stream, forked from and joined to the caller's (fork, join events)
   cudaStream_t batch_stream = nullptr;
   cudaEvent_t batch_fork = nullptr, batch_join = nullptr;
+  // the contraction's thin tiles beside its tensor-core kernel (tc_thin_overlap)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   cudaGraphExec_t gexec[1 << (CK_MAX_ORDER + 1)] = {nullptr};
 
   bool have_randoms = false;       // den_raw holds every multiset of the plan's orders
@@ -324,10 +328,12 @@ int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count, int ctas_per_
 // words for the FP16 scales, filled here).
 // box (device, may be null): only the planes z0..z1 of the support box are
 // summed (plane cells each); splits share them out in whole 256-cell groups.
+// min_smem: dynamic shared memory to request at least (0: what the tile
+// shape needs); a larger request keeps one CTA per SM, leaving room beside it.
 cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
                         int ntc, int ntiles, int splits, const int* box, int64_t plane, unsigned* absmax,
-                        double* partials, int* status, cudaStream_t st);
+                        double* partials, int* status, cudaStream_t st, size_t min_smem = 0);
 // Thin tiles (at most kThinMaxOut outputs, kThinMaxCols columns) t0 .. t0 + nthin - 1 on the CUDA
 // cores in FP32, into the same partials layout (tile width tn).
 constexpr int kThinMaxOut = 256;

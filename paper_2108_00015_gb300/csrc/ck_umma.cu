@@ -648,11 +648,12 @@ template <int TN, int KIND>
 cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns, const int2* rowdesc,
                           int rows, const int2* coldesc, const int4* tiles, const int* collist, int ntc, int ntiles,
                           int splits, const int* box, int64_t plane, const unsigned* absmax, double* partials,
-                          int* status, cudaStream_t st) {
+                          int* status, cudaStream_t st, size_t min_smem) {
   if (ntc == 0) return cudaSuccess;
   const int wcells = umma_wcells<TN, KIND>(ns, (size_t)227 * 1024);
   if (wcells == 0) return cudaErrorInvalidValue;
-  const size_t sm = umma_smem<TN, KIND>(ns, wcells);
+  // the kernel uses umma_smem bytes; a larger request only limits residency
+  const size_t sm = std::min<size_t>(std::max(umma_smem<TN, KIND>(ns, wcells), min_smem), (size_t)227 * 1024);
   cudaError_t e =
       cudaFuncSetAttribute(contract_umma_kernel<TN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -703,7 +704,7 @@ int64_t umma_cells_per_split(int64_t nc, int ntiles, int sm_count, int ctas_per_
 cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, int64_t bstride, int64_t nc, int ns,
                         const int2* rowdesc, int rows, const int2* coldesc, const int4* tiles, const int* collist,
                         int ntc, int ntiles, int splits, const int* box, int64_t plane, unsigned* absmax,
-                        double* partials, int* status, cudaStream_t st) {
+                        double* partials, int* status, cudaStream_t st, size_t min_smem) {
   if (ntc == 0) return cudaSuccess;
   if (kind == UM_FP16) {
     cudaError_t e = cudaMemsetAsync(absmax, 0, (size_t)(ns + 1) * sizeof(unsigned), st);
@@ -715,7 +716,7 @@ cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, in
 #define CK_UMMA_CASE(W, K)                                                                                           \
   case W:                                                                                                            \
     return launch_umma_t<W, K>(w0, bank, bstride, nc, ns, rowdesc, rows, coldesc, tiles, collist, ntc, ntiles, splits, \
-                               box, plane, absmax, partials, status, st);
+                               box, plane, absmax, partials, status, st, min_smem);
 #define CK_UMMA_KIND(K)        \
   switch (tn) {                \
     CK_UMMA_CASE(32, K)        \

@@ -181,7 +181,7 @@ def test_undersized_workspace(lib):
 def test_tuning_entry_points_validate(lib):
     """ck_plan_autotune, ck_plan_set_tuning and ck_plan_get_tuning reject a
     null plan or array (CK_ERR_BAD_POINTER) before any CUDA call."""
-    arr = (ctypes.c_int32 * 6)(8, 8, 16, 2, 32, 0)
+    arr = (ctypes.c_int32 * 7)(8, 8, 16, 2, 32, 0, 0)
     for name in ("ck_plan_autotune", "ck_plan_set_tuning", "ck_plan_get_tuning"):
         fn = getattr(lib, name)
         fn.restype = ctypes.c_int
@@ -190,7 +190,7 @@ def test_tuning_entry_points_validate(lib):
     fn = lib.ck_plan_set_tuning
     fake = ctypes.c_void_p(1 << 20)  # never dereferenced: a null array is refused first
     assert fn(fake, None) == 2
-    for bad in ((7, 8, 16, 2, 32), (8, 32, 16, 2, 32), (8, 8, 16, 0, 32), (8, 8, 16, 4, 32), (8, 8, 8, 2, -1),
-                (8, 8, 8, 2, 129)):
+    for bad in ((7, 8, 16, 2, 32, 0), (8, 32, 16, 2, 32, 0), (8, 8, 16, 0, 32, 0), (8, 8, 16, 4, 32, 0),
+                (8, 8, 8, 2, -1, 0), (8, 8, 8, 2, 129, 0), (8, 8, 8, 2, 32, 2)):
         # out-of-range choices are refused (CK_ERR_ARG) before the plan is read
-        assert fn(fake, ctypes.cast((ctypes.c_int32 * 5)(*bad), ctypes.c_void_p)) == 1, bad
+        assert fn(fake, ctypes.cast((ctypes.c_int32 * 6)(*bad), ctypes.c_void_p)) == 1, bad

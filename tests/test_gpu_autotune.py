@@ -84,8 +84,9 @@ def test_contraction_tile_choices(precision, ns, orders):
     want = {n: O.product_sums(w0.astype(np.float64), [b.astype(np.float64) for b in bank], n) for n in orders}
     for stack in (0, 32, 64):
         for k in (1, 2, 3):
-            plan.set_tuning(8, 8, 8, k, stack)
-            sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=orders)
-            for n in orders:
-                assert normwise(sums[n].cpu().numpy(), *want[n]) <= tol, (stack, k, n)
+            for overlap in (0, 1):
+                plan.set_tuning(8, 8, 8, k, stack, overlap)
+                sums = plan.contract(dev(torch, w0), dev(torch, B), stride, orders=orders)
+                for n in orders:
+                    assert normwise(sums[n].cpu().numpy(), *want[n]) <= tol, (stack, k, overlap, n)
     plan.close()
