@@ -74,3 +74,28 @@ def test_batch_errors(torch):
     with pytest.raises(CkError):  # plan index out of range
         batch_compute([p], [(*dev_cat(torch, m), 1)])
     p.close()
+
+
+def test_batch_with_thin_tiles_beside_tensor_cores(torch):
+    """16 shells, orders 2..4: one tensor-core tile and a thin tile, the thin
+    tile on the plan's second stream inside the captured graph; the batched
+    results equal ck_compute's bit for bit with the overlap on and off."""
+    shells = tuple(20.0 + 5.0 * i for i in range(16))
+    classes = [dict(c, shells=shells, width=5.0) for c in (_class(32, 10.0, 17), _class(40, 8.0, 18))]
+    mocks = _mocks(classes)
+    for overlap in (1, 0):
+        plans = []
+        for c in classes:
+            p = plan_for(c, max_order=4, precision="split_tf32")
+            p.set_tuning(8, 8, 8, 2, 32, overlap)
+            p.set_randoms(*dev_cat(torch, c["randoms"]))
+            plans.append(p)
+        cats = [(*dev_cat(torch, m), j) for j, m in mocks]
+        res = batch_compute(plans, cats, orders=(2, 3, 4), out="host")
+        for (j, m), r in zip(mocks, res):
+            single = plans[j].compute(*dev_cat(torch, m), orders=(2, 3, 4), out="host")
+            for n in (2, 3, 4):
+                for key in ("xi", "num", "den"):
+                    assert np.array_equal(r[key][n].numpy(), single[key][n].numpy()), (overlap, j, n, key)
+        for p in plans:
+            p.close()
