@@ -398,8 +398,8 @@ ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, doub
  * (0, 32 or 64 columns: B's hi and lo side by side in one MMA, two MMAs per
  * k-step instead of three, which also adds the lo*lo term), 1, 2 or 3
  * contraction CTAs per SM, and whether the thin tiles run on a second
- * stream beside the tensor-core kernel -- each candidate once untimed and three times
- * between CUDA events, and keeps the fastest in the plan.  The choices
+ * stream beside the tensor-core kernel -- each candidate once untimed and
+ * five times between CUDA events, and keeps the one with the fastest run.  The choices
  * change launch shapes only: transforms are bit-identical, and the
  * contraction's sums differ by the order of their partial sums (and, for a
  * stacked tile, by its lo*lo term, below 2^-21 relative).  Needs a resident

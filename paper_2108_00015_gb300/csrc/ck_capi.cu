@@ -817,8 +817,9 @@ ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_cata
   return CK_OK;
 }
 
-// Autotuning: each candidate of a choice runs once to warm up and three
-// times between events on the plan's own buffers; the fastest is kept.
+// Autotuning: each candidate of a choice runs once to warm up and five
+// times between events on the plan's own buffers; the candidate with the
+// fastest run is kept.
 ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
   if (!plan) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
@@ -829,16 +830,26 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ck_status s = cuda_status(cudaEventCreate(&e0));
   if (s == CK_OK) s = cuda_status(cudaEventCreate(&e1));
+  // once untimed, then the fastest of five timed runs (robust to other work on the GPU)
   auto timed = [&](auto&& fn, float* ms) -> ck_status {
     fn();
-    CK_TRY(cudaEventRecord(e0, st));
-    for (int r = 0; r < 3; ++r) fn();
-    CK_TRY(cudaEventRecord(e1, st));
-    CK_TRY(cudaEventSynchronize(e1));
-    CK_TRY(cudaEventElapsedTime(ms, e0, e1));
+    *ms = 1e30f;
+    for (int r = 0; r < 5; ++r) {
+      CK_TRY(cudaEventRecord(e0, st));
+      fn();
+      CK_TRY(cudaEventRecord(e1, st));
+      CK_TRY(cudaEventSynchronize(e1));
+      float t = 0.0f;
+      CK_TRY(cudaEventElapsedTime(&t, e0, e1));
+      *ms = std::min(*ms, t);
+    }
     return cuda_status(cudaGetLastError());
   };
   const int ny = p.grid.n[1], nz = p.grid.n[2];
+  // a catalog's field (after ck_set_randoms or a compute): the passes visit
+  // its support box, as in the step itself (the pruned forward transform
+  // gives the same spectrum); a loaded field: every plane and row
+  const int* box = (p.bank_holds == 0 || p.bank_holds == 1) ? p.support : nullptr;
   // the single-field strided passes (the forward transform of the resident field)
   if (s == CK_OK && (ny == 512 || nz == 512)) {
     float best = 1e30f;
@@ -846,7 +857,8 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
     for (int c : {8, 16}) {
       p.tune.fwd_cols = c;
       float ms = 0.0f;
-      if ((s = timed([&] { launch_fft_forward(p, p.field, p.spec, st); }, &ms)) != CK_OK) break;
+      if ((s = timed([&] { launch_fft_forward(p, p.field, p.spec, st, box ? box + 6 : nullptr); }, &ms)) != CK_OK)
+        break;
       if (ms < best) { best = ms; pick = c; }
     }
     p.tune.fwd_cols = pick;
@@ -861,7 +873,7 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
         p.tune.zreg_cols = cz;
         p.tune.yinv_cols = cy;
         float ms = 0.0f;
-        if ((s = timed([&] { launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st); }, &ms)) != CK_OK) break;
+        if ((s = timed([&] { launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st, box); }, &ms)) != CK_OK) break;
         if (ms < best) { best = ms; pz = cz; py = cy; }
       }
     p.tune.zreg_cols = pz;
