@@ -68,9 +68,9 @@ def test_field_exact_across_catalogs(precision):
     """The preparations rewrite only the planes of the occupied box and of
     the previous occupied box: on one plan, catalogs confined to different
     sub-boxes (and a continuous field loaded in between, which may be
-    nonzero anywhere) leave a field buffer that is N (or Rt) on every cell,
-    exactly zero where both histograms are, and sums that match the
-    oracle's."""
+    nonzero anywhere) leave a field buffer that is N (or R) on every cell,
+    exactly zero where both histograms are, count buffers equal to the
+    oracle's histograms, and sums that match the oracle's."""
     torch = cuda_torch()
     n = (30, 40, 36)
     g = GridSpec(n, (0.0, 0.0, 0.0), 1.0, False)
@@ -102,6 +102,11 @@ def test_field_exact_across_catalogs(precision):
         res = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
         assert res["status"] == 0
         check_field(0, D, R)
+        # the count buffers, cleared only where the previous histograms were
+        # (everywhere after the continuous field used the data buffer)
+        gd, gr = plan.grids()
+        assert np.array_equal(gd.cpu().numpy().astype(np.uint32), D)
+        assert np.array_equal(gr.cpu().numpy().astype(np.uint32), R)
         ref = O.correlate(g, shells, 1.0, data, rand, orders=(2, 3), engine="fft")
         _check(res, ref, len(shells))
     plan.close()
