@@ -269,7 +269,7 @@ const float* mapped_host(const float* h) {
 
 ck_status grid_catalog(Plan& p, const float* x, const float* y, const float* z, int64_t n, int which,
                        cudaStream_t st, const float* w = nullptr) {
-  launch_clear_counts(p, which, st);  // before the box it reads is reset
+  CK_TRY(launch_clear_counts(p, which, st));  // before the box it reads is reset
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, which);
   if (w) CK_TRY(cudaMemsetAsync(p.wacc, 0, (size_t)p.nc * 8, st));
   if (n > 0) {
@@ -390,9 +390,9 @@ ck_status capture_compute(Plan& p, int order_mask) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   ck_status s = CK_OK;
   if (e == cudaSuccess) {
-    launch_clear_counts(p, 0, cs);
+    e = launch_clear_counts(p, 0, cs);
     reset_state_kernel<<<1, 1, 0, cs>>>(p.dstate, 0);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) {
       launch_grid_points_ref(p, 0, cs);
       launch_prepare_data(p, cs);
@@ -557,7 +557,7 @@ ck_status ck_set_randoms_factorised(ck_plan* plan, const ck_cosmology* cosmo, co
   Plan& p = *reinterpret_cast<Plan*>(plan);
   cudaStream_t st = S(stream);
   p.have_randoms = p.have_randoms_diag = false;
-  launch_clear_counts(p, 1, st);
+  CK_TRY(launch_clear_counts(p, 1, st));
   reset_state_kernel<<<1, 1, 0, st>>>(p.dstate, 1);
   CK_TRY_S(launch_factorised_randoms(p, cosmo, sel, st));
   launch_prepare_randoms(p, st);
@@ -790,21 +790,26 @@ ck_status ck_batch_compute(ck_plan* const* plans, int32_t n_plans, const ck_cata
       CK_TRY(cudaStreamWaitEvent(p.batch_stream, p.batch_fork, 0));
     }
   bool host_seen = false;
-  for (int32_t i = 0; i < n_cats; ++i) {
+  ck_status s = CK_OK;
+  for (int32_t i = 0; i < n_cats && s == CK_OK; ++i) {
     Plan& p = *reinterpret_cast<Plan*>(plans[cats[i].plan]);
     cudaStream_t ps = fork ? p.batch_stream : st;
     launch_set_catalog_ref(p, cats[i].x, cats[i].y, cats[i].z, cats[i].n, ps);
-    CK_TRY(cudaGraphLaunch(p.gexec[order_mask], ps));
+    s = cuda_status(cudaGraphLaunch(p.gexec[order_mask], ps));
     p.bank_holds = 0;
-    CK_TRY_S(copy_results(p, order_mask, out ? out + i : nullptr, ps, &host_seen));
+    if (s == CK_OK) s = copy_results(p, order_mask, out ? out + i : nullptr, ps, &host_seen);
   }
+  // the plan streams join the caller's stream even after an error, so that
+  // later work on it is ordered after everything launched here
   if (fork)
     for (int32_t j = 0; j < n_plans; ++j) {
       if (!used[(size_t)j]) continue;
       Plan& p = *reinterpret_cast<Plan*>(plans[j]);
-      CK_TRY(cudaEventRecord(p.batch_join, p.batch_stream));
-      CK_TRY(cudaStreamWaitEvent(st, p.batch_join, 0));
+      const ck_status r = cuda_status(cudaEventRecord(p.batch_join, p.batch_stream));
+      const ck_status w = r == CK_OK ? cuda_status(cudaStreamWaitEvent(st, p.batch_join, 0)) : r;
+      if (s == CK_OK) s = w;
     }
+  CK_TRY_S(s);
   CK_TRY(cudaGetLastError());
   if (host_seen) {
     ck_status first = CK_OK;

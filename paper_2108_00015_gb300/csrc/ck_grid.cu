@@ -474,11 +474,13 @@ void launch_support_box(const Plan& p, int mode, cudaStream_t st) {
   support_box_kernel<<<1, 32, 0, st>>>(p.dstate, mode, p.grid.n[0], p.grid.n[1], p.grid.n[2], z_lo, z_hi, p.support);
 }
 
-void launch_clear_counts(const Plan& p, int which, cudaStream_t st) {
+cudaError_t launch_clear_counts(const Plan& p, int which, cudaStream_t st) {
   const int64_t plane = (int64_t)p.grid.n[0] * p.grid.n[1];
   clear_counts_kernel<<<elementwise_blocks(p, p.nc), 256, 0, st>>>(p.dstate, which, p.counts[which], plane,
                                                                    p.grid.n[2]);
-  cudaMemsetAsync(&p.dstate->counts_known[which], 1, sizeof(int), st);  // nonzero: known
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(&p.dstate->counts_known[which], 1, sizeof(int), st);  // nonzero: known
 }
 
 void launch_prepare_randoms(const Plan& p, cudaStream_t st) {

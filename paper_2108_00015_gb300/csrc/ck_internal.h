@@ -268,7 +268,7 @@ void launch_grid_points_ref(const Plan& p, int which, cudaStream_t st);  // cata
 // Zero count buffer `which` where it may be nonzero (the planes of the last
 // histogram's box, or everywhere if unknown) and record it as known; then
 // reset the field's state (kept, box) for a new histogram.
-void launch_clear_counts(const Plan& p, int which, cudaStream_t st);
+cudaError_t launch_clear_counts(const Plan& p, int which, cudaStream_t st);
 void launch_prepare_data(const Plan& p, cudaStream_t st);     // alpha, N -> field, checks
 void launch_prepare_randoms(const Plan& p, cudaStream_t st);  // R (float) -> field
 // p.support = the box where W_0 may be nonzero: mode 0 data (D and R
