@@ -333,7 +333,9 @@ ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, con
                              st));
   }
   if (p.fused) return launch_convolve_contract(p, w0, sums, st, support >= 0 ? p.support : nullptr);
-  launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
+  // the bank on the planes the sums visit (W_0 vanishes outside them);
+  // ck_get_bank and ck_product_map recompute whole fields
+  launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st, support >= 0 ? p.support : nullptr);
   return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st, support >= 0 ? p.support : nullptr);
 }
 
@@ -700,11 +702,10 @@ ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream)
   if (!p.have_randoms_diag) return CK_ERR_NO_RANDOMS;
   if (p.bank_holds != 0) return CK_ERR_ARG;  // needs a catalog's ck_compute just before
   cudaStream_t st = S(stream);
-  const float* ws = p.bank + (size_t)shell * p.field_stride;
-  if (p.fused) {  // recompute W_s from the resident spectrum
-    launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, p.bank, p.field_stride, st);
-    ws = p.bank;
-  }
+  // recompute W_s from the resident spectrum: fused plans keep no bank, and
+  // a catalog's bank holds only the planes its sums visited
+  float* ws = p.fused ? p.bank : p.bank + (size_t)shell * p.field_stride;
+  launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, ws, p.field_stride, st);
   const bool dev = is_device_ptr(map);
   const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
   float* dst = dev ? map : reinterpret_cast<float*>(p.counts[0]);  // host: through the data count buffer
@@ -897,7 +898,8 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
         *knob = k;
         for (bool& r : p.cplan_ready) r = false;
         float ms = 0.0f;
-        const ck_status c = timed([&] { launch_contract(p, mask, p.field, p.bank, p.field_stride, p.sums, st); }, &ms);
+        const ck_status c =
+            timed([&] { launch_contract(p, mask, p.field, p.bank, p.field_stride, p.sums, st, box); }, &ms);
         if (c == CK_ERR_OOM) continue;  // more splits than the partials hold
         if ((s = c) != CK_OK) break;
         if (ms < best) { best = ms; pick = k; }
@@ -1058,12 +1060,11 @@ ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream) {
   if (shell < 0 || shell >= p.ns || p.bank_holds < 0) return CK_ERR_ARG;
   cudaStream_t st = S(stream);
   bool host = false;
-  const float* src = p.bank + (size_t)shell * p.field_stride;
-  if (p.fused) {  // recompute W_s from the resident spectrum
-    launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, p.bank, p.field_stride, st);
-    CK_TRY(cudaGetLastError());
-    src = p.bank;
-  }
+  // recompute W_s from the resident spectrum: fused plans keep no bank, and
+  // a catalog's bank holds only the planes its sums visited
+  float* src = p.fused ? p.bank : p.bank + (size_t)shell * p.field_stride;
+  launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, src, p.field_stride, st);
+  CK_TRY(cudaGetLastError());
   CK_TRY_S(copy_out(out, src, (size_t)p.nc * 4, st, &host));
   if (host) CK_TRY(cudaStreamSynchronize(st));
   return CK_OK;

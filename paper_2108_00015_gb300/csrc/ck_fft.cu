@@ -71,27 +71,33 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
                        p.tune.zreg_cols);
   }
   {
-    // read: the box's planes, written: their box rows
-    ProfScope ps(p, ST_FFT_Y_INV, ybox ? 0.0 : nshells * 16.0 * H, nshells * row, nshells * row * ny, ybox, st);
+    // read: the box's planes; written: their box rows (fused plans, whose
+    // x pass visits the box's rows) or every row of them (the bank's planes
+    // are summed whole)
+    const bool rows_only = p.fused;
+    ProfScope ps(p, ST_FFT_Y_INV, ybox ? 0.0 : nshells * 16.0 * H, rows_only ? nshells * row : 0.0,
+                 (rows_only ? 1.0 : 2.0) * nshells * row * ny, ybox, st);
     StridedView v{p.px, (int64_t)ny * p.px, p.px, (int64_t)nz * nshells};
     fft::launch_strided(ny, true, tmp, tmp, v, p.fy, p.stw[1], p.tw[1], nshells > 1 ? p.tune.yinv_cols : p.tune.fwd_cols,
                         p.sm_count, st, ybox, nz,
-                        fft::kPrunePlanes | fft::kPruneOutY);
+                        fft::kPrunePlanes | (rows_only ? fft::kPruneOutY : 0));
   }
 }
 
 // The whole inverse: the z and y passes, then the x pass from tmp[s] into
 // real fields out + s * out_stride.
 void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp, float* out,
-                        int64_t out_stride, cudaStream_t st) {
+                        int64_t out_stride, cudaStream_t st, const int* box) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const double H = (double)nz * ny * (nx / 2 + 1);
-  launch_inverse_zy(p, spec, khat, nshells, tmp, st);
+  launch_inverse_zy(p, spec, khat, nshells, tmp, st, box);
   {
     const int64_t rows = (int64_t)ny * nz * nshells;
-    ProfScope ps(p, ST_FFT_X_C2R, nshells * (4.0 * (double)p.nc + 8.0 * H), st);
+    // every row, or the rows of the box's planes
+    ProfScope ps(p, ST_FFT_X_C2R, box ? 0.0 : nshells * (4.0 * (double)p.nc + 8.0 * H), 0.0,
+                 nshells * (double)ny * (4.0 * nx + 8.0 * (nx / 2 + 1)), box, st);
     fft::launch_x_c2r(nx / 2, tmp, out, nx, p.px, rows, (int64_t)ny * nz, out_stride, p.fx_half, p.stw[0],
-                      p.tw[0], p.sm_count, st);
+                      p.tw[0], p.sm_count, st, box, ny);
   }
 }
 

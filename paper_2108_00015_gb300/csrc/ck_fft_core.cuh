@@ -698,7 +698,7 @@ template <int MC>
 __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     x_c2r_kernel(const float2* __restrict__ in, float* __restrict__ out, int nx, int px, int64_t rows,
                  int64_t rows_per_shell, int64_t out_shell_stride, FftLen f, const float2* __restrict__ stw,
-                 const float2* __restrict__ tw) {
+                 const float2* __restrict__ tw, const int* __restrict__ box, int ny) {
   extern __shared__ float4 smem4[];
   const int M = MC > 0 ? MC : nx / 2;
   const int NX = 2 * M;
@@ -712,7 +712,20 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   float2* twn = tws + ntw;
   for (int i = threadIdx.x; i < ntw; i += kThreads) tws[i] = __ldg(stw + i);
   for (int i = threadIdx.x; i <= M; i += kThreads) twn[i] = __ldg(tw + i);
-  const int64_t ntiles = (rows + kT - 1) / kT;
+  // visited rows: every row, or (box) the rows of the planes box[4] ..
+  // box[5] of every shell, numbered q = shell * nrb + row in those planes
+  int64_t count = rows, nrb = rows_per_shell, rb0 = 0;
+  if (box) {
+    nrb = box[5] >= box[4] ? (int64_t)(box[5] - box[4] + 1) * ny : 0;
+    rb0 = (int64_t)box[4] * ny;
+    count = (rows / rows_per_shell) * nrb;
+  }
+  auto row_of = [&](int64_t q) -> int64_t {  // the row's index in [shell][rows_per_shell]
+    if (!box) return q;
+    const int64_t sh = q / nrb;
+    return sh * rows_per_shell + rb0 + (q - sh * nrb);
+  };
+  const int64_t ntiles = (count + kT - 1) / kT;
   // X[0..M] as pairs (k, k+1), k even: M/2 + 1 copies per row; for even M
   // the last pair also reads padding column M + 1 (< px)
   const int np = M / 2 + 1;
@@ -720,8 +733,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     const int64_t r0 = tile * kT;
     for (int idx = threadIdx.x; idx < kT * np; idx += kThreads) {
       const int c = idx / np, k = 2 * (idx - c * np);
-      const bool ok = r0 + c < rows;
-      cp_async16(s + c * LP + k, ok ? (const void*)(in + (r0 + c) * px + k) : (const void*)in, ok);
+      const bool ok = r0 + c < count;
+      cp_async16(s + c * LP + k, ok ? (const void*)(in + row_of(r0 + c) * px + k) : (const void*)in, ok);
     }
   };
   int64_t t = blockIdx.x;
@@ -737,7 +750,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     cp_async_wait<1>();
     __syncthreads();
     const int64_t r0 = t * kT;
-    const int valid = (int)(rows - r0 < kT ? rows - r0 : kT);
+    const int valid = (int)(count - r0 < kT ? count - r0 : kT);
     // unpack: Z[k] = (X[k] + conj X[M-k]) + i w^-k (X[k] - conj X[M-k])
     for (int idx = threadIdx.x; idx < kT * half; idx += kThreads) {
       const int c = idx % kT, k = idx / kT;
@@ -749,10 +762,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
     }
     __syncthreads();
     SmemLd ld{u};
-    // rows of this tile may belong to two shells: split the output per row
-    const int64_t sh0 = r0 / rows_per_shell;
-    const int64_t rr0 = r0 - sh0 * rows_per_shell;
-    if (rr0 + valid <= rows_per_shell) {
+    // rows of this tile may belong to two shells (or leave the box's
+    // planes): split the output per row
+    const int64_t f0 = row_of(r0);
+    const int64_t sh0 = f0 / rows_per_shell;
+    const int64_t rr0 = f0 - sh0 * rows_per_shell;
+    if (box ? (r0 % nrb) + valid <= nrb : rr0 + valid <= rows_per_shell) {
       RealRowsOut st{out + sh0 * out_shell_stride + rr0 * NX, NX, valid};
       transform<MC, true>(w, u, tws, f, ld, st);
     } else {
@@ -761,7 +776,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
         for (int h = 0; h < 2; ++h) {
           const int c = 2 * cp + h;
           if (c >= valid) continue;
-          const int64_t row = r0 + c, sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
+          const int64_t row = row_of(r0 + c), sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
           *reinterpret_cast<float2*>(out + sh * out_shell_stride + rr * NX + 2 * m) = h ? hi2(v) : lo2(v);
         }
       };
@@ -800,9 +815,11 @@ void launch_zmulti(int L, const float2* in, float2* out, int64_t out_stride, int
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
                   const float2* stw, const float2* tw, int sm_count, cudaStream_t st, const int* box = nullptr,
                   int ny = 0);
+// box (device, may be null): only the rows of the planes box[4] .. box[5]
+// (ny rows per plane) of every shell are transformed and written.
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,
                   int64_t out_shell_stride, const FftLen& f, const float2* stw, const float2* tw, int sm_count,
-                  cudaStream_t st);
+                  cudaStream_t st, const int* box = nullptr, int ny = 0);
 
 // Persistent grid: the resident CTAs of every SM, at most one CTA per tile.
 template <typename K>

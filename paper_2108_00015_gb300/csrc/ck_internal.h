@@ -294,12 +294,14 @@ ck_status fft_init_attributes();
 void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box = nullptr);
 // Inverse transforms of nshells spectra (spec * K^_s for s < nshells, or spec
 // alone when khat is null) through scratch spectra tmp[s] into real fields
-// out + s * out_stride.
+// out + s * out_stride.  box (device, may be null): only the planes
+// z0..z1 of each field are written (the others keep what they held).
 void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
-                        float* out, int64_t out_stride, cudaStream_t st);
+                        float* out, int64_t out_stride, cudaStream_t st, const int* box = nullptr);
 // Its first two passes alone: tmp[s] = (y, z inverse of spec * K^_s), rows of pitch px.
 // box (device, may be null): only the planes z0..z1 of the output are
-// needed, and of them only the rows y0..y1 (512-point y and z axes).
+// needed (512-point y and z axes), and of them, for fused plans, only the
+// rows y0..y1.
 void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
                        cudaStream_t st, const int* box = nullptr);
 ck_status build_kernel_spectra(Plan& p, cudaStream_t st);

@@ -109,4 +109,35 @@ def test_field_exact_across_catalogs(precision):
         assert np.array_equal(gr.cpu().numpy().astype(np.uint32), R)
         ref = O.correlate(g, shells, 1.0, data, rand, orders=(2, 3), engine="fft")
         _check(res, ref, len(shells))
+        # the whole W_s on request (the plan's own bank covers only the box's planes)
+        _, N, _ = O.density_fields(D, R)
+        for k, rad in enumerate(shells):
+            want = O.convolve_direct(N, O.shell_offsets(rad, 1.0, 1.0), False)
+            got = plan.bank(k).cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(got - want)) <= 1e-5 * max(1.0, np.max(np.abs(want))), (i, k)
+    plan.close()
+
+
+@pytest.mark.parametrize("n,lo,hi", [((30, 40, 36), (8, 9, 10), (22, 30, 26)),
+                                     ((24, 512, 512), (4, 150, 220), (20, 330, 300))])
+def test_bank_planes_higher_orders(n, lo, hi):
+    """Plans that keep the bank (orders up to 4, split-TF32 on the tensor
+    cores) transform and sum only the occupied planes: a confined catalog's
+    sums of every order against the oracle."""
+    torch = cuda_torch()
+    g = GridSpec(n, (0.0, 0.0, 0.0), 1.0, False)
+    shells = (1.5, 2.5, 3.5)
+    data, rand = _confined(n, lo, hi, 300, 80_000, 11)
+    w = dict(grid=g, shells=shells, width=1.0, data=data, randoms=rand)
+    ref = O.correlate(g, shells, 1.0, data, rand, orders=(2, 3, 4), engine="fft")
+    plan = plan_for(w, max_order=4, precision="split_tf32")
+    assert not plan.fused
+    plan.set_randoms(*dev_cat(torch, rand))
+    res = plan.compute(*dev_cat(torch, data), orders=(2, 3, 4), out="host")
+    assert res["status"] == 0
+    for order in (2, 3, 4):
+        for key, akey in (("num", "abs_num"), ("den", "abs_den")):
+            want = O.dense_tensor(ref[f"{key}{order}"], len(shells), order - 1)
+            scale = O.dense_tensor(ref[f"{akey}{order}"], len(shells), order - 1)
+            assert normwise(res[key][order].numpy(), want, scale) <= TOL, (order, key)
     plan.close()
