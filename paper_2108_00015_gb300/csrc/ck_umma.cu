@@ -665,13 +665,18 @@ cudaError_t launch_umma_t(const float* w0, const float* bank, int64_t bstride, i
 }
 
 // Largest |value| of W0 (row 0) and of each bank row (1 + s), as float bits
-// (non-negative floats order as unsigned integers), for the FP16 scales.
+// (non-negative floats order as unsigned integers), for the FP16 scales:
+// over the cells the contraction sums (the box's planes, box may be null),
+// the only ones the bank holds.
 __global__ void absmax_rows_kernel(const float* __restrict__ w0, const float* __restrict__ bank, int64_t bstride,
-                                   int64_t nc, int ns, unsigned* __restrict__ out) {
+                                   int64_t nc, int ns, const int* __restrict__ box, int64_t plane,
+                                   unsigned* __restrict__ out) {
   const int row = blockIdx.y;
   const float* src = row == 0 ? w0 : bank + (int64_t)(row - 1) * bstride;
+  const CellRange r = box_cells(box, plane, nc);
   float m = 0.0f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t i = r.lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < r.hi;
+       i += (int64_t)gridDim.x * blockDim.x)
     m = fmaxf(m, fabsf(__ldg(src + i)));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
@@ -710,7 +715,8 @@ cudaError_t launch_umma(int tn, int kind, const float* w0, const float* bank, in
     cudaError_t e = cudaMemsetAsync(absmax, 0, (size_t)(ns + 1) * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     const int64_t per = std::min<int64_t>(1024, std::max<int64_t>(1, (nc + 4095) / 4096));
-    absmax_rows_kernel<<<dim3((unsigned)per, (unsigned)(ns + 1)), 256, 0, st>>>(w0, bank, bstride, nc, ns, absmax);
+    absmax_rows_kernel<<<dim3((unsigned)per, (unsigned)(ns + 1)), 256, 0, st>>>(w0, bank, bstride, nc, ns, box, plane,
+                                                                                absmax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 #define CK_UMMA_CASE(W, K)                                                                                           \
