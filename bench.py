@@ -58,8 +58,9 @@ def _args():
                     help="keep the default launch shapes (ck_plan_autotune times the choices after warm-up)")
     ap.add_argument("--tuning", default=None,
                     help="fixed launch shapes instead of the autotuner: fwd_cols,zreg_cols,yinv_cols,ctas_per_sm"
-                         "[,stack_cols[,thin_overlap]] (8 or 16 columns per tile of the strided passes, 1..3 contraction CTAs "
-                         "per SM, the widest stacked contraction tile)")
+                         "[,stack_cols[,thin_overlap[,z_direct]]] (8 or 16 columns per tile of the strided passes, 1..3 "
+                         "contraction CTAs per SM, the widest stacked contraction tile, thin tiles on a second stream, "
+                         "the z step by the shells' short filters)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the higher-order workloads timed beside the headline at N = 1 (stress256: xi_2..xi_5, "
                          "survey512_s32: xi_2..xi_4, in every contraction form)")
@@ -601,7 +602,7 @@ def run_gb300(args):
                     "peak_source": (f"{tkind}: MEASURED_PEAKS.json bf16_tflops_sustained x {TF32_PER_BF16:.3f} "
                                     "(nominal TF32/BF16 ratio)" if args.precision == "split_tf32" else
                                     f"{tkind}: MEASURED_PEAKS.json bf16_tflops_sustained (dense BF16/FP16 rate)")}
-    fft_names = [k for k in stages if k.startswith("fft_") or k == "x_c2r_contract"]
+    fft_names = [k for k in stages if k.startswith("fft_") or k in ("x_c2r_contract", "z_conv")]
     fft_bytes = sum(stages[k]["bytes"] for k in fft_names)
     fft_ms = sum(stages[k]["ms"] for k in fft_names)
 

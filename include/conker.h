@@ -391,7 +391,10 @@ ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, doub
 
 /* Autotuner (the batched and survey forms pick their transform and
  * contraction shapes per plan).  Times, on the plan's own buffers, the
- * candidates of each launch-shape choice that has more than one -- 8 or 16
+ * candidates of each launch-shape choice that has more than one -- the z
+ * step of the convolutions by the shells' short filters or by the forward
+ * and K^ z passes (whichever gives the faster forward transform plus
+ * inverse z and y passes), 8 or 16
  * columns per tile of the single-field 512-point strided passes, of the K^ z
  * pass and of the multi-shell inverse y pass (the latter two together), and
  * for the split tensor-core forms that keep a bank the widest tile stacked
@@ -399,12 +402,14 @@ ck_status ck_plan_set_region(ck_plan* plan, int32_t z_begin, int32_t z_end, doub
  * k-step instead of three, which also adds the lo*lo term), 1, 2 or 3
  * contraction CTAs per SM, and whether the thin tiles run on a second
  * stream beside the tensor-core kernel -- each candidate once untimed and
- * five times between CUDA events, and keeps the one with the fastest run.  The choices
- * change launch shapes only: transforms are bit-identical, and the
+ * five times between CUDA events, and keeps the one with the fastest run.  The tile
+ * widths change launch shapes only: transforms are bit-identical, and the
  * contraction's sums differ by the order of their partial sums (and, for a
- * stacked tile, by its lo*lo term, below 2^-21 relative).  Needs a resident
+ * stacked tile, by its lo*lo term, below 2^-21 relative); the two z routes
+ * give W_s that agree to FP32 rounding.  Needs a resident
  * field: the field, spectrum and bank that the last ck_set_randoms or
  * compute left are the inputs it times, and they are left as they were
+ * (the spectrum of the same field, in either route's form)
  * (CK_ERR_NO_RANDOMS before either, and after ck_plan_set_region until the
  * next such call).  Captured graphs of ck_batch_compute are dropped.
  * Synchronises the stream. */
@@ -414,14 +419,17 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream);
  * strided passes, out[1] of the K^ z pass, out[2] of the multi-shell inverse
  * y pass, out[3] contraction CTAs per SM, out[4] the widest stacked
  * contraction tile (columns; 0: none), out[5] 1 when thin tiles overlap
- * the tensor-core kernel, out[6] 1 once ck_plan_autotune has run (else the
- * defaults: 8, 8, 8, 2, 32, 1). */
+ * the tensor-core kernel, out[6] 1 when the convolutions take the z step
+ * by the shells' short filters (plans whose shells reach at most 31 planes
+ * in z; 0: the forward z pass and the K^ z pass), out[7] 1 once
+ * ck_plan_autotune has run (else the defaults: 8, 8, 8, 2, 32, 1, 1 where
+ * the plan has the filters). */
 ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out);
 
-/* Set the choices by hand (in[0..5] as ck_plan_get_tuning's out[0..5]:
- * 8 or 16 columns, 1..3 CTAs per SM, 0..128 stacked columns, 0 or 1;
- * CK_ERR_ARG otherwise).  Host only; drops captured graphs and contraction
- * plans. */
+/* Set the choices by hand (in[0..6] as ck_plan_get_tuning's out[0..6]:
+ * 8 or 16 columns, 1..3 CTAs per SM, 0..128 stacked columns, 0 or 1, 0 or
+ * 1 (a plan without the filters keeps the transform route); CK_ERR_ARG
+ * otherwise).  Host only; drops captured graphs and contraction plans. */
 ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in);
 
 /* Synchronise `stream` and return (and clear) the plan's device status. */
@@ -508,12 +516,13 @@ ck_status ck_debug_force_timeout(int64_t ns);
  * algorithmic bytes that launch must move (inputs read once + outputs written
  * once).  ck_profile_enable resets the accumulators; ck_profile_read
  * synchronises each recorded event and returns the totals. */
-/* Stages 0..13: grid_points, prepare_field, fft_x_r2c, fft_y_fwd, fft_z_fwd,
+/* Stages 0..14: grid_points, prepare_field, fft_x_r2c, fft_y_fwd, fft_z_fwd,
  * fft_z_inv_mul, fft_y_inv, fft_x_c2r, contract, reduce, finalize,
  * x_c2r_contract (the inverse x pass fused with the order-2/3 sums), other,
  * selection_field (the factorised randoms of Eq. 7; bytes = the cells
- * written). */
-#define CK_STAGES 14
+ * written), z_conv (the z step of the convolution by the shells' short
+ * filters, in place of fft_z_fwd and fft_z_inv_mul). */
+#define CK_STAGES 15
 typedef struct ck_stage_times {
   double ms[CK_STAGES];       /* summed event time of the stage's launches   */
   int64_t launches[CK_STAGES];

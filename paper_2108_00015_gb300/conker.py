@@ -68,7 +68,7 @@ class _Info(ctypes.Structure):
                 ("fused", ctypes.c_int32), ("fft_n", ctypes.c_int32 * 3)]
 
 
-CK_STAGES = 14
+CK_STAGES = 15
 
 
 class _StageTimes(ctypes.Structure):
@@ -467,15 +467,16 @@ class Plan:
         return self.tuning()
 
     def set_tuning(self, fwd_cols: int = 8, zreg_cols: int = 8, yinv_cols: int = 8, tc_ctas_per_sm: int = 2,
-                   tc_stack_cols: int = 32, tc_thin_overlap: int = 1):
-        arr = (ctypes.c_int32 * 6)(fwd_cols, zreg_cols, yinv_cols, tc_ctas_per_sm, tc_stack_cols, tc_thin_overlap)
+                   tc_stack_cols: int = 32, tc_thin_overlap: int = 1, z_direct: int = 1):
+        arr = (ctypes.c_int32 * 7)(fwd_cols, zreg_cols, yinv_cols, tc_ctas_per_sm, tc_stack_cols, tc_thin_overlap,
+                                   z_direct)
         _check(_lib().ck_plan_set_tuning(self._h, arr), "ck_plan_set_tuning")
 
     def tuning(self) -> Dict[str, int]:
-        out = (ctypes.c_int32 * 7)()
+        out = (ctypes.c_int32 * 8)()
         _check(_lib().ck_plan_get_tuning(self._h, out), "ck_plan_get_tuning")
         return dict(fwd_cols=out[0], zreg_cols=out[1], yinv_cols=out[2], tc_ctas_per_sm=out[3],
-                    tc_stack_cols=out[4], tc_thin_overlap=out[5], tuned=bool(out[6]))
+                    tc_stack_cols=out[4], tc_thin_overlap=out[5], z_direct=out[6], tuned=bool(out[7]))
 
     def status(self, stream=None) -> int:
         return int(_lib().ck_plan_status(self._h, _stream_ptr(stream)))

@@ -58,7 +58,7 @@ constexpr size_t kProfPool = 16384;
 const char* kStageNames[CK_STAGES] = {"grid_points", "prepare_field", "fft_x_r2c", "fft_y_fwd",
                                       "fft_z_fwd", "fft_z_inv_mul", "fft_y_inv", "fft_x_c2r",
                                       "contract", "reduce", "finalize", "x_c2r_contract", "other",
-                                      "selection_field"};
+                                      "selection_field", "z_conv"};
 
 void prof_collect(ck::Plan& p) {
   ck::Profiler& f = p.prof;
@@ -156,6 +156,7 @@ ck_status carve(Plan& p) {
   p.table_arena = take(p.table_arena_cap);
   p.support = reinterpret_cast<int*>(take(14 * 4));
   p.absmax = reinterpret_cast<unsigned*>(take((size_t)(CK_MAX_SHELLS + 1) * 4));
+  p.kzt = p.kz_dz > 0 ? reinterpret_cast<float*>(take(zconv_table_bytes(p))) : nullptr;
   const size_t used = (size_t)(b - static_cast<unsigned char*>(p.ws));
   return used <= p.ws_bytes ? CK_OK : CK_ERR_OOM;
 }
@@ -324,7 +325,7 @@ ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, con
                            int support = -1) {
   if (!w0) w0 = p.field;
   if (support >= 0) launch_support_box(p, support, st);
-  launch_fft_forward(p, p.field, p.spec, st, support >= 0 ? p.support + 6 : nullptr);
+  launch_fft_forward(p, p.field, p.spec, st, support >= 0 ? p.support + 6 : nullptr, true);
   if (p.region && w0 == p.field) {
     const size_t plane = (size_t)p.grid.n[0] * p.grid.n[1];
     if (p.region_z0 > 0) CK_TRY(cudaMemsetAsync(p.field, 0, plane * p.region_z0 * sizeof(float), st));
@@ -335,7 +336,7 @@ ck_status convolve_and_sum(Plan& p, int mask, double* sums, cudaStream_t st, con
   if (p.fused) return launch_convolve_contract(p, w0, sums, st, support >= 0 ? p.support : nullptr);
   // the bank on the planes the sums visit (W_0 vanishes outside them);
   // ck_get_bank and ck_product_map recompute whole fields
-  launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st, support >= 0 ? p.support : nullptr);
+  launch_fft_inverse(p, p.spec, 0, p.ns, p.tmp, p.bank, p.field_stride, st, support >= 0 ? p.support : nullptr);
   return launch_contract(p, mask, w0, p.bank, p.field_stride, sums, st, support >= 0 ? p.support : nullptr);
 }
 
@@ -582,7 +583,7 @@ ck_status ck_set_randoms_diagonal(ck_plan* plan, const float* x, const float* y,
   CK_TRY_S(grid_catalog(p, x, y, z, n, 1, st));
   launch_prepare_randoms(p, st);
   p.bank_holds = -1;
-  launch_fft_forward(p, p.field, p.spec, st);
+  launch_fft_forward(p, p.field, p.spec, st, nullptr, true);
   bool full = false;
   CK_TRY_S(launch_diagonal_randoms(p, &full, st));
   p.bank_holds = 1;
@@ -705,7 +706,7 @@ ck_status ck_product_map(ck_plan* plan, int32_t shell, float* map, void* stream)
   // recompute W_s from the resident spectrum: fused plans keep no bank, and
   // a catalog's bank holds only the planes its sums visited
   float* ws = p.fused ? p.bank : p.bank + (size_t)shell * p.field_stride;
-  launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, ws, p.field_stride, st);
+  launch_fft_inverse(p, p.spec, shell, 1, p.tmp, ws, p.field_stride, st);
   const bool dev = is_device_ptr(map);
   const size_t bytes = (size_t)p.box_n[0] * p.box_n[1] * p.box_n[2] * sizeof(float);
   float* dst = dev ? map : reinterpret_cast<float*>(p.counts[0]);  // host: through the data count buffer
@@ -732,7 +733,7 @@ ck_status ck_compute_diagonal(ck_plan* plan, const float* x, const float* y, con
   CK_TRY_S(grid_catalog(p, x, y, z, n, 0, st));
   launch_prepare_data(p, st);
   p.bank_holds = -1;
-  launch_fft_forward(p, p.field, p.spec, st);
+  launch_fft_forward(p, p.field, p.spec, st, nullptr, true);
   CK_TRY_S(launch_diagonal(p, order_mask, st));
   p.bank_holds = 0;
   CK_TRY(cudaGetLastError());
@@ -856,34 +857,54 @@ ck_status ck_plan_autotune(ck_plan* plan, void* stream) {
   // its support box, as in the step itself (the pruned forward transform
   // gives the same spectrum); a loaded field: every plane and row
   const int* box = (p.bank_holds == 0 || p.bank_holds == 1) ? p.support : nullptr;
-  // the single-field strided passes (the forward transform of the resident field)
-  if (s == CK_OK && (ny == 512 || nz == 512)) {
+  // the z step (the direct filter, where the plan has one, or the K^ z
+  // pass) with the forward transform each needs, and the tile widths of
+  // the 512-point register passes under each: the single-field strided
+  // passes, then the K^ z pass with the multi-shell inverse y pass; the
+  // route with the faster forward + inverse z and y passes is kept
+  if (s == CK_OK) {
+    const Tuning orig = p.tune;
+    Tuning win = p.tune;
     float best = 1e30f;
-    int pick = p.tune.fwd_cols;
-    for (int c : {8, 16}) {
-      p.tune.fwd_cols = c;
-      float ms = 0.0f;
-      if ((s = timed([&] { launch_fft_forward(p, p.field, p.spec, st, box ? box + 6 : nullptr); }, &ms)) != CK_OK)
-        break;
-      if (ms < best) { best = ms; pick = c; }
-    }
-    p.tune.fwd_cols = pick;
-  }
-  // the K^ z pass and the multi-shell inverse y pass, every shell, into the scratch spectra
-  if (s == CK_OK && (ny == 512 || nz == 512)) {
-    float best = 1e30f;
-    int pz = p.tune.zreg_cols, py = p.tune.yinv_cols;
-    for (int cz : {8, 16})
-      for (int cy : {8, 16}) {
-        if ((nz != 512 && cz != pz) || (ny != 512 && cy != py)) continue;
-        p.tune.zreg_cols = cz;
-        p.tune.yinv_cols = cy;
+    for (int zd = 0; zd <= 1 && s == CK_OK; ++zd) {
+      if (zd == 1 && p.kz_dz == 0) break;
+      p.tune.z_direct = zd;
+      float fbest = 1e30f, ibest = 1e30f;
+      int fc = orig.fwd_cols, pz = orig.zreg_cols, py = orig.yinv_cols;
+      for (int c : {8, 16}) {
+        if (ny != 512 && nz != 512 && c != orig.fwd_cols) continue;
+        p.tune.fwd_cols = c;
         float ms = 0.0f;
-        if ((s = timed([&] { launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st, box); }, &ms)) != CK_OK) break;
-        if (ms < best) { best = ms; pz = cz; py = cy; }
+        if ((s = timed([&] { launch_fft_forward(p, p.field, p.spec, st, box ? box + 6 : nullptr, true); }, &ms)) !=
+            CK_OK)
+          break;
+        if (ms < fbest) { fbest = ms; fc = c; }
       }
-    p.tune.zreg_cols = pz;
-    p.tune.yinv_cols = py;
+      if (s != CK_OK) break;
+      p.tune.fwd_cols = fc;  // the spectrum is in this route's form (every width gives the same)
+      for (int cz : {8, 16})
+        for (int cy : {8, 16}) {
+          if (s != CK_OK) break;
+          if ((zd == 1 || nz != 512) && cz != orig.zreg_cols) continue;
+          if (ny != 512 && cy != orig.yinv_cols) continue;
+          p.tune.zreg_cols = cz;
+          p.tune.yinv_cols = cy;
+          float ms = 0.0f;
+          if ((s = timed([&] { launch_inverse_zy(p, p.spec, 0, p.ns, p.tmp, st, box); }, &ms)) != CK_OK) break;
+          if (ms < ibest) { ibest = ms; pz = cz; py = cy; }
+        }
+      if (s == CK_OK && fbest + ibest < best) {
+        best = fbest + ibest;
+        win.z_direct = zd;
+        win.fwd_cols = fc;
+        win.zreg_cols = pz;
+        win.yinv_cols = py;
+      }
+    }
+    p.tune.z_direct = win.z_direct;
+    p.tune.fwd_cols = win.fwd_cols;
+    p.tune.zreg_cols = win.zreg_cols;
+    p.tune.yinv_cols = win.yinv_cols;
   }
   // the tensor-core contraction's splits, on the randoms' bank
   const bool tensor = p.precision == CK_PREC_SPLIT_TF32 || p.precision == CK_PREC_SPLIT_BF16 ||
@@ -933,7 +954,8 @@ ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in) {
   if (!plan || !in) return CK_ERR_BAD_POINTER;
   for (int i = 0; i < 3; ++i)
     if (in[i] != 8 && in[i] != 16) return CK_ERR_ARG;
-  if (in[3] < 1 || in[3] > 3 || in[4] < 0 || in[4] > 128 || (in[5] != 0 && in[5] != 1)) return CK_ERR_ARG;
+  if (in[3] < 1 || in[3] > 3 || in[4] < 0 || in[4] > 128 || (in[5] != 0 && in[5] != 1) || (in[6] != 0 && in[6] != 1))
+    return CK_ERR_ARG;
   Plan& p = *reinterpret_cast<Plan*>(plan);
   p.tune.fwd_cols = in[0];
   p.tune.zreg_cols = in[1];
@@ -941,6 +963,7 @@ ck_status ck_plan_set_tuning(ck_plan* plan, const int32_t* in) {
   p.tune.tc_ctas_per_sm = in[3];
   p.tune.tc_stack_cols = in[4];
   p.tune.tc_thin_overlap = in[5];
+  p.tune.z_direct = in[6];
   for (bool& r : p.cplan_ready) r = false;
   for (auto& g : p.gexec)
     if (g) {
@@ -959,7 +982,8 @@ ck_status ck_plan_get_tuning(const ck_plan* plan, int32_t* out) {
   out[3] = p.tune.tc_ctas_per_sm;
   out[4] = p.tune.tc_stack_cols;
   out[5] = p.tune.tc_thin_overlap;
-  out[6] = p.tune.tuned ? 1 : 0;
+  out[6] = p.tune.z_direct && p.kz_dz > 0 ? 1 : 0;
+  out[7] = p.tune.tuned ? 1 : 0;
   return CK_OK;
 }
 
@@ -1063,7 +1087,7 @@ ck_status ck_get_bank(ck_plan* plan, int32_t shell, float* out, void* stream) {
   // recompute W_s from the resident spectrum: fused plans keep no bank, and
   // a catalog's bank holds only the planes its sums visited
   float* src = p.fused ? p.bank : p.bank + (size_t)shell * p.field_stride;
-  launch_fft_inverse(p, p.spec, p.khat + (size_t)shell * p.khat_stride, 1, p.tmp, src, p.field_stride, st);
+  launch_fft_inverse(p, p.spec, shell, 1, p.tmp, src, p.field_stride, st);
   CK_TRY(cudaGetLastError());
   CK_TRY_S(copy_out(out, src, (size_t)p.nc * 4, st, &host));
   if (host) CK_TRY(cudaStreamSynchronize(st));
@@ -1098,7 +1122,7 @@ ck_status ck_fft_c2r(ck_plan* plan, const void* in_spec, float* out, void* strea
   if (!is_device_ptr(in_spec) || !is_device_ptr(out)) return CK_ERR_BAD_POINTER;
   if (((uintptr_t)in_spec & 15u) != 0 || ((uintptr_t)out & 15u) != 0) return CK_ERR_BAD_POINTER;
   Plan& p = *reinterpret_cast<Plan*>(plan);
-  launch_fft_inverse(p, static_cast<const float2*>(in_spec), nullptr, 1, p.tmp, out, 0, S(stream));
+  launch_fft_inverse(p, static_cast<const float2*>(in_spec), -1, 1, p.tmp, out, 0, S(stream));
   return cuda_status(cudaGetLastError());
 }
 

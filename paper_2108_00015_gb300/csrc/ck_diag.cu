@@ -151,7 +151,7 @@ __global__ void diag_scatter_kernel(const double* __restrict__ dsums, const Diag
 // bank, then sum_r field W_s^k for every shell, k = 1..max_order - 1, into
 // out[k - 1][s] (max_order - 1 rows of ns doubles).
 ck_status launch_diag_bank_sums(Plan& p, double* out, cudaStream_t st) {
-  launch_fft_inverse(p, p.spec, p.khat, p.ns, p.tmp, p.bank, p.field_stride, st);
+  launch_fft_inverse(p, p.spec, 0, p.ns, p.tmp, p.bank, p.field_stride, st);
   const int64_t nblocks = (p.nc + DG_CELLS - 1) / DG_CELLS;
   if ((size_t)nblocks * p.ns * DG_K > p.partials_cap) return CK_ERR_OOM;
   {

@@ -6,7 +6,10 @@
 // Forward (one field): x pass (real rows -> half spectrum), y pass, z pass.
 // Inverse (all shells of one field at once): one z pass that reads the
 // spectrum once and writes spectrum * K^_s transformed along z for every
-// shell, then one y pass and one x pass over all shells.
+// shell, then one y pass and one x pass over all shells.  Plans whose shells
+// reach few planes take the z step directly (ck_zconv.cu): the forward
+// transform stops after the y pass and the direct filter replaces the K^ z
+// pass.
 #include <math.h>
 
 #include <algorithm>
@@ -22,8 +25,14 @@ using fft::kT;
 
 ck_status fft_init_attributes() { return CK_OK; }
 
-void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box) {
+void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box, bool conv) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
+  // the direct z step reads the spectrum untransformed along z
+  const bool direct = conv && p.tune.z_direct && p.kz_dz > 0;
+  if (conv) {
+    p.spec_direct = direct;
+    p.spec_in_box = box;
+  }
   const int64_t rows = (int64_t)ny * nz;
   const double H = (double)nz * ny * (nx / 2 + 1);
   const double row = 8.0 * (nx / 2 + 1);  // bytes of one half-spectrum row
@@ -41,7 +50,7 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
     fft::launch_strided(ny, false, spec, spec, v, p.fy, p.stw[1], p.tw[1], p.tune.fwd_cols, p.sm_count, st, box, nz,
                         fft::kPrunePlanes | fft::kPruneInY);
   }
-  {
+  if (!direct) {
     ProfScope ps(p, ST_FFT_Z_FWD, box ? 8.0 * H : 16.0 * H, 0.0, row * ny, box, st);
     StridedView v{(int64_t)ny * p.px, 0, ny * p.px, 1};
     fft::launch_strided(nz, false, spec, spec, v, p.fz, p.stw[2], p.tw[2], p.tune.fwd_cols, p.sm_count, st, box, nz,
@@ -49,11 +58,12 @@ void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream
   }
 }
 
-// Inverse z and y passes of nshells spectra: spec * K^_s (khat != nullptr)
-// or spec itself (khat == nullptr, nshells == 1), into the scratch spectra
-// tmp[s] (stride spec_elems).
-void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
-                       cudaStream_t st, const int* box) {
+// Inverse z and y passes of nshells spectra: spec * K^_s for shells shell0 ..
+// (shell0 >= 0) or spec itself (shell0 < 0, nshells == 1), into the scratch
+// spectra tmp[s] (stride spec_elems).  The z step of a convolution of a
+// spectrum left untransformed along z (p.spec_direct) is the direct filter.
+void launch_inverse_zy(const Plan& p, const float2* spec, int shell0, int nshells, float2* tmp, cudaStream_t st,
+                       const int* box) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const double H = (double)nz * ny * (nx / 2 + 1);
   const double row = 8.0 * (nx / 2 + 1);  // bytes of one half-spectrum row
@@ -61,7 +71,17 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
   // transform and write every plane (the fused x pass visits the box alone)
   const int* zbox = nz == 512 ? box : nullptr;
   const int* ybox = ny == 512 ? box : nullptr;
-  {
+  const float* khat = shell0 >= 0 ? p.khat + (size_t)shell0 * p.khat_stride : nullptr;
+  if (shell0 >= 0 && p.spec_direct) {
+    // read: the box's planes of the spectrum and the groups' tables;
+    // written: the box's planes of every shell (or every plane)
+    const double rowb = 8.0 * (double)ny * p.px;  // bytes of one plane of the spectrum
+    const int g0 = shell0 / 8, g1 = (shell0 + nshells + 7) / 8;
+    const double tables = 4.0 * (double)(g1 - g0) * (double)p.kz_group_stride;
+    ProfScope ps(p, ST_Z_CONV, tables + (box ? 0.0 : (1.0 + nshells) * rowb * nz), 0.0, (1.0 + nshells) * rowb, box,
+                 st);
+    launch_zconv(p, spec, shell0, nshells, tmp, p.spec_elems, p.spec_in_box, box, st);
+  } else {
     const double base = 8.0 * H + nshells * (khat ? 4.0 * (double)p.oct_elems : 0.0);
     // written: every plane, or the box's planes
     ProfScope ps(p, ST_FFT_Z_INV_MUL, base + (zbox ? 0.0 : nshells * 8.0 * H), 0.0, nshells * row * ny, zbox, st);
@@ -86,11 +106,11 @@ void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int
 
 // The whole inverse: the z and y passes, then the x pass from tmp[s] into
 // real fields out + s * out_stride.
-void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp, float* out,
+void launch_fft_inverse(const Plan& p, const float2* spec, int shell0, int nshells, float2* tmp, float* out,
                         int64_t out_stride, cudaStream_t st, const int* box) {
   const int nx = p.grid.n[0], ny = p.grid.n[1], nz = p.grid.n[2];
   const double H = (double)nz * ny * (nx / 2 + 1);
-  launch_inverse_zy(p, spec, khat, nshells, tmp, st, box);
+  launch_inverse_zy(p, spec, shell0, nshells, tmp, st, box);
   {
     const int64_t rows = (int64_t)ny * nz * nshells;
     // every row, or the rows of the box's planes
@@ -204,7 +224,9 @@ ck_status build_kernel_spectra(Plan& p, cudaStream_t st) {
   khat_pass_y<<<blocks, 256, 0, st>>>(dA1, dCy, dA2, ns, H1, p.oct[1], p.oct[0]);
   khat_pass_z<<<blocks, 256, 0, st>>>(dA2, dCz, p.khat, ns, H1, p.oct[2], p.oct[1], p.oct[0], p.px,
                                       1.0 / (double)p.nc);
-  e = cudaGetLastError();
+  // the direct z step's table: the (x, y) sums per plane offset
+  e = launch_zconv_table(p, dA2, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   // the host vectors must outlive the copies
   return cuda_status(cudaStreamSynchronize(st));

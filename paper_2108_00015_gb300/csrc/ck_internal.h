@@ -107,7 +107,7 @@ struct ContractPlan {
 // Per-stage event timing (ck_profile_enable / ck_profile_read).
 enum Stage {
   ST_GRID = 0, ST_PREP, ST_FFT_X_R2C, ST_FFT_Y_FWD, ST_FFT_Z_FWD, ST_FFT_Z_INV_MUL, ST_FFT_Y_INV,
-  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_X_C2R_CONTRACT, ST_OTHER, ST_SELECTION
+  ST_FFT_X_C2R, ST_CONTRACT, ST_REDUCE, ST_FINALIZE, ST_X_C2R_CONTRACT, ST_OTHER, ST_SELECTION, ST_Z_CONV
 };
 
 struct Profiler {
@@ -133,6 +133,7 @@ struct Tuning {
   int tc_ctas_per_sm = 2;  // tensor-core contraction: CTAs per SM the splits aim at
   int tc_stack_cols = 32;  // tensor-core tiles of at most this many columns are stacked (0: none)
   int tc_thin_overlap = 1; // 1: thin tiles on a second stream beside the tensor-core kernel
+  int z_direct = 1;        // 1: the z step of the convolution by its short filter (where the plan has one)
   bool tuned = false;
 };
 
@@ -155,6 +156,18 @@ struct Plan {
   int64_t oct_elems = 0;
   int64_t khat_stride = 0;  // floats per shell spectrum: octant rows padded to px (zeros beyond n[0]/2)
   int H = 0;                // max offset over all shells and axes
+  // The z step by direct filtering (ck_zconv.cu): taps per column (0: the
+  // plan has no table), groups of 8 shells, taps per group, the table
+  float* kzt = nullptr;
+  int kz_dz = 0;
+  int kz_groups = 0;
+  int kz_taps[CK_MAX_SHELLS / 8] = {0};
+  int64_t kz_group_stride = 0;  // floats per group of the table
+  // the resident spectrum p.spec was left untransformed along z (the last
+  // forward transform into it took the direct route), and the box (device)
+  // outside whose planes its field vanishes (null: every plane transformed)
+  mutable bool spec_direct = false;
+  mutable const int* spec_in_box = nullptr;
   int64_t n_multisets[CK_MAX_ORDER + 1] = {0};
   int64_t multiset_base[CK_MAX_ORDER + 1] = {0};  // offset of order n in a packed array
   int64_t n_multiset_total = 0;
@@ -291,20 +304,39 @@ void launch_weights_to_cells(const Plan& p, int which, cudaStream_t st);
 ck_status fft_init_attributes();
 // box (device, may be null): the field is zero outside it, and the passes
 // skip the rows and planes that hold only zeros (512-point y and z axes).
-void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box = nullptr);
-// Inverse transforms of nshells spectra (spec * K^_s for s < nshells, or spec
-// alone when khat is null) through scratch spectra tmp[s] into real fields
-// out + s * out_stride.  box (device, may be null): only the planes
-// z0..z1 of each field are written (the others keep what they held).
-void launch_fft_inverse(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
-                        float* out, int64_t out_stride, cudaStream_t st, const int* box = nullptr);
+// conv: the spectrum is for the plan's convolutions (into p.spec), which
+// leave out the z transform when the plan takes the direct z step
+// (p.spec_direct records which form p.spec holds); otherwise a full 3D
+// transform.
+void launch_fft_forward(const Plan& p, const float* in, float2* spec, cudaStream_t st, const int* box = nullptr,
+                        bool conv = false);
+// Inverse transforms of nshells spectra (spec * K^_s for shells shell0 ..
+// shell0 + nshells - 1, or spec alone when shell0 < 0) through scratch
+// spectra tmp[s] into real fields out + s * out_stride.  With shell0 >= 0,
+// spec is p.spec in the form p.spec_direct records.  box (device, may be
+// null): only the planes z0..z1 of each field are written (the others keep
+// what they held).
+void launch_fft_inverse(const Plan& p, const float2* spec, int shell0, int nshells, float2* tmp, float* out,
+                        int64_t out_stride, cudaStream_t st, const int* box = nullptr);
 // Its first two passes alone: tmp[s] = (y, z inverse of spec * K^_s), rows of pitch px.
 // box (device, may be null): only the planes z0..z1 of the output are
-// needed (512-point y and z axes), and of them, for fused plans, only the
-// rows y0..y1.
-void launch_inverse_zy(const Plan& p, const float2* spec, const float* khat, int nshells, float2* tmp,
-                       cudaStream_t st, const int* box = nullptr);
+// needed, and of them, for fused plans, only the rows y0..y1.
+void launch_inverse_zy(const Plan& p, const float2* spec, int shell0, int nshells, float2* tmp, cudaStream_t st,
+                       const int* box = nullptr);
 ck_status build_kernel_spectra(Plan& p, cudaStream_t st);
+
+// ---- the direct z step (ck_zconv.cu) ------------------------------------------
+void zconv_layout(Plan& p);                  // kz_dz, kz_groups, kz_taps, kz_group_stride
+size_t zconv_table_bytes(const Plan& p);     // 0 without a table
+// The table from the FP64 (x, y) cosine sums of build_kernel_spectra.
+cudaError_t launch_zconv_table(const Plan& p, const double* A2, cudaStream_t st);
+// out + (s - shell0) * out_stride = the z step of W_s for shells shell0 ..
+// shell0 + nshells - 1 from spec (transformed along x and y).  in_box
+// (device, may be null): spec vanishes outside its planes z = in_box[4] ..
+// in_box[5], whatever the others hold; out_box (may be null): only its
+// planes are written (null: every plane).
+void launch_zconv(const Plan& p, const float2* spec, int shell0, int nshells, float2* out, int64_t out_stride,
+                  const int* in_box, const int* out_box, cudaStream_t st);
 
 // ---- fused inverse x pass + sums (ck_xc.cu) -----------------------------------
 int xc_pad_shells(int ns);               // supported padded shell count, 0 if none

@@ -201,6 +201,7 @@ ck_status validate_and_layout(const ck_grid* grid, const ck_shells* shells, int 
   const int64_t rtiles = (rows + 127) / 128;
   const int64_t tc = rtiles * (2 * ((rows + 255) / 256 + 1) + (rows + 1) / 2) + 16;
   p->table_arena_cap = (size_t)(1 << (CK_MAX_ORDER + 1)) * (size_t)(2 * rows + std::max(tiles, tc) + 8) * sizeof(int2);
+  zconv_layout(*p);
   return CK_OK;
 }
 
@@ -235,6 +236,7 @@ size_t workspace_bytes(const Plan& p) {
   b += al(p.table_arena_cap);
   b += al(14 * 4);                                                      // support boxes, preparation planes
   b += al((size_t)(CK_MAX_SHELLS + 1) * 4);                             // split-FP16 row maxima
+  b += al(zconv_table_bytes(p));                                        // the direct z step's table
   return b;
 }
 

@@ -74,7 +74,7 @@ ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaS
   const int max_ctas = (int)std::min<size_t>((size_t)2 * p.sm_count, p.partials_cap / nout_pad);
   int ctas = 0;
 
-  launch_inverse_zy(p, p.spec, p.khat, p.ns, p.tmp, st, box);
+  launch_inverse_zy(p, p.spec, 0, p.ns, p.tmp, st, box);
   cudaError_t e;
   {
     const double H = (double)nz * ny * (nx / 2 + 1);

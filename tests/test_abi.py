@@ -181,7 +181,7 @@ def test_undersized_workspace(lib):
 def test_tuning_entry_points_validate(lib):
     """ck_plan_autotune, ck_plan_set_tuning and ck_plan_get_tuning reject a
     null plan or array (CK_ERR_BAD_POINTER) before any CUDA call."""
-    arr = (ctypes.c_int32 * 7)(8, 8, 16, 2, 32, 0, 0)
+    arr = (ctypes.c_int32 * 8)(8, 8, 16, 2, 32, 0, 0, 0)
     for name in ("ck_plan_autotune", "ck_plan_set_tuning", "ck_plan_get_tuning"):
         fn = getattr(lib, name)
         fn.restype = ctypes.c_int
@@ -190,7 +190,8 @@ def test_tuning_entry_points_validate(lib):
     fn = lib.ck_plan_set_tuning
     fake = ctypes.c_void_p(1 << 20)  # never dereferenced: a null array is refused first
     assert fn(fake, None) == 2
-    for bad in ((7, 8, 16, 2, 32, 0), (8, 32, 16, 2, 32, 0), (8, 8, 16, 0, 32, 0), (8, 8, 16, 4, 32, 0),
-                (8, 8, 8, 2, -1, 0), (8, 8, 8, 2, 129, 0), (8, 8, 8, 2, 32, 2)):
+    for bad in ((7, 8, 16, 2, 32, 0, 1), (8, 32, 16, 2, 32, 0, 1), (8, 8, 16, 0, 32, 0, 1), (8, 8, 16, 4, 32, 0, 1),
+                (8, 8, 8, 2, -1, 0, 1), (8, 8, 8, 2, 129, 0, 1), (8, 8, 8, 2, 32, 2, 1), (8, 8, 8, 2, 32, 1, 2),
+                (8, 8, 8, 2, 32, 1, -1)):
         # out-of-range choices are refused (CK_ERR_ARG) before the plan is read
-        assert fn(fake, ctypes.cast((ctypes.c_int32 * 6)(*bad), ctypes.c_void_p)) == 1, bad
+        assert fn(fake, ctypes.cast((ctypes.c_int32 * 7)(*bad), ctypes.c_void_p)) == 1, bad

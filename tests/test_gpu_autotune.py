@@ -1,9 +1,11 @@
-"""The autotuner's choices change launch shapes only.  Every choice of tile
-width of the 512-point strided passes (forward, K^ z pass, inverse y pass)
-gives transforms, and so sums, identical bit for bit to the defaults', and
-every choice of contraction CTAs per SM gives sums within the gate of the
-oracle's; ck_plan_autotune keeps one of the candidates and the results stay
-the same."""
+"""The autotuner's choices.  Under either z route (the shells' short
+filters or the forward and K^ z passes), every choice of tile width of the
+512-point strided passes (forward, K^ z pass, inverse y pass) gives
+transforms, and so sums, identical bit for bit to that route's defaults;
+the two routes' sums agree with the oracle's within the gate; every choice
+of contraction CTAs per SM gives sums within the gate of the oracle's; and
+ck_plan_autotune keeps one of the candidates, whose results are the chosen
+route's."""
 import itertools
 
 import numpy as np
@@ -34,26 +36,41 @@ def test_tile_widths_bit_identical(precision):
     def run():
         plan.set_randoms(*r)
         res = plan.compute(*d, orders=(2, 3), out="host")
-        return {k: res[k][n].numpy().copy() for k in ("num", "den") for n in (2, 3)}, res["status"]
+        return {f"{k}{n}": res[k][n].numpy().copy() for k in ("num", "den") for n in (2, 3)}, res["status"]
 
-    base, st = run()
-    assert st == 0
     assert plan.tuning()["tuned"] is False
-    for fwd, zreg, yinv in itertools.product((8, 16), repeat=3):
-        plan.set_tuning(fwd, zreg, yinv, 2)
-        got, st = run()
+    assert plan.tuning()["z_direct"] == 1  # 3.5-cell shells: short filters
+    bases = {}
+    for zd in (0, 1):
+        plan.set_tuning(z_direct=zd)
+        bases[zd], st = run()
         assert st == 0
-        for k in base:
-            assert np.array_equal(got[k], base[k]), (fwd, zreg, yinv, k)
+        for fwd, zreg, yinv in itertools.product((8, 16), repeat=3):
+            plan.set_tuning(fwd, zreg, yinv, 2, z_direct=zd)
+            got, st = run()
+            assert st == 0
+            for k in bases[zd]:
+                assert np.array_equal(got[k], bases[zd][k]), (zd, fwd, zreg, yinv, k)
+    # the routes sum in different orders: both within the oracle's gate
+    ref = O.correlate(w["grid"], w["shells"], w["width"], w["data"], w["randoms"], orders=(2, 3), engine="fft")
+    ns = len(w["shells"])
+    for zd in (0, 1):
+        for n in (2, 3):
+            for key, akey in (("num", "abs_num"), ("den", "abs_den")):
+                want = O.dense_tensor(ref[f"{key}{n}"], ns, n - 1)
+                scale = O.dense_tensor(ref[f"{akey}{n}"], ns, n - 1)
+                assert normwise(bases[zd][f"{key}{n}"], want, scale) <= 1e-5, (zd, key, n)
     plan.set_tuning()
     plan.set_randoms(*r)
     t = plan.autotune()
     assert t["tuned"] and t["fwd_cols"] in (8, 16) and t["zreg_cols"] in (8, 16) and t["yinv_cols"] in (8, 16)
+    base = bases[t["z_direct"]]
     got, st = run()
     for k in base:
         assert np.array_equal(got[k], base[k]), k
     # after a compute the catalog's field is the one timed
-    plan.autotune()
+    t = plan.autotune()
+    base = bases[t["z_direct"]]
     got, st = run()
     assert st == 0
     for k in base:

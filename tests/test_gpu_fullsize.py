@@ -9,8 +9,9 @@ oracle can compute at this size:
 * W_s at sampled cells, one by one by direct summation;
 * the random bank's sum rule sum_r (R***K_s) = (sum_r R) |O_s|;
 * symmetry and finiteness of the order-3 tensors, and the mixed form's
-  order-3 sums (fused pass over the box of occupied cells, split-TF32
-  tensor cores) against the plain form's (every cell, FP32 CUDA cores).
+  order-3 sums (z step by the shells' short filters, fused pass over the
+  box of occupied cells, split-TF32 tensor cores) against the plain form's
+  (forward and K^ z passes, every cell, FP32 CUDA cores).
 """
 import numpy as np
 import pytest
@@ -27,16 +28,20 @@ TOL = 1e-5
 _ORDER3 = {}
 
 
-@pytest.fixture(scope="module", params=["split_tf32", "fp32"])
+# the mixed form takes the z step by the shells' short filters, the plain
+# form by the forward and K^ z passes, so both routes run at full size
+@pytest.fixture(scope="module", params=[("split_tf32", 1), ("fp32", 0)], ids=["split_tf32", "fp32"])
 def run(request):
     torch = cuda_torch()
     w = workload("survey512")
     g = w["grid"]
-    plan = plan_for(w, max_order=3, precision=request.param)
+    precision, z_direct = request.param
+    plan = plan_for(w, max_order=3, precision=precision)
+    plan.set_tuning(z_direct=z_direct)
     plan.set_randoms(*dev_cat(torch, w["randoms"]))
     bank_r = {s: plan.bank(s).cpu().numpy() for s in (0, 7, 15)}
     res = plan.compute(*dev_cat(torch, w["data"]), orders=(2, 3), out="host")
-    _ORDER3[request.param] = {k: res[k][3].numpy().copy() for k in ("num", "den")}
+    _ORDER3[precision] = {k: res[k][3].numpy().copy() for k in ("num", "den")}
     D, R = plan.grids()
     out = dict(w=w, g=g, plan=plan, res=res, bank_r=bank_r, D=D.cpu().numpy().astype(np.uint32),
                R=R.cpu().numpy().astype(np.uint32), N=plan.field(0).cpu().numpy(),

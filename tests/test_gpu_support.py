@@ -4,7 +4,8 @@ sub-box of a survey box, against the FP64 oracle over every cell.  Covers
 the 512-point y and z passes (planes and rows outside the box skipped), the
 register x pass with several grid rows per tile (8 shells, half-length 16)
 and with one (5 shells, half-length 32), the shared-memory x pass of an odd
-half-length, and the plain path (no pruning) on the same catalog."""
+half-length, and the plain path (no pruning) on the same catalog, each
+with the z step by the shells' short filters and by the K^ z pass."""
 import numpy as np
 import pytest
 
@@ -56,10 +57,12 @@ def test_fused_support_box(n, lo, hi, shells):
     for prec in ("split_tf32", "fp32"):
         plan = plan_for(w, max_order=3, precision=prec)
         assert plan.fused is (prec == "split_tf32")
-        plan.set_randoms(*dev_cat(torch, rand))
-        res = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
-        assert res["status"] == 0
-        _check(res, ref, ns)
+        for zd in (1, 0):  # the z step by the short filters, then by the K^ z pass
+            plan.set_tuning(z_direct=zd)
+            plan.set_randoms(*dev_cat(torch, rand))
+            res = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
+            assert res["status"] == 0
+            _check(res, ref, ns)
         plan.close()
 
 
