@@ -19,9 +19,10 @@
 // x up to zc output planes of the support box.  The staged planes E (the
 // unit's planes plus dz on either side, zeros outside the box) serve every
 // shell group; a thread keeps 8 shells x 4 consecutive planes of one
-// column in registers and slides a 7-plane window down and up the staged
-// column, four taps per step.  Groups of 8 shells' taps are double-buffered
-// through shared memory.
+// column in registers and walks the staged column down and up from them,
+// one tap at a time, with packed FP32x2 adds and FMAs (a complex value is
+// one register pair).  Groups of 8 shells' taps are double-buffered through
+// shared memory.
 #include <algorithm>
 
 #include "ck_device.cuh"
@@ -61,6 +62,31 @@ size_t zconv_smem(int dz, int zc) {
   return (size_t)(zc + 2 * dz) * ZC_EP * sizeof(float2) + 2 * ZC_C * kp * sizeof(float);
 }
 
+// Taps d = 0 .. T - 1 of one pass: acc[j][r] += k_j(d) (E[z - d] + E[z + d])
+// for the planes z = qb + r of a column, e pointing at E's row of plane qb
+// and kc at the column's taps.  T is a compile-time count, so the loop
+// unrolls: each staged row is loaded once, every shared-memory offset is an
+// immediate, and the adds and FMAs are packed FP32x2 operations on the
+// complex values (each lane rounded as fmaf).
+template <int T>
+__device__ __forceinline__ void zconv_taps(const float2* e, const float* kc, float2 (&acc)[ZC_G][ZC_R]) {
+#pragma unroll
+  for (int d = 0; d < T; ++d) {
+    const float4 ka = *reinterpret_cast<const float4*>(kc + d * ZC_G);
+    const float4 kb = *reinterpret_cast<const float4*>(kc + d * ZC_G + 4);
+    const float k[ZC_G] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+    float2 sp[ZC_R];
+#pragma unroll
+    for (int r = 0; r < ZC_R; ++r) sp[r] = __fadd2_rn(e[(r - d) * ZC_EP], e[(r + d) * ZC_EP]);
+#pragma unroll
+    for (int j = 0; j < ZC_G; ++j) {
+      const float2 kk = make_float2(k[j], k[j]);
+#pragma unroll
+      for (int r = 0; r < ZC_R; ++r) acc[j][r] = __ffma2_rn(kk, sp[r], acc[j][r]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
   extern __shared__ float4 smem4[];
   const int MP = a.dz;
@@ -78,11 +104,11 @@ __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
   int z0 = 0, nzb = a.nz, zi = 0, nzi = a.nz;
   if (a.out_box) {
     z0 = a.out_box[4];
-    nzb = max(0, a.out_box[5] - a.out_box[4] + 1);
+    nzb = box_len(a.out_box[4], a.out_box[5]);
   }
   if (a.in_box) {
     zi = a.in_box[4];
-    nzi = max(0, a.in_box[5] - a.in_box[4] + 1);
+    nzi = box_len(a.in_box[4], a.in_box[5]);
   }
   const int64_t ntiles = (a.plane + ZC_C - 1) / ZC_C;
   const int nchunks = (nzb + a.zc - 1) / a.zc;
@@ -121,8 +147,10 @@ __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
     const int q0 = ch * a.zc;  // first output plane of the unit, relative to z0
     const int zcn = min(a.zc, nzb - q0);
     __syncthreads();  // the previous unit's reads of E and the tap buffers are done
-    // E[i] = D at plane z0 + q0 + i - MP (mod n_z), zero outside the field's planes
-    for (int idx = tid; idx < erows * (ZC_C / 2); idx += ZC_NT) {
+    // E[i] = D at plane z0 + q0 + i - MP (mod n_z), zero outside the field's
+    // planes; the passes read rows below ((zcn + 3) & ~3) + 2 MP
+    const int rows = min(erows, ((zcn + 3) & ~3) + 2 * MP);
+    for (int idx = tid; idx < rows * (ZC_C / 2); idx += ZC_NT) {
       const int i = idx / (ZC_C / 2), cp = idx - (idx / (ZC_C / 2)) * (ZC_C / 2);
       int pl = (z0 + q0 + i - MP) % a.nz;
       if (pl < 0) pl += a.nz;
@@ -151,33 +179,16 @@ __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
         for (int j = 0; j < ZC_G; ++j)
 #pragma unroll
           for (int r = 0; r < ZC_R; ++r) acc[j][r] = make_float2(0.f, 0.f);
-        // planes qb - d .. and qb + d .. of the column for taps d = db .. db + 3
-        const float2* eL = E + (MP + qb - 3) * ZC_EP + c;
-        const float2* eU = E + (MP + qb) * ZC_EP + c;
-        for (int db = 0; db < taps; db += 4) {
-          float2 L[7], U[7];
-#pragma unroll
-          for (int i = 0; i < 7; ++i) {
-            L[i] = eL[(i - db) * ZC_EP];
-            U[i] = eU[(db + i) * ZC_EP];
-          }
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const float4 ka = *reinterpret_cast<const float4*>(kc + (db + t) * ZC_G);
-            const float4 kb = *reinterpret_cast<const float4*>(kc + (db + t) * ZC_G + 4);
-            const float k[ZC_G] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
-#pragma unroll
-            for (int r = 0; r < ZC_R; ++r) {
-              // D(z - d) + D(z + d) for plane z = qb + r, tap d = db + t
-              const float2 lo = L[r - t + 3], hi = U[r + t];
-              const float sx = lo.x + hi.x, sy = lo.y + hi.y;
-#pragma unroll
-              for (int j = 0; j < ZC_G; ++j) {
-                acc[j][r].x = fmaf(k[j], sx, acc[j][r].x);
-                acc[j][r].y = fmaf(k[j], sy, acc[j][r].y);
-              }
-            }
-          }
+        const float2* e = E + (MP + qb) * ZC_EP + c;  // row of plane qb
+        switch (taps) {
+          case 4: zconv_taps<4>(e, kc, acc); break;
+          case 8: zconv_taps<8>(e, kc, acc); break;
+          case 12: zconv_taps<12>(e, kc, acc); break;
+          case 16: zconv_taps<16>(e, kc, acc); break;
+          case 20: zconv_taps<20>(e, kc, acc); break;
+          case 24: zconv_taps<24>(e, kc, acc); break;
+          case 28: zconv_taps<28>(e, kc, acc); break;
+          default: zconv_taps<32>(e, kc, acc); break;
         }
         const bool col_ok = i0 + c < a.plane;
 #pragma unroll
@@ -270,9 +281,12 @@ void launch_zconv(const Plan& p, const float2* spec, int shell0, int nshells, fl
   a.g0 = shell0 / ZC_G;
   a.g1 = (shell0 + nshells + ZC_G - 1) / ZC_G;
   for (int g = 0; g < p.kz_groups; ++g) a.taps[g] = p.kz_taps[g];
-  // the most planes per unit (up to the axis) that keep two CTAs per SM
-  int zc = (nz + 3) / 4 * 4;
-  while (zc > 4 && zconv_smem(a.dz, zc) > ZC_SMEM_CAP) zc -= 4;
+  // the most planes per unit (up to the axis) that keep two CTAs per SM,
+  // evened out over the units an axis of planes takes
+  int zmax = (nz + 3) / 4 * 4;
+  while (zmax > 4 && zconv_smem(a.dz, zmax) > ZC_SMEM_CAP) zmax -= 4;
+  const int nch = (nz + zmax - 1) / zmax;
+  const int zc = ((nz + nch - 1) / nch + 3) / 4 * 4;
   a.zc = zc;
   const size_t smem = zconv_smem(a.dz, zc);
   if (smem > 48 * 1024) cudaFuncSetAttribute(zconv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
