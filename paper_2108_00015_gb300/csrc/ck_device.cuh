@@ -105,6 +105,10 @@ struct CellRange {
   int64_t lo, hi;
 };
 
+// Planes (or rows) lo .. hi of a box bound pair: 0 when lo > hi (an empty
+// box is stored as lo = INT_MAX, hi = INT_MIN, whose difference overflows).
+__host__ __device__ __forceinline__ int box_len(int lo, int hi) { return hi >= lo ? hi - lo + 1 : 0; }
+
 __device__ __forceinline__ CellRange box_cells(const int* box, int64_t plane, int64_t nc) {
   if (!box) return CellRange{0, nc};
   const int z0 = box[4], z1 = box[5];

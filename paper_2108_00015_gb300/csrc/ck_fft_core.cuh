@@ -600,9 +600,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   int64_t y0 = 0, nyb = ny > 0 ? ny : 1, z0 = 0, count = rows;
   if (box) {
     y0 = box[2];
-    nyb = box[3] - box[2] + 1;
+    nyb = box_len(box[2], box[3]);
     z0 = box[4];
-    const int64_t nzb = box[5] - box[4] + 1;
+    const int64_t nzb = box_len(box[4], box[5]);
     count = nyb > 0 && nzb > 0 ? nyb * nzb : 0;
     if (nyb <= 0) nyb = 1;
   }
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(MC))
   // box[5] of every shell, numbered q = shell * nrb + row in those planes
   int64_t count = rows, nrb = rows_per_shell, rb0 = 0;
   if (box) {
-    nrb = box[5] >= box[4] ? (int64_t)(box[5] - box[4] + 1) * ny : 0;
+    nrb = (int64_t)box_len(box[4], box[5]) * ny;
     rb0 = (int64_t)box[4] * ny;
     count = (rows / rows_per_shell) * nrb;
   }

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(Sreg<C>::NT, C == 8 ? 2 : 1)
   int zlo = 0, nzb = nz, rlo = 0, rhi = S::L - 1, ilo = 0, ihi = S::L - 1;
   if (planes) {
     zlo = box[4];
-    nzb = max(0, box[5] - box[4] + 1);
+    nzb = box_len(box[4], box[5]);
   }
   if (mode & kPruneOutY) {
     rlo = box[2];

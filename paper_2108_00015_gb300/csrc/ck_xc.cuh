@@ -57,8 +57,8 @@ struct RowMap {
 
 __device__ __forceinline__ RowMap row_map(const int* box, int64_t rows, int ny) {
   if (!box) return RowMap{ny, 0, ny, 0, rows};
-  const int y0 = box[2], y1 = box[3], z0 = box[4], z1 = box[5];
-  const int64_t nyb = y1 - y0 + 1, nzb = z1 - z0 + 1;
+  const int y0 = box[2], z0 = box[4];
+  const int64_t nyb = box_len(y0, box[3]), nzb = box_len(z0, box[5]);
   return RowMap{ny, y0, nyb > 0 ? nyb : 1, z0, nyb > 0 && nzb > 0 ? nyb * nzb : 0};
 }
 

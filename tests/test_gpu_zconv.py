@@ -136,3 +136,36 @@ def test_direct_filter_reach_limit(radius, direct):
     plan = plan_for(dict(grid=g, shells=(radius,), width=1.0), max_order=2, precision="fp32")
     assert plan.tuning()["z_direct"] == direct
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_tf32"])
+def test_empty_catalogs_on_pruned_grid(precision):
+    """An empty catalog, or one whose points all fall outside the box, has
+    an empty support box (stored as lo > hi): every pass, pruned or not, and
+    either z route visits nothing, the call reports CK_ERR_EMPTY_CATALOG,
+    and the plan then serves the next catalog exactly as a new one would."""
+    from paper_2108_00015_gb300 import CkError
+    torch = cuda_torch()
+    n = (32, 512, 512)
+    g = GridSpec(n, (0.0, 0.0, 0.0), 1.0, False)
+    shells = (1.5, 2.5, 3.5)
+    data, rand = _confined(n, (6, 120, 200), (26, 330, 331), 300, 80_000, 95)
+    ref = O.correlate(g, shells, 1.0, data, rand, orders=(2, 3), engine="fft")
+    empty = Catalog(*(np.zeros(0, np.float32) for _ in range(3)))
+    outside = Catalog(*(np.full(50, -5.0, np.float32) for _ in range(3)))
+    plan = plan_for(dict(grid=g, shells=shells, width=1.0), max_order=3, precision=precision)
+    for zd in (1, 0):
+        plan.set_tuning(z_direct=zd)
+        for bad in (empty, outside):
+            try:
+                plan.set_randoms(*dev_cat(torch, bad))
+            except CkError as e:
+                assert e.code == 12
+            plan.set_randoms(*dev_cat(torch, rand))
+            with pytest.raises(CkError) as e:
+                plan.compute(*dev_cat(torch, bad), orders=(2, 3), out="host")
+            assert e.value.code == 12
+            res = plan.compute(*dev_cat(torch, data), orders=(2, 3), out="host")
+            assert res["status"] == 0
+            _check_sums(res, ref, len(shells))
+    plan.close()
