@@ -76,7 +76,7 @@ void launch_inverse_zy(const Plan& p, const float2* spec, int shell0, int nshell
     // read: the box's planes of the spectrum and the groups' tables;
     // written: the box's planes of every shell (or every plane)
     const double rowb = 8.0 * (double)ny * p.px;  // bytes of one plane of the spectrum
-    const int g0 = shell0 / 8, g1 = (shell0 + nshells + 7) / 8;
+    const int g0 = shell0 / kZconvGroup, g1 = (shell0 + nshells + kZconvGroup - 1) / kZconvGroup;
     const double tables = 4.0 * (double)(g1 - g0) * (double)p.kz_group_stride;
     ProfScope ps(p, ST_Z_CONV, tables + (box ? 0.0 : (1.0 + nshells) * rowb * nz), 0.0, (1.0 + nshells) * rowb, box,
                  st);

@@ -157,11 +157,11 @@ struct Plan {
   int64_t khat_stride = 0;  // floats per shell spectrum: octant rows padded to px (zeros beyond n[0]/2)
   int H = 0;                // max offset over all shells and axes
   // The z step by direct filtering (ck_zconv.cu): taps per column (0: the
-  // plan has no table), groups of 8 shells, taps per group, the table
+  // plan has no table), groups of 4 shells, taps per group, the table
   float* kzt = nullptr;
   int kz_dz = 0;
   int kz_groups = 0;
-  int kz_taps[CK_MAX_SHELLS / 8] = {0};
+  int kz_taps[CK_MAX_SHELLS] = {0};
   int64_t kz_group_stride = 0;  // floats per group of the table
   // the resident spectrum p.spec was left untransformed along z (the last
   // forward transform into it took the direct route), and the box (device)
@@ -326,6 +326,7 @@ void launch_inverse_zy(const Plan& p, const float2* spec, int shell0, int nshell
 ck_status build_kernel_spectra(Plan& p, cudaStream_t st);
 
 // ---- the direct z step (ck_zconv.cu) ------------------------------------------
+constexpr int kZconvGroup = 4;               // shells per group of the table
 void zconv_layout(Plan& p);                  // kz_dz, kz_groups, kz_taps, kz_group_stride
 size_t zconv_table_bytes(const Plan& p);     // 0 without a table
 // The table from the FP64 (x, y) cosine sums of build_kernel_spectra.

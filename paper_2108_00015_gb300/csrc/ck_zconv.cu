@@ -10,7 +10,7 @@
 // circular convolution: K^_s(k) = sum_d K_s^xy(d) e^{-2 pi i k_z d / n_z},
 // and the unnormalised inverse z transform of K^_s D^ / N_c is
 // n_z / N_c sum_d K_s^xy(d) D(z - d).  The table therefore holds
-// K_s^xy / (n_x n_y), in groups of 8 shells, with the d = 0 entry halved so
+// K_s^xy / (n_x n_y), in groups of 4 shells, with the d = 0 entry halved so
 // that every tap multiplies the pair D(z - d) + D(z + d):
 //   table[g][kyf][kx][d][j] (kyf = min(ky, n_y - ky): K_s is even in ky;
 //   kx < px, zeros for kx > n_x / 2; d < dz, zeros beyond m_s).
@@ -18,10 +18,10 @@
 // Work unit: 32 adjacent columns of a plane (the flattened (ky, kx) index)
 // x up to zc output planes of the support box.  The staged planes E (the
 // unit's planes plus dz on either side, zeros outside the box) serve every
-// shell group; a thread keeps 8 shells x 4 consecutive planes of one
+// shell group; a thread keeps 4 shells x 4 consecutive planes of one
 // column in registers and walks the staged column down and up from them,
 // one tap at a time, with packed FP32x2 adds and FMAs (a complex value is
-// one register pair).  Groups of 8 shells' taps are double-buffered through
+// one register pair).  Groups of 4 shells' taps are double-buffered through
 // shared memory.
 #include <algorithm>
 
@@ -35,10 +35,12 @@ namespace {
 constexpr int ZC_C = 32;    // columns per unit
 constexpr int ZC_NT = 256;  // threads per CTA
 constexpr int ZC_R = 4;     // consecutive planes per thread
-constexpr int ZC_G = 8;     // shells per group
+constexpr int ZC_G = kZconvGroup;  // shells per group
+static_assert(ZC_G % 4 == 0, "a group's taps of one plane offset are whole 16-byte pieces");
 constexpr int ZC_EP = 34;   // float2 per staged plane (32 columns + 2: conflict-free 8-byte loads)
 constexpr int ZC_PASS = (ZC_NT / ZC_C) * ZC_R;  // planes per pass of the CTA
-constexpr size_t ZC_SMEM_CAP = 110 * 1024;     // two CTAs per SM
+constexpr int ZC_CTAS = 3;  // CTAs per SM
+constexpr size_t ZC_SMEM_CAP = 74 * 1024;      // three CTAs per SM
 
 struct ZconvArgs {
   const float2* spec;     // [n_z][n_y][px], transformed along x and y
@@ -51,7 +53,7 @@ struct ZconvArgs {
   const int* out_box;     // box (device) whose planes are written, or null: every plane
   int px, ny, nz;
   int dz;                 // taps stored per column, a multiple of 4
-  int zc;                 // output planes per unit, a multiple of 4
+  int zc;                 // most output planes per unit (shared memory), a multiple of 4
   int shell0, nshells;    // shells written
   int g0, g1;             // groups g0 .. g1 - 1
   int taps[CK_MAX_SHELLS / ZC_G];  // taps used per group (multiple of 4, <= dz)
@@ -72,9 +74,8 @@ template <int T>
 __device__ __forceinline__ void zconv_taps(const float2* e, const float* kc, float2 (&acc)[ZC_G][ZC_R]) {
 #pragma unroll
   for (int d = 0; d < T; ++d) {
-    const float4 ka = *reinterpret_cast<const float4*>(kc + d * ZC_G);
-    const float4 kb = *reinterpret_cast<const float4*>(kc + d * ZC_G + 4);
-    const float k[ZC_G] = {ka.x, ka.y, ka.z, ka.w, kb.x, kb.y, kb.z, kb.w};
+    const float4 kq = *reinterpret_cast<const float4*>(kc + d * ZC_G);
+    const float k[ZC_G] = {kq.x, kq.y, kq.z, kq.w};
     float2 sp[ZC_R];
 #pragma unroll
     for (int r = 0; r < ZC_R; ++r) sp[r] = __fadd2_rn(e[(r - d) * ZC_EP], e[(r + d) * ZC_EP]);
@@ -87,7 +88,7 @@ __device__ __forceinline__ void zconv_taps(const float2* e, const float* kc, flo
   }
 }
 
-__global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
+__global__ void __launch_bounds__(ZC_NT, ZC_CTAS) zconv_kernel(ZconvArgs a) {
   extern __shared__ float4 smem4[];
   const int MP = a.dz;
   const int KP = a.dz * ZC_G + 4;  // floats per staged column of a group (16-byte multiple, conflict-free)
@@ -110,8 +111,11 @@ __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
     zi = a.in_box[4];
     nzi = box_len(a.in_box[4], a.in_box[5]);
   }
+  // the box's planes in units of at most zc planes (what shared memory
+  // holds), evened out: zce planes per unit, a multiple of 4
   const int64_t ntiles = (a.plane + ZC_C - 1) / ZC_C;
   const int nchunks = (nzb + a.zc - 1) / a.zc;
+  const int zce = nchunks > 0 ? (((nzb + nchunks - 1) / nchunks + 3) & ~3) : a.zc;
   const int64_t units = ntiles * nchunks;
 
   // taps of group g (a compile-time index into the parameter array keeps it
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
   };
   auto stage_k = [&](int64_t i0, int g, int buf) {
     float* kb = Kb + buf * (ZC_C * KP);
-    const int nq = taps_of(g) * 2;  // 16-byte pieces per column
+    const int nq = taps_of(g) * (ZC_G / 4);  // 16-byte pieces per column: ZC_G floats per tap
     for (int idx = tid; idx < ZC_C * nq; idx += ZC_NT) {
       const int cc = idx / nq, q = idx - (idx / nq) * nq;
       const int64_t i = i0 + cc;
@@ -144,8 +148,8 @@ __global__ void __launch_bounds__(ZC_NT, 2) zconv_kernel(ZconvArgs a) {
     const int64_t tile = u / nchunks;
     const int ch = (int)(u - tile * nchunks);
     const int64_t i0 = tile * ZC_C;
-    const int q0 = ch * a.zc;  // first output plane of the unit, relative to z0
-    const int zcn = min(a.zc, nzb - q0);
+    const int q0 = ch * zce;  // first output plane of the unit, relative to z0
+    const int zcn = min(zce, nzb - q0);
     __syncthreads();  // the previous unit's reads of E and the tap buffers are done
     // E[i] = D at plane z0 + q0 + i - MP (mod n_z), zero outside the field's
     // planes; the passes read rows below ((zcn + 3) & ~3) + 2 MP
@@ -226,7 +230,7 @@ __global__ void zconv_table_kernel(const double* __restrict__ A2, float* __restr
 
 }  // namespace
 
-// Taps per column (dz) and per group of 8 shells (taps[g]) for the shells'
+// Taps per column (dz) and per group of shells (taps[g]) for the shells'
 // largest |m_z|; dz = 0 when the direct route does not apply (more than 32
 // taps: the transform route is then the cheaper one).
 void zconv_layout(Plan& p) {
@@ -281,18 +285,16 @@ void launch_zconv(const Plan& p, const float2* spec, int shell0, int nshells, fl
   a.g0 = shell0 / ZC_G;
   a.g1 = (shell0 + nshells + ZC_G - 1) / ZC_G;
   for (int g = 0; g < p.kz_groups; ++g) a.taps[g] = p.kz_taps[g];
-  // the most planes per unit (up to the axis) that keep two CTAs per SM,
-  // evened out over the units an axis of planes takes
-  int zmax = (nz + 3) / 4 * 4;
-  while (zmax > 4 && zconv_smem(a.dz, zmax) > ZC_SMEM_CAP) zmax -= 4;
-  const int nch = (nz + zmax - 1) / zmax;
-  const int zc = ((nz + nch - 1) / nch + 3) / 4 * 4;
+  // the most planes per unit (up to the axis) that keep three CTAs per SM;
+  // the kernel evens the box's planes out over the units they take
+  int zc = (nz + 3) / 4 * 4;
+  while (zc > 4 && zconv_smem(a.dz, zc) > ZC_SMEM_CAP) zc -= 4;
   a.zc = zc;
   const size_t smem = zconv_smem(a.dz, zc);
   if (smem > 48 * 1024) cudaFuncSetAttribute(zconv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t ntiles = (a.plane + ZC_C - 1) / ZC_C;
   const int64_t units = ntiles * ((nz + zc - 1) / zc);  // at most (the box may hold fewer planes)
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)2 * p.sm_count));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)ZC_CTAS * p.sm_count));
   zconv_kernel<<<grid, ZC_NT, smem, st>>>(a);
 }
 
