@@ -408,6 +408,15 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const RowMap rm = row_map(box, rows, ny);
   const int64_t ntiles = (rm.count + ROWS - 1) / ROWS;
+  // the 8-cell k-steps of a row that can meet a nonzero N: those overlapping
+  // the box's cells x0 .. x1 (W_0 = N vanishes outside them, and so do the
+  // terms of both sums)
+  static_assert(NX % 8 == 0, "whole k-steps per grid row");
+  int kx0 = 0, nks = NX / 8;
+  if (box && box[0] <= box[1]) {
+    kx0 = max(box[0], 0) / 8;
+    nks = max(0, min(NX, box[1] + 8) / 8 - kx0);
+  }
   // thread 0: bulk copies of tile t into staging buffer b and N buffer nbi
   // warp 0: lane 0 arms the barrier, then the lanes issue one copy each
   // (a spectrum row per shell and visited row, and the row's N cells)
@@ -515,7 +524,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           dsm32[j][e] = 0.0f;
         }
 #pragma unroll 2
-      for (int c0 = 8 * warp; c0 < TC; c0 += 8 * kWarps) {
+      for (int q = warp; q < ROWS * nks; q += kWarps) {
+        const int c0 = ROWS == 1 ? 8 * (kx0 + q) : (q / nks) * NX + 8 * (kx0 + q % nks);
         const int c = c0 + 2 * tq;
         float2 nn = *reinterpret_cast<const float2*>(nb + c);
         if (c >= vc) nn = make_float2(0.f, 0.f);  // rows past the grid (last tile)
