@@ -1,5 +1,7 @@
 // ck_grid.cu -- mapping (Sec. 2.2): nearest-grid-point histograms of the
-// data and random catalogs with warp-aggregated atomics, and the field
+// data and random catalogs with one 32-bit atomic per point (the L2 absorbs
+// clustered catalogs' repeated cells faster than grouping them per warp
+// would cost), and the field
 // preparation N = D - alpha R (Eq. 8), Rt = alpha R.
 //
 // Cell rule: on each axis a point x (float32) is in cell k iff
@@ -71,7 +73,7 @@ __device__ __forceinline__ bool axis_cell(float x, int a, const GridArgs& A, int
   return true;
 }
 
-// Counts (W = false: warp-aggregated 32-bit atomics on counts) or weights
+// Counts (W = false: a 32-bit atomic on counts per point) or weights
 // (W = true: each weight rounded to a multiple of 2^-32, a 64-bit atomic on
 // acc per point, so the integer sums do not depend on the order of the
 // atomics; a point with a non-finite weight is dropped).
@@ -86,8 +88,10 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
   unsigned long long kept = 0, dropped = 0;
   long long qsum = 0;
   int bmin[3] = {INT_MAX, INT_MAX, INT_MAX}, bmax[3] = {INT_MIN, INT_MIN, INT_MIN};
-  // one point per lane; called by every lane of the warp (in: a real point)
-  auto grid_one = [&](float x, float y, float z, float wt, bool in) {
+  // the cell of one point (0xFFFFFFFF: not a real point, or outside the
+  // box), with its fixed-point weight and the kept / dropped / bounds
+  // bookkeeping (in: a real point)
+  auto cell_of = [&](float x, float y, float z, float wt, bool in, long long* qout) -> uint32_t {
     int kx = 0, ky = 0, kz = 0;
     long long q = 0;
     if (in) {
@@ -107,13 +111,16 @@ __device__ __forceinline__ void grid_points_body(const float* __restrict__ xs, c
       }
       in = ok;
     }
-    const uint32_t cell = in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
-    if constexpr (W) {
-      if (in) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
-    } else {
-      const unsigned peers = __match_any_sync(0xFFFFFFFFu, cell);
-      if (in && lane == __ffs(peers) - 1) atomicAdd(counts + cell, (uint32_t)__popc(peers));
-    }
+    *qout = q;
+    return in ? (uint32_t)(((int64_t)kz * A.dim[1] + ky) * A.dim[0] + kx) : 0xFFFFFFFFu;
+  };
+  // one point: one atomic (integer adds give the same sums in any order)
+  auto grid_one = [&](float x, float y, float z, float wt, bool in) {
+    long long q = 0;
+    const uint32_t cell = cell_of(x, y, z, wt, in, &q);
+    if (cell == 0xFFFFFFFFu) return;
+    if constexpr (W) atomicAdd(reinterpret_cast<unsigned long long*>(acc + cell), (unsigned long long)q);  // two's complement
+    else atomicAdd(counts + cell, 1u);
   };
   // 16-byte aligned arrays: four consecutive points per thread and round,
   // read with one 16-byte load per coordinate.  Trip counts are

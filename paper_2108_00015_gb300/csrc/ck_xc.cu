@@ -58,8 +58,18 @@ __global__ void reduce_xc_kernel(const double* __restrict__ partials, int ctas, 
     src = ns_pad + a * ns_pad - a * (a - 1) / 2 + (b - a);
     dst = base3 + (o - n2);
   }
+  // in CTA order; sixteen loads in flight before their adds (same order,
+  // the same sum)
   double s = 0.0;
-  for (int c = 0; c < ctas; ++c) s += partials[(int64_t)c * nout_pad + src];
+  int c = 0;
+  for (; c + 16 <= ctas; c += 16) {
+    double v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __ldg(partials + (int64_t)(c + k) * nout_pad + src);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) s += v[k];
+  }
+  for (; c < ctas; ++c) s += partials[(int64_t)c * nout_pad + src];
   out[dst] = s;
 }
 
