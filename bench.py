@@ -781,7 +781,13 @@ def run_batch(args):
         return e0.elapsed_time(e1)
 
     tunings = None
-    if not args.no_autotune:
+    if args.tuning:
+        # fixed launch shapes for every grid class
+        tunings = []
+        for p in plans:
+            p.set_tuning(*[int(v) for v in args.tuning.split(",")])
+            tunings.append(p.tuning())
+    elif not args.no_autotune:
         # each grid class's launch shapes, timed on its own randoms
         tunings = []
         for p, r in zip(plans, rnd):
