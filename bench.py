@@ -39,6 +39,16 @@ METRIC = ("ms/catalog for ξ_2..ξ_5 (mixed vs plain FP32, rel err ≤1e-5); FFT
 FALLBACK_HBM_GBS = 6800.0
 
 
+def _sources_sha(source):
+    """First 16 hex digits of the SHA-256 of the named csrc files, concatenated in order."""
+    names = [source] if isinstance(source, str) else list(source)
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2108_00015_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,11 +586,11 @@ def run_gb300(args):
         try:
             tr = json.load(open(tr_path))
             ent = tr.get(args.workload, {}).get(dname)
-            src = os.path.join(ROOT, "paper_2108_00015_gb300", "csrc", ent["source"]) if ent else None
-            # counters of the same source and, where recorded, the same tile width
+            # counters of the same sources (the kernel's file and the headers
+            # it includes, hashed in order) and, where recorded, the same tile width
             cols = {"fft_z_inv_mul": "zreg_cols", "fft_y_inv": "yinv_cols"}.get(dname)
             same_shape = ent is not None and ("cols" not in ent or (tuning or plan.tuning()).get(cols) == ent["cols"])
-            if ent and src and same_shape and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == ent["sha"]:
+            if ent and same_shape and _sources_sha(ent["source"]) == ent["sha"]:
                 traffic = ent["bytes_per_launch"]
         except Exception:
             traffic = None
