@@ -33,6 +33,11 @@ static void run_c2r(const float2* in, float* out, int nx, int px, int64_t rows, 
 
 void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t rows, const FftLen& f,
                   const float2* stw, const float2* tw, int sm_count, cudaStream_t st, const int* box, int ny) {
+  // 512-cell rows: the register form (ck_fft_xr.cu)
+  if (M == 256) {
+    launch_xr2c_reg(in, out, px, rows, tw, sm_count, st, box, ny);
+    return;
+  }
   switch (M) {
 #define CK_CASE(N) case N: run_r2c<N>(in, out, nx, px, rows, f, stw, tw, sm_count, st, box, ny); return;
     CK_HALF_LENGTHS(CK_CASE)

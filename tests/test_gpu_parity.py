@@ -119,7 +119,7 @@ def test_gridding_survey_sample_exact(torch):
 @pytest.mark.parametrize("shape", [(32, 32, 32), (18, 20, 24), (40, 30, 16), (80, 48, 64), (10, 6, 12),
                                    (128, 96, 160), (16, 384, 4), (240, 12, 288), (512, 4, 320),
                                    (160, 160, 160), (256, 256, 256), (16, 512, 64), (512, 16, 32),
-                                   (512, 512, 16)])
+                                   (512, 512, 16), (6, 10, 512), (16, 32, 512), (4, 4, 512)])
 def test_fft_vs_numpy(torch, shape):
     nz, ny, nx = shape
     g = GridSpec((nx, ny, nz), (0.0, 0.0, 0.0), 1.0, True)
