@@ -819,6 +819,11 @@ void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t r
 // arguments for M = 256 (tw: e^{-2 pi i t / 512}).
 void launch_xr2c_reg(const float* in, float2* out, int px, int64_t rows, const float2* tw, int sm_count,
                      cudaStream_t st, const int* box, int ny);
+// The inverse x pass of 512-cell rows in registers: launch_x_c2r's arguments
+// for M = 256 and px = 260.
+void launch_xc2r_reg(const float2* in, float* out, int px, int64_t rows, int64_t rows_per_shell,
+                     int64_t out_shell_stride, const float2* tw, int sm_count, cudaStream_t st, const int* box,
+                     int ny);
 // box (device, may be null): only the rows of the planes box[4] .. box[5]
 // (ny rows per plane) of every shell are transformed and written.
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,

@@ -49,6 +49,11 @@ void launch_x_r2c(int M, const float* in, float2* out, int nx, int px, int64_t r
 void launch_x_c2r(int M, const float2* in, float* out, int nx, int px, int64_t rows, int64_t rows_per_shell,
                   int64_t out_shell_stride, const FftLen& f, const float2* stw, const float2* tw, int sm_count,
                   cudaStream_t st, const int* box, int ny) {
+  // 512-cell rows (pitch 260): the register form (ck_fft_xr.cu)
+  if (M == 256 && px == M + 4) {
+    launch_xc2r_reg(in, out, px, rows, rows_per_shell, out_shell_stride, tw, sm_count, st, box, ny);
+    return;
+  }
   switch (M) {
 #define CK_CASE(N)                                                                                            \
   case N:                                                                                                     \

@@ -1,6 +1,7 @@
-// ck_fft_xr.cu -- the forward x pass of 512-cell rows with the transform in
-// registers: real rows of the field -> half-spectrum rows, the first pass
-// of the forward transform of Sec. 2.4's convolution.
+// ck_fft_xr.cu -- the x passes of 512-cell rows with the transforms in
+// registers: real rows of the field -> half-spectrum rows (the first pass of
+// the forward transform of Sec. 2.4's convolution) and back (the last pass
+// of the inverse, where the plan keeps the bank).
 //
 // A row of NX = 512 reals is z[n] = x[2n] + i x[2n+1], n < M = 256.  With
 // n = 16 n1 + n2 and k = k1 + 16 k2,
@@ -131,9 +132,121 @@ __global__ void __launch_bounds__(kThreads, 2)
   cp_async_wait<0>();
 }
 
+// The inverse x pass of 512-cell rows: half-spectrum rows X[0..M] (pitch
+// px) -> real rows, z = IDFT_M(Z) (unnormalised) with
+// Z[k] = (X[k] + conj X[M-k]) + i e^{2 pi i k / NX} (X[k] - conj X[M-k]), and
+// x[2m] = Re z[m], x[2m+1] = Im z[m].  Step A unpacks and runs the inverse
+// 16-point DFT over k1 (k = 16 k1 + k2), step B the one over k2, writing
+// z[m1 + 16 m2] straight to the output row.  Rows are visited as in
+// x_c2r_kernel: every row, or the rows of the box's planes of every shell;
+// visited row r is in + row(r) px and goes to out + shell * out_shell_stride
+// + (row in the shell) * NX.
+constexpr int XC_LP = XR_M + 4;  // staged row pitch (float2): X[0..M] and padding
+constexpr size_t XC_STAGE = (size_t)XR_ROWS * XC_LP * sizeof(float2);
+constexpr size_t XC_T_OFF = 2 * XC_STAGE;
+constexpr size_t XC_TWQ_OFF = XC_T_OFF + (size_t)XR_ROWS * XR_TP * sizeof(float2);
+constexpr size_t XC_TWU_OFF = XC_TWQ_OFF + (size_t)XR_TP * sizeof(float2);
+constexpr size_t XC_SMEM = XC_TWU_OFF + (size_t)(XR_M + 1) * sizeof(float2);
+
+__global__ void __launch_bounds__(kThreads, 2)
+    xc2r_reg_kernel(const float2* __restrict__ in, float* __restrict__ out, int px, int64_t rows,
+                    int64_t rows_per_shell, int64_t out_shell_stride, const float2* __restrict__ tw,
+                    const int* __restrict__ box, int ny) {
+  extern __shared__ float4 smem4[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
+  float2* T = reinterpret_cast<float2*>(sm + XC_T_OFF);
+  float2* twq = reinterpret_cast<float2*>(sm + XC_TWQ_OFF);  // [k2][m1]: e^{+2 pi i k2 m1 / M}
+  float2* twu = reinterpret_cast<float2*>(sm + XC_TWU_OFF);  // [k]: e^{+2 pi i k / NX}, k <= M
+  for (int i = threadIdx.x; i < XR_P * XR_P; i += kThreads)
+    twq[(i / XR_P) * (XR_P + 1) + i % XR_P] = cconj(__ldg(tw + 2 * ((i / XR_P) * (i % XR_P))));
+  for (int i = threadIdx.x; i <= XR_M; i += kThreads) twu[i] = cconj(__ldg(tw + i));
+  __syncthreads();  // the tables, before any warp uses them
+
+  // visited rows: every row, or the rows of the planes box[4] .. box[5] of
+  // every shell, numbered q = shell * nrb + row in those planes
+  int64_t count = rows, nrb = rows_per_shell, rb0 = 0;
+  if (box) {
+    nrb = (int64_t)box_len(box[4], box[5]) * ny;
+    rb0 = (int64_t)box[4] * ny;
+    count = (rows / rows_per_shell) * nrb;
+  }
+  auto row_of = [&](int64_t q) -> int64_t {  // the row's index in [shell][rows_per_shell]
+    if (!box) return q;
+    const int64_t sh = q / nrb;
+    return sh * rows_per_shell + rb0 + (q - sh * nrb);
+  };
+  const int64_t ntiles = (count + XR_ROWS - 1) / XR_ROWS;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int half = lane >> 4, j = lane & 15;
+  const int r = 2 * warp + half;
+  constexpr int NPC = XC_LP * (int)sizeof(float2) / 16;  // 16-byte pieces per staged row (px = XC_LP)
+  auto stage = [&](int b, int64_t t) {
+    float2* dst = reinterpret_cast<float2*>(sm + b * XC_STAGE);
+    for (int piece = lane; piece < 2 * NPC; piece += 32) {
+      const int rr = 2 * warp + piece / NPC, off = 2 * (piece % NPC);
+      const int64_t c = t * XR_ROWS + rr;
+      const bool ok = c < count;
+      cp_async16(dst + rr * XC_LP + off, ok ? (const void*)(in + row_of(c) * px + off) : (const void*)in, ok);
+    }
+  };
+  int64_t t = blockIdx.x;
+  if (t < ntiles) stage(0, t);
+  cp_async_commit();
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) stage((it + 1) & 1, tn);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();  // the warp's rows of tile t are staged
+    const float2* xr = reinterpret_cast<const float2*>(sm + (it & 1) * XC_STAGE) + r * XC_LP;
+    float2* tr = T + r * XR_TP;
+    // step A: thread (r, k2 = j): unpack Z[16 k1 + k2], inverse DFT over k1, twiddle
+    {
+      float2 v[XR_P];
+#pragma unroll
+      for (int k1 = 0; k1 < XR_P; ++k1) {
+        const int k = XR_P * k1 + j;
+        const float2 a = xr[k], cb = cconj(xr[XR_M - k]);
+        v[k1] = cadd(cadd(a, cb), cmul_mi<true>(cmul(twu[k], csub(a, cb))));
+      }
+      dft<XR_P, true>(v);
+      const float2* tk = twq + j * (XR_P + 1);
+      tr[j * (XR_P + 1)] = v[0];
+#pragma unroll
+      for (int m1 = 1; m1 < XR_P; ++m1) tr[j * (XR_P + 1) + m1] = cmul(v[m1], tk[m1]);
+    }
+    __syncwarp();  // T of the warp's rows complete
+    // step B: thread (r, m1 = j): z[m1 + 16 m2] -> cells 2 (m1 + 16 m2), + 1
+    const int64_t c = t * XR_ROWS + r;
+    {
+      float2 z[XR_P];
+#pragma unroll
+      for (int k2 = 0; k2 < XR_P; ++k2) z[k2] = tr[k2 * (XR_P + 1) + j];
+      dft<XR_P, true>(z);
+      if (c < count) {
+        const int64_t row = row_of(c), sh = row / rows_per_shell, rr = row - sh * rows_per_shell;
+        float* orow = out + sh * out_shell_stride + rr * XR_NX + 2 * j;
+#pragma unroll
+        for (int m2 = 0; m2 < XR_P; ++m2) *reinterpret_cast<float2*>(orow + 2 * XR_P * m2) = z[m2];
+      }
+    }
+    __syncwarp();  // T and the staged rows read before they are written again
+  }
+  cp_async_wait<0>();
+}
+
 }  // namespace
 
-size_t xr2c_reg_smem() { return XR_SMEM; }
+void launch_xc2r_reg(const float2* in, float* out, int px, int64_t rows, int64_t rows_per_shell,
+                     int64_t out_shell_stride, const float2* tw, int sm_count, cudaStream_t st, const int* box,
+                     int ny) {
+  const int64_t ntiles = (rows + XR_ROWS - 1) / XR_ROWS;  // the grid covers every row; a box visits fewer
+  allow_smem(xc2r_reg_kernel, XC_SMEM);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)2 * sm_count));
+  xc2r_reg_kernel<<<grid, kThreads, XC_SMEM, st>>>(in, out, px, rows, rows_per_shell, out_shell_stride, tw, box,
+                                                   ny);
+}
 
 void launch_xr2c_reg(const float* in, float2* out, int px, int64_t rows, const float2* tw, int sm_count,
                      cudaStream_t st, const int* box, int ny) {
