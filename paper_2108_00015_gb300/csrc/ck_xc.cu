@@ -36,12 +36,14 @@ size_t xc_smem_bytes(int M, int ns_pad) {
 }
 
 // Per-CTA partials of the padded layout -> packed per-order sums of the
-// plan's shells, summed over CTAs in CTA order.
+// plan's shells, summed over CTAs in a fixed order (one warp per output).
 __global__ void reduce_xc_kernel(const double* __restrict__ partials, int ctas, int nout_pad, int ns_pad, int ns,
                                  int max_order, int64_t base2, int64_t base3, double* __restrict__ out) {
   const int n2 = ns, n3 = max_order >= 3 ? ns * (ns + 1) / 2 : 0;
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n2 + n3) return;
+  // one warp per output
+  const int o = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (o >= n2 + n3) return;  // whole warps
   int src;
   int64_t dst;
   if (o < n2) {
@@ -58,19 +60,13 @@ __global__ void reduce_xc_kernel(const double* __restrict__ partials, int ctas, 
     src = ns_pad + a * ns_pad - a * (a - 1) / 2 + (b - a);
     dst = base3 + (o - n2);
   }
-  // in CTA order; sixteen loads in flight before their adds (same order,
-  // the same sum)
+  // a fixed order: lane l adds the CTAs l, l + 32, ... in turn, then the
+  // lanes' sums combine in a fixed butterfly (the same sum on every run)
   double s = 0.0;
-  int c = 0;
-  for (; c + 16 <= ctas; c += 16) {
-    double v[16];
+  for (int c = lane; c < ctas; c += 32) s += __ldg(partials + (int64_t)c * nout_pad + src);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __ldg(partials + (int64_t)(c + k) * nout_pad + src);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) s += v[k];
-  }
-  for (; c < ctas; ++c) s += partials[(int64_t)c * nout_pad + src];
-  out[dst] = s;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+  if (lane == 0) out[dst] = s;
 }
 
 ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaStream_t st, const int* box) {
@@ -108,8 +104,8 @@ ck_status launch_convolve_contract(Plan& p, const float* w0, double* sums, cudaS
   if (e != cudaSuccess) return cuda_status(e);
   ProfScope ps2(p, ST_REDUCE, 8.0 * (double)ctas * nout_pad, st);
   const int nkeep = p.ns + (p.max_order >= 3 ? p.ns * (p.ns + 1) / 2 : 0);
-  reduce_xc_kernel<<<(nkeep + 127) / 128, 128, 0, st>>>(p.partials, ctas, nout_pad, ns_pad, p.ns, p.max_order,
-                                                       p.multiset_base[2], p.multiset_base[3], sums);
+  reduce_xc_kernel<<<(nkeep + 3) / 4, 128, 0, st>>>(p.partials, ctas, nout_pad, ns_pad, p.ns, p.max_order,
+                                                   p.multiset_base[2], p.multiset_base[3], sums);
   return cuda_status(cudaGetLastError());
 }
 
